@@ -1,0 +1,847 @@
+/*
+ * CPU oracle for the compressed full-amplitude simulator (test infrastructure).
+ *
+ * This file is the slow, plain, obviously-correct CPU statement of what the
+ * GPU library computes.  Only the test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load it; the product path never does.
+ * It shares no code, header or table with the CUDA library.
+ *
+ * Contents
+ *   O1  dense simulator: the pair / quad update of Sec. II (single-qubit
+ *       gate on qubit k, controlled gate), applied to a full 2^n vector.
+ *   O2  tile codec: the amplitude-aware, point-wise relative error-bounded
+ *       codec (Sec. III, SZ with a relative bound as in ref. [xin2018]) in
+ *       the stream format below, plus the lossless level and the AALC
+ *       error-bound ladder of Algorithm 2.
+ *   O3  compressed simulator: Algorithm 2 (decompress, normalize, gate
+ *       computation, compress with the error-bound ladder) over tiles, one
+ *       sweep (a run of gates) at a time.
+ *   N   the state norm used by "normalize": the exact sum of |a|^2 in
+ *       fixed point (units of 2^-112), rounded once to double.
+ *
+ * Arithmetic conventions (both the oracle and the GPU follow them, each in
+ * its own code):
+ *   - a matrix row is evaluated over its exactly-nonzero entries in column
+ *     order; the first term is a product, later terms are fused
+ *     multiply-adds; an entry with zero imaginary part is "real", one with
+ *     zero real part "imaginary", any other "general" (see row_eval);
+ *   - compiled with -ffp-contract=off so that only the fma() calls fuse.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+typedef unsigned __int128 u128;
+
+/* ------------------------------------------------------------------ */
+/* gates                                                               */
+/* ------------------------------------------------------------------ */
+
+/* One gate: k targets (1 or 2), controls as a mask over global index
+ * bits with the required values, and the 2^k x 2^k complex matrix in
+ * row-major order with (re, im) interleaved.  Sub-index bit i of a row or
+ * column selects the value of qubit t[i]. */
+typedef struct {
+    int32_t k;
+    int32_t t[2];
+    int32_t pad;
+    uint64_t cmask;
+    uint64_t cval;
+    double m[32];
+} or_gate;
+
+/* y = u * x for one matrix entry u (Sec. II pair update, one term). */
+static void term_first(double ur, double ui, double xr, double xi,
+                       double *yr, double *yi)
+{
+    if (ui == 0.0) {            /* real entry */
+        *yr = ur * xr;
+        *yi = ur * xi;
+    } else if (ur == 0.0) {     /* imaginary entry: (i ui)(xr + i xi) */
+        *yr = -(ui * xi);
+        *yi = ui * xr;
+    } else {                    /* general entry */
+        *yr = fma(ur, xr, -(ui * xi));
+        *yi = fma(ur, xi, ui * xr);
+    }
+}
+
+/* acc += u * x for one matrix entry u. */
+static void term_acc(double ur, double ui, double xr, double xi,
+                     double *ar, double *ai)
+{
+    if (ui == 0.0) {
+        *ar = fma(ur, xr, *ar);
+        *ai = fma(ur, xi, *ai);
+    } else if (ur == 0.0) {
+        *ar = fma(-ui, xi, *ar);
+        *ai = fma(ui, xr, *ai);
+    } else {
+        *ar = fma(ur, xr, fma(-ui, xi, *ar));
+        *ai = fma(ur, xi, fma(ui, xr, *ai));
+    }
+}
+
+/* Row r of y = U x over the present sub-indices, skipping exactly-zero
+ * entries.  A row with no nonzero present entry gives +0. */
+static void row_eval(const double *m, int dim, int r, const double *x,
+                     const int *present, double *yr, double *yi)
+{
+    int first = 1;
+    double ar = 0.0, ai = 0.0;
+    for (int c = 0; c < dim; ++c) {
+        if (!present[c]) continue;
+        double ur = m[2 * (r * dim + c)], ui = m[2 * (r * dim + c) + 1];
+        if (ur == 0.0 && ui == 0.0) continue;
+        if (first) {
+            term_first(ur, ui, x[2 * c], x[2 * c + 1], &ar, &ai);
+            first = 0;
+        } else {
+            term_acc(ur, ui, x[2 * c], x[2 * c + 1], &ar, &ai);
+        }
+    }
+    *yr = ar;
+    *yi = ai;
+}
+
+static int gate_is_diagonal(const or_gate *g)
+{
+    int dim = 1 << g->k;
+    for (int r = 0; r < dim; ++r)
+        for (int c = 0; c < dim; ++c)
+            if (r != c && (g->m[2 * (r * dim + c)] != 0.0 ||
+                           g->m[2 * (r * dim + c) + 1] != 0.0))
+                return 0;
+    return 1;
+}
+
+/*
+ * Apply one gate to a buffer of 2^mb amplitudes (re, im interleaved).
+ * Buffer index bit p holds global qubit qb[p]; every other qubit has the
+ * value it has in 'fixed' (bits at global positions).  A target that is
+ * not in the buffer is allowed only for a diagonal gate.
+ * Returns 0, or -1 when a non-diagonal gate has a target outside the buffer.
+ */
+static int apply_gate_buf(double *a, int mb, const int *qb, uint64_t fixed,
+                          const or_gate *g)
+{
+    int k = g->k, dim = 1 << k;
+    int pos[2] = {-1, -1};
+    for (int i = 0; i < k; ++i)
+        for (int p = 0; p < mb; ++p)
+            if (qb[p] == g->t[i]) pos[i] = p;
+    int diag = gate_is_diagonal(g);
+    for (int i = 0; i < k; ++i)
+        if (pos[i] < 0 && !diag) return -1;
+
+    uint64_t nb = 1ull << mb;
+    double x[8], y[8];
+    int present[4];
+    uint64_t idx[4];
+    for (uint64_t l = 0; l < nb; ++l) {
+        int skip = 0;
+        for (int i = 0; i < k; ++i)
+            if (pos[i] >= 0 && ((l >> pos[i]) & 1)) skip = 1;
+        if (skip) continue;
+        uint64_t gl = fixed;
+        for (int p = 0; p < mb; ++p)
+            if ((l >> p) & 1) gl |= 1ull << qb[p];
+        if ((gl & g->cmask) != g->cval) continue;
+        /* gather the sub-vector; sub-indices whose fixed target bits do
+         * not match this buffer are absent */
+        for (int s = 0; s < dim; ++s) {
+            present[s] = 1;
+            idx[s] = l;
+            for (int i = 0; i < k; ++i) {
+                int bit = (s >> i) & 1;
+                if (pos[i] >= 0) {
+                    if (bit) idx[s] |= 1ull << pos[i];
+                } else if ((int)((fixed >> g->t[i]) & 1) != bit) {
+                    present[s] = 0;
+                }
+            }
+            if (present[s]) {
+                x[2 * s] = a[2 * idx[s]];
+                x[2 * s + 1] = a[2 * idx[s] + 1];
+            } else {
+                x[2 * s] = 0.0;
+                x[2 * s + 1] = 0.0;
+            }
+        }
+        for (int r = 0; r < dim; ++r)
+            if (present[r]) row_eval(g->m, dim, r, x, present, &y[2 * r], &y[2 * r + 1]);
+        for (int r = 0; r < dim; ++r)
+            if (present[r]) {
+                a[2 * idx[r]] = y[2 * r];
+                a[2 * idx[r] + 1] = y[2 * r + 1];
+            }
+    }
+    return 0;
+}
+
+/* O1: apply a gate to a dense 2^n state (qubit j <-> index bit j). */
+int or_dense_apply(double *psi, int n, const or_gate *g)
+{
+    int qb[64];
+    for (int p = 0; p < n; ++p) qb[p] = p;
+    return apply_gate_buf(psi, n, qb, 0, g);
+}
+
+/* ------------------------------------------------------------------ */
+/* norm: exact sum of squares in units of 2^-112                        */
+/* ------------------------------------------------------------------ */
+
+#define NORM_FRAC 112
+
+static uint64_t dbits(double x) { uint64_t u; memcpy(&u, &x, 8); return u; }
+static double bitsd(uint64_t u) { double x; memcpy(&x, &u, 8); return x; }
+
+/* floor(x^2 * 2^112).  Sets *range when |x| >= 16 (outside the format). */
+static u128 sq_units(double x, int *range)
+{
+    uint64_t u = dbits(x) & 0x7FFFFFFFFFFFFFFFull;
+    uint64_t E = u >> 52, F = u & 0xFFFFFFFFFFFFFull;
+    if (E >= 2047) { *range = 1; return 0; }
+    uint64_t mant = E ? (F | (1ull << 52)) : F;
+    int64_t Ee = E ? (int64_t)E : 1;
+    if (Ee > 1026) { *range = 1; return 0; }
+    u128 m2 = (u128)mant * (u128)mant;              /* < 2^106 */
+    int64_t sh = 2 * Ee - 2150 + NORM_FRAC;           /* x^2 = m2 * 2^(2Ee-2150) */
+    if (sh >= 0) return m2 << sh;
+    if (-sh >= 106) return 0;
+    return m2 >> (-sh);
+}
+
+/* Correctly rounded double of S * 2^-112. */
+static double units_to_double(u128 S)
+{
+    if (S == 0) return 0.0;
+    int p = 0;
+    for (u128 t = S; t; t >>= 1) ++p;                 /* bit length */
+    uint64_t top;
+    int e;
+    if (p <= 64) {
+        top = (uint64_t)S;
+        e = 0;
+    } else {
+        int drop = p - 64;
+        u128 rest = S & (((u128)1 << drop) - 1);
+        top = (uint64_t)(S >> drop) | (rest != 0);    /* sticky bit */
+        e = drop;
+    }
+    /* top has at most 64 bits; conversion to double rounds to nearest even */
+    return ldexp((double)top, e - NORM_FRAC);
+}
+
+/* exact sum of squares of 2*count components (interleaved or not) */
+static u128 sum_sq(const double *a, uint64_t ncomp, int *range)
+{
+    u128 S = 0;
+    for (uint64_t i = 0; i < ncomp; ++i) S += sq_units(a[i], range);
+    return S;
+}
+
+void or_sum_sq(const double *a, uint64_t ncomp, uint64_t *lo, uint64_t *hi,
+               int *range)
+{
+    int r = 0;
+    u128 S = sum_sq(a, ncomp, &r);
+    *lo = (uint64_t)S;
+    *hi = (uint64_t)(S >> 64);
+    *range = r;
+}
+
+double or_units_to_double(uint64_t lo, uint64_t hi)
+{
+    return units_to_double(((u128)hi << 64) | lo);
+}
+
+/* ------------------------------------------------------------------ */
+/* O2: tile codec                                                      */
+/* ------------------------------------------------------------------ */
+
+
+/*
+ * Tile stream format (little-endian).  A tile is 2^c amplitudes; its two
+ * component streams (re, im) each hold N = 2^c doubles, cut into
+ * G = max(1, N/32) groups of L = min(N, 32) consecutive values.
+ *
+ * Header, 32 bytes:
+ *   [0] mode: 0 CONST, 1 PACKED, 2 RAW      [1] shift s (0..52; 0 in RAW)
+ *   [2] ladder level                          [3] sign modes: bits 0-1 re, 2-3 im
+ *   [4..7]  body length in bytes (multiple of 16)
+ *   [8..15] anchor q_0 of re                  [16..23] anchor q_0 of im
+ *   [24] c                                    [25..31] zero
+ * Codes: B = magnitude bits of x (bits 0-62), q = (B + 2^(s-1)) >> s
+ * (q = B when s = 0); reconstruction x^ = (q << s) | sign << 63.
+ * Residuals r_0 = 0, r_i = q_i - q_{i-1} (mod 2^64); z = zigzag(r).
+ * Group width w = bit length of the OR of its z values.
+ * Sign word of a group: bit l = sign of value l.  Sign modes:
+ *   0 all clear, 1 all set, 2 pattern (u32 P = word of group 0, then
+ *   ceil(G/32) u32 flip words, bit g set when word g == ~P), 3 G u32 words.
+ * CONST: body empty; every value of a component is (anchor << s) with the
+ *   uniform sign of its sign mode (0 or 1).
+ * PACKED body: re sign section, im sign section, G width bytes of re, G of
+ *   im, zero pad to 4, then for re then im, group by group, ceil(L*w/32)
+ *   u32 words holding the group's bit string (value l at bits
+ *   [l*w, (l+1)*w), LSB first); zero pad to 16.
+ * RAW body: the 2N doubles in memory order (re, im interleaved).
+ * Mode rule at one level: CONST when every z is 0 and both sign modes are
+ * 0 or 1; else PACKED when its body is shorter than 16N; else RAW.
+ */
+#define HDR 32
+enum { M_CONST = 0, M_PACKED = 1, M_RAW = 2 };
+enum { S_CLEAR = 0, S_SET = 1, S_PATTERN = 2, S_WORDS = 3 };
+#define MAG 0x7FFFFFFFFFFFFFFFull
+#define MIN_NORMAL 0x0010000000000000ull
+#define LOSSY_LIMIT 0x7FE0000000000000ull   /* |x| < 2^1023 */
+#define INF_BITS 0x7FF0000000000000ull
+
+/* flags reported by the encoder */
+#define OR_F_NONFINITE 1
+#define OR_F_FORCED_LOSSLESS 2
+
+/* Largest shift s in [0, 52] whose bound 2^(s-53) is <= eps; 0 when
+ * eps < 2^-53.  Quantising the magnitude bits with shift s moves them by
+ * at most 2^(s-1) units, which changes |x| by less than 2^(s-53)|x| (one
+ * unit weighs at most 2^-52 |x| inside a binade, and a rounding that
+ * crosses a binade boundary keeps the same bound). */
+int or_shift_for_eps(double eps)
+{
+    for (int s = 52; s >= 1; --s)
+        if (ldexp(1.0, s - 53) <= eps) return s;
+    return 0;
+}
+
+static uint64_t quant(uint64_t B, int s)
+{
+    return s == 0 ? B : (B + (1ull << (s - 1))) >> s;
+}
+
+static int bitlen64(uint64_t v)
+{
+    int b = 0;
+    while (v) { ++b; v >>= 1; }
+    return b;
+}
+
+static void put32(uint8_t *p, uint32_t v) { for (int i = 0; i < 4; ++i) p[i] = (uint8_t)(v >> (8 * i)); }
+static void put64(uint8_t *p, uint64_t v) { for (int i = 0; i < 8; ++i) p[i] = (uint8_t)(v >> (8 * i)); }
+static uint32_t get32(const uint8_t *p) { uint32_t v = 0; for (int i = 3; i >= 0; --i) v = (v << 8) | p[i]; return v; }
+static uint64_t get64(const uint8_t *p) { uint64_t v = 0; for (int i = 7; i >= 0; --i) v = (v << 8) | p[i]; return v; }
+
+static size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+static size_t sign_bytes(int mode, int G)
+{
+    switch (mode) {
+    case S_PATTERN: return 4 + 4 * (size_t)((G + 31) / 32);
+    case S_WORDS: return 4 * (size_t)G;
+    default: return 0;
+    }
+}
+
+/* bound on any stream for a tile of 2^c amplitudes */
+size_t or_stream_cap(int c)
+{
+    return HDR + 16 * ((size_t)1 << c) + 64;
+}
+
+/*
+ * Encode one tile of 2^c amplitudes (re, im interleaved) at quantisation
+ * shift s, as ladder level 'level'.  Writes the stream to out and returns
+ * its length in bytes.
+ */
+static size_t encode_at(const double *a, int c, int s, int level, uint8_t *out)
+{
+    uint64_t N = 1ull << c;
+    int G = N >= 32 ? (int)(N / 32) : 1;
+    int L = N >= 32 ? 32 : (int)N;
+
+    uint64_t *q[2], *z[2];
+    uint32_t *sw[2];
+    int *w[2];
+    int smode[2];
+    for (int k = 0; k < 2; ++k) {
+        q[k] = malloc(N * 8);
+        z[k] = malloc(N * 8);
+        sw[k] = calloc((size_t)G, 4);
+        w[k] = calloc((size_t)G, sizeof(int));
+    }
+    int allzero = 1;
+    for (int k = 0; k < 2; ++k) {
+        int any0 = 0, any1 = 0;
+        for (uint64_t i = 0; i < N; ++i) {
+            uint64_t u = dbits(a[2 * i + k]);
+            uint64_t sg = u >> 63;
+            q[k][i] = quant(u & MAG, s);
+            if (sg) { sw[k][i / 32] |= 1u << (i % 32); any1 = 1; } else any0 = 1;
+        }
+        /* Lorenzo (order 1) residuals on the integer codes, then zigzag */
+        for (uint64_t i = 0; i < N; ++i) {
+            uint64_t r = i == 0 ? 0 : q[k][i] - q[k][i - 1];
+            z[k][i] = (r << 1) ^ (uint64_t)((int64_t)r >> 63);
+            if (z[k][i]) allzero = 0;
+        }
+        for (int g = 0; g < G; ++g) {
+            uint64_t o = 0;
+            for (int l = 0; l < L; ++l) o |= z[k][(uint64_t)g * 32 + l];
+            w[k][g] = bitlen64(o);
+        }
+        if (!any1) smode[k] = S_CLEAR;
+        else if (!any0) smode[k] = S_SET;
+        else {
+            int pat = G >= 2;
+            for (int g = 1; g < G && pat; ++g)
+                if (sw[k][g] != sw[k][0] && sw[k][g] != ~sw[k][0]) pat = 0;
+            smode[k] = pat ? S_PATTERN : S_WORDS;
+        }
+    }
+
+    size_t raw_body = 16 * N;
+    int mode;
+    size_t body;
+    size_t data_words = 0;
+    for (int k = 0; k < 2; ++k)
+        for (int g = 0; g < G; ++g)
+            data_words += ((size_t)L * w[k][g] + 31) / 32;
+    size_t meta = sign_bytes(smode[0], G) + sign_bytes(smode[1], G);
+    size_t wbytes = round_up(2 * (size_t)G, 4);
+    size_t packed_body = round_up(meta + wbytes + 4 * data_words, 16);
+
+    if (allzero && smode[0] <= S_SET && smode[1] <= S_SET) {
+        mode = M_CONST;
+        body = 0;
+    } else if (packed_body < raw_body) {
+        mode = M_PACKED;
+        body = packed_body;
+    } else {
+        mode = M_RAW;
+        body = raw_body;
+    }
+
+    memset(out, 0, HDR + body);
+    out[0] = (uint8_t)mode;
+    out[1] = (uint8_t)(mode == M_RAW ? 0 : s);
+    out[2] = (uint8_t)level;
+    out[3] = (uint8_t)(mode == M_RAW ? 0 : (smode[0] | (smode[1] << 2)));
+    put32(out + 4, (uint32_t)body);
+    if (mode != M_RAW) {
+        put64(out + 8, q[0][0]);
+        put64(out + 16, q[1][0]);
+    }
+    out[24] = (uint8_t)c;
+
+    uint8_t *b = out + HDR;
+    if (mode == M_RAW) {
+        for (uint64_t i = 0; i < 2 * N; ++i) put64(b + 8 * i, dbits(a[i]));
+    } else if (mode == M_PACKED) {
+        size_t off = 0;
+        for (int k = 0; k < 2; ++k) {
+            if (smode[k] == S_PATTERN) {
+                put32(b + off, sw[k][0]);
+                off += 4;
+                for (int g = 0; g < G; ++g)
+                    if (sw[k][g] != sw[k][0]) {
+                        size_t wo = off + 4 * (size_t)(g / 32);
+                        put32(b + wo, get32(b + wo) | (1u << (g % 32)));
+                    }
+                off += 4 * (size_t)((G + 31) / 32);
+            } else if (smode[k] == S_WORDS) {
+                for (int g = 0; g < G; ++g) { put32(b + off, sw[k][g]); off += 4; }
+            }
+        }
+        for (int k = 0; k < 2; ++k)
+            for (int g = 0; g < G; ++g) b[off++] = (uint8_t)w[k][g];
+        off = round_up(off, 4);
+        /* lane-major bit packing: value l of a group occupies bits
+         * [l*w, (l+1)*w) of the group's little-endian bit string */
+        for (int k = 0; k < 2; ++k)
+            for (int g = 0; g < G; ++g) {
+                int wg = w[k][g];
+                size_t nwords = ((size_t)L * wg + 31) / 32;
+                for (int l = 0; l < L; ++l) {
+                    uint64_t v = z[k][(uint64_t)g * 32 + l];
+                    for (int bit = 0; bit < wg; ++bit)
+                        if ((v >> bit) & 1) {
+                            size_t pos = (size_t)l * wg + bit;
+                            b[off + pos / 8] |= (uint8_t)(1u << (pos % 8));
+                        }
+                }
+                off += 4 * nwords;
+            }
+    }
+    for (int k = 0; k < 2; ++k) { free(q[k]); free(z[k]); free(sw[k]); free(w[k]); }
+    return HDR + body;
+}
+
+/*
+ * Encode one tile with the error-bound ladder of Algorithm 2: try the
+ * levels in order (shifts[0..nlev-1], shifts[0] usually 0 = lossless) and
+ * keep the first stream whose size is <= max_bytes (ratio >= theta, with
+ * max_bytes = floor(16*2^c / theta)); if none qualifies, keep the last.
+ * A tile holding a value outside the lossy range (subnormal, |x| >= 2^1023)
+ * is coded with shift 0 at every level; a non-finite value forces RAW and
+ * sets OR_F_NONFINITE.  out must hold or_stream_cap(c) bytes.
+ */
+size_t or_encode_tile(const double *a, int c, const int *shifts, int nlev,
+                      uint64_t max_bytes, uint8_t *out, int *level, int *flags)
+{
+    uint64_t N = 1ull << c;
+    int nonfinite = 0, eligible = 1;
+    for (uint64_t i = 0; i < 2 * N; ++i) {
+        uint64_t B = dbits(a[i]) & MAG;
+        if (B >= INF_BITS) nonfinite = 1;
+        else if (B != 0 && (B < MIN_NORMAL || B >= LOSSY_LIMIT)) eligible = 0;
+    }
+    *flags = 0;
+    if (nonfinite) {
+        /* RAW keeps the bits; the caller reports the error */
+        size_t len = HDR + 16 * N;
+        memset(out, 0, len);
+        out[0] = M_RAW;
+        out[2] = 0;
+        put32(out + 4, (uint32_t)(16 * N));
+        out[24] = (uint8_t)c;
+        for (uint64_t i = 0; i < 2 * N; ++i) put64(out + HDR + 8 * i, dbits(a[i]));
+        *level = 0;
+        *flags = OR_F_NONFINITE;
+        return len;
+    }
+    if (!eligible) *flags |= OR_F_FORCED_LOSSLESS;
+    size_t len = 0;
+    for (int k = 0; k < nlev; ++k) {
+        int s = eligible ? shifts[k] : 0;
+        len = encode_at(a, c, s, k, out);
+        *level = k;
+        if ((uint64_t)len <= max_bytes) break;
+    }
+    return len;
+}
+
+/*
+ * Decode one stream into 2^c amplitudes.  Returns 0, or a negative code
+ * when the stream is malformed (nothing is read past len).
+ */
+int or_decode_tile(const uint8_t *in, size_t len, int c, double *a)
+{
+    if (len < HDR) return -1;
+    uint64_t N = 1ull << c;
+    int G = N >= 32 ? (int)(N / 32) : 1;
+    int L = N >= 32 ? 32 : (int)N;
+    int mode = in[0], s = in[1];
+    int sm[2] = {in[3] & 3, (in[3] >> 2) & 3};
+    size_t body = get32(in + 4);
+    if (in[24] != (uint8_t)c) return -2;
+    if (HDR + body > len) return -3;
+    uint64_t anchor[2] = {get64(in + 8), get64(in + 16)};
+    const uint8_t *b = in + HDR;
+    if (mode == M_RAW) {
+        if (body != 16 * N) return -4;
+        for (uint64_t i = 0; i < 2 * N; ++i) a[i] = bitsd(get64(b + 8 * i));
+        return 0;
+    }
+    if (s > 52) return -5;
+    if (mode == M_CONST) {
+        if (body != 0 || sm[0] > S_SET || sm[1] > S_SET) return -6;
+        for (int k = 0; k < 2; ++k) {
+            uint64_t v = (anchor[k] << s) | ((uint64_t)sm[k] << 63);
+            for (uint64_t i = 0; i < N; ++i) a[2 * i + k] = bitsd(v);
+        }
+        return 0;
+    }
+    if (mode != M_PACKED) return -7;
+    size_t off = 0;
+    uint32_t *sw[2];
+    for (int k = 0; k < 2; ++k) sw[k] = calloc((size_t)G, 4);
+    int rc = 0;
+    for (int k = 0; k < 2 && rc == 0; ++k) {
+        size_t need = sign_bytes(sm[k], G);
+        if (off + need > body) { rc = -8; break; }
+        uint32_t lanes = L == 32 ? 0xFFFFFFFFu : ((1u << L) - 1);
+        for (int g = 0; g < G; ++g) {
+            if (sm[k] == S_CLEAR) sw[k][g] = 0;
+            else if (sm[k] == S_SET) sw[k][g] = lanes;
+            else if (sm[k] == S_PATTERN) {
+                uint32_t P = get32(b + off);
+                uint32_t fl = (get32(b + off + 4 + 4 * (size_t)(g / 32)) >> (g % 32)) & 1;
+                sw[k][g] = fl ? ~P : P;
+            } else sw[k][g] = get32(b + off + 4 * (size_t)g);
+        }
+        off += need;
+    }
+    int *w[2] = {NULL, NULL};
+    if (rc == 0) {
+        if (off + 2 * (size_t)G > body) rc = -9;
+    }
+    if (rc == 0) {
+        for (int k = 0; k < 2; ++k) {
+            w[k] = calloc((size_t)G, sizeof(int));
+            for (int g = 0; g < G; ++g) {
+                w[k][g] = b[off + (size_t)k * G + g];
+                if (w[k][g] > 64) rc = -10;
+            }
+        }
+        off = round_up(off + 2 * (size_t)G, 4);
+    }
+    for (int k = 0; k < 2 && rc == 0; ++k) {
+        uint64_t q = anchor[k];
+        for (int g = 0; g < G && rc == 0; ++g) {
+            int wg = w[k][g];
+            size_t nwords = ((size_t)L * wg + 31) / 32;
+            if (off + 4 * nwords > body) { rc = -11; break; }
+            for (int l = 0; l < L; ++l) {
+                uint64_t v = 0;
+                for (int bit = 0; bit < wg; ++bit) {
+                    size_t pos = (size_t)l * wg + bit;
+                    v |= (uint64_t)((b[off + pos / 8] >> (pos % 8)) & 1) << bit;
+                }
+                uint64_t r = (v >> 1) ^ (0 - (v & 1));   /* un-zigzag */
+                uint64_t i = (uint64_t)g * 32 + l;
+                if (i > 0) q += r;                        /* inclusive prefix sum */
+                uint64_t sg = (sw[k][g] >> l) & 1;
+                a[2 * i + k] = bitsd((q << s) | (sg << 63));
+            }
+            off += 4 * nwords;
+        }
+    }
+    for (int k = 0; k < 2; ++k) { free(sw[k]); free(w[k]); }
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* O3: compressed simulator (Algorithm 2 over tiles)                    */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int n, c, nlev, normalize, err;
+    int shifts[8];
+    uint64_t max_bytes;
+    uint64_t ntiles;
+    uint8_t **st;
+    uint32_t *len;
+    u128 *part;          /* per-tile sum of squares of the stored values */
+    double alpha;        /* scale applied at the next decode ("normalize") */
+    uint64_t hist[8];    /* ladder level of every tile written */
+    uint64_t items_done, items_skipped;
+} or_csim;
+
+static void csim_store(or_csim *cs, uint64_t t, const double *amps)
+{
+    int c = cs->c, level = 0, flags = 0;
+    uint64_t N = 1ull << c;
+    uint8_t *buf = malloc(or_stream_cap(c));
+    size_t len = or_encode_tile(amps, c, cs->shifts, cs->nlev, cs->max_bytes,
+                                buf, &level, &flags);
+    if (flags & OR_F_NONFINITE) cs->err |= 1;
+    free(cs->st[t]);
+    cs->st[t] = realloc(buf, len);
+    cs->len[t] = (uint32_t)len;
+    cs->hist[level] += 1;
+    /* the norm of what the next decode returns */
+    double *rec = malloc(N * 16);
+    or_decode_tile(cs->st[t], len, c, rec);
+    int range = 0;
+    cs->part[t] = sum_sq(rec, 2 * N, &range);
+    if (range) cs->err |= 2;
+    free(rec);
+}
+
+static void csim_update_alpha(or_csim *cs)
+{
+    if (!cs->normalize) { cs->alpha = 1.0; return; }
+    u128 S = 0;
+    for (uint64_t t = 0; t < cs->ntiles; ++t) S += cs->part[t];
+    double nrm = units_to_double(S);
+    cs->alpha = nrm > 0.0 ? 1.0 / sqrt(nrm) : 1.0;
+}
+
+or_csim *or_csim_new(int n, int c, const int *shifts, int nlev,
+                     uint64_t max_bytes, int normalize)
+{
+    if (c > n || nlev < 1 || nlev > 8) return NULL;
+    or_csim *cs = calloc(1, sizeof(or_csim));
+    cs->n = n;
+    cs->c = c;
+    cs->nlev = nlev;
+    for (int i = 0; i < nlev; ++i) cs->shifts[i] = shifts[i];
+    cs->max_bytes = max_bytes;
+    cs->normalize = normalize;
+    cs->ntiles = 1ull << (n - c);
+    cs->st = calloc(cs->ntiles, sizeof(uint8_t *));
+    cs->len = calloc(cs->ntiles, sizeof(uint32_t));
+    cs->part = calloc(cs->ntiles, sizeof(u128));
+    cs->alpha = 1.0;
+    return cs;
+}
+
+void or_csim_free(or_csim *cs)
+{
+    if (!cs) return;
+    for (uint64_t t = 0; t < cs->ntiles; ++t) free(cs->st[t]);
+    free(cs->st);
+    free(cs->len);
+    free(cs->part);
+    free(cs);
+}
+
+/* state |x>: every tile encoded from its dense values */
+void or_csim_reset_basis(or_csim *cs, uint64_t x)
+{
+    uint64_t N = 1ull << cs->c;
+    double *amps = calloc(N, 16);
+    for (uint64_t t = 0; t < cs->ntiles; ++t) {
+        memset(amps, 0, N * 16);
+        if ((x >> cs->c) == t) amps[2 * (x & (N - 1))] = 1.0;
+        csim_store(cs, t, amps);
+    }
+    free(amps);
+    memset(cs->hist, 0, sizeof cs->hist);
+    cs->err = 0;
+    csim_update_alpha(cs);
+}
+
+/* Does gate g change any amplitude of the item whose non-buffer qubits
+ * (mask fmask) have the values in 'fixed'? */
+static int gate_touches(const or_gate *g, uint64_t fixed, uint64_t fmask)
+{
+    if (((fixed ^ g->cval) & g->cmask & fmask) != 0) return 0;
+    int allfixed = 1;
+    for (int i = 0; i < g->k; ++i)
+        if (!((fmask >> g->t[i]) & 1)) allfixed = 0;
+    if (allfixed) {
+        int dim = 1 << g->k, r = 0;
+        for (int i = 0; i < g->k; ++i) r |= (int)((fixed >> g->t[i]) & 1) << i;
+        if (g->m[2 * (r * dim + r)] == 1.0 && g->m[2 * (r * dim + r) + 1] == 0.0) return 0;
+    }
+    return 1;
+}
+
+/*
+ * One sweep: the gates g[0..ng-1] applied to every item.  An item is the
+ * group of 2^h tiles whose tile indices differ only in the bits of the
+ * high qubits H[0..h-1] (ascending, each >= c); its buffer index is
+ * (member j) * 2^c + (low index), member bit i <-> qubit H[i].
+ * Per item (Algorithm 2): decompress its tiles, normalize (multiply by the
+ * scale of the previous sweep when that scale is not 1), apply the gates in
+ * order, compress every tile with the ladder.  An item that no gate
+ * touches is kept as it is when the scale is 1.
+ * Returns 0, or -1 on a malformed stream, -2 on a gate that needs a
+ * target outside the item.
+ */
+int or_csim_sweep(or_csim *cs, const or_gate *g, int ng, const int *H, int h)
+{
+    int c = cs->c, n = cs->n, mb = c + h;
+    uint64_t N = 1ull << c;
+    int qb[64];
+    for (int p = 0; p < c; ++p) qb[p] = p;
+    uint64_t hmask_tile = 0;
+    for (int i = 0; i < h; ++i) {
+        qb[c + i] = H[i];
+        hmask_tile |= 1ull << (H[i] - c);
+    }
+    uint64_t fmask = 0;                          /* fixed qubits of an item */
+    for (int q = c; q < n; ++q) fmask |= 1ull << q;
+    for (int i = 0; i < h; ++i) fmask &= ~(1ull << H[i]);
+
+    double alpha = cs->alpha;
+    double *buf = malloc(((size_t)1 << mb) * 16);
+    int rc = 0;
+    for (uint64_t T = 0; T < cs->ntiles && rc == 0; ++T) {
+        if (T & hmask_tile) continue;
+        uint64_t fixed = T << c;
+        int touched = alpha != 1.0;
+        for (int i = 0; i < ng && !touched; ++i)
+            if (gate_touches(&g[i], fixed, fmask)) touched = 1;
+        if (!touched) { cs->items_skipped++; continue; }
+        cs->items_done++;
+        for (uint64_t j = 0; j < (1ull << h); ++j) {
+            uint64_t Tj = T;
+            for (int i = 0; i < h; ++i)
+                if ((j >> i) & 1) Tj |= 1ull << (H[i] - c);
+            if (or_decode_tile(cs->st[Tj], cs->len[Tj], c, buf + 2 * j * N) != 0) rc = -1;
+        }
+        if (rc) break;
+        if (alpha != 1.0)
+            for (uint64_t i = 0; i < 2 * ((uint64_t)1 << mb); ++i) buf[i] = buf[i] * alpha;
+        for (int i = 0; i < ng && rc == 0; ++i)
+            if (apply_gate_buf(buf, mb, qb, fixed, &g[i]) != 0) rc = -2;
+        if (rc) break;
+        for (uint64_t j = 0; j < (1ull << h); ++j) {
+            uint64_t Tj = T;
+            for (int i = 0; i < h; ++i)
+                if ((j >> i) & 1) Tj |= 1ull << (H[i] - c);
+            csim_store(cs, Tj, buf + 2 * j * N);
+        }
+    }
+    free(buf);
+    csim_update_alpha(cs);
+    return rc;
+}
+
+/* decode every tile into a dense vector (the stored state, unscaled) */
+int or_csim_dense(const or_csim *cs, double *out)
+{
+    uint64_t N = 1ull << cs->c;
+    for (uint64_t t = 0; t < cs->ntiles; ++t)
+        if (or_decode_tile(cs->st[t], cs->len[t], cs->c, out + 2 * t * N) != 0) return -1;
+    return 0;
+}
+
+uint32_t or_csim_stream(const or_csim *cs, uint64_t t, uint8_t *out, uint32_t cap)
+{
+    if (t >= cs->ntiles) return 0;
+    if (out && cap >= cs->len[t]) memcpy(out, cs->st[t], cs->len[t]);
+    return cs->len[t];
+}
+
+/* replace a tile's stream (for decoding streams written elsewhere) and
+ * recompute the norm bookkeeping; returns the decoder's status */
+int or_csim_set_stream(or_csim *cs, uint64_t t, const uint8_t *in, uint32_t len)
+{
+    uint64_t N = 1ull << cs->c;
+    double *rec = malloc(N * 16);
+    int rc = or_decode_tile(in, len, cs->c, rec);
+    if (rc == 0) {
+        free(cs->st[t]);
+        cs->st[t] = malloc(len);
+        memcpy(cs->st[t], in, len);
+        cs->len[t] = len;
+        int range = 0;
+        cs->part[t] = sum_sq(rec, 2 * N, &range);
+    }
+    free(rec);
+    return rc;
+}
+
+void or_csim_refresh_alpha(or_csim *cs) { csim_update_alpha(cs); }
+
+double or_csim_alpha(const or_csim *cs) { return cs->alpha; }
+int or_csim_err(const or_csim *cs) { return cs->err; }
+
+void or_csim_norm_units(const or_csim *cs, uint64_t *lo, uint64_t *hi)
+{
+    u128 S = 0;
+    for (uint64_t t = 0; t < cs->ntiles; ++t) S += cs->part[t];
+    *lo = (uint64_t)S;
+    *hi = (uint64_t)(S >> 64);
+}
+
+uint64_t or_csim_bytes(const or_csim *cs)
+{
+    uint64_t s = 0;
+    for (uint64_t t = 0; t < cs->ntiles; ++t) s += cs->len[t];
+    return s;
+}
+
+void or_csim_hist(const or_csim *cs, uint64_t *out8)
+{
+    for (int i = 0; i < 8; ++i) out8[i] = cs->hist[i];
+}
+
+void or_csim_items(const or_csim *cs, uint64_t *done, uint64_t *skipped)
+{
+    *done = cs->items_done;
+    *skipped = cs->items_skipped;
+}

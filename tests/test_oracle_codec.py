@@ -1,0 +1,244 @@
+"""Pins of the oracle's tile codec (O2).
+
+* Hand-derived streams (tests/golden/codec_examples.txt) fix the byte
+  layout, the quantiser, the residual/zigzag/width stage, the packing and
+  the mode rule.
+* The point-wise relative bound (Sec. III with the relative error bound of
+  ref. [xin2018]): every reconstructed component satisfies
+  |x^ - x| < 2^(s-53) |x| <= eps |x|, checked exactly (rational arithmetic)
+  around every binade boundary and every rounding boundary, and on random
+  values.
+* Lossless level: bit-exact round trip of arbitrary finite bit patterns.
+* Algorithm 2's ladder: the level picked is the first whose stream is
+  within max_bytes, else the last (sizes measured level by level).
+"""
+import os
+import struct
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "codec_examples.txt")
+
+
+def d(bits: int) -> float:
+    return struct.unpack("<d", struct.pack("<Q", bits))[0]
+
+
+def bits(x: float) -> int:
+    return struct.unpack("<Q", struct.pack("<d", x))[0]
+
+
+def load_examples():
+    ex, cur = [], None
+    for line in open(GOLD):
+        if line.startswith("#") or not line.strip():
+            continue
+        if not line.startswith(" "):
+            name, c, s, *spec = line.split()
+            cur = {"name": name, "c": int(c), "s": int(s), "spec": spec, "hex": ""}
+            ex.append(cur)
+        else:
+            cur["hex"] += "".join(line.split())
+    return ex
+
+
+def amplitudes(e):
+    N = 1 << e["c"]
+    spec = e["spec"]
+    if spec == ["ramp"]:
+        re = [d(0x3FE0000000000000 + (i << 39)) for i in range(N)]
+        return np.array(re, dtype=np.complex128)
+    if spec == ["signs"]:
+        out = np.zeros(N, dtype=np.complex128)
+        for i in range(N):
+            g, l = divmod(i, 32)
+            word = 0x0F0F0F0F if g == 0 else 0xF0F0F0F0
+            out[i] = -1.0 if (word >> l) & 1 else 1.0
+        return out
+    vals = []
+    for item in spec:
+        pair, _, cnt = item.partition("*")
+        r, i = pair.split(":")
+        vals += [complex(d(int(r, 16)), d(int(i, 16)))] * (int(cnt) if cnt else 1)
+    return np.array(vals, dtype=np.complex128)
+
+
+@pytest.mark.parametrize("e", load_examples(), ids=lambda e: e["name"])
+def test_golden_stream(e):
+    a = amplitudes(e)
+    stream, level, flags = oracle.encode_tile(a, e["c"], [e["s"]])
+    assert stream.hex() == e["hex"]
+    assert level == 0 and flags == 0
+    back = oracle.decode_tile(stream, e["c"])
+    if e["s"] == 0 or e["name"] in ("const_c5", "ramp_c5", "signs_c6"):
+        # these inputs are exactly representable at their shift
+        assert back.view(np.uint64).tolist() == a.view(np.uint64).tolist()
+
+
+def test_shift_for_eps():
+    # largest s with 2^(s-53) <= eps, checked with exact rationals
+    for eps in (1e-2, 1e-3, 1e-4, 1e-5, 1e-8, 0.3, 2.0**-53, 2.0**-54, 0.0):
+        s = oracle.shift_for_eps(eps)
+        if s == 0:
+            assert Fraction(eps) < Fraction(2) ** (1 - 53)
+        else:
+            assert Fraction(2) ** (s - 53) <= Fraction(eps)
+            assert s == 52 or Fraction(2) ** (s + 1 - 53) > Fraction(eps)
+    assert [oracle.shift_for_eps(e) for e in (1e-2, 1e-3, 1e-4, 1e-5)] == [46, 43, 39, 36]
+
+
+def roundtrip_components(vals: np.ndarray, s: int, c: int = 10) -> np.ndarray:
+    """Encode/decode the components, 2^c amplitudes per tile."""
+    comps = np.ascontiguousarray(vals, dtype=np.float64)
+    per = 2 << c
+    pad = (-comps.size) % per
+    comps = np.concatenate([comps, np.full(pad, 0.5)])
+    out = np.empty_like(comps)
+    for t in range(comps.size // per):
+        a = comps[t * per:(t + 1) * per].view(np.complex128)
+        stream, _, flags = oracle.encode_tile(a, c, [s])
+        assert flags & 1 == 0          # 2 = lossless forced (fine at s = 0)
+        out[t * per:(t + 1) * per] = oracle.decode_tile(stream, c).view(np.float64)
+    return out[:vals.size]
+
+
+def boundary_values(s: int) -> np.ndarray:
+    """Magnitude bit patterns around every binade start and around the
+    rounding points k*2^s + 2^(s-1) nearest to it, both signs."""
+    pats = []
+    for E in range(1, 2046):
+        base = E << 52
+        for k in (-2, -1, 0, 1):
+            mid = base + k * (1 << s) + (1 << (s - 1))
+            for dd in (-2, -1, 0, 1, 2):
+                pats.append(mid + dd)
+        for dd in (-1, 0, 1, 2):
+            pats.append(base + dd)
+    pats = [p for p in pats if 0x0010000000000000 <= p < 0x7FE0000000000000]
+    arr = np.array(pats, dtype=np.uint64)
+    arr = np.concatenate([arr, arr | np.uint64(1 << 63)])
+    return arr.view(np.float64)
+
+
+@pytest.mark.parametrize("s", [36, 39, 43, 46, 52])
+def test_relative_bound_exact_at_boundaries(s):
+    x = boundary_values(s)
+    xr = roundtrip_components(x, s)
+    bound = Fraction(2) ** (s - 53)
+    for a, b in zip(x.tolist(), xr.tolist()):
+        fa, fb = Fraction(a), Fraction(b)
+        assert abs(fb - fa) < bound * abs(fa), (s, a, b)
+        assert (a < 0) == (b < 0)
+
+
+@pytest.mark.parametrize("s", [36, 39, 43, 46])
+def test_relative_bound_random(s):
+    rng = np.random.default_rng(s)
+    # magnitudes over a wide exponent range, both signs
+    e = rng.integers(-300, 300, size=400_000)
+    m = rng.random(400_000) + 1.0
+    x = np.ldexp(m, e) * np.where(rng.random(400_000) < 0.5, -1.0, 1.0)
+    xr = roundtrip_components(x, s)
+    diff = np.abs(xr - x)                # exact (Sterbenz: xr/x in [1/2, 2])
+    assert np.all(diff < np.ldexp(np.abs(x), s - 53))
+    eps = {36: 1e-5, 39: 1e-4, 43: 1e-3, 46: 1e-2}[s]
+    assert np.all(diff <= eps * np.abs(x))
+    assert np.all(np.signbit(xr) == np.signbit(x))
+
+
+def test_lossless_roundtrip_bit_exact():
+    rng = np.random.default_rng(5)
+    pats = rng.integers(0, 2**63, size=60_000, dtype=np.uint64)
+    pats ^= rng.integers(0, 2, size=pats.size, dtype=np.uint64) << np.uint64(63)
+    pats = pats[(pats & np.uint64(0x7FF0000000000000)) != np.uint64(0x7FF0000000000000)]
+    edge = [0x0, 1 << 63, 1, 0x000FFFFFFFFFFFFF, 0x0010000000000000, 0x3FF0000000000000,
+            0x3FEFFFFFFFFFFFFF, 0x7FEFFFFFFFFFFFFF, 0x7FE0000000000000, 0x3CA0000000000000,
+            0x8000000000000001]
+    pats = np.concatenate([np.array(edge, dtype=np.uint64), pats])
+    x = pats.view(np.float64)
+    for c in (1, 4, 5, 6, 10):
+        xr = roundtrip_components(x, 0, c)
+        assert np.array_equal(xr.view(np.uint64), x.view(np.uint64))
+
+
+def test_out_of_lossy_range_forces_lossless():
+    a = np.full(64, 0.3 + 0.1j)
+    a[7] = complex(d(0x0000000000000123), 0.2)      # subnormal component
+    stream, _, flags = oracle.encode_tile(a, 6, [39])
+    back = oracle.decode_tile(stream, 6)
+    assert flags == 2
+    assert np.array_equal(back.view(np.uint64), a.view(np.uint64))
+    a[7] = complex(d(0x7FE0000000000001), 0.2)      # |x| >= 2^1023
+    stream, _, flags = oracle.encode_tile(a, 6, [39])
+    assert flags == 2
+    assert np.array_equal(oracle.decode_tile(stream, 6).view(np.uint64), a.view(np.uint64))
+
+
+def test_nonfinite_is_flagged_and_kept_raw():
+    a = np.full(32, 0.5 + 0.5j)
+    a[3] = complex(float("nan"), 0.0)
+    stream, _, flags = oracle.encode_tile(a, 5, [39])
+    assert flags == 1 and stream[0] == 2
+    back = oracle.decode_tile(stream, 5)
+    assert np.array_equal(back.view(np.uint64), a.view(np.uint64))
+
+
+def test_zero_tile_and_signed_zeros():
+    a = np.zeros(256, dtype=np.complex128)
+    stream, _, _ = oracle.encode_tile(a, 8, [39])
+    assert len(stream) == 32 and stream[0] == 0          # header only
+    a = np.zeros(256, dtype=np.complex128)
+    a.real[5] = -0.0
+    stream, _, _ = oracle.encode_tile(a, 8, [39])
+    back = oracle.decode_tile(stream, 8)
+    assert np.array_equal(back.view(np.uint64), a.view(np.uint64))
+
+
+def test_ladder_picks_first_level_within_limit():
+    rng = np.random.default_rng(11)
+    shifts = [0, 36, 39, 43, 46]
+    c = 8
+    for trial in range(40):
+        ph = rng.random(1 << c) * 2 * np.pi * (trial % 7 + 1)
+        a = np.exp(1j * np.cumsum(ph) / 50) / 16.0
+        if trial % 3 == 0:
+            a = a * (1 + 0.5 * rng.random(1 << c))
+        sizes = [len(oracle.encode_tile(a, c, [s])[0]) for s in shifts]
+        for theta in (1.0, 1.5, 2, 3, 4, 6, 8, 16, 1e9):
+            mb = oracle.max_bytes_for(c, theta)
+            stream, level, _ = oracle.encode_tile(a, c, shifts, mb)
+            want = next((k for k, sz in enumerate(sizes) if sz <= mb), len(shifts) - 1)
+            assert level == want
+            assert len(stream) == sizes[want]
+            assert stream[2] == want
+            single = oracle.encode_tile(a, c, [shifts[want]])[0]
+            assert stream[:2] + stream[3:] == single[:2] + single[3:]
+
+
+def test_malformed_streams_are_rejected():
+    a = np.exp(1j * np.arange(64) * 0.37) / 8
+    stream, _, _ = oracle.encode_tile(a, 6, [39])
+    with pytest.raises(ValueError):
+        oracle.decode_tile(stream[:20], 6)                # short header
+    with pytest.raises(ValueError):
+        oracle.decode_tile(stream[:-16], 6)               # short body
+    bad = bytearray(stream)
+    bad[24] = 7                                           # wrong tile size
+    with pytest.raises(ValueError):
+        oracle.decode_tile(bytes(bad), 6)
+    assert stream[0] == 1
+    G = 2
+    size = {0: 0, 1: 0, 2: 4 + 4 * ((G + 31) // 32), 3: 4 * G}
+    woff = 32 + size[stream[3] & 3] + size[(stream[3] >> 2) & 3]
+    bad = bytearray(stream)
+    bad[woff] = 65                                        # width > 64
+    with pytest.raises(ValueError):
+        oracle.decode_tile(bytes(bad), 6)
+    bad = bytearray(stream)
+    bad[woff] = 64                                        # data past the body
+    with pytest.raises(ValueError):
+        oracle.decode_tile(bytes(bad), 6)
