@@ -1,0 +1,255 @@
+/*
+ * qsim.h -- C ABI of the GB300 compressed full-amplitude simulator.
+ *
+ * The library simulates an n-qubit state vector of FP64 complex amplitudes
+ * (Sec. II of "Amplitude-Aware Lossy Compression for Quantum Circuit
+ * Simulation": 2^n amplitudes, 16 bytes each) stored in GPU memory as
+ * independently compressed tiles (the paper's strides, Sec. III).  Gates are
+ * queued on the host and applied by sweeps: each sweep decompresses a tile
+ * group on chip, normalises it, applies a run of gates and compresses it
+ * again (Algorithm 2), all in one CUDA kernel.
+ *
+ * Conventions
+ *   - Qubit j is bit j of the amplitude index (little-endian).
+ *   - Matrices are row-major 2^k x 2^k complex, (re, im) interleaved;
+ *     row/column sub-index bit i selects the value of targets[i].
+ *   - Every pointer argument is caller-owned; the library copies what it
+ *     keeps.  Host pointers are plain host memory unless noted.
+ *   - Calls are host-synchronous: a call that returns QSIM_OK has finished
+ *     its GPU work, except qsim_apply_gate, which only queues.
+ *   - Errors: every call returns a qsim_status; qsim_last_error gives the
+ *     message of the handle's last failing call.  After a device-side
+ *     error other than arena growth the handle is marked invalid and only
+ *     qsim_destroy, qsim_last_error and qsim_stats remain usable.
+ *   - Not thread-safe per handle; distinct handles may be used from
+ *     distinct threads.
+ *
+ * Tile stream format (identical in the CPU oracle, written independently):
+ *   A tile holds 2^c amplitudes; its re and im components each form a
+ *   stream of N = 2^c doubles cut into G = max(1, N/32) groups of
+ *   L = min(N, 32) values.  Header (32 bytes, little-endian):
+ *     [0] mode 0 CONST / 1 PACKED / 2 RAW   [1] shift s (0..52, 0 for RAW)
+ *     [2] ladder level                       [3] sign modes (re bits 0-1, im 2-3)
+ *     [4..7] body bytes (multiple of 16)     [8..15] anchor q_0 of re
+ *     [16..23] anchor q_0 of im              [24] c   [25..31] zero
+ *   Codes: B = magnitude bits of x, q = (B + 2^(s-1)) >> s (q = B at s = 0);
+ *   reconstruction (q << s) with the sign bit.  Residuals r_0 = 0,
+ *   r_i = q_i - q_{i-1} mod 2^64, zigzag z, group width = bit length of the
+ *   OR of its z.  Sign modes: 0 all clear, 1 all set, 2 pattern (u32 P,
+ *   then ceil(G/32) u32 flip words), 3 one u32 word per group.
+ *   PACKED body: re signs, im signs, G width bytes (re), G (im), zero pad
+ *   to 4, then per component and group ceil(L*w/32) u32 words with value l
+ *   at bits [l*w, (l+1)*w); zero pad to 16.  RAW body: 2N doubles.
+ *   CONST when every z is 0 and signs are uniform; else PACKED when shorter
+ *   than RAW; else RAW.  The relative error of a component is below
+ *   2^(s-53) (Sec. III error bound, made point-wise relative as in the
+ *   paper's ref. [xin2018]).
+ */
+#ifndef QSIM_H
+#define QSIM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qsim_state *qsim_t;
+
+typedef enum {
+    QSIM_OK = 0,
+    QSIM_ERR_ARG = 1,            /* invalid argument (nothing done) */
+    QSIM_ERR_OOM = 2,            /* device or host allocation failed */
+    QSIM_ERR_CUDA = 3,           /* CUDA runtime error (no GPU, launch failure) */
+    QSIM_ERR_NONFINITE = 4,      /* a gate produced NaN/Inf; state invalid */
+    QSIM_ERR_TIMEOUT = 5,        /* reserved: no call waits on the device */
+    QSIM_ERR_STATE_INVALID = 6,  /* handle unusable after an earlier error */
+    QSIM_ERR_FORMAT = 7          /* malformed tile stream (import) */
+} qsim_status;
+
+typedef enum {
+    QSIM_CODEC_NONE = 0,      /* uncompressed FP64 vector (Algorithm 1 without codec) */
+    QSIM_CODEC_LOSSLESS = 1,  /* lossless level only (shift 0) */
+    QSIM_CODEC_REL = 2,       /* fixed point-wise relative bound (Sec. III) */
+    QSIM_CODEC_AALC = 3       /* error-bound ladder with ratio threshold (Algorithm 2) */
+} qsim_codec;
+
+/*
+ * qsim_create -- new state |0...0> of n_qubits (1..40), stored in tiles of
+ * 2^min(block_log2, n_qubits, 10) amplitudes (Sec. III strides; block_log2
+ * >= 1).  codec as above; rel_err_bound is the point-wise relative bound
+ * eps of REL, and the largest ladder bound of AALC (default ladder
+ * {lossless, 1e-5, 1e-4, 1e-3, 1e-2} cut at eps, theta = 16; see
+ * qsim_set_aalc).  REL and AALC normalise before every sweep (Algorithm 2);
+ * NONE and LOSSLESS do not (Algorithm 1).  *out receives the handle.
+ * Errors: ARG (ranges), CUDA (no device), OOM.
+ */
+qsim_status qsim_create(qsim_t *out, int n_qubits, int block_log2, qsim_codec codec,
+                        double rel_err_bound);
+
+/* qsim_destroy -- release the handle and its device memory (NULL is OK). */
+qsim_status qsim_destroy(qsim_t h);
+
+/*
+ * qsim_set_stream -- run the handle's work on cuda_stream (a cudaStream_t,
+ * e.g. a PyTorch stream); NULL selects the handle's own stream.  The stream
+ * must outlive its use by the handle.
+ */
+qsim_status qsim_set_stream(qsim_t h, void *cuda_stream);
+
+/*
+ * qsim_set_aalc -- AALC ladder (Algorithm 2): levels delta_0 = lossless,
+ * then eps_levels[0..n_levels-1] ascending (each > 0, n_levels <= 7), and
+ * the ratio threshold theta (> 0).  A tile is stored at the first level
+ * whose ratio 16*2^c / stream bytes is >= theta, else at the last level.
+ * Only for QSIM_CODEC_AALC handles; flushes queued gates first.
+ */
+qsim_status qsim_set_aalc(qsim_t h, double theta, const double *eps_levels, int n_levels);
+
+/*
+ * qsim_set_normalize -- switch Algorithm 2's normalize step (on = 1) for
+ * REL/AALC handles.  Flushes first.
+ */
+qsim_status qsim_set_normalize(qsim_t h, int on);
+
+/*
+ * qsim_set_schedule -- tile_log2 c (1..10, <= n), pair slots hmax (1..2,
+ * c + hmax <= 12) and sweep depth (max gates per sweep, 1..4096).  Re-tiles
+ * the current state (lossless re-encode is exact only for RAW/lossless
+ * tiles; call it before the first gate).  Used by the autotuner.
+ */
+qsim_status qsim_set_schedule(qsim_t h, int tile_log2, int hmax, int depth);
+
+/* qsim_reset_basis -- state |x> (x < 2^n); drops queued gates. */
+qsim_status qsim_reset_basis(qsim_t h, unsigned long long x);
+
+/*
+ * qsim_set_amplitudes -- replace the state by amps (host, 2^n complex128,
+ * interleaved), encoded with the handle's codec.  Drops queued gates.
+ */
+qsim_status qsim_set_amplitudes(qsim_t h, const double *amps);
+
+/*
+ * qsim_apply_gate -- queue U (Sec. II: single-qubit gate, controlled gate;
+ * generalised to 1-2 targets and any number of controls).  matrix is
+ * 2^n_targets x 2^n_targets complex (copied).  controls[i] must hold value
+ * bit i of control_values (pass ~0ULL for "all ones").  Validated on the
+ * host: qubits in range and distinct, entries finite, unitary within 1e-12.
+ * Errors: ARG.
+ */
+qsim_status qsim_apply_gate(qsim_t h, const double *matrix, const int *targets, int n_targets,
+                            const int *controls, int n_controls,
+                            unsigned long long control_values);
+
+/* qsim_flush -- run every queued gate (sweeps) and wait for the device. */
+qsim_status qsim_flush(qsim_t h);
+
+/*
+ * qsim_probabilities -- flush, then out[j] (host, 2^nq doubles) = total
+ * probability of the outcomes whose bits on qubits[0..nq-1] spell j (bit i
+ * of j <-> qubits[i]), computed as RN(S_j) / RN(S) where S_j and S are the
+ * exact sums of |a|^2 over the stored amplitudes (units of 2^-112, each
+ * rounded once to double).  nq in 0..24, qubits distinct.
+ */
+qsim_status qsim_probabilities(qsim_t h, const int *qubits, int nq, double *out);
+
+/*
+ * qsim_amplitudes -- flush, then out (host, 2*count doubles, interleaved)
+ * = stored amplitudes start .. start+count-1 (the decompressed state; the
+ * pending normalisation scale is not applied).
+ */
+qsim_status qsim_amplitudes(qsim_t h, unsigned long long start, unsigned long long count,
+                            double *out);
+
+/* Reference state for qsim_fidelity. */
+typedef enum {
+    QSIM_REF_HANDLE = 0,       /* another handle with the same n and tile size */
+    QSIM_REF_QFT_BASIS = 1,    /* QFT|x>: e^{2 pi i x k / 2^n} / sqrt(2^n) */
+    QSIM_REF_GROVER = 2,       /* Grover after `iterations` from |0..0>, marked item */
+    QSIM_REF_DENSE_HOST = 3,   /* host array of 2^n complex128 */
+    QSIM_REF_DENSE_DEVICE = 4  /* device array of 2^n complex128 */
+} qsim_ref_kind;
+
+typedef struct {
+    int kind;                  /* qsim_ref_kind */
+    qsim_t other;              /* QSIM_REF_HANDLE */
+    unsigned long long x;      /* QFT basis index, or Grover marked item */
+    int iterations;            /* Grover iterations */
+    const double *dense;       /* QSIM_REF_DENSE_* */
+} qsim_ref;
+
+/*
+ * qsim_fidelity -- flush, then the pure-state fidelity of Sec. II between
+ * the stored state psi and ref, both normalised:
+ * *F = |<ref|psi>|^2 / (<ref|ref><psi|psi>) and *overlap_abs = sqrt(*F)
+ * (the paper writes F = <psi_rho|psi_sigma>; the modulus squared is the
+ * reading used here).  Either output may be NULL.
+ */
+qsim_status qsim_fidelity(qsim_t h, const qsim_ref *ref, double *F, double *overlap_abs);
+
+/*
+ * qsim_compressed_bytes -- flush, then *stream_bytes = sum of tile stream
+ * sizes (headers included) and *footprint_bytes = device bytes held by the
+ * state (both arenas, tile table, norm partials).  Either may be NULL.
+ */
+qsim_status qsim_compressed_bytes(qsim_t h, unsigned long long *stream_bytes,
+                                  unsigned long long *footprint_bytes);
+
+/* Counters since creation (or the last reset). */
+typedef struct {
+    unsigned long long gates;          /* gates applied */
+    unsigned long long sweeps;         /* sweeps run */
+    unsigned long long items_done;     /* tile groups decoded and re-encoded */
+    unsigned long long items_skipped;  /* tile groups carried over unchanged */
+    unsigned long long level_hist[8];  /* tiles written per ladder level */
+    unsigned long long stream_bytes;   /* current sum of stream sizes */
+    unsigned long long min_stream_bytes_seen; /* smallest total after a sweep */
+    unsigned long long max_stream_bytes_seen; /* largest total after a sweep */
+    unsigned long long arena_regrows;  /* sweeps re-run after growing the arena */
+    double alpha;                      /* scale of the next normalize step */
+    int tile_log2, hmax, depth, n_qubits;
+} qsim_stats_t;
+
+qsim_status qsim_stats(qsim_t h, qsim_stats_t *out);
+
+/* Message of the handle's last failing call ("" if none; h NULL: global). */
+const char *qsim_last_error(qsim_t h);
+
+/*
+ * qsim_export_tiles -- flush, then copy the streams of tiles
+ * first .. first+count-1, concatenated in tile order, into out (host, cap
+ * bytes) and their sizes into sizes (host, count entries).  With out NULL
+ * only the sizes are written.  Errors: ARG when cap is too small.
+ */
+qsim_status qsim_export_tiles(qsim_t h, unsigned long long first, unsigned long long count,
+                              void *out, unsigned long long cap, unsigned long long *sizes);
+
+/*
+ * qsim_import_tiles -- flush, then replace tiles first .. first+count-1 by
+ * the concatenated streams in data (host) with the given sizes; each stream
+ * is validated on the device (FORMAT on error, state unchanged... except
+ * the tiles already replaced), and the normalisation scale is recomputed.
+ */
+qsim_status qsim_import_tiles(qsim_t h, unsigned long long first, unsigned long long count,
+                              const void *data, const unsigned long long *sizes);
+
+/*
+ * qsim_plan_sweeps -- host-only: the sweep partition the library uses for
+ * a gate list (no GPU needed).  Gate g has ntargets[g] targets in
+ * targets[2g..], matrix in matrices[32g..] (row-major complex, zero-padded).
+ * Writes per sweep its first gate to out_lo, its pair count to out_h and
+ * its pair qubits to out_H[2s..].  Returns the number of sweeps, or -1 on
+ * bad arguments, or -2 when cap is too small.
+ */
+int qsim_plan_sweeps(int n, int tile_log2, int hmax, int depth, int ngates,
+                     const int *ntargets, const int *targets, const double *matrices,
+                     int *out_lo, int *out_h, int *out_H, int cap);
+
+/* qsim_version -- library version string. */
+const char *qsim_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QSIM_H */

@@ -1,0 +1,1000 @@
+// Host side of the compressed simulator: the C ABI of include/qsim.h, the
+// sweep planner (gate run partition, partner-tile pairing) and the pass
+// driver (launch, arena regrowth, re-run after an overflow).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "qsim.h"
+#include "qsim_dev.cuh"
+
+namespace qs {
+size_t sweep_smem_bytes(int mb);
+cudaError_t launch_sweep(const SweepParams &p, int grid, cudaStream_t st);
+cudaError_t launch_finalize(DevScalars *scal, int use_alpha, unsigned long long *used_hist,
+                            unsigned slot, int record_used, cudaStream_t st);
+cudaError_t launch_init(const double2 *dense, unsigned long long x, const CodecCfg &cc,
+                        unsigned long long ntiles, uint8_t *arena, unsigned long long cap,
+                        unsigned long long *table, unsigned long long *part, DevScalars *scal,
+                        int grid, cudaStream_t st);
+cudaError_t launch_norm_from_parts(const unsigned long long *part, unsigned long long ntiles,
+                                   DevScalars *scal, int grid, cudaStream_t st);
+cudaError_t launch_sizes(const uint8_t *arena, const unsigned long long *table,
+                         unsigned long long first, unsigned long long count,
+                         unsigned long long *sizes, int grid, cudaStream_t st);
+cudaError_t launch_sum_sizes(const uint8_t *arena, const unsigned long long *table,
+                             unsigned long long ntiles, unsigned long long *total, int grid,
+                             cudaStream_t st);
+cudaError_t launch_gather(const uint8_t *arena, const unsigned long long *table,
+                          unsigned long long first, unsigned long long count,
+                          const unsigned long long *offs, const unsigned long long *sizes,
+                          uint8_t *out, int grid, cudaStream_t st);
+cudaError_t launch_validate(const uint8_t *buf, const unsigned long long *offs,
+                            const unsigned long long *sizes, unsigned long long count, int c,
+                            unsigned long long *parts, unsigned int *bad, int grid, cudaStream_t st);
+cudaError_t launch_place(const uint8_t *buf, const unsigned long long *offs,
+                         const unsigned long long *sizes, unsigned long long count,
+                         unsigned long long first, unsigned long long base, uint8_t *arena,
+                         unsigned long long *table, const unsigned long long *parts,
+                         unsigned long long *part, int grid, cudaStream_t st);
+cudaError_t launch_amplitudes(const uint8_t *arena, const unsigned long long *table, int c,
+                              unsigned long long start, unsigned long long count, double2 *out,
+                              DevScalars *scal, int grid, cudaStream_t st);
+cudaError_t launch_probs(const uint8_t *arena, const unsigned long long *table, int c,
+                         unsigned long long ntiles, const int *qsel, int nq,
+                         unsigned long long *buckets, DevScalars *scal, int grid, cudaStream_t st);
+cudaError_t launch_fidelity(const uint8_t *arena, const unsigned long long *table, int c,
+                            unsigned long long ntiles, const RefSpec &rs, Acc4 *tile_sums,
+                            DevScalars *scal, int grid, cudaStream_t st);
+cudaError_t launch_pair_sum(const Acc4 *in, Acc4 *out, unsigned long long nout, int grid,
+                            cudaStream_t st);
+cudaError_t configure_kernels();
+int sweep_blocks_per_sm(int mb);
+}  // namespace qs
+
+namespace {
+
+constexpr int MAX_QUBITS = 40;
+constexpr double UNITARY_TOL = 1e-12;
+
+struct HostGate {
+    int k;
+    int t[2];
+    unsigned long long cm, cv;
+    double m[32];
+    bool diag;
+};
+
+struct Sweep {
+    int lo, hi, h;
+    int H[2];
+};
+
+std::string g_last_error;
+
+bool matrix_is_diagonal(int k, const double *m) {
+    int dim = 1 << k;
+    for (int r = 0; r < dim; ++r)
+        for (int c = 0; c < dim; ++c)
+            if (r != c && (m[2 * (r * dim + c)] != 0.0 || m[2 * (r * dim + c) + 1] != 0.0))
+                return false;
+    return true;
+}
+
+int popcount64(unsigned long long v) { return __builtin_popcountll(v); }
+
+// Gate run partition: extend the open sweep while the union of its paired
+// high qubits and the gate's mixing high qubits fits hmax and the sweep
+// holds fewer than `depth` gates; diagonal gates mix nothing.
+int plan_sweeps(int n, int c, int hmax, int depth, const std::vector<HostGate> &g,
+                std::vector<Sweep> &out) {
+    out.clear();
+    int hcap = std::min(hmax, n - c);
+    if (hcap < 0) hcap = 0;
+    int lo = 0;
+    unsigned long long H = 0;
+    auto emit = [&](int a, int b, unsigned long long Hm) {
+        Sweep s{a, b, 0, {0, 0}};
+        for (int q = 0; q < 64; ++q)
+            if ((Hm >> q) & 1ull) s.H[s.h++] = q;
+        out.push_back(s);
+    };
+    for (int i = 0; i < (int)g.size(); ++i) {
+        unsigned long long mix = 0;
+        if (!g[i].diag)
+            for (int j = 0; j < g[i].k; ++j)
+                if (g[i].t[j] >= c) mix |= 1ull << g[i].t[j];
+        if (popcount64(mix) > hcap) return -1;
+        if (i > lo && (popcount64(H | mix) > hcap || i - lo >= depth)) {
+            emit(lo, i, H);
+            lo = i;
+            H = 0;
+        }
+        H |= mix;
+    }
+    if (lo < (int)g.size()) emit(lo, (int)g.size(), H);
+    return (int)out.size();
+}
+
+int shift_for_eps(double eps) {
+    for (int s = 52; s >= 1; --s)
+        if (std::ldexp(1.0, s - 53) <= eps) return s;
+    return 0;
+}
+
+// correctly rounded double of a 128-bit count of 2^-112 units
+double units_to_double_host(unsigned long long lo, unsigned long long hi) {
+    if (hi == 0) {
+        if (lo == 0) return 0.0;
+        return std::ldexp((double)lo, -112);
+    }
+    int p = 128 - __builtin_clzll(hi);
+    int drop = p - 64;
+    unsigned long long top, rest;
+    if (drop == 64) { top = hi; rest = lo; }
+    else { top = (hi << (64 - drop)) | (lo >> drop); rest = lo & ((1ull << drop) - 1); }
+    top |= rest ? 1ull : 0ull;
+    return std::ldexp((double)top, drop - 112);
+}
+
+}  // namespace
+
+struct qsim_state {
+    int n = 0, c = 0, hmax = 2, depth = 64;
+    qsim_codec codec = QSIM_CODEC_REL;
+    double eps = 0.0;
+    int normalize = 0;
+    double theta = 16.0;
+    qs::CodecCfg cc{};
+    int device = 0, sms = 1;
+    cudaStream_t stream = nullptr, own_stream = nullptr;
+    unsigned long long ntiles = 0;
+    uint8_t *arena[2] = {nullptr, nullptr};
+    unsigned long long cap[2] = {0, 0};
+    int cur = 0;
+    unsigned long long used = 0;          // bytes in arena[cur]
+    unsigned long long *table[2] = {nullptr, nullptr};
+    unsigned long long *part = nullptr;
+    qs::DevScalars *scal = nullptr;
+    qs::DevScalars *hscal = nullptr;      // pinned mirror
+    qs::DGate *dgates = nullptr;
+    size_t dgates_cap = 0;
+    qs::DGate *hgates = nullptr;          // pinned staging
+    size_t hgates_cap = 0;
+    unsigned long long *used_hist = nullptr;
+    size_t used_hist_cap = 0;
+    unsigned long long *hused = nullptr;  // pinned
+    size_t hused_cap = 0;
+    unsigned sweep_counter = 0;
+    std::vector<HostGate> queue;
+    qsim_stats_t st{};
+    std::string err;
+    bool invalid = false;
+};
+
+namespace {
+
+qsim_status fail(qsim_t h, qsim_status code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else g_last_error = buf;
+    return code;
+}
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(h, e_ == cudaErrorMemoryAllocation ? QSIM_ERR_OOM : QSIM_ERR_CUDA, \
+                        "%s: %s", #call, cudaGetErrorString(e_));                        \
+    } while (0)
+
+unsigned long long tile_bytes_worst(const qsim_state *h) {
+    return (unsigned long long)qs::HDR + (16ull << h->c);
+}
+
+unsigned long long round_up(unsigned long long v, unsigned long long a) { return (v + a - 1) / a * a; }
+
+int grid_for(const qsim_state *h, unsigned long long work, int per_sm) {
+    unsigned long long g = (unsigned long long)h->sms * (unsigned long long)per_sm;
+    if (work < g) g = work;
+    return g ? (int)g : 1;
+}
+
+qsim_status ensure_arena(qsim_t h, int which, unsigned long long need) {
+    if (h->cap[which] >= need) return QSIM_OK;
+    unsigned long long worst = h->ntiles * tile_bytes_worst(h);
+    unsigned long long nc = std::max(need, h->cap[which] + h->cap[which] / 2);
+    nc = std::min(round_up(nc, 1ull << 21), round_up(worst, 256));
+    if (nc < need) nc = need;
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->arena[which]) CK(cudaFree(h->arena[which]));
+    h->arena[which] = nullptr;
+    h->cap[which] = 0;
+    CK(cudaMalloc(&h->arena[which], nc));
+    h->cap[which] = nc;
+    return QSIM_OK;
+}
+
+qsim_status read_scalars(qsim_t h) {
+    CK(cudaMemcpyAsync(h->hscal, h->scal, sizeof(qs::DevScalars), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return QSIM_OK;
+}
+
+qsim_status clear_pass_state(qsim_t h) {
+    // err, err_sweep, bump and the running norm restart from zero
+    qs::DevScalars z{};
+    CK(cudaMemcpyAsync(&h->scal->bump, &z.bump, sizeof z.bump, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemsetAsync(&h->scal->err, 0, 2 * sizeof(unsigned), h->stream));
+    CK(cudaMemsetAsync(&h->scal->acc_lo, 0, 2 * sizeof(unsigned long long), h->stream));
+    return QSIM_OK;
+}
+
+qsim_status device_error(qsim_t h, unsigned err) {
+    h->invalid = true;
+    if (err & qs::ERR_NONFINITE) return fail(h, QSIM_ERR_NONFINITE, "a gate produced a non-finite amplitude");
+    if (err & qs::ERR_FORMAT) return fail(h, QSIM_ERR_FORMAT, "malformed tile stream on the device");
+    if (err & qs::ERR_RANGE) return fail(h, QSIM_ERR_NONFINITE, "amplitude magnitude >= 16 (state not normalised)");
+    return fail(h, QSIM_ERR_CUDA, "device error 0x%x", err);
+}
+
+// Encode a dense state (device) or |x> into arena[cur], retrying with a
+// larger arena after an overflow.
+qsim_status encode_fresh(qsim_t h, const double2 *dense, unsigned long long x) {
+    unsigned long long need = dense ? h->ntiles * tile_bytes_worst(h)
+                                    : (h->cc.force_raw ? h->ntiles * tile_bytes_worst(h)
+                                                       : h->ntiles * qs::HDR + tile_bytes_worst(h));
+    if (dense) need = std::min(need, std::max<unsigned long long>(h->cap[h->cur], 1ull << 22));
+    for (int attempt = 0; attempt < 64; ++attempt) {
+        qsim_status s = ensure_arena(h, h->cur, need);
+        if (s != QSIM_OK) return s;
+        CK(cudaMemsetAsync(h->scal, 0, sizeof(qs::DevScalars), h->stream));
+        CK(qs::launch_init(dense, x, h->cc, h->ntiles, h->arena[h->cur], h->cap[h->cur],
+                           h->table[h->cur], h->part, h->scal, grid_for(h, h->ntiles, 4), h->stream));
+        CK(qs::launch_finalize(h->scal, h->normalize, nullptr, 0, 1, h->stream));
+        if ((s = read_scalars(h)) != QSIM_OK) return s;
+        if (h->hscal->err & qs::ERR_OVERFLOW) {
+            need = std::max(need + need / 2, h->hscal->bump + h->hscal->bump / 8);
+            continue;
+        }
+        if (h->hscal->err) return device_error(h, h->hscal->err);
+        h->used = h->hscal->used;
+        h->st.stream_bytes = h->used;
+        return QSIM_OK;
+    }
+    return fail(h, QSIM_ERR_OOM, "arena could not hold the state");
+}
+
+qsim_status alloc_tiles(qsim_t h) {
+    h->ntiles = 1ull << (h->n - h->c);
+    for (int i = 0; i < 2; ++i) {
+        CK(cudaMalloc(&h->table[i], h->ntiles * sizeof(unsigned long long)));
+    }
+    CK(cudaMalloc(&h->part, h->ntiles * 2 * sizeof(unsigned long long)));
+    return QSIM_OK;
+}
+
+void free_tiles(qsim_t h) {
+    for (int i = 0; i < 2; ++i) {
+        if (h->table[i]) cudaFree(h->table[i]);
+        if (h->arena[i]) cudaFree(h->arena[i]);
+        h->table[i] = nullptr;
+        h->arena[i] = nullptr;
+        h->cap[i] = 0;
+    }
+    if (h->part) cudaFree(h->part);
+    h->part = nullptr;
+}
+
+void set_codec(qsim_t h) {
+    qs::CodecCfg &cc = h->cc;
+    cc = qs::CodecCfg{};
+    cc.c = h->c;
+    cc.max_bytes = ~0ull;
+    switch (h->codec) {
+        case QSIM_CODEC_NONE:
+            cc.force_raw = 1; cc.nlev = 1; cc.shifts[0] = 0; h->normalize = 0; break;
+        case QSIM_CODEC_LOSSLESS:
+            cc.nlev = 1; cc.shifts[0] = 0; h->normalize = 0; break;
+        case QSIM_CODEC_REL:
+            cc.nlev = 1; cc.shifts[0] = shift_for_eps(h->eps); h->normalize = 1; break;
+        case QSIM_CODEC_AALC: {
+            const double lad[4] = {1e-5, 1e-4, 1e-3, 1e-2};
+            cc.nlev = 1;
+            cc.shifts[0] = 0;
+            for (double e : lad)
+                if (e <= h->eps * (1 + 1e-12)) cc.shifts[cc.nlev++] = shift_for_eps(e);
+            cc.max_bytes = (unsigned long long)std::floor(16.0 * (double)(1ull << h->c) / h->theta);
+            h->normalize = 1;
+            break;
+        }
+    }
+}
+
+qsim_status check_usable(qsim_t h) {
+    if (!h) return fail(nullptr, QSIM_ERR_ARG, "null handle");
+    if (h->invalid) return fail(h, QSIM_ERR_STATE_INVALID, "state invalid after an earlier error: %s", h->err.c_str());
+    return QSIM_OK;
+}
+
+qs::DGate prepare_gate(const HostGate &g, int c, const Sweep &sw) {
+    qs::DGate d{};
+    std::memcpy(d.m, g.m, sizeof d.m);
+    d.k = g.k;
+    d.diag = g.diag ? 1 : 0;
+    auto pos = [&](int q) -> int {
+        if (q < c) return q;
+        for (int i = 0; i < sw.h; ++i)
+            if (sw.H[i] == q) return c + i;
+        return -1;
+    };
+    for (int i = 0; i < 2; ++i) {
+        d.t[i] = i < g.k ? g.t[i] : 0;
+        d.pos[i] = i < g.k ? pos(g.t[i]) : -1;
+    }
+    for (int q = 0; q < 64; ++q) {
+        if (!((g.cm >> q) & 1ull)) continue;
+        int p = pos(q);
+        unsigned long long v = (g.cv >> q) & 1ull;
+        if (p >= 0) { d.lcm |= 1ull << p; d.lcv |= v << p; }
+        else { d.fcm |= 1ull << q; d.fcv |= v << q; }
+    }
+    return d;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *qsim_version(void) { return "qsim-aalc 0.1 (sm_103a)"; }
+
+const char *qsim_last_error(qsim_t h) { return h ? h->err.c_str() : g_last_error.c_str(); }
+
+qsim_status qsim_create(qsim_t *out, int n_qubits, int block_log2, qsim_codec codec, double rel_err_bound) {
+    qsim_t h = nullptr;
+    if (!out) return fail(nullptr, QSIM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_qubits < 1 || n_qubits > MAX_QUBITS) return fail(nullptr, QSIM_ERR_ARG, "n_qubits must be 1..%d", MAX_QUBITS);
+    if (block_log2 < 1) return fail(nullptr, QSIM_ERR_ARG, "block_log2 must be >= 1");
+    if (codec < QSIM_CODEC_NONE || codec > QSIM_CODEC_AALC) return fail(nullptr, QSIM_ERR_ARG, "unknown codec");
+    if ((codec == QSIM_CODEC_REL || codec == QSIM_CODEC_AALC) && !(rel_err_bound >= 0.0 && rel_err_bound < 1.0))
+        return fail(nullptr, QSIM_ERR_ARG, "rel_err_bound must be in [0, 1)");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+        return fail(nullptr, QSIM_ERR_CUDA, "no CUDA device");
+    h = new qsim_state();
+    h->n = n_qubits;
+    h->c = std::min(std::min(block_log2, n_qubits), qs::MAX_C);
+    h->hmax = 2;
+    h->depth = 64;
+    h->codec = codec;
+    h->eps = rel_err_bound;
+    qsim_status s = QSIM_OK;
+    auto bail = [&](qsim_status code) { qsim_destroy(h); return code; };
+    if (cudaGetDevice(&h->device) != cudaSuccess) return bail(fail(nullptr, QSIM_ERR_CUDA, "cudaGetDevice failed"));
+    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = qs::configure_kernels();
+        if (e != cudaSuccess) return bail(fail(nullptr, QSIM_ERR_CUDA, "kernel setup: %s", cudaGetErrorString(e)));
+        configured = true;
+    }
+    if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(nullptr, QSIM_ERR_CUDA, "stream creation failed"));
+    h->stream = h->own_stream;
+    if (cudaMalloc(&h->scal, sizeof(qs::DevScalars)) != cudaSuccess ||
+        cudaMallocHost(&h->hscal, sizeof(qs::DevScalars)) != cudaSuccess)
+        return bail(fail(nullptr, QSIM_ERR_OOM, "scalar allocation failed"));
+    cudaMemset(h->scal, 0, sizeof(qs::DevScalars));
+    set_codec(h);
+    if ((s = alloc_tiles(h)) != QSIM_OK) { g_last_error = h->err; return bail(s); }
+    if ((s = qsim_reset_basis(h, 0)) != QSIM_OK) { g_last_error = h->err; return bail(s); }
+    *out = h;
+    return QSIM_OK;
+}
+
+qsim_status qsim_destroy(qsim_t h) {
+    if (!h) return QSIM_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_tiles(h);
+    if (h->scal) cudaFree(h->scal);
+    if (h->hscal) cudaFreeHost(h->hscal);
+    if (h->dgates) cudaFree(h->dgates);
+    if (h->hgates) cudaFreeHost(h->hgates);
+    if (h->used_hist) cudaFree(h->used_hist);
+    if (h->hused) cudaFreeHost(h->hused);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    delete h;
+    return QSIM_OK;
+}
+
+qsim_status qsim_set_stream(qsim_t h, void *cuda_stream) {
+    if (!h) return fail(nullptr, QSIM_ERR_ARG, "null handle");
+    CK(cudaStreamSynchronize(h->stream));
+    h->stream = cuda_stream ? (cudaStream_t)cuda_stream : h->own_stream;
+    return QSIM_OK;
+}
+
+qsim_status qsim_reset_basis(qsim_t h, unsigned long long x) {
+    if (!h) return fail(nullptr, QSIM_ERR_ARG, "null handle");
+    if (h->invalid) return check_usable(h);
+    if (x >> h->n) return fail(h, QSIM_ERR_ARG, "basis index out of range");
+    h->queue.clear();
+    qsim_status s = encode_fresh(h, nullptr, x);
+    if (s == QSIM_OK) {
+        h->st = qsim_stats_t{};
+        h->st.stream_bytes = h->used;
+        h->st.min_stream_bytes_seen = h->st.max_stream_bytes_seen = h->used;
+    }
+    return s;
+}
+
+qsim_status qsim_set_amplitudes(qsim_t h, const double *amps) {
+    qsim_status s = check_usable(h);
+    if (s != QSIM_OK) return s;
+    if (!amps) return fail(h, QSIM_ERR_ARG, "amps is NULL");
+    h->queue.clear();
+    size_t bytes = (size_t)16 << h->n;
+    double2 *d = nullptr;
+    CK(cudaMalloc(&d, bytes));
+    cudaError_t e = cudaMemcpyAsync(d, amps, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) s = encode_fresh(h, d, 0);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(h, QSIM_ERR_CUDA, "copy: %s", cudaGetErrorString(e));
+    if (s == QSIM_OK) {
+        h->st.stream_bytes = h->used;
+        h->st.min_stream_bytes_seen = h->st.max_stream_bytes_seen = h->used;
+    }
+    return s;
+}
+
+qsim_status qsim_apply_gate(qsim_t h, const double *matrix, const int *targets, int n_targets,
+                            const int *controls, int n_controls, unsigned long long control_values) {
+    qsim_status s = check_usable(h);
+    if (s != QSIM_OK) return s;
+    if (!matrix || !targets) return fail(h, QSIM_ERR_ARG, "matrix/targets NULL");
+    if (n_targets < 1 || n_targets > 2) return fail(h, QSIM_ERR_ARG, "1 or 2 targets supported");
+    if (n_controls < 0 || (n_controls > 0 && !controls)) return fail(h, QSIM_ERR_ARG, "bad controls");
+    HostGate g{};
+    g.k = n_targets;
+    unsigned long long used = 0;
+    for (int i = 0; i < n_targets; ++i) {
+        int q = targets[i];
+        if (q < 0 || q >= h->n) return fail(h, QSIM_ERR_ARG, "target %d out of range", q);
+        if ((used >> q) & 1ull) return fail(h, QSIM_ERR_ARG, "repeated qubit %d", q);
+        used |= 1ull << q;
+        g.t[i] = q;
+    }
+    for (int i = 0; i < n_controls; ++i) {
+        int q = controls[i];
+        if (q < 0 || q >= h->n) return fail(h, QSIM_ERR_ARG, "control %d out of range", q);
+        if ((used >> q) & 1ull) return fail(h, QSIM_ERR_ARG, "repeated qubit %d", q);
+        used |= 1ull << q;
+        g.cm |= 1ull << q;
+        if (i >= 64 || ((control_values >> i) & 1ull)) g.cv |= 1ull << q;
+    }
+    int dim = 1 << n_targets;
+    for (int i = 0; i < 2 * dim * dim; ++i) {
+        if (!std::isfinite(matrix[i])) return fail(h, QSIM_ERR_ARG, "matrix entry not finite");
+        g.m[i] = matrix[i];
+    }
+    // unitarity: max |(U^dagger U - I)_{ij}| <= 1e-12
+    for (int i = 0; i < dim; ++i)
+        for (int j = 0; j < dim; ++j) {
+            double sr = 0, si = 0;
+            for (int r = 0; r < dim; ++r) {
+                double ar = g.m[2 * (r * dim + i)], ai = -g.m[2 * (r * dim + i) + 1];
+                double br = g.m[2 * (r * dim + j)], bi = g.m[2 * (r * dim + j) + 1];
+                sr += ar * br - ai * bi;
+                si += ar * bi + ai * br;
+            }
+            if (std::fabs(sr - (i == j ? 1.0 : 0.0)) > UNITARY_TOL || std::fabs(si) > UNITARY_TOL)
+                return fail(h, QSIM_ERR_ARG, "matrix is not unitary within 1e-12");
+        }
+    g.diag = matrix_is_diagonal(n_targets, g.m);
+    if (!g.diag && h->hmax < 2 && n_targets == 2 && g.t[0] >= h->c && g.t[1] >= h->c && h->n - h->c >= 2)
+        return fail(h, QSIM_ERR_ARG, "two high targets need hmax = 2");
+    h->queue.push_back(g);
+    return QSIM_OK;
+}
+
+qsim_status qsim_flush(qsim_t h) {
+    qsim_status s = check_usable(h);
+    if (s != QSIM_OK) return s;
+    if (h->queue.empty()) return QSIM_OK;
+    std::vector<Sweep> sweeps;
+    if (plan_sweeps(h->n, h->c, h->hmax, h->depth, h->queue, sweeps) < 0)
+        return fail(h, QSIM_ERR_ARG, "a gate needs more paired qubits than hmax");
+    const size_t ng = h->queue.size(), ns = sweeps.size();
+    // stage every gate, prepared for its sweep, in one upload
+    if (h->hgates_cap < ng) {
+        if (h->hgates) cudaFreeHost(h->hgates);
+        h->hgates = nullptr;
+        h->hgates_cap = 0;
+        CK(cudaMallocHost(&h->hgates, ng * sizeof(qs::DGate)));
+        h->hgates_cap = ng;
+    }
+    if (h->dgates_cap < ng) {
+        CK(cudaStreamSynchronize(h->stream));
+        if (h->dgates) cudaFree(h->dgates);
+        h->dgates = nullptr;
+        h->dgates_cap = 0;
+        CK(cudaMalloc(&h->dgates, ng * sizeof(qs::DGate)));
+        h->dgates_cap = ng;
+    }
+    if (h->used_hist_cap < ns) {
+        CK(cudaStreamSynchronize(h->stream));
+        if (h->used_hist) cudaFree(h->used_hist);
+        if (h->hused) cudaFreeHost(h->hused);
+        h->used_hist = nullptr;
+        h->hused = nullptr;
+        h->used_hist_cap = 0;
+        CK(cudaMalloc(&h->used_hist, ns * sizeof(unsigned long long)));
+        CK(cudaMallocHost(&h->hused, ns * sizeof(unsigned long long)));
+        h->used_hist_cap = ns;
+    }
+    for (size_t si = 0; si < ns; ++si)
+        for (int gi = sweeps[si].lo; gi < sweeps[si].hi; ++gi)
+            h->hgates[gi] = prepare_gate(h->queue[gi], h->c, sweeps[si]);
+    CK(cudaMemcpyAsync(h->dgates, h->hgates, ng * sizeof(qs::DGate), cudaMemcpyHostToDevice, h->stream));
+
+    const int cur0 = h->cur;
+    const unsigned id0 = h->sweep_counter;
+    size_t k = 0;
+    int regrows = 0;
+    // the output of a sweep never needs more than its input plus this slack
+    // on the first try; overflows are re-run with the exact size
+    unsigned long long first_need = std::max<unsigned long long>(h->used + h->used / 4 + (1ull << 20), 1ull << 22);
+    if ((s = ensure_arena(h, h->cur ^ 1, first_need)) != QSIM_OK) return s;
+    while (k < ns) {
+        for (size_t j = k; j < ns; ++j) {
+            const Sweep &sw = sweeps[j];
+            int in = cur0 ^ (int)(j & 1), outa = in ^ 1;
+            qs::SweepParams p{};
+            p.in_arena = h->arena[in];
+            p.in_table = h->table[in];
+            p.out_arena = h->arena[outa];
+            p.out_table = h->table[outa];
+            p.out_cap = h->cap[outa];
+            p.part = h->part;
+            p.scal = h->scal;
+            p.gates = h->dgates + sw.lo;
+            p.ngates = sw.hi - sw.lo;
+            p.n = h->n;
+            p.h = sw.h;
+            p.H[0] = sw.H[0];
+            p.H[1] = sw.H[1];
+            p.cc = h->cc;
+            p.nitems = h->ntiles >> sw.h;
+            p.sweep_id = id0 + (unsigned)j;
+            p.use_alpha = h->normalize;
+            int per_sm = qs::sweep_blocks_per_sm(h->c + sw.h);
+            CK(qs::launch_sweep(p, grid_for(h, p.nitems, per_sm), h->stream));
+            CK(qs::launch_finalize(h->scal, h->normalize, h->used_hist, (unsigned)j, 1, h->stream));
+        }
+        if ((s = read_scalars(h)) != QSIM_OK) return s;
+        unsigned err = h->hscal->err;
+        if (err & qs::ERR_OVERFLOW) {
+            unsigned failed = h->hscal->err_sweep - 1u - id0;
+            if (failed >= ns) return device_error(h, err);
+            int outa = (cur0 ^ (int)(failed & 1)) ^ 1;
+            unsigned long long need = h->hscal->bump + h->hscal->bump / 8 + (1ull << 20);
+            if ((s = ensure_arena(h, outa, need)) != QSIM_OK) return s;
+            if ((s = clear_pass_state(h)) != QSIM_OK) return s;
+            k = failed;
+            ++regrows;
+            continue;
+        }
+        if (err) return device_error(h, err);
+        break;
+    }
+    CK(cudaMemcpyAsync(h->hused, h->used_hist, ns * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->cur = cur0 ^ (int)(ns & 1);
+    h->used = h->hscal->used;
+    h->sweep_counter += (unsigned)ns;
+    h->st.gates += ng;
+    h->st.sweeps += ns;
+    h->st.arena_regrows += (unsigned long long)regrows;
+    for (size_t j = 0; j < ns; ++j) {
+        h->st.min_stream_bytes_seen = std::min(h->st.min_stream_bytes_seen, h->hused[j]);
+        h->st.max_stream_bytes_seen = std::max(h->st.max_stream_bytes_seen, h->hused[j]);
+    }
+    h->st.stream_bytes = h->used;
+    h->queue.clear();
+    return QSIM_OK;
+}
+
+qsim_status qsim_set_aalc(qsim_t h, double theta, const double *eps_levels, int n_levels) {
+    qsim_status s = check_usable(h);
+    if (s != QSIM_OK) return s;
+    if (h->codec != QSIM_CODEC_AALC) return fail(h, QSIM_ERR_ARG, "handle does not use the AALC codec");
+    if (!(theta > 0.0) || !std::isfinite(theta)) return fail(h, QSIM_ERR_ARG, "theta must be > 0");
+    if (n_levels < 0 || n_levels > qs::MAX_LEVELS - 1 || (n_levels > 0 && !eps_levels))
+        return fail(h, QSIM_ERR_ARG, "0..%d levels", qs::MAX_LEVELS - 1);
+    for (int i = 0; i < n_levels; ++i)
+        if (!(eps_levels[i] > 0.0 && eps_levels[i] < 1.0) || (i && eps_levels[i] <= eps_levels[i - 1]))
+            return fail(h, QSIM_ERR_ARG, "levels must ascend in (0, 1)");
+    if ((s = qsim_flush(h)) != QSIM_OK) return s;
+    h->theta = theta;
+    h->cc.nlev = 1 + n_levels;
+    h->cc.shifts[0] = 0;
+    for (int i = 0; i < n_levels; ++i) h->cc.shifts[1 + i] = shift_for_eps(eps_levels[i]);
+    h->cc.max_bytes = (unsigned long long)std::floor(16.0 * (double)(1ull << h->c) / theta);
+    return QSIM_OK;
+}
+
+qsim_status qsim_set_normalize(qsim_t h, int on) {
+    qsim_status s = check_usable(h);
+    if (s != QSIM_OK) return s;
+    if (h->codec != QSIM_CODEC_REL && h->codec != QSIM_CODEC_AALC)
+        return fail(h, QSIM_ERR_ARG, "normalize applies to REL and AALC handles");
+    if ((s = qsim_flush(h)) != QSIM_OK) return s;
+    h->normalize = on ? 1 : 0;
+    // the scale of the next pass follows the switch
+    CK(cudaMemsetAsync(&h->scal->acc_lo, 0, 2 * sizeof(unsigned long long), h->stream));
+    CK(qs::launch_norm_from_parts(h->part, h->ntiles, h->scal, grid_for(h, h->ntiles / qs::THREADS + 1, 4), h->stream));
+    CK(qs::launch_finalize(h->scal, h->normalize, nullptr, 0, 0, h->stream));
+    return read_scalars(h);
+}
+
+qsim_status qsim_set_schedule(qsim_t h, int tile_log2, int hmax, int depth) {
+    qsim_status s = check_usable(h);
+    if (s != QSIM_OK) return s;
+    if (tile_log2 < 1 || tile_log2 > qs::MAX_C || tile_log2 > h->n) return fail(h, QSIM_ERR_ARG, "tile_log2 must be 1..min(10, n)");
+    if (hmax < 1 || hmax > 2 || tile_log2 + hmax > qs::MAX_ITEM_LOG2) return fail(h, QSIM_ERR_ARG, "hmax must be 1..2");
+    if (depth < 1 || depth > 4096) return fail(h, QSIM_ERR_ARG, "depth must be 1..4096");
+    if ((s = qsim_flush(h)) != QSIM_OK) return s;
+    h->hmax = hmax;
+    h->depth = depth;
+    if (tile_log2 == h->c) return QSIM_OK;
+    if (h->n > 32) return fail(h, QSIM_ERR_ARG, "re-tiling needs n <= 32");
+    size_t bytes = (size_t)16 << h->n;
+    double2 *d = nullptr;
+    CK(cudaMalloc(&d, bytes));
+    cudaError_t e = qs::launch_amplitudes(h->arena[h->cur], h->table[h->cur], h->c, 0, 1ull << h->n, d,
+                                          h->scal, grid_for(h, h->ntiles, 4), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) { cudaFree(d); return fail(h, QSIM_ERR_CUDA, "re-tile: %s", cudaGetErrorString(e)); }
+    free_tiles(h);
+    h->c = tile_log2;
+    double theta = h->theta;
+    int nlev = h->cc.nlev;
+    int shifts[qs::MAX_LEVELS];
+    std::memcpy(shifts, h->cc.shifts, sizeof shifts);
+    int force = h->cc.force_raw;
+    h->cc.c = h->c;
+    h->cc.nlev = nlev;
+    std::memcpy(h->cc.shifts, shifts, sizeof shifts);
+    h->cc.force_raw = force;
+    if (h->codec == QSIM_CODEC_AALC)
+        h->cc.max_bytes = (unsigned long long)std::floor(16.0 * (double)(1ull << h->c) / theta);
+    h->used = 0;
+    if ((s = alloc_tiles(h)) != QSIM_OK) { cudaFree(d); return s; }
+    s = encode_fresh(h, d, 0);
+    cudaFree(d);
+    return s;
+}
+
+qsim_status qsim_amplitudes(qsim_t h, unsigned long long start, unsigned long long count, double *out) {
+    qsim_status s = check_usable(h);
+    if (s != QSIM_OK) return s;
+    if (!out && count) return fail(h, QSIM_ERR_ARG, "out is NULL");
+    if (start > (1ull << h->n) || count > (1ull << h->n) - start) return fail(h, QSIM_ERR_ARG, "range outside the state");
+    if ((s = qsim_flush(h)) != QSIM_OK) return s;
+    const unsigned long long chunk = 1ull << 26;
+    double2 *d = nullptr;
+    unsigned long long first = std::min(count, chunk);
+    if (count == 0) return QSIM_OK;
+    CK(cudaMalloc(&d, first * 16));
+    for (unsigned long long done = 0; done < count;) {
+        unsigned long long cnt = std::min(chunk, count - done);
+        unsigned long long tiles = ((start + done + cnt - 1) >> h->c) - ((start + done) >> h->c) + 1;
+        cudaError_t e = qs::launch_amplitudes(h->arena[h->cur], h->table[h->cur], h->c, start + done, cnt, d,
+                                              h->scal, grid_for(h, tiles, 4), h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out + 2 * done, d, cnt * 16, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) { cudaFree(d); return fail(h, QSIM_ERR_CUDA, "amplitudes: %s", cudaGetErrorString(e)); }
+        done += cnt;
+    }
+    cudaFree(d);
+    if ((s = read_scalars(h)) != QSIM_OK) return s;
+    if (h->hscal->err) return device_error(h, h->hscal->err);
+    return QSIM_OK;
+}
+
+qsim_status qsim_probabilities(qsim_t h, const int *qubits, int nq, double *out) {
+    qsim_status s = check_usable(h);
+    if (s != QSIM_OK) return s;
+    if (nq < 0 || nq > 24 || nq > h->n || !out || (nq && !qubits)) return fail(h, QSIM_ERR_ARG, "nq must be 0..24 with valid buffers");
+    unsigned long long used = 0;
+    for (int i = 0; i < nq; ++i) {
+        if (qubits[i] < 0 || qubits[i] >= h->n || ((used >> qubits[i]) & 1ull)) return fail(h, QSIM_ERR_ARG, "bad qubit list");
+        used |= 1ull << qubits[i];
+    }
+    if ((s = qsim_flush(h)) != QSIM_OK) return s;
+    const size_t nb = (size_t)1 << nq;
+    unsigned long long *dbk = nullptr;
+    int *dq = nullptr;
+    CK(cudaMalloc(&dbk, nb * 16));
+    CK(cudaMalloc(&dq, 32 * sizeof(int)));
+    std::vector<unsigned long long> hb(2 * nb);
+    cudaError_t e = cudaMemsetAsync(dbk, 0, nb * 16, h->stream);
+    if (e == cudaSuccess && nq) e = cudaMemcpyAsync(dq, qubits, nq * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = qs::launch_probs(h->arena[h->cur], h->table[h->cur], h->c, h->ntiles, dq, nq, dbk,
+                                               h->scal, grid_for(h, h->ntiles, 4), h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), dbk, nb * 16, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(dbk);
+    cudaFree(dq);
+    if (e != cudaSuccess) return fail(h, QSIM_ERR_CUDA, "probabilities: %s", cudaGetErrorString(e));
+    unsigned __int128 tot = 0;
+    for (size_t j = 0; j < nb; ++j) tot += ((unsigned __int128)hb[2 * j + 1] << 64) | hb[2 * j];
+    double dt = units_to_double_host((unsigned long long)tot, (unsigned long long)(tot >> 64));
+    for (size_t j = 0; j < nb; ++j) {
+        double v = units_to_double_host(hb[2 * j], hb[2 * j + 1]);
+        out[j] = dt > 0.0 ? v / dt : 0.0;
+    }
+    if ((s = read_scalars(h)) != QSIM_OK) return s;
+    if (h->hscal->err) return device_error(h, h->hscal->err);
+    return QSIM_OK;
+}
+
+qsim_status qsim_fidelity(qsim_t h, const qsim_ref *ref, double *F, double *overlap_abs) {
+    qsim_status s = check_usable(h);
+    if (s != QSIM_OK) return s;
+    if (!ref) return fail(h, QSIM_ERR_ARG, "ref is NULL");
+    if ((s = qsim_flush(h)) != QSIM_OK) return s;
+    qs::RefSpec rs{};
+    rs.kind = ref->kind;
+    rs.n = h->n;
+    double2 *tmp = nullptr;
+    const unsigned long long N = 1ull << h->n;
+    switch (ref->kind) {
+        case QSIM_REF_HANDLE: {
+            qsim_t o = ref->other;
+            if (!o || o->n != h->n || o->c != h->c) return fail(h, QSIM_ERR_ARG, "reference handle needs the same n and tile size");
+            if (o != h && (s = qsim_flush(o)) != QSIM_OK) return fail(h, s, "reference flush failed: %s", o->err.c_str());
+            CK(cudaStreamSynchronize(o->stream));
+            rs.kind = 0;
+            rs.o_arena = o->arena[o->cur];
+            rs.o_table = o->table[o->cur];
+            break;
+        }
+        case QSIM_REF_QFT_BASIS:
+            if (ref->x >= N) return fail(h, QSIM_ERR_ARG, "x out of range");
+            rs.kind = 1;
+            rs.x = ref->x;
+            rs.qft_mag = 1.0 / std::sqrt((double)N);
+            break;
+        case QSIM_REF_GROVER: {
+            if (ref->x >= N || ref->iterations < 0) return fail(h, QSIM_ERR_ARG, "bad Grover reference");
+            rs.kind = 2;
+            rs.x = ref->x;
+            double th = std::asin(1.0 / std::sqrt((double)N));
+            int k = ref->iterations;
+            double sg = (k & 1) ? -1.0 : 1.0;
+            rs.grov_m = sg * std::sin((2 * k + 1) * th);
+            rs.grov_o = N > 1 ? sg * std::cos((2 * k + 1) * th) / std::sqrt((double)(N - 1)) : 0.0;
+            break;
+        }
+        case QSIM_REF_DENSE_HOST:
+            if (!ref->dense) return fail(h, QSIM_ERR_ARG, "dense is NULL");
+            CK(cudaMalloc(&tmp, N * 16));
+            CK(cudaMemcpyAsync(tmp, ref->dense, N * 16, cudaMemcpyHostToDevice, h->stream));
+            rs.kind = 3;
+            rs.dense = tmp;
+            break;
+        case QSIM_REF_DENSE_DEVICE:
+            if (!ref->dense) return fail(h, QSIM_ERR_ARG, "dense is NULL");
+            rs.kind = 3;
+            rs.dense = reinterpret_cast<const double2 *>(ref->dense);
+            break;
+        default:
+            return fail(h, QSIM_ERR_ARG, "unknown reference kind");
+    }
+    qs::Acc4 *a = nullptr, *b = nullptr;
+    cudaError_t e = cudaMalloc(&a, h->ntiles * sizeof(qs::Acc4));
+    if (e == cudaSuccess) e = cudaMalloc(&b, std::max<unsigned long long>(1, h->ntiles / 2) * sizeof(qs::Acc4));
+    if (e == cudaSuccess)
+        e = qs::launch_fidelity(h->arena[h->cur], h->table[h->cur], h->c, h->ntiles, rs, a, h->scal,
+                                grid_for(h, h->ntiles, 4), h->stream);
+    unsigned long long cnt = h->ntiles;
+    while (e == cudaSuccess && cnt > 1) {
+        e = qs::launch_pair_sum(a, b, cnt / 2, grid_for(h, cnt / 2 / qs::THREADS + 1, 8), h->stream);
+        std::swap(a, b);
+        cnt /= 2;
+    }
+    qs::Acc4 r{};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&r, a, sizeof r, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (a) cudaFree(a);
+    if (b) cudaFree(b);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return fail(h, QSIM_ERR_CUDA, "fidelity: %s", cudaGetErrorString(e));
+    double f = (r.z > 0 && r.w > 0) ? (r.x * r.x + r.y * r.y) / (r.z * r.w) : 0.0;
+    if (F) *F = f;
+    if (overlap_abs) *overlap_abs = std::sqrt(f);
+    if ((s = read_scalars(h)) != QSIM_OK) return s;
+    if (h->hscal->err) return device_error(h, h->hscal->err);
+    return QSIM_OK;
+}
+
+qsim_status qsim_compressed_bytes(qsim_t h, unsigned long long *stream_bytes, unsigned long long *footprint_bytes) {
+    qsim_status s = check_usable(h);
+    if (s != QSIM_OK) return s;
+    if ((s = qsim_flush(h)) != QSIM_OK) return s;
+    unsigned long long *d = nullptr, tot = 0;
+    CK(cudaMalloc(&d, sizeof(unsigned long long)));
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof *d, h->stream);
+    if (e == cudaSuccess)
+        e = qs::launch_sum_sizes(h->arena[h->cur], h->table[h->cur], h->ntiles, d,
+                                 grid_for(h, h->ntiles / qs::THREADS + 1, 8), h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, d, sizeof tot, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(h, QSIM_ERR_CUDA, "sizes: %s", cudaGetErrorString(e));
+    if (stream_bytes) *stream_bytes = tot;
+    if (footprint_bytes)
+        *footprint_bytes = h->cap[0] + h->cap[1] + h->ntiles * 32ull + sizeof(qs::DevScalars);
+    return QSIM_OK;
+}
+
+qsim_status qsim_stats(qsim_t h, qsim_stats_t *out) {
+    if (!h || !out) return fail(h, QSIM_ERR_ARG, "null argument");
+    if (!h->invalid) {
+        qsim_status s = read_scalars(h);
+        if (s != QSIM_OK) return s;
+    }
+    *out = h->st;
+    for (int i = 0; i < 8; ++i) out->level_hist[i] = h->hscal->hist[i];
+    out->items_done = h->hscal->items_done;
+    out->items_skipped = h->hscal->items_skipped;
+    out->alpha = h->hscal->alpha;
+    out->tile_log2 = h->c;
+    out->hmax = h->hmax;
+    out->depth = h->depth;
+    out->n_qubits = h->n;
+    return QSIM_OK;
+}
+
+qsim_status qsim_export_tiles(qsim_t h, unsigned long long first, unsigned long long count, void *out,
+                              unsigned long long cap, unsigned long long *sizes) {
+    qsim_status s = check_usable(h);
+    if (s != QSIM_OK) return s;
+    if (!sizes || first > h->ntiles || count > h->ntiles - first) return fail(h, QSIM_ERR_ARG, "bad tile range");
+    if ((s = qsim_flush(h)) != QSIM_OK) return s;
+    if (count == 0) return QSIM_OK;
+    unsigned long long *dsz = nullptr, *doff = nullptr;
+    uint8_t *dbuf = nullptr;
+    CK(cudaMalloc(&dsz, count * 8));
+    cudaError_t e = qs::launch_sizes(h->arena[h->cur], h->table[h->cur], first, count, dsz,
+                                     grid_for(h, count / qs::THREADS + 1, 8), h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sizes, dsz, count * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) { cudaFree(dsz); return fail(h, QSIM_ERR_CUDA, "export sizes: %s", cudaGetErrorString(e)); }
+    if (!out) { cudaFree(dsz); return QSIM_OK; }
+    std::vector<unsigned long long> offs(count);
+    unsigned long long tot = 0;
+    for (unsigned long long i = 0; i < count; ++i) { offs[i] = tot; tot += sizes[i]; }
+    if (tot > cap) { cudaFree(dsz); return fail(h, QSIM_ERR_ARG, "export needs %llu bytes", tot); }
+    e = cudaMalloc(&doff, count * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&dbuf, tot);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(doff, offs.data(), count * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = qs::launch_gather(h->arena[h->cur], h->table[h->cur], first, count, doff, dsz, dbuf,
+                              grid_for(h, count, 8), h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dbuf, tot, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(dsz);
+    if (doff) cudaFree(doff);
+    if (dbuf) cudaFree(dbuf);
+    if (e != cudaSuccess) return fail(h, QSIM_ERR_CUDA, "export: %s", cudaGetErrorString(e));
+    return QSIM_OK;
+}
+
+qsim_status qsim_import_tiles(qsim_t h, unsigned long long first, unsigned long long count, const void *data,
+                              const unsigned long long *sizes) {
+    qsim_status s = check_usable(h);
+    if (s != QSIM_OK) return s;
+    if (!data || !sizes || first > h->ntiles || count > h->ntiles - first) return fail(h, QSIM_ERR_ARG, "bad tile range");
+    if ((s = qsim_flush(h)) != QSIM_OK) return s;
+    if (count == 0) return QSIM_OK;
+    std::vector<unsigned long long> offs(count);
+    unsigned long long tot = 0;
+    for (unsigned long long i = 0; i < count; ++i) {
+        if (sizes[i] < (unsigned long long)qs::HDR || (sizes[i] & 15ull) || sizes[i] > tile_bytes_worst(h))
+            return fail(h, QSIM_ERR_FORMAT, "tile %llu: bad stream size %llu", first + i, sizes[i]);
+        offs[i] = tot;
+        tot += sizes[i];
+    }
+    uint8_t *dbuf = nullptr;
+    unsigned long long *doff = nullptr, *dsz = nullptr, *dparts = nullptr;
+    unsigned int *dbad = nullptr, hbad = 0;
+    CK(cudaMalloc(&dbuf, tot));
+    cudaError_t e = cudaMalloc(&doff, count * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&dsz, count * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&dparts, count * 16);
+    if (e == cudaSuccess) e = cudaMalloc(&dbad, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemsetAsync(dbad, 0, sizeof(unsigned), h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dbuf, data, tot, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(doff, offs.data(), count * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dsz, sizes, count * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = qs::launch_validate(dbuf, doff, dsz, count, h->c, dparts, dbad, grid_for(h, count, 4), h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, dbad, sizeof hbad, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(h->stream);
+        if (dbuf) cudaFree(dbuf);
+        if (doff) cudaFree(doff);
+        if (dsz) cudaFree(dsz);
+        if (dparts) cudaFree(dparts);
+        if (dbad) cudaFree(dbad);
+    };
+    if (e != cudaSuccess) { cleanup(); return fail(h, QSIM_ERR_CUDA, "import: %s", cudaGetErrorString(e)); }
+    if (hbad) { cleanup(); return fail(h, QSIM_ERR_FORMAT, "%u imported stream(s) failed to decode", hbad); }
+    // append after the live bytes of the current arena (grow by copying)
+    unsigned long long need = h->used + tot;
+    if (h->cap[h->cur] < need) {
+        uint8_t *na = nullptr;
+        unsigned long long nc = round_up(need + need / 4, 1ull << 21);
+        e = cudaMalloc(&na, nc);
+        if (e == cudaSuccess && h->used) e = cudaMemcpyAsync(na, h->arena[h->cur], h->used, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) { if (na) cudaFree(na); cleanup(); return fail(h, QSIM_ERR_OOM, "import: %s", cudaGetErrorString(e)); }
+        cudaFree(h->arena[h->cur]);
+        h->arena[h->cur] = na;
+        h->cap[h->cur] = nc;
+    }
+    e = qs::launch_place(dbuf, doff, dsz, count, first, h->used, h->arena[h->cur], h->table[h->cur], dparts, h->part,
+                         grid_for(h, count, 8), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&h->scal->acc_lo, 0, 2 * sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess) e = qs::launch_norm_from_parts(h->part, h->ntiles, h->scal, grid_for(h, h->ntiles / qs::THREADS + 1, 4), h->stream);
+    if (e == cudaSuccess) e = qs::launch_finalize(h->scal, h->normalize, nullptr, 0, 0, h->stream);
+    cleanup();
+    if (e != cudaSuccess) return fail(h, QSIM_ERR_CUDA, "import: %s", cudaGetErrorString(e));
+    h->used += tot;
+    return read_scalars(h);
+}
+
+int qsim_plan_sweeps(int n, int tile_log2, int hmax, int depth, int ngates, const int *ntargets,
+                     const int *targets, const double *matrices, int *out_lo, int *out_h, int *out_H,
+                     int cap) {
+    if (n < 1 || n > MAX_QUBITS || tile_log2 < 1 || tile_log2 > n || hmax < 1 || hmax > 2 || depth < 1 ||
+        ngates < 0 || (ngates && (!ntargets || !targets || !matrices)))
+        return -1;
+    std::vector<HostGate> g(ngates);
+    for (int i = 0; i < ngates; ++i) {
+        if (ntargets[i] < 1 || ntargets[i] > 2) return -1;
+        g[i].k = ntargets[i];
+        for (int j = 0; j < g[i].k; ++j) {
+            g[i].t[j] = targets[2 * i + j];
+            if (g[i].t[j] < 0 || g[i].t[j] >= n) return -1;
+        }
+        std::memcpy(g[i].m, matrices + 32 * i, sizeof g[i].m);
+        g[i].diag = matrix_is_diagonal(g[i].k, g[i].m);
+    }
+    std::vector<Sweep> sw;
+    if (plan_sweeps(n, tile_log2, hmax, depth, g, sw) < 0) return -1;
+    if ((int)sw.size() > cap) return -2;
+    for (size_t i = 0; i < sw.size(); ++i) {
+        if (out_lo) out_lo[i] = sw[i].lo;
+        if (out_h) out_h[i] = sw[i].h;
+        if (out_H) { out_H[2 * i] = sw[i].H[0]; out_H[2 * i + 1] = sw[i].H[1]; }
+    }
+    return (int)sw.size();
+}
+
+}  // extern "C"

@@ -1,0 +1,1244 @@
+// Device code of the compressed simulator: the tile codec (decode/encode),
+// the fused decompress -> normalize -> gate run -> compress sweep
+// (Algorithm 2 of the paper, over tile groups), and the read-out kernels.
+//
+// Arithmetic contract (kept bit-identical with the CPU oracle, which is
+// written separately):
+//   * gate rows skip exactly-zero entries; first term a product, later
+//     terms fused multiply-adds; real / imaginary / general entries as in
+//     term_first / term_acc; explicit __dmul_rn/__fma_rn (no contraction);
+//   * normalize multiplies each component by alpha (skipped when alpha==1);
+//   * the codec is integer-only; the norm is an exact fixed-point sum.
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "qsim_dev.cuh"
+
+namespace qs {
+
+constexpr unsigned long long MAG = 0x7FFFFFFFFFFFFFFFull;
+constexpr unsigned long long MIN_NORMAL = 0x0010000000000000ull;
+constexpr unsigned long long LOSSY_LIMIT = 0x7FE0000000000000ull;
+constexpr unsigned long long INF_BITS = 0x7FF0000000000000ull;
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+enum { M_CONST = 0, M_PACKED = 1, M_RAW = 2 };
+enum { S_CLEAR = 0, S_SET = 1, S_PATTERN = 2, S_WORDS = 3 };
+
+__device__ __forceinline__ Acc4 make_acc4(double x, double y, double z, double w) {
+    Acc4 a;
+    a.x = x; a.y = y; a.z = z; a.w = w;
+    return a;
+}
+__device__ __forceinline__ unsigned long long dbits(double x) {
+    return (unsigned long long)__double_as_longlong(x);
+}
+__device__ __forceinline__ double bitsd(unsigned long long u) {
+    return __longlong_as_double((long long)u);
+}
+__device__ __forceinline__ unsigned long long quant(unsigned long long B, int s) {
+    return s == 0 ? B : (B + (1ull << (s - 1))) >> s;
+}
+__device__ __forceinline__ unsigned long long zigzag(unsigned long long r) {
+    return (r << 1) ^ (unsigned long long)((long long)r >> 63);
+}
+__device__ __forceinline__ unsigned long long unzigzag(unsigned long long z) {
+    return (z >> 1) ^ (0ull - (z & 1ull));
+}
+__device__ __forceinline__ int bitlen64(unsigned long long v) { return 64 - __clzll(v); }
+
+__device__ __forceinline__ unsigned long long shfl64(unsigned long long v, int src) {
+    unsigned lo = __shfl_sync(FULL, (unsigned)v, src);
+    unsigned hi = __shfl_sync(FULL, (unsigned)(v >> 32), src);
+    return ((unsigned long long)hi << 32) | lo;
+}
+__device__ __forceinline__ unsigned long long shfl_up64(unsigned long long v, int d) {
+    unsigned lo = __shfl_up_sync(FULL, (unsigned)v, d);
+    unsigned hi = __shfl_up_sync(FULL, (unsigned)(v >> 32), d);
+    return ((unsigned long long)hi << 32) | lo;
+}
+__device__ __forceinline__ unsigned long long warp_or64(unsigned long long v) {
+    unsigned lo = __reduce_or_sync(FULL, (unsigned)v);
+    unsigned hi = __reduce_or_sync(FULL, (unsigned)(v >> 32));
+    return ((unsigned long long)hi << 32) | lo;
+}
+
+// ---------------------------------------------------------------- norm
+// floor(x^2 * 2^112) as (hi, lo); *range set when |x| >= 16.
+__device__ __forceinline__ void sq_units(unsigned long long u, unsigned long long &lo,
+                                         unsigned long long &hi, unsigned &range) {
+    u &= MAG;
+    unsigned long long E = u >> 52, F = u & 0xFFFFFFFFFFFFFull;
+    lo = hi = 0;
+    if (E >= 1027) { range = 1; return; }
+    unsigned long long mant = E ? (F | (1ull << 52)) : F;
+    long long Ee = E ? (long long)E : 1;
+    unsigned long long pl = mant * mant, ph = __umul64hi(mant, mant);   // < 2^106
+    long long sh = 2 * Ee - 2150 + 112;
+    if (sh >= 0) {                       // sh <= 14
+        if (sh == 0) { lo = pl; hi = ph; }
+        else { hi = (ph << sh) | (pl >> (64 - sh)); lo = pl << sh; }
+    } else {
+        long long r = -sh;
+        if (r >= 106) return;
+        if (r >= 64) { lo = ph >> (r - 64); hi = 0; }
+        else { lo = (pl >> r) | (r ? (ph << (64 - r)) : 0ull); hi = ph >> r; }
+    }
+}
+
+__device__ __forceinline__ void add128(unsigned long long &lo, unsigned long long &hi,
+                                       unsigned long long alo, unsigned long long ahi) {
+    unsigned long long nlo = lo + alo;
+    hi += ahi + (nlo < lo ? 1ull : 0ull);
+    lo = nlo;
+}
+
+__device__ __forceinline__ void warp_sum128(unsigned long long &lo, unsigned long long &hi) {
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long olo = shfl64(lo, (threadIdx.x & 31) ^ o);
+        unsigned long long ohi = shfl64(hi, (threadIdx.x & 31) ^ o);
+        add128(lo, hi, olo, ohi);
+    }
+}
+
+// add (lo, hi) to a global 128-bit accumulator; exact under concurrency
+__device__ __forceinline__ void atomic_add128(unsigned long long *alo, unsigned long long *ahi,
+                                              unsigned long long lo, unsigned long long hi) {
+    unsigned long long old = atomicAdd(alo, lo);
+    unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+    if (hi + carry) atomicAdd(ahi, hi + carry);
+}
+
+// correctly rounded double of (hi, lo) * 2^-112
+__device__ double units_to_double(unsigned long long lo, unsigned long long hi) {
+    if (hi == 0 && lo == 0) return 0.0;
+    if (hi == 0) {
+        int p = bitlen64(lo);
+        if (p <= 64) return ldexp(__ull2double_rn(lo), -112);
+    }
+    int p = 64 + bitlen64(hi);           // hi != 0
+    int drop = p - 64;                   // 1..64
+    unsigned long long top, rest;
+    if (drop == 64) { top = hi; rest = lo; }
+    else {
+        top = (hi << (64 - drop)) | (lo >> drop);
+        rest = lo & ((1ull << drop) - 1);
+    }
+    top |= (rest != 0) ? 1ull : 0ull;    // sticky bit keeps round-to-nearest exact
+    return ldexp(__ull2double_rn(top), drop - 112);
+}
+
+// ---------------------------------------------------------------- gates
+// y = u * x for one matrix entry (first term of a row)
+__device__ __forceinline__ void term_first(double ur, double ui, double xr, double xi,
+                                           double &yr, double &yi) {
+    if (ui == 0.0) {
+        if (ur == 1.0) { yr = xr; yi = xi; }                 // == 1.0 * x exactly
+        else if (ur == -1.0) { yr = -xr; yi = -xi; }         // == -1.0 * x exactly
+        else { yr = __dmul_rn(ur, xr); yi = __dmul_rn(ur, xi); }
+    } else if (ur == 0.0) {
+        yr = -__dmul_rn(ui, xi);
+        yi = __dmul_rn(ui, xr);
+    } else {
+        yr = __fma_rn(ur, xr, -__dmul_rn(ui, xi));
+        yi = __fma_rn(ur, xi, __dmul_rn(ui, xr));
+    }
+}
+
+// acc += u * x
+__device__ __forceinline__ void term_acc(double ur, double ui, double xr, double xi,
+                                         double &ar, double &ai) {
+    if (ui == 0.0) {
+        ar = __fma_rn(ur, xr, ar);
+        ai = __fma_rn(ur, xi, ai);
+    } else if (ur == 0.0) {
+        ar = __fma_rn(-ui, xi, ar);
+        ai = __fma_rn(ui, xr, ai);
+    } else {
+        ar = __fma_rn(ur, xr, __fma_rn(-ui, xi, ar));
+        ai = __fma_rn(ur, xi, __fma_rn(ui, xr, ai));
+    }
+}
+
+template <int DIM>
+__device__ __forceinline__ void row_eval(const double *m, int r, const double *xr,
+                                         const double *xi, double &yr, double &yi) {
+    bool first = true;
+    double ar = 0.0, ai = 0.0;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+        double ur = m[2 * (r * DIM + c)], ui = m[2 * (r * DIM + c) + 1];
+        if (ur == 0.0 && ui == 0.0) continue;
+        if (first) { term_first(ur, ui, xr[c], xi[c], ar, ai); first = false; }
+        else term_acc(ur, ui, xr[c], xi[c], ar, ai);
+    }
+    yr = ar;
+    yi = ai;
+}
+
+__device__ __forceinline__ unsigned insert_zero(unsigned v, int p) {
+    unsigned lowm = (1u << p) - 1u;
+    return ((v & ~lowm) << 1) | (v & lowm);
+}
+
+// Apply the sweep's gates to an item buffer of 2^mb amplitudes (planar
+// re/im in shared memory).  fixed = global index bits of the item's
+// non-buffer qubits.
+__device__ void apply_gates(double *re, double *im, int mb, const DGate *gates, int ngates,
+                            unsigned long long fixed) {
+    const unsigned M = 1u << mb;
+    for (int gi = 0; gi < ngates; ++gi) {
+        const DGate &g = gates[gi];
+        if (((fixed ^ g.fcv) & g.fcm) != 0ull) continue;     // fixed control not met
+        const unsigned lcm = (unsigned)g.lcm, lcv = (unsigned)g.lcv;
+        if (g.diag) {
+            const int dim = 1 << g.k;
+            int fr = 0, bmask_p0 = g.pos[0], bmask_p1 = g.k > 1 ? g.pos[1] : -1;
+            if (bmask_p0 < 0) fr |= (int)((fixed >> g.t[0]) & 1ull);
+            if (g.k > 1 && bmask_p1 < 0) fr |= (int)((fixed >> g.t[1]) & 1ull) << 1;
+            for (unsigned l = threadIdx.x; l < M; l += THREADS) {
+                if ((l & lcm) != lcv) continue;
+                int r = fr;
+                if (bmask_p0 >= 0) r |= (int)((l >> bmask_p0) & 1u);
+                if (bmask_p1 >= 0) r |= (int)((l >> bmask_p1) & 1u) << 1;
+                double ur = g.m[2 * (r * dim + r)], ui = g.m[2 * (r * dim + r) + 1];
+                if (ui == 0.0 && ur == 1.0) continue;
+                double yr, yi;
+                if (ur == 0.0 && ui == 0.0) { yr = 0.0; yi = 0.0; }
+                else term_first(ur, ui, re[l], im[l], yr, yi);
+                re[l] = yr;
+                im[l] = yi;
+            }
+        } else if (g.k == 1) {
+            const int p = g.pos[0];
+            const unsigned bit = 1u << p;
+            for (unsigned pi = threadIdx.x; pi < (M >> 1); pi += THREADS) {
+                unsigned l0 = insert_zero(pi, p);
+                if ((l0 & lcm) != lcv) continue;
+                unsigned l1 = l0 | bit;
+                double xr[2] = {re[l0], re[l1]}, xi[2] = {im[l0], im[l1]};
+                double y0r, y0i, y1r, y1i;
+                row_eval<2>(g.m, 0, xr, xi, y0r, y0i);
+                row_eval<2>(g.m, 1, xr, xi, y1r, y1i);
+                re[l0] = y0r; im[l0] = y0i;
+                re[l1] = y1r; im[l1] = y1i;
+            }
+        } else {
+            const int p0 = g.pos[0], p1 = g.pos[1];
+            const int plo = p0 < p1 ? p0 : p1, phi = p0 < p1 ? p1 : p0;
+            for (unsigned qi = threadIdx.x; qi < (M >> 2); qi += THREADS) {
+                unsigned l = insert_zero(insert_zero(qi, plo), phi);
+                if ((l & lcm) != lcv) continue;
+                unsigned idx[4];
+                double xr[4], xi[4];
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    idx[s] = l | ((unsigned)(s & 1) << p0) | ((unsigned)(s >> 1) << p1);
+                    xr[s] = re[idx[s]];
+                    xi[s] = im[idx[s]];
+                }
+                double yr[4], yi[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) row_eval<4>(g.m, r, xr, xi, yr[r], yi[r]);
+#pragma unroll
+                for (int s = 0; s < 4; ++s) { re[idx[s]] = yr[s]; im[idx[s]] = yi[s]; }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Does gate g change any amplitude of the item with fixed bits `fixed`?
+__device__ __forceinline__ bool gate_touches(const DGate &g, unsigned long long fixed) {
+    if (((fixed ^ g.fcv) & g.fcm) != 0ull) return false;
+    bool allfixed = g.pos[0] < 0 && (g.k < 2 || g.pos[1] < 0);
+    if (allfixed) {
+        int dim = 1 << g.k, r = (int)((fixed >> g.t[0]) & 1ull);
+        if (g.k > 1) r |= (int)((fixed >> g.t[1]) & 1ull) << 1;
+        if (g.m[2 * (r * dim + r)] == 1.0 && g.m[2 * (r * dim + r) + 1] == 0.0) return false;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------- codec scratch
+struct Scratch {
+    uint32_t sw[64];          // sign word per (comp, group): index k*G + g
+    uint32_t nw[64];          // data words per (comp, group)
+    uint32_t woff[64];        // exclusive prefix of nw (words)
+    long long gtot[64];       // decode: group sums of residuals
+    long long gpre[64];       // decode: exclusive prefix of group sums
+    uint32_t wd[64];          // widths
+    uint32_t lvl_words[MAX_LEVELS];
+    uint32_t lvl_nonzero[MAX_LEVELS];
+    uint32_t hdr[8];
+    unsigned long long red_lo[NWARPS], red_hi[NWARPS];
+    unsigned long long anchor[2];
+    unsigned long long off;
+    uint32_t body, size, data_off, wtotal;
+    int mode, s, level, smode[2], ok, bad;
+    int flag_nonfinite, flag_inelig;
+};
+
+__device__ __forceinline__ uint32_t sign_bytes(int mode, int G) {
+    return mode == S_PATTERN ? 4u + 4u * (uint32_t)((G + 31) / 32)
+                             : (mode == S_WORDS ? 4u * (uint32_t)G : 0u);
+}
+
+// warp 0: exclusive scan of sc.nw[0..cnt) into sc.woff, total in sc.wtotal
+__device__ __forceinline__ void scan_words_warp0(Scratch &sc, int cnt) {
+    if (threadIdx.x >= 32) return;
+    int lane = threadIdx.x;
+    uint32_t carry = 0;
+    for (int base = 0; base < cnt; base += 32) {
+        uint32_t v = (base + lane < cnt) ? sc.nw[base + lane] : 0u;
+        uint32_t inc = v;
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t o = __shfl_up_sync(FULL, inc, d);
+            if (lane >= d) inc += o;
+        }
+        if (base + lane < cnt) sc.woff[base + lane] = carry + inc - v;
+        carry += __shfl_sync(FULL, inc, 31);
+    }
+    if (lane == 0) sc.wtotal = carry;
+}
+
+// ---------------------------------------------------------------- decode
+// Decode one stream into planar re/im (2^c values each).  CTA-wide; all
+// threads must call it.  Returns nonzero (and zero-fills) on a malformed
+// stream.
+__device__ int decode_tile(const uint8_t *src, int c, double *re, double *im, Scratch &sc) {
+    const int N = 1 << c;
+    const int G = N >= 32 ? N / 32 : 1;
+    const int L = N >= 32 ? 32 : N;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < 8) sc.hdr[tid] = reinterpret_cast<const uint32_t *>(src)[tid];
+    __syncthreads();
+    const uint32_t h0 = sc.hdr[0];
+    const int mode = h0 & 0xFF, s = (h0 >> 8) & 0xFF;
+    const int sm0 = (h0 >> 24) & 3, sm1 = (h0 >> 26) & 3;
+    const uint32_t body = sc.hdr[1];
+    const unsigned long long a0 = ((unsigned long long)sc.hdr[3] << 32) | sc.hdr[2];
+    const unsigned long long a1 = ((unsigned long long)sc.hdr[5] << 32) | sc.hdr[4];
+    const int hc = sc.hdr[6] & 0xFF;
+    const uint8_t *b = src + HDR;
+    bool bad = hc != c || mode > 2 || (mode != M_RAW && s > 52) || (body & 15u);
+    if (!bad && mode == M_RAW) bad = body != 16u * (uint32_t)N;
+    if (!bad && mode == M_CONST) bad = body != 0 || sm0 > 1 || sm1 > 1;
+    if (!bad && mode == M_PACKED) {
+        uint32_t meta = sign_bytes(sm0, G) + sign_bytes(sm1, G);
+        bad = meta + 2u * G > body;
+    }
+    if (bad) {
+        for (int i = tid; i < N; i += THREADS) { re[i] = 0.0; im[i] = 0.0; }
+        __syncthreads();
+        return 1;
+    }
+    if (mode == M_CONST) {
+        double v0 = bitsd((a0 << s) | ((unsigned long long)sm0 << 63));
+        double v1 = bitsd((a1 << s) | ((unsigned long long)sm1 << 63));
+        for (int i = tid; i < N; i += THREADS) { re[i] = v0; im[i] = v1; }
+        __syncthreads();
+        return 0;
+    }
+    if (mode == M_RAW) {
+        const double2 *v = reinterpret_cast<const double2 *>(b);
+        for (int i = tid; i < N; i += THREADS) {
+            double2 x = v[i];
+            re[i] = x.x;
+            im[i] = x.y;
+        }
+        __syncthreads();
+        return 0;
+    }
+    // PACKED: sign words and widths
+    const uint32_t sb0 = sign_bytes(sm0, G), sb1 = sign_bytes(sm1, G);
+    const uint32_t lanes = L == 32 ? FULL : ((1u << L) - 1u);
+    for (int t = tid; t < 2 * G; t += THREADS) {
+        int k = t / G, g = t % G;
+        int md = k ? sm1 : sm0;
+        const uint8_t *sec = b + (k ? sb0 : 0);
+        uint32_t v;
+        if (md == S_CLEAR) v = 0;
+        else if (md == S_SET) v = lanes;
+        else if (md == S_PATTERN) {
+            uint32_t P = reinterpret_cast<const uint32_t *>(sec)[0];
+            uint32_t fl = (reinterpret_cast<const uint32_t *>(sec)[1 + g / 32] >> (g % 32)) & 1u;
+            v = fl ? ~P : P;
+        } else v = reinterpret_cast<const uint32_t *>(sec)[g];
+        sc.sw[t] = v;
+        uint32_t w = b[sb0 + sb1 + t];
+        sc.wd[t] = w;
+        sc.nw[t] = ((uint32_t)L * w + 31u) / 32u;
+    }
+    __syncthreads();
+    scan_words_warp0(sc, 2 * G);
+    if (tid == 0) {
+        int bd = 0;
+        for (int t = 0; t < 2 * G; ++t) bd |= sc.wd[t] > 64;
+        uint32_t doff = (sb0 + sb1 + 2u * G + 3u) & ~3u;
+        sc.data_off = doff;
+        if ((unsigned long long)doff + 4ull * sc.wtotal > body) bd = 1;
+        sc.bad = bd;
+    }
+    __syncthreads();
+    if (sc.bad) {
+        for (int i = tid; i < N; i += THREADS) { re[i] = 0.0; im[i] = 0.0; }
+        __syncthreads();
+        return 1;
+    }
+    const uint32_t *data = reinterpret_cast<const uint32_t *>(b + sc.data_off);
+    long long *reI = reinterpret_cast<long long *>(re);
+    long long *imI = reinterpret_cast<long long *>(im);
+    for (int t = warp; t < 2 * G; t += NWARPS) {
+        int k = t / G, g = t % G;
+        uint32_t w = sc.wd[t], nwd = sc.nw[t];
+        const uint32_t *base = data + sc.woff[t];
+        unsigned long long z = 0;
+        if (lane < L && w) {
+            uint32_t bo = (uint32_t)lane * w, j0 = bo >> 5, sh = bo & 31u;
+            uint32_t w0 = base[j0];
+            uint32_t w1 = j0 + 1 < nwd ? base[j0 + 1] : 0u;
+            uint32_t w2 = j0 + 2 < nwd ? base[j0 + 2] : 0u;
+            unsigned long long lo = (unsigned long long)w0 | ((unsigned long long)w1 << 32);
+            unsigned long long v = sh ? ((lo >> sh) | ((unsigned long long)w2 << (64 - sh))) : lo;
+            z = w == 64 ? v : (v & ((1ull << w) - 1ull));
+        }
+        unsigned long long r = unzigzag(z);
+        if (g == 0 && lane == 0) r = 0;
+        if (lane >= L) r = 0;
+        unsigned long long inc = r;
+        for (int d = 1; d < 32; d <<= 1) {
+            unsigned long long o = shfl_up64(inc, d);
+            if (lane >= d) inc += o;
+        }
+        if (lane < L) (k ? imI : reI)[g * 32 + lane] = (long long)inc;
+        if (lane == L - 1) sc.gtot[t] = (long long)inc;
+    }
+    __syncthreads();
+    if (warp < 2) {               // warp k scans the group sums of component k
+        int k = warp;
+        unsigned long long carry = 0;
+        for (int base = 0; base < G; base += 32) {
+            unsigned long long v = base + lane < G ? (unsigned long long)sc.gtot[k * G + base + lane] : 0ull;
+            unsigned long long inc = v;
+            for (int d = 1; d < 32; d <<= 1) {
+                unsigned long long o = shfl_up64(inc, d);
+                if (lane >= d) inc += o;
+            }
+            if (base + lane < G) sc.gpre[k * G + base + lane] = (long long)(carry + inc - v);
+            carry += shfl64(inc, 31);
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < N; i += THREADS) {
+        int g = i >> 5, l = i & 31;
+        unsigned long long q0 = a0 + (unsigned long long)sc.gpre[g] + (unsigned long long)reI[i];
+        unsigned long long q1 = a1 + (unsigned long long)sc.gpre[G + g] + (unsigned long long)imI[i];
+        unsigned long long s0 = (sc.sw[g] >> l) & 1u, s1 = (sc.sw[G + g] >> l) & 1u;
+        re[i] = bitsd((q0 << s) | (s0 << 63));
+        im[i] = bitsd((q1 << s) | (s1 << 63));
+    }
+    __syncthreads();
+    return 0;
+}
+
+// ---------------------------------------------------------------- encode
+struct EncodeOut {
+    unsigned long long off;
+    bool ok;
+};
+
+// Quantised code of component value i (lane context) for comp k
+__device__ __forceinline__ unsigned long long code_of(const double *v, int i, int s) {
+    return quant(dbits(v[i]) & MAG, s);
+}
+
+// z of this lane for task (k, g) at shift s; lanes >= L give 0
+__device__ __forceinline__ unsigned long long lane_z(const double *v, int g, int lane, int L, int s) {
+    int i = g * 32 + lane;
+    unsigned long long q = lane < L ? code_of(v, i, s) : 0ull;
+    unsigned long long qp = shfl_up64(q, 1);
+    if (lane == 0) qp = g > 0 ? code_of(v, i - 1, s) : q;
+    unsigned long long z = zigzag(q - qp);
+    return lane < L ? z : 0ull;
+}
+
+// Encode planar re/im (2^c values each) of tile `tile` into the output
+// arena with Algorithm 2's ladder.  CTA-wide.  Writes the stream, its
+// offset in out_table, its norm partial, and adds to the running norm.
+__device__ EncodeOut encode_tile(const double *re, const double *im, const CodecCfg &cc,
+                                 unsigned long long tile, uint8_t *out_arena,
+                                 unsigned long long out_cap, unsigned long long *out_table,
+                                 unsigned long long *part, DevScalars *scal,
+                                 unsigned sweep_id, Scratch &sc) {
+    const int c = cc.c, N = 1 << c;
+    const int G = N >= 32 ? N / 32 : 1;
+    const int L = N >= 32 ? 32 : N;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lanes = L == 32 ? FULL : ((1u << L) - 1u);
+
+    // A: value classes
+    int nonfin = 0, inel = 0;
+    for (int i = tid; i < N; i += THREADS) {
+        unsigned long long B0 = dbits(re[i]) & MAG, B1 = dbits(im[i]) & MAG;
+        nonfin |= (B0 >= INF_BITS) | (B1 >= INF_BITS);
+        inel |= (B0 != 0 && (B0 < MIN_NORMAL || B0 >= LOSSY_LIMIT)) |
+                (B1 != 0 && (B1 < MIN_NORMAL || B1 >= LOSSY_LIMIT));
+    }
+    nonfin = __syncthreads_or(nonfin);
+    inel = __syncthreads_or(inel);
+    const bool raw_only = cc.force_raw || nonfin;
+
+    // B: sign words
+    if (!raw_only) {
+        for (int t = warp; t < 2 * G; t += NWARPS) {
+            int k = t / G, g = t % G;
+            const double *v = k ? im : re;
+            bool sg = lane < L && (dbits(v[g * 32 + lane]) >> 63);
+            uint32_t word = __ballot_sync(FULL, sg);
+            if (lane == 0) sc.sw[t] = word;
+        }
+        if (tid < MAX_LEVELS) { sc.lvl_words[tid] = 0; sc.lvl_nonzero[tid] = 0; }
+    }
+    __syncthreads();
+    // C: sign modes (warp k, lane g; G <= 32)
+    if (!raw_only && warp < 2) {
+        int k = warp;
+        uint32_t v = lane < G ? sc.sw[k * G + lane] : 0u;
+        bool any1 = __any_sync(FULL, lane < G && v != 0u);
+        bool allset = __all_sync(FULL, lane >= G || v == lanes);
+        uint32_t P = __shfl_sync(FULL, v, 0);
+        bool pat = G >= 2 && __all_sync(FULL, lane >= G || v == P || v == ~P);
+        if (lane == 0) sc.smode[k] = !any1 ? S_CLEAR : (allset ? S_SET : (pat ? S_PATTERN : S_WORDS));
+    }
+    // D: data words per level
+    if (!raw_only) {
+        for (int t = warp; t < 2 * G; t += NWARPS) {
+            int k = t / G, g = t % G;
+            const double *v = k ? im : re;
+            for (int lv = 0; lv < cc.nlev; ++lv) {
+                int s = inel ? 0 : cc.shifts[lv];
+                unsigned long long z = lane_z(v, g, lane, L, s);
+                unsigned long long oz = warp_or64(z);
+                if (lane == 0) {
+                    uint32_t w = oz ? (uint32_t)bitlen64(oz) : 0u;
+                    atomicAdd(&sc.lvl_words[lv], ((uint32_t)L * w + 31u) / 32u);
+                    if (oz) atomicOr(&sc.lvl_nonzero[lv], 1u);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // E: ladder decision (first level within max_bytes, else the last)
+    if (tid == 0) {
+        const uint32_t raw_body = 16u * (uint32_t)N;
+        if (raw_only) {
+            sc.mode = M_RAW; sc.s = 0; sc.level = 0; sc.body = raw_body;
+        } else {
+            uint32_t meta = sign_bytes(sc.smode[0], G) + sign_bytes(sc.smode[1], G);
+            uint32_t wb = (2u * G + 3u) & ~3u;
+            int pick = cc.nlev - 1;
+            int pmode = 0;
+            uint32_t pbody = 0;
+            for (int lv = 0; lv < cc.nlev; ++lv) {
+                int md;
+                uint32_t bd;
+                if (!sc.lvl_nonzero[lv] && sc.smode[0] <= S_SET && sc.smode[1] <= S_SET) {
+                    md = M_CONST; bd = 0;
+                } else {
+                    uint32_t pb = (meta + wb + 4u * sc.lvl_words[lv] + 15u) & ~15u;
+                    if (pb < raw_body) { md = M_PACKED; bd = pb; }
+                    else { md = M_RAW; bd = raw_body; }
+                }
+                pick = lv; pmode = md; pbody = bd;
+                if ((unsigned long long)(HDR + bd) <= cc.max_bytes) break;
+            }
+            sc.level = pick;
+            sc.mode = pmode;
+            sc.body = pbody;
+            sc.s = pmode == M_RAW ? 0 : (inel ? 0 : cc.shifts[pick]);
+        }
+        sc.size = HDR + sc.body;
+        sc.flag_nonfinite = nonfin;
+    }
+    __syncthreads();
+    const int mode = sc.mode, s = sc.s;
+    // F: widths at the chosen level
+    if (mode == M_PACKED) {
+        for (int t = warp; t < 2 * G; t += NWARPS) {
+            int k = t / G, g = t % G;
+            unsigned long long z = lane_z(k ? im : re, g, lane, L, s);
+            unsigned long long oz = warp_or64(z);
+            if (lane == 0) {
+                uint32_t w = oz ? (uint32_t)bitlen64(oz) : 0u;
+                sc.wd[t] = w;
+                sc.nw[t] = ((uint32_t)L * w + 31u) / 32u;
+            }
+        }
+    }
+    __syncthreads();
+    // G: word offsets, anchors, allocation
+    if (mode == M_PACKED) scan_words_warp0(sc, 2 * G);
+    if (tid == 32) {
+        unsigned long long off = atomicAdd(&scal->bump, (unsigned long long)sc.size);
+        bool ok = off + sc.size <= out_cap;
+        if (!ok) {
+            atomicOr(&scal->err, ERR_OVERFLOW);
+            atomicCAS(&scal->err_sweep, 0u, sweep_id + 1u);
+        }
+        sc.off = off;
+        sc.ok = ok;
+        if (mode != M_RAW) {
+            sc.anchor[0] = quant(dbits(re[0]) & MAG, s);
+            sc.anchor[1] = quant(dbits(im[0]) & MAG, s);
+        } else {
+            sc.anchor[0] = sc.anchor[1] = 0;
+        }
+        if (nonfin) atomicOr(&scal->err, ERR_NONFINITE);
+    }
+    __syncthreads();
+    EncodeOut res{sc.off, sc.ok != 0};
+    if (!res.ok) return res;
+    uint8_t *dst = out_arena + res.off;
+    // H: header
+    if (tid < 8) {
+        uint32_t v = 0;
+        switch (tid) {
+            case 0: {
+                uint32_t smb = mode == M_RAW ? 0u : (uint32_t)(sc.smode[0] | (sc.smode[1] << 2));
+                v = (uint32_t)mode | ((uint32_t)s << 8) | ((uint32_t)sc.level << 16) | (smb << 24);
+                break;
+            }
+            case 1: v = sc.body; break;
+            case 2: v = (uint32_t)sc.anchor[0]; break;
+            case 3: v = (uint32_t)(sc.anchor[0] >> 32); break;
+            case 4: v = (uint32_t)sc.anchor[1]; break;
+            case 5: v = (uint32_t)(sc.anchor[1] >> 32); break;
+            case 6: v = (uint32_t)c; break;
+            default: v = 0; break;
+        }
+        reinterpret_cast<uint32_t *>(dst)[tid] = v;
+    }
+    uint8_t *b = dst + HDR;
+    if (mode == M_RAW) {
+        double2 *o = reinterpret_cast<double2 *>(b);
+        for (int i = tid; i < N; i += THREADS) o[i] = make_double2(re[i], im[i]);
+    } else if (mode == M_PACKED) {
+        const int sm0 = sc.smode[0], sm1 = sc.smode[1];
+        const uint32_t sb0 = sign_bytes(sm0, G), sb1 = sign_bytes(sm1, G);
+        // sign sections (warp k)
+        if (warp < 2) {
+            int k = warp, md = k ? sm1 : sm0;
+            uint32_t *sec = reinterpret_cast<uint32_t *>(b + (k ? sb0 : 0));
+            uint32_t v = lane < G ? sc.sw[k * G + lane] : 0u;
+            if (md == S_PATTERN) {
+                uint32_t P = __shfl_sync(FULL, v, 0);
+                uint32_t fl = __ballot_sync(FULL, lane < G && v != P);
+                if (lane == 0) { sec[0] = P; sec[1] = fl; }
+            } else if (md == S_WORDS) {
+                if (lane < G) sec[lane] = v;
+            }
+        }
+        // width bytes and their padding
+        const uint32_t wb = (2u * G + 3u) & ~3u;
+        for (int t = tid; t < (int)wb; t += THREADS)
+            b[sb0 + sb1 + t] = t < 2 * G ? (uint8_t)sc.wd[t] : (uint8_t)0;
+        const uint32_t doff = sb0 + sb1 + wb;
+        uint32_t *data = reinterpret_cast<uint32_t *>(b + doff);
+        // data words: word j of a group gathers the lanes whose bits it holds
+        for (int t = warp; t < 2 * G; t += NWARPS) {
+            int k = t / G, g = t % G;
+            uint32_t w = sc.wd[t], nwd = sc.nw[t];
+            if (w == 0) continue;
+            unsigned long long z = lane_z(k ? im : re, g, lane, L, s);
+            uint32_t *gd = data + sc.woff[t];
+            const int span = (int)((32u + w - 1u) / w) + 1;
+            for (int rnd = 0; rnd < 2; ++rnd) {
+                int j = lane + 32 * rnd;
+                if (rnd == 1 && nwd <= 32) break;        // uniform across the warp
+                int a = (32 * j) / (int)w;
+                int bl = (32 * j + 31) / (int)w;
+                if (bl > L - 1) bl = L - 1;
+                uint32_t acc = 0;
+                for (int it = 0; it < span; ++it) {
+                    int src = a + it;
+                    unsigned long long v = shfl64(z, src & 31);
+                    if (src <= bl) {
+                        int o = src * (int)w - 32 * j;
+                        if (o >= 0) acc |= (uint32_t)(v << o);
+                        else acc |= (uint32_t)(v >> (-o));
+                    }
+                }
+                if ((uint32_t)j < nwd) gd[j] = acc;
+            }
+        }
+        // zero tail up to the 16-byte boundary
+        const uint32_t dend = doff + 4u * sc.wtotal;
+        for (uint32_t p = dend + tid; p < sc.body; p += THREADS) b[p] = 0;
+    }
+    // I: norm of the stored (reconstructed) values
+    unsigned long long lo = 0, hi = 0;
+    unsigned rng = 0;
+    for (int i = tid; i < N; i += THREADS) {
+        unsigned long long u0 = dbits(re[i]), u1 = dbits(im[i]);
+        if (mode != M_RAW) {
+            u0 = (quant(u0 & MAG, s) << s) | (u0 & ~MAG);
+            u1 = (quant(u1 & MAG, s) << s) | (u1 & ~MAG);
+        }
+        unsigned long long l0, h0, l1, h1;
+        sq_units(u0, l0, h0, rng);
+        sq_units(u1, l1, h1, rng);
+        add128(lo, hi, l0, h0);
+        add128(lo, hi, l1, h1);
+    }
+    rng = __syncthreads_or(rng);
+    warp_sum128(lo, hi);
+    if (lane == 0) { sc.red_lo[warp] = lo; sc.red_hi[warp] = hi; }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long tl = 0, th = 0;
+        for (int w = 0; w < NWARPS; ++w) add128(tl, th, sc.red_lo[w], sc.red_hi[w]);
+        part[2 * tile] = tl;
+        part[2 * tile + 1] = th;
+        atomic_add128(&scal->acc_lo, &scal->acc_hi, tl, th);
+        out_table[tile] = res.off;
+        atomicAdd(&scal->hist[sc.level], 1ull);
+        if (rng) atomicOr(&scal->err, ERR_RANGE);
+    }
+    __syncthreads();
+    return res;
+}
+
+// Copy one stream unchanged into the output arena (an item no gate touches).
+__device__ void carry_tile(const uint8_t *in_arena, const unsigned long long *in_table,
+                           unsigned long long tile, uint8_t *out_arena, unsigned long long out_cap,
+                           unsigned long long *out_table, const unsigned long long *part,
+                           DevScalars *scal, unsigned sweep_id, Scratch &sc) {
+    const uint8_t *src = in_arena + in_table[tile];
+    if (threadIdx.x == 0) {
+        uint32_t body = reinterpret_cast<const uint32_t *>(src)[1];
+        uint32_t size = HDR + body;
+        unsigned long long off = atomicAdd(&scal->bump, (unsigned long long)size);
+        bool ok = off + size <= out_cap;
+        if (!ok) {
+            atomicOr(&scal->err, ERR_OVERFLOW);
+            atomicCAS(&scal->err_sweep, 0u, sweep_id + 1u);
+        }
+        sc.off = off;
+        sc.ok = ok;
+        sc.size = size;
+        atomic_add128(&scal->acc_lo, &scal->acc_hi, part[2 * tile], part[2 * tile + 1]);
+        if (ok) out_table[tile] = off;
+    }
+    __syncthreads();
+    if (sc.ok) {
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+        uint4 *d4 = reinterpret_cast<uint4 *>(out_arena + sc.off);
+        for (uint32_t i = threadIdx.x; i < sc.size / 16u; i += THREADS) d4[i] = s4[i];
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- kernels
+__device__ __forceinline__ unsigned long long expand_item(unsigned long long item, int h,
+                                                           const int *Hbits) {
+    // insert zero bits at the tile-index positions of the paired qubits
+    unsigned long long v = item;
+    for (int i = 0; i < h; ++i) {
+        unsigned long long lowm = (1ull << Hbits[i]) - 1ull;
+        v = ((v & ~lowm) << 1) | (v & lowm);
+    }
+    return v;
+}
+
+// One sweep of Algorithm 2 over all items: decompress, normalize, apply
+// the gate run, compress with the ladder.  Persistent CTAs loop over items.
+__global__ void __launch_bounds__(THREADS) sweep_kernel(SweepParams p) {
+    extern __shared__ double smem[];
+    __shared__ Scratch sc;
+    __shared__ int s_touch;
+    if (threadIdx.x == 0) s_touch = *((volatile unsigned *)&p.scal->err) != 0u;
+    __syncthreads();
+    if (s_touch) return;                      // an earlier pass failed: leave the state
+    __syncthreads();
+    const int c = p.cc.c, N = 1 << c, mb = c + p.h;
+    double *re = smem, *im = smem + (1 << mb);
+    const double alpha = p.use_alpha ? p.scal->alpha : 1.0;
+    int Hbits[2] = {p.h > 0 ? p.H[0] - c : 0, p.h > 1 ? p.H[1] - c : 0};
+    for (unsigned long long item = blockIdx.x; item < p.nitems; item += gridDim.x) {
+        const unsigned long long T = expand_item(item, p.h, Hbits);
+        const unsigned long long fixed = T << c;
+        if (threadIdx.x == 0) {
+            int touch = alpha != 1.0;
+            for (int gi = 0; gi < p.ngates && !touch; ++gi)
+                if (gate_touches(p.gates[gi], fixed)) touch = 1;
+            s_touch = touch;
+        }
+        __syncthreads();
+        const int touched = s_touch;
+        __syncthreads();
+        if (!touched) {
+            for (int j = 0; j < (1 << p.h); ++j) {
+                unsigned long long Tj = T;
+                for (int i = 0; i < p.h; ++i)
+                    if ((j >> i) & 1) Tj |= 1ull << Hbits[i];
+                carry_tile(p.in_arena, p.in_table, Tj, p.out_arena, p.out_cap, p.out_table,
+                           p.part, p.scal, p.sweep_id, sc);
+            }
+            if (threadIdx.x == 0) atomicAdd(&p.scal->items_skipped, 1ull);
+            continue;
+        }
+        int bad = 0;
+        for (int j = 0; j < (1 << p.h); ++j) {
+            unsigned long long Tj = T;
+            for (int i = 0; i < p.h; ++i)
+                if ((j >> i) & 1) Tj |= 1ull << Hbits[i];
+            bad |= decode_tile(p.in_arena + p.in_table[Tj], c, re + j * N, im + j * N, sc);
+        }
+        if (bad && threadIdx.x == 0) atomicOr(&p.scal->err, ERR_FORMAT);
+        if (alpha != 1.0) {
+            for (int i = threadIdx.x; i < (1 << mb); i += THREADS) {
+                re[i] = __dmul_rn(re[i], alpha);
+                im[i] = __dmul_rn(im[i], alpha);
+            }
+            __syncthreads();
+        }
+        apply_gates(re, im, mb, p.gates, p.ngates, fixed);
+        for (int j = 0; j < (1 << p.h); ++j) {
+            unsigned long long Tj = T;
+            for (int i = 0; i < p.h; ++i)
+                if ((j >> i) & 1) Tj |= 1ull << Hbits[i];
+            encode_tile(re + j * N, im + j * N, p.cc, Tj, p.out_arena, p.out_cap, p.out_table,
+                        p.part, p.scal, p.sweep_id, sc);
+        }
+        if (threadIdx.x == 0) atomicAdd(&p.scal->items_done, 1ull);
+    }
+}
+
+// Finish a pass: publish the norm, the next normalize scale and the used
+// bytes; reset the accumulators.  Leaves everything alone after an error
+// so that the host can re-run the failed pass.
+__global__ void finalize_kernel(DevScalars *scal, int use_alpha, unsigned long long *used_hist,
+                                unsigned int slot, int record_used) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (scal->err) return;
+    scal->norm_lo = scal->acc_lo;
+    scal->norm_hi = scal->acc_hi;
+    scal->acc_lo = scal->acc_hi = 0;
+    if (record_used) {
+        scal->used = scal->bump;
+        if (used_hist) used_hist[slot] = scal->bump;
+        scal->bump = 0;
+    }
+    double nrm = units_to_double(scal->norm_lo, scal->norm_hi);
+    scal->alpha = (use_alpha && nrm > 0.0) ? __ddiv_rn(1.0, __dsqrt_rn(nrm)) : 1.0;
+}
+
+// Encode a state given densely (device, interleaved) or the basis state
+// |x> (dense == nullptr) into every tile.
+__global__ void __launch_bounds__(THREADS) init_kernel(const double2 *dense, unsigned long long x,
+                                                     CodecCfg cc, unsigned long long ntiles,
+                                                     uint8_t *out_arena, unsigned long long out_cap,
+                                                     unsigned long long *out_table,
+                                                     unsigned long long *part, DevScalars *scal) {
+    extern __shared__ double smem[];
+    __shared__ Scratch sc;
+    const int c = cc.c, N = 1 << c;
+    double *re = smem, *im = smem + N;
+    for (unsigned long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        if (dense == nullptr && (x >> c) != t) {
+            // all-zero tile: CONST at every level (32 bytes); ladder pick
+            if (threadIdx.x == 0) {
+                int lv = cc.max_bytes >= (unsigned long long)HDR ? 0 : cc.nlev - 1;
+                int s = cc.force_raw ? 0 : cc.shifts[lv];
+                unsigned long long off = atomicAdd(&scal->bump, (unsigned long long)(cc.force_raw ? HDR + 16 * N : HDR));
+                uint32_t size = cc.force_raw ? HDR + 16u * N : HDR;
+                if (off + size > out_cap) {
+                    atomicOr(&scal->err, ERR_OVERFLOW);
+                    sc.ok = 0;
+                } else {
+                    uint32_t *d = reinterpret_cast<uint32_t *>(out_arena + off);
+                    uint32_t h0 = cc.force_raw ? (uint32_t)M_RAW : ((uint32_t)s << 8) | ((uint32_t)lv << 16);
+                    d[0] = h0;
+                    d[1] = cc.force_raw ? 16u * N : 0u;
+                    d[2] = d[3] = d[4] = d[5] = 0;
+                    d[6] = (uint32_t)c;
+                    d[7] = 0;
+                    out_table[t] = off;
+                    part[2 * t] = part[2 * t + 1] = 0;
+                    if (!cc.force_raw) atomicAdd(&scal->hist[lv], 1ull);
+                    else atomicAdd(&scal->hist[0], 1ull);
+                    sc.ok = 1;
+                    sc.off = off;
+                }
+            }
+            __syncthreads();
+            if (cc.force_raw && sc.ok) {
+                uint4 *d4 = reinterpret_cast<uint4 *>(out_arena + sc.off + HDR);
+                for (int i = threadIdx.x; i < N; i += THREADS) d4[i] = make_uint4(0, 0, 0, 0);
+            }
+            __syncthreads();
+            continue;
+        }
+        for (int i = threadIdx.x; i < N; i += THREADS) {
+            if (dense) {
+                double2 v = dense[t * (unsigned long long)N + i];
+                re[i] = v.x;
+                im[i] = v.y;
+            } else {
+                bool one = (((t << c) | (unsigned long long)i) == x);
+                re[i] = one ? 1.0 : 0.0;
+                im[i] = 0.0;
+            }
+        }
+        __syncthreads();
+        encode_tile(re, im, cc, t, out_arena, out_cap, out_table, part, scal, 0u, sc);
+    }
+}
+
+// Recompute the running norm from the per-tile partials (after an import).
+__global__ void norm_from_parts_kernel(const unsigned long long *part, unsigned long long ntiles,
+                                       DevScalars *scal) {
+    unsigned long long lo = 0, hi = 0;
+    for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < ntiles;
+         t += (unsigned long long)gridDim.x * blockDim.x)
+        add128(lo, hi, part[2 * t], part[2 * t + 1]);
+    warp_sum128(lo, hi);
+    if ((threadIdx.x & 31) == 0 && (lo | hi)) atomic_add128(&scal->acc_lo, &scal->acc_hi, lo, hi);
+}
+
+// Stream sizes of tiles first..first+count-1
+__global__ void sizes_kernel(const uint8_t *arena, const unsigned long long *table,
+                             unsigned long long first, unsigned long long count,
+                             unsigned long long *sizes) {
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < count;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t *h = reinterpret_cast<const uint32_t *>(arena + table[first + i]);
+        sizes[i] = HDR + (unsigned long long)h[1];
+    }
+}
+
+// Sum of the stream sizes of all tiles
+__global__ void sum_sizes_kernel(const uint8_t *arena, const unsigned long long *table,
+                                 unsigned long long ntiles, unsigned long long *total) {
+    unsigned long long s = 0;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < ntiles;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t *h = reinterpret_cast<const uint32_t *>(arena + table[i]);
+        s += HDR + (unsigned long long)h[1];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(total, s);
+}
+
+// Gather streams into a contiguous buffer at the given offsets
+__global__ void gather_kernel(const uint8_t *arena, const unsigned long long *table,
+                              unsigned long long first, unsigned long long count,
+                              const unsigned long long *offs, const unsigned long long *sizes,
+                              uint8_t *out) {
+    for (unsigned long long i = blockIdx.x; i < count; i += gridDim.x) {
+        const uint4 *s = reinterpret_cast<const uint4 *>(arena + table[first + i]);
+        uint4 *d = reinterpret_cast<uint4 *>(out + offs[i]);
+        for (unsigned long long j = threadIdx.x; j < sizes[i] / 16; j += blockDim.x) d[j] = s[j];
+    }
+}
+
+// Validate imported streams (each at offs[i] in buf, sizes[i] bytes) by
+// decoding them; record their norm partials.  bad[0] counts failures.
+__global__ void __launch_bounds__(THREADS) validate_kernel(const uint8_t *buf, const unsigned long long *offs,
+                                                         const unsigned long long *sizes,
+                                                         unsigned long long count, int c,
+                                                         unsigned long long *parts,
+                                                         unsigned int *bad) {
+    extern __shared__ double smem[];
+    __shared__ Scratch sc;
+    const int N = 1 << c;
+    double *re = smem, *im = smem + N;
+    for (unsigned long long i = blockIdx.x; i < count; i += gridDim.x) {
+        const uint8_t *src = buf + offs[i];
+        const uint32_t *h = reinterpret_cast<const uint32_t *>(src);
+        int fail = 0;
+        if (sizes[i] < HDR || (sizes[i] & 15ull) || HDR + (unsigned long long)h[1] != sizes[i]) fail = 1;
+        fail = __syncthreads_or(fail);
+        if (!fail) fail = decode_tile(src, c, re, im, sc);
+        unsigned long long lo = 0, hi = 0;
+        unsigned rng = 0;
+        if (!fail) {
+            for (int j = threadIdx.x; j < N; j += THREADS) {
+                unsigned long long l0, h0, l1, h1;
+                sq_units(dbits(re[j]), l0, h0, rng);
+                sq_units(dbits(im[j]), l1, h1, rng);
+                add128(lo, hi, l0, h0);
+                add128(lo, hi, l1, h1);
+            }
+        }
+        rng = __syncthreads_or(rng);
+        warp_sum128(lo, hi);
+        if ((threadIdx.x & 31) == 0) { sc.red_lo[threadIdx.x >> 5] = lo; sc.red_hi[threadIdx.x >> 5] = hi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long tl = 0, th = 0;
+            for (int w = 0; w < NWARPS; ++w) add128(tl, th, sc.red_lo[w], sc.red_hi[w]);
+            parts[2 * i] = tl;
+            parts[2 * i + 1] = th;
+            if (fail || rng) atomicAdd(bad, 1u);
+        }
+        __syncthreads();
+    }
+}
+
+// Copy validated streams into the arena and point the table at them.
+__global__ void place_kernel(const uint8_t *buf, const unsigned long long *offs,
+                             const unsigned long long *sizes, unsigned long long count,
+                             unsigned long long first, unsigned long long base, uint8_t *arena,
+                             unsigned long long *table, const unsigned long long *parts,
+                             unsigned long long *part) {
+    for (unsigned long long i = blockIdx.x; i < count; i += gridDim.x) {
+        const uint4 *s = reinterpret_cast<const uint4 *>(buf + offs[i]);
+        uint4 *d = reinterpret_cast<uint4 *>(arena + base + offs[i]);
+        for (unsigned long long j = threadIdx.x; j < sizes[i] / 16; j += blockDim.x) d[j] = s[j];
+        if (threadIdx.x == 0) {
+            table[first + i] = base + offs[i];
+            part[2 * (first + i)] = parts[2 * i];
+            part[2 * (first + i) + 1] = parts[2 * i + 1];
+        }
+    }
+}
+
+// Decode tiles covering [start, start+count) into out (interleaved).
+__global__ void __launch_bounds__(THREADS) amplitudes_kernel(const uint8_t *arena, const unsigned long long *table,
+                                                           int c, unsigned long long start,
+                                                           unsigned long long count, double2 *out,
+                                                           DevScalars *scal) {
+    extern __shared__ double smem[];
+    __shared__ Scratch sc;
+    const int N = 1 << c;
+    double *re = smem, *im = smem + N;
+    unsigned long long t0 = start >> c, t1 = (start + count - 1) >> c;
+    for (unsigned long long t = t0 + blockIdx.x; t <= t1; t += gridDim.x) {
+        if (decode_tile(arena + table[t], c, re, im, sc) && threadIdx.x == 0)
+            atomicOr(&scal->err, ERR_FORMAT);
+        for (int i = threadIdx.x; i < N; i += THREADS) {
+            unsigned long long gidx = (t << c) | (unsigned long long)i;
+            if (gidx >= start && gidx < start + count) out[gidx - start] = make_double2(re[i], im[i]);
+        }
+        __syncthreads();
+    }
+}
+
+// Exact per-outcome sums of |a|^2: bucket j gathers bit i of j from qubit qs[i].
+__global__ void __launch_bounds__(THREADS) probs_kernel(const uint8_t *arena, const unsigned long long *table,
+                                                      int c, unsigned long long ntiles, const int *qs,
+                                                      int nq, unsigned long long *buckets,
+                                                      DevScalars *scal) {
+    extern __shared__ double smem[];
+    __shared__ Scratch sc;
+    __shared__ int sq[32];
+    const int N = 1 << c;
+    double *re = smem, *im = smem + N;
+    if (threadIdx.x < nq) sq[threadIdx.x] = qs[threadIdx.x];
+    __syncthreads();
+    for (unsigned long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        if (decode_tile(arena + table[t], c, re, im, sc) && threadIdx.x == 0)
+            atomicOr(&scal->err, ERR_FORMAT);
+        for (int i = threadIdx.x; i < N; i += THREADS) {
+            unsigned long long gidx = (t << c) | (unsigned long long)i;
+            unsigned j = 0;
+            for (int b = 0; b < nq; ++b) j |= (unsigned)((gidx >> sq[b]) & 1ull) << b;
+            unsigned long long l0, h0, l1, h1;
+            unsigned rng = 0;
+            sq_units(dbits(re[i]), l0, h0, rng);
+            sq_units(dbits(im[i]), l1, h1, rng);
+            add128(l0, h0, l1, h1);
+            if (l0 | h0) atomic_add128(&buckets[2 * j], &buckets[2 * j + 1], l0, h0);
+        }
+        __syncthreads();
+    }
+}
+
+// Fidelity partials per tile: <ref|psi> (re, im), <psi|psi>, <ref|ref>,
+// each summed over the tile in a fixed (pairwise) order.
+__global__ void __launch_bounds__(THREADS) fidelity_kernel(const uint8_t *arena, const unsigned long long *table,
+                                                         int c, unsigned long long ntiles, RefSpec rs,
+                                                         Acc4 *tile_sums, DevScalars *scal) {
+    extern __shared__ double smem[];
+    __shared__ Scratch sc;
+    __shared__ Acc4 red[THREADS];
+    const int N = 1 << c;
+    double *re = smem, *im = smem + N, *rre = smem + 2 * N, *rim = smem + 3 * N;
+    for (unsigned long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        int bad = decode_tile(arena + table[t], c, re, im, sc);
+        if (rs.kind == 0) bad |= decode_tile(rs.o_arena + rs.o_table[t], c, rre, rim, sc);
+        if (bad && threadIdx.x == 0) atomicOr(&scal->err, ERR_FORMAT);
+        Acc4 acc = make_acc4(0, 0, 0, 0);
+        // thread-contiguous chunks, then a pairwise tree over threads
+        const int per = (N + THREADS - 1) / THREADS;
+        for (int q = 0; q < per; ++q) {
+            int i = threadIdx.x * per + q;
+            if (i >= N) break;
+            unsigned long long gidx = (t << c) | (unsigned long long)i;
+            double ar, ai;
+            if (rs.kind == 0) { ar = rre[i]; ai = rim[i]; }
+            else if (rs.kind == 1) {
+                unsigned long long Nn = 1ull << rs.n;
+                unsigned long long ph = (rs.x * gidx) & (Nn - 1ull);
+                double sn, cs;
+                sincospi(ldexp((double)ph, 1 - rs.n), &sn, &cs);
+                ar = cs * rs.qft_mag;
+                ai = sn * rs.qft_mag;
+            } else if (rs.kind == 2) {
+                ar = gidx == rs.x ? rs.grov_m : rs.grov_o;
+                ai = 0.0;
+            } else {
+                double2 v = rs.dense[gidx];
+                ar = v.x;
+                ai = v.y;
+            }
+            double pr = re[i], pi = im[i];
+            acc.x = __fma_rn(ar, pr, __fma_rn(ai, pi, acc.x));     // Re <ref|psi>
+            acc.y = __fma_rn(ar, pi, __fma_rn(-ai, pr, acc.y));    // Im <ref|psi>
+            acc.z = __fma_rn(pr, pr, __fma_rn(pi, pi, acc.z));
+            acc.w = __fma_rn(ar, ar, __fma_rn(ai, ai, acc.w));
+        }
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int st = THREADS / 2; st > 0; st >>= 1) {
+            if (threadIdx.x < st) {
+                Acc4 a = red[threadIdx.x], b = red[threadIdx.x + st];
+                red[threadIdx.x] = make_acc4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) tile_sums[t] = red[0];
+        __syncthreads();
+    }
+}
+
+// One level of a pairwise tree: out[i] = in[2i] + in[2i+1]
+__global__ void pair_sum_kernel(const Acc4 *in, Acc4 *out, unsigned long long nout) {
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < nout;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        Acc4 a = in[2 * i], b = in[2 * i + 1];
+        out[i] = make_acc4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+    }
+}
+
+}  // namespace qs
+
+// ---------------------------------------------------------------- launchers
+namespace qs {
+
+size_t sweep_smem_bytes(int mb) { return (size_t)16 << mb; }
+
+cudaError_t launch_sweep(const SweepParams &p, int grid, cudaStream_t st) {
+    size_t smem = sweep_smem_bytes(p.cc.c + p.h);
+    sweep_kernel<<<grid, THREADS, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(DevScalars *scal, int use_alpha, unsigned long long *used_hist,
+                            unsigned slot, int record_used, cudaStream_t st) {
+    finalize_kernel<<<1, 32, 0, st>>>(scal, use_alpha, used_hist, slot, record_used);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(const double2 *dense, unsigned long long x, const CodecCfg &cc,
+                        unsigned long long ntiles, uint8_t *arena, unsigned long long cap,
+                        unsigned long long *table, unsigned long long *part, DevScalars *scal,
+                        int grid, cudaStream_t st) {
+    init_kernel<<<grid, THREADS, (size_t)16 << cc.c, st>>>(dense, x, cc, ntiles, arena, cap, table,
+                                                            part, scal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norm_from_parts(const unsigned long long *part, unsigned long long ntiles,
+                                   DevScalars *scal, int grid, cudaStream_t st) {
+    norm_from_parts_kernel<<<grid, THREADS, 0, st>>>(part, ntiles, scal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sizes(const uint8_t *arena, const unsigned long long *table,
+                         unsigned long long first, unsigned long long count,
+                         unsigned long long *sizes, int grid, cudaStream_t st) {
+    sizes_kernel<<<grid, THREADS, 0, st>>>(arena, table, first, count, sizes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_sizes(const uint8_t *arena, const unsigned long long *table,
+                             unsigned long long ntiles, unsigned long long *total, int grid,
+                             cudaStream_t st) {
+    sum_sizes_kernel<<<grid, THREADS, 0, st>>>(arena, table, ntiles, total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const uint8_t *arena, const unsigned long long *table,
+                          unsigned long long first, unsigned long long count,
+                          const unsigned long long *offs, const unsigned long long *sizes,
+                          uint8_t *out, int grid, cudaStream_t st) {
+    gather_kernel<<<grid, THREADS, 0, st>>>(arena, table, first, count, offs, sizes, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const uint8_t *buf, const unsigned long long *offs,
+                            const unsigned long long *sizes, unsigned long long count, int c,
+                            unsigned long long *parts, unsigned int *bad, int grid, cudaStream_t st) {
+    validate_kernel<<<grid, THREADS, (size_t)16 << c, st>>>(buf, offs, sizes, count, c, parts, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_place(const uint8_t *buf, const unsigned long long *offs,
+                         const unsigned long long *sizes, unsigned long long count,
+                         unsigned long long first, unsigned long long base, uint8_t *arena,
+                         unsigned long long *table, const unsigned long long *parts,
+                         unsigned long long *part, int grid, cudaStream_t st) {
+    place_kernel<<<grid, THREADS, 0, st>>>(buf, offs, sizes, count, first, base, arena, table, parts,
+                                           part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_amplitudes(const uint8_t *arena, const unsigned long long *table, int c,
+                              unsigned long long start, unsigned long long count, double2 *out,
+                              DevScalars *scal, int grid, cudaStream_t st) {
+    amplitudes_kernel<<<grid, THREADS, (size_t)16 << c, st>>>(arena, table, c, start, count, out, scal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_probs(const uint8_t *arena, const unsigned long long *table, int c,
+                         unsigned long long ntiles, const int *qsel, int nq,
+                         unsigned long long *buckets, DevScalars *scal, int grid, cudaStream_t st) {
+    probs_kernel<<<grid, THREADS, (size_t)16 << c, st>>>(arena, table, c, ntiles, qsel, nq, buckets, scal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fidelity(const uint8_t *arena, const unsigned long long *table, int c,
+                            unsigned long long ntiles, const RefSpec &rs, Acc4 *tile_sums,
+                            DevScalars *scal, int grid, cudaStream_t st) {
+    fidelity_kernel<<<grid, THREADS, (size_t)32 << c, st>>>(arena, table, c, ntiles, rs, tile_sums, scal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_sum(const Acc4 *in, Acc4 *out, unsigned long long nout, int grid,
+                            cudaStream_t st) {
+    pair_sum_kernel<<<grid, THREADS, 0, st>>>(in, out, nout);
+    return cudaGetLastError();
+}
+
+cudaError_t configure_kernels() {
+    cudaError_t e;
+    int maxsm = (int)sweep_smem_bytes(MAX_ITEM_LOG2);
+    if ((e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm))) return e;
+    if ((e = cudaFuncSetAttribute(init_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 << MAX_C))) return e;
+    if ((e = cudaFuncSetAttribute(validate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 << MAX_C))) return e;
+    if ((e = cudaFuncSetAttribute(amplitudes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 << MAX_C))) return e;
+    if ((e = cudaFuncSetAttribute(probs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 << MAX_C))) return e;
+    if ((e = cudaFuncSetAttribute(fidelity_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 << MAX_C))) return e;
+    return cudaSuccess;
+}
+
+int sweep_blocks_per_sm(int mb) {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel, THREADS, sweep_smem_bytes(mb));
+    return nb > 0 ? nb : 1;
+}
+
+}  // namespace qs

@@ -1,0 +1,282 @@
+"""Python binding of the C ABI in include/qsim.h (argument marshalling only).
+
+Every step of the simulation runs in libqsim.so.  Importing this module
+loads that library and fails loudly if it has not been built; there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import inputs
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libqsim.so")
+
+CODECS = {"none": 0, "lossless": 1, "rel": 2, "aalc": 3}
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NONFINITE",
+          5: "ERR_TIMEOUT", 6: "ERR_STATE_INVALID", 7: "ERR_FORMAT"}
+REF_HANDLE, REF_QFT, REF_GROVER, REF_DENSE_HOST, REF_DENSE_DEVICE = range(5)
+
+EXPORTS = ["qsim_create", "qsim_destroy", "qsim_set_stream", "qsim_set_aalc", "qsim_set_normalize",
+           "qsim_set_schedule", "qsim_reset_basis", "qsim_set_amplitudes", "qsim_apply_gate",
+           "qsim_flush", "qsim_probabilities", "qsim_amplitudes", "qsim_fidelity",
+           "qsim_compressed_bytes", "qsim_stats", "qsim_last_error", "qsim_export_tiles",
+           "qsim_import_tiles", "qsim_plan_sweeps", "qsim_version"]
+
+
+class QsimError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+class Ref(C.Structure):
+    _fields_ = [("kind", C.c_int), ("other", C.c_void_p), ("x", C.c_ulonglong),
+                ("iterations", C.c_int), ("dense", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("gates", C.c_ulonglong), ("sweeps", C.c_ulonglong),
+                ("items_done", C.c_ulonglong), ("items_skipped", C.c_ulonglong),
+                ("level_hist", C.c_ulonglong * 8), ("stream_bytes", C.c_ulonglong),
+                ("min_stream_bytes_seen", C.c_ulonglong), ("max_stream_bytes_seen", C.c_ulonglong),
+                ("arena_regrows", C.c_ulonglong), ("alpha", C.c_double),
+                ("tile_log2", C.c_int), ("hmax", C.c_int), ("depth", C.c_int),
+                ("n_qubits", C.c_int)]
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load libqsim.so (built by __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = C.CDLL(LIB_PATH)
+    vp, dp, ip, u64 = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_ulonglong
+    u64p = C.POINTER(C.c_ulonglong)
+    sig = {
+        "qsim_create": ([C.POINTER(vp), C.c_int, C.c_int, C.c_int, C.c_double], C.c_int),
+        "qsim_destroy": ([vp], C.c_int),
+        "qsim_set_stream": ([vp, vp], C.c_int),
+        "qsim_set_aalc": ([vp, C.c_double, dp, C.c_int], C.c_int),
+        "qsim_set_normalize": ([vp, C.c_int], C.c_int),
+        "qsim_set_schedule": ([vp, C.c_int, C.c_int, C.c_int], C.c_int),
+        "qsim_reset_basis": ([vp, u64], C.c_int),
+        "qsim_set_amplitudes": ([vp, dp], C.c_int),
+        "qsim_apply_gate": ([vp, dp, ip, C.c_int, ip, C.c_int, u64], C.c_int),
+        "qsim_flush": ([vp], C.c_int),
+        "qsim_probabilities": ([vp, ip, C.c_int, dp], C.c_int),
+        "qsim_amplitudes": ([vp, u64, u64, dp], C.c_int),
+        "qsim_fidelity": ([vp, C.POINTER(Ref), dp, dp], C.c_int),
+        "qsim_compressed_bytes": ([vp, u64p, u64p], C.c_int),
+        "qsim_stats": ([vp, C.POINTER(Stats)], C.c_int),
+        "qsim_last_error": ([vp], C.c_char_p),
+        "qsim_export_tiles": ([vp, u64, u64, vp, u64, u64p], C.c_int),
+        "qsim_import_tiles": ([vp, u64, u64, vp, u64p], C.c_int),
+        "qsim_plan_sweeps": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, ip, ip, dp, ip, ip,
+                              ip, C.c_int], C.c_int),
+        "qsim_version": ([], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def gate_args(g: inputs.Gate):
+    """(matrix, targets, n_targets, controls, n_controls, control_values) for qsim_apply_gate."""
+    m = np.ascontiguousarray(np.asarray(g.matrix, dtype=np.complex128)).view(np.float64)
+    t = (C.c_int * 2)(*g.targets, *([0] * (2 - len(g.targets))))
+    nc = len(g.controls)
+    ctl = (C.c_int * max(1, nc))(*g.controls)
+    vals = 0
+    for i, v in enumerate(g.cvals()):
+        if v:
+            vals |= 1 << i
+    return m, t, len(g.targets), ctl, nc, vals
+
+
+def plan_sweeps(n: int, c: int, hmax: int, depth: int, gates) -> list[tuple[int, int, tuple]]:
+    """The library's sweep partition of a gate list (host only, no GPU)."""
+    L = load()
+    ng = len(gates)
+    nt = (C.c_int * max(1, ng))(*[len(g.targets) for g in gates])
+    tg = (C.c_int * max(2, 2 * ng))()
+    mats = np.zeros((max(1, ng), 32))
+    for i, g in enumerate(gates):
+        for j, q in enumerate(g.targets):
+            tg[2 * i + j] = q
+        m = np.asarray(g.matrix, dtype=np.complex128).reshape(-1)
+        mats[i, :2 * m.size] = m.view(np.float64)
+    cap = max(1, ng)
+    lo, hh, HH = (C.c_int * cap)(), (C.c_int * cap)(), (C.c_int * (2 * cap))()
+    r = L.qsim_plan_sweeps(n, c, hmax, depth, ng, nt, tg, _dp(mats), lo, hh, HH, cap)
+    if r < 0:
+        raise ValueError(f"qsim_plan_sweeps failed ({r})")
+    out = []
+    for s in range(r):
+        hi = lo[s + 1] if s + 1 < r else ng
+        out.append((lo[s], hi, tuple(HH[2 * s + i] for i in range(hh[s]))))
+    return out
+
+
+class State:
+    """An n-qubit state held compressed on the GPU (one qsim_t handle)."""
+
+    def __init__(self, n: int, block_log2: int, codec: str = "rel", eps: float = 1e-4,
+                 stream=None):
+        self._L = load()
+        h = C.c_void_p()
+        self._check(self._L.qsim_create(C.byref(h), n, block_log2, CODECS[codec], eps), None)
+        self.h = h
+        self.n = n
+        self.codec = codec
+        if stream is not None:
+            self.set_stream(stream)
+
+    # -- plumbing
+    def _check(self, status: int, h=-1):
+        if status != 0:
+            hh = self.h if h == -1 else h
+            msg = self._L.qsim_last_error(hh).decode()
+            raise QsimError(status, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.qsim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+        ptr = getattr(stream, "cuda_stream", stream)
+        self._check(self._L.qsim_set_stream(self.h, C.c_void_p(ptr or 0)))
+
+    # -- configuration
+    def set_aalc(self, theta: float, levels):
+        arr = (C.c_double * max(1, len(levels)))(*levels)
+        self._check(self._L.qsim_set_aalc(self.h, theta, arr, len(levels)))
+
+    def set_normalize(self, on: bool):
+        self._check(self._L.qsim_set_normalize(self.h, int(bool(on))))
+
+    def set_schedule(self, tile_log2: int, hmax: int = 2, depth: int = 64):
+        self._check(self._L.qsim_set_schedule(self.h, tile_log2, hmax, depth))
+
+    # -- state
+    def reset_basis(self, x: int = 0):
+        self._check(self._L.qsim_reset_basis(self.h, x))
+
+    def set_amplitudes(self, psi: np.ndarray):
+        a = np.ascontiguousarray(psi, dtype=np.complex128)
+        assert a.size == 1 << self.n
+        self._check(self._L.qsim_set_amplitudes(self.h, _dp(a.view(np.float64))))
+
+    def apply(self, g: inputs.Gate):
+        m, t, nt, ctl, nc, vals = gate_args(g)
+        self._check(self._L.qsim_apply_gate(self.h, _dp(m), t, nt, ctl, nc, vals))
+
+    def apply_all(self, gates):
+        for g in gates:
+            self.apply(g)
+
+    def flush(self):
+        self._check(self._L.qsim_flush(self.h))
+
+    # -- read-outs
+    def amplitudes(self, start: int = 0, count: int | None = None) -> np.ndarray:
+        if count is None:
+            count = (1 << self.n) - start
+        out = np.zeros(count, dtype=np.complex128)
+        self._check(self._L.qsim_amplitudes(self.h, start, count, _dp(out.view(np.float64))))
+        return out
+
+    def probabilities(self, qubits) -> np.ndarray:
+        qs = (C.c_int * max(1, len(qubits)))(*qubits)
+        out = np.zeros(1 << len(qubits))
+        self._check(self._L.qsim_probabilities(self.h, qs, len(qubits), _dp(out)))
+        return out
+
+    def _fid(self, ref: Ref) -> tuple[float, float]:
+        F, ov = C.c_double(), C.c_double()
+        self._check(self._L.qsim_fidelity(self.h, C.byref(ref), C.byref(F), C.byref(ov)))
+        return F.value, ov.value
+
+    def fidelity_qft(self, x: int) -> float:
+        return self._fid(Ref(REF_QFT, None, x, 0, None))[0]
+
+    def fidelity_grover(self, marked: int, iterations: int) -> float:
+        return self._fid(Ref(REF_GROVER, None, marked, iterations, None))[0]
+
+    def fidelity_dense(self, psi: np.ndarray) -> float:
+        a = np.ascontiguousarray(psi, dtype=np.complex128)
+        return self._fid(Ref(REF_DENSE_HOST, None, 0, 0, a.ctypes.data))[0]
+
+    def fidelity_device(self, ptr: int) -> float:
+        return self._fid(Ref(REF_DENSE_DEVICE, None, 0, 0, ptr))[0]
+
+    def fidelity_state(self, other: "State") -> float:
+        return self._fid(Ref(REF_HANDLE, other.h, 0, 0, None))[0]
+
+    def compressed_bytes(self) -> tuple[int, int]:
+        a, b = C.c_ulonglong(), C.c_ulonglong()
+        self._check(self._L.qsim_compressed_bytes(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(self._L.qsim_stats(self.h, C.byref(s)))
+        d = {f: getattr(s, f) for f, _ in Stats._fields_}
+        d["level_hist"] = list(s.level_hist)
+        return d
+
+    # -- tile streams
+    def export_tiles(self, first: int = 0, count: int | None = None) -> list[bytes]:
+        st = self.stats()
+        ntiles = 1 << (self.n - st["tile_log2"])
+        if count is None:
+            count = ntiles - first
+        sizes = (C.c_ulonglong * max(1, count))()
+        self._check(self._L.qsim_export_tiles(self.h, first, count, None, 0, sizes))
+        total = sum(sizes[:count])
+        buf = (C.c_uint8 * max(1, total))()
+        self._check(self._L.qsim_export_tiles(self.h, first, count, buf, total, sizes))
+        raw = bytes(buf)[:total]
+        out, off = [], 0
+        for i in range(count):
+            out.append(raw[off:off + sizes[i]])
+            off += sizes[i]
+        return out
+
+    def import_tiles(self, first: int, streams):
+        data = b"".join(streams)
+        sizes = (C.c_ulonglong * max(1, len(streams)))(*[len(s) for s in streams])
+        buf = (C.c_uint8 * max(1, len(data))).from_buffer_copy(data) if data else (C.c_uint8 * 1)()
+        self._check(self._L.qsim_import_tiles(self.h, first, len(streams), buf, sizes))
