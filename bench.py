@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark of the compressed simulator's hot path on GB300.
+
+Workload (one step): the 28-qubit QFT (420 gates: H, controlled phases,
+final swaps) on a seeded basis state, state stored as compressed tiles of
+2^10 amplitudes in blocks of 2^20, point-wise relative bound 1e-4,
+normalize on (Algorithm 2), sweeps of up to 64 fused gates.  A step is
+reset to |x>, all 420 gates, flush (every sweep of decompress -> normalize
+-> gates -> compress), i.e. one full circuit.
+
+Prints one JSON line: gates/s (whole job), the sweep kernel's roofline
+(FP64 pipe), the HBM fraction, fidelity against the uncompressed FP64 GPU
+run and the closed form, compression ratios per bound, an end-to-end
+number through the public API, clock samples, and the CPU oracle timed on
+a bounded sample of the same workload.
+
+Multi-GPU (torchrun): every rank runs an independent replica (its own
+seeded basis state); there is no exchange step, so the scaling is weak.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gates/s and HBM fraction at fixed fidelity; compression ratio; circuits/s + p99 latency"
+N_QUBITS, BLOCK_LOG2, EPS = 28, 20, 1e-4
+FP64_PEAK_TFLOPS = 1.25        # nominal dense FP64 of GB300 (no measured FP64 peak on this machine)
+PROFILE_FILE = os.path.join(ROOT, "profiles", "sweep_kernel_qft28.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_1811_05140_gb300", "csrc", "kernels.cu")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N_QUBITS)
+    ap.add_argument("--eps", type=float, default=EPS)
+    ap.add_argument("--depth", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip bound sweep / AALC / e2e")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def traffic_from_profile():
+    """Per-launch DRAM bytes of the sweep kernel from the committed ncu
+    summary, when it was taken on the current kernel source."""
+    try:
+        text = open(PROFILE_FILE).read()
+    except OSError:
+        return None, None
+    m = re.search(r"kernels\.cu sha256:\s*([0-9a-f]{64})", text)
+    t = re.search(r"dram bytes per full-size launch:\s*([0-9.eE+]+)", text)
+    if not m or not t:
+        return None, None
+    cur = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+    if cur != m.group(1):
+        return None, "kernel changed since the ncu capture"
+    return float(t.group(1)), None
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(n, eps, depth, xval, items_per_sweep, budget_s=None):
+    """Time the oracle (Algorithm 2 over tiles, plain C, 1 thread) on the
+    first `items_per_sweep` tile groups of every sweep of the QFT and
+    extrapolate to the whole circuit.  Returns (gates/s, seconds, desc)."""
+    import oracle
+    from paper_1811_05140_gb300 import inputs as I
+
+    c = min(BLOCK_LOG2, n, 10)
+    gates = I.qft(n)
+    cs = oracle.CSim(n, c, [oracle.shift_for_eps(eps)], None, True)
+    cs.reset_basis(xval)
+    sweeps = oracle.partition(gates, n, c, 2, depth)
+    est_total, spent = 0.0, 0.0
+    for lo, hi, H in sweeps:
+        nitems = 1 << (n - c - len(H))
+        k = min(items_per_sweep, nitems)
+        t0 = time.perf_counter()
+        cs.sweep_sample(gates[lo:hi], H, 0, k)
+        dt = time.perf_counter() - t0
+        spent += dt
+        est_total += dt * nitems / k
+    desc = (f"oracle (plain C, 1 thread) on the first {items_per_sweep} tile groups of each of "
+            f"the {len(sweeps)} sweeps of the {n}-qubit QFT, extrapolated by group count")
+    return len(gates) / est_total, spent, desc
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_1811_05140_gb300 import build as B
+    from paper_1811_05140_gb300 import inputs as I
+    from paper_1811_05140_gb300 import qsim
+
+    if rank == 0:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.set_device(local_rank)
+    n, eps = args.n, args.eps
+    c = min(BLOCK_LOG2, n, 10)
+    xval = I.seeded_basis(n, I.BASE_SEED + rank)
+    gates = I.qft(n)
+    stream = torch.cuda.Stream()
+    st = qsim.State(n, BLOCK_LOG2, "rel", eps, stream=stream)
+    if args.depth != 64:
+        st.set_schedule(c, 2, args.depth)
+
+    def step():
+        st.reset_basis(xval)
+        st.apply_all(gates)
+        st.flush()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    st.set_profiling(True)
+    launches0 = st.stats()["kernel_launches"]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = ev0.elapsed_time(ev1)
+    prof = st.profile()
+    launches = st.stats()["kernel_launches"] - launches0
+    stats = st.stats()
+    ms_t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    result = {
+        "ms": ms_max, "prof": prof, "launches": launches, "stats": stats,
+        "clocks": clk.summary(), "xval": xval,
+    }
+    if rank != 0:
+        return None
+    # quality and ratios (untimed)
+    raw = 16.0 * (1 << n)
+    sb, fp = st.compressed_bytes()
+    ref = qsim.State(n, BLOCK_LOG2, "none", 0.0, stream=stream)
+    ref.reset_basis(xval)
+    ref.apply_all(gates)
+    ref.flush()
+    F_ref = st.fidelity_state(ref)
+    F_cf = st.fidelity_qft(xval)
+    result.update(F_ref=F_ref, F_cf=F_cf, ratio_final=raw / sb,
+                  ratio_min=raw / max(1, stats["max_stream_bytes_seen"]), footprint=fp)
+    if not args.no_extras:
+        per_bound = []
+        for e in (1e-2, 1e-3, 1e-4, 1e-5):
+            s2 = qsim.State(n, BLOCK_LOG2, "rel", e, stream=stream)
+            s2.reset_basis(xval)
+            t0 = time.perf_counter()
+            s2.apply_all(gates)
+            s2.flush()
+            dt = time.perf_counter() - t0
+            b2, _ = s2.compressed_bytes()
+            st2 = s2.stats()
+            per_bound.append({"eps": e, "fidelity_vs_fp64": round(s2.fidelity_state(ref), 9),
+                              "ratio_final": round(raw / b2, 3),
+                              "ratio_min": round(raw / max(1, st2["max_stream_bytes_seen"]), 3),
+                              "gates_per_s": round(len(gates) / dt, 1)})
+            s2.close()
+        result["per_bound"] = per_bound
+        s3 = qsim.State(n, BLOCK_LOG2, "aalc", 1e-2, stream=stream)
+        s3.set_aalc(16.0, [1e-5, 1e-4, 1e-3, 1e-2])
+        s3.reset_basis(xval)
+        s3.apply_all(gates)
+        s3.flush()
+        b3, _ = s3.compressed_bytes()
+        st3 = s3.stats()
+        result["aalc_theta16"] = {"fidelity_vs_fp64": round(s3.fidelity_state(ref), 9),
+                                  "ratio_final": round(raw / b3, 3),
+                                  "ratio_min": round(raw / max(1, st3["max_stream_bytes_seen"]), 3),
+                                  "level_hist": st3["level_hist"][:5]}
+        s3.close()
+        # end to end through the public API: host gate list in, host result out
+        qs = [0, n // 2, n - 1]
+        st.reset_basis(xval)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            st.reset_basis(xval)
+            st.apply_all(gates)
+            probs = st.probabilities(qs)
+        t1 = time.perf_counter()
+        result["e2e_s"] = (t1 - t0) / args.steps
+        result["e2e_h2d"] = len(gates) * 312
+        result["e2e_d2h"] = len(probs) * 16
+    ref.close()
+    return result
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step times a bounded sample."""
+    from paper_1811_05140_gb300 import inputs as I
+    import oracle
+    oracle.build()
+    xval = I.seeded_basis(args.n, I.BASE_SEED)
+    vals = []
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        v, spent, desc = oracle_sample(args.n, args.eps, args.depth, xval, 2)
+        if i >= args.warmup:
+            vals.append(v)
+    v = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "gates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * 420 / v, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"qft{args.n}_rel{args.eps:g}", "n_qubits": args.n,
+                   "block_log2": BLOCK_LOG2, "rel_err_bound": args.eps, "gates": 420},
+        "cpu_baseline": {"value": v, "unit": "gates/s", "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": v, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+    import torch
+    if world > 1:
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    res = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        n = args.n
+        ng = 420 if n == 28 else len(__import__("paper_1811_05140_gb300.inputs", fromlist=["qft"]).qft(n))
+        ms_step = res["ms"] / args.steps
+        value = world * ng * args.steps / (res["ms"] / 1000.0)
+        prof = res["prof"]
+        sweep_s = prof["sweep_ms"] / 1000.0
+        launches = max(1, prof["sweep_launches"])
+        per_launch_s = sweep_s / launches
+        achieved_tflops = 2.0 * prof["dp_ops"] / sweep_s / 1e12 if sweep_s > 0 else 0.0
+        hbm_gbs = prof["bytes"] / sweep_s / 1e9 if sweep_s > 0 else 0.0
+        peaks = measured_peaks()
+        hbm_peak = peaks.get("hbm_gbs", 6800.0)
+        traffic, why = traffic_from_profile()
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            v, spent, desc = oracle_sample(n, args.eps, args.depth, res["xval"], 24)
+            cpu = {"value": v, "unit": "gates/s", "cores": 1, "kind": "oracle", "sample": desc,
+                   "seconds": round(spent, 2)}
+        line = {
+            "metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"qft{n}_rel{args.eps:g}", "n_qubits": n,
+                       "block_log2": BLOCK_LOG2, "tile_log2": min(10, n), "rel_err_bound": args.eps,
+                       "gates": ng, "sweep_depth": args.depth, "normalize": True,
+                       "l2": "inputs larger than L2 (compressed state > 129 MB), no flush",
+                       "parallelism": f"replicas x{world}"},
+            "fidelity_vs_fp64_gpu": res["F_ref"], "fidelity_vs_closed_form": res["F_cf"],
+            "compression_ratio_final": res["ratio_final"], "compression_ratio_min": res["ratio_min"],
+            "hbm_frac": hbm_gbs / hbm_peak,
+            "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
+                         "traffic": traffic,
+                         "kernel": "sweep_kernel", "per_launch_ms": per_launch_s * 1e3,
+                         "peak_source": "nominal FP64 (no measured FP64 peak); FMA-slot flops",
+                         "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": hbm_peak,
+                         "hbm_peak_source": "measured" if "hbm_gbs" in peaks else "fallback"},
+            "gpu_launches": res["launches"],
+            "clocks": res["clocks"],
+        }
+        if why:
+            line["roofline"]["traffic_note"] = why
+        if cpu:
+            line["cpu_baseline"] = cpu
+        if "e2e_s" in res:
+            line["e2e"] = {"value": ng / res["e2e_s"], "unit": "gates/s",
+                           "h2d_bytes_per_step": res["e2e_h2d"], "d2h_bytes_per_step": res["e2e_d2h"]}
+            line["per_bound"] = res["per_bound"]
+            line["aalc_theta16"] = res["aalc_theta16"]
+        print(json.dumps(line))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -206,11 +206,37 @@ typedef struct {
     unsigned long long min_stream_bytes_seen; /* smallest total after a sweep */
     unsigned long long max_stream_bytes_seen; /* largest total after a sweep */
     unsigned long long arena_regrows;  /* sweeps re-run after growing the arena */
+    unsigned long long kernel_launches; /* kernels launched by the handle */
     double alpha;                      /* scale of the next normalize step */
     int tile_log2, hmax, depth, n_qubits;
 } qsim_stats_t;
 
 qsim_status qsim_stats(qsim_t h, qsim_stats_t *out);
+
+/*
+ * Profile of the sweep kernels (Algorithm 2 passes) since profiling was
+ * switched on.  Device times come from CUDA events recorded on the
+ * handle's stream around each sweep launch.  dp_ops counts the FP64
+ * instructions of the canonical gate arithmetic (per matrix entry: first
+ * term real/imaginary 1 per component, general 2; later terms 1 or 2;
+ * entries 0 and leading +-1 free) plus 2 per amplitude for normalize;
+ * bytes counts compressed stream bytes read and written plus 32 bytes per
+ * tile of table and norm traffic.
+ */
+typedef struct {
+    unsigned long long sweep_launches;
+    double sweep_ms;
+    double dp_ops;
+    double bytes;
+    unsigned long long kernel_launches;   /* every kernel the handle launched */
+} qsim_profile_t;
+
+/* qsim_set_profiling -- on = 1 starts recording (and zeroes the counters),
+ * 0 stops.  Recording adds two event records per sweep. */
+qsim_status qsim_set_profiling(qsim_t h, int on);
+
+/* qsim_profile -- copy the counters (flushes first). */
+qsim_status qsim_profile(qsim_t h, qsim_profile_t *out);
 
 /* Message of the handle's last failing call ("" if none; h NULL: global). */
 const char *qsim_last_error(qsim_t h);
@@ -226,9 +252,9 @@ qsim_status qsim_export_tiles(qsim_t h, unsigned long long first, unsigned long 
 
 /*
  * qsim_import_tiles -- flush, then replace tiles first .. first+count-1 by
- * the concatenated streams in data (host) with the given sizes; each stream
- * is validated on the device (FORMAT on error, state unchanged... except
- * the tiles already replaced), and the normalisation scale is recomputed.
+ * the concatenated streams in data (host) with the given sizes.  Every
+ * stream is first decoded on the device; if any fails, FORMAT is returned
+ * and the state is unchanged.  The normalisation scale is recomputed.
  */
 qsim_status qsim_import_tiles(qsim_t h, unsigned long long first, unsigned long long count,
                               const void *data, const unsigned long long *sizes);

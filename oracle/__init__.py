@@ -80,6 +80,9 @@ def lib():
         L.or_csim_reset_basis.argtypes = [C.c_void_p, C.c_uint64]
         L.or_csim_sweep.argtypes = [C.c_void_p, C.POINTER(OrGate), C.c_int, ip, C.c_int]
         L.or_csim_sweep.restype = C.c_int
+        L.or_csim_sweep_sample.argtypes = [C.c_void_p, C.POINTER(OrGate), C.c_int, ip, C.c_int,
+                                           C.c_uint64, C.c_uint64]
+        L.or_csim_sweep_sample.restype = C.c_int
         L.or_csim_dense.argtypes = [C.c_void_p, dp]
         L.or_csim_dense.restype = C.c_int
         L.or_csim_stream.argtypes = [C.c_void_p, C.c_uint64, u8p, C.c_uint32]
@@ -238,6 +241,15 @@ class CSim:
         arr = gate_array(gates)
         hh = (C.c_int * max(1, len(H)))(*H)
         rc = lib().or_csim_sweep(self.h, arr, len(gates), hh, len(H))
+        if rc != 0:
+            raise RuntimeError(f"oracle sweep failed ({rc})")
+
+    def sweep_sample(self, gates, H, item_lo: int, item_hi: int):
+        """The sweep on items item_lo..item_hi-1 only (timing samples)."""
+        H = sorted(H)
+        arr = gate_array(gates)
+        hh = (C.c_int * max(1, len(H)))(*H)
+        rc = lib().or_csim_sweep_sample(self.h, arr, len(gates), hh, len(H), item_lo, item_hi)
         if rc != 0:
             raise RuntimeError(f"oracle sweep failed ({rc})")
 

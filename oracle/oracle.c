@@ -730,7 +730,25 @@ static int gate_touches(const or_gate *g, uint64_t fixed, uint64_t fmask)
  * Returns 0, or -1 on a malformed stream, -2 on a gate that needs a
  * target outside the item.
  */
+static int csim_sweep_items(or_csim *cs, const or_gate *g, int ng, const int *H, int h,
+                            uint64_t item_lo, uint64_t item_hi, int update_alpha);
+
 int or_csim_sweep(or_csim *cs, const or_gate *g, int ng, const int *H, int h)
+{
+    return csim_sweep_items(cs, g, ng, H, h, 0, UINT64_MAX, 1);
+}
+
+/* The same sweep restricted to items item_lo .. item_hi-1 (item k is the
+ * k-th tile group in increasing tile order) and without the norm update:
+ * used to time a bounded sample of a large workload. */
+int or_csim_sweep_sample(or_csim *cs, const or_gate *g, int ng, const int *H, int h,
+                         uint64_t item_lo, uint64_t item_hi)
+{
+    return csim_sweep_items(cs, g, ng, H, h, item_lo, item_hi, 0);
+}
+
+static int csim_sweep_items(or_csim *cs, const or_gate *g, int ng, const int *H, int h,
+                            uint64_t item_lo, uint64_t item_hi, int update_alpha)
 {
     int c = cs->c, n = cs->n, mb = c + h;
     uint64_t N = 1ull << c;
@@ -748,8 +766,11 @@ int or_csim_sweep(or_csim *cs, const or_gate *g, int ng, const int *H, int h)
     double alpha = cs->alpha;
     double *buf = malloc(((size_t)1 << mb) * 16);
     int rc = 0;
+    uint64_t item = 0;
     for (uint64_t T = 0; T < cs->ntiles && rc == 0; ++T) {
         if (T & hmask_tile) continue;
+        if (item < item_lo || item >= item_hi) { ++item; continue; }
+        ++item;
         uint64_t fixed = T << c;
         int touched = alpha != 1.0;
         for (int i = 0; i < ng && !touched; ++i)
@@ -776,7 +797,7 @@ int or_csim_sweep(or_csim *cs, const or_gate *g, int ng, const int *H, int h)
         }
     }
     free(buf);
-    csim_update_alpha(cs);
+    if (update_alpha) csim_update_alpha(cs);
     return rc;
 }
 

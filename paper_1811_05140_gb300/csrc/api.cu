@@ -143,6 +143,37 @@ double units_to_double_host(unsigned long long lo, unsigned long long hi) {
     return std::ldexp((double)top, drop - 112);
 }
 
+// FP64 instructions of one matrix entry's term, per component: zero and a
+// leading +-1 are free, real and imaginary entries take one, general two.
+double entry_cost(double ur, double ui, bool first) {
+    if (ur == 0.0 && ui == 0.0) return 0.0;
+    if (ui == 0.0) return (first && (ur == 1.0 || ur == -1.0)) ? 0.0 : 1.0;
+    if (ur == 0.0) return 1.0;
+    return 2.0;
+}
+
+// FP64 instructions a gate needs on an n-qubit state (controls restrict it)
+double gate_dp_ops(const HostGate &g, int n) {
+    int dim = 1 << g.k;
+    double groups = std::ldexp(1.0, n - g.k - popcount64(g.cm));
+    double per = 0.0;
+    for (int r = 0; r < dim; ++r) {
+        if (g.diag) {
+            double ur = g.m[2 * (r * dim + r)], ui = g.m[2 * (r * dim + r) + 1];
+            if (!(ur == 1.0 && ui == 0.0)) per += 2.0 * entry_cost(ur, ui, true);
+            continue;
+        }
+        bool first = true;
+        for (int c = 0; c < dim; ++c) {
+            double ur = g.m[2 * (r * dim + c)], ui = g.m[2 * (r * dim + c) + 1];
+            if (ur == 0.0 && ui == 0.0) continue;
+            per += 2.0 * entry_cost(ur, ui, first);
+            first = false;
+        }
+    }
+    return groups * per;
+}
+
 }  // namespace
 
 struct qsim_state {
@@ -174,6 +205,10 @@ struct qsim_state {
     unsigned sweep_counter = 0;
     std::vector<HostGate> queue;
     qsim_stats_t st{};
+    unsigned long long launches = 0;
+    int profiling = 0;
+    qsim_profile_t prof{};
+    std::vector<cudaEvent_t> events;
     std::string err;
     bool invalid = false;
 };
@@ -260,9 +295,9 @@ qsim_status encode_fresh(qsim_t h, const double2 *dense, unsigned long long x) {
         qsim_status s = ensure_arena(h, h->cur, need);
         if (s != QSIM_OK) return s;
         CK(cudaMemsetAsync(h->scal, 0, sizeof(qs::DevScalars), h->stream));
-        CK(qs::launch_init(dense, x, h->cc, h->ntiles, h->arena[h->cur], h->cap[h->cur],
+        ++h->launches; CK(qs::launch_init(dense, x, h->cc, h->ntiles, h->arena[h->cur], h->cap[h->cur],
                            h->table[h->cur], h->part, h->scal, grid_for(h, h->ntiles, 4), h->stream));
-        CK(qs::launch_finalize(h->scal, h->normalize, nullptr, 0, 1, h->stream));
+        ++h->launches; CK(qs::launch_finalize(h->scal, h->normalize, nullptr, 0, 1, h->stream));
         if ((s = read_scalars(h)) != QSIM_OK) return s;
         if (h->hscal->err & qs::ERR_OVERFLOW) {
             need = std::max(need + need / 2, h->hscal->bump + h->hscal->bump / 8);
@@ -414,6 +449,7 @@ qsim_status qsim_destroy(qsim_t h) {
     if (h->hgates) cudaFreeHost(h->hgates);
     if (h->used_hist) cudaFree(h->used_hist);
     if (h->hused) cudaFreeHost(h->hused);
+    for (cudaEvent_t ev : h->events) cudaEventDestroy(ev);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
     return QSIM_OK;
@@ -550,6 +586,14 @@ qsim_status qsim_flush(qsim_t h) {
             h->hgates[gi] = prepare_gate(h->queue[gi], h->c, sweeps[si]);
     CK(cudaMemcpyAsync(h->dgates, h->hgates, ng * sizeof(qs::DGate), cudaMemcpyHostToDevice, h->stream));
 
+    if (h->profiling) {
+        while (h->events.size() < 2 * ns) {
+            cudaEvent_t ev;
+            CK(cudaEventCreate(&ev));
+            h->events.push_back(ev);
+        }
+    }
+    const unsigned long long used_before = h->used;
     const int cur0 = h->cur;
     const unsigned id0 = h->sweep_counter;
     size_t k = 0;
@@ -581,8 +625,10 @@ qsim_status qsim_flush(qsim_t h) {
             p.sweep_id = id0 + (unsigned)j;
             p.use_alpha = h->normalize;
             int per_sm = qs::sweep_blocks_per_sm(h->c + sw.h);
-            CK(qs::launch_sweep(p, grid_for(h, p.nitems, per_sm), h->stream));
-            CK(qs::launch_finalize(h->scal, h->normalize, h->used_hist, (unsigned)j, 1, h->stream));
+            if (h->profiling) CK(cudaEventRecord(h->events[2 * j], h->stream));
+            ++h->launches; CK(qs::launch_sweep(p, grid_for(h, p.nitems, per_sm), h->stream));
+            if (h->profiling) CK(cudaEventRecord(h->events[2 * j + 1], h->stream));
+            ++h->launches; CK(qs::launch_finalize(h->scal, h->normalize, h->used_hist, (unsigned)j, 1, h->stream));
         }
         if ((s = read_scalars(h)) != QSIM_OK) return s;
         unsigned err = h->hscal->err;
@@ -613,7 +659,39 @@ qsim_status qsim_flush(qsim_t h) {
         h->st.max_stream_bytes_seen = std::max(h->st.max_stream_bytes_seen, h->hused[j]);
     }
     h->st.stream_bytes = h->used;
+    if (h->profiling) {
+        for (size_t j = 0; j < ns; ++j) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, h->events[2 * j], h->events[2 * j + 1]));
+            h->prof.sweep_ms += ms;
+            h->prof.sweep_launches += 1;
+            double dp = h->normalize ? 2.0 * std::ldexp(1.0, h->n) : 0.0;
+            for (int gi = sweeps[j].lo; gi < sweeps[j].hi; ++gi) dp += gate_dp_ops(h->queue[gi], h->n);
+            h->prof.dp_ops += dp;
+            unsigned long long in = j == 0 ? used_before : h->hused[j - 1];
+            h->prof.bytes += (double)in + (double)h->hused[j] + 32.0 * (double)h->ntiles;
+        }
+    }
     h->queue.clear();
+    return QSIM_OK;
+}
+
+qsim_status qsim_set_profiling(qsim_t h, int on) {
+    qsim_status s = check_usable(h);
+    if (s != QSIM_OK) return s;
+    if ((s = qsim_flush(h)) != QSIM_OK) return s;
+    h->profiling = on ? 1 : 0;
+    h->prof = qsim_profile_t{};
+    return QSIM_OK;
+}
+
+qsim_status qsim_profile(qsim_t h, qsim_profile_t *out) {
+    qsim_status s = check_usable(h);
+    if (s != QSIM_OK) return s;
+    if (!out) return fail(h, QSIM_ERR_ARG, "out is NULL");
+    if ((s = qsim_flush(h)) != QSIM_OK) return s;
+    *out = h->prof;
+    out->kernel_launches = h->launches;
     return QSIM_OK;
 }
 
@@ -645,8 +723,8 @@ qsim_status qsim_set_normalize(qsim_t h, int on) {
     h->normalize = on ? 1 : 0;
     // the scale of the next pass follows the switch
     CK(cudaMemsetAsync(&h->scal->acc_lo, 0, 2 * sizeof(unsigned long long), h->stream));
-    CK(qs::launch_norm_from_parts(h->part, h->ntiles, h->scal, grid_for(h, h->ntiles / qs::THREADS + 1, 4), h->stream));
-    CK(qs::launch_finalize(h->scal, h->normalize, nullptr, 0, 0, h->stream));
+    ++h->launches; CK(qs::launch_norm_from_parts(h->part, h->ntiles, h->scal, grid_for(h, h->ntiles / qs::THREADS + 1, 4), h->stream));
+    ++h->launches; CK(qs::launch_finalize(h->scal, h->normalize, nullptr, 0, 0, h->stream));
     return read_scalars(h);
 }
 
@@ -664,6 +742,7 @@ qsim_status qsim_set_schedule(qsim_t h, int tile_log2, int hmax, int depth) {
     size_t bytes = (size_t)16 << h->n;
     double2 *d = nullptr;
     CK(cudaMalloc(&d, bytes));
+    ++h->launches;
     cudaError_t e = qs::launch_amplitudes(h->arena[h->cur], h->table[h->cur], h->c, 0, 1ull << h->n, d,
                                           h->scal, grid_for(h, h->ntiles, 4), h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -702,6 +781,7 @@ qsim_status qsim_amplitudes(qsim_t h, unsigned long long start, unsigned long lo
     for (unsigned long long done = 0; done < count;) {
         unsigned long long cnt = std::min(chunk, count - done);
         unsigned long long tiles = ((start + done + cnt - 1) >> h->c) - ((start + done) >> h->c) + 1;
+        ++h->launches;
         cudaError_t e = qs::launch_amplitudes(h->arena[h->cur], h->table[h->cur], h->c, start + done, cnt, d,
                                               h->scal, grid_for(h, tiles, 4), h->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(out + 2 * done, d, cnt * 16, cudaMemcpyDeviceToHost, h->stream);
@@ -733,7 +813,7 @@ qsim_status qsim_probabilities(qsim_t h, const int *qubits, int nq, double *out)
     std::vector<unsigned long long> hb(2 * nb);
     cudaError_t e = cudaMemsetAsync(dbk, 0, nb * 16, h->stream);
     if (e == cudaSuccess && nq) e = cudaMemcpyAsync(dq, qubits, nq * sizeof(int), cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = qs::launch_probs(h->arena[h->cur], h->table[h->cur], h->c, h->ntiles, dq, nq, dbk,
+    if (e == cudaSuccess) ++h->launches, e = qs::launch_probs(h->arena[h->cur], h->table[h->cur], h->c, h->ntiles, dq, nq, dbk,
                                                h->scal, grid_for(h, h->ntiles, 4), h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), dbk, nb * 16, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -809,11 +889,11 @@ qsim_status qsim_fidelity(qsim_t h, const qsim_ref *ref, double *F, double *over
     cudaError_t e = cudaMalloc(&a, h->ntiles * sizeof(qs::Acc4));
     if (e == cudaSuccess) e = cudaMalloc(&b, std::max<unsigned long long>(1, h->ntiles / 2) * sizeof(qs::Acc4));
     if (e == cudaSuccess)
-        e = qs::launch_fidelity(h->arena[h->cur], h->table[h->cur], h->c, h->ntiles, rs, a, h->scal,
+        ++h->launches, e = qs::launch_fidelity(h->arena[h->cur], h->table[h->cur], h->c, h->ntiles, rs, a, h->scal,
                                 grid_for(h, h->ntiles, 4), h->stream);
     unsigned long long cnt = h->ntiles;
     while (e == cudaSuccess && cnt > 1) {
-        e = qs::launch_pair_sum(a, b, cnt / 2, grid_for(h, cnt / 2 / qs::THREADS + 1, 8), h->stream);
+        ++h->launches, e = qs::launch_pair_sum(a, b, cnt / 2, grid_for(h, cnt / 2 / qs::THREADS + 1, 8), h->stream);
         std::swap(a, b);
         cnt /= 2;
     }
@@ -840,7 +920,7 @@ qsim_status qsim_compressed_bytes(qsim_t h, unsigned long long *stream_bytes, un
     CK(cudaMalloc(&d, sizeof(unsigned long long)));
     cudaError_t e = cudaMemsetAsync(d, 0, sizeof *d, h->stream);
     if (e == cudaSuccess)
-        e = qs::launch_sum_sizes(h->arena[h->cur], h->table[h->cur], h->ntiles, d,
+        ++h->launches, e = qs::launch_sum_sizes(h->arena[h->cur], h->table[h->cur], h->ntiles, d,
                                  grid_for(h, h->ntiles / qs::THREADS + 1, 8), h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, d, sizeof tot, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -860,6 +940,7 @@ qsim_status qsim_stats(qsim_t h, qsim_stats_t *out) {
     }
     *out = h->st;
     for (int i = 0; i < 8; ++i) out->level_hist[i] = h->hscal->hist[i];
+    out->kernel_launches = h->launches;
     out->items_done = h->hscal->items_done;
     out->items_skipped = h->hscal->items_skipped;
     out->alpha = h->hscal->alpha;
@@ -880,6 +961,7 @@ qsim_status qsim_export_tiles(qsim_t h, unsigned long long first, unsigned long 
     unsigned long long *dsz = nullptr, *doff = nullptr;
     uint8_t *dbuf = nullptr;
     CK(cudaMalloc(&dsz, count * 8));
+    ++h->launches;
     cudaError_t e = qs::launch_sizes(h->arena[h->cur], h->table[h->cur], first, count, dsz,
                                      grid_for(h, count / qs::THREADS + 1, 8), h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sizes, dsz, count * 8, cudaMemcpyDeviceToHost, h->stream);
@@ -894,7 +976,7 @@ qsim_status qsim_export_tiles(qsim_t h, unsigned long long first, unsigned long 
     if (e == cudaSuccess) e = cudaMalloc(&dbuf, tot);
     if (e == cudaSuccess) e = cudaMemcpyAsync(doff, offs.data(), count * 8, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
-        e = qs::launch_gather(h->arena[h->cur], h->table[h->cur], first, count, doff, dsz, dbuf,
+        ++h->launches, e = qs::launch_gather(h->arena[h->cur], h->table[h->cur], first, count, doff, dsz, dbuf,
                               grid_for(h, count, 8), h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, dbuf, tot, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -932,7 +1014,7 @@ qsim_status qsim_import_tiles(qsim_t h, unsigned long long first, unsigned long 
     if (e == cudaSuccess) e = cudaMemcpyAsync(dbuf, data, tot, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(doff, offs.data(), count * 8, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dsz, sizes, count * 8, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = qs::launch_validate(dbuf, doff, dsz, count, h->c, dparts, dbad, grid_for(h, count, 4), h->stream);
+    if (e == cudaSuccess) ++h->launches, e = qs::launch_validate(dbuf, doff, dsz, count, h->c, dparts, dbad, grid_for(h, count, 4), h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, dbad, sizeof hbad, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     auto cleanup = [&]() {
@@ -958,11 +1040,11 @@ qsim_status qsim_import_tiles(qsim_t h, unsigned long long first, unsigned long 
         h->arena[h->cur] = na;
         h->cap[h->cur] = nc;
     }
-    e = qs::launch_place(dbuf, doff, dsz, count, first, h->used, h->arena[h->cur], h->table[h->cur], dparts, h->part,
+    ++h->launches, e = qs::launch_place(dbuf, doff, dsz, count, first, h->used, h->arena[h->cur], h->table[h->cur], dparts, h->part,
                          grid_for(h, count, 8), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(&h->scal->acc_lo, 0, 2 * sizeof(unsigned long long), h->stream);
-    if (e == cudaSuccess) e = qs::launch_norm_from_parts(h->part, h->ntiles, h->scal, grid_for(h, h->ntiles / qs::THREADS + 1, 4), h->stream);
-    if (e == cudaSuccess) e = qs::launch_finalize(h->scal, h->normalize, nullptr, 0, 0, h->stream);
+    if (e == cudaSuccess) ++h->launches, e = qs::launch_norm_from_parts(h->part, h->ntiles, h->scal, grid_for(h, h->ntiles / qs::THREADS + 1, 4), h->stream);
+    if (e == cudaSuccess) ++h->launches, e = qs::launch_finalize(h->scal, h->normalize, nullptr, 0, 0, h->stream);
     cleanup();
     if (e != cudaSuccess) return fail(h, QSIM_ERR_CUDA, "import: %s", cudaGetErrorString(e));
     h->used += tot;

@@ -25,7 +25,8 @@ EXPORTS = ["qsim_create", "qsim_destroy", "qsim_set_stream", "qsim_set_aalc", "q
            "qsim_set_schedule", "qsim_reset_basis", "qsim_set_amplitudes", "qsim_apply_gate",
            "qsim_flush", "qsim_probabilities", "qsim_amplitudes", "qsim_fidelity",
            "qsim_compressed_bytes", "qsim_stats", "qsim_last_error", "qsim_export_tiles",
-           "qsim_import_tiles", "qsim_plan_sweeps", "qsim_version"]
+           "qsim_import_tiles", "qsim_plan_sweeps", "qsim_version", "qsim_set_profiling",
+           "qsim_profile"]
 
 
 class QsimError(RuntimeError):
@@ -45,9 +46,16 @@ class Stats(C.Structure):
                 ("items_done", C.c_ulonglong), ("items_skipped", C.c_ulonglong),
                 ("level_hist", C.c_ulonglong * 8), ("stream_bytes", C.c_ulonglong),
                 ("min_stream_bytes_seen", C.c_ulonglong), ("max_stream_bytes_seen", C.c_ulonglong),
-                ("arena_regrows", C.c_ulonglong), ("alpha", C.c_double),
+                ("arena_regrows", C.c_ulonglong), ("kernel_launches", C.c_ulonglong),
+                ("alpha", C.c_double),
                 ("tile_log2", C.c_int), ("hmax", C.c_int), ("depth", C.c_int),
                 ("n_qubits", C.c_int)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("sweep_launches", C.c_ulonglong), ("sweep_ms", C.c_double),
+                ("dp_ops", C.c_double), ("bytes", C.c_double),
+                ("kernel_launches", C.c_ulonglong)]
 
 
 _lib = None
@@ -86,6 +94,8 @@ def load() -> C.CDLL:
         "qsim_plan_sweeps": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, ip, ip, dp, ip, ip,
                               ip, C.c_int], C.c_int),
         "qsim_version": ([], C.c_char_p),
+        "qsim_set_profiling": ([vp, C.c_int], C.c_int),
+        "qsim_profile": ([vp, C.POINTER(Profile)], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -256,6 +266,14 @@ class State:
         d = {f: getattr(s, f) for f, _ in Stats._fields_}
         d["level_hist"] = list(s.level_hist)
         return d
+
+    def set_profiling(self, on: bool = True):
+        self._check(self._L.qsim_set_profiling(self.h, int(bool(on))))
+
+    def profile(self) -> dict:
+        p = Profile()
+        self._check(self._L.qsim_profile(self.h, C.byref(p)))
+        return {f: getattr(p, f) for f, _ in Profile._fields_}
 
     # -- tile streams
     def export_tiles(self, first: int = 0, count: int | None = None) -> list[bytes]:
