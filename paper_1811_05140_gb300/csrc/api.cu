@@ -143,6 +143,14 @@ double units_to_double_host(unsigned long long lo, unsigned long long hi) {
     return std::ldexp((double)top, drop - 112);
 }
 
+// class of a matrix entry (see the EC_* codes)
+unsigned entry_class(double ur, double ui) {
+    if (ur == 0.0 && ui == 0.0) return qs::EC_ZERO;
+    if (ui == 0.0) return ur == 1.0 ? qs::EC_ONE : (ur == -1.0 ? qs::EC_MINUS_ONE : qs::EC_REAL);
+    if (ur == 0.0) return qs::EC_IMAG;
+    return qs::EC_GENERAL;
+}
+
 // FP64 instructions of one matrix entry's term, per component: zero and a
 // leading +-1 are free, real and imaginary entries take one, general two.
 double entry_cost(double ur, double ui, bool first) {
@@ -177,7 +185,7 @@ double gate_dp_ops(const HostGate &g, int n) {
 }  // namespace
 
 struct qsim_state {
-    int n = 0, c = 0, hmax = 2, depth = 64;
+    int n = 0, c = 0, hmax = 2, depth = qs::MAX_SWEEP_GATES;
     qsim_codec codec = QSIM_CODEC_REL;
     double eps = 0.0;
     int normalize = 0;
@@ -198,6 +206,7 @@ struct qsim_state {
     size_t dgates_cap = 0;
     qs::DGate *hgates = nullptr;          // pinned staging
     size_t hgates_cap = 0;
+    qs::SGate *dsg = nullptr, *hsg = nullptr;
     unsigned long long *used_hist = nullptr;
     size_t used_hist_cap = 0;
     unsigned long long *hused = nullptr;  // pinned
@@ -363,8 +372,9 @@ qsim_status check_usable(qsim_t h) {
     return QSIM_OK;
 }
 
-qs::DGate prepare_gate(const HostGate &g, int c, const Sweep &sw) {
-    qs::DGate d{};
+void prepare_gate(const HostGate &g, int c, const Sweep &sw, qs::DGate &d, qs::SGate &sgt) {
+    d = qs::DGate{};
+    sgt = qs::SGate{};
     std::memcpy(d.m, g.m, sizeof d.m);
     d.k = g.k;
     d.diag = g.diag ? 1 : 0;
@@ -385,7 +395,36 @@ qs::DGate prepare_gate(const HostGate &g, int c, const Sweep &sw) {
         if (p >= 0) { d.lcm |= 1ull << p; d.lcv |= v << p; }
         else { d.fcm |= 1ull << q; d.fcv |= v << q; }
     }
-    return d;
+    // compact form
+    const int dim = 1 << g.k;
+    sgt.kind = g.diag ? 0 : (uint8_t)g.k;
+    sgt.k = (uint8_t)g.k;
+    sgt.p0 = (int8_t)d.pos[0];
+    sgt.p1 = (int8_t)(g.k > 1 ? d.pos[1] : -1);
+    sgt.t0 = (uint8_t)d.t[0];
+    sgt.t1 = (uint8_t)d.t[1];
+    sgt.fcm = d.fcm;
+    sgt.fcv = d.fcv;
+    sgt.lcm = (uint32_t)d.lcm;
+    sgt.lcv = (uint32_t)d.lcv;
+    if (g.diag) {
+        for (int r = 0; r < dim; ++r) {
+            sgt.d[2 * r] = g.m[2 * (r * dim + r)];
+            sgt.d[2 * r + 1] = g.m[2 * (r * dim + r) + 1];
+            unsigned code = entry_class(sgt.d[2 * r], sgt.d[2 * r + 1]);
+            sgt.cls |= (unsigned long long)code << (3 * r);
+            if (code == qs::EC_ONE) sgt.one_mask |= (uint8_t)(1u << r);
+        }
+    } else {
+        for (int e = 0; e < dim * dim; ++e)
+            sgt.cls |= (unsigned long long)entry_class(g.m[2 * e], g.m[2 * e + 1]) << (3 * e);
+    }
+    // buffer bits pinned by local controls and buffer targets, ascending
+    unsigned pinned = (unsigned)d.lcm;
+    for (int i = 0; i < g.k; ++i)
+        if (d.pos[i] >= 0) pinned |= 1u << d.pos[i];
+    for (int b = 0; b < 32; ++b)
+        if ((pinned >> b) & 1u) sgt.ins[sgt.nins++] = (uint8_t)b;
 }
 
 }  // namespace
@@ -412,7 +451,7 @@ qsim_status qsim_create(qsim_t *out, int n_qubits, int block_log2, qsim_codec co
     h->n = n_qubits;
     h->c = std::min(std::min(block_log2, n_qubits), qs::MAX_C);
     h->hmax = 2;
-    h->depth = 64;
+    h->depth = qs::MAX_SWEEP_GATES;
     h->codec = codec;
     h->eps = rel_err_bound;
     qsim_status s = QSIM_OK;
@@ -447,6 +486,8 @@ qsim_status qsim_destroy(qsim_t h) {
     if (h->hscal) cudaFreeHost(h->hscal);
     if (h->dgates) cudaFree(h->dgates);
     if (h->hgates) cudaFreeHost(h->hgates);
+    if (h->dsg) cudaFree(h->dsg);
+    if (h->hsg) cudaFreeHost(h->hsg);
     if (h->used_hist) cudaFree(h->used_hist);
     if (h->hused) cudaFreeHost(h->hused);
     for (cudaEvent_t ev : h->events) cudaEventDestroy(ev);
@@ -557,17 +598,23 @@ qsim_status qsim_flush(qsim_t h) {
     // stage every gate, prepared for its sweep, in one upload
     if (h->hgates_cap < ng) {
         if (h->hgates) cudaFreeHost(h->hgates);
+        if (h->hsg) cudaFreeHost(h->hsg);
         h->hgates = nullptr;
+        h->hsg = nullptr;
         h->hgates_cap = 0;
         CK(cudaMallocHost(&h->hgates, ng * sizeof(qs::DGate)));
+        CK(cudaMallocHost(&h->hsg, ng * sizeof(qs::SGate)));
         h->hgates_cap = ng;
     }
     if (h->dgates_cap < ng) {
         CK(cudaStreamSynchronize(h->stream));
         if (h->dgates) cudaFree(h->dgates);
+        if (h->dsg) cudaFree(h->dsg);
         h->dgates = nullptr;
+        h->dsg = nullptr;
         h->dgates_cap = 0;
         CK(cudaMalloc(&h->dgates, ng * sizeof(qs::DGate)));
+        CK(cudaMalloc(&h->dsg, ng * sizeof(qs::SGate)));
         h->dgates_cap = ng;
     }
     if (h->used_hist_cap < ns) {
@@ -583,8 +630,9 @@ qsim_status qsim_flush(qsim_t h) {
     }
     for (size_t si = 0; si < ns; ++si)
         for (int gi = sweeps[si].lo; gi < sweeps[si].hi; ++gi)
-            h->hgates[gi] = prepare_gate(h->queue[gi], h->c, sweeps[si]);
+            prepare_gate(h->queue[gi], h->c, sweeps[si], h->hgates[gi], h->hsg[gi]);
     CK(cudaMemcpyAsync(h->dgates, h->hgates, ng * sizeof(qs::DGate), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->dsg, h->hsg, ng * sizeof(qs::SGate), cudaMemcpyHostToDevice, h->stream));
 
     if (h->profiling) {
         while (h->events.size() < 2 * ns) {
@@ -615,6 +663,7 @@ qsim_status qsim_flush(qsim_t h) {
             p.part = h->part;
             p.scal = h->scal;
             p.gates = h->dgates + sw.lo;
+            p.sgates = h->dsg + sw.lo;
             p.ngates = sw.hi - sw.lo;
             p.n = h->n;
             p.h = sw.h;
@@ -733,7 +782,7 @@ qsim_status qsim_set_schedule(qsim_t h, int tile_log2, int hmax, int depth) {
     if (s != QSIM_OK) return s;
     if (tile_log2 < 1 || tile_log2 > qs::MAX_C || tile_log2 > h->n) return fail(h, QSIM_ERR_ARG, "tile_log2 must be 1..min(10, n)");
     if (hmax < 1 || hmax > 2 || tile_log2 + hmax > qs::MAX_ITEM_LOG2) return fail(h, QSIM_ERR_ARG, "hmax must be 1..2");
-    if (depth < 1 || depth > 4096) return fail(h, QSIM_ERR_ARG, "depth must be 1..4096");
+    if (depth < 1 || depth > qs::MAX_SWEEP_GATES) return fail(h, QSIM_ERR_ARG, "depth must be 1..%d", qs::MAX_SWEEP_GATES);
     if ((s = qsim_flush(h)) != QSIM_OK) return s;
     h->hmax = hmax;
     h->depth = depth;

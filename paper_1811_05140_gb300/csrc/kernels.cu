@@ -129,29 +129,30 @@ __device__ double units_to_double(unsigned long long lo, unsigned long long hi) 
 }
 
 // ---------------------------------------------------------------- gates
-// y = u * x for one matrix entry (first term of a row)
-__device__ __forceinline__ void term_first(double ur, double ui, double xr, double xi,
-                                           double &yr, double &yi) {
-    if (ui == 0.0) {
-        if (ur == 1.0) { yr = xr; yi = xi; }                 // == 1.0 * x exactly
-        else if (ur == -1.0) { yr = -xr; yi = -xi; }         // == -1.0 * x exactly
-        else { yr = __dmul_rn(ur, xr); yi = __dmul_rn(ur, xi); }
-    } else if (ur == 0.0) {
-        yr = -__dmul_rn(ui, xi);
-        yi = __dmul_rn(ui, xr);
-    } else {
-        yr = __fma_rn(ur, xr, -__dmul_rn(ui, xi));
-        yi = __fma_rn(ur, xi, __dmul_rn(ui, xr));
+// y = u * x for one matrix entry of class `code` (first term of a row).
+// The class only selects which operations run; the arithmetic is the
+// canonical one (a leading +-1 is an exact copy / sign flip).
+__device__ __forceinline__ void term_first(unsigned code, double ur, double ui, double xr,
+                                           double xi, double &yr, double &yi) {
+    switch (code) {
+        case EC_ONE: yr = xr; yi = xi; break;
+        case EC_MINUS_ONE: yr = -xr; yi = -xi; break;
+        case EC_REAL: yr = __dmul_rn(ur, xr); yi = __dmul_rn(ur, xi); break;
+        case EC_IMAG: yr = -__dmul_rn(ui, xi); yi = __dmul_rn(ui, xr); break;
+        default:
+            yr = __fma_rn(ur, xr, -__dmul_rn(ui, xi));
+            yi = __fma_rn(ur, xi, __dmul_rn(ui, xr));
+            break;
     }
 }
 
 // acc += u * x
-__device__ __forceinline__ void term_acc(double ur, double ui, double xr, double xi,
-                                         double &ar, double &ai) {
-    if (ui == 0.0) {
+__device__ __forceinline__ void term_acc(unsigned code, double ur, double ui, double xr,
+                                         double xi, double &ar, double &ai) {
+    if (code <= EC_REAL) {
         ar = __fma_rn(ur, xr, ar);
         ai = __fma_rn(ur, xi, ai);
-    } else if (ur == 0.0) {
+    } else if (code == EC_IMAG) {
         ar = __fma_rn(-ui, xi, ar);
         ai = __fma_rn(ui, xr, ai);
     } else {
@@ -160,17 +161,20 @@ __device__ __forceinline__ void term_acc(double ur, double ui, double xr, double
     }
 }
 
+// Row r of y = U x over the nonzero entries, in column order.
 template <int DIM>
-__device__ __forceinline__ void row_eval(const double *m, int r, const double *xr,
-                                         const double *xi, double &yr, double &yi) {
+__device__ __forceinline__ void row_eval(const double *m, unsigned long long cls, int r,
+                                         const double *xr, const double *xi, double &yr,
+                                         double &yi) {
     bool first = true;
     double ar = 0.0, ai = 0.0;
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
+        unsigned code = (unsigned)(cls >> (3 * (r * DIM + c))) & 7u;
+        if (code == EC_ZERO) continue;
         double ur = m[2 * (r * DIM + c)], ui = m[2 * (r * DIM + c) + 1];
-        if (ur == 0.0 && ui == 0.0) continue;
-        if (first) { term_first(ur, ui, xr[c], xi[c], ar, ai); first = false; }
-        else term_acc(ur, ui, xr[c], xi[c], ar, ai);
+        if (first) { term_first(code, ur, ui, xr[c], xi[c], ar, ai); first = false; }
+        else term_acc(code, ur, ui, xr[c], xi[c], ar, ai);
     }
     yr = ar;
     yi = ai;
@@ -181,93 +185,117 @@ __device__ __forceinline__ unsigned insert_zero(unsigned v, int p) {
     return ((v & ~lowm) << 1) | (v & lowm);
 }
 
-// Apply the sweep's gates to an item buffer of 2^mb amplitudes (planar
-// re/im in shared memory).  fixed = global index bits of the item's
-// non-buffer qubits.
-__device__ void apply_gates(double *re, double *im, int mb, const DGate *gates, int ngates,
-                            unsigned long long fixed) {
-    const unsigned M = 1u << mb;
-    for (int gi = 0; gi < ngates; ++gi) {
-        const DGate &g = gates[gi];
-        if (((fixed ^ g.fcv) & g.fcm) != 0ull) continue;     // fixed control not met
-        const unsigned lcm = (unsigned)g.lcm, lcv = (unsigned)g.lcv;
-        if (g.diag) {
-            const int dim = 1 << g.k;
-            int fr = 0, bmask_p0 = g.pos[0], bmask_p1 = g.k > 1 ? g.pos[1] : -1;
-            if (bmask_p0 < 0) fr |= (int)((fixed >> g.t[0]) & 1ull);
-            if (g.k > 1 && bmask_p1 < 0) fr |= (int)((fixed >> g.t[1]) & 1ull) << 1;
-            for (unsigned l = threadIdx.x; l < M; l += THREADS) {
-                if ((l & lcm) != lcv) continue;
-                int r = fr;
-                if (bmask_p0 >= 0) r |= (int)((l >> bmask_p0) & 1u);
-                if (bmask_p1 >= 0) r |= (int)((l >> bmask_p1) & 1u) << 1;
-                double ur = g.m[2 * (r * dim + r)], ui = g.m[2 * (r * dim + r) + 1];
-                if (ui == 0.0 && ur == 1.0) continue;
-                double yr, yi;
-                if (ur == 0.0 && ui == 0.0) { yr = 0.0; yi = 0.0; }
-                else term_first(ur, ui, re[l], im[l], yr, yi);
-                re[l] = yr;
-                im[l] = yi;
-            }
-        } else if (g.k == 1) {
-            const int p = g.pos[0];
-            const unsigned bit = 1u << p;
-            for (unsigned pi = threadIdx.x; pi < (M >> 1); pi += THREADS) {
-                unsigned l0 = insert_zero(pi, p);
-                if ((l0 & lcm) != lcv) continue;
-                unsigned l1 = l0 | bit;
-                double xr[2] = {re[l0], re[l1]}, xi[2] = {im[l0], im[l1]};
-                double y0r, y0i, y1r, y1i;
-                row_eval<2>(g.m, 0, xr, xi, y0r, y0i);
-                row_eval<2>(g.m, 1, xr, xi, y1r, y1i);
-                re[l0] = y0r; im[l0] = y0i;
-                re[l1] = y1r; im[l1] = y1i;
-            }
-        } else {
-            const int p0 = g.pos[0], p1 = g.pos[1];
-            const int plo = p0 < p1 ? p0 : p1, phi = p0 < p1 ? p1 : p0;
-            for (unsigned qi = threadIdx.x; qi < (M >> 2); qi += THREADS) {
-                unsigned l = insert_zero(insert_zero(qi, plo), phi);
-                if ((l & lcm) != lcv) continue;
-                unsigned idx[4];
-                double xr[4], xi[4];
-#pragma unroll
-                for (int s = 0; s < 4; ++s) {
-                    idx[s] = l | ((unsigned)(s & 1) << p0) | ((unsigned)(s >> 1) << p1);
-                    xr[s] = re[idx[s]];
-                    xi[s] = im[idx[s]];
-                }
-                double yr[4], yi[4];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) row_eval<4>(g.m, r, xr, xi, yr[r], yi[r]);
-#pragma unroll
-                for (int s = 0; s < 4; ++s) { re[idx[s]] = yr[s]; im[idx[s]] = yi[s]; }
-            }
-        }
-        __syncthreads();
+// buffer index of the f-th amplitude whose pinned bits (ascending ins[]) are 0
+__device__ __forceinline__ unsigned deposit(unsigned f, const SGate &s) {
+    for (int i = 0; i < s.nins; ++i) f = insert_zero(f, s.ins[i]);
+    return f;
+}
+
+// Which gates of the sweep change something in the item with fixed bits
+// `fixed`: fixed controls met, and for a diagonal gate whose targets are all
+// fixed, its entry there is not exactly 1.  Bit g of the result.
+__device__ __forceinline__ bool gate_active(const SGate &s, unsigned long long fixed) {
+    if (((fixed ^ s.fcv) & s.fcm) != 0ull) return false;
+    if (s.kind == 0 && s.p0 < 0 && (s.k < 2 || s.p1 < 0)) {
+        int r = (int)((fixed >> s.t0) & 1ull);
+        if (s.k > 1) r |= (int)((fixed >> s.t1) & 1ull) << 1;
+        if ((s.one_mask >> r) & 1) return false;
+    }
+    return true;
+}
+
+// One diagonal gate, applied only where it changes something: the
+// amplitudes whose local controls hold and whose target sub-index r has an
+// entry other than exactly 1.  Enumerating just those keeps every lane of
+// every FP64 instruction busy (masked lanes cost the same on this part).
+__device__ void diag_gate(double *re, double *im, int mb, const SGate &s,
+                          unsigned long long fixed) {
+    // sub-indices r to visit: entry != 1 and consistent with fixed targets
+    unsigned rpack = 0;          // sub-indices, 2 bits each
+    int nr = 0;
+    const int dim = 1 << s.k;
+    int fmask = 0, fval = 0;
+    if (s.p0 < 0) { fmask |= 1; fval |= (int)((fixed >> s.t0) & 1ull); }
+    if (s.k > 1 && s.p1 < 0) { fmask |= 2; fval |= (int)((fixed >> s.t1) & 1ull) << 1; }
+    for (int r = 0; r < dim; ++r)
+        if ((r & fmask) == fval && !((s.one_mask >> r) & 1)) rpack |= (unsigned)r << (2 * nr++);
+    if (nr == 0) return;
+    const int fb = mb - s.nins;                 // free bits
+    const unsigned cnt = (unsigned)nr << fb;
+    for (unsigned f = threadIdx.x; f < cnt; f += THREADS) {
+        int r = (int)((rpack >> (2 * (f >> fb))) & 3u);
+        unsigned l = deposit(f & ((1u << fb) - 1u), s) | s.lcv;
+        if (s.p0 >= 0) l |= (unsigned)(r & 1) << s.p0;
+        if (s.k > 1 && s.p1 >= 0) l |= (unsigned)((r >> 1) & 1) << s.p1;
+        unsigned code = (unsigned)(s.cls >> (3 * r)) & 7u;
+        double yr = 0.0, yi = 0.0;
+        if (code != EC_ZERO) term_first(code, s.d[2 * r], s.d[2 * r + 1], re[l], im[l], yr, yi);
+        re[l] = yr;
+        im[l] = yi;
     }
 }
 
-// Does gate g change any amplitude of the item with fixed bits `fixed`?
-__device__ __forceinline__ bool gate_touches(const DGate &g, unsigned long long fixed) {
-    if (((fixed ^ g.fcv) & g.fcm) != 0ull) return false;
-    bool allfixed = g.pos[0] < 0 && (g.k < 2 || g.pos[1] < 0);
-    if (allfixed) {
-        int dim = 1 << g.k, r = (int)((fixed >> g.t[0]) & 1ull);
-        if (g.k > 1) r |= (int)((fixed >> g.t[1]) & 1ull) << 1;
-        if (g.m[2 * (r * dim + r)] == 1.0 && g.m[2 * (r * dim + r) + 1] == 0.0) return false;
+__device__ void one_target(double *re, double *im, int mb, const SGate &s, const DGate &dg) {
+    double m[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) m[i] = dg.m[i];
+    const unsigned bit = 1u << s.p0;
+    const unsigned cnt = 1u << (mb - s.nins);
+    for (unsigned f = threadIdx.x; f < cnt; f += THREADS) {
+        unsigned l0 = deposit(f, s) | s.lcv;
+        unsigned l1 = l0 | bit;
+        double xr[2] = {re[l0], re[l1]}, xi[2] = {im[l0], im[l1]};
+        double y0r, y0i, y1r, y1i;
+        row_eval<2>(m, s.cls, 0, xr, xi, y0r, y0i);
+        row_eval<2>(m, s.cls, 1, xr, xi, y1r, y1i);
+        re[l0] = y0r; im[l0] = y0i;
+        re[l1] = y1r; im[l1] = y1i;
     }
-    return true;
+}
+
+__device__ void two_target(double *re, double *im, int mb, const SGate &s, const DGate &dg) {
+    const unsigned cnt = 1u << (mb - s.nins);
+    for (unsigned f = threadIdx.x; f < cnt; f += THREADS) {
+        unsigned l = deposit(f, s) | s.lcv;
+        unsigned idx[4];
+        double xr[4], xi[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            idx[q] = l | ((unsigned)(q & 1) << s.p0) | ((unsigned)(q >> 1) << s.p1);
+            xr[q] = re[idx[q]];
+            xi[q] = im[idx[q]];
+        }
+        double yr[4], yi[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) row_eval<4>(dg.m, s.cls, r, xr, xi, yr[r], yi[r]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { re[idx[q]] = yr[q]; im[idx[q]] = yi[q]; }
+    }
+}
+
+// Apply the sweep's gates (in order) to an item buffer of 2^mb amplitudes.
+// active: bit g set when gate g changes something in this item.
+__device__ void apply_gates(double *re, double *im, int mb, const SGate *sg, const DGate *dg,
+                            int ngates, unsigned long long active, unsigned long long fixed) {
+    for (int g = 0; g < ngates; ++g) {
+        if (!((active >> g) & 1ull)) continue;
+        const SGate &s = sg[g];
+        if (s.kind == 0) diag_gate(re, im, mb, s, fixed);
+        else if (s.kind == 1) one_target(re, im, mb, s, dg[g]);
+        else two_target(re, im, mb, s, dg[g]);
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------- codec scratch
 struct Scratch {
     uint32_t sw[64];          // sign word per (comp, group): index k*G + g
-    uint32_t nw[64];          // data words per (comp, group)
+    uint32_t nw[64];          // data words per (comp, group) at the chosen level
     uint32_t woff[64];        // exclusive prefix of nw (words)
     long long gtot[64];       // decode: group sums of residuals
     long long gpre[64];       // decode: exclusive prefix of group sums
-    uint32_t wd[64];          // widths
+    uint8_t wd[64];           // decode: widths
+    uint8_t wl[MAX_LEVELS][64];   // encode: width per level and (comp, group)
     uint32_t lvl_words[MAX_LEVELS];
     uint32_t lvl_nonzero[MAX_LEVELS];
     uint32_t hdr[8];
@@ -276,7 +304,6 @@ struct Scratch {
     unsigned long long off;
     uint32_t body, size, data_off, wtotal;
     int mode, s, level, smode[2], ok, bad;
-    int flag_nonfinite, flag_inelig;
 };
 
 __device__ __forceinline__ uint32_t sign_bytes(int mode, int G) {
@@ -284,34 +311,36 @@ __device__ __forceinline__ uint32_t sign_bytes(int mode, int G) {
                              : (mode == S_WORDS ? 4u * (uint32_t)G : 0u);
 }
 
-// warp 0: exclusive scan of sc.nw[0..cnt) into sc.woff, total in sc.wtotal
-__device__ __forceinline__ void scan_words_warp0(Scratch &sc, int cnt) {
-    if (threadIdx.x >= 32) return;
-    int lane = threadIdx.x;
+// exclusive scan of cnt (<= 64) word counts by one warp; returns the total
+__device__ __forceinline__ uint32_t warp_scan_words(const uint32_t *in, uint32_t *out, int cnt) {
+    int lane = threadIdx.x & 31;
     uint32_t carry = 0;
     for (int base = 0; base < cnt; base += 32) {
-        uint32_t v = (base + lane < cnt) ? sc.nw[base + lane] : 0u;
+        uint32_t v = (base + lane < cnt) ? in[base + lane] : 0u;
         uint32_t inc = v;
         for (int d = 1; d < 32; d <<= 1) {
             uint32_t o = __shfl_up_sync(FULL, inc, d);
             if (lane >= d) inc += o;
         }
-        if (base + lane < cnt) sc.woff[base + lane] = carry + inc - v;
+        if (base + lane < cnt) out[base + lane] = carry + inc - v;
         carry += __shfl_sync(FULL, inc, 31);
     }
-    if (lane == 0) sc.wtotal = carry;
+    return carry;
 }
 
 // ---------------------------------------------------------------- decode
-// Decode one stream into planar re/im (2^c values each).  CTA-wide; all
+// Decode one stream into planar re/im (2^c values each), multiplied by
+// alpha when `scale` is set (Algorithm 2's normalize, fused; the caller
+// decides scale = (alpha != 1) once per launch).  CTA-wide; all
 // threads must call it.  Returns nonzero (and zero-fills) on a malformed
 // stream.
-__device__ int decode_tile(const uint8_t *src, int c, double *re, double *im, Scratch &sc) {
+__device__ int decode_tile(const uint8_t *src, int c, double *re, double *im, Scratch &sc,
+                           double alpha, bool scale) {
     const int N = 1 << c;
     const int G = N >= 32 ? N / 32 : 1;
     const int L = N >= 32 ? 32 : N;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid < 8) sc.hdr[tid] = reinterpret_cast<const uint32_t *>(src)[tid];
+    if (tid < 8) sc.hdr[tid] = __ldg(reinterpret_cast<const uint32_t *>(src) + tid);
     __syncthreads();
     const uint32_t h0 = sc.hdr[0];
     const int mode = h0 & 0xFF, s = (h0 >> 8) & 0xFF;
@@ -336,6 +365,7 @@ __device__ int decode_tile(const uint8_t *src, int c, double *re, double *im, Sc
     if (mode == M_CONST) {
         double v0 = bitsd((a0 << s) | ((unsigned long long)sm0 << 63));
         double v1 = bitsd((a1 << s) | ((unsigned long long)sm1 << 63));
+        if (scale) { v0 = __dmul_rn(v0, alpha); v1 = __dmul_rn(v1, alpha); }
         for (int i = tid; i < N; i += THREADS) { re[i] = v0; im[i] = v1; }
         __syncthreads();
         return 0;
@@ -343,7 +373,8 @@ __device__ int decode_tile(const uint8_t *src, int c, double *re, double *im, Sc
     if (mode == M_RAW) {
         const double2 *v = reinterpret_cast<const double2 *>(b);
         for (int i = tid; i < N; i += THREADS) {
-            double2 x = v[i];
+            double2 x = __ldg(v + i);
+            if (scale) { x.x = __dmul_rn(x.x, alpha); x.y = __dmul_rn(x.y, alpha); }
             re[i] = x.x;
             im[i] = x.y;
         }
@@ -356,29 +387,31 @@ __device__ int decode_tile(const uint8_t *src, int c, double *re, double *im, Sc
     for (int t = tid; t < 2 * G; t += THREADS) {
         int k = t / G, g = t % G;
         int md = k ? sm1 : sm0;
-        const uint8_t *sec = b + (k ? sb0 : 0);
+        const uint32_t *sec = reinterpret_cast<const uint32_t *>(b + (k ? sb0 : 0));
         uint32_t v;
         if (md == S_CLEAR) v = 0;
         else if (md == S_SET) v = lanes;
         else if (md == S_PATTERN) {
-            uint32_t P = reinterpret_cast<const uint32_t *>(sec)[0];
-            uint32_t fl = (reinterpret_cast<const uint32_t *>(sec)[1 + g / 32] >> (g % 32)) & 1u;
+            uint32_t P = __ldg(sec);
+            uint32_t fl = (__ldg(sec + 1 + g / 32) >> (g % 32)) & 1u;
             v = fl ? ~P : P;
-        } else v = reinterpret_cast<const uint32_t *>(sec)[g];
+        } else v = __ldg(sec + g);
         sc.sw[t] = v;
         uint32_t w = b[sb0 + sb1 + t];
         sc.wd[t] = w;
         sc.nw[t] = ((uint32_t)L * w + 31u) / 32u;
     }
     __syncthreads();
-    scan_words_warp0(sc, 2 * G);
-    if (tid == 0) {
-        int bd = 0;
-        for (int t = 0; t < 2 * G; ++t) bd |= sc.wd[t] > 64;
-        uint32_t doff = (sb0 + sb1 + 2u * G + 3u) & ~3u;
-        sc.data_off = doff;
-        if ((unsigned long long)doff + 4ull * sc.wtotal > body) bd = 1;
-        sc.bad = bd;
+    if (warp == 0) {
+        uint32_t tot = warp_scan_words(sc.nw, sc.woff, 2 * G);
+        uint32_t wmax = 0;
+        for (int t = lane; t < 2 * G; t += 32) wmax = max(wmax, sc.wd[t]);
+        wmax = __reduce_max_sync(FULL, wmax);
+        if (lane == 0) {
+            uint32_t doff = (sb0 + sb1 + 2u * G + 3u) & ~3u;
+            sc.data_off = doff;
+            sc.bad = wmax > 64 || (unsigned long long)doff + 4ull * tot > body;
+        }
     }
     __syncthreads();
     if (sc.bad) {
@@ -396,38 +429,44 @@ __device__ int decode_tile(const uint8_t *src, int c, double *re, double *im, Sc
         unsigned long long z = 0;
         if (lane < L && w) {
             uint32_t bo = (uint32_t)lane * w, j0 = bo >> 5, sh = bo & 31u;
-            uint32_t w0 = base[j0];
-            uint32_t w1 = j0 + 1 < nwd ? base[j0 + 1] : 0u;
-            uint32_t w2 = j0 + 2 < nwd ? base[j0 + 2] : 0u;
+            uint32_t w0 = __ldg(base + j0);
+            uint32_t w1 = j0 + 1 < nwd ? __ldg(base + j0 + 1) : 0u;
+            uint32_t w2 = j0 + 2 < nwd ? __ldg(base + j0 + 2) : 0u;
             unsigned long long lo = (unsigned long long)w0 | ((unsigned long long)w1 << 32);
             unsigned long long v = sh ? ((lo >> sh) | ((unsigned long long)w2 << (64 - sh))) : lo;
             z = w == 64 ? v : (v & ((1ull << w) - 1ull));
         }
         unsigned long long r = unzigzag(z);
-        if (g == 0 && lane == 0) r = 0;
-        if (lane >= L) r = 0;
-        unsigned long long inc = r;
+        if ((g == 0 && lane == 0) || lane >= L) r = 0;
+        long long inc;
+        if (w <= 27) {                      // 32 partial sums of |r| < 2^26 fit in int32
+            int v32 = (int)(long long)r;
+            for (int d = 1; d < 32; d <<= 1) {
+                int o = __shfl_up_sync(FULL, v32, d);
+                if (lane >= d) v32 += o;
+            }
+            inc = v32;
+        } else {
+            unsigned long long u = r;
+            for (int d = 1; d < 32; d <<= 1) {
+                unsigned long long o = shfl_up64(u, d);
+                if (lane >= d) u += o;
+            }
+            inc = (long long)u;
+        }
+        if (lane < L) (k ? imI : reI)[g * 32 + lane] = inc;
+        if (lane == L - 1) sc.gtot[t] = inc;
+    }
+    __syncthreads();
+    if (warp < 2) {               // warp k: exclusive prefix of the group sums (G <= 32)
+        int k = warp;
+        unsigned long long v = lane < G ? (unsigned long long)sc.gtot[k * G + lane] : 0ull;
+        unsigned long long inc = v;
         for (int d = 1; d < 32; d <<= 1) {
             unsigned long long o = shfl_up64(inc, d);
             if (lane >= d) inc += o;
         }
-        if (lane < L) (k ? imI : reI)[g * 32 + lane] = (long long)inc;
-        if (lane == L - 1) sc.gtot[t] = (long long)inc;
-    }
-    __syncthreads();
-    if (warp < 2) {               // warp k scans the group sums of component k
-        int k = warp;
-        unsigned long long carry = 0;
-        for (int base = 0; base < G; base += 32) {
-            unsigned long long v = base + lane < G ? (unsigned long long)sc.gtot[k * G + base + lane] : 0ull;
-            unsigned long long inc = v;
-            for (int d = 1; d < 32; d <<= 1) {
-                unsigned long long o = shfl_up64(inc, d);
-                if (lane >= d) inc += o;
-            }
-            if (base + lane < G) sc.gpre[k * G + base + lane] = (long long)(carry + inc - v);
-            carry += shfl64(inc, 31);
-        }
+        if (lane < G) sc.gpre[k * G + lane] = (long long)(inc - v);
     }
     __syncthreads();
     for (int i = tid; i < N; i += THREADS) {
@@ -435,8 +474,10 @@ __device__ int decode_tile(const uint8_t *src, int c, double *re, double *im, Sc
         unsigned long long q0 = a0 + (unsigned long long)sc.gpre[g] + (unsigned long long)reI[i];
         unsigned long long q1 = a1 + (unsigned long long)sc.gpre[G + g] + (unsigned long long)imI[i];
         unsigned long long s0 = (sc.sw[g] >> l) & 1u, s1 = (sc.sw[G + g] >> l) & 1u;
-        re[i] = bitsd((q0 << s) | (s0 << 63));
-        im[i] = bitsd((q1 << s) | (s1 << 63));
+        double v0 = bitsd((q0 << s) | (s0 << 63)), v1 = bitsd((q1 << s) | (s1 << 63));
+        if (scale) { v0 = __dmul_rn(v0, alpha); v1 = __dmul_rn(v1, alpha); }
+        re[i] = v0;
+        im[i] = v1;
     }
     __syncthreads();
     return 0;
@@ -448,159 +489,161 @@ struct EncodeOut {
     bool ok;
 };
 
-// Quantised code of component value i (lane context) for comp k
-__device__ __forceinline__ unsigned long long code_of(const double *v, int i, int s) {
-    return quant(dbits(v[i]) & MAG, s);
+// magnitude bits of value i and of its predecessor in the stream (lane view
+// of group g; lanes >= L get zeros)
+__device__ __forceinline__ void lane_bits(const double *v, int g, int lane, int L,
+                                          unsigned long long &B, unsigned long long &Bp,
+                                          unsigned long long &sg) {
+    unsigned long long u = lane < L ? dbits(v[g * 32 + lane]) : 0ull;
+    B = u & MAG;
+    sg = u >> 63;
+    Bp = shfl_up64(B, 1);
+    if (lane == 0) Bp = g > 0 ? (dbits(v[g * 32 - 1]) & MAG) : B;
 }
 
-// z of this lane for task (k, g) at shift s; lanes >= L give 0
-__device__ __forceinline__ unsigned long long lane_z(const double *v, int g, int lane, int L, int s) {
-    int i = g * 32 + lane;
-    unsigned long long q = lane < L ? code_of(v, i, s) : 0ull;
-    unsigned long long qp = shfl_up64(q, 1);
-    if (lane == 0) qp = g > 0 ? code_of(v, i - 1, s) : q;
-    unsigned long long z = zigzag(q - qp);
+__device__ __forceinline__ unsigned long long lane_z(unsigned long long B, unsigned long long Bp,
+                                                     int s, int lane, int L) {
+    unsigned long long z = zigzag(quant(B, s) - quant(Bp, s));
     return lane < L ? z : 0ull;
 }
 
 // Encode planar re/im (2^c values each) of tile `tile` into the output
-// arena with Algorithm 2's ladder.  CTA-wide.  Writes the stream, its
-// offset in out_table, its norm partial, and adds to the running norm.
+// arena with Algorithm 2's ladder (all levels sized in one pass).  CTA-wide.
+// Writes the stream, its table entry and norm partial, adds to the
+// running norm.  stage: 64 words of shared memory per warp.
 __device__ EncodeOut encode_tile(const double *re, const double *im, const CodecCfg &cc,
                                  unsigned long long tile, uint8_t *out_arena,
                                  unsigned long long out_cap, unsigned long long *out_table,
                                  unsigned long long *part, DevScalars *scal,
-                                 unsigned sweep_id, Scratch &sc) {
+                                 unsigned sweep_id, Scratch &sc, uint32_t *stage) {
     const int c = cc.c, N = 1 << c;
     const int G = N >= 32 ? N / 32 : 1;
     const int L = N >= 32 ? 32 : N;
+    const int T = 2 * G;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lanes = L == 32 ? FULL : ((1u << L) - 1u);
+    uint32_t *wstage = stage + 64 * warp;
 
-    // A: value classes
+    // 1: sign words, value classes, widths of every level
+    if (tid < MAX_LEVELS) { sc.lvl_words[tid] = 0; sc.lvl_nonzero[tid] = 0; }
+    __syncthreads();
     int nonfin = 0, inel = 0;
-    for (int i = tid; i < N; i += THREADS) {
-        unsigned long long B0 = dbits(re[i]) & MAG, B1 = dbits(im[i]) & MAG;
-        nonfin |= (B0 >= INF_BITS) | (B1 >= INF_BITS);
-        inel |= (B0 != 0 && (B0 < MIN_NORMAL || B0 >= LOSSY_LIMIT)) |
-                (B1 != 0 && (B1 < MIN_NORMAL || B1 >= LOSSY_LIMIT));
+    if (!cc.force_raw) {
+        for (int t = warp; t < T; t += NWARPS) {
+            int k = t / G, g = t % G;
+            unsigned long long B, Bp, sg;
+            lane_bits(k ? im : re, g, lane, L, B, Bp, sg);
+            nonfin |= lane < L && B >= INF_BITS;
+            inel |= lane < L && B != 0 && (B < MIN_NORMAL || B >= LOSSY_LIMIT);
+            uint32_t word = __ballot_sync(FULL, lane < L && sg);
+            if (lane == 0) sc.sw[t] = word;
+            for (int lv = 0; lv < cc.nlev; ++lv) {
+                unsigned long long oz = warp_or64(lane_z(B, Bp, cc.shifts[lv], lane, L));
+                if (lane == 0) {
+                    uint32_t w = oz ? (uint32_t)bitlen64(oz) : 0u;
+                    sc.wl[lv][t] = (uint8_t)w;
+                    atomicAdd(&sc.lvl_words[lv], ((uint32_t)L * w + 31u) / 32u);
+                    if (oz) sc.lvl_nonzero[lv] = 1u;
+                }
+            }
+        }
     }
     nonfin = __syncthreads_or(nonfin);
     inel = __syncthreads_or(inel);
     const bool raw_only = cc.force_raw || nonfin;
-
-    // B: sign words
-    if (!raw_only) {
-        for (int t = warp; t < 2 * G; t += NWARPS) {
-            int k = t / G, g = t % G;
-            const double *v = k ? im : re;
-            bool sg = lane < L && (dbits(v[g * 32 + lane]) >> 63);
-            uint32_t word = __ballot_sync(FULL, sg);
-            if (lane == 0) sc.sw[t] = word;
-        }
+    if (!raw_only && inel) {          // values outside the lossy range: shift 0 at every level
         if (tid < MAX_LEVELS) { sc.lvl_words[tid] = 0; sc.lvl_nonzero[tid] = 0; }
-    }
-    __syncthreads();
-    // C: sign modes (warp k, lane g; G <= 32)
-    if (!raw_only && warp < 2) {
-        int k = warp;
-        uint32_t v = lane < G ? sc.sw[k * G + lane] : 0u;
-        bool any1 = __any_sync(FULL, lane < G && v != 0u);
-        bool allset = __all_sync(FULL, lane >= G || v == lanes);
-        uint32_t P = __shfl_sync(FULL, v, 0);
-        bool pat = G >= 2 && __all_sync(FULL, lane >= G || v == P || v == ~P);
-        if (lane == 0) sc.smode[k] = !any1 ? S_CLEAR : (allset ? S_SET : (pat ? S_PATTERN : S_WORDS));
-    }
-    // D: data words per level
-    if (!raw_only) {
-        for (int t = warp; t < 2 * G; t += NWARPS) {
+        __syncthreads();
+        for (int t = warp; t < T; t += NWARPS) {
             int k = t / G, g = t % G;
-            const double *v = k ? im : re;
-            for (int lv = 0; lv < cc.nlev; ++lv) {
-                int s = inel ? 0 : cc.shifts[lv];
-                unsigned long long z = lane_z(v, g, lane, L, s);
-                unsigned long long oz = warp_or64(z);
-                if (lane == 0) {
-                    uint32_t w = oz ? (uint32_t)bitlen64(oz) : 0u;
-                    atomicAdd(&sc.lvl_words[lv], ((uint32_t)L * w + 31u) / 32u);
-                    if (oz) atomicOr(&sc.lvl_nonzero[lv], 1u);
-                }
-            }
-        }
-    }
-    __syncthreads();
-    // E: ladder decision (first level within max_bytes, else the last)
-    if (tid == 0) {
-        const uint32_t raw_body = 16u * (uint32_t)N;
-        if (raw_only) {
-            sc.mode = M_RAW; sc.s = 0; sc.level = 0; sc.body = raw_body;
-        } else {
-            uint32_t meta = sign_bytes(sc.smode[0], G) + sign_bytes(sc.smode[1], G);
-            uint32_t wb = (2u * G + 3u) & ~3u;
-            int pick = cc.nlev - 1;
-            int pmode = 0;
-            uint32_t pbody = 0;
-            for (int lv = 0; lv < cc.nlev; ++lv) {
-                int md;
-                uint32_t bd;
-                if (!sc.lvl_nonzero[lv] && sc.smode[0] <= S_SET && sc.smode[1] <= S_SET) {
-                    md = M_CONST; bd = 0;
-                } else {
-                    uint32_t pb = (meta + wb + 4u * sc.lvl_words[lv] + 15u) & ~15u;
-                    if (pb < raw_body) { md = M_PACKED; bd = pb; }
-                    else { md = M_RAW; bd = raw_body; }
-                }
-                pick = lv; pmode = md; pbody = bd;
-                if ((unsigned long long)(HDR + bd) <= cc.max_bytes) break;
-            }
-            sc.level = pick;
-            sc.mode = pmode;
-            sc.body = pbody;
-            sc.s = pmode == M_RAW ? 0 : (inel ? 0 : cc.shifts[pick]);
-        }
-        sc.size = HDR + sc.body;
-        sc.flag_nonfinite = nonfin;
-    }
-    __syncthreads();
-    const int mode = sc.mode, s = sc.s;
-    // F: widths at the chosen level
-    if (mode == M_PACKED) {
-        for (int t = warp; t < 2 * G; t += NWARPS) {
-            int k = t / G, g = t % G;
-            unsigned long long z = lane_z(k ? im : re, g, lane, L, s);
-            unsigned long long oz = warp_or64(z);
+            unsigned long long B, Bp, sg;
+            lane_bits(k ? im : re, g, lane, L, B, Bp, sg);
+            unsigned long long oz = warp_or64(lane_z(B, Bp, 0, lane, L));
             if (lane == 0) {
                 uint32_t w = oz ? (uint32_t)bitlen64(oz) : 0u;
-                sc.wd[t] = w;
-                sc.nw[t] = ((uint32_t)L * w + 31u) / 32u;
+                for (int lv = 0; lv < cc.nlev; ++lv) {
+                    sc.wl[lv][t] = (uint8_t)w;
+                    atomicAdd(&sc.lvl_words[lv], ((uint32_t)L * w + 31u) / 32u);
+                    if (oz) sc.lvl_nonzero[lv] = 1u;
+                }
             }
         }
+        __syncthreads();
     }
-    __syncthreads();
-    // G: word offsets, anchors, allocation
-    if (mode == M_PACKED) scan_words_warp0(sc, 2 * G);
-    if (tid == 32) {
-        unsigned long long off = atomicAdd(&scal->bump, (unsigned long long)sc.size);
-        bool ok = off + sc.size <= out_cap;
-        if (!ok) {
-            atomicOr(&scal->err, ERR_OVERFLOW);
-            atomicCAS(&scal->err_sweep, 0u, sweep_id + 1u);
+
+    // 2: sign modes, ladder decision, word offsets, allocation (warp 0)
+    if (warp == 0) {
+        if (!raw_only) {
+            for (int k = 0; k < 2; ++k) {
+                uint32_t v = lane < G ? sc.sw[k * G + lane] : 0u;
+                bool any1 = __any_sync(FULL, lane < G && v != 0u);
+                bool allset = __all_sync(FULL, lane >= G || v == lanes);
+                uint32_t P = __shfl_sync(FULL, v, 0);
+                bool pat = G >= 2 && __all_sync(FULL, lane >= G || v == P || v == ~P);
+                if (lane == 0) sc.smode[k] = !any1 ? S_CLEAR : (allset ? S_SET : (pat ? S_PATTERN : S_WORDS));
+            }
         }
-        sc.off = off;
-        sc.ok = ok;
-        if (mode != M_RAW) {
-            sc.anchor[0] = quant(dbits(re[0]) & MAG, s);
-            sc.anchor[1] = quant(dbits(im[0]) & MAG, s);
-        } else {
-            sc.anchor[0] = sc.anchor[1] = 0;
+        __syncwarp();
+        if (lane == 0) {
+            const uint32_t raw_body = 16u * (uint32_t)N;
+            if (raw_only) {
+                sc.mode = M_RAW; sc.s = 0; sc.level = 0; sc.body = raw_body;
+            } else {
+                uint32_t meta = sign_bytes(sc.smode[0], G) + sign_bytes(sc.smode[1], G);
+                uint32_t wb = (2u * G + 3u) & ~3u;
+                int pick = cc.nlev - 1, pmode = 0;
+                uint32_t pbody = 0;
+                for (int lv = 0; lv < cc.nlev; ++lv) {
+                    int md;
+                    uint32_t bd;
+                    if (!sc.lvl_nonzero[lv] && sc.smode[0] <= S_SET && sc.smode[1] <= S_SET) {
+                        md = M_CONST; bd = 0;
+                    } else {
+                        uint32_t pb = (meta + wb + 4u * sc.lvl_words[lv] + 15u) & ~15u;
+                        if (pb < raw_body) { md = M_PACKED; bd = pb; }
+                        else { md = M_RAW; bd = raw_body; }
+                    }
+                    pick = lv; pmode = md; pbody = bd;
+                    if ((unsigned long long)(HDR + bd) <= cc.max_bytes) break;
+                }
+                sc.level = pick;
+                sc.mode = pmode;
+                sc.body = pbody;
+                sc.s = pmode == M_RAW ? 0 : (inel ? 0 : cc.shifts[pick]);
+            }
+            sc.size = HDR + sc.body;
         }
-        if (nonfin) atomicOr(&scal->err, ERR_NONFINITE);
+        __syncwarp();
+        if (sc.mode == M_PACKED) {
+            for (int t = lane; t < T; t += 32) sc.nw[t] = ((uint32_t)L * sc.wl[sc.level][t] + 31u) / 32u;
+            __syncwarp();
+            sc.wtotal = warp_scan_words(sc.nw, sc.woff, T);
+        }
+        if (lane == 0) {
+            unsigned long long off = atomicAdd(&scal->bump, (unsigned long long)sc.size);
+            bool ok = off + sc.size <= out_cap;
+            if (!ok) {
+                atomicOr(&scal->err, ERR_OVERFLOW);
+                atomicCAS(&scal->err_sweep, 0u, sweep_id + 1u);
+            }
+            sc.off = off;
+            sc.ok = ok;
+            if (sc.mode != M_RAW) {
+                sc.anchor[0] = quant(dbits(re[0]) & MAG, sc.s);
+                sc.anchor[1] = quant(dbits(im[0]) & MAG, sc.s);
+            } else {
+                sc.anchor[0] = sc.anchor[1] = 0;
+            }
+            if (nonfin) atomicOr(&scal->err, ERR_NONFINITE);
+        }
     }
     __syncthreads();
     EncodeOut res{sc.off, sc.ok != 0};
     if (!res.ok) return res;
+    const int mode = sc.mode, s = sc.s;
     uint8_t *dst = out_arena + res.off;
-    // H: header
+
+    // 3: write the stream and take the norm of what the decoder will return
     if (tid < 8) {
         uint32_t v = 0;
         switch (tid) {
@@ -620,13 +663,11 @@ __device__ EncodeOut encode_tile(const double *re, const double *im, const Codec
         reinterpret_cast<uint32_t *>(dst)[tid] = v;
     }
     uint8_t *b = dst + HDR;
-    if (mode == M_RAW) {
-        double2 *o = reinterpret_cast<double2 *>(b);
-        for (int i = tid; i < N; i += THREADS) o[i] = make_double2(re[i], im[i]);
-    } else if (mode == M_PACKED) {
+    unsigned long long nlo = 0, nhi = 0;
+    unsigned rng = 0;
+    if (mode == M_PACKED) {
         const int sm0 = sc.smode[0], sm1 = sc.smode[1];
         const uint32_t sb0 = sign_bytes(sm0, G), sb1 = sign_bytes(sm1, G);
-        // sign sections (warp k)
         if (warp < 2) {
             int k = warp, md = k ? sm1 : sm0;
             uint32_t *sec = reinterpret_cast<uint32_t *>(b + (k ? sb0 : 0));
@@ -639,62 +680,60 @@ __device__ EncodeOut encode_tile(const double *re, const double *im, const Codec
                 if (lane < G) sec[lane] = v;
             }
         }
-        // width bytes and their padding
         const uint32_t wb = (2u * G + 3u) & ~3u;
-        for (int t = tid; t < (int)wb; t += THREADS)
-            b[sb0 + sb1 + t] = t < 2 * G ? (uint8_t)sc.wd[t] : (uint8_t)0;
+        const uint8_t *wsel = sc.wl[sc.level];
+        for (int t = tid; t < (int)wb; t += THREADS) b[sb0 + sb1 + t] = t < T ? wsel[t] : (uint8_t)0;
         const uint32_t doff = sb0 + sb1 + wb;
         uint32_t *data = reinterpret_cast<uint32_t *>(b + doff);
-        // data words: word j of a group gathers the lanes whose bits it holds
-        for (int t = warp; t < 2 * G; t += NWARPS) {
+        for (int t = warp; t < T; t += NWARPS) {
             int k = t / G, g = t % G;
-            uint32_t w = sc.wd[t], nwd = sc.nw[t];
-            if (w == 0) continue;
-            unsigned long long z = lane_z(k ? im : re, g, lane, L, s);
-            uint32_t *gd = data + sc.woff[t];
-            const int span = (int)((32u + w - 1u) / w) + 1;
-            for (int rnd = 0; rnd < 2; ++rnd) {
-                int j = lane + 32 * rnd;
-                if (rnd == 1 && nwd <= 32) break;        // uniform across the warp
-                int a = (32 * j) / (int)w;
-                int bl = (32 * j + 31) / (int)w;
-                if (bl > L - 1) bl = L - 1;
-                uint32_t acc = 0;
-                for (int it = 0; it < span; ++it) {
-                    int src = a + it;
-                    unsigned long long v = shfl64(z, src & 31);
-                    if (src <= bl) {
-                        int o = src * (int)w - 32 * j;
-                        if (o >= 0) acc |= (uint32_t)(v << o);
-                        else acc |= (uint32_t)(v >> (-o));
-                    }
-                }
-                if ((uint32_t)j < nwd) gd[j] = acc;
+            unsigned long long B, Bp, sg;
+            lane_bits(k ? im : re, g, lane, L, B, Bp, sg);
+            unsigned long long q = quant(B, s);
+            if (lane < L) {
+                unsigned long long l0, h0;
+                sq_units(q << s, l0, h0, rng);
+                add128(nlo, nhi, l0, h0);
             }
+            uint32_t w = wsel[t];
+            if (w == 0) continue;
+            unsigned long long z = lane < L ? zigzag(q - quant(Bp, s)) : 0ull;
+            const uint32_t nwd = sc.nw[t];
+            wstage[lane] = 0u;
+            wstage[lane + 32] = 0u;
+            __syncwarp();
+            if (lane < L) {
+                uint32_t bo = (uint32_t)lane * w, j0 = bo >> 5, sh = bo & 31u;
+                atomicOr(&wstage[j0], (uint32_t)(z << sh));
+                if (sh + w > 32) atomicOr(&wstage[j0 + 1], (uint32_t)(z >> (32 - sh)));
+                if (sh + w > 64) atomicOr(&wstage[j0 + 2], (uint32_t)(z >> (64 - sh)));
+            }
+            __syncwarp();
+            uint32_t *gd = data + sc.woff[t];
+            if ((uint32_t)lane < nwd) gd[lane] = wstage[lane];
+            if ((uint32_t)lane + 32 < nwd) gd[lane + 32] = wstage[lane + 32];
+            __syncwarp();
         }
-        // zero tail up to the 16-byte boundary
         const uint32_t dend = doff + 4u * sc.wtotal;
         for (uint32_t p = dend + tid; p < sc.body; p += THREADS) b[p] = 0;
-    }
-    // I: norm of the stored (reconstructed) values
-    unsigned long long lo = 0, hi = 0;
-    unsigned rng = 0;
-    for (int i = tid; i < N; i += THREADS) {
-        unsigned long long u0 = dbits(re[i]), u1 = dbits(im[i]);
-        if (mode != M_RAW) {
-            u0 = (quant(u0 & MAG, s) << s) | (u0 & ~MAG);
-            u1 = (quant(u1 & MAG, s) << s) | (u1 & ~MAG);
+    } else {
+        if (mode == M_RAW) {
+            double2 *o = reinterpret_cast<double2 *>(b);
+            for (int i = tid; i < N; i += THREADS) o[i] = make_double2(re[i], im[i]);
         }
-        unsigned long long l0, h0, l1, h1;
-        sq_units(u0, l0, h0, rng);
-        sq_units(u1, l1, h1, rng);
-        add128(lo, hi, l0, h0);
-        add128(lo, hi, l1, h1);
+        for (int i = tid; i < N; i += THREADS) {
+            unsigned long long u0 = dbits(re[i]) & MAG, u1 = dbits(im[i]) & MAG;
+            if (mode == M_CONST) { u0 = quant(u0, s) << s; u1 = quant(u1, s) << s; }
+            unsigned long long l0, h0, l1, h1;
+            sq_units(u0, l0, h0, rng);
+            sq_units(u1, l1, h1, rng);
+            add128(nlo, nhi, l0, h0);
+            add128(nlo, nhi, l1, h1);
+        }
     }
+    warp_sum128(nlo, nhi);
+    if (lane == 0) { sc.red_lo[warp] = nlo; sc.red_hi[warp] = nhi; }
     rng = __syncthreads_or(rng);
-    warp_sum128(lo, hi);
-    if (lane == 0) { sc.red_lo[warp] = lo; sc.red_hi[warp] = hi; }
-    __syncthreads();
     if (tid == 0) {
         unsigned long long tl = 0, th = 0;
         for (int w = 0; w < NWARPS; ++w) add128(tl, th, sc.red_lo[w], sc.red_hi[w]);
@@ -751,33 +790,42 @@ __device__ __forceinline__ unsigned long long expand_item(unsigned long long ite
     return v;
 }
 
-// One sweep of Algorithm 2 over all items: decompress, normalize, apply
-// the gate run, compress with the ladder.  Persistent CTAs loop over items.
-__global__ void __launch_bounds__(THREADS) sweep_kernel(SweepParams p) {
+// One sweep of Algorithm 2 over all items: decompress (with normalize),
+// apply the gate run, compress with the ladder.  Persistent CTAs loop over
+// items.
+__global__ void __launch_bounds__(THREADS, 3) sweep_kernel(SweepParams p) {
     extern __shared__ double smem[];
     __shared__ Scratch sc;
-    __shared__ int s_touch;
-    if (threadIdx.x == 0) s_touch = *((volatile unsigned *)&p.scal->err) != 0u;
+    __shared__ SGate sg[MAX_SWEEP_GATES];
+    __shared__ uint32_t stage[64 * NWARPS];
+    __shared__ unsigned s_act[2];
+    __shared__ int s_flag;
+    if (threadIdx.x == 0) s_flag = *((volatile unsigned *)&p.scal->err) != 0u;
+    {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(p.sgates);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(sg);
+        const int words = p.ngates * (int)(sizeof(SGate) / 4);
+        for (int i = threadIdx.x; i < words; i += THREADS) dst[i] = src[i];
+    }
     __syncthreads();
-    if (s_touch) return;                      // an earlier pass failed: leave the state
-    __syncthreads();
+    if (s_flag) return;                       // an earlier pass failed: leave the state
     const int c = p.cc.c, N = 1 << c, mb = c + p.h;
     double *re = smem, *im = smem + (1 << mb);
     const double alpha = p.use_alpha ? p.scal->alpha : 1.0;
+    const bool scale = alpha != 1.0;           // one compare per thread and launch
     int Hbits[2] = {p.h > 0 ? p.H[0] - c : 0, p.h > 1 ? p.H[1] - c : 0};
     for (unsigned long long item = blockIdx.x; item < p.nitems; item += gridDim.x) {
         const unsigned long long T = expand_item(item, p.h, Hbits);
         const unsigned long long fixed = T << c;
-        if (threadIdx.x == 0) {
-            int touch = alpha != 1.0;
-            for (int gi = 0; gi < p.ngates && !touch; ++gi)
-                if (gate_touches(p.gates[gi], fixed)) touch = 1;
-            s_touch = touch;
+        if (threadIdx.x < 64) {
+            bool a = (int)threadIdx.x < p.ngates && gate_active(sg[threadIdx.x], fixed);
+            unsigned bal = __ballot_sync(FULL, a);
+            if ((threadIdx.x & 31) == 0) s_act[threadIdx.x >> 5] = bal;
         }
         __syncthreads();
-        const int touched = s_touch;
+        const unsigned long long active = (unsigned long long)s_act[0] | ((unsigned long long)s_act[1] << 32);
         __syncthreads();
-        if (!touched) {
+        if (!active && !scale) {
             for (int j = 0; j < (1 << p.h); ++j) {
                 unsigned long long Tj = T;
                 for (int i = 0; i < p.h; ++i)
@@ -793,23 +841,16 @@ __global__ void __launch_bounds__(THREADS) sweep_kernel(SweepParams p) {
             unsigned long long Tj = T;
             for (int i = 0; i < p.h; ++i)
                 if ((j >> i) & 1) Tj |= 1ull << Hbits[i];
-            bad |= decode_tile(p.in_arena + p.in_table[Tj], c, re + j * N, im + j * N, sc);
+            bad |= decode_tile(p.in_arena + p.in_table[Tj], c, re + j * N, im + j * N, sc, alpha, scale);
         }
         if (bad && threadIdx.x == 0) atomicOr(&p.scal->err, ERR_FORMAT);
-        if (alpha != 1.0) {
-            for (int i = threadIdx.x; i < (1 << mb); i += THREADS) {
-                re[i] = __dmul_rn(re[i], alpha);
-                im[i] = __dmul_rn(im[i], alpha);
-            }
-            __syncthreads();
-        }
-        apply_gates(re, im, mb, p.gates, p.ngates, fixed);
+        apply_gates(re, im, mb, sg, p.gates, p.ngates, active, fixed);
         for (int j = 0; j < (1 << p.h); ++j) {
             unsigned long long Tj = T;
             for (int i = 0; i < p.h; ++i)
                 if ((j >> i) & 1) Tj |= 1ull << Hbits[i];
             encode_tile(re + j * N, im + j * N, p.cc, Tj, p.out_arena, p.out_cap, p.out_table,
-                        p.part, p.scal, p.sweep_id, sc);
+                        p.part, p.scal, p.sweep_id, sc, stage);
         }
         if (threadIdx.x == 0) atomicAdd(&p.scal->items_done, 1ull);
     }
@@ -843,6 +884,7 @@ __global__ void __launch_bounds__(THREADS) init_kernel(const double2 *dense, uns
                                                      unsigned long long *part, DevScalars *scal) {
     extern __shared__ double smem[];
     __shared__ Scratch sc;
+    __shared__ uint32_t stage[64 * NWARPS];
     const int c = cc.c, N = 1 << c;
     double *re = smem, *im = smem + N;
     for (unsigned long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -892,7 +934,7 @@ __global__ void __launch_bounds__(THREADS) init_kernel(const double2 *dense, uns
             }
         }
         __syncthreads();
-        encode_tile(re, im, cc, t, out_arena, out_cap, out_table, part, scal, 0u, sc);
+        encode_tile(re, im, cc, t, out_arena, out_cap, out_table, part, scal, 0u, sc, stage);
     }
 }
 
@@ -960,7 +1002,7 @@ __global__ void __launch_bounds__(THREADS) validate_kernel(const uint8_t *buf, c
         int fail = 0;
         if (sizes[i] < HDR || (sizes[i] & 15ull) || HDR + (unsigned long long)h[1] != sizes[i]) fail = 1;
         fail = __syncthreads_or(fail);
-        if (!fail) fail = decode_tile(src, c, re, im, sc);
+        if (!fail) fail = decode_tile(src, c, re, im, sc, 1.0, false);
         unsigned long long lo = 0, hi = 0;
         unsigned rng = 0;
         if (!fail) {
@@ -1016,7 +1058,7 @@ __global__ void __launch_bounds__(THREADS) amplitudes_kernel(const uint8_t *aren
     double *re = smem, *im = smem + N;
     unsigned long long t0 = start >> c, t1 = (start + count - 1) >> c;
     for (unsigned long long t = t0 + blockIdx.x; t <= t1; t += gridDim.x) {
-        if (decode_tile(arena + table[t], c, re, im, sc) && threadIdx.x == 0)
+        if (decode_tile(arena + table[t], c, re, im, sc, 1.0, false) && threadIdx.x == 0)
             atomicOr(&scal->err, ERR_FORMAT);
         for (int i = threadIdx.x; i < N; i += THREADS) {
             unsigned long long gidx = (t << c) | (unsigned long long)i;
@@ -1039,7 +1081,7 @@ __global__ void __launch_bounds__(THREADS) probs_kernel(const uint8_t *arena, co
     if (threadIdx.x < nq) sq[threadIdx.x] = qs[threadIdx.x];
     __syncthreads();
     for (unsigned long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        if (decode_tile(arena + table[t], c, re, im, sc) && threadIdx.x == 0)
+        if (decode_tile(arena + table[t], c, re, im, sc, 1.0, false) && threadIdx.x == 0)
             atomicOr(&scal->err, ERR_FORMAT);
         for (int i = threadIdx.x; i < N; i += THREADS) {
             unsigned long long gidx = (t << c) | (unsigned long long)i;
@@ -1067,8 +1109,8 @@ __global__ void __launch_bounds__(THREADS) fidelity_kernel(const uint8_t *arena,
     const int N = 1 << c;
     double *re = smem, *im = smem + N, *rre = smem + 2 * N, *rim = smem + 3 * N;
     for (unsigned long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        int bad = decode_tile(arena + table[t], c, re, im, sc);
-        if (rs.kind == 0) bad |= decode_tile(rs.o_arena + rs.o_table[t], c, rre, rim, sc);
+        int bad = decode_tile(arena + table[t], c, re, im, sc, 1.0, false);
+        if (rs.kind == 0) bad |= decode_tile(rs.o_arena + rs.o_table[t], c, rre, rim, sc, 1.0, false);
         if (bad && threadIdx.x == 0) atomicOr(&scal->err, ERR_FORMAT);
         Acc4 acc = make_acc4(0, 0, 0, 0);
         // thread-contiguous chunks, then a pairwise tree over threads

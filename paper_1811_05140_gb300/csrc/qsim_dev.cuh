@@ -46,6 +46,36 @@ struct DGate {
     int t[2];                       // global qubit of target i
 };
 
+// A gate as staged in shared memory for one sweep (compact form).
+struct SGate {
+    double d[8];                    // diagonal gates: entry r (re, im), r < 2^k
+    unsigned long long cls;         // entry classes, 3 bits each (see entry classes below)
+    unsigned long long fcm, fcv;    // controls on fixed qubits (global bits)
+    uint32_t lcm, lcv;              // controls on buffer bits
+    uint8_t kind;                   // 0 diagonal, 1 one-target, 2 two-target (non-diagonal)
+    uint8_t k;                      // number of targets
+    int8_t p0, p1;                  // buffer bit of each target, -1 when fixed
+    uint8_t t0, t1;                 // global qubit of each target
+    uint8_t one_mask;               // diagonal: bit r set when entry r is exactly 1
+    uint8_t nins;                   // buffer bits pinned by targets and local controls
+    uint8_t ins[12];                // those bits, ascending
+};
+
+// Entry classes of a matrix entry u, decided on the host so that device
+// code never compares doubles (FP64 compares occupy the FP64 pipe):
+// diagonal gates use bits 3r of SGate::cls for entry (r, r); other gates
+// bits 3(r*dim + c) for entry (r, c).
+enum : unsigned {
+    EC_ZERO = 0,       // u == 0
+    EC_ONE = 1,        // u == 1 exactly
+    EC_MINUS_ONE = 2,  // u == -1 exactly
+    EC_REAL = 3,       // imaginary part 0
+    EC_IMAG = 4,       // real part 0
+    EC_GENERAL = 5
+};
+
+constexpr int MAX_SWEEP_GATES = 48;     // gates per sweep (depth limit; shared memory)
+
 // Codec configuration of a state.
 struct CodecCfg {
     int c;                          // tile_log2
@@ -63,7 +93,8 @@ struct SweepParams {
     unsigned long long out_cap;
     unsigned long long *part;       // per tile: sum of |a^|^2, 2 words
     DevScalars *scal;
-    const DGate *gates;
+    const DGate *gates;             // full matrices (non-diagonal gates)
+    const SGate *sgates;            // compact gates, staged in shared memory
     int ngates;
     int n, h;
     int H[2];                       // paired high qubits, ascending

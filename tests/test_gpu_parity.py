@@ -38,10 +38,10 @@ def oracle_cfg(codec, eps, c, aalc=None):
     raise ValueError(codec)
 
 
-def run_both(n, b, codec, eps, gates, x=0, hmax=2, depth=64, aalc=None):
+def run_both(n, b, codec, eps, gates, x=0, hmax=2, depth=48, aalc=None):
     c = min(b, n, 10)
     st = qsim.State(n, b, codec, eps)
-    if (hmax, depth) != (2, 64):
+    if (hmax, depth) != (2, 48):
         st.set_schedule(c, hmax, depth)
     if aalc:
         st.set_aalc(*aalc)
@@ -102,7 +102,7 @@ def test_grover_streams_and_closed_form():
     assert st.fidelity_grover(m, 3) > 0.9999
 
 
-@pytest.mark.parametrize("depth", [1, 3, 4096])
+@pytest.mark.parametrize("depth", [1, 3, 48])
 def test_fusion_depths(depth):
     n = 10
     gates = I.basis_gates(n, 0x2D3) + I.qft(n)
