@@ -338,6 +338,7 @@ __device__ int decode_tile(const uint8_t *src, int c, double *re, double *im, Sc
                            double alpha, bool scale) {
     const int N = 1 << c;
     const int G = N >= 32 ? N / 32 : 1;
+    const int lgG = c >= 5 ? c - 5 : 0;
     const int L = N >= 32 ? 32 : N;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid < 8) sc.hdr[tid] = __ldg(reinterpret_cast<const uint32_t *>(src) + tid);
@@ -385,7 +386,7 @@ __device__ int decode_tile(const uint8_t *src, int c, double *re, double *im, Sc
     const uint32_t sb0 = sign_bytes(sm0, G), sb1 = sign_bytes(sm1, G);
     const uint32_t lanes = L == 32 ? FULL : ((1u << L) - 1u);
     for (int t = tid; t < 2 * G; t += THREADS) {
-        int k = t / G, g = t % G;
+        int k = t >> lgG, g = t & (G - 1);
         int md = k ? sm1 : sm0;
         const uint32_t *sec = reinterpret_cast<const uint32_t *>(b + (k ? sb0 : 0));
         uint32_t v;
@@ -423,7 +424,7 @@ __device__ int decode_tile(const uint8_t *src, int c, double *re, double *im, Sc
     long long *reI = reinterpret_cast<long long *>(re);
     long long *imI = reinterpret_cast<long long *>(im);
     for (int t = warp; t < 2 * G; t += NWARPS) {
-        int k = t / G, g = t % G;
+        int k = t >> lgG, g = t & (G - 1);
         uint32_t w = sc.wd[t], nwd = sc.nw[t];
         const uint32_t *base = data + sc.woff[t];
         unsigned long long z = 0;
@@ -518,6 +519,7 @@ __device__ EncodeOut encode_tile(const double *re, const double *im, const Codec
                                  unsigned sweep_id, Scratch &sc, uint32_t *stage) {
     const int c = cc.c, N = 1 << c;
     const int G = N >= 32 ? N / 32 : 1;
+    const int lgG = c >= 5 ? c - 5 : 0;
     const int L = N >= 32 ? 32 : N;
     const int T = 2 * G;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -530,7 +532,7 @@ __device__ EncodeOut encode_tile(const double *re, const double *im, const Codec
     int nonfin = 0, inel = 0;
     if (!cc.force_raw) {
         for (int t = warp; t < T; t += NWARPS) {
-            int k = t / G, g = t % G;
+            int k = t >> lgG, g = t & (G - 1);
             unsigned long long B, Bp, sg;
             lane_bits(k ? im : re, g, lane, L, B, Bp, sg);
             nonfin |= lane < L && B >= INF_BITS;
@@ -555,7 +557,7 @@ __device__ EncodeOut encode_tile(const double *re, const double *im, const Codec
         if (tid < MAX_LEVELS) { sc.lvl_words[tid] = 0; sc.lvl_nonzero[tid] = 0; }
         __syncthreads();
         for (int t = warp; t < T; t += NWARPS) {
-            int k = t / G, g = t % G;
+            int k = t >> lgG, g = t & (G - 1);
             unsigned long long B, Bp, sg;
             lane_bits(k ? im : re, g, lane, L, B, Bp, sg);
             unsigned long long oz = warp_or64(lane_z(B, Bp, 0, lane, L));
@@ -686,7 +688,7 @@ __device__ EncodeOut encode_tile(const double *re, const double *im, const Codec
         const uint32_t doff = sb0 + sb1 + wb;
         uint32_t *data = reinterpret_cast<uint32_t *>(b + doff);
         for (int t = warp; t < T; t += NWARPS) {
-            int k = t / G, g = t % G;
+            int k = t >> lgG, g = t & (G - 1);
             unsigned long long B, Bp, sg;
             lane_bits(k ? im : re, g, lane, L, B, Bp, sg);
             unsigned long long q = quant(B, s);
@@ -779,15 +781,20 @@ __device__ void carry_tile(const uint8_t *in_arena, const unsigned long long *in
 }
 
 // ---------------------------------------------------------------- kernels
-__device__ __forceinline__ unsigned long long expand_item(unsigned long long item, int h,
-                                                           const int *Hbits) {
-    // insert zero bits at the tile-index positions of the paired qubits
+// tile index of an item: zero bits inserted at the tile-index positions
+// hb0 < hb1 of the paired qubits (h of them)
+__device__ __forceinline__ unsigned long long expand_item(unsigned long long item, int h, int hb0,
+                                                           int hb1) {
     unsigned long long v = item;
-    for (int i = 0; i < h; ++i) {
-        unsigned long long lowm = (1ull << Hbits[i]) - 1ull;
-        v = ((v & ~lowm) << 1) | (v & lowm);
-    }
+    if (h > 0) { unsigned long long m = (1ull << hb0) - 1ull; v = ((v & ~m) << 1) | (v & m); }
+    if (h > 1) { unsigned long long m = (1ull << hb1) - 1ull; v = ((v & ~m) << 1) | (v & m); }
     return v;
+}
+
+// tile of member j of the item whose first tile is T
+__device__ __forceinline__ unsigned long long member_tile(unsigned long long T, int j, int hb0,
+                                                          int hb1) {
+    return T | ((unsigned long long)(j & 1) << hb0) | ((unsigned long long)((j >> 1) & 1) << hb1);
 }
 
 // One sweep of Algorithm 2 over all items: decompress (with normalize),
@@ -813,9 +820,9 @@ __global__ void __launch_bounds__(THREADS, 3) sweep_kernel(SweepParams p) {
     double *re = smem, *im = smem + (1 << mb);
     const double alpha = p.use_alpha ? p.scal->alpha : 1.0;
     const bool scale = alpha != 1.0;           // one compare per thread and launch
-    int Hbits[2] = {p.h > 0 ? p.H[0] - c : 0, p.h > 1 ? p.H[1] - c : 0};
+    const int hb0 = p.h > 0 ? p.H[0] - c : 0, hb1 = p.h > 1 ? p.H[1] - c : 0;
     for (unsigned long long item = blockIdx.x; item < p.nitems; item += gridDim.x) {
-        const unsigned long long T = expand_item(item, p.h, Hbits);
+        const unsigned long long T = expand_item(item, p.h, hb0, hb1);
         const unsigned long long fixed = T << c;
         if (threadIdx.x < 64) {
             bool a = (int)threadIdx.x < p.ngates && gate_active(sg[threadIdx.x], fixed);
@@ -827,9 +834,7 @@ __global__ void __launch_bounds__(THREADS, 3) sweep_kernel(SweepParams p) {
         __syncthreads();
         if (!active && !scale) {
             for (int j = 0; j < (1 << p.h); ++j) {
-                unsigned long long Tj = T;
-                for (int i = 0; i < p.h; ++i)
-                    if ((j >> i) & 1) Tj |= 1ull << Hbits[i];
+                const unsigned long long Tj = member_tile(T, j, hb0, hb1);
                 carry_tile(p.in_arena, p.in_table, Tj, p.out_arena, p.out_cap, p.out_table,
                            p.part, p.scal, p.sweep_id, sc);
             }
@@ -838,17 +843,13 @@ __global__ void __launch_bounds__(THREADS, 3) sweep_kernel(SweepParams p) {
         }
         int bad = 0;
         for (int j = 0; j < (1 << p.h); ++j) {
-            unsigned long long Tj = T;
-            for (int i = 0; i < p.h; ++i)
-                if ((j >> i) & 1) Tj |= 1ull << Hbits[i];
+            const unsigned long long Tj = member_tile(T, j, hb0, hb1);
             bad |= decode_tile(p.in_arena + p.in_table[Tj], c, re + j * N, im + j * N, sc, alpha, scale);
         }
         if (bad && threadIdx.x == 0) atomicOr(&p.scal->err, ERR_FORMAT);
         apply_gates(re, im, mb, sg, p.gates, p.ngates, active, fixed);
         for (int j = 0; j < (1 << p.h); ++j) {
-            unsigned long long Tj = T;
-            for (int i = 0; i < p.h; ++i)
-                if ((j >> i) & 1) Tj |= 1ull << Hbits[i];
+            const unsigned long long Tj = member_tile(T, j, hb0, hb1);
             encode_tile(re + j * N, im + j * N, p.cc, Tj, p.out_arena, p.out_cap, p.out_table,
                         p.part, p.scal, p.sweep_id, sc, stage);
         }
