@@ -271,6 +271,43 @@ int qsim_plan_sweeps(int n, int tile_log2, int hmax, int depth, int ngates,
                      const int *ntargets, const int *targets, const double *matrices,
                      int *out_lo, int *out_h, int *out_H, int cap);
 
+/*
+ * qsim_encode_noalloc -- encode a dense state that already sits in device
+ * memory into tile streams, allocating nothing.  The paper has no
+ * counterpart: this entry point exists for callers that are not allowed to
+ * allocate device memory, such as code that runs under an application
+ * allocator owning all of the GPU's memory, a callback invoked from inside
+ * such an allocator, or a latency-critical path that must not pay for the
+ * device-wide synchronisation an allocation implies.
+ *
+ * dev_amps: device, 2^n_qubits complex128 (interleaved), 16-byte aligned.
+ * Tiles of 2^tile_log2 amplitudes (1..min(10, n_qubits)), coded with the
+ * fixed point-wise relative bound rel_err_bound (0 = lossless) in the
+ * stream format above, exactly as qsim_set_amplitudes stores them for a
+ * QSIM_CODEC_REL handle.  Outputs, all caller-owned: dev_out (device,
+ * out_cap bytes, 16-byte aligned) receives the streams in no particular
+ * order, dev_table (device, one entry per tile) the byte offset of each
+ * tile's stream in dev_out, *stream_bytes (host) the bytes used.  The
+ * call runs on cuda_stream (NULL = legacy default stream) and returns
+ * after the work has finished.
+ *
+ * Scratch: one static device array, at most 4096 tiles
+ * (n_qubits - tile_log2 <= 12), held by every GPU that loads the library
+ * until the process exits.  Larger states are rejected with ERR_ARG.
+ * The first call on a device looks up the array's device address (and sets
+ * kernel attributes); make that first call before any stream capture.  All
+ * calls share the array and it keeps the last call's contents; each call
+ * clears what must start at zero.  Calls that overlap on the GPU (several
+ * streams or threads at once) race on the array and must be serialised by
+ * the caller.  Errors: ARG (ranges, alignment, out_cap too small: then
+ * *stream_bytes holds the size needed), NONFINITE, CUDA; the message is in
+ * qsim_last_error(NULL).
+ */
+qsim_status qsim_encode_noalloc(const double *dev_amps, int n_qubits, int tile_log2,
+                                double rel_err_bound, void *dev_out, unsigned long long out_cap,
+                                unsigned long long *dev_table, unsigned long long *stream_bytes,
+                                void *cuda_stream);
+
 /* qsim_version -- library version string. */
 const char *qsim_version(void);
 

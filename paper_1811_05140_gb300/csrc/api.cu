@@ -15,6 +15,7 @@
 #include "qsim_dev.cuh"
 
 namespace qs {
+void set_global_error(const char *msg);
 size_t sweep_smem_bytes(int mb);
 cudaError_t launch_sweep(const SweepParams &p, int grid, cudaStream_t st);
 cudaError_t launch_finalize(DevScalars *scal, int use_alpha, unsigned long long *used_hist,
@@ -183,6 +184,8 @@ double gate_dp_ops(const HostGate &g, int n) {
 }
 
 }  // namespace
+
+void qs::set_global_error(const char *msg) { g_last_error = msg; }
 
 struct qsim_state {
     int n = 0, c = 0, hmax = 2, depth = qs::MAX_SWEEP_GATES;

@@ -26,7 +26,7 @@ EXPORTS = ["qsim_create", "qsim_destroy", "qsim_set_stream", "qsim_set_aalc", "q
            "qsim_flush", "qsim_probabilities", "qsim_amplitudes", "qsim_fidelity",
            "qsim_compressed_bytes", "qsim_stats", "qsim_last_error", "qsim_export_tiles",
            "qsim_import_tiles", "qsim_plan_sweeps", "qsim_version", "qsim_set_profiling",
-           "qsim_profile"]
+           "qsim_profile", "qsim_encode_noalloc"]
 
 
 class QsimError(RuntimeError):
@@ -96,6 +96,7 @@ def load() -> C.CDLL:
         "qsim_version": ([], C.c_char_p),
         "qsim_set_profiling": ([vp, C.c_int], C.c_int),
         "qsim_profile": ([vp, C.POINTER(Profile)], C.c_int),
+        "qsim_encode_noalloc": ([vp, C.c_int, C.c_int, C.c_double, vp, u64, vp, u64p, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -144,6 +145,19 @@ def plan_sweeps(n: int, c: int, hmax: int, depth: int, gates) -> list[tuple[int,
         hi = lo[s + 1] if s + 1 < r else ng
         out.append((lo[s], hi, tuple(HH[2 * s + i] for i in range(hh[s]))))
     return out
+
+
+def encode_noalloc(dev_amps: int, n: int, tile_log2: int, eps: float, dev_out: int,
+                   out_cap: int, dev_table: int, stream=None) -> int:
+    """qsim_encode_noalloc on device pointers; returns the stream bytes used."""
+    L = load()
+    used = C.c_ulonglong()
+    ptr = getattr(stream, "cuda_stream", stream)
+    st = L.qsim_encode_noalloc(C.c_void_p(dev_amps), n, tile_log2, eps, C.c_void_p(dev_out),
+                               out_cap, C.c_void_p(dev_table), C.byref(used), C.c_void_p(ptr or 0))
+    if st != 0:
+        raise QsimError(st, L.qsim_last_error(None).decode())
+    return used.value
 
 
 class State:
