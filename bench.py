@@ -3,7 +3,7 @@
 
 Workload (one step): the 28-qubit QFT (420 gates: H, controlled phases,
 final swaps) on a seeded basis state, state stored as compressed tiles of
-2^10 amplitudes in blocks of 2^20, point-wise relative bound 1e-4,
+2^8 amplitudes (items of 16 tiles: up to four paired high qubits) in blocks of 2^20, point-wise relative bound 1e-4,
 normalize on (Algorithm 2), sweeps of up to 48 fused gates.  A step is
 reset to |x>, all 420 gates, flush (every sweep of decompress -> normalize
 -> gates -> compress), i.e. one full circuit.
@@ -140,11 +140,11 @@ def oracle_sample(n, eps, depth, xval, items_per_sweep, budget_s=None):
     import oracle
     from paper_1811_05140_gb300 import inputs as I
 
-    c = min(BLOCK_LOG2, n, 10)
+    c = min(BLOCK_LOG2, n, 8)
     gates = I.qft(n)
     cs = oracle.CSim(n, c, [oracle.shift_for_eps(eps)], None, True)
     cs.reset_basis(xval)
-    sweeps = oracle.partition(gates, n, c, 2, depth)
+    sweeps = oracle.partition(gates, n, c, 4, depth)
     est_total, spent = 0.0, 0.0
     for lo, hi, H in sweeps:
         nitems = 1 << (n - c - len(H))
@@ -173,13 +173,13 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.barrier()
     torch.cuda.set_device(local_rank)
     n, eps = args.n, args.eps
-    c = min(BLOCK_LOG2, n, 10)
+    c = min(BLOCK_LOG2, n, 8)
     xval = I.seeded_basis(n, I.BASE_SEED + rank)
     gates = I.qft(n)
     stream = torch.cuda.Stream()
     st = qsim.State(n, BLOCK_LOG2, "rel", eps, stream=stream)
     if args.depth != 48:
-        st.set_schedule(c, 2, args.depth)
+        st.set_schedule(c, 4, args.depth)
 
     def step():
         st.reset_basis(xval)
@@ -341,7 +341,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"qft{n}_rel{args.eps:g}", "n_qubits": n,
-                       "block_log2": BLOCK_LOG2, "tile_log2": min(10, n), "rel_err_bound": args.eps,
+                       "block_log2": BLOCK_LOG2, "tile_log2": min(8, n), "pair_slots": 4, "rel_err_bound": args.eps,
                        "gates": ng, "sweep_depth": args.depth, "normalize": True,
                        "l2": "inputs larger than L2 (compressed state > 129 MB), no flush",
                        "parallelism": f"replicas x{world}"},

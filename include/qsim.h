@@ -76,8 +76,8 @@ typedef enum {
 
 /*
  * qsim_create -- new state |0...0> of n_qubits (1..40), stored in tiles of
- * 2^min(block_log2, n_qubits, 10) amplitudes (Sec. III strides; block_log2
- * >= 1).  codec as above; rel_err_bound is the point-wise relative bound
+ * 2^min(block_log2, n_qubits, 8) amplitudes (Sec. III strides; block_log2
+ * >= 1; qsim_set_schedule changes the tile size, up to 2^10).  codec as above; rel_err_bound is the point-wise relative bound
  * eps of REL, and the largest ladder bound of AALC (default ladder
  * {lossless, 1e-5, 1e-4, 1e-3, 1e-2} cut at eps, theta = 16; see
  * qsim_set_aalc).  REL and AALC normalise before every sweep (Algorithm 2);
@@ -113,8 +113,9 @@ qsim_status qsim_set_aalc(qsim_t h, double theta, const double *eps_levels, int 
 qsim_status qsim_set_normalize(qsim_t h, int on);
 
 /*
- * qsim_set_schedule -- tile_log2 c (1..10, <= n), pair slots hmax (1..2,
- * c + hmax <= 12) and sweep depth (max gates per sweep, 1..48; default 48).  Re-tiles
+ * qsim_set_schedule -- tile_log2 c (1..10, <= n), pair slots hmax (1..4,
+ * c + hmax <= 12; default 4) and sweep depth (max gates per sweep, 1..48;
+ * default 48).  Re-tiles
  * the current state (lossless re-encode is exact only for RAW/lossless
  * tiles; call it before the first gate).  Used by the autotuner.
  */
@@ -264,7 +265,7 @@ qsim_status qsim_import_tiles(qsim_t h, unsigned long long first, unsigned long 
  * a gate list (no GPU needed).  Gate g has ntargets[g] targets in
  * targets[2g..], matrix in matrices[32g..] (row-major complex, zero-padded).
  * Writes per sweep its first gate to out_lo, its pair count to out_h and
- * its pair qubits to out_H[2s..].  Returns the number of sweeps, or -1 on
+ * its pair qubits to out_H[4s..] (ascending; unused slots 0).  Returns the number of sweeps, or -1 on
  * bad arguments, or -2 when cap is too small.
  */
 int qsim_plan_sweeps(int n, int tile_log2, int hmax, int depth, int ngates,

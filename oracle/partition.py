@@ -14,7 +14,9 @@ matrix has a nonzero off-diagonal entry, otherwise empty (a diagonal gate
 only scales amplitudes and can use any qubit).  Add the gate to the open
 sweep while the union of H with the gate's high mixing qubits has at most
 hmax members and the sweep has fewer than `depth` gates; otherwise close
-the sweep and open a new one with this gate.
+the sweep and open a new one with this gate.  A closed sweep's H is then
+filled up to min(hmax, n - c) qubits with the smallest high qubits not
+already in it, so that every item holds the same number of tiles.
 """
 from __future__ import annotations
 
@@ -31,6 +33,15 @@ def partition(gates, n: int, c: int, hmax: int, depth: int):
     """Return [(lo, hi, H)] with gates[lo:hi] forming one sweep."""
     hcap = min(hmax, n - c)
     sweeps = []
+
+    def padded(H):
+        H = set(H)
+        q = c
+        while len(H) < hcap and q < n:
+            H.add(q)
+            q += 1
+        return tuple(sorted(H))
+
     lo = 0
     H: set = set()
     for i, g in enumerate(gates):
@@ -38,10 +49,10 @@ def partition(gates, n: int, c: int, hmax: int, depth: int):
         if len(mix) > hcap:
             raise ValueError("gate needs more paired high qubits than allowed")
         if i > lo and (len(H | mix) > hcap or i - lo >= depth):
-            sweeps.append((lo, i, tuple(sorted(H))))
+            sweeps.append((lo, i, padded(H)))
             lo = i
             H = set()
         H |= mix
     if lo < len(gates):
-        sweeps.append((lo, len(gates), tuple(sorted(H))))
+        sweeps.append((lo, len(gates), padded(H)))
     return sweeps

@@ -62,6 +62,7 @@ int sweep_blocks_per_sm(int mb);
 namespace {
 
 constexpr int MAX_QUBITS = 40;
+constexpr int DEFAULT_TILE_LOG2 = 8;    // 2^8-amplitude tiles, up to 4 paired high qubits
 constexpr double UNITARY_TOL = 1e-12;
 
 struct HostGate {
@@ -74,7 +75,7 @@ struct HostGate {
 
 struct Sweep {
     int lo, hi, h;
-    int H[2];
+    int H[4];
 };
 
 std::string g_last_error;
@@ -92,7 +93,9 @@ int popcount64(unsigned long long v) { return __builtin_popcountll(v); }
 
 // Gate run partition: extend the open sweep while the union of its paired
 // high qubits and the gate's mixing high qubits fits hmax and the sweep
-// holds fewer than `depth` gates; diagonal gates mix nothing.
+// holds fewer than `depth` gates; diagonal gates mix nothing.  Each sweep's
+// pair set is then filled up to min(hmax, n - c) with the smallest high
+// qubits not in it, so that every item holds the same number of tiles.
 int plan_sweeps(int n, int c, int hmax, int depth, const std::vector<HostGate> &g,
                 std::vector<Sweep> &out) {
     out.clear();
@@ -101,7 +104,8 @@ int plan_sweeps(int n, int c, int hmax, int depth, const std::vector<HostGate> &
     int lo = 0;
     unsigned long long H = 0;
     auto emit = [&](int a, int b, unsigned long long Hm) {
-        Sweep s{a, b, 0, {0, 0}};
+        for (int q = c; q < n && popcount64(Hm) < hcap; ++q) Hm |= 1ull << q;
+        Sweep s{a, b, 0, {0, 0, 0, 0}};
         for (int q = 0; q < 64; ++q)
             if ((Hm >> q) & 1ull) s.H[s.h++] = q;
         out.push_back(s);
@@ -452,8 +456,8 @@ qsim_status qsim_create(qsim_t *out, int n_qubits, int block_log2, qsim_codec co
         return fail(nullptr, QSIM_ERR_CUDA, "no CUDA device");
     h = new qsim_state();
     h->n = n_qubits;
-    h->c = std::min(std::min(block_log2, n_qubits), qs::MAX_C);
-    h->hmax = 2;
+    h->c = std::min(std::min(block_log2, n_qubits), DEFAULT_TILE_LOG2);
+    h->hmax = qs::MAX_PAIRS;
     h->depth = qs::MAX_SWEEP_GATES;
     h->codec = codec;
     h->eps = rel_err_bound;
@@ -585,7 +589,7 @@ qsim_status qsim_apply_gate(qsim_t h, const double *matrix, const int *targets, 
         }
     g.diag = matrix_is_diagonal(n_targets, g.m);
     if (!g.diag && h->hmax < 2 && n_targets == 2 && g.t[0] >= h->c && g.t[1] >= h->c && h->n - h->c >= 2)
-        return fail(h, QSIM_ERR_ARG, "two high targets need hmax = 2");
+        return fail(h, QSIM_ERR_ARG, "two high targets need hmax >= 2");
     h->queue.push_back(g);
     return QSIM_OK;
 }
@@ -670,8 +674,7 @@ qsim_status qsim_flush(qsim_t h) {
             p.ngates = sw.hi - sw.lo;
             p.n = h->n;
             p.h = sw.h;
-            p.H[0] = sw.H[0];
-            p.H[1] = sw.H[1];
+            for (int i = 0; i < 4; ++i) p.H[i] = sw.H[i];
             p.cc = h->cc;
             p.nitems = h->ntiles >> sw.h;
             p.sweep_id = id0 + (unsigned)j;
@@ -784,7 +787,8 @@ qsim_status qsim_set_schedule(qsim_t h, int tile_log2, int hmax, int depth) {
     qsim_status s = check_usable(h);
     if (s != QSIM_OK) return s;
     if (tile_log2 < 1 || tile_log2 > qs::MAX_C || tile_log2 > h->n) return fail(h, QSIM_ERR_ARG, "tile_log2 must be 1..min(10, n)");
-    if (hmax < 1 || hmax > 2 || tile_log2 + hmax > qs::MAX_ITEM_LOG2) return fail(h, QSIM_ERR_ARG, "hmax must be 1..2");
+    if (hmax < 1 || hmax > qs::MAX_PAIRS || tile_log2 + hmax > qs::MAX_ITEM_LOG2)
+        return fail(h, QSIM_ERR_ARG, "hmax must be 1..4 with tile_log2 + hmax <= 12");
     if (depth < 1 || depth > qs::MAX_SWEEP_GATES) return fail(h, QSIM_ERR_ARG, "depth must be 1..%d", qs::MAX_SWEEP_GATES);
     if ((s = qsim_flush(h)) != QSIM_OK) return s;
     h->hmax = hmax;
@@ -1106,7 +1110,7 @@ qsim_status qsim_import_tiles(qsim_t h, unsigned long long first, unsigned long 
 int qsim_plan_sweeps(int n, int tile_log2, int hmax, int depth, int ngates, const int *ntargets,
                      const int *targets, const double *matrices, int *out_lo, int *out_h, int *out_H,
                      int cap) {
-    if (n < 1 || n > MAX_QUBITS || tile_log2 < 1 || tile_log2 > n || hmax < 1 || hmax > 2 || depth < 1 ||
+    if (n < 1 || n > MAX_QUBITS || tile_log2 < 1 || tile_log2 > n || hmax < 1 || hmax > qs::MAX_PAIRS || depth < 1 ||
         ngates < 0 || (ngates && (!ntargets || !targets || !matrices)))
         return -1;
     std::vector<HostGate> g(ngates);
@@ -1126,7 +1130,8 @@ int qsim_plan_sweeps(int n, int tile_log2, int hmax, int depth, int ngates, cons
     for (size_t i = 0; i < sw.size(); ++i) {
         if (out_lo) out_lo[i] = sw[i].lo;
         if (out_h) out_h[i] = sw[i].h;
-        if (out_H) { out_H[2 * i] = sw[i].H[0]; out_H[2 * i + 1] = sw[i].H[1]; }
+        if (out_H)
+            for (int j = 0; j < 4; ++j) out_H[4 * i + j] = sw[i].H[j];
     }
     return (int)sw.size();
 }

@@ -287,443 +287,390 @@ __device__ void apply_gates(double *re, double *im, int mb, const SGate *sg, con
     }
 }
 
-// ---------------------------------------------------------------- codec scratch
-struct Scratch {
-    uint32_t sw[64];          // sign word per (comp, group): index k*G + g
-    uint32_t nw[64];          // data words per (comp, group) at the chosen level
-    uint32_t woff[64];        // exclusive prefix of nw (words)
-    long long gtot[64];       // decode: group sums of residuals
-    long long gpre[64];       // decode: exclusive prefix of group sums
-    uint8_t wd[64];           // decode: widths
-    uint8_t wl[MAX_LEVELS][64];   // encode: width per level and (comp, group)
-    uint32_t lvl_words[MAX_LEVELS];
-    uint32_t lvl_nonzero[MAX_LEVELS];
-    uint32_t hdr[8];
-    unsigned long long red_lo[NWARPS], red_hi[NWARPS];
-    unsigned long long anchor[2];
-    unsigned long long off;
-    uint32_t body, size, data_off, wtotal;
-    int mode, s, level, smode[2], ok, bad;
-};
+// ---------------------------------------------------------------- warp codec
+// One warp codes one whole tile: lane g holds the metadata of group g, the
+// groups are walked in order with the running prefix (decode) or the last
+// code of the previous group (encode) carried in registers.  No CTA
+// barriers are involved, so the warps of a CTA code different tiles
+// independently.
 
 __device__ __forceinline__ uint32_t sign_bytes(int mode, int G) {
     return mode == S_PATTERN ? 4u + 4u * (uint32_t)((G + 31) / 32)
                              : (mode == S_WORDS ? 4u * (uint32_t)G : 0u);
 }
 
-// exclusive scan of cnt (<= 64) word counts by one warp; returns the total
-__device__ __forceinline__ uint32_t warp_scan_words(const uint32_t *in, uint32_t *out, int cnt) {
-    int lane = threadIdx.x & 31;
-    uint32_t carry = 0;
-    for (int base = 0; base < cnt; base += 32) {
-        uint32_t v = (base + lane < cnt) ? in[base + lane] : 0u;
-        uint32_t inc = v;
-        for (int d = 1; d < 32; d <<= 1) {
-            uint32_t o = __shfl_up_sync(FULL, inc, d);
-            if (lane >= d) inc += o;
-        }
-        if (base + lane < cnt) out[base + lane] = carry + inc - v;
-        carry += __shfl_sync(FULL, inc, 31);
+// exclusive prefix of v over the lanes; *total = sum over the warp
+__device__ __forceinline__ uint32_t warp_exscan(uint32_t v, uint32_t &total) {
+    const int lane = threadIdx.x & 31;
+    uint32_t inc = v;
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t o = __shfl_up_sync(FULL, inc, d);
+        if (lane >= d) inc += o;
     }
-    return carry;
+    total = __shfl_sync(FULL, inc, 31);
+    return inc - v;
 }
 
-// ---------------------------------------------------------------- decode
+// sign word of group g from a sign section in mode md
+__device__ __forceinline__ uint32_t sign_word(const uint8_t *sec, int md, int g, uint32_t lanes) {
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(sec);
+    if (md == S_CLEAR) return 0u;
+    if (md == S_SET) return lanes;
+    if (md == S_PATTERN) {
+        uint32_t P = __ldg(w);
+        return ((__ldg(w + 1 + g / 32) >> (g % 32)) & 1u) ? ~P : P;
+    }
+    return __ldg(w + g);
+}
+
 // Decode one stream into planar re/im (2^c values each), multiplied by
-// alpha when `scale` is set (Algorithm 2's normalize, fused; the caller
-// decides scale = (alpha != 1) once per launch).  CTA-wide; all
-// threads must call it.  Returns nonzero (and zero-fills) on a malformed
-// stream.
-__device__ int decode_tile(const uint8_t *src, int c, double *re, double *im, Scratch &sc,
-                           double alpha, bool scale) {
+// alpha when `scale` (Algorithm 2's normalize, fused).  Warp-wide; returns
+// nonzero (and zero-fills) on a malformed stream.
+__device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double alpha, bool scale) {
     const int N = 1 << c;
-    const int G = N >= 32 ? N / 32 : 1;
-    const int lgG = c >= 5 ? c - 5 : 0;
+    const int G = N >= 32 ? N >> 5 : 1;
     const int L = N >= 32 ? 32 : N;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid < 8) sc.hdr[tid] = __ldg(reinterpret_cast<const uint32_t *>(src) + tid);
-    __syncthreads();
-    const uint32_t h0 = sc.hdr[0];
+    const int lane = threadIdx.x & 31;
+    const uint32_t hw = lane < 8 ? __ldg(reinterpret_cast<const uint32_t *>(src) + lane) : 0u;
+    const uint32_t h0 = __shfl_sync(FULL, hw, 0), body = __shfl_sync(FULL, hw, 1);
+    const unsigned long long a0 = ((unsigned long long)__shfl_sync(FULL, hw, 3) << 32) | __shfl_sync(FULL, hw, 2);
+    const unsigned long long a1 = ((unsigned long long)__shfl_sync(FULL, hw, 5) << 32) | __shfl_sync(FULL, hw, 4);
+    const int hc = __shfl_sync(FULL, hw, 6) & 0xFF;
     const int mode = h0 & 0xFF, s = (h0 >> 8) & 0xFF;
     const int sm0 = (h0 >> 24) & 3, sm1 = (h0 >> 26) & 3;
-    const uint32_t body = sc.hdr[1];
-    const unsigned long long a0 = ((unsigned long long)sc.hdr[3] << 32) | sc.hdr[2];
-    const unsigned long long a1 = ((unsigned long long)sc.hdr[5] << 32) | sc.hdr[4];
-    const int hc = sc.hdr[6] & 0xFF;
     const uint8_t *b = src + HDR;
     bool bad = hc != c || mode > 2 || (mode != M_RAW && s > 52) || (body & 15u);
     if (!bad && mode == M_RAW) bad = body != 16u * (uint32_t)N;
     if (!bad && mode == M_CONST) bad = body != 0 || sm0 > 1 || sm1 > 1;
-    if (!bad && mode == M_PACKED) {
-        uint32_t meta = sign_bytes(sm0, G) + sign_bytes(sm1, G);
-        bad = meta + 2u * G > body;
-    }
-    if (bad) {
-        for (int i = tid; i < N; i += THREADS) { re[i] = 0.0; im[i] = 0.0; }
-        __syncthreads();
-        return 1;
-    }
-    if (mode == M_CONST) {
+    if (!bad && mode == M_PACKED) bad = sign_bytes(sm0, G) + sign_bytes(sm1, G) + 2u * G > body;
+    if (!bad && mode == M_CONST) {
         double v0 = bitsd((a0 << s) | ((unsigned long long)sm0 << 63));
         double v1 = bitsd((a1 << s) | ((unsigned long long)sm1 << 63));
         if (scale) { v0 = __dmul_rn(v0, alpha); v1 = __dmul_rn(v1, alpha); }
-        for (int i = tid; i < N; i += THREADS) { re[i] = v0; im[i] = v1; }
-        __syncthreads();
+        for (int i = lane; i < N; i += 32) { re[i] = v0; im[i] = v1; }
         return 0;
     }
-    if (mode == M_RAW) {
+    if (!bad && mode == M_RAW) {
         const double2 *v = reinterpret_cast<const double2 *>(b);
-        for (int i = tid; i < N; i += THREADS) {
+        for (int i = lane; i < N; i += 32) {
             double2 x = __ldg(v + i);
             if (scale) { x.x = __dmul_rn(x.x, alpha); x.y = __dmul_rn(x.y, alpha); }
             re[i] = x.x;
             im[i] = x.y;
         }
-        __syncthreads();
         return 0;
     }
-    // PACKED: sign words and widths
-    const uint32_t sb0 = sign_bytes(sm0, G), sb1 = sign_bytes(sm1, G);
-    const uint32_t lanes = L == 32 ? FULL : ((1u << L) - 1u);
-    for (int t = tid; t < 2 * G; t += THREADS) {
-        int k = t >> lgG, g = t & (G - 1);
-        int md = k ? sm1 : sm0;
-        const uint32_t *sec = reinterpret_cast<const uint32_t *>(b + (k ? sb0 : 0));
-        uint32_t v;
-        if (md == S_CLEAR) v = 0;
-        else if (md == S_SET) v = lanes;
-        else if (md == S_PATTERN) {
-            uint32_t P = __ldg(sec);
-            uint32_t fl = (__ldg(sec + 1 + g / 32) >> (g % 32)) & 1u;
-            v = fl ? ~P : P;
-        } else v = __ldg(sec + g);
-        sc.sw[t] = v;
-        uint32_t w = b[sb0 + sb1 + t];
-        sc.wd[t] = w;
-        sc.nw[t] = ((uint32_t)L * w + 31u) / 32u;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t tot = warp_scan_words(sc.nw, sc.woff, 2 * G);
-        uint32_t wmax = 0;
-        for (int t = lane; t < 2 * G; t += 32) wmax = max(wmax, sc.wd[t]);
-        wmax = __reduce_max_sync(FULL, wmax);
-        if (lane == 0) {
-            uint32_t doff = (sb0 + sb1 + 2u * G + 3u) & ~3u;
-            sc.data_off = doff;
-            sc.bad = wmax > 64 || (unsigned long long)doff + 4ull * tot > body;
+    uint32_t sw0 = 0, sw1 = 0, w0 = 0, w1 = 0, doff = 0, off0 = 0, off1 = 0, tot0 = 0, tot1 = 0;
+    if (!bad) {
+        const uint32_t sb0 = sign_bytes(sm0, G), sb1 = sign_bytes(sm1, G);
+        const uint32_t lanes = L == 32 ? FULL : ((1u << L) - 1u);
+        if (lane < G) {
+            sw0 = sign_word(b, sm0, lane, lanes);
+            sw1 = sign_word(b + sb0, sm1, lane, lanes);
+            w0 = b[sb0 + sb1 + lane];
+            w1 = b[sb0 + sb1 + G + lane];
         }
+        off0 = warp_exscan(((uint32_t)L * w0 + 31u) >> 5, tot0);
+        off1 = warp_exscan(((uint32_t)L * w1 + 31u) >> 5, tot1) + tot0;
+        doff = (sb0 + sb1 + 2u * G + 3u) & ~3u;
+        uint32_t wmax = __reduce_max_sync(FULL, max(w0, w1));
+        bad = wmax > 64 || (unsigned long long)doff + 4ull * (tot0 + tot1) > body;
     }
-    __syncthreads();
-    if (sc.bad) {
-        for (int i = tid; i < N; i += THREADS) { re[i] = 0.0; im[i] = 0.0; }
-        __syncthreads();
+    if (bad) {
+        for (int i = lane; i < N; i += 32) { re[i] = 0.0; im[i] = 0.0; }
         return 1;
     }
-    const uint32_t *data = reinterpret_cast<const uint32_t *>(b + sc.data_off);
-    long long *reI = reinterpret_cast<long long *>(re);
-    long long *imI = reinterpret_cast<long long *>(im);
-    for (int t = warp; t < 2 * G; t += NWARPS) {
-        int k = t >> lgG, g = t & (G - 1);
-        uint32_t w = sc.wd[t], nwd = sc.nw[t];
-        const uint32_t *base = data + sc.woff[t];
-        unsigned long long z = 0;
-        if (lane < L && w) {
-            uint32_t bo = (uint32_t)lane * w, j0 = bo >> 5, sh = bo & 31u;
-            uint32_t w0 = __ldg(base + j0);
-            uint32_t w1 = j0 + 1 < nwd ? __ldg(base + j0 + 1) : 0u;
-            uint32_t w2 = j0 + 2 < nwd ? __ldg(base + j0 + 2) : 0u;
-            unsigned long long lo = (unsigned long long)w0 | ((unsigned long long)w1 << 32);
-            unsigned long long v = sh ? ((lo >> sh) | ((unsigned long long)w2 << (64 - sh))) : lo;
-            z = w == 64 ? v : (v & ((1ull << w) - 1ull));
-        }
-        unsigned long long r = unzigzag(z);
-        if ((g == 0 && lane == 0) || lane >= L) r = 0;
-        long long inc;
-        if (w <= 27) {                      // 32 partial sums of |r| < 2^26 fit in int32
-            int v32 = (int)(long long)r;
-            for (int d = 1; d < 32; d <<= 1) {
-                int o = __shfl_up_sync(FULL, v32, d);
-                if (lane >= d) v32 += o;
+    const uint32_t *data = reinterpret_cast<const uint32_t *>(b + doff);
+    for (int k = 0; k < 2; ++k) {
+        double *v = k ? im : re;
+        unsigned long long carry = k ? a1 : a0;
+        const uint32_t wk = k ? w1 : w0, offk = k ? off1 : off0, swk = k ? sw1 : sw0;
+        for (int g = 0; g < G; ++g) {
+            const uint32_t w = __shfl_sync(FULL, wk, g);
+            const uint32_t wo = __shfl_sync(FULL, offk, g);
+            const uint32_t sgw = __shfl_sync(FULL, swk, g);
+            const uint32_t nwd = ((uint32_t)L * w + 31u) >> 5;
+            unsigned long long z = 0;
+            if (lane < L && w) {
+                const uint32_t *base = data + wo;
+                uint32_t bo = (uint32_t)lane * w, j0 = bo >> 5, sh = bo & 31u;
+                uint32_t x0 = __ldg(base + j0);
+                uint32_t x1 = j0 + 1 < nwd ? __ldg(base + j0 + 1) : 0u;
+                uint32_t x2 = j0 + 2 < nwd ? __ldg(base + j0 + 2) : 0u;
+                unsigned long long lo = (unsigned long long)x0 | ((unsigned long long)x1 << 32);
+                unsigned long long vv = sh ? ((lo >> sh) | ((unsigned long long)x2 << (64 - sh))) : lo;
+                z = w == 64 ? vv : (vv & ((1ull << w) - 1ull));
             }
-            inc = v32;
-        } else {
-            unsigned long long u = r;
-            for (int d = 1; d < 32; d <<= 1) {
-                unsigned long long o = shfl_up64(u, d);
-                if (lane >= d) u += o;
+            unsigned long long r = unzigzag(z);
+            if ((g == 0 && lane == 0) || lane >= L) r = 0;
+            unsigned long long inc;
+            if (w <= 27) {                      // 32 partial sums of |r| < 2^26 fit in int32
+                int v32 = (int)(long long)r;
+                for (int d = 1; d < 32; d <<= 1) {
+                    int o = __shfl_up_sync(FULL, v32, d);
+                    if (lane >= d) v32 += o;
+                }
+                inc = (unsigned long long)(long long)v32;
+            } else {
+                inc = r;
+                for (int d = 1; d < 32; d <<= 1) {
+                    unsigned long long o = shfl_up64(inc, d);
+                    if (lane >= d) inc += o;
+                }
             }
-            inc = (long long)u;
+            const unsigned long long q = carry + inc;
+            if (lane < L) {
+                double x = bitsd((q << s) | ((unsigned long long)((sgw >> lane) & 1u) << 63));
+                if (scale) x = __dmul_rn(x, alpha);
+                v[g * 32 + lane] = x;
+            }
+            carry = shfl64(q, L - 1);
         }
-        if (lane < L) (k ? imI : reI)[g * 32 + lane] = inc;
-        if (lane == L - 1) sc.gtot[t] = inc;
     }
-    __syncthreads();
-    if (warp < 2) {               // warp k: exclusive prefix of the group sums (G <= 32)
-        int k = warp;
-        unsigned long long v = lane < G ? (unsigned long long)sc.gtot[k * G + lane] : 0ull;
-        unsigned long long inc = v;
-        for (int d = 1; d < 32; d <<= 1) {
-            unsigned long long o = shfl_up64(inc, d);
-            if (lane >= d) inc += o;
-        }
-        if (lane < G) sc.gpre[k * G + lane] = (long long)(inc - v);
-    }
-    __syncthreads();
-    for (int i = tid; i < N; i += THREADS) {
-        int g = i >> 5, l = i & 31;
-        unsigned long long q0 = a0 + (unsigned long long)sc.gpre[g] + (unsigned long long)reI[i];
-        unsigned long long q1 = a1 + (unsigned long long)sc.gpre[G + g] + (unsigned long long)imI[i];
-        unsigned long long s0 = (sc.sw[g] >> l) & 1u, s1 = (sc.sw[G + g] >> l) & 1u;
-        double v0 = bitsd((q0 << s) | (s0 << 63)), v1 = bitsd((q1 << s) | (s1 << 63));
-        if (scale) { v0 = __dmul_rn(v0, alpha); v1 = __dmul_rn(v1, alpha); }
-        re[i] = v0;
-        im[i] = v1;
-    }
-    __syncthreads();
     return 0;
 }
 
-// ---------------------------------------------------------------- encode
 struct EncodeOut {
     unsigned long long off;
     bool ok;
 };
 
-// magnitude bits of value i and of its predecessor in the stream (lane view
-// of group g; lanes >= L get zeros)
-__device__ __forceinline__ void lane_bits(const double *v, int g, int lane, int L,
-                                          unsigned long long &B, unsigned long long &Bp,
-                                          unsigned long long &sg) {
-    unsigned long long u = lane < L ? dbits(v[g * 32 + lane]) : 0ull;
-    B = u & MAG;
-    sg = u >> 63;
-    Bp = shfl_up64(B, 1);
-    if (lane == 0) Bp = g > 0 ? (dbits(v[g * 32 - 1]) & MAG) : B;
-}
+// widths (8 bits per ladder level) and word totals of one pass over a tile
+struct LevelSizes {
+    unsigned long long wl0, wl1;      // lane g: width of group g per level (byte lv)
+    uint32_t words[MAX_LEVELS];       // data words per level (warp-uniform)
+    uint32_t nz;                      // bit lv: some residual nonzero at level lv
+    uint32_t sw0, sw1;                // lane g: sign words
+};
 
-__device__ __forceinline__ unsigned long long lane_z(unsigned long long B, unsigned long long Bp,
-                                                     int s, int lane, int L) {
-    unsigned long long z = zigzag(quant(B, s) - quant(Bp, s));
-    return lane < L ? z : 0ull;
+// Pass 1 of the encoder: sign words and group widths at every level.
+// force0: code every level with shift 0 (values outside the lossy range).
+__device__ __forceinline__ void size_levels(const double *re, const double *im, const CodecCfg &cc,
+                                            int G, int L, bool force0, LevelSizes &ls, int &nonfin,
+                                            int &inel) {
+    const int lane = threadIdx.x & 31;
+    ls.wl0 = ls.wl1 = 0;
+    ls.nz = 0;
+    ls.sw0 = ls.sw1 = 0;
+#pragma unroll
+    for (int lv = 0; lv < MAX_LEVELS; ++lv) ls.words[lv] = 0;
+    for (int k = 0; k < 2; ++k) {
+        const double *v = k ? im : re;
+        unsigned long long carry[MAX_LEVELS];
+#pragma unroll
+        for (int lv = 0; lv < MAX_LEVELS; ++lv) carry[lv] = 0;
+        for (int g = 0; g < G; ++g) {
+            const unsigned long long u = lane < L ? dbits(v[g * 32 + lane]) : 0ull;
+            const unsigned long long B = u & MAG;
+            nonfin |= lane < L && B >= INF_BITS;
+            inel |= lane < L && B != 0 && (B < MIN_NORMAL || B >= LOSSY_LIMIT);
+            const uint32_t sw = __ballot_sync(FULL, lane < L && (u >> 63));
+            if (lane == g) { if (k) ls.sw1 = sw; else ls.sw0 = sw; }
+#pragma unroll
+            for (int lv = 0; lv < MAX_LEVELS; ++lv) {
+                if (lv >= cc.nlev) continue;
+                const int s = force0 ? 0 : cc.shifts[lv];
+                const unsigned long long q = quant(B, s);
+                unsigned long long qp = shfl_up64(q, 1);
+                if (lane == 0) qp = g == 0 ? q : carry[lv];
+                const unsigned long long z = lane < L ? zigzag(q - qp) : 0ull;
+                const unsigned long long oz = warp_or64(z);
+                const uint32_t w = oz ? (uint32_t)bitlen64(oz) : 0u;
+                if (lane == g) {
+                    if (k) ls.wl1 |= (unsigned long long)w << (8 * lv);
+                    else ls.wl0 |= (unsigned long long)w << (8 * lv);
+                }
+                ls.words[lv] += ((uint32_t)L * w + 31u) >> 5;
+                if (oz) ls.nz |= 1u << lv;
+                carry[lv] = shfl64(q, L - 1);
+            }
+        }
+    }
 }
 
 // Encode planar re/im (2^c values each) of tile `tile` into the output
-// arena with Algorithm 2's ladder (all levels sized in one pass).  CTA-wide.
-// Writes the stream, its table entry and norm partial, adds to the
-// running norm.  stage: 64 words of shared memory per warp.
-__device__ EncodeOut encode_tile(const double *re, const double *im, const CodecCfg &cc,
-                                 unsigned long long tile, uint8_t *out_arena,
-                                 unsigned long long out_cap, unsigned long long *out_table,
-                                 unsigned long long *part, DevScalars *scal,
-                                 unsigned sweep_id, Scratch &sc, uint32_t *stage) {
+// arena with Algorithm 2's ladder (every level sized in one pass).
+// Warp-wide.  Writes the stream, its table entry and norm partial, and adds
+// to the running norm.  wstage: 64 words of shared memory of this warp.
+__device__ EncodeOut wencode(const double *re, const double *im, const CodecCfg &cc,
+                             unsigned long long tile, uint8_t *out_arena, unsigned long long out_cap,
+                             unsigned long long *out_table, unsigned long long *part,
+                             DevScalars *scal, unsigned sweep_id, uint32_t *wstage) {
     const int c = cc.c, N = 1 << c;
-    const int G = N >= 32 ? N / 32 : 1;
-    const int lgG = c >= 5 ? c - 5 : 0;
+    const int G = N >= 32 ? N >> 5 : 1;
     const int L = N >= 32 ? 32 : N;
-    const int T = 2 * G;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lane = threadIdx.x & 31;
     const uint32_t lanes = L == 32 ? FULL : ((1u << L) - 1u);
-    uint32_t *wstage = stage + 64 * warp;
 
-    // 1: sign words, value classes, widths of every level
-    if (tid < MAX_LEVELS) { sc.lvl_words[tid] = 0; sc.lvl_nonzero[tid] = 0; }
-    __syncthreads();
+    LevelSizes ls;
     int nonfin = 0, inel = 0;
     if (!cc.force_raw) {
-        for (int t = warp; t < T; t += NWARPS) {
-            int k = t >> lgG, g = t & (G - 1);
-            unsigned long long B, Bp, sg;
-            lane_bits(k ? im : re, g, lane, L, B, Bp, sg);
-            nonfin |= lane < L && B >= INF_BITS;
-            inel |= lane < L && B != 0 && (B < MIN_NORMAL || B >= LOSSY_LIMIT);
-            uint32_t word = __ballot_sync(FULL, lane < L && sg);
-            if (lane == 0) sc.sw[t] = word;
-            for (int lv = 0; lv < cc.nlev; ++lv) {
-                unsigned long long oz = warp_or64(lane_z(B, Bp, cc.shifts[lv], lane, L));
-                if (lane == 0) {
-                    uint32_t w = oz ? (uint32_t)bitlen64(oz) : 0u;
-                    sc.wl[lv][t] = (uint8_t)w;
-                    atomicAdd(&sc.lvl_words[lv], ((uint32_t)L * w + 31u) / 32u);
-                    if (oz) sc.lvl_nonzero[lv] = 1u;
-                }
-            }
+        size_levels(re, im, cc, G, L, false, ls, nonfin, inel);
+        nonfin = __any_sync(FULL, nonfin);
+        inel = __any_sync(FULL, inel);
+        if (inel && !nonfin) {
+            int d0 = 0, d1 = 0;
+            size_levels(re, im, cc, G, L, true, ls, d0, d1);
         }
     }
-    nonfin = __syncthreads_or(nonfin);
-    inel = __syncthreads_or(inel);
     const bool raw_only = cc.force_raw || nonfin;
-    if (!raw_only && inel) {          // values outside the lossy range: shift 0 at every level
-        if (tid < MAX_LEVELS) { sc.lvl_words[tid] = 0; sc.lvl_nonzero[tid] = 0; }
-        __syncthreads();
-        for (int t = warp; t < T; t += NWARPS) {
-            int k = t >> lgG, g = t & (G - 1);
-            unsigned long long B, Bp, sg;
-            lane_bits(k ? im : re, g, lane, L, B, Bp, sg);
-            unsigned long long oz = warp_or64(lane_z(B, Bp, 0, lane, L));
-            if (lane == 0) {
-                uint32_t w = oz ? (uint32_t)bitlen64(oz) : 0u;
-                for (int lv = 0; lv < cc.nlev; ++lv) {
-                    sc.wl[lv][t] = (uint8_t)w;
-                    atomicAdd(&sc.lvl_words[lv], ((uint32_t)L * w + 31u) / 32u);
-                    if (oz) sc.lvl_nonzero[lv] = 1u;
-                }
-            }
-        }
-        __syncthreads();
-    }
 
-    // 2: sign modes, ladder decision, word offsets, allocation (warp 0)
-    if (warp == 0) {
-        if (!raw_only) {
-            for (int k = 0; k < 2; ++k) {
-                uint32_t v = lane < G ? sc.sw[k * G + lane] : 0u;
-                bool any1 = __any_sync(FULL, lane < G && v != 0u);
-                bool allset = __all_sync(FULL, lane >= G || v == lanes);
-                uint32_t P = __shfl_sync(FULL, v, 0);
-                bool pat = G >= 2 && __all_sync(FULL, lane >= G || v == P || v == ~P);
-                if (lane == 0) sc.smode[k] = !any1 ? S_CLEAR : (allset ? S_SET : (pat ? S_PATTERN : S_WORDS));
-            }
+    // decision (warp-uniform)
+    int mode, level = 0, s = 0, sm[2] = {0, 0};
+    uint32_t bodyb;
+    const uint32_t raw_body = 16u * (uint32_t)N;
+    if (raw_only) {
+        mode = M_RAW;
+        bodyb = raw_body;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const uint32_t v = lane < G ? (k ? ls.sw1 : ls.sw0) : 0u;
+            const bool any1 = __any_sync(FULL, lane < G && v != 0u);
+            const bool allset = __all_sync(FULL, lane >= G || v == lanes);
+            const uint32_t P = __shfl_sync(FULL, v, 0);
+            const bool pat = G >= 2 && __all_sync(FULL, lane >= G || v == P || v == ~P);
+            sm[k] = !any1 ? S_CLEAR : (allset ? S_SET : (pat ? S_PATTERN : S_WORDS));
         }
-        __syncwarp();
-        if (lane == 0) {
-            const uint32_t raw_body = 16u * (uint32_t)N;
-            if (raw_only) {
-                sc.mode = M_RAW; sc.s = 0; sc.level = 0; sc.body = raw_body;
+        const uint32_t meta = sign_bytes(sm[0], G) + sign_bytes(sm[1], G);
+        const uint32_t wb = (2u * G + 3u) & ~3u;
+        mode = M_RAW;
+        bodyb = raw_body;
+        bool found = false;                  // first level within the size limit, else the last
+#pragma unroll
+        for (int lv = 0; lv < MAX_LEVELS; ++lv) {
+            if (lv >= cc.nlev || found) continue;
+            if (!((ls.nz >> lv) & 1u) && sm[0] <= S_SET && sm[1] <= S_SET) {
+                mode = M_CONST; bodyb = 0;
             } else {
-                uint32_t meta = sign_bytes(sc.smode[0], G) + sign_bytes(sc.smode[1], G);
-                uint32_t wb = (2u * G + 3u) & ~3u;
-                int pick = cc.nlev - 1, pmode = 0;
-                uint32_t pbody = 0;
-                for (int lv = 0; lv < cc.nlev; ++lv) {
-                    int md;
-                    uint32_t bd;
-                    if (!sc.lvl_nonzero[lv] && sc.smode[0] <= S_SET && sc.smode[1] <= S_SET) {
-                        md = M_CONST; bd = 0;
-                    } else {
-                        uint32_t pb = (meta + wb + 4u * sc.lvl_words[lv] + 15u) & ~15u;
-                        if (pb < raw_body) { md = M_PACKED; bd = pb; }
-                        else { md = M_RAW; bd = raw_body; }
-                    }
-                    pick = lv; pmode = md; pbody = bd;
-                    if ((unsigned long long)(HDR + bd) <= cc.max_bytes) break;
-                }
-                sc.level = pick;
-                sc.mode = pmode;
-                sc.body = pbody;
-                sc.s = pmode == M_RAW ? 0 : (inel ? 0 : cc.shifts[pick]);
+                const uint32_t pb = (meta + wb + 4u * ls.words[lv] + 15u) & ~15u;
+                if (pb < raw_body) { mode = M_PACKED; bodyb = pb; }
+                else { mode = M_RAW; bodyb = raw_body; }
             }
-            sc.size = HDR + sc.body;
+            level = lv;
+            found = (unsigned long long)(HDR + bodyb) <= cc.max_bytes;
         }
-        __syncwarp();
-        if (sc.mode == M_PACKED) {
-            for (int t = lane; t < T; t += 32) sc.nw[t] = ((uint32_t)L * sc.wl[sc.level][t] + 31u) / 32u;
-            __syncwarp();
-            sc.wtotal = warp_scan_words(sc.nw, sc.woff, T);
-        }
-        if (lane == 0) {
-            unsigned long long off = atomicAdd(&scal->bump, (unsigned long long)sc.size);
-            bool ok = off + sc.size <= out_cap;
-            if (!ok) {
-                atomicOr(&scal->err, ERR_OVERFLOW);
-                atomicCAS(&scal->err_sweep, 0u, sweep_id + 1u);
-            }
-            sc.off = off;
-            sc.ok = ok;
-            if (sc.mode != M_RAW) {
-                sc.anchor[0] = quant(dbits(re[0]) & MAG, sc.s);
-                sc.anchor[1] = quant(dbits(im[0]) & MAG, sc.s);
-            } else {
-                sc.anchor[0] = sc.anchor[1] = 0;
-            }
-            if (nonfin) atomicOr(&scal->err, ERR_NONFINITE);
-        }
+        s = mode == M_RAW ? 0 : (inel ? 0 : cc.shifts[level]);
     }
-    __syncthreads();
-    EncodeOut res{sc.off, sc.ok != 0};
-    if (!res.ok) return res;
-    const int mode = sc.mode, s = sc.s;
-    uint8_t *dst = out_arena + res.off;
+    const uint32_t size = HDR + bodyb;
+    unsigned long long off = 0;
+    int ok = 0;
+    if (lane == 0) {
+        off = atomicAdd(&scal->bump, (unsigned long long)size);
+        ok = off + size <= out_cap;
+        if (!ok) {
+            atomicOr(&scal->err, ERR_OVERFLOW);
+            atomicCAS(&scal->err_sweep, 0u, sweep_id + 1u);
+        }
+        if (nonfin) atomicOr(&scal->err, ERR_NONFINITE);
+    }
+    off = shfl64(off, 0);
+    ok = __shfl_sync(FULL, ok, 0);
+    EncodeOut res{off, ok != 0};
+    if (!ok) return res;
+    uint8_t *dst = out_arena + off;
 
-    // 3: write the stream and take the norm of what the decoder will return
-    if (tid < 8) {
+    // header
+    unsigned long long anc0 = 0, anc1 = 0;
+    if (mode != M_RAW) {
+        anc0 = quant(dbits(re[0]) & MAG, s);
+        anc1 = quant(dbits(im[0]) & MAG, s);
+    }
+    if (lane < 8) {
         uint32_t v = 0;
-        switch (tid) {
+        switch (lane) {
             case 0: {
-                uint32_t smb = mode == M_RAW ? 0u : (uint32_t)(sc.smode[0] | (sc.smode[1] << 2));
-                v = (uint32_t)mode | ((uint32_t)s << 8) | ((uint32_t)sc.level << 16) | (smb << 24);
+                const uint32_t smb = mode == M_RAW ? 0u : (uint32_t)(sm[0] | (sm[1] << 2));
+                v = (uint32_t)mode | ((uint32_t)s << 8) | ((uint32_t)level << 16) | (smb << 24);
                 break;
             }
-            case 1: v = sc.body; break;
-            case 2: v = (uint32_t)sc.anchor[0]; break;
-            case 3: v = (uint32_t)(sc.anchor[0] >> 32); break;
-            case 4: v = (uint32_t)sc.anchor[1]; break;
-            case 5: v = (uint32_t)(sc.anchor[1] >> 32); break;
+            case 1: v = bodyb; break;
+            case 2: v = (uint32_t)anc0; break;
+            case 3: v = (uint32_t)(anc0 >> 32); break;
+            case 4: v = (uint32_t)anc1; break;
+            case 5: v = (uint32_t)(anc1 >> 32); break;
             case 6: v = (uint32_t)c; break;
             default: v = 0; break;
         }
-        reinterpret_cast<uint32_t *>(dst)[tid] = v;
+        reinterpret_cast<uint32_t *>(dst)[lane] = v;
     }
     uint8_t *b = dst + HDR;
     unsigned long long nlo = 0, nhi = 0;
     unsigned rng = 0;
     if (mode == M_PACKED) {
-        const int sm0 = sc.smode[0], sm1 = sc.smode[1];
-        const uint32_t sb0 = sign_bytes(sm0, G), sb1 = sign_bytes(sm1, G);
-        if (warp < 2) {
-            int k = warp, md = k ? sm1 : sm0;
+        const uint32_t sb0 = sign_bytes(sm[0], G), sb1 = sign_bytes(sm[1], G);
+        // sign sections
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
             uint32_t *sec = reinterpret_cast<uint32_t *>(b + (k ? sb0 : 0));
-            uint32_t v = lane < G ? sc.sw[k * G + lane] : 0u;
-            if (md == S_PATTERN) {
-                uint32_t P = __shfl_sync(FULL, v, 0);
-                uint32_t fl = __ballot_sync(FULL, lane < G && v != P);
+            const uint32_t v = lane < G ? (k ? ls.sw1 : ls.sw0) : 0u;
+            if (sm[k] == S_PATTERN) {
+                const uint32_t P = __shfl_sync(FULL, v, 0);
+                const uint32_t fl = __ballot_sync(FULL, lane < G && v != P);
                 if (lane == 0) { sec[0] = P; sec[1] = fl; }
-            } else if (md == S_WORDS) {
+            } else if (sm[k] == S_WORDS) {
                 if (lane < G) sec[lane] = v;
             }
         }
+        // widths at the chosen level, word offsets
+        const uint32_t ws0 = (uint32_t)(ls.wl0 >> (8 * level)) & 0xFFu;
+        const uint32_t ws1 = (uint32_t)(ls.wl1 >> (8 * level)) & 0xFFu;
+        uint32_t tot0, tot1;
+        const uint32_t off0 = warp_exscan(lane < G ? ((uint32_t)L * ws0 + 31u) >> 5 : 0u, tot0);
+        const uint32_t off1 = warp_exscan(lane < G ? ((uint32_t)L * ws1 + 31u) >> 5 : 0u, tot1) + tot0;
         const uint32_t wb = (2u * G + 3u) & ~3u;
-        const uint8_t *wsel = sc.wl[sc.level];
-        for (int t = tid; t < (int)wb; t += THREADS) b[sb0 + sb1 + t] = t < T ? wsel[t] : (uint8_t)0;
+        for (uint32_t base = 0; base < wb; base += 32) {          // uniform trip count
+            const int t = (int)base + lane;
+            const int src = t < G ? t : (t < 2 * G ? t - G : 0);
+            const uint32_t a = __shfl_sync(FULL, ws0, src & 31);
+            const uint32_t bb = __shfl_sync(FULL, ws1, src & 31);
+            if ((uint32_t)t < wb) b[sb0 + sb1 + t] = (uint8_t)(t < G ? a : (t < 2 * G ? bb : 0u));
+        }
         const uint32_t doff = sb0 + sb1 + wb;
         uint32_t *data = reinterpret_cast<uint32_t *>(b + doff);
-        for (int t = warp; t < T; t += NWARPS) {
-            int k = t >> lgG, g = t & (G - 1);
-            unsigned long long B, Bp, sg;
-            lane_bits(k ? im : re, g, lane, L, B, Bp, sg);
-            unsigned long long q = quant(B, s);
-            if (lane < L) {
-                unsigned long long l0, h0;
-                sq_units(q << s, l0, h0, rng);
-                add128(nlo, nhi, l0, h0);
+        for (int k = 0; k < 2; ++k) {
+            const double *v = k ? im : re;
+            const uint32_t wk = k ? ws1 : ws0, offk = k ? off1 : off0;
+            unsigned long long carry = 0;
+            for (int g = 0; g < G; ++g) {
+                const unsigned long long B = lane < L ? (dbits(v[g * 32 + lane]) & MAG) : 0ull;
+                const unsigned long long q = quant(B, s);
+                unsigned long long qp = shfl_up64(q, 1);
+                if (lane == 0) qp = g == 0 ? q : carry;
+                carry = shfl64(q, L - 1);
+                if (lane < L) {
+                    unsigned long long l0, h0;
+                    sq_units(q << s, l0, h0, rng);
+                    add128(nlo, nhi, l0, h0);
+                }
+                const uint32_t w = __shfl_sync(FULL, wk, g);
+                if (w == 0) continue;
+                const uint32_t wo = __shfl_sync(FULL, offk, g);
+                const uint32_t nwd = ((uint32_t)L * w + 31u) >> 5;
+                const unsigned long long z = lane < L ? zigzag(q - qp) : 0ull;
+                wstage[lane] = 0u;
+                wstage[lane + 32] = 0u;
+                __syncwarp();
+                if (lane < L) {
+                    const uint32_t bo = (uint32_t)lane * w, j0 = bo >> 5, sh = bo & 31u;
+                    atomicOr(&wstage[j0], (uint32_t)(z << sh));
+                    if (sh + w > 32) atomicOr(&wstage[j0 + 1], (uint32_t)(z >> (32 - sh)));
+                    if (sh + w > 64) atomicOr(&wstage[j0 + 2], (uint32_t)(z >> (64 - sh)));
+                }
+                __syncwarp();
+                uint32_t *gd = data + wo;
+                if ((uint32_t)lane < nwd) gd[lane] = wstage[lane];
+                if ((uint32_t)lane + 32 < nwd) gd[lane + 32] = wstage[lane + 32];
+                __syncwarp();
             }
-            uint32_t w = wsel[t];
-            if (w == 0) continue;
-            unsigned long long z = lane < L ? zigzag(q - quant(Bp, s)) : 0ull;
-            const uint32_t nwd = sc.nw[t];
-            wstage[lane] = 0u;
-            wstage[lane + 32] = 0u;
-            __syncwarp();
-            if (lane < L) {
-                uint32_t bo = (uint32_t)lane * w, j0 = bo >> 5, sh = bo & 31u;
-                atomicOr(&wstage[j0], (uint32_t)(z << sh));
-                if (sh + w > 32) atomicOr(&wstage[j0 + 1], (uint32_t)(z >> (32 - sh)));
-                if (sh + w > 64) atomicOr(&wstage[j0 + 2], (uint32_t)(z >> (64 - sh)));
-            }
-            __syncwarp();
-            uint32_t *gd = data + sc.woff[t];
-            if ((uint32_t)lane < nwd) gd[lane] = wstage[lane];
-            if ((uint32_t)lane + 32 < nwd) gd[lane + 32] = wstage[lane + 32];
-            __syncwarp();
         }
-        const uint32_t dend = doff + 4u * sc.wtotal;
-        for (uint32_t p = dend + tid; p < sc.body; p += THREADS) b[p] = 0;
+        for (uint32_t p = doff + 4u * (tot0 + tot1) + lane; p < bodyb; p += 32) b[p] = 0;
     } else {
         if (mode == M_RAW) {
             double2 *o = reinterpret_cast<double2 *>(b);
-            for (int i = tid; i < N; i += THREADS) o[i] = make_double2(re[i], im[i]);
+            for (int i = lane; i < N; i += 32) o[i] = make_double2(re[i], im[i]);
         }
-        for (int i = tid; i < N; i += THREADS) {
+        for (int i = lane; i < N; i += 32) {
             unsigned long long u0 = dbits(re[i]) & MAG, u1 = dbits(im[i]) & MAG;
             if (mode == M_CONST) { u0 = quant(u0, s) << s; u1 = quant(u1, s) << s; }
             unsigned long long l0, h0, l1, h1;
@@ -734,75 +681,95 @@ __device__ EncodeOut encode_tile(const double *re, const double *im, const Codec
         }
     }
     warp_sum128(nlo, nhi);
-    if (lane == 0) { sc.red_lo[warp] = nlo; sc.red_hi[warp] = nhi; }
-    rng = __syncthreads_or(rng);
-    if (tid == 0) {
-        unsigned long long tl = 0, th = 0;
-        for (int w = 0; w < NWARPS; ++w) add128(tl, th, sc.red_lo[w], sc.red_hi[w]);
-        part[2 * tile] = tl;
-        part[2 * tile + 1] = th;
-        atomic_add128(&scal->acc_lo, &scal->acc_hi, tl, th);
-        out_table[tile] = res.off;
-        atomicAdd(&scal->hist[sc.level], 1ull);
+    rng = __any_sync(FULL, rng);
+    if (lane == 0) {
+        part[2 * tile] = nlo;
+        part[2 * tile + 1] = nhi;
+        atomic_add128(&scal->acc_lo, &scal->acc_hi, nlo, nhi);
+        out_table[tile] = off;
+        atomicAdd(&scal->hist[level], 1ull);
         if (rng) atomicOr(&scal->err, ERR_RANGE);
     }
-    __syncthreads();
+    __syncwarp();
     return res;
 }
 
-// Copy one stream unchanged into the output arena (an item no gate touches).
-__device__ void carry_tile(const uint8_t *in_arena, const unsigned long long *in_table,
-                           unsigned long long tile, uint8_t *out_arena, unsigned long long out_cap,
-                           unsigned long long *out_table, const unsigned long long *part,
-                           DevScalars *scal, unsigned sweep_id, Scratch &sc) {
+// Copy one stream unchanged into the output arena (a tile no gate touches).
+// Warp-wide.
+__device__ void wcarry(const uint8_t *in_arena, const unsigned long long *in_table,
+                       unsigned long long tile, uint8_t *out_arena, unsigned long long out_cap,
+                       unsigned long long *out_table, const unsigned long long *part,
+                       DevScalars *scal, unsigned sweep_id) {
+    const int lane = threadIdx.x & 31;
     const uint8_t *src = in_arena + in_table[tile];
-    if (threadIdx.x == 0) {
-        uint32_t body = reinterpret_cast<const uint32_t *>(src)[1];
-        uint32_t size = HDR + body;
-        unsigned long long off = atomicAdd(&scal->bump, (unsigned long long)size);
-        bool ok = off + size <= out_cap;
+    const uint32_t size = HDR + reinterpret_cast<const uint32_t *>(src)[1];
+    unsigned long long off = 0;
+    int ok = 0;
+    if (lane == 0) {
+        off = atomicAdd(&scal->bump, (unsigned long long)size);
+        ok = off + size <= out_cap;
         if (!ok) {
             atomicOr(&scal->err, ERR_OVERFLOW);
             atomicCAS(&scal->err_sweep, 0u, sweep_id + 1u);
         }
-        sc.off = off;
-        sc.ok = ok;
-        sc.size = size;
         atomic_add128(&scal->acc_lo, &scal->acc_hi, part[2 * tile], part[2 * tile + 1]);
         if (ok) out_table[tile] = off;
     }
-    __syncthreads();
-    if (sc.ok) {
+    off = shfl64(off, 0);
+    ok = __shfl_sync(FULL, ok, 0);
+    if (ok) {
         const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
-        uint4 *d4 = reinterpret_cast<uint4 *>(out_arena + sc.off);
-        for (uint32_t i = threadIdx.x; i < sc.size / 16u; i += THREADS) d4[i] = s4[i];
+        uint4 *d4 = reinterpret_cast<uint4 *>(out_arena + off);
+        for (uint32_t i = lane; i < size / 16u; i += 32) d4[i] = s4[i];
     }
-    __syncthreads();
+    __syncwarp();
+}
+
+// exact norm of a decoded tile (warp-wide), for validation of imports
+__device__ void wnorm(const double *re, const double *im, int N, unsigned long long &lo,
+                      unsigned long long &hi, unsigned &rng) {
+    lo = hi = 0;
+    for (int i = threadIdx.x & 31; i < N; i += 32) {
+        unsigned long long l0, h0, l1, h1;
+        sq_units(dbits(re[i]), l0, h0, rng);
+        sq_units(dbits(im[i]), l1, h1, rng);
+        add128(lo, hi, l0, h0);
+        add128(lo, hi, l1, h1);
+    }
+    warp_sum128(lo, hi);
 }
 
 // ---------------------------------------------------------------- kernels
 // tile index of an item: zero bits inserted at the tile-index positions
-// hb0 < hb1 of the paired qubits (h of them)
-__device__ __forceinline__ unsigned long long expand_item(unsigned long long item, int h, int hb0,
-                                                           int hb1) {
+// hb[0] < hb[1] < ... of the h paired qubits
+__device__ __forceinline__ unsigned long long expand_item(unsigned long long item, int h,
+                                                           const int *hb) {
     unsigned long long v = item;
-    if (h > 0) { unsigned long long m = (1ull << hb0) - 1ull; v = ((v & ~m) << 1) | (v & m); }
-    if (h > 1) { unsigned long long m = (1ull << hb1) - 1ull; v = ((v & ~m) << 1) | (v & m); }
+#pragma unroll
+    for (int i = 0; i < MAX_PAIRS; ++i) {
+        if (i >= h) break;
+        const unsigned long long m = (1ull << hb[i]) - 1ull;
+        v = ((v & ~m) << 1) | (v & m);
+    }
     return v;
 }
 
 // tile of member j of the item whose first tile is T
-__device__ __forceinline__ unsigned long long member_tile(unsigned long long T, int j, int hb0,
-                                                          int hb1) {
-    return T | ((unsigned long long)(j & 1) << hb0) | ((unsigned long long)((j >> 1) & 1) << hb1);
+__device__ __forceinline__ unsigned long long member_tile(unsigned long long T, int j, int h,
+                                                          const int *hb) {
+#pragma unroll
+    for (int i = 0; i < MAX_PAIRS; ++i) {
+        if (i >= h) break;
+        T |= (unsigned long long)((j >> i) & 1) << hb[i];
+    }
+    return T;
 }
 
 // One sweep of Algorithm 2 over all items: decompress (with normalize),
 // apply the gate run, compress with the ladder.  Persistent CTAs loop over
-// items.
+// items; within an item every warp codes its own tiles.
 __global__ void __launch_bounds__(THREADS, 3) sweep_kernel(SweepParams p) {
     extern __shared__ double smem[];
-    __shared__ Scratch sc;
     __shared__ SGate sg[MAX_SWEEP_GATES];
     __shared__ uint32_t stage[64 * NWARPS];
     __shared__ unsigned s_act[2];
@@ -816,43 +783,46 @@ __global__ void __launch_bounds__(THREADS, 3) sweep_kernel(SweepParams p) {
     }
     __syncthreads();
     if (s_flag) return;                       // an earlier pass failed: leave the state
-    const int c = p.cc.c, N = 1 << c, mb = c + p.h;
+    const int c = p.cc.c, N = 1 << c, mb = c + p.h, ntl = 1 << p.h;
     double *re = smem, *im = smem + (1 << mb);
     const double alpha = p.use_alpha ? p.scal->alpha : 1.0;
     const bool scale = alpha != 1.0;           // one compare per thread and launch
-    const int hb0 = p.h > 0 ? p.H[0] - c : 0, hb1 = p.h > 1 ? p.H[1] - c : 0;
+    int hb[MAX_PAIRS];
+#pragma unroll
+    for (int i = 0; i < MAX_PAIRS; ++i) hb[i] = i < p.h ? p.H[i] - c : 0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *wst = stage + 64 * warp;
     for (unsigned long long item = blockIdx.x; item < p.nitems; item += gridDim.x) {
-        const unsigned long long T = expand_item(item, p.h, hb0, hb1);
+        const unsigned long long T = expand_item(item, p.h, hb);
         const unsigned long long fixed = T << c;
+        __syncthreads();
         if (threadIdx.x < 64) {
-            bool a = (int)threadIdx.x < p.ngates && gate_active(sg[threadIdx.x], fixed);
-            unsigned bal = __ballot_sync(FULL, a);
-            if ((threadIdx.x & 31) == 0) s_act[threadIdx.x >> 5] = bal;
+            const bool a = (int)threadIdx.x < p.ngates && gate_active(sg[threadIdx.x], fixed);
+            const unsigned bal = __ballot_sync(FULL, a);
+            if (lane == 0) s_act[warp] = bal;
         }
         __syncthreads();
         const unsigned long long active = (unsigned long long)s_act[0] | ((unsigned long long)s_act[1] << 32);
-        __syncthreads();
         if (!active && !scale) {
-            for (int j = 0; j < (1 << p.h); ++j) {
-                const unsigned long long Tj = member_tile(T, j, hb0, hb1);
-                carry_tile(p.in_arena, p.in_table, Tj, p.out_arena, p.out_cap, p.out_table,
-                           p.part, p.scal, p.sweep_id, sc);
-            }
+            for (int j = warp; j < ntl; j += NWARPS)
+                wcarry(p.in_arena, p.in_table, member_tile(T, j, p.h, hb), p.out_arena, p.out_cap,
+                       p.out_table, p.part, p.scal, p.sweep_id);
             if (threadIdx.x == 0) atomicAdd(&p.scal->items_skipped, 1ull);
             continue;
         }
         int bad = 0;
-        for (int j = 0; j < (1 << p.h); ++j) {
-            const unsigned long long Tj = member_tile(T, j, hb0, hb1);
-            bad |= decode_tile(p.in_arena + p.in_table[Tj], c, re + j * N, im + j * N, sc, alpha, scale);
+        for (int j = warp; j < ntl; j += NWARPS) {
+            const unsigned long long Tj = member_tile(T, j, p.h, hb);
+            bad |= wdecode(p.in_arena + p.in_table[Tj], c, re + j * N, im + j * N, alpha, scale);
         }
-        if (bad && threadIdx.x == 0) atomicOr(&p.scal->err, ERR_FORMAT);
-        apply_gates(re, im, mb, sg, p.gates, p.ngates, active, fixed);
-        for (int j = 0; j < (1 << p.h); ++j) {
-            const unsigned long long Tj = member_tile(T, j, hb0, hb1);
-            encode_tile(re + j * N, im + j * N, p.cc, Tj, p.out_arena, p.out_cap, p.out_table,
-                        p.part, p.scal, p.sweep_id, sc, stage);
+        if (bad && lane == 0) atomicOr(&p.scal->err, ERR_FORMAT);
+        if (active) {
+            __syncthreads();
+            apply_gates(re, im, mb, sg, p.gates, p.ngates, active, fixed);
         }
+        for (int j = warp; j < ntl; j += NWARPS)
+            wencode(re + j * N, im + j * N, p.cc, member_tile(T, j, p.h, hb), p.out_arena, p.out_cap,
+                    p.out_table, p.part, p.scal, p.sweep_id, wst);
         if (threadIdx.x == 0) atomicAdd(&p.scal->items_done, 1ull);
     }
 }
@@ -876,66 +846,70 @@ __global__ void finalize_kernel(DevScalars *scal, int use_alpha, unsigned long l
     scal->alpha = (use_alpha && nrm > 0.0) ? __ddiv_rn(1.0, __dsqrt_rn(nrm)) : 1.0;
 }
 
+// Per-warp tile kernels: TILE_WARPS warps per CTA, each owning a tile buffer
+// of 2^c amplitudes (planar) in dynamic shared memory.
+constexpr int TILE_WARPS = 4;
+
 // Encode a state given densely (device, interleaved) or the basis state
 // |x> (dense == nullptr) into every tile.
-__global__ void __launch_bounds__(THREADS) init_kernel(const double2 *dense, unsigned long long x,
-                                                     CodecCfg cc, unsigned long long ntiles,
-                                                     uint8_t *out_arena, unsigned long long out_cap,
-                                                     unsigned long long *out_table,
-                                                     unsigned long long *part, DevScalars *scal) {
+__global__ void __launch_bounds__(32 * TILE_WARPS) init_kernel(
+    const double2 *dense, unsigned long long x, CodecCfg cc, unsigned long long ntiles,
+    uint8_t *out_arena, unsigned long long out_cap, unsigned long long *out_table,
+    unsigned long long *part, DevScalars *scal) {
     extern __shared__ double smem[];
-    __shared__ Scratch sc;
-    __shared__ uint32_t stage[64 * NWARPS];
+    __shared__ uint32_t stage[64 * TILE_WARPS];
     const int c = cc.c, N = 1 << c;
-    double *re = smem, *im = smem + N;
-    for (unsigned long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *re = smem + (size_t)warp * 2 * N, *im = re + N;
+    uint32_t *wst = stage + 64 * warp;
+    for (unsigned long long t = (unsigned long long)blockIdx.x * TILE_WARPS + warp; t < ntiles;
+         t += (unsigned long long)gridDim.x * TILE_WARPS) {
         if (dense == nullptr && (x >> c) != t) {
-            // all-zero tile: CONST at every level (32 bytes); ladder pick
-            if (threadIdx.x == 0) {
-                int lv = cc.max_bytes >= (unsigned long long)HDR ? 0 : cc.nlev - 1;
-                int s = cc.force_raw ? 0 : cc.shifts[lv];
-                unsigned long long off = atomicAdd(&scal->bump, (unsigned long long)(cc.force_raw ? HDR + 16 * N : HDR));
-                uint32_t size = cc.force_raw ? HDR + 16u * N : HDR;
-                if (off + size > out_cap) {
-                    atomicOr(&scal->err, ERR_OVERFLOW);
-                    sc.ok = 0;
-                } else {
-                    uint32_t *d = reinterpret_cast<uint32_t *>(out_arena + off);
-                    uint32_t h0 = cc.force_raw ? (uint32_t)M_RAW : ((uint32_t)s << 8) | ((uint32_t)lv << 16);
-                    d[0] = h0;
-                    d[1] = cc.force_raw ? 16u * N : 0u;
-                    d[2] = d[3] = d[4] = d[5] = 0;
-                    d[6] = (uint32_t)c;
-                    d[7] = 0;
-                    out_table[t] = off;
-                    part[2 * t] = part[2 * t + 1] = 0;
-                    if (!cc.force_raw) atomicAdd(&scal->hist[lv], 1ull);
-                    else atomicAdd(&scal->hist[0], 1ull);
-                    sc.ok = 1;
-                    sc.off = off;
-                }
+            // all-zero tile: CONST at every level (32 bytes), or RAW zeros
+            const uint32_t size = cc.force_raw ? HDR + 16u * N : HDR;
+            unsigned long long off = 0;
+            int ok = 0;
+            if (lane == 0) {
+                off = atomicAdd(&scal->bump, (unsigned long long)size);
+                ok = off + size <= out_cap;
+                if (!ok) atomicOr(&scal->err, ERR_OVERFLOW);
             }
-            __syncthreads();
-            if (cc.force_raw && sc.ok) {
-                uint4 *d4 = reinterpret_cast<uint4 *>(out_arena + sc.off + HDR);
-                for (int i = threadIdx.x; i < N; i += THREADS) d4[i] = make_uint4(0, 0, 0, 0);
+            off = shfl64(off, 0);
+            ok = __shfl_sync(FULL, ok, 0);
+            if (!ok) continue;
+            const int lv = cc.max_bytes >= (unsigned long long)HDR ? 0 : cc.nlev - 1;
+            const int s = cc.force_raw ? 0 : cc.shifts[lv];
+            uint32_t *d = reinterpret_cast<uint32_t *>(out_arena + off);
+            if (lane < 8) {
+                uint32_t v = 0;
+                if (lane == 0) v = cc.force_raw ? (uint32_t)M_RAW : (((uint32_t)s << 8) | ((uint32_t)lv << 16));
+                else if (lane == 1) v = cc.force_raw ? 16u * N : 0u;
+                else if (lane == 6) v = (uint32_t)c;
+                d[lane] = v;
             }
-            __syncthreads();
+            if (cc.force_raw) {
+                uint4 *d4 = reinterpret_cast<uint4 *>(out_arena + off + HDR);
+                for (int i = lane; i < N; i += 32) d4[i] = make_uint4(0, 0, 0, 0);
+            }
+            if (lane == 0) {
+                out_table[t] = off;
+                part[2 * t] = part[2 * t + 1] = 0;
+                atomicAdd(&scal->hist[cc.force_raw ? 0 : lv], 1ull);
+            }
             continue;
         }
-        for (int i = threadIdx.x; i < N; i += THREADS) {
+        for (int i = lane; i < N; i += 32) {
             if (dense) {
-                double2 v = dense[t * (unsigned long long)N + i];
+                const double2 v = dense[t * (unsigned long long)N + i];
                 re[i] = v.x;
                 im[i] = v.y;
             } else {
-                bool one = (((t << c) | (unsigned long long)i) == x);
-                re[i] = one ? 1.0 : 0.0;
+                re[i] = (((t << c) | (unsigned long long)i) == x) ? 1.0 : 0.0;
                 im[i] = 0.0;
             }
         }
-        __syncthreads();
-        encode_tile(re, im, cc, t, out_arena, out_cap, out_table, part, scal, 0u, sc, stage);
+        __syncwarp();
+        wencode(re, im, cc, t, out_arena, out_cap, out_table, part, scal, 0u, wst);
     }
 }
 
@@ -988,45 +962,29 @@ __global__ void gather_kernel(const uint8_t *arena, const unsigned long long *ta
 
 // Validate imported streams (each at offs[i] in buf, sizes[i] bytes) by
 // decoding them; record their norm partials.  bad[0] counts failures.
-__global__ void __launch_bounds__(THREADS) validate_kernel(const uint8_t *buf, const unsigned long long *offs,
-                                                         const unsigned long long *sizes,
-                                                         unsigned long long count, int c,
-                                                         unsigned long long *parts,
-                                                         unsigned int *bad) {
+__global__ void __launch_bounds__(32 * TILE_WARPS) validate_kernel(
+    const uint8_t *buf, const unsigned long long *offs, const unsigned long long *sizes,
+    unsigned long long count, int c, unsigned long long *parts, unsigned int *bad) {
     extern __shared__ double smem[];
-    __shared__ Scratch sc;
     const int N = 1 << c;
-    double *re = smem, *im = smem + N;
-    for (unsigned long long i = blockIdx.x; i < count; i += gridDim.x) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *re = smem + (size_t)warp * 2 * N, *im = re + N;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * TILE_WARPS + warp; i < count;
+         i += (unsigned long long)gridDim.x * TILE_WARPS) {
         const uint8_t *src = buf + offs[i];
-        const uint32_t *h = reinterpret_cast<const uint32_t *>(src);
-        int fail = 0;
-        if (sizes[i] < HDR || (sizes[i] & 15ull) || HDR + (unsigned long long)h[1] != sizes[i]) fail = 1;
-        fail = __syncthreads_or(fail);
-        if (!fail) fail = decode_tile(src, c, re, im, sc, 1.0, false);
+        const uint32_t body = reinterpret_cast<const uint32_t *>(src)[1];
+        int fail = sizes[i] < HDR || (sizes[i] & 15ull) || HDR + (unsigned long long)body != sizes[i];
+        if (!fail) fail = wdecode(src, c, re, im, 1.0, false);
         unsigned long long lo = 0, hi = 0;
         unsigned rng = 0;
-        if (!fail) {
-            for (int j = threadIdx.x; j < N; j += THREADS) {
-                unsigned long long l0, h0, l1, h1;
-                sq_units(dbits(re[j]), l0, h0, rng);
-                sq_units(dbits(im[j]), l1, h1, rng);
-                add128(lo, hi, l0, h0);
-                add128(lo, hi, l1, h1);
-            }
-        }
-        rng = __syncthreads_or(rng);
-        warp_sum128(lo, hi);
-        if ((threadIdx.x & 31) == 0) { sc.red_lo[threadIdx.x >> 5] = lo; sc.red_hi[threadIdx.x >> 5] = hi; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long tl = 0, th = 0;
-            for (int w = 0; w < NWARPS; ++w) add128(tl, th, sc.red_lo[w], sc.red_hi[w]);
-            parts[2 * i] = tl;
-            parts[2 * i + 1] = th;
+        if (!fail) wnorm(re, im, N, lo, hi, rng);
+        rng = __any_sync(FULL, rng);
+        if (lane == 0) {
+            parts[2 * i] = lo;
+            parts[2 * i + 1] = hi;
             if (fail || rng) atomicAdd(bad, 1u);
         }
-        __syncthreads();
+        __syncwarp();
     }
 }
 
@@ -1049,43 +1007,43 @@ __global__ void place_kernel(const uint8_t *buf, const unsigned long long *offs,
 }
 
 // Decode tiles covering [start, start+count) into out (interleaved).
-__global__ void __launch_bounds__(THREADS) amplitudes_kernel(const uint8_t *arena, const unsigned long long *table,
-                                                           int c, unsigned long long start,
-                                                           unsigned long long count, double2 *out,
-                                                           DevScalars *scal) {
+__global__ void __launch_bounds__(32 * TILE_WARPS) amplitudes_kernel(
+    const uint8_t *arena, const unsigned long long *table, int c, unsigned long long start,
+    unsigned long long count, double2 *out, DevScalars *scal) {
     extern __shared__ double smem[];
-    __shared__ Scratch sc;
     const int N = 1 << c;
-    double *re = smem, *im = smem + N;
-    unsigned long long t0 = start >> c, t1 = (start + count - 1) >> c;
-    for (unsigned long long t = t0 + blockIdx.x; t <= t1; t += gridDim.x) {
-        if (decode_tile(arena + table[t], c, re, im, sc, 1.0, false) && threadIdx.x == 0)
-            atomicOr(&scal->err, ERR_FORMAT);
-        for (int i = threadIdx.x; i < N; i += THREADS) {
-            unsigned long long gidx = (t << c) | (unsigned long long)i;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *re = smem + (size_t)warp * 2 * N, *im = re + N;
+    const unsigned long long t0 = start >> c, t1 = (start + count - 1) >> c;
+    for (unsigned long long t = t0 + (unsigned long long)blockIdx.x * TILE_WARPS + warp; t <= t1;
+         t += (unsigned long long)gridDim.x * TILE_WARPS) {
+        if (wdecode(arena + table[t], c, re, im, 1.0, false) && lane == 0) atomicOr(&scal->err, ERR_FORMAT);
+        __syncwarp();
+        for (int i = lane; i < N; i += 32) {
+            const unsigned long long gidx = (t << c) | (unsigned long long)i;
             if (gidx >= start && gidx < start + count) out[gidx - start] = make_double2(re[i], im[i]);
         }
-        __syncthreads();
+        __syncwarp();
     }
 }
 
 // Exact per-outcome sums of |a|^2: bucket j gathers bit i of j from qubit qs[i].
-__global__ void __launch_bounds__(THREADS) probs_kernel(const uint8_t *arena, const unsigned long long *table,
-                                                      int c, unsigned long long ntiles, const int *qs,
-                                                      int nq, unsigned long long *buckets,
-                                                      DevScalars *scal) {
+__global__ void __launch_bounds__(32 * TILE_WARPS) probs_kernel(
+    const uint8_t *arena, const unsigned long long *table, int c, unsigned long long ntiles,
+    const int *qs, int nq, unsigned long long *buckets, DevScalars *scal) {
     extern __shared__ double smem[];
-    __shared__ Scratch sc;
     __shared__ int sq[32];
     const int N = 1 << c;
-    double *re = smem, *im = smem + N;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *re = smem + (size_t)warp * 2 * N, *im = re + N;
     if (threadIdx.x < nq) sq[threadIdx.x] = qs[threadIdx.x];
     __syncthreads();
-    for (unsigned long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        if (decode_tile(arena + table[t], c, re, im, sc, 1.0, false) && threadIdx.x == 0)
-            atomicOr(&scal->err, ERR_FORMAT);
-        for (int i = threadIdx.x; i < N; i += THREADS) {
-            unsigned long long gidx = (t << c) | (unsigned long long)i;
+    for (unsigned long long t = (unsigned long long)blockIdx.x * TILE_WARPS + warp; t < ntiles;
+         t += (unsigned long long)gridDim.x * TILE_WARPS) {
+        if (wdecode(arena + table[t], c, re, im, 1.0, false) && lane == 0) atomicOr(&scal->err, ERR_FORMAT);
+        __syncwarp();
+        for (int i = lane; i < N; i += 32) {
+            const unsigned long long gidx = (t << c) | (unsigned long long)i;
             unsigned j = 0;
             for (int b = 0; b < nq; ++b) j |= (unsigned)((gidx >> sq[b]) & 1ull) << b;
             unsigned long long l0, h0, l1, h1;
@@ -1095,36 +1053,37 @@ __global__ void __launch_bounds__(THREADS) probs_kernel(const uint8_t *arena, co
             add128(l0, h0, l1, h1);
             if (l0 | h0) atomic_add128(&buckets[2 * j], &buckets[2 * j + 1], l0, h0);
         }
-        __syncthreads();
+        __syncwarp();
     }
 }
 
 // Fidelity partials per tile: <ref|psi> (re, im), <psi|psi>, <ref|ref>,
-// each summed over the tile in a fixed (pairwise) order.
-__global__ void __launch_bounds__(THREADS) fidelity_kernel(const uint8_t *arena, const unsigned long long *table,
-                                                         int c, unsigned long long ntiles, RefSpec rs,
-                                                         Acc4 *tile_sums, DevScalars *scal) {
+// each summed over the tile in a fixed order (lane chunks, then a
+// pairwise shuffle tree).
+__global__ void __launch_bounds__(32 * TILE_WARPS) fidelity_kernel(
+    const uint8_t *arena, const unsigned long long *table, int c, unsigned long long ntiles,
+    RefSpec rs, Acc4 *tile_sums, DevScalars *scal) {
     extern __shared__ double smem[];
-    __shared__ Scratch sc;
-    __shared__ Acc4 red[THREADS];
     const int N = 1 << c;
-    double *re = smem, *im = smem + N, *rre = smem + 2 * N, *rim = smem + 3 * N;
-    for (unsigned long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        int bad = decode_tile(arena + table[t], c, re, im, sc, 1.0, false);
-        if (rs.kind == 0) bad |= decode_tile(rs.o_arena + rs.o_table[t], c, rre, rim, sc, 1.0, false);
-        if (bad && threadIdx.x == 0) atomicOr(&scal->err, ERR_FORMAT);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *re = smem + (size_t)warp * 4 * N, *im = re + N, *rre = re + 2 * N, *rim = re + 3 * N;
+    for (unsigned long long t = (unsigned long long)blockIdx.x * TILE_WARPS + warp; t < ntiles;
+         t += (unsigned long long)gridDim.x * TILE_WARPS) {
+        int bad = wdecode(arena + table[t], c, re, im, 1.0, false);
+        if (rs.kind == 0) bad |= wdecode(rs.o_arena + rs.o_table[t], c, rre, rim, 1.0, false);
+        if (bad && lane == 0) atomicOr(&scal->err, ERR_FORMAT);
+        __syncwarp();
         Acc4 acc = make_acc4(0, 0, 0, 0);
-        // thread-contiguous chunks, then a pairwise tree over threads
-        const int per = (N + THREADS - 1) / THREADS;
+        const int per = (N + 31) / 32;
         for (int q = 0; q < per; ++q) {
-            int i = threadIdx.x * per + q;
+            const int i = lane * per + q;
             if (i >= N) break;
-            unsigned long long gidx = (t << c) | (unsigned long long)i;
+            const unsigned long long gidx = (t << c) | (unsigned long long)i;
             double ar, ai;
             if (rs.kind == 0) { ar = rre[i]; ai = rim[i]; }
             else if (rs.kind == 1) {
-                unsigned long long Nn = 1ull << rs.n;
-                unsigned long long ph = (rs.x * gidx) & (Nn - 1ull);
+                const unsigned long long Nn = 1ull << rs.n;
+                const unsigned long long ph = (rs.x * gidx) & (Nn - 1ull);
                 double sn, cs;
                 sincospi(ldexp((double)ph, 1 - rs.n), &sn, &cs);
                 ar = cs * rs.qft_mag;
@@ -1133,27 +1092,23 @@ __global__ void __launch_bounds__(THREADS) fidelity_kernel(const uint8_t *arena,
                 ar = gidx == rs.x ? rs.grov_m : rs.grov_o;
                 ai = 0.0;
             } else {
-                double2 v = rs.dense[gidx];
+                const double2 v = rs.dense[gidx];
                 ar = v.x;
                 ai = v.y;
             }
-            double pr = re[i], pi = im[i];
+            const double pr = re[i], pi = im[i];
             acc.x = __fma_rn(ar, pr, __fma_rn(ai, pi, acc.x));     // Re <ref|psi>
             acc.y = __fma_rn(ar, pi, __fma_rn(-ai, pr, acc.y));    // Im <ref|psi>
             acc.z = __fma_rn(pr, pr, __fma_rn(pi, pi, acc.z));
             acc.w = __fma_rn(ar, ar, __fma_rn(ai, ai, acc.w));
         }
-        red[threadIdx.x] = acc;
-        __syncthreads();
-        for (int st = THREADS / 2; st > 0; st >>= 1) {
-            if (threadIdx.x < st) {
-                Acc4 a = red[threadIdx.x], b = red[threadIdx.x + st];
-                red[threadIdx.x] = make_acc4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
-            }
-            __syncthreads();
+        for (int o = 1; o < 32; o <<= 1) {
+            const double bx = __shfl_down_sync(FULL, acc.x, o), by = __shfl_down_sync(FULL, acc.y, o);
+            const double bz = __shfl_down_sync(FULL, acc.z, o), bw = __shfl_down_sync(FULL, acc.w, o);
+            if ((lane & (2 * o - 1)) == 0) { acc.x += bx; acc.y += by; acc.z += bz; acc.w += bw; }
         }
-        if (threadIdx.x == 0) tile_sums[t] = red[0];
-        __syncthreads();
+        if (lane == 0) tile_sums[t] = acc;
+        __syncwarp();
     }
 }
 
@@ -1161,7 +1116,7 @@ __global__ void __launch_bounds__(THREADS) fidelity_kernel(const uint8_t *arena,
 __global__ void pair_sum_kernel(const Acc4 *in, Acc4 *out, unsigned long long nout) {
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < nout;
          i += (unsigned long long)gridDim.x * blockDim.x) {
-        Acc4 a = in[2 * i], b = in[2 * i + 1];
+        const Acc4 a = in[2 * i], b = in[2 * i + 1];
         out[i] = make_acc4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
     }
 }
@@ -1172,10 +1127,10 @@ __global__ void pair_sum_kernel(const Acc4 *in, Acc4 *out, unsigned long long no
 namespace qs {
 
 size_t sweep_smem_bytes(int mb) { return (size_t)16 << mb; }
+static size_t tile_smem_bytes(int c, int bufs) { return (size_t)TILE_WARPS * bufs * (16u << c); }
 
 cudaError_t launch_sweep(const SweepParams &p, int grid, cudaStream_t st) {
-    size_t smem = sweep_smem_bytes(p.cc.c + p.h);
-    sweep_kernel<<<grid, THREADS, smem, st>>>(p);
+    sweep_kernel<<<grid, THREADS, sweep_smem_bytes(p.cc.c + p.h), st>>>(p);
     return cudaGetLastError();
 }
 
@@ -1185,12 +1140,19 @@ cudaError_t launch_finalize(DevScalars *scal, int use_alpha, unsigned long long 
     return cudaGetLastError();
 }
 
+static int tile_grid(int grid, unsigned long long ntiles) {
+    unsigned long long need = (ntiles + TILE_WARPS - 1) / TILE_WARPS;
+    unsigned long long g = (unsigned long long)grid;
+    if (need < g) g = need;
+    return g ? (int)g : 1;
+}
+
 cudaError_t launch_init(const double2 *dense, unsigned long long x, const CodecCfg &cc,
                         unsigned long long ntiles, uint8_t *arena, unsigned long long cap,
                         unsigned long long *table, unsigned long long *part, DevScalars *scal,
                         int grid, cudaStream_t st) {
-    init_kernel<<<grid, THREADS, (size_t)16 << cc.c, st>>>(dense, x, cc, ntiles, arena, cap, table,
-                                                            part, scal);
+    init_kernel<<<tile_grid(grid, ntiles), 32 * TILE_WARPS, tile_smem_bytes(cc.c, 1), st>>>(
+        dense, x, cc, ntiles, arena, cap, table, part, scal);
     return cudaGetLastError();
 }
 
@@ -1225,7 +1187,8 @@ cudaError_t launch_gather(const uint8_t *arena, const unsigned long long *table,
 cudaError_t launch_validate(const uint8_t *buf, const unsigned long long *offs,
                             const unsigned long long *sizes, unsigned long long count, int c,
                             unsigned long long *parts, unsigned int *bad, int grid, cudaStream_t st) {
-    validate_kernel<<<grid, THREADS, (size_t)16 << c, st>>>(buf, offs, sizes, count, c, parts, bad);
+    validate_kernel<<<tile_grid(grid, count), 32 * TILE_WARPS, tile_smem_bytes(c, 1), st>>>(
+        buf, offs, sizes, count, c, parts, bad);
     return cudaGetLastError();
 }
 
@@ -1242,21 +1205,25 @@ cudaError_t launch_place(const uint8_t *buf, const unsigned long long *offs,
 cudaError_t launch_amplitudes(const uint8_t *arena, const unsigned long long *table, int c,
                               unsigned long long start, unsigned long long count, double2 *out,
                               DevScalars *scal, int grid, cudaStream_t st) {
-    amplitudes_kernel<<<grid, THREADS, (size_t)16 << c, st>>>(arena, table, c, start, count, out, scal);
+    const unsigned long long tiles = ((start + count - 1) >> c) - (start >> c) + 1;
+    amplitudes_kernel<<<tile_grid(grid, tiles), 32 * TILE_WARPS, tile_smem_bytes(c, 1), st>>>(
+        arena, table, c, start, count, out, scal);
     return cudaGetLastError();
 }
 
 cudaError_t launch_probs(const uint8_t *arena, const unsigned long long *table, int c,
                          unsigned long long ntiles, const int *qsel, int nq,
                          unsigned long long *buckets, DevScalars *scal, int grid, cudaStream_t st) {
-    probs_kernel<<<grid, THREADS, (size_t)16 << c, st>>>(arena, table, c, ntiles, qsel, nq, buckets, scal);
+    probs_kernel<<<tile_grid(grid, ntiles), 32 * TILE_WARPS, tile_smem_bytes(c, 1), st>>>(
+        arena, table, c, ntiles, qsel, nq, buckets, scal);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fidelity(const uint8_t *arena, const unsigned long long *table, int c,
                             unsigned long long ntiles, const RefSpec &rs, Acc4 *tile_sums,
                             DevScalars *scal, int grid, cudaStream_t st) {
-    fidelity_kernel<<<grid, THREADS, (size_t)32 << c, st>>>(arena, table, c, ntiles, rs, tile_sums, scal);
+    fidelity_kernel<<<tile_grid(grid, ntiles), 32 * TILE_WARPS, tile_smem_bytes(c, 2), st>>>(
+        arena, table, c, ntiles, rs, tile_sums, scal);
     return cudaGetLastError();
 }
 
@@ -1268,13 +1235,14 @@ cudaError_t launch_pair_sum(const Acc4 *in, Acc4 *out, unsigned long long nout, 
 
 cudaError_t configure_kernels() {
     cudaError_t e;
-    int maxsm = (int)sweep_smem_bytes(MAX_ITEM_LOG2);
+    const int maxsm = (int)sweep_smem_bytes(MAX_ITEM_LOG2);
     if ((e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm))) return e;
-    if ((e = cudaFuncSetAttribute(init_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 << MAX_C))) return e;
-    if ((e = cudaFuncSetAttribute(validate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 << MAX_C))) return e;
-    if ((e = cudaFuncSetAttribute(amplitudes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 << MAX_C))) return e;
-    if ((e = cudaFuncSetAttribute(probs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 << MAX_C))) return e;
-    if ((e = cudaFuncSetAttribute(fidelity_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 << MAX_C))) return e;
+    const int t1 = (int)tile_smem_bytes(MAX_C, 1), t2 = (int)tile_smem_bytes(MAX_C, 2);
+    if ((e = cudaFuncSetAttribute(init_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, t1))) return e;
+    if ((e = cudaFuncSetAttribute(validate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, t1))) return e;
+    if ((e = cudaFuncSetAttribute(amplitudes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, t1))) return e;
+    if ((e = cudaFuncSetAttribute(probs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, t1))) return e;
+    if ((e = cudaFuncSetAttribute(fidelity_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, t2))) return e;
     return cudaSuccess;
 }
 

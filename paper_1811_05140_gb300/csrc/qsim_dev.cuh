@@ -10,6 +10,7 @@ constexpr int THREADS = 256;            // CTA size of every tile kernel
 constexpr int NWARPS = THREADS / 32;
 constexpr int MAX_C = 10;               // tile_log2 limit: G = 2^c/32 <= 32 groups
 constexpr int MAX_ITEM_LOG2 = 12;       // c + pair count: 4096 amplitudes on chip
+constexpr int MAX_PAIRS = 4;            // paired high qubits per sweep
 constexpr int HDR = 32;                 // tile header bytes
 constexpr int MAX_LEVELS = 8;
 
@@ -97,7 +98,7 @@ struct SweepParams {
     const SGate *sgates;            // compact gates, staged in shared memory
     int ngates;
     int n, h;
-    int H[2];                       // paired high qubits, ascending
+    int H[MAX_PAIRS];               // paired high qubits, ascending
     CodecCfg cc;
     unsigned long long nitems;
     unsigned int sweep_id;

@@ -136,14 +136,14 @@ def plan_sweeps(n: int, c: int, hmax: int, depth: int, gates) -> list[tuple[int,
         m = np.asarray(g.matrix, dtype=np.complex128).reshape(-1)
         mats[i, :2 * m.size] = m.view(np.float64)
     cap = max(1, ng)
-    lo, hh, HH = (C.c_int * cap)(), (C.c_int * cap)(), (C.c_int * (2 * cap))()
+    lo, hh, HH = (C.c_int * cap)(), (C.c_int * cap)(), (C.c_int * (4 * cap))()
     r = L.qsim_plan_sweeps(n, c, hmax, depth, ng, nt, tg, _dp(mats), lo, hh, HH, cap)
     if r < 0:
         raise ValueError(f"qsim_plan_sweeps failed ({r})")
     out = []
     for s in range(r):
         hi = lo[s + 1] if s + 1 < r else ng
-        out.append((lo[s], hi, tuple(HH[2 * s + i] for i in range(hh[s]))))
+        out.append((lo[s], hi, tuple(HH[4 * s + i] for i in range(hh[s]))))
     return out
 
 
@@ -211,7 +211,7 @@ class State:
     def set_normalize(self, on: bool):
         self._check(self._L.qsim_set_normalize(self.h, int(bool(on))))
 
-    def set_schedule(self, tile_log2: int, hmax: int = 2, depth: int = 64):
+    def set_schedule(self, tile_log2: int, hmax: int = 4, depth: int = 48):
         self._check(self._L.qsim_set_schedule(self.h, tile_log2, hmax, depth))
 
     # -- state

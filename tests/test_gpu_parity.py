@@ -38,10 +38,10 @@ def oracle_cfg(codec, eps, c, aalc=None):
     raise ValueError(codec)
 
 
-def run_both(n, b, codec, eps, gates, x=0, hmax=2, depth=48, aalc=None):
-    c = min(b, n, 10)
+def run_both(n, b, codec, eps, gates, x=0, hmax=4, depth=48, aalc=None):
+    c = min(b, n, 8)
     st = qsim.State(n, b, codec, eps)
-    if (hmax, depth) != (2, 48):
+    if (hmax, depth) != (4, 48):
         st.set_schedule(c, hmax, depth)
     if aalc:
         st.set_aalc(*aalc)
@@ -210,7 +210,7 @@ def test_oracle_streams_decode_on_gpu_and_back():
     n, c = 10, 6
     cs = oracle.CSim(n, c, [oracle.shift_for_eps(1e-3)], None, True)
     cs.reset_basis(0)
-    cs.run(I.random_grid(2, 5, 8, 3), 2, 64)
+    cs.run(I.random_grid(2, 5, 8, 3), 4, 48)
     st = qsim.State(n, c, "rel", 1e-3)
     streams = [cs.stream(t) for t in range(1 << (n - c))]
     st.import_tiles(0, streams)

@@ -136,12 +136,15 @@ def test_partition_properties():
         assert sw[0][0] == 0 and sw[-1][1] == len(gates)
         for (lo, hi, H), nxt in zip(sw, sw[1:] + [None]):
             assert 0 < hi - lo <= depth
-            assert len(H) <= hmax and all(q >= c for q in H)
+            assert len(H) == min(hmax, n - c) and all(q >= c for q in H)
             mix = set()
             for g in gates[lo:hi]:
                 if not is_diagonal(g.matrix):
                     mix |= {t for t in g.targets if t >= c}
-            assert mix == set(H)
+            assert mix <= set(H)
+            pad = sorted(set(H) - mix)
+            free = [q for q in range(c, n) if q not in mix]
+            assert pad == free[:len(pad)]               # padding: smallest free high qubits
             if nxt is not None:
                 g = gates[hi]
                 gm = set() if is_diagonal(g.matrix) else {t for t in g.targets if t >= c}
