@@ -146,6 +146,18 @@ qsim_status qsim_apply_gate(qsim_t h, const double *matrix, const int *targets, 
 qsim_status qsim_flush(qsim_t h);
 
 /*
+ * qsim_flush_batch -- flush several handles together: round r runs the r-th
+ * pending sweep of every handle that has one, all rounds as one persistent
+ * launch each (plus one small finalize launch) on the first handle's stream,
+ * optionally captured into a CUDA graph (use_graph = 1).  Each handle's
+ * result is byte-identical to its own qsim_flush.  A handle whose output
+ * arena overflows is grown and finished alone afterwards.  The handles must
+ * be distinct and on one device.  Returns the first handle error (each
+ * handle keeps its own qsim_last_error).
+ */
+qsim_status qsim_flush_batch(qsim_t *handles, int count, int use_graph);
+
+/*
  * qsim_probabilities -- flush, then out[j] (host, 2^nq doubles) = total
  * probability of the outcomes whose bits on qubits[0..nq-1] spell j (bit i
  * of j <-> qubits[i]), computed as RN(S_j) / RN(S) where S_j and S are the

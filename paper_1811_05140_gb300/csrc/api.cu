@@ -17,7 +17,9 @@
 namespace qs {
 void set_global_error(const char *msg);
 size_t sweep_smem_bytes(int mb);
-cudaError_t launch_sweep(const SweepParams &p, int grid, cudaStream_t st);
+cudaError_t launch_sweep(const SweepParams *plist, const unsigned long long *istart, int nlist,
+                         int mb, int grid, cudaStream_t st);
+cudaError_t launch_finalize_list(const FinalizeEntry *list, int n, cudaStream_t st);
 cudaError_t launch_finalize(DevScalars *scal, int use_alpha, unsigned long long *used_hist,
                             unsigned slot, int record_used, cudaStream_t st);
 cudaError_t launch_init(const double2 *dense, unsigned long long x, const CodecCfg &cc,
@@ -214,6 +216,9 @@ struct qsim_state {
     qs::DGate *hgates = nullptr;          // pinned staging
     size_t hgates_cap = 0;
     qs::SGate *dsg = nullptr, *hsg = nullptr;
+    qs::SweepParams *dparams = nullptr, *hparams = nullptr;   // one entry per sweep
+    unsigned long long *distart = nullptr, *histart = nullptr; // (0, nitems) per sweep
+    size_t params_cap = 0;
     unsigned long long *used_hist = nullptr;
     size_t used_hist_cap = 0;
     unsigned long long *hused = nullptr;  // pinned
@@ -495,6 +500,10 @@ qsim_status qsim_destroy(qsim_t h) {
     if (h->hgates) cudaFreeHost(h->hgates);
     if (h->dsg) cudaFree(h->dsg);
     if (h->hsg) cudaFreeHost(h->hsg);
+    if (h->dparams) cudaFree(h->dparams);
+    if (h->hparams) cudaFreeHost(h->hparams);
+    if (h->distart) cudaFree(h->distart);
+    if (h->histart) cudaFreeHost(h->histart);
     if (h->used_hist) cudaFree(h->used_hist);
     if (h->hused) cudaFreeHost(h->hused);
     for (cudaEvent_t ev : h->events) cudaEventDestroy(ev);
@@ -594,15 +603,28 @@ qsim_status qsim_apply_gate(qsim_t h, const double *matrix, const int *targets, 
     return QSIM_OK;
 }
 
-qsim_status qsim_flush(qsim_t h) {
-    qsim_status s = check_usable(h);
-    if (s != QSIM_OK) return s;
-    if (h->queue.empty()) return QSIM_OK;
+}  // extern "C"
+
+namespace {
+
+// One flush in progress: its sweeps and where its passes stand.
+struct FlushCtx {
     std::vector<Sweep> sweeps;
-    if (plan_sweeps(h->n, h->c, h->hmax, h->depth, h->queue, sweeps) < 0)
+    size_t ng = 0, ns = 0;
+    int cur0 = 0;
+    unsigned id0 = 0;
+    unsigned long long used_before = 0;
+    int regrows = 0;
+};
+
+// Plan the queued gates into sweeps and upload them (prepared for their
+// sweep) on stream st; size the per-sweep buffers.
+qsim_status stage_flush(qsim_t h, FlushCtx &fc, cudaStream_t st) {
+    if (plan_sweeps(h->n, h->c, h->hmax, h->depth, h->queue, fc.sweeps) < 0)
         return fail(h, QSIM_ERR_ARG, "a gate needs more paired qubits than hmax");
-    const size_t ng = h->queue.size(), ns = sweeps.size();
-    // stage every gate, prepared for its sweep, in one upload
+    const size_t ng = h->queue.size(), ns = fc.sweeps.size();
+    fc.ng = ng;
+    fc.ns = ns;
     if (h->hgates_cap < ng) {
         if (h->hgates) cudaFreeHost(h->hgates);
         if (h->hsg) cudaFreeHost(h->hsg);
@@ -614,7 +636,7 @@ qsim_status qsim_flush(qsim_t h) {
         h->hgates_cap = ng;
     }
     if (h->dgates_cap < ng) {
-        CK(cudaStreamSynchronize(h->stream));
+        CK(cudaStreamSynchronize(st));
         if (h->dgates) cudaFree(h->dgates);
         if (h->dsg) cudaFree(h->dsg);
         h->dgates = nullptr;
@@ -625,7 +647,7 @@ qsim_status qsim_flush(qsim_t h) {
         h->dgates_cap = ng;
     }
     if (h->used_hist_cap < ns) {
-        CK(cudaStreamSynchronize(h->stream));
+        CK(cudaStreamSynchronize(st));
         if (h->used_hist) cudaFree(h->used_hist);
         if (h->hused) cudaFreeHost(h->hused);
         h->used_hist = nullptr;
@@ -635,12 +657,26 @@ qsim_status qsim_flush(qsim_t h) {
         CK(cudaMallocHost(&h->hused, ns * sizeof(unsigned long long)));
         h->used_hist_cap = ns;
     }
+    if (h->params_cap < ns) {
+        CK(cudaStreamSynchronize(st));
+        if (h->dparams) cudaFree(h->dparams);
+        if (h->hparams) cudaFreeHost(h->hparams);
+        if (h->distart) cudaFree(h->distart);
+        if (h->histart) cudaFreeHost(h->histart);
+        h->dparams = h->hparams = nullptr;
+        h->distart = h->histart = nullptr;
+        h->params_cap = 0;
+        CK(cudaMalloc(&h->dparams, ns * sizeof(qs::SweepParams)));
+        CK(cudaMallocHost(&h->hparams, ns * sizeof(qs::SweepParams)));
+        CK(cudaMalloc(&h->distart, 2 * ns * sizeof(unsigned long long)));
+        CK(cudaMallocHost(&h->histart, 2 * ns * sizeof(unsigned long long)));
+        h->params_cap = ns;
+    }
     for (size_t si = 0; si < ns; ++si)
-        for (int gi = sweeps[si].lo; gi < sweeps[si].hi; ++gi)
-            prepare_gate(h->queue[gi], h->c, sweeps[si], h->hgates[gi], h->hsg[gi]);
-    CK(cudaMemcpyAsync(h->dgates, h->hgates, ng * sizeof(qs::DGate), cudaMemcpyHostToDevice, h->stream));
-    CK(cudaMemcpyAsync(h->dsg, h->hsg, ng * sizeof(qs::SGate), cudaMemcpyHostToDevice, h->stream));
-
+        for (int gi = fc.sweeps[si].lo; gi < fc.sweeps[si].hi; ++gi)
+            prepare_gate(h->queue[gi], h->c, fc.sweeps[si], h->hgates[gi], h->hsg[gi]);
+    CK(cudaMemcpyAsync(h->dgates, h->hgates, ng * sizeof(qs::DGate), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h->dsg, h->hsg, ng * sizeof(qs::SGate), cudaMemcpyHostToDevice, st));
     if (h->profiling) {
         while (h->events.size() < 2 * ns) {
             cudaEvent_t ev;
@@ -648,87 +684,271 @@ qsim_status qsim_flush(qsim_t h) {
             h->events.push_back(ev);
         }
     }
-    const unsigned long long used_before = h->used;
-    const int cur0 = h->cur;
-    const unsigned id0 = h->sweep_counter;
-    size_t k = 0;
-    int regrows = 0;
-    // the output of a sweep never needs more than its input plus this slack
-    // on the first try; overflows are re-run with the exact size
-    unsigned long long first_need = std::max<unsigned long long>(h->used + h->used / 4 + (1ull << 20), 1ull << 22);
-    if ((s = ensure_arena(h, h->cur ^ 1, first_need)) != QSIM_OK) return s;
+    fc.used_before = h->used;
+    fc.cur0 = h->cur;
+    fc.id0 = h->sweep_counter;
+    fc.regrows = 0;
+    // the output of a pass rarely needs more than its input plus this slack;
+    // an overflow is re-run with the exact size
+    const unsigned long long first_need =
+        std::max<unsigned long long>(h->used + h->used / 4 + (1ull << 20), 1ull << 22);
+    return ensure_arena(h, h->cur ^ 1, first_need);
+}
+
+// Parameters of sweep j of a flush (arena parity alternates per sweep).
+qs::SweepParams sweep_params(qsim_t h, const FlushCtx &fc, size_t j) {
+    const Sweep &sw = fc.sweeps[j];
+    const int in = fc.cur0 ^ (int)(j & 1), outa = in ^ 1;
+    qs::SweepParams p{};
+    p.in_arena = h->arena[in];
+    p.in_table = h->table[in];
+    p.out_arena = h->arena[outa];
+    p.out_table = h->table[outa];
+    p.out_cap = h->cap[outa];
+    p.part = h->part;
+    p.scal = h->scal;
+    p.gates = h->dgates + sw.lo;
+    p.sgates = h->dsg + sw.lo;
+    p.ngates = sw.hi - sw.lo;
+    p.n = h->n;
+    p.h = sw.h;
+    for (int i = 0; i < 4; ++i) p.H[i] = sw.H[i];
+    p.cc = h->cc;
+    p.nitems = h->ntiles >> sw.h;
+    p.sweep_id = fc.id0 + (unsigned)j;
+    p.use_alpha = h->normalize;
+    return p;
+}
+
+// Run sweeps k .. ns-1 of a flush on the handle's stream, growing the
+// output arena and re-running a pass whenever it overflows.
+qsim_status run_from(qsim_t h, FlushCtx &fc, size_t k) {
+    qsim_status s;
+    const size_t ns = fc.ns;
     while (k < ns) {
         for (size_t j = k; j < ns; ++j) {
-            const Sweep &sw = sweeps[j];
-            int in = cur0 ^ (int)(j & 1), outa = in ^ 1;
-            qs::SweepParams p{};
-            p.in_arena = h->arena[in];
-            p.in_table = h->table[in];
-            p.out_arena = h->arena[outa];
-            p.out_table = h->table[outa];
-            p.out_cap = h->cap[outa];
-            p.part = h->part;
-            p.scal = h->scal;
-            p.gates = h->dgates + sw.lo;
-            p.sgates = h->dsg + sw.lo;
-            p.ngates = sw.hi - sw.lo;
-            p.n = h->n;
-            p.h = sw.h;
-            for (int i = 0; i < 4; ++i) p.H[i] = sw.H[i];
-            p.cc = h->cc;
-            p.nitems = h->ntiles >> sw.h;
-            p.sweep_id = id0 + (unsigned)j;
-            p.use_alpha = h->normalize;
-            int per_sm = qs::sweep_blocks_per_sm(h->c + sw.h);
+            h->hparams[j] = sweep_params(h, fc, j);
+            h->histart[2 * j] = 0;
+            h->histart[2 * j + 1] = h->hparams[j].nitems;
+        }
+        CK(cudaMemcpyAsync(h->dparams + k, h->hparams + k, (ns - k) * sizeof(qs::SweepParams),
+                           cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(h->distart + 2 * k, h->histart + 2 * k, 2 * (ns - k) * sizeof(unsigned long long),
+                           cudaMemcpyHostToDevice, h->stream));
+        for (size_t j = k; j < ns; ++j) {
+            const int mb = h->c + fc.sweeps[j].h;
+            const int per_sm = qs::sweep_blocks_per_sm(mb);
             if (h->profiling) CK(cudaEventRecord(h->events[2 * j], h->stream));
-            ++h->launches; CK(qs::launch_sweep(p, grid_for(h, p.nitems, per_sm), h->stream));
+            ++h->launches;
+            CK(qs::launch_sweep(h->dparams + j, h->distart + 2 * j, 1, mb,
+                                grid_for(h, h->hparams[j].nitems, per_sm), h->stream));
             if (h->profiling) CK(cudaEventRecord(h->events[2 * j + 1], h->stream));
-            ++h->launches; CK(qs::launch_finalize(h->scal, h->normalize, h->used_hist, (unsigned)j, 1, h->stream));
+            ++h->launches;
+            CK(qs::launch_finalize(h->scal, h->normalize, h->used_hist, (unsigned)j, 1, h->stream));
         }
         if ((s = read_scalars(h)) != QSIM_OK) return s;
-        unsigned err = h->hscal->err;
+        const unsigned err = h->hscal->err;
         if (err & qs::ERR_OVERFLOW) {
-            unsigned failed = h->hscal->err_sweep - 1u - id0;
+            const unsigned failed = h->hscal->err_sweep - 1u - fc.id0;
             if (failed >= ns) return device_error(h, err);
-            int outa = (cur0 ^ (int)(failed & 1)) ^ 1;
-            unsigned long long need = h->hscal->bump + h->hscal->bump / 8 + (1ull << 20);
+            const int outa = (fc.cur0 ^ (int)(failed & 1)) ^ 1;
+            const unsigned long long need = h->hscal->bump + h->hscal->bump / 8 + (1ull << 20);
             if ((s = ensure_arena(h, outa, need)) != QSIM_OK) return s;
             if ((s = clear_pass_state(h)) != QSIM_OK) return s;
             k = failed;
-            ++regrows;
+            ++fc.regrows;
             continue;
         }
         if (err) return device_error(h, err);
         break;
     }
+    return QSIM_OK;
+}
+
+// Bookkeeping after every pass of a flush has succeeded.
+qsim_status finish_flush(qsim_t h, FlushCtx &fc, bool timed) {
+    const size_t ns = fc.ns;
     CK(cudaMemcpyAsync(h->hused, h->used_hist, ns * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    h->cur = cur0 ^ (int)(ns & 1);
+    h->cur = fc.cur0 ^ (int)(ns & 1);
     h->used = h->hscal->used;
     h->sweep_counter += (unsigned)ns;
-    h->st.gates += ng;
+    h->st.gates += fc.ng;
     h->st.sweeps += ns;
-    h->st.arena_regrows += (unsigned long long)regrows;
+    h->st.arena_regrows += (unsigned long long)fc.regrows;
     for (size_t j = 0; j < ns; ++j) {
         h->st.min_stream_bytes_seen = std::min(h->st.min_stream_bytes_seen, h->hused[j]);
         h->st.max_stream_bytes_seen = std::max(h->st.max_stream_bytes_seen, h->hused[j]);
     }
     h->st.stream_bytes = h->used;
-    if (h->profiling) {
+    if (h->profiling && timed) {
         for (size_t j = 0; j < ns; ++j) {
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, h->events[2 * j], h->events[2 * j + 1]));
             h->prof.sweep_ms += ms;
             h->prof.sweep_launches += 1;
             double dp = h->normalize ? 2.0 * std::ldexp(1.0, h->n) : 0.0;
-            for (int gi = sweeps[j].lo; gi < sweeps[j].hi; ++gi) dp += gate_dp_ops(h->queue[gi], h->n);
+            for (int gi = fc.sweeps[j].lo; gi < fc.sweeps[j].hi; ++gi) dp += gate_dp_ops(h->queue[gi], h->n);
             h->prof.dp_ops += dp;
-            unsigned long long in = j == 0 ? used_before : h->hused[j - 1];
+            const unsigned long long in = j == 0 ? fc.used_before : h->hused[j - 1];
             h->prof.bytes += (double)in + (double)h->hused[j] + 32.0 * (double)h->ntiles;
         }
     }
     h->queue.clear();
     return QSIM_OK;
+}
+
+// Per-process workspace of batched flushes (grown, never shrunk).
+struct BatchSpace {
+    qs::SweepParams *dP = nullptr, *hP = nullptr;
+    unsigned long long *dI = nullptr, *hI = nullptr;
+    qs::FinalizeEntry *dF = nullptr, *hF = nullptr;
+    size_t capP = 0, capI = 0;
+} g_batch;
+
+}  // namespace
+
+extern "C" {
+
+qsim_status qsim_flush(qsim_t h) {
+    qsim_status s = check_usable(h);
+    if (s != QSIM_OK) return s;
+    if (h->queue.empty()) return QSIM_OK;
+    FlushCtx fc;
+    if ((s = stage_flush(h, fc, h->stream)) != QSIM_OK) return s;
+    if ((s = run_from(h, fc, 0)) != QSIM_OK) return s;
+    return finish_flush(h, fc, true);
+}
+
+qsim_status qsim_flush_batch(qsim_t *handles, int count, int use_graph) {
+    if (!handles || count < 1) return fail(nullptr, QSIM_ERR_ARG, "qsim_flush_batch: no handles");
+    for (int i = 0; i < count; ++i) {
+        if (!handles[i]) return fail(nullptr, QSIM_ERR_ARG, "qsim_flush_batch: NULL handle");
+        for (int j = 0; j < i; ++j)
+            if (handles[j] == handles[i]) return fail(nullptr, QSIM_ERR_ARG, "qsim_flush_batch: repeated handle");
+        qsim_status s = check_usable(handles[i]);
+        if (s != QSIM_OK) return s;
+        if (handles[i]->device != handles[0]->device)
+            return fail(nullptr, QSIM_ERR_ARG, "qsim_flush_batch: handles on different devices");
+    }
+    qsim_t h0 = handles[0];
+    cudaStream_t st = h0->stream;
+    for (int i = 1; i < count; ++i)
+        if (handles[i]->stream != st && cudaStreamSynchronize(handles[i]->stream) != cudaSuccess)
+            return fail(handles[i], QSIM_ERR_CUDA, "stream synchronisation failed");
+    std::vector<FlushCtx> fcs(count);
+    size_t rounds = 0, entries = 0;
+    for (int i = 0; i < count; ++i) {
+        qsim_t h = handles[i];
+        if (h->queue.empty()) continue;
+        qsim_status s = stage_flush(h, fcs[i], st);
+        if (s != QSIM_OK) return s;
+        rounds = std::max(rounds, fcs[i].ns);
+        entries += fcs[i].ns;
+    }
+    if (rounds == 0) return QSIM_OK;
+    qsim_t h = h0;   // for CK messages
+    // work lists: round r holds sweep r of every handle that has one
+    if (g_batch.capP < entries || g_batch.capI < entries + rounds) {
+        CK(cudaStreamSynchronize(st));
+        if (g_batch.dP) cudaFree(g_batch.dP);
+        if (g_batch.hP) cudaFreeHost(g_batch.hP);
+        if (g_batch.dI) cudaFree(g_batch.dI);
+        if (g_batch.hI) cudaFreeHost(g_batch.hI);
+        if (g_batch.dF) cudaFree(g_batch.dF);
+        if (g_batch.hF) cudaFreeHost(g_batch.hF);
+        g_batch = BatchSpace{};
+        const size_t cp = std::max<size_t>(entries, 64), ci = cp + std::max<size_t>(rounds, 64);
+        CK(cudaMalloc(&g_batch.dP, cp * sizeof(qs::SweepParams)));
+        CK(cudaMallocHost(&g_batch.hP, cp * sizeof(qs::SweepParams)));
+        CK(cudaMalloc(&g_batch.dF, cp * sizeof(qs::FinalizeEntry)));
+        CK(cudaMallocHost(&g_batch.hF, cp * sizeof(qs::FinalizeEntry)));
+        CK(cudaMalloc(&g_batch.dI, ci * sizeof(unsigned long long)));
+        CK(cudaMallocHost(&g_batch.hI, ci * sizeof(unsigned long long)));
+        g_batch.capP = cp;
+        g_batch.capI = ci;
+    }
+    std::vector<size_t> rstart(rounds + 1), rmb(rounds), ritems(rounds);
+    size_t e = 0, ii = 0;
+    std::vector<size_t> istart_at(rounds);
+    for (size_t r = 0; r < rounds; ++r) {
+        rstart[r] = e;
+        istart_at[r] = ii;
+        unsigned long long acc = 0;
+        int mb = 0;
+        for (int i = 0; i < count; ++i) {
+            if (fcs[i].ns <= r) continue;
+            qsim_t hh = handles[i];
+            g_batch.hP[e] = sweep_params(hh, fcs[i], r);
+            g_batch.hF[e] = qs::FinalizeEntry{hh->scal, hh->used_hist, (unsigned)r, hh->normalize, 1};
+            g_batch.hI[ii++] = acc;
+            acc += g_batch.hP[e].nitems;
+            mb = std::max(mb, hh->c + fcs[i].sweeps[r].h);
+            ++e;
+        }
+        g_batch.hI[ii++] = acc;
+        rmb[r] = (size_t)mb;
+        ritems[r] = acc;
+    }
+    rstart[rounds] = e;
+    CK(cudaMemcpyAsync(g_batch.dP, g_batch.hP, e * sizeof(qs::SweepParams), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(g_batch.dF, g_batch.hF, e * sizeof(qs::FinalizeEntry), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(g_batch.dI, g_batch.hI, ii * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (use_graph) CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    for (size_t r = 0; r < rounds; ++r) {
+        const int n_r = (int)(rstart[r + 1] - rstart[r]);
+        const int mb = (int)rmb[r];
+        const int per_sm = qs::sweep_blocks_per_sm(mb);
+        cudaError_t le = qs::launch_sweep(g_batch.dP + rstart[r], g_batch.dI + istart_at[r], n_r, mb,
+                                          grid_for(h0, ritems[r], per_sm), st);
+        if (le == cudaSuccess) le = qs::launch_finalize_list(g_batch.dF + rstart[r], n_r, st);
+        if (le != cudaSuccess) {
+            if (use_graph) { cudaStreamEndCapture(st, &graph); if (graph) cudaGraphDestroy(graph); }
+            return fail(h0, QSIM_ERR_CUDA, "batched launch: %s", cudaGetErrorString(le));
+        }
+        h0->launches += 2;
+    }
+    if (use_graph) {
+        CK(cudaStreamEndCapture(st, &graph));
+        cudaError_t ge = cudaGraphInstantiate(&exec, graph, 0);
+        if (ge == cudaSuccess) ge = cudaGraphLaunch(exec, st);
+        if (ge == cudaSuccess) ge = cudaStreamSynchronize(st);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (ge != cudaSuccess) return fail(h0, QSIM_ERR_CUDA, "batch graph: %s", cudaGetErrorString(ge));
+    }
+    CK(cudaStreamSynchronize(st));
+    // per handle: finish, or grow and re-run from its failed pass
+    qsim_status first_err = QSIM_OK;
+    for (int i = 0; i < count; ++i) {
+        qsim_t hh = handles[i];
+        FlushCtx &fc = fcs[i];
+        if (fc.ns == 0) continue;
+        qsim_status s = read_scalars(hh);
+        if (s == QSIM_OK) {
+            const unsigned err = hh->hscal->err;
+            if (err & qs::ERR_OVERFLOW) {
+                const unsigned failed = hh->hscal->err_sweep - 1u - fc.id0;
+                if (failed >= fc.ns) s = device_error(hh, err);
+                else {
+                    const int outa = (fc.cur0 ^ (int)(failed & 1)) ^ 1;
+                    const unsigned long long need = hh->hscal->bump + hh->hscal->bump / 8 + (1ull << 20);
+                    s = ensure_arena(hh, outa, need);
+                    if (s == QSIM_OK) s = clear_pass_state(hh);
+                    ++fc.regrows;
+                    if (s == QSIM_OK) s = run_from(hh, fc, failed);
+                }
+            } else if (err) {
+                s = device_error(hh, err);
+            }
+        }
+        if (s == QSIM_OK) s = finish_flush(hh, fc, false);
+        if (s != QSIM_OK && first_err == QSIM_OK) first_err = s;
+    }
+    if (first_err != QSIM_OK) g_last_error = "qsim_flush_batch: a handle failed (see its qsim_last_error)";
+    return first_err;
 }
 
 qsim_status qsim_set_profiling(qsim_t h, int on) {

@@ -765,39 +765,72 @@ __device__ __forceinline__ unsigned long long member_tile(unsigned long long T, 
     return T;
 }
 
-// One sweep of Algorithm 2 over all items: decompress (with normalize),
-// apply the gate run, compress with the ladder.  Persistent CTAs loop over
-// items; within an item every warp codes its own tiles.
-__global__ void __launch_bounds__(THREADS, 3) sweep_kernel(SweepParams p) {
+// Sweeps of Algorithm 2 over all items of a work list: entry e of plist is
+// one sweep of one state, owning the global item indices istart[e] ..
+// istart[e+1]-1.  A single-state flush passes a one-entry list; a batch
+// passes one entry per state.  Per item: decompress (with normalize), apply
+// the gate run, compress with the ladder.  Persistent CTAs loop over items;
+// within an item every warp codes its own tiles.  A CTA reloads the
+// parameters and gates whenever it crosses into another entry's items.
+__global__ void __launch_bounds__(THREADS, 3) sweep_kernel(const SweepParams *__restrict__ plist,
+                                                          const unsigned long long *__restrict__ istart,
+                                                          int nlist) {
     extern __shared__ double smem[];
     __shared__ SGate sg[MAX_SWEEP_GATES];
     __shared__ uint32_t stage[64 * NWARPS];
+    __shared__ SweepParams P;
     __shared__ unsigned s_act[2];
-    __shared__ int s_flag;
-    if (threadIdx.x == 0) s_flag = *((volatile unsigned *)&p.scal->err) != 0u;
-    {
-        const uint32_t *src = reinterpret_cast<const uint32_t *>(p.sgates);
-        uint32_t *dst = reinterpret_cast<uint32_t *>(sg);
-        const int words = p.ngates * (int)(sizeof(SGate) / 4);
-        for (int i = threadIdx.x; i < words; i += THREADS) dst[i] = src[i];
-    }
-    __syncthreads();
-    if (s_flag) return;                       // an earlier pass failed: leave the state
-    const int c = p.cc.c, N = 1 << c, mb = c + p.h, ntl = 1 << p.h;
-    double *re = smem, *im = smem + (1 << mb);
-    const double alpha = p.use_alpha ? p.scal->alpha : 1.0;
-    const bool scale = alpha != 1.0;           // one compare per thread and launch
-    int hb[MAX_PAIRS];
-#pragma unroll
-    for (int i = 0; i < MAX_PAIRS; ++i) hb[i] = i < p.h ? p.H[i] - c : 0;
+    __shared__ int s_entry, s_skip;
+    __shared__ double s_alpha;
+    const unsigned long long total = istart[nlist];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *wst = stage + 64 * warp;
-    for (unsigned long long item = blockIdx.x; item < p.nitems; item += gridDim.x) {
-        const unsigned long long T = expand_item(item, p.h, hb);
-        const unsigned long long fixed = T << c;
+    int cur = -1;
+    for (unsigned long long gi = blockIdx.x; gi < total; gi += gridDim.x) {
+        __syncthreads();                  // previous item finished by every warp
+        if (threadIdx.x == 0) {           // entry owning gi: last e with istart[e] <= gi
+            int lo = 0, hi = nlist - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (istart[mid] <= gi) lo = mid; else hi = mid - 1;
+            }
+            s_entry = lo;
+        }
         __syncthreads();
+        const int e = s_entry;
+        if (e != cur) {
+            {
+                const uint32_t *src = reinterpret_cast<const uint32_t *>(plist + e);
+                uint32_t *dst = reinterpret_cast<uint32_t *>(&P);
+                for (int i = threadIdx.x; i < (int)(sizeof(SweepParams) / 4); i += THREADS) dst[i] = src[i];
+            }
+            __syncthreads();
+            {
+                const uint32_t *src = reinterpret_cast<const uint32_t *>(P.sgates);
+                uint32_t *dst = reinterpret_cast<uint32_t *>(sg);
+                const int words = P.ngates * (int)(sizeof(SGate) / 4);
+                for (int i = threadIdx.x; i < words; i += THREADS) dst[i] = src[i];
+            }
+            if (threadIdx.x == 0) {
+                // an earlier pass of this state failed: leave its state alone
+                s_skip = *((volatile unsigned *)&P.scal->err) != 0u;
+                s_alpha = P.use_alpha ? P.scal->alpha : 1.0;
+            }
+            __syncthreads();
+            cur = e;
+        }
+        if (s_skip) continue;
+        const int c = P.cc.c, N = 1 << c, h = P.h, mb = c + h, ntl = 1 << h;
+        double *re = smem, *im = smem + (1 << mb);
+        const double alpha = s_alpha;
+        const bool scale = alpha != 1.0;
+        int hb[MAX_PAIRS];
+#pragma unroll
+        for (int i = 0; i < MAX_PAIRS; ++i) hb[i] = i < h ? P.H[i] - c : 0;
+        const unsigned long long T = expand_item(gi - istart[e], h, hb);
+        const unsigned long long fixed = T << c;
         if (threadIdx.x < 64) {
-            const bool a = (int)threadIdx.x < p.ngates && gate_active(sg[threadIdx.x], fixed);
+            const bool a = (int)threadIdx.x < P.ngates && gate_active(sg[threadIdx.x], fixed);
             const unsigned bal = __ballot_sync(FULL, a);
             if (lane == 0) s_act[warp] = bal;
         }
@@ -805,45 +838,53 @@ __global__ void __launch_bounds__(THREADS, 3) sweep_kernel(SweepParams p) {
         const unsigned long long active = (unsigned long long)s_act[0] | ((unsigned long long)s_act[1] << 32);
         if (!active && !scale) {
             for (int j = warp; j < ntl; j += NWARPS)
-                wcarry(p.in_arena, p.in_table, member_tile(T, j, p.h, hb), p.out_arena, p.out_cap,
-                       p.out_table, p.part, p.scal, p.sweep_id);
-            if (threadIdx.x == 0) atomicAdd(&p.scal->items_skipped, 1ull);
+                wcarry(P.in_arena, P.in_table, member_tile(T, j, h, hb), P.out_arena, P.out_cap,
+                       P.out_table, P.part, P.scal, P.sweep_id);
+            if (threadIdx.x == 0) atomicAdd(&P.scal->items_skipped, 1ull);
             continue;
         }
         int bad = 0;
         for (int j = warp; j < ntl; j += NWARPS) {
-            const unsigned long long Tj = member_tile(T, j, p.h, hb);
-            bad |= wdecode(p.in_arena + p.in_table[Tj], c, re + j * N, im + j * N, alpha, scale);
+            const unsigned long long Tj = member_tile(T, j, h, hb);
+            bad |= wdecode(P.in_arena + P.in_table[Tj], c, re + j * N, im + j * N, alpha, scale);
         }
-        if (bad && lane == 0) atomicOr(&p.scal->err, ERR_FORMAT);
+        if (bad && lane == 0) atomicOr(&P.scal->err, ERR_FORMAT);
         if (active) {
             __syncthreads();
-            apply_gates(re, im, mb, sg, p.gates, p.ngates, active, fixed);
+            apply_gates(re, im, mb, sg, P.gates, P.ngates, active, fixed);
         }
         for (int j = warp; j < ntl; j += NWARPS)
-            wencode(re + j * N, im + j * N, p.cc, member_tile(T, j, p.h, hb), p.out_arena, p.out_cap,
-                    p.out_table, p.part, p.scal, p.sweep_id, wst);
-        if (threadIdx.x == 0) atomicAdd(&p.scal->items_done, 1ull);
+            wencode(re + j * N, im + j * N, P.cc, member_tile(T, j, h, hb), P.out_arena, P.out_cap,
+                    P.out_table, P.part, P.scal, P.sweep_id, wst);
+        if (threadIdx.x == 0) atomicAdd(&P.scal->items_done, 1ull);
     }
 }
 
-// Finish a pass: publish the norm, the next normalize scale and the used
-// bytes; reset the accumulators.  Leaves everything alone after an error
-// so that the host can re-run the failed pass.
-__global__ void finalize_kernel(DevScalars *scal, int use_alpha, unsigned long long *used_hist,
-                                unsigned int slot, int record_used) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Finish a pass of one state: publish the norm, the next normalize scale
+// and the used bytes; reset the accumulators.  Leaves everything alone after
+// an error so that the host can re-run the failed pass.
+__device__ void finalize_state(const FinalizeEntry &f) {
+    DevScalars *scal = f.scal;
     if (scal->err) return;
     scal->norm_lo = scal->acc_lo;
     scal->norm_hi = scal->acc_hi;
     scal->acc_lo = scal->acc_hi = 0;
-    if (record_used) {
+    if (f.record_used) {
         scal->used = scal->bump;
-        if (used_hist) used_hist[slot] = scal->bump;
+        if (f.used_hist) f.used_hist[f.slot] = scal->bump;
         scal->bump = 0;
     }
-    double nrm = units_to_double(scal->norm_lo, scal->norm_hi);
-    scal->alpha = (use_alpha && nrm > 0.0) ? __ddiv_rn(1.0, __dsqrt_rn(nrm)) : 1.0;
+    const double nrm = units_to_double(scal->norm_lo, scal->norm_hi);
+    scal->alpha = (f.use_alpha && nrm > 0.0) ? __ddiv_rn(1.0, __dsqrt_rn(nrm)) : 1.0;
+}
+
+__global__ void finalize_kernel(FinalizeEntry f) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) finalize_state(f);
+}
+
+__global__ void finalize_list_kernel(const FinalizeEntry *list, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        finalize_state(list[i]);
 }
 
 // Per-warp tile kernels: TILE_WARPS warps per CTA, each owning a tile buffer
@@ -1129,14 +1170,21 @@ namespace qs {
 size_t sweep_smem_bytes(int mb) { return (size_t)16 << mb; }
 static size_t tile_smem_bytes(int c, int bufs) { return (size_t)TILE_WARPS * bufs * (16u << c); }
 
-cudaError_t launch_sweep(const SweepParams &p, int grid, cudaStream_t st) {
-    sweep_kernel<<<grid, THREADS, sweep_smem_bytes(p.cc.c + p.h), st>>>(p);
+cudaError_t launch_sweep(const SweepParams *plist, const unsigned long long *istart, int nlist,
+                         int mb, int grid, cudaStream_t st) {
+    sweep_kernel<<<grid, THREADS, sweep_smem_bytes(mb), st>>>(plist, istart, nlist);
     return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(DevScalars *scal, int use_alpha, unsigned long long *used_hist,
                             unsigned slot, int record_used, cudaStream_t st) {
-    finalize_kernel<<<1, 32, 0, st>>>(scal, use_alpha, used_hist, slot, record_used);
+    FinalizeEntry f{scal, used_hist, slot, use_alpha, record_used};
+    finalize_kernel<<<1, 32, 0, st>>>(f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_list(const FinalizeEntry *list, int n, cudaStream_t st) {
+    finalize_list_kernel<<<(n + 127) / 128, 128, 0, st>>>(list, n);
     return cudaGetLastError();
 }
 

@@ -105,6 +105,15 @@ struct SweepParams {
     int use_alpha;
 };
 
+// End-of-pass bookkeeping of one state (norm, scale, used bytes).
+struct FinalizeEntry {
+    DevScalars *scal;
+    unsigned long long *used_hist;   // per-sweep used bytes (may be null)
+    unsigned slot;
+    int use_alpha;
+    int record_used;
+};
+
 // Four FP64 sums of a fidelity pass: Re<ref|psi>, Im<ref|psi>, <psi|psi>, <ref|ref>.
 struct __align__(16) Acc4 {
     double x, y, z, w;

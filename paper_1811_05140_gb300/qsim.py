@@ -26,7 +26,7 @@ EXPORTS = ["qsim_create", "qsim_destroy", "qsim_set_stream", "qsim_set_aalc", "q
            "qsim_flush", "qsim_probabilities", "qsim_amplitudes", "qsim_fidelity",
            "qsim_compressed_bytes", "qsim_stats", "qsim_last_error", "qsim_export_tiles",
            "qsim_import_tiles", "qsim_plan_sweeps", "qsim_version", "qsim_set_profiling",
-           "qsim_profile", "qsim_encode_noalloc"]
+           "qsim_profile", "qsim_encode_noalloc", "qsim_flush_batch"]
 
 
 class QsimError(RuntimeError):
@@ -83,6 +83,7 @@ def load() -> C.CDLL:
         "qsim_set_amplitudes": ([vp, dp], C.c_int),
         "qsim_apply_gate": ([vp, dp, ip, C.c_int, ip, C.c_int, u64], C.c_int),
         "qsim_flush": ([vp], C.c_int),
+        "qsim_flush_batch": ([C.POINTER(vp), C.c_int, C.c_int], C.c_int),
         "qsim_probabilities": ([vp, ip, C.c_int, dp], C.c_int),
         "qsim_amplitudes": ([vp, u64, u64, dp], C.c_int),
         "qsim_fidelity": ([vp, C.POINTER(Ref), dp, dp], C.c_int),
@@ -158,6 +159,16 @@ def encode_noalloc(dev_amps: int, n: int, tile_log2: int, eps: float, dev_out: i
     if st != 0:
         raise QsimError(st, L.qsim_last_error(None).decode())
     return used.value
+
+
+def flush_batch(states, use_graph: bool = False):
+    """Flush several states together (qsim_flush_batch)."""
+    L = load()
+    arr = (C.c_void_p * len(states))(*[s.h for s in states])
+    st = L.qsim_flush_batch(arr, len(states), int(bool(use_graph)))
+    if st != 0:
+        msgs = [s._L.qsim_last_error(s.h).decode() for s in states]
+        raise QsimError(st, "; ".join(m for m in msgs if m) or L.qsim_last_error(None).decode())
 
 
 class State:
