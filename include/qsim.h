@@ -321,6 +321,89 @@ qsim_status qsim_encode_noalloc(const double *dev_amps, int n_qubits, int tile_l
                                 unsigned long long *dev_table, unsigned long long *stream_bytes,
                                 void *cuda_stream);
 
+/* ------------------------------------------------------------------ */
+/* Serving: continuous batching of many circuits on one GPU            */
+/* ------------------------------------------------------------------ */
+
+/* One gate of a request, fixed size; controls as masks over qubit bits. */
+typedef struct {
+    int n_targets;                      /* 1 or 2 */
+    int targets[2];
+    int pad;
+    unsigned long long control_mask;    /* bit q set: qubit q is a control */
+    unsigned long long control_values;  /* bit q: required value of control q */
+    double matrix[32];                  /* 2^k x 2^k complex, row-major, (re, im) */
+} qsim_gate_rec;
+
+/* One circuit to run: state |basis> of n_qubits, the gates in order, and
+ * the qubits whose outcome probabilities are read out at the end. */
+typedef struct {
+    int n_qubits;
+    int block_log2;
+    int codec;                          /* qsim_codec */
+    int n_readout;                      /* 0..16 */
+    double rel_err_bound;
+    double theta;                       /* AALC threshold; 0 keeps the default ladder */
+    unsigned long long basis;
+    const qsim_gate_rec *gates;         /* copied by qsim_server_submit */
+    int n_gates;
+    int readout[16];
+} qsim_request;
+
+typedef struct {
+    int done;                           /* 1 once finished (or failed) */
+    int status;                         /* QSIM_OK or the failing code */
+    double submit_s, admit_s, finish_s; /* seconds since the server started */
+    unsigned long long stream_bytes;    /* final compressed size */
+    unsigned long long peak_footprint;  /* device bytes the circuit held at its peak */
+} qsim_ticket_info;
+
+typedef struct {
+    unsigned long long submitted, completed, failed, ticks;
+    unsigned long long peak_footprint;  /* device bytes of resident circuits, peak */
+    unsigned long long budget;
+    double busy_s;                      /* time spent in ticks */
+    double p50_latency_s, p99_latency_s, mean_latency_s;
+    double throughput_cps;              /* completed circuits / (last finish - first submit) */
+    int max_resident_seen;
+} qsim_server_stats_t;
+
+typedef struct qsim_server *qsim_server_t;
+
+/*
+ * qsim_server_create -- start a serving loop on the current device (one
+ * host thread and one CUDA stream of its own).  A waiting circuit is
+ * admitted while the measured device footprint of the resident circuits
+ * plus the newcomer's initial footprint stays within three quarters of
+ * mem_budget_bytes (the rest is headroom for growth) and fewer than
+ * max_resident circuits run.  Each tick applies the next sweeps_per_tick
+ * sweeps of every resident circuit (cut at the circuit's own sweep
+ * boundaries, qsim_plan_sweeps) as one batched flush
+ * (qsim_flush_batch, CUDA-graph captured when use_graph), so newcomers join
+ * at the next tick.  Results are identical to running each circuit alone.
+ */
+qsim_status qsim_server_create(qsim_server_t *out, unsigned long long mem_budget_bytes, int max_resident,
+                               int sweeps_per_tick, int use_graph);
+
+/* qsim_server_submit -- queue a circuit (copied); *ticket identifies it. */
+qsim_status qsim_server_submit(qsim_server_t s, const qsim_request *req, unsigned long long *ticket);
+
+/* qsim_server_result -- status of a ticket; once done, probs (host,
+ * 2^n_readout doubles, may be NULL) receives the read-out probabilities. */
+qsim_status qsim_server_result(qsim_server_t s, unsigned long long ticket, qsim_ticket_info *info,
+                               double *probs);
+
+/* qsim_server_wait / qsim_server_drain -- block until the ticket / every
+ * submitted circuit is done, or timeout_s passes (QSIM_ERR_TIMEOUT). */
+qsim_status qsim_server_wait(qsim_server_t s, unsigned long long ticket, double timeout_s);
+qsim_status qsim_server_drain(qsim_server_t s, double timeout_s);
+
+/* qsim_server_stats -- counters, p50/p99 latency, throughput. */
+qsim_status qsim_server_stats(qsim_server_t s, qsim_server_stats_t *out);
+
+/* qsim_server_destroy -- finish the queued circuits, stop, release all. */
+qsim_status qsim_server_destroy(qsim_server_t s);
+
 /* qsim_version -- library version string. */
 const char *qsim_version(void);
 

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libqsim.so")
 BUILD = os.path.join(ROOT, "_build")
 
-SOURCES = ["kernels.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["kernels.cu", "api.cu", "noalloc.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC,-O2",
            "-I" + INCLUDE, "-I" + CSRC]

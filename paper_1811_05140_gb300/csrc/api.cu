@@ -193,6 +193,8 @@ double gate_dp_ops(const HostGate &g, int n) {
 
 void qs::set_global_error(const char *msg) { g_last_error = msg; }
 
+unsigned long long qs_handle_footprint(qsim_t h);
+
 struct qsim_state {
     int n = 0, c = 0, hmax = 2, depth = qs::MAX_SWEEP_GATES;
     qsim_codec codec = QSIM_CODEC_REL;
@@ -440,6 +442,11 @@ void prepare_gate(const HostGate &g, int c, const Sweep &sw, qs::DGate &d, qs::S
 }
 
 }  // namespace
+
+// device bytes held by a state: both arenas, tile tables, norm partials
+unsigned long long qs_handle_footprint(qsim_t h) {
+    return h ? h->cap[0] + h->cap[1] + h->ntiles * 32ull : 0ull;
+}
 
 extern "C" {
 

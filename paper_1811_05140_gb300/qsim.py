@@ -26,7 +26,9 @@ EXPORTS = ["qsim_create", "qsim_destroy", "qsim_set_stream", "qsim_set_aalc", "q
            "qsim_flush", "qsim_probabilities", "qsim_amplitudes", "qsim_fidelity",
            "qsim_compressed_bytes", "qsim_stats", "qsim_last_error", "qsim_export_tiles",
            "qsim_import_tiles", "qsim_plan_sweeps", "qsim_version", "qsim_set_profiling",
-           "qsim_profile", "qsim_encode_noalloc", "qsim_flush_batch"]
+           "qsim_profile", "qsim_encode_noalloc", "qsim_flush_batch", "qsim_server_create",
+           "qsim_server_submit", "qsim_server_result", "qsim_server_wait", "qsim_server_drain",
+           "qsim_server_stats", "qsim_server_destroy"]
 
 
 class QsimError(RuntimeError):
@@ -58,6 +60,34 @@ class Profile(C.Structure):
                 ("kernel_launches", C.c_ulonglong)]
 
 
+class GateRec(C.Structure):
+    _fields_ = [("n_targets", C.c_int), ("targets", C.c_int * 2), ("pad", C.c_int),
+                ("control_mask", C.c_ulonglong), ("control_values", C.c_ulonglong),
+                ("matrix", C.c_double * 32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("n_qubits", C.c_int), ("block_log2", C.c_int), ("codec", C.c_int),
+                ("n_readout", C.c_int), ("rel_err_bound", C.c_double), ("theta", C.c_double),
+                ("basis", C.c_ulonglong), ("gates", C.POINTER(GateRec)), ("n_gates", C.c_int),
+                ("readout", C.c_int * 16)]
+
+
+class TicketInfo(C.Structure):
+    _fields_ = [("done", C.c_int), ("status", C.c_int), ("submit_s", C.c_double),
+                ("admit_s", C.c_double), ("finish_s", C.c_double),
+                ("stream_bytes", C.c_ulonglong), ("peak_footprint", C.c_ulonglong)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_ulonglong), ("completed", C.c_ulonglong),
+                ("failed", C.c_ulonglong), ("ticks", C.c_ulonglong),
+                ("peak_footprint", C.c_ulonglong), ("budget", C.c_ulonglong),
+                ("busy_s", C.c_double), ("p50_latency_s", C.c_double),
+                ("p99_latency_s", C.c_double), ("mean_latency_s", C.c_double),
+                ("throughput_cps", C.c_double), ("max_resident_seen", C.c_int)]
+
+
 _lib = None
 
 
@@ -84,6 +114,13 @@ def load() -> C.CDLL:
         "qsim_apply_gate": ([vp, dp, ip, C.c_int, ip, C.c_int, u64], C.c_int),
         "qsim_flush": ([vp], C.c_int),
         "qsim_flush_batch": ([C.POINTER(vp), C.c_int, C.c_int], C.c_int),
+        "qsim_server_create": ([C.POINTER(vp), u64, C.c_int, C.c_int, C.c_int], C.c_int),
+        "qsim_server_submit": ([vp, C.POINTER(Request), u64p], C.c_int),
+        "qsim_server_result": ([vp, u64, C.POINTER(TicketInfo), dp], C.c_int),
+        "qsim_server_wait": ([vp, u64, C.c_double], C.c_int),
+        "qsim_server_drain": ([vp, C.c_double], C.c_int),
+        "qsim_server_stats": ([vp, C.POINTER(ServerStats)], C.c_int),
+        "qsim_server_destroy": ([vp], C.c_int),
         "qsim_probabilities": ([vp, ip, C.c_int, dp], C.c_int),
         "qsim_amplitudes": ([vp, u64, u64, dp], C.c_int),
         "qsim_fidelity": ([vp, C.POINTER(Ref), dp, dp], C.c_int),
@@ -323,3 +360,83 @@ class State:
         sizes = (C.c_ulonglong * max(1, len(streams)))(*[len(s) for s in streams])
         buf = (C.c_uint8 * max(1, len(data))).from_buffer_copy(data) if data else (C.c_uint8 * 1)()
         self._check(self._L.qsim_import_tiles(self.h, first, len(streams), buf, sizes))
+
+
+def gate_rec(g: inputs.Gate) -> GateRec:
+    r = GateRec()
+    r.n_targets = len(g.targets)
+    for i, t in enumerate(g.targets):
+        r.targets[i] = t
+    r.control_mask, r.control_values = g.masks()
+    m = np.asarray(g.matrix, dtype=np.complex128).reshape(-1)
+    for i, v in enumerate(m):
+        r.matrix[2 * i] = v.real
+        r.matrix[2 * i + 1] = v.imag
+    return r
+
+
+class Server:
+    """Continuous-batching serving loop (qsim_server_*)."""
+
+    def __init__(self, mem_budget_bytes: int, max_resident: int = 64, sweeps_per_tick: int = 4,
+                 use_graph: bool = False):
+        self._L = load()
+        h = C.c_void_p()
+        st = self._L.qsim_server_create(C.byref(h), mem_budget_bytes, max_resident, sweeps_per_tick,
+                                        int(bool(use_graph)))
+        if st != 0:
+            raise QsimError(st, "qsim_server_create failed")
+        self.h = h
+        self.readout = {}
+
+    def submit(self, n: int, gates, block_log2: int = 8, codec: str = "rel", eps: float = 1e-4,
+               basis: int = 0, readout=(), theta: float = 0.0) -> int:
+        arr = (GateRec * max(1, len(gates)))(*[gate_rec(g) for g in gates])
+        req = Request()
+        req.n_qubits, req.block_log2, req.codec = n, block_log2, CODECS[codec]
+        req.n_readout = len(readout)
+        req.rel_err_bound, req.theta, req.basis = eps, theta, basis
+        req.gates, req.n_gates = arr, len(gates)
+        for i, q in enumerate(readout):
+            req.readout[i] = q
+        t = C.c_ulonglong()
+        st = self._L.qsim_server_submit(self.h, C.byref(req), C.byref(t))
+        if st != 0:
+            raise QsimError(st, "qsim_server_submit failed")
+        self.readout[t.value] = len(readout)
+        return t.value
+
+    def result(self, ticket: int):
+        info = TicketInfo()
+        probs = np.zeros(1 << self.readout[ticket])
+        st = self._L.qsim_server_result(self.h, ticket, C.byref(info), probs.ctypes.data_as(C.POINTER(C.c_double)))
+        if st != 0:
+            raise QsimError(st, "qsim_server_result failed")
+        d = {f: getattr(info, f) for f, _ in TicketInfo._fields_}
+        return d, probs
+
+    def wait(self, ticket: int, timeout: float = 600.0):
+        st = self._L.qsim_server_wait(self.h, ticket, timeout)
+        if st != 0:
+            raise QsimError(st, "qsim_server_wait timed out")
+
+    def drain(self, timeout: float = 3600.0):
+        st = self._L.qsim_server_drain(self.h, timeout)
+        if st != 0:
+            raise QsimError(st, "qsim_server_drain timed out")
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        self._L.qsim_server_stats(self.h, C.byref(s))
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.qsim_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
