@@ -51,6 +51,13 @@ def parse_args():
     ap.add_argument("--depth", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip bound sweep / AALC / e2e")
+    ap.add_argument("--workload", choices=["qft28", "serving"], default="qft28")
+    ap.add_argument("--requests", type=int, default=2000, help="serving: circuits")
+    ap.add_argument("--nmin", type=int, default=10, help="serving: smallest qubit count")
+    ap.add_argument("--nmax", type=int, default=30, help="serving: largest qubit count")
+    ap.add_argument("--alone", type=int, default=0, help="serving: circuits timed one at a time (0 = all)")
+    ap.add_argument("--rate-factor", type=float, default=1.5, help="serving: arrival rate / one-at-a-time capacity")
+    ap.add_argument("--tune", action="store_true", help="serving: autotuned schedule per (n, class)")
     return ap.parse_args()
 
 
@@ -275,6 +282,119 @@ def run_ours(args, rank, world, local_rank):
     return result
 
 
+# ------------------------------------------------------------------ serving mix
+def serving_requests(count, nmin, nmax, seed):
+    """The serving mix: 40% QFT on a random basis state, 30% Grover (2-6
+    iterations), 30% random grid (depth 8-20); n uniform in [nmin, nmax];
+    relative bound 1e-3 or 1e-4; three read-out qubits."""
+    from paper_1811_05140_gb300 import inputs as I
+    rng = I.Rng(seed)
+    reqs = []
+    cache = {}
+    for _ in range(count):
+        n = nmin + rng.below(nmax - nmin + 1)
+        u = rng.below(10)
+        eps = (1e-3, 1e-4)[rng.below(2)]
+        if u < 4:
+            cls = "qft"
+            if ("qft", n) not in cache:
+                cache[("qft", n)] = I.qft(n)
+            gates, x = cache[("qft", n)], rng.below(1 << n)
+        elif u < 7:
+            cls = "grover"
+            gates, x = I.grover(n, rng.below(1 << n), 2 + rng.below(5)), 0
+        else:
+            cls = "grid"
+            r, c = I.grid_shape(n)
+            gates, x = I.random_grid(r, c, 8 + rng.below(13), rng.next()), 0
+        readout = list(dict.fromkeys(rng.below(n) for _ in range(3)))
+        reqs.append({"n": n, "cls": cls, "gates": gates, "x": x, "eps": eps, "readout": readout})
+    return reqs
+
+
+def run_serving(args):
+    import numpy as np
+    import torch
+
+    from paper_1811_05140_gb300 import build as B
+    from paper_1811_05140_gb300 import inputs as I
+    from paper_1811_05140_gb300 import qsim
+
+    B.build()
+    torch.cuda.set_device(0)
+    reqs = serving_requests(args.requests, args.nmin, args.nmax, I.BASE_SEED + 5)
+    sched = {}
+    if args.tune:
+        from paper_1811_05140_gb300 import autotune
+        tuner = autotune.Tuner(reps=1)
+        for q in reqs:
+            key = (q["n"], q["cls"], q["eps"])
+            if key not in sched:
+                sched[key] = tuner.schedule(q["n"], q["cls"], q["gates"], "rel", q["eps"], q["x"])
+    # one circuit at a time through the same library (create, run, read out, free)
+    n_alone = len(reqs) if args.alone <= 0 else min(args.alone, len(reqs))
+    alone_probs = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for q in reqs[:n_alone]:
+        st = qsim.State(q["n"], 8, "rel", q["eps"])
+        sc = sched.get((q["n"], q["cls"], q["eps"]))
+        if sc:
+            st.set_schedule(*sc)
+        st.reset_basis(q["x"])
+        st.apply_all(q["gates"])
+        alone_probs.append(st.probabilities(q["readout"]))
+        st.close()
+    alone_s = time.perf_counter() - t0
+    cps_alone = n_alone / alone_s
+    free, total = torch.cuda.mem_get_info()
+    budget = int(free * 0.8)
+
+    def serve(arrival_rate):
+        srv = qsim.Server(budget, max_resident=64, sweeps_per_tick=2)
+        rng = I.Rng(I.BASE_SEED + 9)
+        tickets = []
+        t_start = time.perf_counter()
+        next_t = 0.0
+        for q in reqs:
+            if arrival_rate:
+                next_t += -np.log(1.0 - rng.uniform()) / arrival_rate
+                dt = next_t - (time.perf_counter() - t_start)
+                if dt > 0:
+                    time.sleep(dt)
+            tickets.append(srv.submit(q["n"], q["gates"], eps=q["eps"], basis=q["x"], readout=q["readout"],
+                                      schedule=sched.get((q["n"], q["cls"], q["eps"]))))
+        srv.drain(36000)
+        st = srv.stats()
+        same = all(np.array_equal(srv.result(t)[1], p) for t, p in zip(tickets, alone_probs))
+        srv.close()
+        return st, same
+
+    sat, same_sat = serve(0.0)                       # everything queued at once
+    lam = args.rate_factor * cps_alone
+    poi, same_poi = serve(lam)                       # Poisson arrivals
+    raw = sum(16 << q["n"] for q in reqs)
+    line = {
+        "metric": "circuits/s + p99 latency (serving mix)", "value": sat["throughput_cps"],
+        "unit": "circuits/s", "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "serving_mix", "requests": len(reqs), "n_range": [args.nmin, args.nmax],
+                   "mix": "40% QFT / 30% Grover 2-6 it / 30% random grid depth 8-20",
+                   "bounds": [1e-3, 1e-4], "tuned_schedules": bool(args.tune),
+                   "budget_bytes": budget},
+        "one_at_a_time_cps": cps_alone, "one_at_a_time_circuits": n_alone,
+        "saturated": {"cps": sat["throughput_cps"], "p50_s": sat["p50_latency_s"], "p99_s": sat["p99_latency_s"],
+                      "peak_footprint": sat["peak_footprint"], "max_resident": sat["max_resident_seen"],
+                      "ticks": sat["ticks"], "same_as_alone": same_sat},
+        "poisson": {"rate_cps": lam, "cps": poi["throughput_cps"], "p50_s": poi["p50_latency_s"],
+                    "p99_s": poi["p99_latency_s"], "peak_footprint": poi["peak_footprint"],
+                    "max_resident": poi["max_resident_seen"], "same_as_alone": same_poi},
+        "speedup_vs_one_at_a_time": sat["throughput_cps"] / cps_alone,
+        "uncompressed_bytes_all_circuits": raw,
+    }
+    print(json.dumps(line))
+
+
 def run_reference(args):
     """The oracle as the reference arm: each step times a bounded sample."""
     from paper_1811_05140_gb300 import inputs as I
@@ -310,6 +430,10 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             run_reference(args)
+        return
+    if args.workload == "serving":
+        if rank == 0:
+            run_serving(args)
         return
     import torch
     if world > 1:

@@ -348,6 +348,7 @@ typedef struct {
     const qsim_gate_rec *gates;         /* copied by qsim_server_submit */
     int n_gates;
     int readout[16];
+    int tile_log2, hmax, depth;         /* schedule (qsim_set_schedule); 0 = default */
 } qsim_request;
 
 typedef struct {

@@ -80,7 +80,7 @@ namespace {
 
 // initial device bytes of a fresh state (tables, norm partials, two arenas)
 unsigned long long initial_footprint(const qsim_request &r) {
-    int c = std::min(std::min(r.block_log2, r.n_qubits), 8);
+    int c = r.tile_log2 ? r.tile_log2 : std::min(std::min(r.block_log2, r.n_qubits), 8);
     unsigned long long ntiles = 1ull << (r.n_qubits - c);
     unsigned long long tile = 32ull + (16ull << c);
     unsigned long long a0 = ntiles * 32ull + tile;
@@ -127,6 +127,13 @@ int admit(qsim_server *S, Req *q) {
         for (double e : lad)
             if (e <= r.rel_err_bound * (1 + 1e-12)) lv[nl++] = e;
         if ((st = qsim_set_aalc(q->h, r.theta, lv, nl)) != QSIM_OK) return st;
+    }
+    if (r.tile_log2 || r.hmax || r.depth) {
+        qsim_stats_t d;
+        if ((st = qsim_stats(q->h, &d)) != QSIM_OK) return st;
+        st = qsim_set_schedule(q->h, r.tile_log2 ? r.tile_log2 : d.tile_log2, r.hmax ? r.hmax : d.hmax,
+                               r.depth ? r.depth : d.depth);
+        if (st != QSIM_OK) return st;
     }
     if (r.basis && (st = qsim_reset_basis(q->h, r.basis)) != QSIM_OK) return st;
     // the circuit's own sweep partition: ticks cut only at sweep boundaries,

@@ -70,7 +70,8 @@ class Request(C.Structure):
     _fields_ = [("n_qubits", C.c_int), ("block_log2", C.c_int), ("codec", C.c_int),
                 ("n_readout", C.c_int), ("rel_err_bound", C.c_double), ("theta", C.c_double),
                 ("basis", C.c_ulonglong), ("gates", C.POINTER(GateRec)), ("n_gates", C.c_int),
-                ("readout", C.c_int * 16)]
+                ("readout", C.c_int * 16), ("tile_log2", C.c_int), ("hmax", C.c_int),
+                ("depth", C.c_int)]
 
 
 class TicketInfo(C.Structure):
@@ -390,7 +391,7 @@ class Server:
         self.readout = {}
 
     def submit(self, n: int, gates, block_log2: int = 8, codec: str = "rel", eps: float = 1e-4,
-               basis: int = 0, readout=(), theta: float = 0.0) -> int:
+               basis: int = 0, readout=(), theta: float = 0.0, schedule=None) -> int:
         arr = (GateRec * max(1, len(gates)))(*[gate_rec(g) for g in gates])
         req = Request()
         req.n_qubits, req.block_log2, req.codec = n, block_log2, CODECS[codec]
@@ -399,6 +400,8 @@ class Server:
         req.gates, req.n_gates = arr, len(gates)
         for i, q in enumerate(readout):
             req.readout[i] = q
+        if schedule:
+            req.tile_log2, req.hmax, req.depth = schedule
         t = C.c_ulonglong()
         st = self._L.qsim_server_submit(self.h, C.byref(req), C.byref(t))
         if st != 0:

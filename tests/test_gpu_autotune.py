@@ -1,0 +1,37 @@
+"""Autotuner: picks a valid schedule by timing, and a circuit run under the
+chosen schedule still matches the oracle run with that partition."""
+import pytest
+
+import oracle
+from paper_1811_05140_gb300 import autotune
+from paper_1811_05140_gb300 import inputs as I
+from paper_1811_05140_gb300 import qsim
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1811_05140_gb300 import build
+    build.build()
+
+
+def test_tuned_schedule_is_valid_and_exact():
+    n = 12
+    gates = I.qft(n)
+    x = I.seeded_basis(n)
+    res = autotune.tune(n, gates, "rel", 1e-4, x, reps=1)
+    c, hmax, depth = res["best"]
+    assert autotune.valid(n, c, hmax) and len(res["table"]) >= 3
+    assert all(r["seconds"] > 0 for r in res["table"])
+    st = qsim.State(n, 20, "rel", 1e-4)
+    st.set_schedule(c, hmax, depth)
+    st.reset_basis(x)
+    st.apply_all(gates)
+    st.flush()
+    cs = oracle.CSim(n, c, [oracle.shift_for_eps(1e-4)], None, True)
+    cs.reset_basis(x)
+    cs.run(gates, hmax, depth)
+    assert all(s == cs.stream(t) for t, s in enumerate(st.export_tiles()))
+    tuner = autotune.Tuner(reps=1)
+    assert tuner.schedule(n, "qft", gates, "rel", 1e-4, x) == tuner.schedule(n, "qft", gates, "rel", 1e-4, x)
