@@ -83,6 +83,11 @@ def lib():
         L.or_csim_sweep_sample.argtypes = [C.c_void_p, C.POINTER(OrGate), C.c_int, ip, C.c_int,
                                            C.c_uint64, C.c_uint64]
         L.or_csim_sweep_sample.restype = C.c_int
+        L.or_item_sweep.argtypes = [C.c_int, C.c_int, ip, C.c_int, C.c_uint64,
+                                    C.POINTER(C.c_void_p), C.POINTER(C.c_uint32), C.c_double,
+                                    C.POINTER(OrGate), C.c_int, ip, C.c_int, C.c_uint64, u8p,
+                                    C.c_size_t, C.POINTER(C.c_uint32)]
+        L.or_item_sweep.restype = C.c_int
         L.or_csim_dense.argtypes = [C.c_void_p, dp]
         L.or_csim_dense.restype = C.c_int
         L.or_csim_stream.argtypes = [C.c_void_p, C.c_uint64, u8p, C.c_uint32]
@@ -207,6 +212,35 @@ def decode_tile(stream: bytes, c: int) -> np.ndarray:
     if rc != 0:
         raise ValueError(f"malformed stream ({rc})")
     return a
+
+
+def item_sweep(n: int, c: int, H, base_tile: int, streams, alpha: float, gates, shifts,
+               max_bytes: int | None = None):
+    """One item of a sweep on its own (sampled checks of large states):
+    member j is tile base_tile | bits of j at H; returns the new streams."""
+    H = sorted(H)
+    h = len(H)
+    assert len(streams) == 1 << h
+    bufs = [(C.c_uint8 * len(st)).from_buffer_copy(st) for st in streams]
+    ptrs = (C.c_void_p * len(bufs))(*[C.addressof(b) for b in bufs])
+    lens = (C.c_uint32 * len(bufs))(*[len(st) for st in streams])
+    hh = (C.c_int * max(1, h))(*H)
+    sh = (C.c_int * len(shifts))(*shifts)
+    cap = len(streams) * lib().or_stream_cap(c)
+    out = (C.c_uint8 * cap)()
+    out_len = (C.c_uint32 * len(streams))()
+    arr = gate_array(gates)
+    mb = (1 << 64) - 1 if max_bytes is None else max_bytes
+    rc = lib().or_item_sweep(n, c, hh, h, base_tile, ptrs, lens, alpha, arr, len(gates), sh,
+                             len(shifts), mb, out, cap, out_len)
+    if rc != 0:
+        raise RuntimeError(f"oracle item sweep failed ({rc})")
+    res, off = [], 0
+    raw = bytes(out)
+    for j in range(len(streams)):
+        res.append(raw[off:off + out_len[j]])
+        off += out_len[j]
+    return res
 
 
 # ---------------------------------------------------------------- O3

@@ -801,6 +801,65 @@ static int csim_sweep_items(or_csim *cs, const or_gate *g, int ng, const int *H,
     return rc;
 }
 
+/*
+ * One item of a sweep on its own, for sampled checks of states too large
+ * for the oracle: in[j] (in_len[j] bytes) is the stream of member j, the
+ * tile base_tile | (bits of j at the positions H[i]-c); alpha is the
+ * normalize scale of the pass.  Applies the same steps as or_csim_sweep to
+ * this item (kept as it is when alpha is 1 and no gate touches it) and
+ * writes the members' new streams, concatenated, to out (out_len[j] each).
+ * Returns 0, -1 on a malformed stream, -2 on a gate outside the item, -3
+ * when out is too small.
+ */
+int or_item_sweep(int n, int c, const int *H, int h, uint64_t base_tile,
+                  const uint8_t *const *in, const uint32_t *in_len, double alpha,
+                  const or_gate *g, int ng, const int *shifts, int nlev, uint64_t max_bytes,
+                  uint8_t *out, size_t out_cap, uint32_t *out_len)
+{
+    uint64_t N = 1ull << c;
+    int mb = c + h;
+    int qb[64];
+    for (int p = 0; p < c; ++p) qb[p] = p;
+    for (int i = 0; i < h; ++i) qb[c + i] = H[i];
+    uint64_t fmask = 0;
+    for (int q = c; q < n; ++q) fmask |= 1ull << q;
+    for (int i = 0; i < h; ++i) fmask &= ~(1ull << H[i]);
+    uint64_t fixed = base_tile << c;
+    int touched = alpha != 1.0;
+    for (int i = 0; i < ng && !touched; ++i)
+        if (gate_touches(&g[i], fixed, fmask)) touched = 1;
+    size_t used = 0;
+    if (!touched) {
+        for (uint64_t j = 0; j < (1ull << h); ++j) {
+            if (used + in_len[j] > out_cap) return -3;
+            memcpy(out + used, in[j], in_len[j]);
+            out_len[j] = in_len[j];
+            used += in_len[j];
+        }
+        return 0;
+    }
+    double *buf = malloc(((size_t)1 << mb) * 16);
+    uint8_t *tmp = malloc(or_stream_cap(c));
+    int rc = 0;
+    for (uint64_t j = 0; j < (1ull << h) && rc == 0; ++j)
+        if (or_decode_tile(in[j], in_len[j], c, buf + 2 * j * N) != 0) rc = -1;
+    if (rc == 0 && alpha != 1.0)
+        for (uint64_t i = 0; i < 2 * ((uint64_t)1 << mb); ++i) buf[i] = buf[i] * alpha;
+    for (int i = 0; i < ng && rc == 0; ++i)
+        if (apply_gate_buf(buf, mb, qb, fixed, &g[i]) != 0) rc = -2;
+    for (uint64_t j = 0; j < (1ull << h) && rc == 0; ++j) {
+        int level = 0, flags = 0;
+        size_t len = or_encode_tile(buf + 2 * j * N, c, shifts, nlev, max_bytes, tmp, &level, &flags);
+        if (used + len > out_cap) { rc = -3; break; }
+        memcpy(out + used, tmp, len);
+        out_len[j] = (uint32_t)len;
+        used += len;
+    }
+    free(buf);
+    free(tmp);
+    return rc;
+}
+
 /* decode every tile into a dense vector (the stored state, unscaled) */
 int or_csim_dense(const or_csim *cs, double *out)
 {
