@@ -29,21 +29,33 @@
  *   stream of N = 2^c doubles cut into G = max(1, N/32) groups of
  *   L = min(N, 32) values.  Header (32 bytes, little-endian):
  *     [0] mode 0 CONST / 1 PACKED / 2 RAW   [1] shift s (0..52, 0 for RAW)
- *     [2] ladder level                       [3] sign modes (re bits 0-1, im 2-3)
- *     [4..7] body bytes (multiple of 16)     [8..15] anchor q_0 of re
- *     [16..23] anchor q_0 of im              [24] c   [25..31] zero
+ *     [2] ladder level                       [3] sign modes (re bits 0-2,
+ *                                                im 3-5; 0 for RAW)
+ *     [4..7] body bytes (multiple of 16)     [8..15] anchor of re
+ *     [16..23] anchor of im                  [24] c
+ *     [25] zero modes (re bits 0-2, im 3-5; PACKED only, else 0)
+ *     [26..31] zero
  *   Codes: B = magnitude bits of x, q = (B + 2^(s-1)) >> s (q = B at s = 0);
- *   reconstruction (q << s) with the sign bit.  Residuals r_0 = 0,
- *   r_i = q_i - q_{i-1} mod 2^64, zigzag z, group width = bit length of the
- *   OR of its z.  Sign modes: 0 all clear, 1 all set, 2 pattern (u32 P,
- *   then ceil(G/32) u32 flip words), 3 one u32 word per group.
- *   PACKED body: re signs, im signs, G width bytes (re), G (im), zero pad
- *   to 4, then per component and group ceil(L*w/32) u32 words with value l
- *   at bits [l*w, (l+1)*w); zero pad to 16.  RAW body: 2N doubles.
- *   CONST when every z is 0 and signs are uniform; else PACKED when shorter
- *   than RAW; else RAW.  The relative error of a component is below
- *   2^(s-53) (Sec. III error bound, made point-wise relative as in the
- *   paper's ref. [xin2018]).
+ *   reconstruction (q << s) with the sign bit.  q = 0 only for x = +-0
+ *   (other values below the lossy range force s = 0); at s > 0 a zero's
+ *   sign is stored as 0.  Anchor = first nonzero code (0 if none).
+ *   Residuals run along the nonzero codes: r = q - previous nonzero code
+ *   (the anchor for the first) mod 2^64, zigzag z, group width = bit
+ *   length of the OR of the z of its nonzero values.
+ *   Word sections (sign words; zero words, bit l set when value l is a
+ *   zero), modes: 0 all words 0, 1 all words all-set, 2 / 3 exceptions to
+ *   0 / to all-set (ceil(G/32) u32 bitmap words, bit g set when word g
+ *   differs, then the differing words in group order), 4 one u32 word per
+ *   group.  The encoder takes 0 or 1 when it applies, else the shortest of
+ *   2, 3, 4, the lower on a tie.
+ *   PACKED body: re signs, im signs, re zeros, im zeros, G width bytes
+ *   (re), G (im), zero pad to 4, then per component and group
+ *   ceil(nz*w/32) u32 words (nz nonzero values) with the k-th nonzero value
+ *   at bits [k*w, (k+1)*w); zero pad to 16.  RAW body: 2N doubles.
+ *   CONST when every z is 0 and every sign and zero mode is 0 or 1; else
+ *   PACKED when shorter than RAW; else RAW.  The relative error of a
+ *   component is below 2^(s-53) (Sec. III error bound, made point-wise
+ *   relative as in the paper's ref. [xin2018]).
  */
 #ifndef QSIM_H
 #define QSIM_H

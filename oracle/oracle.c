@@ -24,7 +24,9 @@
  *   - a matrix row is evaluated over its exactly-nonzero entries in column
  *     order; the first term is a product, later terms are fused
  *     multiply-adds; an entry with zero imaginary part is "real", one with
- *     zero real part "imaginary", any other "general" (see row_eval);
+ *     zero real part "imaginary", any other "general"; a row whose nonzero
+ *     entries are all d, -d, i d or -i d for its first entry d is summed
+ *     first and multiplied by d once (see row_eval);
  *   - compiled with -ffp-contract=off so that only the fma() calls fuse.
  */
 #include <stdint.h>
@@ -83,20 +85,69 @@ static void term_acc(double ur, double ui, double xr, double xi,
     }
 }
 
+/* Factor of entry (ur, ui) relative to d = (dr, di), exact comparisons:
+ * 0 when u == d, 1 when u == -d, 2 when u == i d, 3 when u == -i d, -1
+ * otherwise (the first match counts). */
+static int unit_factor(double ur, double ui, double dr, double di)
+{
+    if (ur == dr && ui == di) return 0;
+    if (ur == -dr && ui == -di) return 1;
+    if (ur == -di && ui == dr) return 2;
+    if (ur == di && ui == -dr) return 3;
+    return -1;
+}
+
 /* Row r of y = U x over the present sub-indices, skipping exactly-zero
- * entries.  A row with no nonzero present entry gives +0. */
+ * entries.  A row with no nonzero present entry gives +0.
+ *
+ * Factored rows: when a row has two or more nonzero entries and each one
+ * is f_j d with f_j in {1, -1, i, -i} and d the row's first nonzero entry,
+ * the row is evaluated as y = d * S with S = sum_j f_j x_j: S starts as the
+ * first term (an exact copy) and each later term is one rounded addition
+ * per component; then y is one term_first of d and S.  Mathematically this
+ * is the same row; in rounding it makes equal inputs cancel exactly (a
+ * Hadamard row on two equal amplitudes gives an exact zero).  Every other
+ * row: the first term is a product, later terms fused multiply-adds. */
 static void row_eval(const double *m, int dim, int r, const double *x,
                      const int *present, double *yr, double *yi)
 {
-    int first = 1;
+    int first = -1, count = 0, factored = 1;
+    for (int c = 0; c < dim; ++c) {
+        double ur = m[2 * (r * dim + c)], ui = m[2 * (r * dim + c) + 1];
+        if (ur == 0.0 && ui == 0.0) continue;
+        ++count;
+        if (first < 0) first = c;
+        else if (unit_factor(ur, ui, m[2 * (r * dim + first)], m[2 * (r * dim + first) + 1]) < 0)
+            factored = 0;
+    }
+    if (count >= 2 && factored) {
+        double dr = m[2 * (r * dim + first)], di = m[2 * (r * dim + first) + 1];
+        double sr = 0.0, si = 0.0;
+        int started = 0;
+        for (int c = 0; c < dim; ++c) {
+            double ur = m[2 * (r * dim + c)], ui = m[2 * (r * dim + c) + 1];
+            if (!present[c] || (ur == 0.0 && ui == 0.0)) continue;
+            double xr = x[2 * c], xi = x[2 * c + 1];
+            int f = unit_factor(ur, ui, dr, di);
+            /* f x: 1 -> x, -1 -> -x, i -> (-xi, xr), -i -> (xi, -xr) */
+            double tr = f == 0 ? xr : (f == 1 ? -xr : (f == 2 ? -xi : xi));
+            double ti = f == 0 ? xi : (f == 1 ? -xi : (f == 2 ? xr : -xr));
+            if (!started) { sr = tr; si = ti; started = 1; }
+            else { sr = sr + tr; si = si + ti; }
+        }
+        if (!started) { *yr = 0.0; *yi = 0.0; return; }
+        term_first(dr, di, sr, si, yr, yi);
+        return;
+    }
+    int firstt = 1;
     double ar = 0.0, ai = 0.0;
     for (int c = 0; c < dim; ++c) {
         if (!present[c]) continue;
         double ur = m[2 * (r * dim + c)], ui = m[2 * (r * dim + c) + 1];
         if (ur == 0.0 && ui == 0.0) continue;
-        if (first) {
+        if (firstt) {
             term_first(ur, ui, x[2 * c], x[2 * c + 1], &ar, &ai);
-            first = 0;
+            firstt = 0;
         } else {
             term_acc(ur, ui, x[2 * c], x[2 * c + 1], &ar, &ai);
         }
@@ -269,30 +320,42 @@ double or_units_to_double(uint64_t lo, uint64_t hi)
  *
  * Header, 32 bytes:
  *   [0] mode: 0 CONST, 1 PACKED, 2 RAW      [1] shift s (0..52; 0 in RAW)
- *   [2] ladder level                          [3] sign modes: bits 0-1 re, 2-3 im
+ *   [2] ladder level                          [3] sign mode of re (bits 0-2)
+ *       and of im (bits 3-5); 0 in RAW
  *   [4..7]  body length in bytes (multiple of 16)
- *   [8..15] anchor q_0 of re                  [16..23] anchor q_0 of im
- *   [24] c                                    [25..31] zero
+ *   [8..15] anchor of re                      [16..23] anchor of im
+ *   [24] c                                    [25] zero mode of re (bits
+ *       0-2) and of im (bits 3-5); 0 unless PACKED      [26..31] zero
  * Codes: B = magnitude bits of x (bits 0-62), q = (B + 2^(s-1)) >> s
- * (q = B when s = 0); reconstruction x^ = (q << s) | sign << 63.
- * Residuals r_0 = 0, r_i = q_i - q_{i-1} (mod 2^64); z = zigzag(r).
- * Group width w = bit length of the OR of its z values.
- * Sign word of a group: bit l = sign of value l.  Sign modes:
- *   0 all clear, 1 all set, 2 pattern (u32 P = word of group 0, then
- *   ceil(G/32) u32 flip words, bit g set when word g == ~P), 3 G u32 words.
+ * (q = B when s = 0); reconstruction x^ = (q << s) | sign << 63.  A value
+ * with q = 0 is a zero (q = 0 only for x = +-0: smaller nonzero values
+ * force the lossless level); at s > 0 a zero's sign is stored as 0.  The
+ * anchor is the first nonzero code (0 if none).  Residuals run along the
+ * nonzero codes only: r = q - (previous nonzero code, the anchor for the
+ * first), z = zigzag(r).  Group width w = bit length of the OR of the z of
+ * its nonzero values.
+ * Word sections (sign words: bit l = stored sign of value l; zero words:
+ * bit l set when value l is a zero), mode: 0 every word 0, 1 every word
+ * all L bits set, 2 / 3 exceptions to 0 / to all-set: ceil(G/32) u32
+ * bitmap words (bit g set when word g differs from the base), then the
+ * differing words in group order, 4 G u32 words.  The encoder picks 0 or
+ * 1 when it applies, else the shortest of 2, 3, 4 (lowest on a tie).
  * CONST: body empty; every value of a component is (anchor << s) with the
  *   uniform sign of its sign mode (0 or 1).
- * PACKED body: re sign section, im sign section, G width bytes of re, G of
- *   im, zero pad to 4, then for re then im, group by group, ceil(L*w/32)
- *   u32 words holding the group's bit string (value l at bits
- *   [l*w, (l+1)*w), LSB first); zero pad to 16.
+ * PACKED body: sign sections of re and im, zero sections of re and im, G
+ *   width bytes of re, G of im, zero pad to 4, then for re then im, group
+ *   by group, ceil(nz*w/32) u32 words (nz = nonzero values of the group)
+ *   holding the k-th nonzero value's z at bits [k*w, (k+1)*w), LSB first;
+ *   zero pad to 16.
  * RAW body: the 2N doubles in memory order (re, im interleaved).
- * Mode rule at one level: CONST when every z is 0 and both sign modes are
- * 0 or 1; else PACKED when its body is shorter than 16N; else RAW.
+ * Mode rule at one level: CONST when every z is 0, both sign modes are 0
+ * or 1 and both zero modes are 0 or 1; else PACKED when its body is
+ * shorter than 16N; else RAW.
  */
 #define HDR 32
 enum { M_CONST = 0, M_PACKED = 1, M_RAW = 2 };
-enum { S_CLEAR = 0, S_SET = 1, S_PATTERN = 2, S_WORDS = 3 };
+/* modes of a section of per-group bit words (sign words, zero words) */
+enum { S_CLEAR = 0, S_SET = 1, S_EXC_CLEAR = 2, S_EXC_SET = 3, S_WORDS = 4 };
 #define MAG 0x7FFFFFFFFFFFFFFFull
 #define MIN_NORMAL 0x0010000000000000ull
 #define LOSSY_LIMIT 0x7FE0000000000000ull   /* |x| < 2^1023 */
@@ -333,13 +396,68 @@ static uint64_t get64(const uint8_t *p) { uint64_t v = 0; for (int i = 7; i >= 0
 
 static size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-static size_t sign_bytes(int mode, int G)
+/* base word of an exception mode */
+static uint32_t section_base(int mode, uint32_t lanes)
 {
-    switch (mode) {
-    case S_PATTERN: return 4 + 4 * (size_t)((G + 31) / 32);
-    case S_WORDS: return 4 * (size_t)G;
-    default: return 0;
+    return mode == S_EXC_SET ? lanes : 0;
+}
+
+/* bytes of a word section in the given mode */
+static size_t section_bytes(int mode, const uint32_t *wd, int G, uint32_t lanes)
+{
+    if (mode == S_CLEAR || mode == S_SET) return 0;
+    if (mode == S_WORDS) return 4 * (size_t)G;
+    uint32_t base = section_base(mode, lanes);
+    size_t n = 4 * (size_t)((G + 31) / 32);
+    for (int g = 0; g < G; ++g)
+        if (wd[g] != base) n += 4;
+    return n;
+}
+
+/* mode of a word section: 0 when every word is 0, 1 when every word has
+ * all L bits set, else the smallest of 2 (exceptions to 0), 3 (exceptions
+ * to all-set) and 4 (every word), the lower mode on a tie */
+static int word_mode(const uint32_t *wd, int G, uint32_t lanes)
+{
+    int any1 = 0, any0 = 0;
+    for (int g = 0; g < G; ++g) {
+        if (wd[g]) any1 = 1;
+        if (wd[g] != lanes) any0 = 1;
     }
+    if (!any1) return S_CLEAR;
+    if (!any0) return S_SET;
+    int best = S_EXC_CLEAR;
+    for (int m = S_EXC_SET; m <= S_WORDS; ++m)
+        if (section_bytes(m, wd, G, lanes) < section_bytes(best, wd, G, lanes)) best = m;
+    return best;
+}
+
+static size_t write_section(uint8_t *b, size_t off, int mode, const uint32_t *wd, int G, uint32_t lanes)
+{
+    if (mode == S_WORDS) {
+        for (int g = 0; g < G; ++g) put32(b + off + 4 * (size_t)g, wd[g]);
+        return off + 4 * (size_t)G;
+    }
+    if (mode == S_EXC_CLEAR || mode == S_EXC_SET) {
+        uint32_t base = section_base(mode, lanes);
+        size_t nb = (size_t)((G + 31) / 32), e = off + 4 * nb;
+        for (int g = 0; g < G; ++g)
+            if (wd[g] != base) {
+                size_t bo = off + 4 * (size_t)(g / 32);
+                put32(b + bo, get32(b + bo) | (1u << (g % 32)));
+                put32(b + e, wd[g]);
+                e += 4;
+            }
+        return e;
+    }
+    return off;
+}
+
+static int popcount32(uint32_t v)
+{
+    int n = 0;
+    while (v) { n += v & 1; v >>= 1; }
+    return n;
 }
 
 /* bound on any stream for a tile of 2^c amplitudes */
@@ -358,29 +476,39 @@ static size_t encode_at(const double *a, int c, int s, int level, uint8_t *out)
     uint64_t N = 1ull << c;
     int G = N >= 32 ? (int)(N / 32) : 1;
     int L = N >= 32 ? 32 : (int)N;
+    uint32_t lanes = L == 32 ? 0xFFFFFFFFu : ((1u << L) - 1);
 
-    uint64_t *q[2], *z[2];
-    uint32_t *sw[2];
-    int *w[2];
-    int smode[2];
+    uint64_t *q[2], *z[2], anchor[2];
+    uint32_t *sw[2], *zw[2];
+    int *w[2], *nnz[2];
+    int smode[2], zmode[2];
     for (int k = 0; k < 2; ++k) {
         q[k] = malloc(N * 8);
-        z[k] = malloc(N * 8);
+        z[k] = calloc(N, 8);
         sw[k] = calloc((size_t)G, 4);
+        zw[k] = calloc((size_t)G, 4);
         w[k] = calloc((size_t)G, sizeof(int));
+        nnz[k] = calloc((size_t)G, sizeof(int));
     }
     int allzero = 1;
     for (int k = 0; k < 2; ++k) {
-        int any0 = 0, any1 = 0;
         for (uint64_t i = 0; i < N; ++i) {
             uint64_t u = dbits(a[2 * i + k]);
-            uint64_t sg = u >> 63;
             q[k][i] = quant(u & MAG, s);
-            if (sg) { sw[k][i / 32] |= 1u << (i % 32); any1 = 1; } else any0 = 1;
+            /* a zero keeps its sign only at the lossless level */
+            if ((u >> 63) && (q[k][i] || s == 0)) sw[k][i / 32] |= 1u << (i % 32);
+            if (q[k][i] == 0) zw[k][i / 32] |= 1u << (i % 32);
         }
-        /* Lorenzo (order 1) residuals on the integer codes, then zigzag */
+        /* order-1 Lorenzo residuals along the nonzero codes, from the
+         * anchor (the first nonzero code), then zigzag */
+        anchor[k] = 0;
+        for (uint64_t i = 0; i < N; ++i)
+            if (q[k][i]) { anchor[k] = q[k][i]; break; }
+        uint64_t prev = anchor[k];
         for (uint64_t i = 0; i < N; ++i) {
-            uint64_t r = i == 0 ? 0 : q[k][i] - q[k][i - 1];
+            if (!q[k][i]) continue;
+            uint64_t r = q[k][i] - prev;
+            prev = q[k][i];
             z[k][i] = (r << 1) ^ (uint64_t)((int64_t)r >> 63);
             if (z[k][i]) allzero = 0;
         }
@@ -388,15 +516,10 @@ static size_t encode_at(const double *a, int c, int s, int level, uint8_t *out)
             uint64_t o = 0;
             for (int l = 0; l < L; ++l) o |= z[k][(uint64_t)g * 32 + l];
             w[k][g] = bitlen64(o);
+            nnz[k][g] = popcount32(~zw[k][g] & lanes);
         }
-        if (!any1) smode[k] = S_CLEAR;
-        else if (!any0) smode[k] = S_SET;
-        else {
-            int pat = G >= 2;
-            for (int g = 1; g < G && pat; ++g)
-                if (sw[k][g] != sw[k][0] && sw[k][g] != ~sw[k][0]) pat = 0;
-            smode[k] = pat ? S_PATTERN : S_WORDS;
-        }
+        smode[k] = word_mode(sw[k], G, lanes);
+        zmode[k] = word_mode(zw[k], G, lanes);
     }
 
     size_t raw_body = 16 * N;
@@ -405,12 +528,14 @@ static size_t encode_at(const double *a, int c, int s, int level, uint8_t *out)
     size_t data_words = 0;
     for (int k = 0; k < 2; ++k)
         for (int g = 0; g < G; ++g)
-            data_words += ((size_t)L * w[k][g] + 31) / 32;
-    size_t meta = sign_bytes(smode[0], G) + sign_bytes(smode[1], G);
-    size_t wbytes = round_up(2 * (size_t)G, 4);
+            data_words += ((size_t)nnz[k][g] * w[k][g] + 31) / 32;
+    size_t meta = 0;
+    for (int k = 0; k < 2; ++k)
+        meta += section_bytes(smode[k], sw[k], G, lanes) + section_bytes(zmode[k], zw[k], G, lanes);
+    size_t wbytes = round_up(meta + 2 * (size_t)G, 4) - meta;
     size_t packed_body = round_up(meta + wbytes + 4 * data_words, 16);
 
-    if (allzero && smode[0] <= S_SET && smode[1] <= S_SET) {
+    if (allzero && smode[0] <= S_SET && smode[1] <= S_SET && zmode[0] <= S_SET && zmode[1] <= S_SET) {
         mode = M_CONST;
         body = 0;
     } else if (packed_body < raw_body) {
@@ -425,11 +550,12 @@ static size_t encode_at(const double *a, int c, int s, int level, uint8_t *out)
     out[0] = (uint8_t)mode;
     out[1] = (uint8_t)(mode == M_RAW ? 0 : s);
     out[2] = (uint8_t)level;
-    out[3] = (uint8_t)(mode == M_RAW ? 0 : (smode[0] | (smode[1] << 2)));
+    if (mode != M_RAW) out[3] = (uint8_t)(smode[0] | (smode[1] << 3));
+    if (mode == M_PACKED) out[25] = (uint8_t)(zmode[0] | (zmode[1] << 3));
     put32(out + 4, (uint32_t)body);
     if (mode != M_RAW) {
-        put64(out + 8, q[0][0]);
-        put64(out + 16, q[1][0]);
+        put64(out + 8, anchor[0]);
+        put64(out + 16, anchor[1]);
     }
     out[24] = (uint8_t)c;
 
@@ -438,41 +564,36 @@ static size_t encode_at(const double *a, int c, int s, int level, uint8_t *out)
         for (uint64_t i = 0; i < 2 * N; ++i) put64(b + 8 * i, dbits(a[i]));
     } else if (mode == M_PACKED) {
         size_t off = 0;
-        for (int k = 0; k < 2; ++k) {
-            if (smode[k] == S_PATTERN) {
-                put32(b + off, sw[k][0]);
-                off += 4;
-                for (int g = 0; g < G; ++g)
-                    if (sw[k][g] != sw[k][0]) {
-                        size_t wo = off + 4 * (size_t)(g / 32);
-                        put32(b + wo, get32(b + wo) | (1u << (g % 32)));
-                    }
-                off += 4 * (size_t)((G + 31) / 32);
-            } else if (smode[k] == S_WORDS) {
-                for (int g = 0; g < G; ++g) { put32(b + off, sw[k][g]); off += 4; }
-            }
-        }
+        for (int k = 0; k < 2; ++k) off = write_section(b, off, smode[k], sw[k], G, lanes);
+        for (int k = 0; k < 2; ++k) off = write_section(b, off, zmode[k], zw[k], G, lanes);
         for (int k = 0; k < 2; ++k)
             for (int g = 0; g < G; ++g) b[off++] = (uint8_t)w[k][g];
         off = round_up(off, 4);
-        /* lane-major bit packing: value l of a group occupies bits
-         * [l*w, (l+1)*w) of the group's little-endian bit string */
+        /* lane-major bit packing of the nonzero values: the k-th nonzero
+         * value of a group occupies bits [k*w, (k+1)*w) of the group's
+         * little-endian bit string */
         for (int k = 0; k < 2; ++k)
             for (int g = 0; g < G; ++g) {
                 int wg = w[k][g];
-                size_t nwords = ((size_t)L * wg + 31) / 32;
+                size_t nwords = ((size_t)nnz[k][g] * wg + 31) / 32;
+                size_t rank = 0;
                 for (int l = 0; l < L; ++l) {
-                    uint64_t v = z[k][(uint64_t)g * 32 + l];
+                    uint64_t i = (uint64_t)g * 32 + l;
+                    if (!q[k][i]) continue;
+                    uint64_t v = z[k][i];
                     for (int bit = 0; bit < wg; ++bit)
                         if ((v >> bit) & 1) {
-                            size_t pos = (size_t)l * wg + bit;
+                            size_t pos = rank * wg + bit;
                             b[off + pos / 8] |= (uint8_t)(1u << (pos % 8));
                         }
+                    ++rank;
                 }
                 off += 4 * nwords;
             }
     }
-    for (int k = 0; k < 2; ++k) { free(q[k]); free(z[k]); free(sw[k]); free(w[k]); }
+    for (int k = 0; k < 2; ++k) {
+        free(q[k]); free(z[k]); free(sw[k]); free(zw[k]); free(w[k]); free(nnz[k]);
+    }
     return HDR + body;
 }
 
@@ -530,8 +651,10 @@ int or_decode_tile(const uint8_t *in, size_t len, int c, double *a)
     uint64_t N = 1ull << c;
     int G = N >= 32 ? (int)(N / 32) : 1;
     int L = N >= 32 ? 32 : (int)N;
+    uint32_t lanes = L == 32 ? 0xFFFFFFFFu : ((1u << L) - 1);
     int mode = in[0], s = in[1];
-    int sm[2] = {in[3] & 3, (in[3] >> 2) & 3};
+    int sm[2] = {in[3] & 7, (in[3] >> 3) & 7};
+    int zm[2] = {in[25] & 7, (in[25] >> 3) & 7};
     size_t body = get32(in + 4);
     if (in[24] != (uint8_t)c) return -2;
     if (HDR + body > len) return -3;
@@ -544,7 +667,7 @@ int or_decode_tile(const uint8_t *in, size_t len, int c, double *a)
     }
     if (s > 52) return -5;
     if (mode == M_CONST) {
-        if (body != 0 || sm[0] > S_SET || sm[1] > S_SET) return -6;
+        if (body != 0 || sm[0] > S_SET || sm[1] > S_SET || in[25]) return -6;
         for (int k = 0; k < 2; ++k) {
             uint64_t v = (anchor[k] << s) | ((uint64_t)sm[k] << 63);
             for (uint64_t i = 0; i < N; ++i) a[2 * i + k] = bitsd(v);
@@ -553,28 +676,38 @@ int or_decode_tile(const uint8_t *in, size_t len, int c, double *a)
     }
     if (mode != M_PACKED) return -7;
     size_t off = 0;
-    uint32_t *sw[2];
-    for (int k = 0; k < 2; ++k) sw[k] = calloc((size_t)G, 4);
+    uint32_t *sw[2], *zw[2];
+    for (int k = 0; k < 2; ++k) { sw[k] = calloc((size_t)G, 4); zw[k] = calloc((size_t)G, 4); }
     int rc = 0;
-    for (int k = 0; k < 2 && rc == 0; ++k) {
-        size_t need = sign_bytes(sm[k], G);
-        if (off + need > body) { rc = -8; break; }
-        uint32_t lanes = L == 32 ? 0xFFFFFFFFu : ((1u << L) - 1);
-        for (int g = 0; g < G; ++g) {
-            if (sm[k] == S_CLEAR) sw[k][g] = 0;
-            else if (sm[k] == S_SET) sw[k][g] = lanes;
-            else if (sm[k] == S_PATTERN) {
-                uint32_t P = get32(b + off);
-                uint32_t fl = (get32(b + off + 4 + 4 * (size_t)(g / 32)) >> (g % 32)) & 1;
-                sw[k][g] = fl ? ~P : P;
-            } else sw[k][g] = get32(b + off + 4 * (size_t)g);
+    /* sign sections, then zero sections */
+    for (int pass = 0; pass < 4 && rc == 0; ++pass) {
+        int k = pass & 1, md = pass < 2 ? sm[k] : zm[k];
+        uint32_t *dst = pass < 2 ? sw[k] : zw[k];
+        if (md > S_WORDS) { rc = -8; break; }
+        if (md == S_CLEAR || md == S_SET) {
+            for (int g = 0; g < G; ++g) dst[g] = md == S_SET ? lanes : 0;
+        } else if (md == S_WORDS) {
+            if (off + 4 * (size_t)G > body) { rc = -8; break; }
+            for (int g = 0; g < G; ++g) dst[g] = get32(b + off + 4 * (size_t)g);
+            off += 4 * (size_t)G;
+        } else {
+            /* exception bitmap, then the words that differ from the base */
+            size_t nb = (size_t)((G + 31) / 32);
+            if (off + 4 * nb > body) { rc = -8; break; }
+            size_t e = off + 4 * nb;
+            for (int g = 0; g < G && rc == 0; ++g) {
+                dst[g] = section_base(md, lanes);
+                if ((get32(b + off + 4 * (size_t)(g / 32)) >> (g % 32)) & 1) {
+                    if (e + 4 > body) { rc = -8; break; }
+                    dst[g] = get32(b + e);
+                    e += 4;
+                }
+            }
+            off = e;
         }
-        off += need;
     }
     int *w[2] = {NULL, NULL};
-    if (rc == 0) {
-        if (off + 2 * (size_t)G > body) rc = -9;
-    }
+    if (rc == 0 && off + 2 * (size_t)G > body) rc = -9;
     if (rc == 0) {
         for (int k = 0; k < 2; ++k) {
             w[k] = calloc((size_t)G, sizeof(int));
@@ -589,24 +722,30 @@ int or_decode_tile(const uint8_t *in, size_t len, int c, double *a)
         uint64_t q = anchor[k];
         for (int g = 0; g < G && rc == 0; ++g) {
             int wg = w[k][g];
-            size_t nwords = ((size_t)L * wg + 31) / 32;
+            size_t nnz = (size_t)popcount32(~zw[k][g] & lanes);
+            size_t nwords = (nnz * wg + 31) / 32;
             if (off + 4 * nwords > body) { rc = -11; break; }
+            size_t rank = 0;
             for (int l = 0; l < L; ++l) {
+                uint64_t i = (uint64_t)g * 32 + l;
+                uint64_t sg = (sw[k][g] >> l) & 1;
+                if ((zw[k][g] >> l) & 1) {           /* a zero value */
+                    a[2 * i + k] = bitsd(sg << 63);
+                    continue;
+                }
                 uint64_t v = 0;
                 for (int bit = 0; bit < wg; ++bit) {
-                    size_t pos = (size_t)l * wg + bit;
+                    size_t pos = rank * wg + bit;
                     v |= (uint64_t)((b[off + pos / 8] >> (pos % 8)) & 1) << bit;
                 }
-                uint64_t r = (v >> 1) ^ (0 - (v & 1));   /* un-zigzag */
-                uint64_t i = (uint64_t)g * 32 + l;
-                if (i > 0) q += r;                        /* inclusive prefix sum */
-                uint64_t sg = (sw[k][g] >> l) & 1;
+                ++rank;
+                q += (v >> 1) ^ (0 - (v & 1));       /* un-zigzag, running sum */
                 a[2 * i + k] = bitsd((q << s) | (sg << 63));
             }
             off += 4 * nwords;
         }
     }
-    for (int k = 0; k < 2; ++k) { free(sw[k]); free(w[k]); }
+    for (int k = 0; k < 2; ++k) { free(sw[k]); free(zw[k]); free(w[k]); }
     return rc;
 }
 

@@ -158,6 +158,41 @@ unsigned entry_class(double ur, double ui) {
     return qs::EC_GENERAL;
 }
 
+// Factor of entry u relative to d (exact comparisons): 0 u == d, 1 u == -d,
+// 2 u == i d, 3 u == -i d, -1 none; the first match counts.
+int unit_factor(double ur, double ui, double dr, double di) {
+    if (ur == dr && ui == di) return 0;
+    if (ur == -dr && ui == -di) return 1;
+    if (ur == -di && ui == dr) return 2;
+    if (ur == di && ui == -dr) return 3;
+    return -1;
+}
+
+// Row factoring of a non-diagonal gate: bit r set when row r has two or
+// more nonzero entries, each f d for its first nonzero entry d and f in
+// {1, -1, i, -i}; the code of f for entry e in bits 8 + 2e.
+unsigned long long row_factoring(const HostGate &g) {
+    const int dim = 1 << g.k;
+    unsigned long long fac = 0;
+    for (int r = 0; r < dim; ++r) {
+        int first = -1, count = 0;
+        bool ok = true;
+        unsigned long long codes = 0;
+        for (int c = 0; c < dim; ++c) {
+            const int e = r * dim + c;
+            const double ur = g.m[2 * e], ui = g.m[2 * e + 1];
+            if (ur == 0.0 && ui == 0.0) continue;
+            ++count;
+            if (first < 0) { first = e; continue; }
+            const int f = unit_factor(ur, ui, g.m[2 * first], g.m[2 * first + 1]);
+            if (f < 0) ok = false;
+            else codes |= (unsigned long long)f << (8 + 2 * e);
+        }
+        if (ok && count >= 2) fac |= (1ull << r) | codes;
+    }
+    return fac;
+}
+
 // FP64 instructions of one matrix entry's term, per component: zero and a
 // leading +-1 are free, real and imaginary entries take one, general two.
 double entry_cost(double ur, double ui, bool first) {
@@ -171,6 +206,7 @@ double entry_cost(double ur, double ui, bool first) {
 double gate_dp_ops(const HostGate &g, int n) {
     int dim = 1 << g.k;
     double groups = std::ldexp(1.0, n - g.k - popcount64(g.cm));
+    const unsigned long long fac = g.diag ? 0ull : row_factoring(g);
     double per = 0.0;
     for (int r = 0; r < dim; ++r) {
         if (g.diag) {
@@ -179,10 +215,12 @@ double gate_dp_ops(const HostGate &g, int n) {
             continue;
         }
         bool first = true;
+        const bool factored = (fac >> r) & 1ull;
         for (int c = 0; c < dim; ++c) {
             double ur = g.m[2 * (r * dim + c)], ui = g.m[2 * (r * dim + c) + 1];
             if (ur == 0.0 && ui == 0.0) continue;
-            per += 2.0 * entry_cost(ur, ui, first);
+            // factored: one addition per later term, the first entry's product once
+            per += 2.0 * (factored ? (first ? entry_cost(ur, ui, true) : 1.0) : entry_cost(ur, ui, first));
             first = false;
         }
     }
@@ -432,6 +470,7 @@ void prepare_gate(const HostGate &g, int c, const Sweep &sw, qs::DGate &d, qs::S
     } else {
         for (int e = 0; e < dim * dim; ++e)
             sgt.cls |= (unsigned long long)entry_class(g.m[2 * e], g.m[2 * e + 1]) << (3 * e);
+        sgt.fac = row_factoring(g);
     }
     // buffer bits pinned by local controls and buffer targets, ascending
     unsigned pinned = (unsigned)d.lcm;

@@ -23,7 +23,7 @@ constexpr unsigned long long INF_BITS = 0x7FF0000000000000ull;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
 enum { M_CONST = 0, M_PACKED = 1, M_RAW = 2 };
-enum { S_CLEAR = 0, S_SET = 1, S_PATTERN = 2, S_WORDS = 3 };
+enum { S_CLEAR = 0, S_SET = 1, S_EXC_CLEAR = 2, S_EXC_SET = 3, S_WORDS = 4 };
 
 __device__ __forceinline__ Acc4 make_acc4(double x, double y, double z, double w) {
     Acc4 a;
@@ -161,13 +161,40 @@ __device__ __forceinline__ void term_acc(unsigned code, double ur, double ui, do
     }
 }
 
-// Row r of y = U x over the nonzero entries, in column order.
+// Row r of y = U x over the nonzero entries, in column order.  A factored
+// row (bit r of fac: every nonzero entry is f d, f in {1, -1, i, -i}, d
+// the first nonzero entry; f of entry e in bits 8 + 2e, codes 0..3 for
+// 1, -1, i, -i) is summed first, S = sum f x with one rounded addition per
+// later term, and multiplied by d once; equal inputs then cancel exactly.
 template <int DIM>
-__device__ __forceinline__ void row_eval(const double *m, unsigned long long cls, int r,
-                                         const double *xr, const double *xi, double &yr,
+__device__ __forceinline__ void row_eval(const double *m, unsigned long long cls, unsigned long long fac,
+                                         int r, const double *xr, const double *xi, double &yr,
                                          double &yi) {
     bool first = true;
     double ar = 0.0, ai = 0.0;
+    if ((fac >> r) & 1ull) {
+        unsigned dcode = 0;
+        double dr = 0.0, di = 0.0;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+            const int e = r * DIM + c;
+            const unsigned code = (unsigned)(cls >> (3 * e)) & 7u;
+            if (code == EC_ZERO) continue;
+            const unsigned f = (unsigned)(fac >> (8 + 2 * e)) & 3u;
+            const double tr = f == 0 ? xr[c] : (f == 1 ? -xr[c] : (f == 2 ? -xi[c] : xi[c]));
+            const double ti = f == 0 ? xi[c] : (f == 1 ? -xi[c] : (f == 2 ? xr[c] : -xr[c]));
+            if (first) {
+                ar = tr; ai = ti;
+                dcode = code; dr = m[2 * e]; di = m[2 * e + 1];
+                first = false;
+            } else {
+                ar = __dadd_rn(ar, tr);
+                ai = __dadd_rn(ai, ti);
+            }
+        }
+        term_first(dcode, dr, di, ar, ai, yr, yi);
+        return;
+    }
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
         unsigned code = (unsigned)(cls >> (3 * (r * DIM + c))) & 7u;
@@ -246,8 +273,8 @@ __device__ void one_target(double *re, double *im, int mb, const SGate &s, const
         unsigned l1 = l0 | bit;
         double xr[2] = {re[l0], re[l1]}, xi[2] = {im[l0], im[l1]};
         double y0r, y0i, y1r, y1i;
-        row_eval<2>(m, s.cls, 0, xr, xi, y0r, y0i);
-        row_eval<2>(m, s.cls, 1, xr, xi, y1r, y1i);
+        row_eval<2>(m, s.cls, s.fac, 0, xr, xi, y0r, y0i);
+        row_eval<2>(m, s.cls, s.fac, 1, xr, xi, y1r, y1i);
         re[l0] = y0r; im[l0] = y0i;
         re[l1] = y1r; im[l1] = y1i;
     }
@@ -267,7 +294,7 @@ __device__ void two_target(double *re, double *im, int mb, const SGate &s, const
         }
         double yr[4], yi[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) row_eval<4>(dg.m, s.cls, r, xr, xi, yr[r], yi[r]);
+        for (int r = 0; r < 4; ++r) row_eval<4>(dg.m, s.cls, s.fac, r, xr, xi, yr[r], yi[r]);
 #pragma unroll
         for (int q = 0; q < 4; ++q) { re[idx[q]] = yr[q]; im[idx[q]] = yi[q]; }
     }
@@ -294,11 +321,6 @@ __device__ void apply_gates(double *re, double *im, int mb, const SGate *sg, con
 // barriers are involved, so the warps of a CTA code different tiles
 // independently.
 
-__device__ __forceinline__ uint32_t sign_bytes(int mode, int G) {
-    return mode == S_PATTERN ? 4u + 4u * (uint32_t)((G + 31) / 32)
-                             : (mode == S_WORDS ? 4u * (uint32_t)G : 0u);
-}
-
 // exclusive prefix of v over the lanes; *total = sum over the warp
 __device__ __forceinline__ uint32_t warp_exscan(uint32_t v, uint32_t &total) {
     const int lane = threadIdx.x & 31;
@@ -311,16 +333,66 @@ __device__ __forceinline__ uint32_t warp_exscan(uint32_t v, uint32_t &total) {
     return inc - v;
 }
 
-// sign word of group g from a sign section in mode md
-__device__ __forceinline__ uint32_t sign_word(const uint8_t *sec, int md, int g, uint32_t lanes) {
-    const uint32_t *w = reinterpret_cast<const uint32_t *>(sec);
-    if (md == S_CLEAR) return 0u;
-    if (md == S_SET) return lanes;
-    if (md == S_PATTERN) {
-        uint32_t P = __ldg(w);
-        return ((__ldg(w + 1 + g / 32) >> (g % 32)) & 1u) ? ~P : P;
+// bit mask of the lanes below this one
+__device__ __forceinline__ uint32_t lanes_below() {
+    return (1u << (threadIdx.x & 31)) - 1u;
+}
+
+// Word section of per-group bit words (lane g holds the word of group g):
+// mode 0 every word 0, 1 every word == lanes, else the shortest of 2
+// (exceptions to 0), 3 (exceptions to `lanes`) and 4 (every word), the
+// lower mode on a tie.  Exception modes store a bitmap word (bit g: word g
+// differs from the base) and then the differing words in group order.
+// Warp-uniform result; *bytes = the section's size.
+__device__ __forceinline__ int section_mode(uint32_t v, int G, uint32_t lanes, uint32_t &bytes) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t n0 = __popc(__ballot_sync(FULL, lane < G && v != 0u));
+    const uint32_t n1 = __popc(__ballot_sync(FULL, lane < G && v != lanes));
+    if (n0 == 0) { bytes = 0; return S_CLEAR; }
+    if (n1 == 0) { bytes = 0; return S_SET; }
+    const uint32_t nb = 4u * (uint32_t)((G + 31) >> 5);
+    const uint32_t b2 = nb + 4u * n0, b3 = nb + 4u * n1, b4 = 4u * (uint32_t)G;
+    int m = S_EXC_CLEAR;
+    bytes = b2;
+    if (b3 < bytes) { m = S_EXC_SET; bytes = b3; }
+    if (b4 < bytes) { m = S_WORDS; bytes = b4; }
+    return m;
+}
+
+// write a word section in mode md at sec (4-byte aligned)
+__device__ __forceinline__ void write_section(uint32_t *sec, int md, uint32_t v, int G, uint32_t lanes) {
+    const int lane = threadIdx.x & 31;
+    if (md == S_WORDS) {
+        if (lane < G) sec[lane] = v;
+    } else if (md == S_EXC_CLEAR || md == S_EXC_SET) {
+        const uint32_t base = md == S_EXC_SET ? lanes : 0u;
+        const uint32_t bm = __ballot_sync(FULL, lane < G && v != base);
+        if (lane == 0) sec[0] = bm;
+        if ((bm >> lane) & 1u) sec[1 + __popc(bm & lanes_below())] = v;
     }
-    return __ldg(w + g);
+}
+
+// read a word section in mode md at b + off (body bytes in total): lane g
+// gets the word of group g; returns the section's size, or sets bad
+__device__ __forceinline__ uint32_t read_section(const uint8_t *b, uint32_t off, uint32_t body, int md,
+                                                 int G, uint32_t lanes, uint32_t &v, bool &bad) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t *sec = reinterpret_cast<const uint32_t *>(b + off);
+    v = 0u;
+    if (md == S_CLEAR) return 0u;
+    if (md == S_SET) { v = lane < G ? lanes : 0u; return 0u; }
+    if (md == S_WORDS) {
+        if (off + 4u * (uint32_t)G > body) { bad = true; return 0u; }
+        if (lane < G) v = __ldg(sec + lane);
+        return 4u * (uint32_t)G;
+    }
+    if (md > S_WORDS || off + 4u > body) { bad = true; return 0u; }
+    const uint32_t gm = G == 32 ? FULL : ((1u << G) - 1u);
+    const uint32_t bm = __ldg(sec) & gm;
+    const uint32_t size = 4u + 4u * __popc(bm);
+    if (off + size > body) { bad = true; return 0u; }
+    if (lane < G) v = ((bm >> lane) & 1u) ? __ldg(sec + 1 + __popc(bm & lanes_below())) : (md == S_EXC_SET ? lanes : 0u);
+    return size;
 }
 
 // Decode one stream into planar re/im (2^c values each), multiplied by
@@ -335,14 +407,15 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
     const uint32_t h0 = __shfl_sync(FULL, hw, 0), body = __shfl_sync(FULL, hw, 1);
     const unsigned long long a0 = ((unsigned long long)__shfl_sync(FULL, hw, 3) << 32) | __shfl_sync(FULL, hw, 2);
     const unsigned long long a1 = ((unsigned long long)__shfl_sync(FULL, hw, 5) << 32) | __shfl_sync(FULL, hw, 4);
-    const int hc = __shfl_sync(FULL, hw, 6) & 0xFF;
+    const uint32_t h6 = __shfl_sync(FULL, hw, 6);
+    const int hc = h6 & 0xFF;
     const int mode = h0 & 0xFF, s = (h0 >> 8) & 0xFF;
-    const int sm0 = (h0 >> 24) & 3, sm1 = (h0 >> 26) & 3;
+    const int sm0 = (h0 >> 24) & 7, sm1 = (h0 >> 27) & 7;
+    const int zm0 = (h6 >> 8) & 7, zm1 = (h6 >> 11) & 7;
     const uint8_t *b = src + HDR;
     bool bad = hc != c || mode > 2 || (mode != M_RAW && s > 52) || (body & 15u);
     if (!bad && mode == M_RAW) bad = body != 16u * (uint32_t)N;
-    if (!bad && mode == M_CONST) bad = body != 0 || sm0 > 1 || sm1 > 1;
-    if (!bad && mode == M_PACKED) bad = sign_bytes(sm0, G) + sign_bytes(sm1, G) + 2u * G > body;
+    if (!bad && mode == M_CONST) bad = body != 0 || sm0 > 1 || sm1 > 1 || ((h6 >> 8) & 0xFFu);
     if (!bad && mode == M_CONST) {
         double v0 = bitsd((a0 << s) | ((unsigned long long)sm0 << 63));
         double v1 = bitsd((a1 << s) | ((unsigned long long)sm1 << 63));
@@ -360,40 +433,49 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
         }
         return 0;
     }
-    uint32_t sw0 = 0, sw1 = 0, w0 = 0, w1 = 0, doff = 0, off0 = 0, off1 = 0, tot0 = 0, tot1 = 0;
+    const uint32_t lanes = L == 32 ? FULL : ((1u << L) - 1u);
+    uint32_t sw0 = 0, sw1 = 0, zw0 = 0, zw1 = 0, w0 = 0, w1 = 0, doff = 0, off0 = 0, off1 = 0;
     if (!bad) {
-        const uint32_t sb0 = sign_bytes(sm0, G), sb1 = sign_bytes(sm1, G);
-        const uint32_t lanes = L == 32 ? FULL : ((1u << L) - 1u);
-        if (lane < G) {
-            sw0 = sign_word(b, sm0, lane, lanes);
-            sw1 = sign_word(b + sb0, sm1, lane, lanes);
-            w0 = b[sb0 + sb1 + lane];
-            w1 = b[sb0 + sb1 + G + lane];
+        uint32_t off = 0;
+        off += read_section(b, off, body, sm0, G, lanes, sw0, bad);
+        if (!bad) off += read_section(b, off, body, sm1, G, lanes, sw1, bad);
+        if (!bad) off += read_section(b, off, body, zm0, G, lanes, zw0, bad);
+        if (!bad) off += read_section(b, off, body, zm1, G, lanes, zw1, bad);
+        if (!bad && off + 2u * G > body) bad = true;
+        if (!bad) {
+            if (lane < G) {
+                w0 = b[off + lane];
+                w1 = b[off + G + lane];
+            }
+            uint32_t tot0, tot1;
+            off0 = warp_exscan(((uint32_t)__popc(~zw0 & lanes) * w0 + 31u) >> 5, tot0);
+            off1 = warp_exscan(((uint32_t)__popc(~zw1 & lanes) * w1 + 31u) >> 5, tot1) + tot0;
+            doff = (off + 2u * G + 3u) & ~3u;
+            const uint32_t wmax = __reduce_max_sync(FULL, max(w0, w1));
+            bad = wmax > 64 || (unsigned long long)doff + 4ull * (tot0 + tot1) > body;
         }
-        off0 = warp_exscan(((uint32_t)L * w0 + 31u) >> 5, tot0);
-        off1 = warp_exscan(((uint32_t)L * w1 + 31u) >> 5, tot1) + tot0;
-        doff = (sb0 + sb1 + 2u * G + 3u) & ~3u;
-        uint32_t wmax = __reduce_max_sync(FULL, max(w0, w1));
-        bad = wmax > 64 || (unsigned long long)doff + 4ull * (tot0 + tot1) > body;
     }
     if (bad) {
         for (int i = lane; i < N; i += 32) { re[i] = 0.0; im[i] = 0.0; }
         return 1;
     }
     const uint32_t *data = reinterpret_cast<const uint32_t *>(b + doff);
+    const uint32_t below = lanes_below();
     for (int k = 0; k < 2; ++k) {
         double *v = k ? im : re;
         unsigned long long carry = k ? a1 : a0;
-        const uint32_t wk = k ? w1 : w0, offk = k ? off1 : off0, swk = k ? sw1 : sw0;
+        const uint32_t wk = k ? w1 : w0, offk = k ? off1 : off0, swk = k ? sw1 : sw0, zwk = k ? zw1 : zw0;
         for (int g = 0; g < G; ++g) {
             const uint32_t w = __shfl_sync(FULL, wk, g);
             const uint32_t wo = __shfl_sync(FULL, offk, g);
             const uint32_t sgw = __shfl_sync(FULL, swk, g);
-            const uint32_t nwd = ((uint32_t)L * w + 31u) >> 5;
+            const uint32_t nzw = ~__shfl_sync(FULL, zwk, g) & lanes;
+            const bool nzl = (nzw >> lane) & 1u;
+            const uint32_t nwd = ((uint32_t)__popc(nzw) * w + 31u) >> 5;
             unsigned long long z = 0;
-            if (lane < L && w) {
+            if (nzl && w) {
                 const uint32_t *base = data + wo;
-                uint32_t bo = (uint32_t)lane * w, j0 = bo >> 5, sh = bo & 31u;
+                uint32_t bo = (uint32_t)__popc(nzw & below) * w, j0 = bo >> 5, sh = bo & 31u;
                 uint32_t x0 = __ldg(base + j0);
                 uint32_t x1 = j0 + 1 < nwd ? __ldg(base + j0 + 1) : 0u;
                 uint32_t x2 = j0 + 2 < nwd ? __ldg(base + j0 + 2) : 0u;
@@ -401,8 +483,7 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
                 unsigned long long vv = sh ? ((lo >> sh) | ((unsigned long long)x2 << (64 - sh))) : lo;
                 z = w == 64 ? vv : (vv & ((1ull << w) - 1ull));
             }
-            unsigned long long r = unzigzag(z);
-            if ((g == 0 && lane == 0) || lane >= L) r = 0;
+            const unsigned long long r = unzigzag(z);        // 0 for zeros and lanes >= L
             unsigned long long inc;
             if (w <= 27) {                      // 32 partial sums of |r| < 2^26 fit in int32
                 int v32 = (int)(long long)r;
@@ -420,7 +501,8 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
             }
             const unsigned long long q = carry + inc;
             if (lane < L) {
-                double x = bitsd((q << s) | ((unsigned long long)((sgw >> lane) & 1u) << 63));
+                const unsigned long long sg = (unsigned long long)((sgw >> lane) & 1u) << 63;
+                double x = bitsd(nzl ? ((q << s) | sg) : sg);
                 if (scale) x = __dmul_rn(x, alpha);
                 v[g * 32 + lane] = x;
             }
@@ -435,23 +517,31 @@ struct EncodeOut {
     bool ok;
 };
 
-// widths (8 bits per ladder level) and word totals of one pass over a tile
+// One pass over a tile: zero and sign words, the first nonzero magnitude,
+// and group widths and word totals at every ladder level.
 struct LevelSizes {
     unsigned long long wl0, wl1;      // lane g: width of group g per level (byte lv)
     uint32_t words[MAX_LEVELS];       // data words per level (warp-uniform)
     uint32_t nz;                      // bit lv: some residual nonzero at level lv
-    uint32_t sw0, sw1;                // lane g: sign words
+    uint32_t sw0, sw1;                // lane g: sign words (every value)
+    uint32_t zw0, zw1;                // lane g: zero words (bit l: magnitude 0)
+    unsigned long long f0, f1;        // first nonzero magnitude bits (0 if none), warp-uniform
 };
 
-// Pass 1 of the encoder: sign words and group widths at every level.
+// Pass 1 of the encoder.  Residuals run along the nonzero values of a
+// component: each against the previous nonzero code, the first against
+// itself (the anchor).  A zero code only arises from a zero magnitude: any
+// other value below the lossy range forces shift 0.
 // force0: code every level with shift 0 (values outside the lossy range).
 __device__ __forceinline__ void size_levels(const double *re, const double *im, const CodecCfg &cc,
                                             int G, int L, bool force0, LevelSizes &ls, int &nonfin,
                                             int &inel) {
     const int lane = threadIdx.x & 31;
+    const uint32_t below = lanes_below();
     ls.wl0 = ls.wl1 = 0;
     ls.nz = 0;
-    ls.sw0 = ls.sw1 = 0;
+    ls.sw0 = ls.sw1 = ls.zw0 = ls.zw1 = 0;
+    ls.f0 = ls.f1 = 0;
 #pragma unroll
     for (int lv = 0; lv < MAX_LEVELS; ++lv) ls.words[lv] = 0;
     for (int k = 0; k < 2; ++k) {
@@ -459,32 +549,46 @@ __device__ __forceinline__ void size_levels(const double *re, const double *im, 
         unsigned long long carry[MAX_LEVELS];
 #pragma unroll
         for (int lv = 0; lv < MAX_LEVELS; ++lv) carry[lv] = 0;
+        bool seen = false;
+        unsigned long long first = 0;
         for (int g = 0; g < G; ++g) {
             const unsigned long long u = lane < L ? dbits(v[g * 32 + lane]) : 0ull;
             const unsigned long long B = u & MAG;
             nonfin |= lane < L && B >= INF_BITS;
             inel |= lane < L && B != 0 && (B < MIN_NORMAL || B >= LOSSY_LIMIT);
             const uint32_t sw = __ballot_sync(FULL, lane < L && (u >> 63));
-            if (lane == g) { if (k) ls.sw1 = sw; else ls.sw0 = sw; }
+            const uint32_t nzm = __ballot_sync(FULL, lane < L && B != 0);
+            if (lane == g) {
+                if (k) { ls.sw1 = sw; ls.zw1 = ~nzm & (L == 32 ? FULL : ((1u << L) - 1u)); }
+                else { ls.sw0 = sw; ls.zw0 = ~nzm & (L == 32 ? FULL : ((1u << L) - 1u)); }
+            }
+            const uint32_t pm = nzm & below;                 // nonzero lanes before this one
+            const int src = pm ? 31 - __clz(pm) : lane;
+            const int last = nzm ? 31 - __clz(nzm) : 0;
+            const uint32_t nnz = __popc(nzm);
+            if (!seen && nzm) first = shfl64(B, __ffs(nzm) - 1);
 #pragma unroll
             for (int lv = 0; lv < MAX_LEVELS; ++lv) {
                 if (lv >= cc.nlev) continue;
                 const int s = force0 ? 0 : cc.shifts[lv];
                 const unsigned long long q = quant(B, s);
-                unsigned long long qp = shfl_up64(q, 1);
-                if (lane == 0) qp = g == 0 ? q : carry[lv];
-                const unsigned long long z = lane < L ? zigzag(q - qp) : 0ull;
+                const unsigned long long qs = shfl64(q, src);
+                const unsigned long long qp = pm ? qs : (seen ? carry[lv] : q);
+                const unsigned long long z = (lane < L && B != 0) ? zigzag(q - qp) : 0ull;
                 const unsigned long long oz = warp_or64(z);
                 const uint32_t w = oz ? (uint32_t)bitlen64(oz) : 0u;
                 if (lane == g) {
                     if (k) ls.wl1 |= (unsigned long long)w << (8 * lv);
                     else ls.wl0 |= (unsigned long long)w << (8 * lv);
                 }
-                ls.words[lv] += ((uint32_t)L * w + 31u) >> 5;
+                ls.words[lv] += (nnz * w + 31u) >> 5;
                 if (oz) ls.nz |= 1u << lv;
-                carry[lv] = shfl64(q, L - 1);
+                const unsigned long long ql = shfl64(q, last);
+                if (nzm) carry[lv] = ql;
             }
+            seen |= nzm != 0;
         }
+        if (k) ls.f1 = first; else ls.f0 = first;
     }
 }
 
@@ -515,24 +619,23 @@ __device__ EncodeOut wencode(const double *re, const double *im, const CodecCfg 
     }
     const bool raw_only = cc.force_raw || nonfin;
 
-    // decision (warp-uniform)
-    int mode, level = 0, s = 0, sm[2] = {0, 0};
+    // decision (warp-uniform).  A zero's sign is kept at shift 0 only, so
+    // the sign sections come in two variants: every sign (lossless) and
+    // the signs of the nonzero values (lossy).
+    int mode, level = 0, s = 0, sm[2] = {0, 0}, zm[2] = {0, 0};
     uint32_t bodyb;
     const uint32_t raw_body = 16u * (uint32_t)N;
     if (raw_only) {
         mode = M_RAW;
         bodyb = raw_body;
     } else {
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const uint32_t v = lane < G ? (k ? ls.sw1 : ls.sw0) : 0u;
-            const bool any1 = __any_sync(FULL, lane < G && v != 0u);
-            const bool allset = __all_sync(FULL, lane >= G || v == lanes);
-            const uint32_t P = __shfl_sync(FULL, v, 0);
-            const bool pat = G >= 2 && __all_sync(FULL, lane >= G || v == P || v == ~P);
-            sm[k] = !any1 ? S_CLEAR : (allset ? S_SET : (pat ? S_PATTERN : S_WORDS));
-        }
-        const uint32_t meta = sign_bytes(sm[0], G) + sign_bytes(sm[1], G);
+        uint32_t zb0, zb1, sbl0, sbl1, sby0, sby1;
+        zm[0] = section_mode(ls.zw0, G, lanes, zb0);
+        zm[1] = section_mode(ls.zw1, G, lanes, zb1);
+        const int sml0 = section_mode(ls.sw0, G, lanes, sbl0);
+        const int sml1 = section_mode(ls.sw1, G, lanes, sbl1);
+        const int smy0 = section_mode(ls.sw0 & ~ls.zw0, G, lanes, sby0);
+        const int smy1 = section_mode(ls.sw1 & ~ls.zw1, G, lanes, sby1);
         const uint32_t wb = (2u * G + 3u) & ~3u;
         mode = M_RAW;
         bodyb = raw_body;
@@ -540,7 +643,10 @@ __device__ EncodeOut wencode(const double *re, const double *im, const CodecCfg 
 #pragma unroll
         for (int lv = 0; lv < MAX_LEVELS; ++lv) {
             if (lv >= cc.nlev || found) continue;
-            if (!((ls.nz >> lv) & 1u) && sm[0] <= S_SET && sm[1] <= S_SET) {
+            const int slv = inel ? 0 : cc.shifts[lv];
+            const int s0 = slv ? smy0 : sml0, s1 = slv ? smy1 : sml1;
+            const uint32_t meta = (slv ? sby0 + sby1 : sbl0 + sbl1) + zb0 + zb1;
+            if (!((ls.nz >> lv) & 1u) && s0 <= S_SET && s1 <= S_SET && zm[0] <= S_SET && zm[1] <= S_SET) {
                 mode = M_CONST; bodyb = 0;
             } else {
                 const uint32_t pb = (meta + wb + 4u * ls.words[lv] + 15u) & ~15u;
@@ -548,6 +654,8 @@ __device__ EncodeOut wencode(const double *re, const double *im, const CodecCfg 
                 else { mode = M_RAW; bodyb = raw_body; }
             }
             level = lv;
+            sm[0] = s0;
+            sm[1] = s1;
             found = (unsigned long long)(HDR + bodyb) <= cc.max_bytes;
         }
         s = mode == M_RAW ? 0 : (inel ? 0 : cc.shifts[level]);
@@ -573,14 +681,14 @@ __device__ EncodeOut wencode(const double *re, const double *im, const CodecCfg 
     // header
     unsigned long long anc0 = 0, anc1 = 0;
     if (mode != M_RAW) {
-        anc0 = quant(dbits(re[0]) & MAG, s);
-        anc1 = quant(dbits(im[0]) & MAG, s);
+        anc0 = quant(ls.f0, s);
+        anc1 = quant(ls.f1, s);
     }
     if (lane < 8) {
         uint32_t v = 0;
         switch (lane) {
             case 0: {
-                const uint32_t smb = mode == M_RAW ? 0u : (uint32_t)(sm[0] | (sm[1] << 2));
+                const uint32_t smb = mode == M_RAW ? 0u : (uint32_t)(sm[0] | (sm[1] << 3));
                 v = (uint32_t)mode | ((uint32_t)s << 8) | ((uint32_t)level << 16) | (smb << 24);
                 break;
             }
@@ -589,7 +697,11 @@ __device__ EncodeOut wencode(const double *re, const double *im, const CodecCfg 
             case 3: v = (uint32_t)(anc0 >> 32); break;
             case 4: v = (uint32_t)anc1; break;
             case 5: v = (uint32_t)(anc1 >> 32); break;
-            case 6: v = (uint32_t)c; break;
+            case 6: {
+                const uint32_t zmb = mode == M_PACKED ? (uint32_t)(zm[0] | (zm[1] << 3)) : 0u;
+                v = (uint32_t)c | (zmb << 8);
+                break;
+            }
             default: v = 0; break;
         }
         reinterpret_cast<uint32_t *>(dst)[lane] = v;
@@ -598,46 +710,48 @@ __device__ EncodeOut wencode(const double *re, const double *im, const CodecCfg 
     unsigned long long nlo = 0, nhi = 0;
     unsigned rng = 0;
     if (mode == M_PACKED) {
-        const uint32_t sb0 = sign_bytes(sm[0], G), sb1 = sign_bytes(sm[1], G);
-        // sign sections
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            uint32_t *sec = reinterpret_cast<uint32_t *>(b + (k ? sb0 : 0));
-            const uint32_t v = lane < G ? (k ? ls.sw1 : ls.sw0) : 0u;
-            if (sm[k] == S_PATTERN) {
-                const uint32_t P = __shfl_sync(FULL, v, 0);
-                const uint32_t fl = __ballot_sync(FULL, lane < G && v != P);
-                if (lane == 0) { sec[0] = P; sec[1] = fl; }
-            } else if (sm[k] == S_WORDS) {
-                if (lane < G) sec[lane] = v;
-            }
-        }
+        // sign sections, then zero sections
+        const uint32_t sv0 = s ? ls.sw0 & ~ls.zw0 : ls.sw0, sv1 = s ? ls.sw1 & ~ls.zw1 : ls.sw1;
+        uint32_t moff = 0, sz;
+        write_section(reinterpret_cast<uint32_t *>(b + moff), sm[0], sv0, G, lanes);
+        moff += (section_mode(sv0, G, lanes, sz), sz);
+        write_section(reinterpret_cast<uint32_t *>(b + moff), sm[1], sv1, G, lanes);
+        moff += (section_mode(sv1, G, lanes, sz), sz);
+        write_section(reinterpret_cast<uint32_t *>(b + moff), zm[0], ls.zw0, G, lanes);
+        moff += (section_mode(ls.zw0, G, lanes, sz), sz);
+        write_section(reinterpret_cast<uint32_t *>(b + moff), zm[1], ls.zw1, G, lanes);
+        moff += (section_mode(ls.zw1, G, lanes, sz), sz);
         // widths at the chosen level, word offsets
         const uint32_t ws0 = (uint32_t)(ls.wl0 >> (8 * level)) & 0xFFu;
         const uint32_t ws1 = (uint32_t)(ls.wl1 >> (8 * level)) & 0xFFu;
         uint32_t tot0, tot1;
-        const uint32_t off0 = warp_exscan(lane < G ? ((uint32_t)L * ws0 + 31u) >> 5 : 0u, tot0);
-        const uint32_t off1 = warp_exscan(lane < G ? ((uint32_t)L * ws1 + 31u) >> 5 : 0u, tot1) + tot0;
+        const uint32_t nn0 = __popc(~ls.zw0 & lanes), nn1 = __popc(~ls.zw1 & lanes);
+        const uint32_t off0 = warp_exscan(lane < G ? (nn0 * ws0 + 31u) >> 5 : 0u, tot0);
+        const uint32_t off1 = warp_exscan(lane < G ? (nn1 * ws1 + 31u) >> 5 : 0u, tot1) + tot0;
         const uint32_t wb = (2u * G + 3u) & ~3u;
         for (uint32_t base = 0; base < wb; base += 32) {          // uniform trip count
             const int t = (int)base + lane;
             const int src = t < G ? t : (t < 2 * G ? t - G : 0);
             const uint32_t a = __shfl_sync(FULL, ws0, src & 31);
             const uint32_t bb = __shfl_sync(FULL, ws1, src & 31);
-            if ((uint32_t)t < wb) b[sb0 + sb1 + t] = (uint8_t)(t < G ? a : (t < 2 * G ? bb : 0u));
+            if ((uint32_t)t < wb) b[moff + t] = (uint8_t)(t < G ? a : (t < 2 * G ? bb : 0u));
         }
-        const uint32_t doff = sb0 + sb1 + wb;
+        const uint32_t doff = moff + wb;
         uint32_t *data = reinterpret_cast<uint32_t *>(b + doff);
+        const uint32_t below = lanes_below();
         for (int k = 0; k < 2; ++k) {
             const double *v = k ? im : re;
             const uint32_t wk = k ? ws1 : ws0, offk = k ? off1 : off0;
-            unsigned long long carry = 0;
+            unsigned long long carry = quant(k ? ls.f1 : ls.f0, s);     // the anchor
             for (int g = 0; g < G; ++g) {
                 const unsigned long long B = lane < L ? (dbits(v[g * 32 + lane]) & MAG) : 0ull;
                 const unsigned long long q = quant(B, s);
-                unsigned long long qp = shfl_up64(q, 1);
-                if (lane == 0) qp = g == 0 ? q : carry;
-                carry = shfl64(q, L - 1);
+                const uint32_t nzm = __ballot_sync(FULL, lane < L && B != 0);
+                const uint32_t pm = nzm & below;
+                const unsigned long long qs = shfl64(q, pm ? 31 - __clz(pm) : lane);
+                const unsigned long long qp = pm ? qs : carry;
+                const unsigned long long ql = shfl64(q, nzm ? 31 - __clz(nzm) : 0);
+                if (nzm) carry = ql;
                 if (lane < L) {
                     unsigned long long l0, h0;
                     sq_units(q << s, l0, h0, rng);
@@ -646,13 +760,14 @@ __device__ EncodeOut wencode(const double *re, const double *im, const CodecCfg 
                 const uint32_t w = __shfl_sync(FULL, wk, g);
                 if (w == 0) continue;
                 const uint32_t wo = __shfl_sync(FULL, offk, g);
-                const uint32_t nwd = ((uint32_t)L * w + 31u) >> 5;
-                const unsigned long long z = lane < L ? zigzag(q - qp) : 0ull;
+                const uint32_t nwd = ((uint32_t)__popc(nzm) * w + 31u) >> 5;
+                const bool nzl = (nzm >> lane) & 1u;
+                const unsigned long long z = nzl ? zigzag(q - qp) : 0ull;
                 wstage[lane] = 0u;
                 wstage[lane + 32] = 0u;
                 __syncwarp();
-                if (lane < L) {
-                    const uint32_t bo = (uint32_t)lane * w, j0 = bo >> 5, sh = bo & 31u;
+                if (nzl) {
+                    const uint32_t bo = (uint32_t)__popc(nzm & below) * w, j0 = bo >> 5, sh = bo & 31u;
                     atomicOr(&wstage[j0], (uint32_t)(z << sh));
                     if (sh + w > 32) atomicOr(&wstage[j0 + 1], (uint32_t)(z >> (32 - sh)));
                     if (sh + w > 64) atomicOr(&wstage[j0 + 2], (uint32_t)(z >> (64 - sh)));

@@ -51,6 +51,7 @@ struct DGate {
 struct SGate {
     double d[8];                    // diagonal gates: entry r (re, im), r < 2^k
     unsigned long long cls;         // entry classes, 3 bits each (see entry classes below)
+    unsigned long long fac;         // factored rows: bit r row r; bits 8+2e factor of entry e
     unsigned long long fcm, fcv;    // controls on fixed qubits (global bits)
     uint32_t lcm, lcv;              // controls on buffer bits
     uint8_t kind;                   // 0 diagonal, 1 one-target, 2 two-target (non-diagonal)

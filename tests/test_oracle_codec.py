@@ -52,11 +52,17 @@ def amplitudes(e):
     if spec == ["ramp"]:
         re = [d(0x3FE0000000000000 + (i << 39)) for i in range(N)]
         return np.array(re, dtype=np.complex128)
+    if spec == ["sparse"]:
+        re = [d(0x3FE0000000000000 + ((i // 2) << 39)) if i % 2 == 0 else 0.0 for i in range(N)]
+        return np.array(re, dtype=np.complex128)
     if spec == ["signs"]:
         out = np.zeros(N, dtype=np.complex128)
         for i in range(N):
             g, l = divmod(i, 32)
-            word = 0x0F0F0F0F if g == 0 else 0xF0F0F0F0
+            if N == 64:
+                word = 0x0F0F0F0F if g == 0 else 0xF0F0F0F0
+            else:
+                word = 0x0F0F0F0F if g == 2 else 0xFFFFFFFF
             out[i] = -1.0 if (word >> l) & 1 else 1.0
         return out
     vals = []
@@ -74,7 +80,8 @@ def test_golden_stream(e):
     assert stream.hex() == e["hex"]
     assert level == 0 and flags == 0
     back = oracle.decode_tile(stream, e["c"])
-    if e["s"] == 0 or e["name"] in ("const_c5", "ramp_c5", "signs_c6"):
+    if e["s"] == 0 or e["name"] in ("const_c5", "ramp_c5", "signs_c6", "signs_c7", "delta_c6",
+                                         "sparse_c5"):
         # these inputs are exactly representable at their shift
         assert back.view(np.uint64).tolist() == a.view(np.uint64).tolist()
 
@@ -193,7 +200,12 @@ def test_zero_tile_and_signed_zeros():
     assert len(stream) == 32 and stream[0] == 0          # header only
     a = np.zeros(256, dtype=np.complex128)
     a.real[5] = -0.0
+    # lossy level: a zero's sign is not kept, the tile is still CONST
     stream, _, _ = oracle.encode_tile(a, 8, [39])
+    assert len(stream) == 32 and stream[0] == 0
+    assert np.array_equal(oracle.decode_tile(stream, 8).view(np.uint64), np.zeros(512, np.uint64))
+    # lossless level: bit-exact, -0 included
+    stream, _, _ = oracle.encode_tile(a, 8, [0])
     back = oracle.decode_tile(stream, 8)
     assert np.array_equal(back.view(np.uint64), a.view(np.uint64))
 
@@ -220,7 +232,7 @@ def test_ladder_picks_first_level_within_limit():
 
 
 def test_malformed_streams_are_rejected():
-    a = np.exp(1j * np.arange(64) * 0.37) / 8
+    a = np.exp(1j * (np.arange(64) * 0.37 + 0.1)) / 8
     stream, _, _ = oracle.encode_tile(a, 6, [39])
     with pytest.raises(ValueError):
         oracle.decode_tile(stream[:20], 6)                # short header
@@ -231,9 +243,10 @@ def test_malformed_streams_are_rejected():
     with pytest.raises(ValueError):
         oracle.decode_tile(bytes(bad), 6)
     assert stream[0] == 1
-    G = 2
-    size = {0: 0, 1: 0, 2: 4 + 4 * ((G + 31) // 32), 3: 4 * G}
-    woff = 32 + size[stream[3] & 3] + size[(stream[3] >> 2) & 3]
+    # a phase ramp: nonzero, mixed signs; no zero sections, sign words in
+    # mode 4 (two groups of mixed words)
+    assert stream[3] == 4 | 4 << 3 and stream[25] == 0
+    woff = 32 + 8 + 8
     bad = bytearray(stream)
     bad[woff] = 65                                        # width > 64
     with pytest.raises(ValueError):
@@ -242,3 +255,45 @@ def test_malformed_streams_are_rejected():
     bad[woff] = 64                                        # data past the body
     with pytest.raises(ValueError):
         oracle.decode_tile(bytes(bad), 6)
+
+
+@pytest.mark.parametrize("s", [0, 39])
+def test_sparse_tiles_keep_zeros_and_bound(s):
+    """Zero words: zero components (either sign) come back bit-exact, the
+    others within the bound, for tiles from fully dense to a single spike."""
+    rng = np.random.default_rng(17 + s)
+    c = 8
+    N = 1 << c
+    for frac in (0.0, 0.3, 0.7, 0.97, 1.0):
+        comps = rng.standard_normal(2 * N) / 16
+        comps[rng.random(2 * N) < frac] = 0.0
+        neg0 = (comps == 0) & (rng.random(2 * N) < 0.5)
+        comps[neg0] = -0.0
+        a = comps.view(np.complex128)
+        stream, _, flags = oracle.encode_tile(a, c, [s])
+        assert flags & 1 == 0
+        back = oracle.decode_tile(stream, c).view(np.float64)
+        z = comps == 0
+        # zeros come back exactly; their sign only at the lossless level
+        want = comps[z] if s == 0 else np.zeros(int(z.sum()))
+        assert np.array_equal(back[z].view(np.uint64), want.view(np.uint64))
+        if s == 0:
+            assert np.array_equal(back.view(np.uint64), comps.view(np.uint64))
+        else:
+            diff = np.abs(back[~z] - comps[~z])
+            assert np.all(diff < np.ldexp(np.abs(comps[~z]), s - 53))
+
+
+def test_single_spike_tile_is_small():
+    """A tile holding one nonzero amplitude costs a header, the zero words
+    and the width bytes, not a word per value."""
+    c = 8
+    for pos in (0, 77, 255):
+        a = np.zeros(1 << c, dtype=np.complex128)
+        a[pos] = 0.3 - 0.7j
+        stream, _, _ = oracle.encode_tile(a, c, [39])
+        # header 32 + re zero exceptions 8 + im sign exceptions 8 + im
+        # zero exceptions 8 + 16 width bytes = 72 -> body padded: 80
+        assert stream[0] == 1 and len(stream) == 80
+        back = oracle.decode_tile(stream, c)
+        assert np.count_nonzero(back) == 1 and abs(back[pos] - a[pos]) < 1e-4

@@ -165,3 +165,50 @@ def test_non_diagonal_gate_needs_its_target():
     psi = oracle.dense_zero(3)
     oracle.dense_apply(psi, 3, I.h(2))
     assert abs(psi[0] - I.S2) < 1e-16 and abs(psi[4] - I.S2) < 1e-16
+
+
+def unit_factor_matrix(rng, dim):
+    """Rows whose nonzero entries are f * d, f in {1, -1, i, -i}, d the
+    row's first nonzero entry of a random class: the factored rows."""
+    M = np.zeros((dim, dim), dtype=np.complex128)
+    for r in range(dim):
+        d = complex(rng.normal(), rng.normal())
+        kind = rng.integers(0, 3)
+        if kind == 1:
+            d = complex(d.real, 0.0)
+        elif kind == 2:
+            d = complex(0.0, d.imag)
+        cols = [c for c in range(dim) if c == 0 or rng.random() < 0.8]
+        for j, c in enumerate(cols):
+            M[r, c] = d if j == 0 else d * [1, -1, 1j, -1j][rng.integers(0, 4)]
+    return M
+
+
+@pytest.mark.parametrize("n", [2, 4, 6])
+def test_factored_rows_match_definition(n):
+    rng = np.random.default_rng(300 + n)
+    for trial in range(16):
+        k = 1 + trial % 2
+        targets = tuple(int(q) for q in rng.permutation(n)[:k])
+        g = I.Gate(unit_factor_matrix(rng, 1 << k), targets)
+        psi = random_state(rng, n)
+        ref = operator_from_definition(n, g) @ psi
+        out = psi.copy()
+        oracle.dense_apply(out, n, g)
+        assert np.max(np.abs(out - ref)) < 1e-14, (targets, g.matrix)
+
+
+def test_hadamards_cancel_equal_amplitudes_exactly():
+    """A Hadamard row is factored: on a uniform state H on every qubit
+    leaves exact zeros everywhere but index 0, and H on one qubit of a
+    pairwise-equal state leaves exact zeros in the odd half."""
+    n = 8
+    psi = np.full(1 << n, complex(0.37, -0.21))
+    for q in range(n):
+        oracle.dense_apply(psi, n, I.h(q))
+    assert np.count_nonzero(psi) == 1 and abs(psi[0] - 16 * complex(0.37, -0.21)) < 1e-13
+    rng = np.random.default_rng(9)
+    half = rng.normal(size=1 << (n - 1)) + 1j * rng.normal(size=1 << (n - 1))
+    psi = np.repeat(half, 2)                     # equal in qubit 0
+    oracle.dense_apply(psi, n, I.h(0))
+    assert np.all(psi[1::2] == 0)
