@@ -21,6 +21,7 @@ constexpr unsigned long long MIN_NORMAL = 0x0010000000000000ull;
 constexpr unsigned long long LOSSY_LIMIT = 0x7FE0000000000000ull;
 constexpr unsigned long long INF_BITS = 0x7FF0000000000000ull;
 constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr unsigned long long SIGN_BIT = 0x8000000000000000ull;
 
 enum { M_CONST = 0, M_PACKED = 1, M_RAW = 2 };
 enum { S_CLEAR = 0, S_SET = 1, S_EXC_CLEAR = 2, S_EXC_SET = 3, S_WORDS = 4 };
@@ -161,6 +162,16 @@ __device__ __forceinline__ void term_acc(unsigned code, double ur, double ui, do
     }
 }
 
+// t = f x for a factor code f (0: 1, 1: -1, 2: i, 3: -i): a selection and
+// sign-bit flips, exact and off the FP64 pipe
+__device__ __forceinline__ void unit_times(unsigned f, double xr, double xi, double &tr, double &ti) {
+    const unsigned long long nr = (f == 1u || f == 2u) ? SIGN_BIT : 0ull;
+    const unsigned long long ni = (f == 1u || f == 3u) ? SIGN_BIT : 0ull;
+    const bool sw = f >= 2u;
+    tr = bitsd(dbits(sw ? xi : xr) ^ nr);
+    ti = bitsd(dbits(sw ? xr : xi) ^ ni);
+}
+
 // Row r of y = U x over the nonzero entries, in column order.  A factored
 // row (bit r of fac: every nonzero entry is f d, f in {1, -1, i, -i}, d
 // the first nonzero entry; f of entry e in bits 8 + 2e, codes 0..3 for
@@ -180,17 +191,16 @@ __device__ __forceinline__ void row_eval(const double *m, unsigned long long cls
             const int e = r * DIM + c;
             const unsigned code = (unsigned)(cls >> (3 * e)) & 7u;
             if (code == EC_ZERO) continue;
-            const unsigned f = (unsigned)(fac >> (8 + 2 * e)) & 3u;
-            const double tr = f == 0 ? xr[c] : (f == 1 ? -xr[c] : (f == 2 ? -xi[c] : xi[c]));
-            const double ti = f == 0 ? xi[c] : (f == 1 ? -xi[c] : (f == 2 ? xr[c] : -xr[c]));
-            if (first) {
-                ar = tr; ai = ti;
+            if (first) {                      // the first entry is d itself: factor 1
+                ar = xr[c]; ai = xi[c];
                 dcode = code; dr = m[2 * e]; di = m[2 * e + 1];
                 first = false;
-            } else {
-                ar = __dadd_rn(ar, tr);
-                ai = __dadd_rn(ai, ti);
+                continue;
             }
+            double tr, ti;
+            unit_times((unsigned)(fac >> (8 + 2 * e)) & 3u, xr[c], xi[c], tr, ti);
+            ar = __dadd_rn(ar, tr);
+            ai = __dadd_rn(ai, ti);
         }
         term_first(dcode, dr, di, ar, ai, yr, yi);
         return;
@@ -268,6 +278,25 @@ __device__ void one_target(double *re, double *im, int mb, const SGate &s, const
     for (int i = 0; i < 8; ++i) m[i] = dg.m[i];
     const unsigned bit = 1u << s.p0;
     const unsigned cnt = 1u << (mb - s.nins);
+    if ((s.fac & 3ull) == 3ull && (s.cls & 7ull) == EC_REAL && ((s.cls >> 6) & 7ull) == EC_REAL) {
+        // both rows factored with a real first entry (Hadamard-like):
+        // y_r = d_r (x_0 + f_r x_1), the same arithmetic as row_eval
+        const double d0 = m[0], d1 = m[4];
+        const unsigned f0 = (unsigned)(s.fac >> 10) & 3u, f1 = (unsigned)(s.fac >> 14) & 3u;
+        for (unsigned f = threadIdx.x; f < cnt; f += THREADS) {
+            const unsigned l0 = deposit(f, s) | s.lcv;
+            const unsigned l1 = l0 | bit;
+            const double x0r = re[l0], x0i = im[l0], x1r = re[l1], x1i = im[l1];
+            double t0r, t0i, t1r, t1i;
+            unit_times(f0, x1r, x1i, t0r, t0i);
+            unit_times(f1, x1r, x1i, t1r, t1i);
+            re[l0] = __dmul_rn(d0, __dadd_rn(x0r, t0r));
+            im[l0] = __dmul_rn(d0, __dadd_rn(x0i, t0i));
+            re[l1] = __dmul_rn(d1, __dadd_rn(x0r, t1r));
+            im[l1] = __dmul_rn(d1, __dadd_rn(x0i, t1i));
+        }
+        return;
+    }
     for (unsigned f = threadIdx.x; f < cnt; f += THREADS) {
         unsigned l0 = deposit(f, s) | s.lcv;
         unsigned l1 = l0 | bit;
@@ -471,11 +500,13 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
             const uint32_t sgw = __shfl_sync(FULL, swk, g);
             const uint32_t nzw = ~__shfl_sync(FULL, zwk, g) & lanes;
             const bool nzl = (nzw >> lane) & 1u;
-            const uint32_t nwd = ((uint32_t)__popc(nzw) * w + 31u) >> 5;
+            const bool dense = nzw == lanes;                 // uniform: no zero in the group
+            const uint32_t nwd = ((dense ? (uint32_t)L : (uint32_t)__popc(nzw)) * w + 31u) >> 5;
             unsigned long long z = 0;
             if (nzl && w) {
                 const uint32_t *base = data + wo;
-                uint32_t bo = (uint32_t)__popc(nzw & below) * w, j0 = bo >> 5, sh = bo & 31u;
+                const uint32_t rank = dense ? (uint32_t)lane : (uint32_t)__popc(nzw & below);
+                uint32_t bo = rank * w, j0 = bo >> 5, sh = bo & 31u;
                 uint32_t x0 = __ldg(base + j0);
                 uint32_t x1 = j0 + 1 < nwd ? __ldg(base + j0 + 1) : 0u;
                 uint32_t x2 = j0 + 2 < nwd ? __ldg(base + j0 + 2) : 0u;
@@ -518,10 +549,9 @@ struct EncodeOut {
 };
 
 // One pass over a tile: zero and sign words, the first nonzero magnitude,
-// and group widths and word totals at every ladder level.
+// and group widths at every ladder level.
 struct LevelSizes {
     unsigned long long wl0, wl1;      // lane g: width of group g per level (byte lv)
-    uint32_t words[MAX_LEVELS];       // data words per level (warp-uniform)
     uint32_t nz;                      // bit lv: some residual nonzero at level lv
     uint32_t sw0, sw1;                // lane g: sign words (every value)
     uint32_t zw0, zw1;                // lane g: zero words (bit l: magnitude 0)
@@ -531,26 +561,23 @@ struct LevelSizes {
 // Pass 1 of the encoder.  Residuals run along the nonzero values of a
 // component: each against the previous nonzero code, the first against
 // itself (the anchor).  A zero code only arises from a zero magnitude: any
-// other value below the lossy range forces shift 0.
+// other value below the lossy range forces shift 0.  The predecessor's
+// magnitude bits are found once per group; each level quantises both.
 // force0: code every level with shift 0 (values outside the lossy range).
 __device__ __forceinline__ void size_levels(const double *re, const double *im, const CodecCfg &cc,
                                             int G, int L, bool force0, LevelSizes &ls, int &nonfin,
                                             int &inel) {
     const int lane = threadIdx.x & 31;
     const uint32_t below = lanes_below();
+    const uint32_t lanes = L == 32 ? FULL : ((1u << L) - 1u);
     ls.wl0 = ls.wl1 = 0;
     ls.nz = 0;
     ls.sw0 = ls.sw1 = ls.zw0 = ls.zw1 = 0;
     ls.f0 = ls.f1 = 0;
-#pragma unroll
-    for (int lv = 0; lv < MAX_LEVELS; ++lv) ls.words[lv] = 0;
     for (int k = 0; k < 2; ++k) {
         const double *v = k ? im : re;
-        unsigned long long carry[MAX_LEVELS];
-#pragma unroll
-        for (int lv = 0; lv < MAX_LEVELS; ++lv) carry[lv] = 0;
         bool seen = false;
-        unsigned long long first = 0;
+        unsigned long long first = 0, lastB = 0, wl = 0;
         for (int g = 0; g < G; ++g) {
             const unsigned long long u = lane < L ? dbits(v[g * 32 + lane]) : 0ull;
             const unsigned long long B = u & MAG;
@@ -559,36 +586,38 @@ __device__ __forceinline__ void size_levels(const double *re, const double *im, 
             const uint32_t sw = __ballot_sync(FULL, lane < L && (u >> 63));
             const uint32_t nzm = __ballot_sync(FULL, lane < L && B != 0);
             if (lane == g) {
-                if (k) { ls.sw1 = sw; ls.zw1 = ~nzm & (L == 32 ? FULL : ((1u << L) - 1u)); }
-                else { ls.sw0 = sw; ls.zw0 = ~nzm & (L == 32 ? FULL : ((1u << L) - 1u)); }
+                if (k) { ls.sw1 = sw; ls.zw1 = ~nzm & lanes; }
+                else { ls.sw0 = sw; ls.zw0 = ~nzm & lanes; }
             }
-            const uint32_t pm = nzm & below;                 // nonzero lanes before this one
-            const int src = pm ? 31 - __clz(pm) : lane;
-            const int last = nzm ? 31 - __clz(nzm) : 0;
-            const uint32_t nnz = __popc(nzm);
+            // magnitude bits of the previous nonzero value (uniform branch:
+            // a group without zeros, the common case, takes the lane below)
+            unsigned long long Bp;
+            if (nzm == lanes) {
+                const unsigned long long up = shfl_up64(B, 1);
+                Bp = lane ? up : (seen ? lastB : B);
+            } else {
+                const uint32_t pm = nzm & below;             // nonzero lanes before this one
+                const unsigned long long Bs = shfl64(B, pm ? 31 - __clz(pm) : lane);
+                Bp = pm ? Bs : (seen ? lastB : B);
+            }
             if (!seen && nzm) first = shfl64(B, __ffs(nzm) - 1);
+            const bool nzl = (nzm >> lane) & 1u;
+            unsigned long long wg = 0;
 #pragma unroll
             for (int lv = 0; lv < MAX_LEVELS; ++lv) {
                 if (lv >= cc.nlev) continue;
                 const int s = force0 ? 0 : cc.shifts[lv];
-                const unsigned long long q = quant(B, s);
-                const unsigned long long qs = shfl64(q, src);
-                const unsigned long long qp = pm ? qs : (seen ? carry[lv] : q);
-                const unsigned long long z = (lane < L && B != 0) ? zigzag(q - qp) : 0ull;
+                const unsigned long long z = nzl ? zigzag(quant(B, s) - quant(Bp, s)) : 0ull;
                 const unsigned long long oz = warp_or64(z);
                 const uint32_t w = oz ? (uint32_t)bitlen64(oz) : 0u;
-                if (lane == g) {
-                    if (k) ls.wl1 |= (unsigned long long)w << (8 * lv);
-                    else ls.wl0 |= (unsigned long long)w << (8 * lv);
-                }
-                ls.words[lv] += (nnz * w + 31u) >> 5;
+                wg |= (unsigned long long)w << (8 * lv);
                 if (oz) ls.nz |= 1u << lv;
-                const unsigned long long ql = shfl64(q, last);
-                if (nzm) carry[lv] = ql;
             }
+            if (lane == g) wl = wg;
+            if (nzm) lastB = shfl64(B, 31 - __clz(nzm));
             seen |= nzm != 0;
         }
-        if (k) ls.f1 = first; else ls.f0 = first;
+        if (k) { ls.f1 = first; ls.wl1 = wl; } else { ls.f0 = first; ls.wl0 = wl; }
     }
 }
 
@@ -637,6 +666,8 @@ __device__ EncodeOut wencode(const double *re, const double *im, const CodecCfg 
         const int smy0 = section_mode(ls.sw0 & ~ls.zw0, G, lanes, sby0);
         const int smy1 = section_mode(ls.sw1 & ~ls.zw1, G, lanes, sby1);
         const uint32_t wb = (2u * G + 3u) & ~3u;
+        const uint32_t nn0 = lane < G ? (uint32_t)__popc(~ls.zw0 & lanes) : 0u;
+        const uint32_t nn1 = lane < G ? (uint32_t)__popc(~ls.zw1 & lanes) : 0u;
         mode = M_RAW;
         bodyb = raw_body;
         bool found = false;                  // first level within the size limit, else the last
@@ -649,7 +680,9 @@ __device__ EncodeOut wencode(const double *re, const double *im, const CodecCfg 
             if (!((ls.nz >> lv) & 1u) && s0 <= S_SET && s1 <= S_SET && zm[0] <= S_SET && zm[1] <= S_SET) {
                 mode = M_CONST; bodyb = 0;
             } else {
-                const uint32_t pb = (meta + wb + 4u * ls.words[lv] + 15u) & ~15u;
+                const uint32_t w0 = (uint32_t)(ls.wl0 >> (8 * lv)) & 0xFFu, w1 = (uint32_t)(ls.wl1 >> (8 * lv)) & 0xFFu;
+                const uint32_t words = __reduce_add_sync(FULL, ((nn0 * w0 + 31u) >> 5) + ((nn1 * w1 + 31u) >> 5));
+                const uint32_t pb = (meta + wb + 4u * words + 15u) & ~15u;
                 if (pb < raw_body) { mode = M_PACKED; bodyb = pb; }
                 else { mode = M_RAW; bodyb = raw_body; }
             }
@@ -747,10 +780,17 @@ __device__ EncodeOut wencode(const double *re, const double *im, const CodecCfg 
                 const unsigned long long B = lane < L ? (dbits(v[g * 32 + lane]) & MAG) : 0ull;
                 const unsigned long long q = quant(B, s);
                 const uint32_t nzm = __ballot_sync(FULL, lane < L && B != 0);
-                const uint32_t pm = nzm & below;
-                const unsigned long long qs = shfl64(q, pm ? 31 - __clz(pm) : lane);
-                const unsigned long long qp = pm ? qs : carry;
-                const unsigned long long ql = shfl64(q, nzm ? 31 - __clz(nzm) : 0);
+                const bool dense = nzm == lanes;             // uniform: no zero in the group
+                unsigned long long qp;
+                if (dense) {
+                    const unsigned long long up = shfl_up64(q, 1);
+                    qp = lane ? up : carry;
+                } else {
+                    const uint32_t pm = nzm & below;
+                    const unsigned long long qs = shfl64(q, pm ? 31 - __clz(pm) : lane);
+                    qp = pm ? qs : carry;
+                }
+                const unsigned long long ql = shfl64(q, dense ? L - 1 : (nzm ? 31 - __clz(nzm) : 0));
                 if (nzm) carry = ql;
                 if (lane < L) {
                     unsigned long long l0, h0;
@@ -767,7 +807,8 @@ __device__ EncodeOut wencode(const double *re, const double *im, const CodecCfg 
                 wstage[lane + 32] = 0u;
                 __syncwarp();
                 if (nzl) {
-                    const uint32_t bo = (uint32_t)__popc(nzm & below) * w, j0 = bo >> 5, sh = bo & 31u;
+                    const uint32_t rank = dense ? (uint32_t)lane : (uint32_t)__popc(nzm & below);
+                    const uint32_t bo = rank * w, j0 = bo >> 5, sh = bo & 31u;
                     atomicOr(&wstage[j0], (uint32_t)(z << sh));
                     if (sh + w > 32) atomicOr(&wstage[j0 + 1], (uint32_t)(z >> (32 - sh)));
                     if (sh + w > 64) atomicOr(&wstage[j0 + 2], (uint32_t)(z >> (64 - sh)));
