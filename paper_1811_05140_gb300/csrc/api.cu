@@ -763,6 +763,14 @@ qs::SweepParams sweep_params(qsim_t h, const FlushCtx &fc, size_t j) {
     p.nitems = h->ntiles >> sw.h;
     p.sweep_id = fc.id0 + (unsigned)j;
     p.use_alpha = h->normalize;
+    p.low_free = 1;
+    const unsigned long long lowm = (1ull << h->c) - 1ull;
+    for (int gi = sw.lo; gi < sw.hi && p.low_free; ++gi) {
+        const HostGate &g = h->queue[gi];
+        if (g.cm & lowm) p.low_free = 0;
+        for (int i = 0; i < g.k; ++i)
+            if (g.t[i] < h->c) p.low_free = 0;
+    }
     return p;
 }
 

@@ -246,7 +246,7 @@ __device__ __forceinline__ bool gate_active(const SGate &s, unsigned long long f
 // entry other than exactly 1.  Enumerating just those keeps every lane of
 // every FP64 instruction busy (masked lanes cost the same on this part).
 __device__ void diag_gate(double *re, double *im, int mb, const SGate &s,
-                          unsigned long long fixed) {
+                          unsigned long long fixed, int red) {
     // sub-indices r to visit: entry != 1 and consistent with fixed targets
     unsigned rpack = 0;          // sub-indices, 2 bits each
     int nr = 0;
@@ -257,11 +257,11 @@ __device__ void diag_gate(double *re, double *im, int mb, const SGate &s,
     for (int r = 0; r < dim; ++r)
         if ((r & fmask) == fval && !((s.one_mask >> r) & 1)) rpack |= (unsigned)r << (2 * nr++);
     if (nr == 0) return;
-    const int fb = mb - s.nins;                 // free bits
+    const int fb = mb - s.nins - red;           // free bits (the low `red` bits stay 0)
     const unsigned cnt = (unsigned)nr << fb;
     for (unsigned f = threadIdx.x; f < cnt; f += THREADS) {
         int r = (int)((rpack >> (2 * (f >> fb))) & 3u);
-        unsigned l = deposit(f & ((1u << fb) - 1u), s) | s.lcv;
+        unsigned l = deposit((f & ((1u << fb) - 1u)) << red, s) | s.lcv;
         if (s.p0 >= 0) l |= (unsigned)(r & 1) << s.p0;
         if (s.k > 1 && s.p1 >= 0) l |= (unsigned)((r >> 1) & 1) << s.p1;
         unsigned code = (unsigned)(s.cls >> (3 * r)) & 7u;
@@ -272,19 +272,19 @@ __device__ void diag_gate(double *re, double *im, int mb, const SGate &s,
     }
 }
 
-__device__ void one_target(double *re, double *im, int mb, const SGate &s, const DGate &dg) {
+__device__ void one_target(double *re, double *im, int mb, const SGate &s, const DGate &dg, int red) {
     double m[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) m[i] = dg.m[i];
     const unsigned bit = 1u << s.p0;
-    const unsigned cnt = 1u << (mb - s.nins);
+    const unsigned cnt = 1u << (mb - s.nins - red);
     if ((s.fac & 3ull) == 3ull && (s.cls & 7ull) == EC_REAL && ((s.cls >> 6) & 7ull) == EC_REAL) {
         // both rows factored with a real first entry (Hadamard-like):
         // y_r = d_r (x_0 + f_r x_1), the same arithmetic as row_eval
         const double d0 = m[0], d1 = m[4];
         const unsigned f0 = (unsigned)(s.fac >> 10) & 3u, f1 = (unsigned)(s.fac >> 14) & 3u;
         for (unsigned f = threadIdx.x; f < cnt; f += THREADS) {
-            const unsigned l0 = deposit(f, s) | s.lcv;
+            const unsigned l0 = deposit(f << red, s) | s.lcv;
             const unsigned l1 = l0 | bit;
             const double x0r = re[l0], x0i = im[l0], x1r = re[l1], x1i = im[l1];
             double t0r, t0i, t1r, t1i;
@@ -298,7 +298,7 @@ __device__ void one_target(double *re, double *im, int mb, const SGate &s, const
         return;
     }
     for (unsigned f = threadIdx.x; f < cnt; f += THREADS) {
-        unsigned l0 = deposit(f, s) | s.lcv;
+        unsigned l0 = deposit(f << red, s) | s.lcv;
         unsigned l1 = l0 | bit;
         double xr[2] = {re[l0], re[l1]}, xi[2] = {im[l0], im[l1]};
         double y0r, y0i, y1r, y1i;
@@ -309,10 +309,10 @@ __device__ void one_target(double *re, double *im, int mb, const SGate &s, const
     }
 }
 
-__device__ void two_target(double *re, double *im, int mb, const SGate &s, const DGate &dg) {
-    const unsigned cnt = 1u << (mb - s.nins);
+__device__ void two_target(double *re, double *im, int mb, const SGate &s, const DGate &dg, int red) {
+    const unsigned cnt = 1u << (mb - s.nins - red);
     for (unsigned f = threadIdx.x; f < cnt; f += THREADS) {
-        unsigned l = deposit(f, s) | s.lcv;
+        unsigned l = deposit(f << red, s) | s.lcv;
         unsigned idx[4];
         double xr[4], xi[4];
 #pragma unroll
@@ -330,15 +330,17 @@ __device__ void two_target(double *re, double *im, int mb, const SGate &s, const
 }
 
 // Apply the sweep's gates (in order) to an item buffer of 2^mb amplitudes.
-// active: bit g set when gate g changes something in this item.
-__device__ void apply_gates(double *re, double *im, int mb, const SGate *sg, const DGate *dg,
+// active: bit g set when gate g changes something in this item.  red > 0:
+// only the amplitudes whose low `red` index bits are 0 (one per tile, for
+// an item of uniform tiles under gates that touch no low qubit).
+__device__ void apply_gates(double *re, double *im, int mb, int red, const SGate *sg, const DGate *dg,
                             int ngates, unsigned long long active, unsigned long long fixed) {
     for (int g = 0; g < ngates; ++g) {
         if (!((active >> g) & 1ull)) continue;
         const SGate &s = sg[g];
-        if (s.kind == 0) diag_gate(re, im, mb, s, fixed);
-        else if (s.kind == 1) one_target(re, im, mb, s, dg[g]);
-        else two_target(re, im, mb, s, dg[g]);
+        if (s.kind == 0) diag_gate(re, im, mb, s, fixed, red);
+        else if (s.kind == 1) one_target(re, im, mb, s, dg[g], red);
+        else two_target(re, im, mb, s, dg[g], red);
         __syncthreads();
     }
 }
@@ -500,6 +502,14 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
             const uint32_t sgw = __shfl_sync(FULL, swk, g);
             const uint32_t nzw = ~__shfl_sync(FULL, zwk, g) & lanes;
             const bool nzl = (nzw >> lane) & 1u;
+            if (nzw == 0u) {                                 // all zeros: signs only
+                if (lane < L) {
+                    double x = bitsd((unsigned long long)((sgw >> lane) & 1u) << 63);
+                    if (scale) x = __dmul_rn(x, alpha);
+                    v[g * 32 + lane] = x;
+                }
+                continue;
+            }
             const bool dense = nzw == lanes;                 // uniform: no zero in the group
             const uint32_t nwd = ((dense ? (uint32_t)L : (uint32_t)__popc(nzw)) * w + 31u) >> 5;
             unsigned long long z = 0;
@@ -516,7 +526,9 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
             }
             const unsigned long long r = unzigzag(z);        // 0 for zeros and lanes >= L
             unsigned long long inc;
-            if (w <= 27) {                      // 32 partial sums of |r| < 2^26 fit in int32
+            if (w == 0) {                                    // every residual 0
+                inc = 0;
+            } else if (w <= 27) {                      // 32 partial sums of |r| < 2^26 fit in int32
                 int v32 = (int)(long long)r;
                 for (int d = 1; d < 32; d <<= 1) {
                     int o = __shfl_up_sync(FULL, v32, d);
@@ -589,6 +601,7 @@ __device__ __forceinline__ void size_levels(const double *re, const double *im, 
                 if (k) { ls.sw1 = sw; ls.zw1 = ~nzm & lanes; }
                 else { ls.sw0 = sw; ls.zw0 = ~nzm & lanes; }
             }
+            if (nzm == 0u) continue;                         // all zeros: width 0 at every level
             // magnitude bits of the previous nonzero value (uniform branch:
             // a group without zeros, the common case, takes the lane below)
             unsigned long long Bp;
@@ -780,6 +793,7 @@ __device__ EncodeOut wencode(const double *re, const double *im, const CodecCfg 
                 const unsigned long long B = lane < L ? (dbits(v[g * 32 + lane]) & MAG) : 0ull;
                 const unsigned long long q = quant(B, s);
                 const uint32_t nzm = __ballot_sync(FULL, lane < L && B != 0);
+                if (nzm == 0u) continue;                     // all zeros: no norm, no data
                 const bool dense = nzm == lanes;             // uniform: no zero in the group
                 unsigned long long qp;
                 if (dense) {
@@ -848,6 +862,97 @@ __device__ EncodeOut wencode(const double *re, const double *im, const CodecCfg 
     }
     __syncwarp();
     return res;
+}
+
+// Value of a well-formed CONST stream (the checks of wdecode), scaled like
+// wdecode; false for any other stream.  One thread.
+__device__ __forceinline__ bool const_value(const uint8_t *src, int c, double alpha, bool scale,
+                                            double &vr, double &vi) {
+    const uint4 w0 = __ldg(reinterpret_cast<const uint4 *>(src));
+    const uint4 w1 = __ldg(reinterpret_cast<const uint4 *>(src) + 1);
+    const int mode = w0.x & 0xFF, sh = (w0.x >> 8) & 0xFF;
+    const int sm0 = (w0.x >> 24) & 7, sm1 = (w0.x >> 27) & 7;
+    if (mode != M_CONST || sh > 52 || w0.y != 0u || sm0 > 1 || sm1 > 1 || (w1.z & 0xFFu) != (unsigned)c ||
+        ((w1.z >> 8) & 0xFFu))
+        return false;
+    const unsigned long long a0 = ((unsigned long long)w0.w << 32) | w0.z;
+    const unsigned long long a1 = ((unsigned long long)w1.y << 32) | w1.x;
+    vr = bitsd((a0 << sh) | ((unsigned long long)sm0 << 63));
+    vi = bitsd((a1 << sh) | ((unsigned long long)sm1 << 63));
+    if (scale) { vr = __dmul_rn(vr, alpha); vi = __dmul_rn(vi, alpha); }
+    return true;
+}
+
+// Encode a uniform tile (every amplitude equal to re[0], im[0]) exactly as
+// wencode would: a CONST stream at the first level whose 32 bytes fit the
+// size limit, else at the last level.  Components that are non-finite or
+// outside the lossy range, and uncompressed storage, are left to wencode:
+// the tile is filled and false returned.  Warp-wide.
+__device__ bool wencode_uniform(double *re, double *im, const CodecCfg &cc, unsigned long long tile,
+                                uint8_t *out_arena, unsigned long long out_cap,
+                                unsigned long long *out_table, unsigned long long *part,
+                                DevScalars *scal, unsigned sweep_id) {
+    const int c = cc.c, N = 1 << c;
+    const int lane = threadIdx.x & 31;
+    const double vr = re[0], vi = im[0];
+    const unsigned long long u0 = dbits(vr), u1 = dbits(vi), B0 = u0 & MAG, B1 = u1 & MAG;
+    const bool odd0 = B0 >= INF_BITS || (B0 != 0 && (B0 < MIN_NORMAL || B0 >= LOSSY_LIMIT));
+    const bool odd1 = B1 >= INF_BITS || (B1 != 0 && (B1 < MIN_NORMAL || B1 >= LOSSY_LIMIT));
+    if (cc.force_raw || odd0 || odd1) {
+        __syncwarp();
+        for (int i = lane; i < N; i += 32) { re[i] = vr; im[i] = vi; }
+        __syncwarp();
+        return false;
+    }
+    const int level = cc.max_bytes >= (unsigned long long)HDR ? 0 : cc.nlev - 1;
+    const int s = cc.shifts[level];
+    // stored signs: a zero keeps its sign only at shift 0
+    const uint32_t sm0 = ((u0 >> 63) && (s == 0 || B0 != 0)) ? S_SET : S_CLEAR;
+    const uint32_t sm1 = ((u1 >> 63) && (s == 0 || B1 != 0)) ? S_SET : S_CLEAR;
+    const unsigned long long q0 = quant(B0, s), q1 = quant(B1, s);
+    unsigned long long off = 0;
+    int ok = 0;
+    if (lane == 0) {
+        off = atomicAdd(&scal->bump, (unsigned long long)HDR);
+        ok = off + HDR <= out_cap;
+        if (!ok) {
+            atomicOr(&scal->err, ERR_OVERFLOW);
+            atomicCAS(&scal->err_sweep, 0u, sweep_id + 1u);
+        }
+    }
+    off = shfl64(off, 0);
+    ok = __shfl_sync(FULL, ok, 0);
+    if (!ok) return true;
+    if (lane < 8) {
+        uint32_t v = 0;
+        switch (lane) {
+            case 0: v = ((uint32_t)s << 8) | ((uint32_t)level << 16) | ((sm0 | (sm1 << 3)) << 24); break;
+            case 2: v = (uint32_t)q0; break;
+            case 3: v = (uint32_t)(q0 >> 32); break;
+            case 4: v = (uint32_t)q1; break;
+            case 5: v = (uint32_t)(q1 >> 32); break;
+            case 6: v = (uint32_t)c; break;
+            default: v = 0; break;
+        }
+        reinterpret_cast<uint32_t *>(out_arena + off)[lane] = v;
+    }
+    if (lane == 0) {
+        // norm partial: N times the exact square of each reconstructed component
+        unsigned long long l0, h0, l1, h1;
+        unsigned rng = 0;
+        sq_units(q0 << s, l0, h0, rng);
+        sq_units(q1 << s, l1, h1, rng);
+        add128(l0, h0, l1, h1);
+        const unsigned long long nlo = l0 << c, nhi = (h0 << c) | (c ? l0 >> (64 - c) : 0ull);
+        part[2 * tile] = nlo;
+        part[2 * tile + 1] = nhi;
+        atomic_add128(&scal->acc_lo, &scal->acc_hi, nlo, nhi);
+        out_table[tile] = off;
+        atomicAdd(&scal->hist[level], 1ull);
+        if (rng) atomicOr(&scal->err, ERR_RANGE);
+    }
+    __syncwarp();
+    return true;
 }
 
 // Copy one stream unchanged into the output arena (a tile no gate touches).
@@ -999,19 +1104,42 @@ __global__ void __launch_bounds__(THREADS, 3) sweep_kernel(const SweepParams *__
             if (threadIdx.x == 0) atomicAdd(&P.scal->items_skipped, 1ull);
             continue;
         }
-        int bad = 0;
-        for (int j = warp; j < ntl; j += NWARPS) {
-            const unsigned long long Tj = member_tile(T, j, h, hb);
-            bad |= wdecode(P.in_arena + P.in_table[Tj], c, re + j * N, im + j * N, alpha, scale);
+        // Uniform items: when every member tile is CONST and no gate of the
+        // sweep touches a low qubit, every tile stays uniform; the gates run
+        // on one amplitude per tile, each with the operands every amplitude
+        // of the tile would see, and the tiles are written back as CONST.
+        bool uni = false;
+        if (P.low_free || !active) {
+            bool ok = true;
+            if ((int)threadIdx.x < ntl) {
+                double vr, vi;
+                ok = const_value(P.in_arena + P.in_table[member_tile(T, threadIdx.x, h, hb)], c, alpha,
+                                 scale, vr, vi);
+                re[threadIdx.x * N] = vr;
+                im[threadIdx.x * N] = vi;
+            }
+            uni = __syncthreads_and(ok);
         }
-        if (bad && lane == 0) atomicOr(&P.scal->err, ERR_FORMAT);
+        if (!uni) {
+            int bad = 0;
+            for (int j = warp; j < ntl; j += NWARPS) {
+                const unsigned long long Tj = member_tile(T, j, h, hb);
+                bad |= wdecode(P.in_arena + P.in_table[Tj], c, re + j * N, im + j * N, alpha, scale);
+            }
+            if (bad && lane == 0) atomicOr(&P.scal->err, ERR_FORMAT);
+        }
         if (active) {
             __syncthreads();
-            apply_gates(re, im, mb, sg, P.gates, P.ngates, active, fixed);
+            apply_gates(re, im, mb, uni ? c : 0, sg, P.gates, P.ngates, active, fixed);
         }
-        for (int j = warp; j < ntl; j += NWARPS)
-            wencode(re + j * N, im + j * N, P.cc, member_tile(T, j, h, hb), P.out_arena, P.out_cap,
-                    P.out_table, P.part, P.scal, P.sweep_id, wst);
+        for (int j = warp; j < ntl; j += NWARPS) {
+            const unsigned long long Tj = member_tile(T, j, h, hb);
+            if (uni && wencode_uniform(re + j * N, im + j * N, P.cc, Tj, P.out_arena, P.out_cap, P.out_table,
+                                       P.part, P.scal, P.sweep_id))
+                continue;
+            wencode(re + j * N, im + j * N, P.cc, Tj, P.out_arena, P.out_cap, P.out_table, P.part, P.scal,
+                    P.sweep_id, wst);
+        }
         if (threadIdx.x == 0) atomicAdd(&P.scal->items_done, 1ull);
     }
 }

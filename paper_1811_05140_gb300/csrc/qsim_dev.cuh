@@ -104,6 +104,7 @@ struct SweepParams {
     unsigned long long nitems;
     unsigned int sweep_id;
     int use_alpha;
+    int low_free;                   // no gate of the sweep targets or controls a qubit < c
 };
 
 // End-of-pass bookkeeping of one state (norm, scale, used bytes).
