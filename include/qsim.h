@@ -133,6 +133,24 @@ qsim_status qsim_set_normalize(qsim_t h, int on);
  */
 qsim_status qsim_set_schedule(qsim_t h, int tile_log2, int hmax, int depth);
 
+/* Place the state's two stream arenas in a caller-owned device buffer (for
+ * example the storage of a torch tensor) instead of library allocations
+ * (Sec. III: the strides are stored compressed; this chooses where).
+ *   dev_ptr: device memory of the handle's GPU, 256-byte aligned; bytes:
+ *   its size.  The buffer is split into two arenas of floor(bytes/2)
+ *   rounded down to 256 bytes; queued gates are flushed first and the
+ *   current stream is copied in.  The caller keeps ownership: the buffer
+ *   must stay allocated until qsim_destroy or the next qsim_set_pool, and
+ *   the library never frees it.  Arenas in a pool do not grow: a flush
+ *   whose output does not fit returns QSIM_ERR_OOM and leaves the handle
+ *   STATE_INVALID.  dev_ptr = NULL with bytes = 0 moves the state back to
+ *   library-owned arenas.  Tile tables, norm partials and counters stay
+ *   library-allocated (24 bytes per tile plus a few KiB).
+ *   Errors: QSIM_ERR_ARG (misaligned, not device memory of this GPU, a
+ *   half smaller than the current stream or than 4 KiB, NULL with
+ *   bytes != 0), QSIM_ERR_CUDA. */
+qsim_status qsim_set_pool(qsim_t h, void *dev_ptr, size_t bytes);
+
 /* qsim_reset_basis -- state |x> (x < 2^n); drops queued gates. */
 qsim_status qsim_reset_basis(qsim_t h, unsigned long long x);
 

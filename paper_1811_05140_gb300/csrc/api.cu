@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -272,6 +273,7 @@ struct qsim_state {
     std::vector<cudaEvent_t> events;
     std::string err;
     bool invalid = false;
+    bool pool = false;                    // arenas live in a caller-owned buffer
 };
 
 namespace {
@@ -309,6 +311,8 @@ int grid_for(const qsim_state *h, unsigned long long work, int per_sm) {
 
 qsim_status ensure_arena(qsim_t h, int which, unsigned long long need) {
     if (h->cap[which] >= need) return QSIM_OK;
+    if (h->pool)
+        return fail(h, QSIM_ERR_OOM, "pool arena of %llu bytes cannot hold %llu bytes", h->cap[which], need);
     unsigned long long worst = h->ntiles * tile_bytes_worst(h);
     unsigned long long nc = std::max(need, h->cap[which] + h->cap[which] / 2);
     nc = std::min(round_up(nc, 1ull << 21), round_up(worst, 256));
@@ -352,9 +356,13 @@ qsim_status encode_fresh(qsim_t h, const double2 *dense, unsigned long long x) {
                                     : (h->cc.force_raw ? h->ntiles * tile_bytes_worst(h)
                                                        : h->ntiles * qs::HDR + tile_bytes_worst(h));
     if (dense) need = std::min(need, std::max<unsigned long long>(h->cap[h->cur], 1ull << 22));
+    if (h->pool) need = std::min(need, h->cap[h->cur]);
     for (int attempt = 0; attempt < 64; ++attempt) {
         qsim_status s = ensure_arena(h, h->cur, need);
-        if (s != QSIM_OK) return s;
+        if (s != QSIM_OK) {
+            h->invalid = attempt > 0;     // an attempt wrote into the arena
+            return s;
+        }
         CK(cudaMemsetAsync(h->scal, 0, sizeof(qs::DevScalars), h->stream));
         ++h->launches; CK(qs::launch_init(dense, x, h->cc, h->ntiles, h->arena[h->cur], h->cap[h->cur],
                            h->table[h->cur], h->part, h->scal, grid_for(h, h->ntiles, 4), h->stream));
@@ -384,8 +392,9 @@ qsim_status alloc_tiles(qsim_t h) {
 void free_tiles(qsim_t h) {
     for (int i = 0; i < 2; ++i) {
         if (h->table[i]) cudaFree(h->table[i]);
-        if (h->arena[i]) cudaFree(h->arena[i]);
         h->table[i] = nullptr;
+        if (h->pool) continue;            // the caller's buffer stays in place
+        if (h->arena[i]) cudaFree(h->arena[i]);
         h->arena[i] = nullptr;
         h->cap[i] = 0;
     }
@@ -565,6 +574,51 @@ qsim_status qsim_set_stream(qsim_t h, void *cuda_stream) {
     return QSIM_OK;
 }
 
+qsim_status qsim_set_pool(qsim_t h, void *dev_ptr, size_t bytes) {
+    qsim_status s = check_usable(h);
+    if (s != QSIM_OK) return s;
+    if ((s = qsim_flush(h)) != QSIM_OK) return s;
+    CK(cudaStreamSynchronize(h->stream));
+    if (!dev_ptr) {
+        if (bytes) return fail(h, QSIM_ERR_ARG, "null pool with nonzero size");
+        if (!h->pool) return QSIM_OK;
+        // back to library-owned arenas: copy the current stream out
+        const unsigned long long cap = std::max<unsigned long long>(round_up(h->used, 1ull << 21), 1ull << 22);
+        uint8_t *own = nullptr;
+        CK(cudaMalloc(&own, cap));
+        cudaError_t e = cudaMemcpyAsync(own, h->arena[h->cur], h->used, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) { cudaFree(own); return fail(h, QSIM_ERR_CUDA, "set_pool: %s", cudaGetErrorString(e)); }
+        h->arena[h->cur] = own;
+        h->cap[h->cur] = cap;
+        h->arena[h->cur ^ 1] = nullptr;
+        h->cap[h->cur ^ 1] = 0;
+        h->pool = false;
+        return QSIM_OK;
+    }
+    if (reinterpret_cast<uintptr_t>(dev_ptr) & 255u) return fail(h, QSIM_ERR_ARG, "pool must be 256-byte aligned");
+    cudaPointerAttributes attr{};
+    if (cudaPointerGetAttributes(&attr, dev_ptr) != cudaSuccess || attr.type != cudaMemoryTypeDevice ||
+        attr.device != h->device) {
+        cudaGetLastError();
+        return fail(h, QSIM_ERR_ARG, "pool is not device memory of the handle's GPU");
+    }
+    const unsigned long long half = ((unsigned long long)bytes / 2) & ~255ull;
+    if (half < h->used || half < 4096) return fail(h, QSIM_ERR_ARG, "pool of %zu bytes cannot hold the state (%llu bytes per arena)", bytes, h->used);
+    uint8_t *base = static_cast<uint8_t *>(dev_ptr);
+    uint8_t *dst = base + (h->cur ? half : 0);
+    CK(cudaMemcpyAsync(dst, h->arena[h->cur], h->used, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (!h->pool)
+        for (int i = 0; i < 2; ++i)
+            if (h->arena[i]) cudaFree(h->arena[i]);
+    h->arena[0] = base;
+    h->arena[1] = base + half;
+    h->cap[0] = h->cap[1] = half;
+    h->pool = true;
+    return QSIM_OK;
+}
+
 qsim_status qsim_reset_basis(qsim_t h, unsigned long long x) {
     if (!h) return fail(nullptr, QSIM_ERR_ARG, "null handle");
     if (h->invalid) return check_usable(h);
@@ -738,6 +792,7 @@ qsim_status stage_flush(qsim_t h, FlushCtx &fc, cudaStream_t st) {
     // an overflow is re-run with the exact size
     const unsigned long long first_need =
         std::max<unsigned long long>(h->used + h->used / 4 + (1ull << 20), 1ull << 22);
+    if (h->pool) return QSIM_OK;          // fixed arenas: a pass that overflows fails
     return ensure_arena(h, h->cur ^ 1, first_need);
 }
 
@@ -870,7 +925,11 @@ qsim_status qsim_flush(qsim_t h) {
     if (h->queue.empty()) return QSIM_OK;
     FlushCtx fc;
     if ((s = stage_flush(h, fc, h->stream)) != QSIM_OK) return s;
-    if ((s = run_from(h, fc, 0)) != QSIM_OK) return s;
+    if ((s = run_from(h, fc, 0)) != QSIM_OK) {
+        // passes may have overwritten the input arena: the state is lost
+        h->invalid = true;
+        return s;
+    }
     return finish_flush(h, fc, true);
 }
 
@@ -999,6 +1058,7 @@ qsim_status qsim_flush_batch(qsim_t *handles, int count, int use_graph) {
             }
         }
         if (s == QSIM_OK) s = finish_flush(hh, fc, false);
+        else hh->invalid = true;          // passes may have overwritten its input arena
         if (s != QSIM_OK && first_err == QSIM_OK) first_err = s;
     }
     if (first_err != QSIM_OK) g_last_error = "qsim_flush_batch: a handle failed (see its qsim_last_error)";

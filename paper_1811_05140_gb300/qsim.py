@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(PKG, "libqsim.so")
 CODECS = {"none": 0, "lossless": 1, "rel": 2, "aalc": 3}
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NONFINITE",
           5: "ERR_TIMEOUT", 6: "ERR_STATE_INVALID", 7: "ERR_FORMAT"}
+QSIM_OK, QSIM_ERR_ARG, QSIM_ERR_OOM, QSIM_ERR_CUDA = 0, 1, 2, 3
+QSIM_ERR_NONFINITE, QSIM_ERR_TIMEOUT, QSIM_ERR_STATE_INVALID, QSIM_ERR_FORMAT = 4, 5, 6, 7
 REF_HANDLE, REF_QFT, REF_GROVER, REF_DENSE_HOST, REF_DENSE_DEVICE = range(5)
 
 EXPORTS = ["qsim_create", "qsim_destroy", "qsim_set_stream", "qsim_set_aalc", "qsim_set_normalize",
@@ -28,7 +30,7 @@ EXPORTS = ["qsim_create", "qsim_destroy", "qsim_set_stream", "qsim_set_aalc", "q
            "qsim_import_tiles", "qsim_plan_sweeps", "qsim_version", "qsim_set_profiling",
            "qsim_profile", "qsim_encode_noalloc", "qsim_flush_batch", "qsim_server_create",
            "qsim_server_submit", "qsim_server_result", "qsim_server_wait", "qsim_server_drain",
-           "qsim_server_stats", "qsim_server_destroy"]
+           "qsim_server_stats", "qsim_server_destroy", "qsim_set_pool"]
 
 
 class QsimError(RuntimeError):
@@ -110,6 +112,7 @@ def load() -> C.CDLL:
         "qsim_set_aalc": ([vp, C.c_double, dp, C.c_int], C.c_int),
         "qsim_set_normalize": ([vp, C.c_int], C.c_int),
         "qsim_set_schedule": ([vp, C.c_int, C.c_int, C.c_int], C.c_int),
+        "qsim_set_pool": ([vp, vp, C.c_size_t], C.c_int),
         "qsim_reset_basis": ([vp, u64], C.c_int),
         "qsim_set_amplitudes": ([vp, dp], C.c_int),
         "qsim_apply_gate": ([vp, dp, ip, C.c_int, ip, C.c_int, u64], C.c_int),
@@ -262,6 +265,22 @@ class State:
 
     def set_schedule(self, tile_log2: int, hmax: int = 4, depth: int = 48):
         self._check(self._L.qsim_set_schedule(self.h, tile_log2, hmax, depth))
+
+    def set_pool(self, buf=None, nbytes: int | None = None):
+        """Put the stream arenas in a caller-owned device buffer: a CUDA
+        torch tensor (its storage is used; keep the tensor alive) or a raw
+        device pointer with nbytes.  None moves them back to the library."""
+        if buf is None:
+            self._check(self._L.qsim_set_pool(self.h, None, 0))
+            self._pool = None
+            return
+        if hasattr(buf, "data_ptr"):
+            ptr = buf.data_ptr()
+            size = buf.numel() * buf.element_size() if nbytes is None else nbytes
+        else:
+            ptr, size = int(buf), int(nbytes)
+        self._check(self._L.qsim_set_pool(self.h, C.c_void_p(ptr), size))
+        self._pool = buf                  # keeps a tensor alive with the handle
 
     # -- state
     def reset_basis(self, x: int = 0):
