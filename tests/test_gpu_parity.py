@@ -38,11 +38,12 @@ def oracle_cfg(codec, eps, c, aalc=None):
     raise ValueError(codec)
 
 
-def run_both(n, b, codec, eps, gates, x=0, hmax=4, depth=48, aalc=None):
+def run_both(n, b, codec, eps, gates, x=0, hmax=4, depth=None, aalc=None):
     c = min(b, n, 8)
     st = qsim.State(n, b, codec, eps)
-    if (hmax, depth) != (4, 48):
-        st.set_schedule(c, hmax, depth)
+    if hmax != 4 or depth is not None:
+        st.set_schedule(c, hmax, depth or 512)
+    depth = st.stats()["depth"]
     if aalc:
         st.set_aalc(*aalc)
     st.reset_basis(x)
@@ -102,11 +103,21 @@ def test_grover_streams_and_closed_form():
     assert st.fidelity_grover(m, 3) > 0.9999
 
 
-@pytest.mark.parametrize("depth", [1, 3, 48])
+@pytest.mark.parametrize("depth", [1, 3, 48, 49, 97, 512])
 def test_fusion_depths(depth):
     n = 10
     gates = I.basis_gates(n, 0x2D3) + I.qft(n)
     st, cs, c = run_both(n, 5, "rel", 1e-3, gates, depth=depth)
+    assert_same_streams(st, cs, n, c)
+
+
+def test_long_sweep_many_gate_chunks():
+    # about 500 gates in one sweep: the compact gates pass through shared
+    # memory in chunks of 48, skipped chunks included
+    n = 10
+    gates = I.random_grid(2, 5, 40, 12) + I.qft(n)
+    st, cs, c = run_both(n, 10, "rel", 1e-4, gates)
+    assert st.stats()["sweeps"] <= 2
     assert_same_streams(st, cs, n, c)
 
 
@@ -314,3 +325,47 @@ def test_compressed_bytes_counts_streams():
     sb, fp = st.compressed_bytes()
     assert sb == sum(len(s) for s in st.export_tiles())
     assert fp >= sb
+
+
+def test_decoders_agree_on_corrupted_streams():
+    """Byte-level fuzz of the stream format: for streams with zero words,
+    exception sections and packed data, flip bytes of the body and the
+    mode bytes; the GPU decoder (through qsim_import_tiles) accepts
+    exactly the streams the oracle's decoder accepts and yields the same
+    bits, apart from streams whose values leave the state's range (|x|
+    >= 16 or non-finite), which the import rejects by design."""
+    rng = np.random.default_rng(2024)
+    c = 6
+    N = 1 << c
+    comps = rng.standard_normal(2 * N) / 8
+    comps[rng.random(2 * N) < 0.6] = 0.0
+    a = comps.view(np.complex128)
+    base, _, _ = oracle.encode_tile(a, c, [39])
+    assert base[0] == 1 and (base[3] or base[25])
+    st = qsim.State(c, c, "rel", 1e-4)
+    agree = 0
+    for trial in range(300):
+        bad = bytearray(base)
+        for _ in range(1 + trial % 3):
+            pos = int(rng.choice([3, 25])) if trial % 5 == 0 else int(rng.integers(32, len(bad)))
+            bad[pos] ^= int(rng.integers(1, 256))
+        try:
+            want = oracle.decode_tile(bytes(bad), c)
+        except ValueError:
+            want = None
+        try:
+            st.import_tiles(0, [bytes(bad)])
+            got = st.amplitudes()
+        except qsim.QsimError as e:
+            assert e.status == 7
+            got = None
+        if want is None:
+            assert got is None, trial
+        elif got is None:
+            w = want.view(np.float64)
+            assert not np.all(np.isfinite(w)) or np.max(np.abs(w)) >= 16, trial
+        else:
+            assert np.array_equal(got.view(np.uint64), want.view(np.uint64)), trial
+            agree += 1
+    assert agree >= 30
+    st.close()
