@@ -4,7 +4,7 @@
 Workload (one step): the 28-qubit QFT (420 gates: H, controlled phases,
 final swaps) on a seeded basis state, state stored as compressed tiles of
 2^8 amplitudes (items of 16 tiles: up to four paired high qubits) in blocks of 2^20, point-wise relative bound 1e-4,
-normalize on (Algorithm 2), sweeps of up to 48 fused gates.  A step is
+normalize on (Algorithm 2), sweeps of up to 512 fused gates.  A step is
 reset to |x>, all 420 gates, flush (every sweep of decompress -> normalize
 -> gates -> compress), i.e. one full circuit.
 
@@ -48,7 +48,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=N_QUBITS)
     ap.add_argument("--eps", type=float, default=EPS)
-    ap.add_argument("--depth", type=int, default=48)
+    ap.add_argument("--depth", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip bound sweep / AALC / e2e")
     ap.add_argument("--workload", choices=["qft28", "serving", "grover"], default="qft28")
@@ -187,7 +187,7 @@ def run_ours(args, rank, world, local_rank):
     gates = I.qft(n)
     stream = torch.cuda.Stream()
     st = qsim.State(n, BLOCK_LOG2, "rel", eps, stream=stream)
-    if args.depth != 48:
+    if args.depth != 512:
         st.set_schedule(c, 4, args.depth)
 
     def step():

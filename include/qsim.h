@@ -126,8 +126,8 @@ qsim_status qsim_set_normalize(qsim_t h, int on);
 
 /*
  * qsim_set_schedule -- tile_log2 c (1..10, <= n), pair slots hmax (1..4,
- * c + hmax <= 12; default 4) and sweep depth (max gates per sweep, 1..48;
- * default 48).  Re-tiles
+ * c + hmax <= 12; default 4) and sweep depth (max gates per sweep, 1..512;
+ * default 512).  Re-tiles
  * the current state (lossless re-encode is exact only for RAW/lossless
  * tiles; call it before the first gate).  Used by the autotuner.
  */

@@ -19,7 +19,7 @@ import time
 from . import qsim
 
 # (tile_log2, hmax, depth): items of 2^(c + hmax) <= 4096 amplitudes
-CANDIDATES = [(8, 4, 48), (8, 4, 24), (9, 3, 48), (10, 2, 48), (7, 4, 48), (6, 4, 48), (8, 4, 12)]
+CANDIDATES = [(8, 4, 512), (8, 4, 48), (9, 3, 512), (10, 2, 512), (7, 4, 512), (6, 4, 512), (8, 4, 12)]
 
 
 def valid(n: int, c: int, hmax: int) -> bool:

@@ -87,6 +87,26 @@ __device__ __forceinline__ void sq_units(unsigned long long u, unsigned long lon
     }
 }
 
+// sq_units for a reconstructed value at shift s >= 21 (u = q << s): the
+// significand's low s bits are zero, so (significand >> s)^2 fits one
+// 32 x 32 -> 64-bit multiply and the result is placed by a shift.  Same
+// value as sq_units(u); nonzero lossy values are normal.
+__device__ __forceinline__ void sq_units_q(unsigned long long u, int s, unsigned long long &lo,
+                                           unsigned long long &hi, unsigned &range) {
+    u &= MAG;
+    const unsigned long long E = u >> 52;
+    lo = hi = 0;
+    if (E >= 1027) { range = 1; return; }
+    if (u == 0) return;
+    const uint32_t m = (uint32_t)(((u & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> s);
+    const unsigned long long sq = (unsigned long long)m * m;            // < 2^(106 - 2s)
+    const int sh = 2 * (int)E - 2038 + 2 * s;                            // x^2 2^112 = sq 2^sh
+    if (sh >= 64) { hi = sq << (sh - 64); }
+    else if (sh > 0) { lo = sq << sh; hi = sq >> (64 - sh); }
+    else if (sh == 0) { lo = sq; }
+    else if (sh > -64) { lo = sq >> (-sh); }
+}
+
 __device__ __forceinline__ void add128(unsigned long long &lo, unsigned long long &hi,
                                        unsigned long long alo, unsigned long long ahi) {
     unsigned long long nlo = lo + alo;
@@ -259,12 +279,55 @@ __device__ void diag_gate(double *re, double *im, int mb, const SGate &s,
     if (nr == 0) return;
     const int fb = mb - s.nins - red;           // free bits (the low `red` bits stay 0)
     const unsigned cnt = (unsigned)nr << fb;
-    for (unsigned f = threadIdx.x; f < cnt; f += THREADS) {
+    for (unsigned f = threadIdx.x; f < cnt; f += SWEEP_THREADS) {
         int r = (int)((rpack >> (2 * (f >> fb))) & 3u);
         unsigned l = deposit((f & ((1u << fb) - 1u)) << red, s) | s.lcv;
         if (s.p0 >= 0) l |= (unsigned)(r & 1) << s.p0;
         if (s.k > 1 && s.p1 >= 0) l |= (unsigned)((r >> 1) & 1) << s.p1;
         unsigned code = (unsigned)(s.cls >> (3 * r)) & 7u;
+        double yr = 0.0, yi = 0.0;
+        if (code != EC_ZERO) term_first(code, s.d[2 * r], s.d[2 * r + 1], re[l], im[l], yr, yi);
+        re[l] = yr;
+        im[l] = yi;
+    }
+}
+
+// Warp-local form of diag_gate for an item of 2^mb amplitudes: warp w
+// handles the amplitudes whose top LOG_NWARPS index bits equal w, so
+// consecutive diagonal gates need only __syncwarp between them (each
+// amplitude still sees the gates in order, with the same arithmetic).
+// Needs mb - LOG_NWARPS >= 5.
+__device__ void diag_gate_warp(double *re, double *im, int mb, const SGate &s, unsigned long long fixed) {
+    const int lane = threadIdx.x & 31;
+    const int cb = mb - LOG_NWARPS;                 // index bits that vary inside a warp's part
+    const unsigned inmask = (1u << cb) - 1u;
+    const unsigned W = (unsigned)(threadIdx.x >> 5) << cb;
+    if (((W ^ s.lcv) & s.lcm & ~inmask) != 0u) return;      // a control outside the part fails
+    int fmask = 0, fval = 0;                         // target bits fixed for this warp
+    if (s.p0 < 0) { fmask |= 1; fval |= (int)((fixed >> s.t0) & 1ull); }
+    else if (s.p0 >= cb) { fmask |= 1; fval |= (int)((W >> s.p0) & 1u); }
+    if (s.k > 1) {
+        if (s.p1 < 0) { fmask |= 2; fval |= (int)((fixed >> s.t1) & 1ull) << 1; }
+        else if (s.p1 >= cb) { fmask |= 2; fval |= (int)((W >> s.p1) & 1u) << 1; }
+    }
+    unsigned rpack = 0;
+    int nr = 0;
+    for (int r = 0; r < (1 << s.k); ++r)
+        if ((r & fmask) == fval && !((s.one_mask >> r) & 1)) rpack |= (unsigned)r << (2 * nr++);
+    if (nr == 0) return;
+    int nin = 0;                                     // pinned bits inside the part (ins is ascending)
+    while (nin < s.nins && s.ins[nin] < cb) ++nin;
+    const int fb = cb - nin;
+    const unsigned cnt = (unsigned)nr << fb;
+    const unsigned base = (s.lcv & inmask) | W;
+    for (unsigned f = lane; f < cnt; f += 32) {
+        const int r = (int)((rpack >> (2 * (f >> fb))) & 3u);
+        unsigned l = f & ((1u << fb) - 1u);
+        for (int i = 0; i < nin; ++i) l = insert_zero(l, s.ins[i]);
+        l |= base;
+        if (s.p0 >= 0 && s.p0 < cb) l |= (unsigned)(r & 1) << s.p0;
+        if (s.k > 1 && s.p1 >= 0 && s.p1 < cb) l |= (unsigned)((r >> 1) & 1) << s.p1;
+        const unsigned code = (unsigned)(s.cls >> (3 * r)) & 7u;
         double yr = 0.0, yi = 0.0;
         if (code != EC_ZERO) term_first(code, s.d[2 * r], s.d[2 * r + 1], re[l], im[l], yr, yi);
         re[l] = yr;
@@ -283,7 +346,7 @@ __device__ void one_target(double *re, double *im, int mb, const SGate &s, const
         // y_r = d_r (x_0 + f_r x_1), the same arithmetic as row_eval
         const double d0 = m[0], d1 = m[4];
         const unsigned f0 = (unsigned)(s.fac >> 10) & 3u, f1 = (unsigned)(s.fac >> 14) & 3u;
-        for (unsigned f = threadIdx.x; f < cnt; f += THREADS) {
+        for (unsigned f = threadIdx.x; f < cnt; f += SWEEP_THREADS) {
             const unsigned l0 = deposit(f << red, s) | s.lcv;
             const unsigned l1 = l0 | bit;
             const double x0r = re[l0], x0i = im[l0], x1r = re[l1], x1i = im[l1];
@@ -297,7 +360,7 @@ __device__ void one_target(double *re, double *im, int mb, const SGate &s, const
         }
         return;
     }
-    for (unsigned f = threadIdx.x; f < cnt; f += THREADS) {
+    for (unsigned f = threadIdx.x; f < cnt; f += SWEEP_THREADS) {
         unsigned l0 = deposit(f << red, s) | s.lcv;
         unsigned l1 = l0 | bit;
         double xr[2] = {re[l0], re[l1]}, xi[2] = {im[l0], im[l1]};
@@ -311,7 +374,7 @@ __device__ void one_target(double *re, double *im, int mb, const SGate &s, const
 
 __device__ void two_target(double *re, double *im, int mb, const SGate &s, const DGate &dg, int red) {
     const unsigned cnt = 1u << (mb - s.nins - red);
-    for (unsigned f = threadIdx.x; f < cnt; f += THREADS) {
+    for (unsigned f = threadIdx.x; f < cnt; f += SWEEP_THREADS) {
         unsigned l = deposit(f << red, s) | s.lcv;
         unsigned idx[4];
         double xr[4], xi[4];
@@ -330,19 +393,55 @@ __device__ void two_target(double *re, double *im, int mb, const SGate &s, const
 }
 
 // Apply the sweep's gates (in order) to an item buffer of 2^mb amplitudes.
-// active: bit g set when gate g changes something in this item.  red > 0:
-// only the amplitudes whose low `red` index bits are 0 (one per tile, for
-// an item of uniform tiles under gates that touch no low qubit).
-__device__ void apply_gates(double *re, double *im, int mb, int red, const SGate *sg, const DGate *dg,
-                            int ngates, unsigned long long active, unsigned long long fixed) {
-    for (int g = 0; g < ngates; ++g) {
-        if (!((active >> g) & 1ull)) continue;
-        const SGate &s = sg[g];
-        if (s.kind == 0) diag_gate(re, im, mb, s, fixed, red);
-        else if (s.kind == 1) one_target(re, im, mb, s, dg[g], red);
-        else two_target(re, im, mb, s, dg[g], red);
-        __syncthreads();
+// act: bit g set when gate g changes something in this item.  The compact
+// gates are staged in shared memory GATE_CHUNK at a time (*chunk = first
+// gate staged, -1 none); chunks without an active gate are not staged.
+// red > 0: only the amplitudes whose low `red` index bits are 0 (one per
+// tile, for an item of uniform tiles under gates that touch no low qubit).
+// CTA-wide; every thread must call it.
+__device__ __noinline__ void apply_gates(double *re, double *im, int mb, int red, const SGate *gsrc, SGate *sg,
+                            int *chunk, const DGate *dg, int ngates, const unsigned *act,
+                            unsigned long long fixed) {
+    const bool warp_parts = red == 0 && mb - LOG_NWARPS >= 5;
+    bool dirty = false;                              // warp-local gates since the last CTA barrier
+    for (int base = 0; base < ngates; base += GATE_CHUNK) {
+        const int cn = min(GATE_CHUNK, ngates - base);
+        bool any = false;
+        for (int w = base >> 5; w <= (base + cn - 1) >> 5; ++w) {
+            unsigned m = act[w];
+            const int lo = max(base, w << 5) - (w << 5), hi = min(base + cn, (w + 1) << 5) - (w << 5);
+            m &= (hi == 32 ? FULL : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
+            any |= m != 0u;
+        }
+        if (!any) continue;
+        if (*chunk != base) {
+            __syncthreads();
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(gsrc + base);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(sg);
+            const int words = cn * (int)(sizeof(SGate) / 4);
+            for (int i = threadIdx.x; i < words; i += SWEEP_THREADS) dst[i] = src[i];
+            if (threadIdx.x == 0) *chunk = base;
+            __syncthreads();
+        }
+        for (int i = 0; i < cn; ++i) {
+            const int g = base + i;
+            if (!((act[g >> 5] >> (g & 31)) & 1u)) continue;
+            const SGate &s = sg[i];
+            if (s.kind == 0 && warp_parts) {
+                // runs of diagonal gates: warp-local, no CTA barrier between them
+                diag_gate_warp(re, im, mb, s, fixed);
+                __syncwarp();
+                dirty = true;
+                continue;
+            }
+            if (dirty) { __syncthreads(); dirty = false; }
+            if (s.kind == 0) diag_gate(re, im, mb, s, fixed, red);
+            else if (s.kind == 1) one_target(re, im, mb, s, dg[g], red);
+            else two_target(re, im, mb, s, dg[g], red);
+            __syncthreads();
+        }
     }
+    if (dirty) __syncthreads();
 }
 
 // ---------------------------------------------------------------- warp codec
@@ -403,32 +502,44 @@ __device__ __forceinline__ void write_section(uint32_t *sec, int md, uint32_t v,
     }
 }
 
-// read a word section in mode md at b + off (body bytes in total): lane g
-// gets the word of group g; returns the section's size, or sets bad
-__device__ __forceinline__ uint32_t read_section(const uint8_t *b, uint32_t off, uint32_t body, int md,
-                                                 int G, uint32_t lanes, uint32_t &v, bool &bad) {
+// Word i of a stream body: from mw (lane l holds body word l, l < 32,
+// loaded once) when i < 32, else from memory.  Every lane must call it
+// (the shuffle is warp-wide); `want` says whether this lane needs a value.
+__device__ __forceinline__ uint32_t body_word(const uint32_t *b32, uint32_t mw, uint32_t i, bool want) {
+    const uint32_t sv = __shfl_sync(FULL, mw, (int)(i & 31u));
+    if (!want) return 0u;
+    return i < 32u ? sv : __ldg(b32 + i);
+}
+
+// read a word section in mode md at body byte off (body bytes in total):
+// lane g gets the word of group g; returns the section's size, or sets bad
+__device__ __forceinline__ uint32_t read_section(const uint32_t *b32, uint32_t mw, uint32_t off, uint32_t body,
+                                                 int md, int G, uint32_t lanes, uint32_t &v, bool &bad) {
     const int lane = threadIdx.x & 31;
-    const uint32_t *sec = reinterpret_cast<const uint32_t *>(b + off);
     v = 0u;
     if (md == S_CLEAR) return 0u;
     if (md == S_SET) { v = lane < G ? lanes : 0u; return 0u; }
     if (md == S_WORDS) {
         if (off + 4u * (uint32_t)G > body) { bad = true; return 0u; }
-        if (lane < G) v = __ldg(sec + lane);
+        v = body_word(b32, mw, (off >> 2) + (uint32_t)lane, lane < G);
         return 4u * (uint32_t)G;
     }
     if (md > S_WORDS || off + 4u > body) { bad = true; return 0u; }
     const uint32_t gm = G == 32 ? FULL : ((1u << G) - 1u);
-    const uint32_t bm = __ldg(sec) & gm;
+    const uint32_t bm = body_word(b32, mw, off >> 2, true) & gm;
     const uint32_t size = 4u + 4u * __popc(bm);
     if (off + size > body) { bad = true; return 0u; }
-    if (lane < G) v = ((bm >> lane) & 1u) ? __ldg(sec + 1 + __popc(bm & lanes_below())) : (md == S_EXC_SET ? lanes : 0u);
+    const bool exc = lane < G && ((bm >> lane) & 1u);
+    const uint32_t w = body_word(b32, mw, (off >> 2) + 1u + __popc(bm & lanes_below()), exc);
+    if (lane < G) v = exc ? w : (md == S_EXC_SET ? lanes : 0u);
     return size;
 }
 
 // Decode one stream into planar re/im (2^c values each), multiplied by
 // alpha when `scale` (Algorithm 2's normalize, fused).  Warp-wide; returns
-// nonzero (and zero-fills) on a malformed stream.
+// nonzero (and zero-fills) on a malformed stream.  The first 128 body bytes
+// (sections and widths, usually) come in with one load, and the packed
+// words of the next group are loaded while the current one is scanned.
 __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double alpha, bool scale) {
     const int N = 1 << c;
     const int G = N >= 32 ? N >> 5 : 1;
@@ -444,6 +555,7 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
     const int sm0 = (h0 >> 24) & 7, sm1 = (h0 >> 27) & 7;
     const int zm0 = (h6 >> 8) & 7, zm1 = (h6 >> 11) & 7;
     const uint8_t *b = src + HDR;
+    const uint32_t *b32 = reinterpret_cast<const uint32_t *>(b);
     bool bad = hc != c || mode > 2 || (mode != M_RAW && s > 52) || (body & 15u);
     if (!bad && mode == M_RAW) bad = body != 16u * (uint32_t)N;
     if (!bad && mode == M_CONST) bad = body != 0 || sm0 > 1 || sm1 > 1 || ((h6 >> 8) & 0xFFu);
@@ -467,16 +579,21 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
     const uint32_t lanes = L == 32 ? FULL : ((1u << L) - 1u);
     uint32_t sw0 = 0, sw1 = 0, zw0 = 0, zw1 = 0, w0 = 0, w1 = 0, doff = 0, off0 = 0, off1 = 0;
     if (!bad) {
+        const uint32_t mw = 4u * (uint32_t)lane < body ? __ldg(b32 + lane) : 0u;
         uint32_t off = 0;
-        off += read_section(b, off, body, sm0, G, lanes, sw0, bad);
-        if (!bad) off += read_section(b, off, body, sm1, G, lanes, sw1, bad);
-        if (!bad) off += read_section(b, off, body, zm0, G, lanes, zw0, bad);
-        if (!bad) off += read_section(b, off, body, zm1, G, lanes, zw1, bad);
+        off += read_section(b32, mw, off, body, sm0, G, lanes, sw0, bad);
+        if (!bad) off += read_section(b32, mw, off, body, sm1, G, lanes, sw1, bad);
+        if (!bad) off += read_section(b32, mw, off, body, zm0, G, lanes, zw0, bad);
+        if (!bad) off += read_section(b32, mw, off, body, zm1, G, lanes, zw1, bad);
         if (!bad && off + 2u * G > body) bad = true;
         if (!bad) {
+            // width bytes off + g (re) and off + G + g (im)
+            const uint32_t i0 = off + (uint32_t)lane, i1 = off + (uint32_t)G + (uint32_t)lane;
+            const uint32_t x0 = body_word(b32, mw, i0 >> 2, lane < G);
+            const uint32_t x1 = body_word(b32, mw, i1 >> 2, lane < G);
             if (lane < G) {
-                w0 = b[off + lane];
-                w1 = b[off + G + lane];
+                w0 = (x0 >> (8u * (i0 & 3u))) & 0xFFu;
+                w1 = (x1 >> (8u * (i1 & 3u))) & 0xFFu;
             }
             uint32_t tot0, tot1;
             off0 = warp_exscan(((uint32_t)__popc(~zw0 & lanes) * w0 + 31u) >> 5, tot0);
@@ -492,43 +609,65 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
     }
     const uint32_t *data = reinterpret_cast<const uint32_t *>(b + doff);
     const uint32_t below = lanes_below();
-    for (int k = 0; k < 2; ++k) {
-        double *v = k ? im : re;
-        unsigned long long carry = k ? a1 : a0;
-        const uint32_t wk = k ? w1 : w0, offk = k ? off1 : off0, swk = k ? sw1 : sw0, zwk = k ? zw1 : zw0;
-        for (int g = 0; g < G; ++g) {
-            const uint32_t w = __shfl_sync(FULL, wk, g);
-            const uint32_t wo = __shfl_sync(FULL, offk, g);
-            const uint32_t sgw = __shfl_sync(FULL, swk, g);
-            const uint32_t nzw = ~__shfl_sync(FULL, zwk, g) & lanes;
-            const bool nzl = (nzw >> lane) & 1u;
-            if (nzw == 0u) {                                 // all zeros: signs only
-                if (lane < L) {
-                    double x = bitsd((unsigned long long)((sgw >> lane) & 1u) << 63);
-                    if (scale) x = __dmul_rn(x, alpha);
-                    v[g * 32 + lane] = x;
-                }
-                continue;
-            }
-            const bool dense = nzw == lanes;                 // uniform: no zero in the group
+    // group t = k * G + g (component k, group g): uniform metadata, then
+    // this lane's packed words
+    auto meta = [&](int t, uint32_t &w, uint32_t &wo, uint32_t &sgw, uint32_t &nzw) {
+        const bool k = t >= G;
+        const int g = k ? t - G : t;
+        w = __shfl_sync(FULL, k ? w1 : w0, g);
+        wo = __shfl_sync(FULL, k ? off1 : off0, g);
+        sgw = __shfl_sync(FULL, k ? sw1 : sw0, g);
+        nzw = ~__shfl_sync(FULL, k ? zw1 : zw0, g) & lanes;
+    };
+    auto fetch = [&](uint32_t w, uint32_t wo, uint32_t nzw, uint32_t &x0, uint32_t &x1, uint32_t &x2,
+                     uint32_t &sh) {
+        x0 = x1 = x2 = sh = 0u;
+        if (((nzw >> lane) & 1u) && w) {
+            const bool dense = nzw == lanes;
             const uint32_t nwd = ((dense ? (uint32_t)L : (uint32_t)__popc(nzw)) * w + 31u) >> 5;
+            const uint32_t rank = dense ? (uint32_t)lane : (uint32_t)__popc(nzw & below);
+            const uint32_t bo = rank * w, j0 = bo >> 5;
+            const uint32_t *base = data + wo;
+            sh = bo & 31u;
+            x0 = __ldg(base + j0);
+            x1 = j0 + 1 < nwd ? __ldg(base + j0 + 1) : 0u;
+            x2 = j0 + 2 < nwd ? __ldg(base + j0 + 2) : 0u;
+        }
+    };
+    const int T = 2 * G;
+    uint32_t w, wo, sgw, nzw, x0, x1, x2, sh;
+    meta(0, w, wo, sgw, nzw);
+    fetch(w, wo, nzw, x0, x1, x2, sh);
+    unsigned long long carry = a0;
+    for (int t = 0; t < T; ++t) {
+        uint32_t wn = 0, won = 0, sgwn = 0, nzwn = 0, y0 = 0, y1 = 0, y2 = 0, shn = 0;
+        if (t + 1 < T) {                                     // next group's words, in flight meanwhile
+            meta(t + 1, wn, won, sgwn, nzwn);
+            fetch(wn, won, nzwn, y0, y1, y2, shn);
+        }
+        const bool k = t >= G;
+        const int g = k ? t - G : t;
+        if (t == G) carry = a1;
+        double *v = k ? im : re;
+        if (nzw == 0u) {                                     // all zeros: signs only
+            if (lane < L) {
+                double x = bitsd((unsigned long long)((sgw >> lane) & 1u) << 63);
+                if (scale) x = __dmul_rn(x, alpha);
+                v[g * 32 + lane] = x;
+            }
+        } else {
+            const bool nzl = (nzw >> lane) & 1u;
             unsigned long long z = 0;
             if (nzl && w) {
-                const uint32_t *base = data + wo;
-                const uint32_t rank = dense ? (uint32_t)lane : (uint32_t)__popc(nzw & below);
-                uint32_t bo = rank * w, j0 = bo >> 5, sh = bo & 31u;
-                uint32_t x0 = __ldg(base + j0);
-                uint32_t x1 = j0 + 1 < nwd ? __ldg(base + j0 + 1) : 0u;
-                uint32_t x2 = j0 + 2 < nwd ? __ldg(base + j0 + 2) : 0u;
-                unsigned long long lo = (unsigned long long)x0 | ((unsigned long long)x1 << 32);
-                unsigned long long vv = sh ? ((lo >> sh) | ((unsigned long long)x2 << (64 - sh))) : lo;
+                const unsigned long long lo = (unsigned long long)x0 | ((unsigned long long)x1 << 32);
+                const unsigned long long vv = sh ? ((lo >> sh) | ((unsigned long long)x2 << (64 - sh))) : lo;
                 z = w == 64 ? vv : (vv & ((1ull << w) - 1ull));
             }
             const unsigned long long r = unzigzag(z);        // 0 for zeros and lanes >= L
             unsigned long long inc;
             if (w == 0) {                                    // every residual 0
                 inc = 0;
-            } else if (w <= 27) {                      // 32 partial sums of |r| < 2^26 fit in int32
+            } else if (w <= 27) {                            // 32 partial sums of |r| < 2^26 fit in int32
                 int v32 = (int)(long long)r;
                 for (int d = 1; d < 32; d <<= 1) {
                     int o = __shfl_up_sync(FULL, v32, d);
@@ -551,6 +690,8 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
             }
             carry = shfl64(q, L - 1);
         }
+        w = wn; wo = won; sgw = sgwn; nzw = nzwn;
+        x0 = y0; x1 = y1; x2 = y2; sh = shn;
     }
     return 0;
 }
@@ -620,11 +761,19 @@ __device__ __forceinline__ void size_levels(const double *re, const double *im, 
             for (int lv = 0; lv < MAX_LEVELS; ++lv) {
                 if (lv >= cc.nlev) continue;
                 const int s = force0 ? 0 : cc.shifts[lv];
-                const unsigned long long z = nzl ? zigzag(quant(B, s) - quant(Bp, s)) : 0ull;
-                const unsigned long long oz = warp_or64(z);
-                const uint32_t w = oz ? (uint32_t)bitlen64(oz) : 0u;
+                uint32_t w;
+                if (s >= 32) {                               // codes < 2^31: 32-bit residuals
+                    const uint32_t r = (uint32_t)quant(B, s) - (uint32_t)quant(Bp, s);
+                    const uint32_t z = nzl ? (r << 1) ^ (uint32_t)((int)r >> 31) : 0u;
+                    const uint32_t oz = __reduce_or_sync(FULL, z);
+                    w = oz ? 32u - (uint32_t)__clz(oz) : 0u;
+                } else {
+                    const unsigned long long z = nzl ? zigzag(quant(B, s) - quant(Bp, s)) : 0ull;
+                    const unsigned long long oz = warp_or64(z);
+                    w = oz ? (uint32_t)bitlen64(oz) : 0u;
+                }
                 wg |= (unsigned long long)w << (8 * lv);
-                if (oz) ls.nz |= 1u << lv;
+                if (w) ls.nz |= 1u << lv;
             }
             if (lane == g) wl = wg;
             if (nzm) lastB = shfl64(B, 31 - __clz(nzm));
@@ -785,7 +934,54 @@ __device__ EncodeOut wencode(const double *re, const double *im, const CodecCfg 
         const uint32_t doff = moff + wb;
         uint32_t *data = reinterpret_cast<uint32_t *>(b + doff);
         const uint32_t below = lanes_below();
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < 2 && s >= 32; ++k) {
+            // codes < 2^31 at shift >= 32: 32-bit codes, residuals and shuffles,
+            // values spanning at most two words (the same bits as below)
+            const double *v = k ? im : re;
+            const uint32_t wk = k ? ws1 : ws0, offk = k ? off1 : off0;
+            uint32_t carry = (uint32_t)quant(k ? ls.f1 : ls.f0, s);     // the anchor
+            for (int g = 0; g < G; ++g) {
+                const unsigned long long B = lane < L ? (dbits(v[g * 32 + lane]) & MAG) : 0ull;
+                const uint32_t nzm = __ballot_sync(FULL, lane < L && B != 0);
+                if (nzm == 0u) continue;                     // all zeros: no norm, no data
+                const uint32_t q = (uint32_t)quant(B, s);
+                const bool dense = nzm == lanes;
+                uint32_t qp;
+                if (dense) {
+                    const uint32_t up = __shfl_up_sync(FULL, q, 1);
+                    qp = lane ? up : carry;
+                } else {
+                    const uint32_t pm = nzm & below;
+                    const uint32_t qs = __shfl_sync(FULL, q, pm ? 31 - __clz(pm) : lane);
+                    qp = pm ? qs : carry;
+                }
+                carry = __shfl_sync(FULL, q, dense ? L - 1 : 31 - __clz(nzm));
+                if (lane < L) {
+                    unsigned long long l0, h0;
+                    sq_units_q((unsigned long long)q << s, s, l0, h0, rng);
+                    add128(nlo, nhi, l0, h0);
+                }
+                const uint32_t w = __shfl_sync(FULL, wk, g);
+                if (w == 0) continue;
+                const uint32_t wo = __shfl_sync(FULL, offk, g);
+                const uint32_t nwd = ((uint32_t)__popc(nzm) * w + 31u) >> 5;
+                const bool nzl = (nzm >> lane) & 1u;
+                const uint32_t r = q - qp;
+                const uint32_t z = nzl ? (r << 1) ^ (uint32_t)((int)r >> 31) : 0u;
+                wstage[lane] = 0u;
+                __syncwarp();
+                if (nzl) {
+                    const uint32_t rank = dense ? (uint32_t)lane : (uint32_t)__popc(nzm & below);
+                    const uint32_t bo = rank * w, j0 = bo >> 5, sh = bo & 31u;
+                    atomicOr(&wstage[j0], z << sh);
+                    if (sh + w > 32) atomicOr(&wstage[j0 + 1], z >> (32 - sh));
+                }
+                __syncwarp();
+                if ((uint32_t)lane < nwd) (data + wo)[lane] = wstage[lane];
+                __syncwarp();
+            }
+        }
+        for (int k = 0; k < 2 && s < 32; ++k) {
             const double *v = k ? im : re;
             const uint32_t wk = k ? ws1 : ws0, offk = k ? off1 : off0;
             unsigned long long carry = quant(k ? ls.f1 : ls.f0, s);     // the anchor
@@ -844,8 +1040,13 @@ __device__ EncodeOut wencode(const double *re, const double *im, const CodecCfg 
             unsigned long long u0 = dbits(re[i]) & MAG, u1 = dbits(im[i]) & MAG;
             if (mode == M_CONST) { u0 = quant(u0, s) << s; u1 = quant(u1, s) << s; }
             unsigned long long l0, h0, l1, h1;
-            sq_units(u0, l0, h0, rng);
-            sq_units(u1, l1, h1, rng);
+            if (mode == M_CONST && s >= 21) {
+                sq_units_q(u0, s, l0, h0, rng);
+                sq_units_q(u1, s, l1, h1, rng);
+            } else {
+                sq_units(u0, l0, h0, rng);
+                sq_units(u1, l1, h1, rng);
+            }
             add128(nlo, nhi, l0, h0);
             add128(nlo, nhi, l1, h1);
         }
@@ -1033,15 +1234,15 @@ __device__ __forceinline__ unsigned long long member_tile(unsigned long long T, 
 // the gate run, compress with the ladder.  Persistent CTAs loop over items;
 // within an item every warp codes its own tiles.  A CTA reloads the
 // parameters and gates whenever it crosses into another entry's items.
-__global__ void __launch_bounds__(THREADS, 3) sweep_kernel(const SweepParams *__restrict__ plist,
+__global__ void __launch_bounds__(SWEEP_THREADS, QS_SWEEP_MIN_BLOCKS) sweep_kernel(const SweepParams *__restrict__ plist,
                                                           const unsigned long long *__restrict__ istart,
                                                           int nlist) {
     extern __shared__ double smem[];
-    __shared__ SGate sg[MAX_SWEEP_GATES];
+    __shared__ SGate sg[GATE_CHUNK];
     __shared__ uint32_t stage[64 * NWARPS];
     __shared__ SweepParams P;
-    __shared__ unsigned s_act[2];
-    __shared__ int s_entry, s_skip;
+    __shared__ unsigned s_act[MAX_SWEEP_GATES / 32];
+    __shared__ int s_entry, s_skip, s_chunk, s_any;
     __shared__ double s_alpha;
     const unsigned long long total = istart[nlist];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1063,16 +1264,11 @@ __global__ void __launch_bounds__(THREADS, 3) sweep_kernel(const SweepParams *__
             {
                 const uint32_t *src = reinterpret_cast<const uint32_t *>(plist + e);
                 uint32_t *dst = reinterpret_cast<uint32_t *>(&P);
-                for (int i = threadIdx.x; i < (int)(sizeof(SweepParams) / 4); i += THREADS) dst[i] = src[i];
+                for (int i = threadIdx.x; i < (int)(sizeof(SweepParams) / 4); i += SWEEP_THREADS) dst[i] = src[i];
             }
             __syncthreads();
-            {
-                const uint32_t *src = reinterpret_cast<const uint32_t *>(P.sgates);
-                uint32_t *dst = reinterpret_cast<uint32_t *>(sg);
-                const int words = P.ngates * (int)(sizeof(SGate) / 4);
-                for (int i = threadIdx.x; i < words; i += THREADS) dst[i] = src[i];
-            }
             if (threadIdx.x == 0) {
+                s_chunk = -1;                 // gates are staged on first use
                 // an earlier pass of this state failed: leave its state alone
                 s_skip = *((volatile unsigned *)&P.scal->err) != 0u;
                 s_alpha = P.use_alpha ? P.scal->alpha : 1.0;
@@ -1090,13 +1286,21 @@ __global__ void __launch_bounds__(THREADS, 3) sweep_kernel(const SweepParams *__
         for (int i = 0; i < MAX_PAIRS; ++i) hb[i] = i < h ? P.H[i] - c : 0;
         const unsigned long long T = expand_item(gi - istart[e], h, hb);
         const unsigned long long fixed = T << c;
-        if (threadIdx.x < 64) {
-            const bool a = (int)threadIdx.x < P.ngates && gate_active(sg[threadIdx.x], fixed);
+        // which gates change something in this item (from the compact
+        // gates in global memory; one word of 32 gates per warp)
+        if (threadIdx.x == 0) s_any = 0;
+        __syncthreads();
+        for (int w = warp; w < (P.ngates + 31) >> 5; w += NWARPS) {
+            const int g = (w << 5) + lane;
+            const bool a = g < P.ngates && gate_active(P.sgates[g], fixed);
             const unsigned bal = __ballot_sync(FULL, a);
-            if (lane == 0) s_act[warp] = bal;
+            if (lane == 0) {
+                s_act[w] = bal;
+                if (bal) s_any = 1;
+            }
         }
         __syncthreads();
-        const unsigned long long active = (unsigned long long)s_act[0] | ((unsigned long long)s_act[1] << 32);
+        const bool active = s_any != 0;
         if (!active && !scale) {
             for (int j = warp; j < ntl; j += NWARPS)
                 wcarry(P.in_arena, P.in_table, member_tile(T, j, h, hb), P.out_arena, P.out_cap,
@@ -1130,7 +1334,7 @@ __global__ void __launch_bounds__(THREADS, 3) sweep_kernel(const SweepParams *__
         }
         if (active) {
             __syncthreads();
-            apply_gates(re, im, mb, uni ? c : 0, sg, P.gates, P.ngates, active, fixed);
+            apply_gates(re, im, mb, uni ? c : 0, P.sgates, sg, &s_chunk, P.gates, P.ngates, s_act, fixed);
         }
         for (int j = warp; j < ntl; j += NWARPS) {
             const unsigned long long Tj = member_tile(T, j, h, hb);
@@ -1456,7 +1660,7 @@ static size_t tile_smem_bytes(int c, int bufs) { return (size_t)TILE_WARPS * buf
 
 cudaError_t launch_sweep(const SweepParams *plist, const unsigned long long *istart, int nlist,
                          int mb, int grid, cudaStream_t st) {
-    sweep_kernel<<<grid, THREADS, sweep_smem_bytes(mb), st>>>(plist, istart, nlist);
+    sweep_kernel<<<grid, SWEEP_THREADS, sweep_smem_bytes(mb), st>>>(plist, istart, nlist);
     return cudaGetLastError();
 }
 
@@ -1580,7 +1784,7 @@ cudaError_t configure_kernels() {
 
 int sweep_blocks_per_sm(int mb) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel, THREADS, sweep_smem_bytes(mb));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel, SWEEP_THREADS, sweep_smem_bytes(mb));
     return nb > 0 ? nb : 1;
 }
 

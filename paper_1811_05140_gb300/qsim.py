@@ -263,7 +263,7 @@ class State:
     def set_normalize(self, on: bool):
         self._check(self._L.qsim_set_normalize(self.h, int(bool(on))))
 
-    def set_schedule(self, tile_log2: int, hmax: int = 4, depth: int = 48):
+    def set_schedule(self, tile_log2: int, hmax: int = 4, depth: int = 512):
         self._check(self._L.qsim_set_schedule(self.h, tile_log2, hmax, depth))
 
     def set_pool(self, buf=None, nbytes: int | None = None):

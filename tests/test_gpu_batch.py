@@ -66,7 +66,7 @@ def test_batch_equals_alone(use_graph):
     n, b, codec, eps, gates, x = jobs[3]
     cs = oracle.CSim(n, min(b, n, 8), [oracle.shift_for_eps(eps)], None, True)
     cs.reset_basis(x)
-    cs.run(gates, 4, 48)
+    cs.run(gates, 4, batch[3].stats()["depth"])
     got = batch[3].export_tiles()
     assert all(s == cs.stream(t) for t, s in enumerate(got))
 

@@ -50,8 +50,9 @@ def test_pool_streams_identical_and_in_tensor():
         assert raw.find(got[t]) >= 0
     cs = oracle.CSim(n, 8, [oracle.shift_for_eps(1e-4)], None, True)
     cs.reset_basis(x)
-    cs.run(gates[: len(gates) // 2], 4, 48)         # the same two flushes
-    cs.run(gates[len(gates) // 2:], 4, 48)
+    d = st.stats()["depth"]
+    cs.run(gates[: len(gates) // 2], 4, d)          # the same two flushes
+    cs.run(gates[len(gates) // 2:], 4, d)
     assert all(s == cs.stream(t) for t, s in enumerate(got))
     st.close()
 
