@@ -857,6 +857,58 @@ static int gate_touches(const or_gate *g, uint64_t fixed, uint64_t fmask)
     return 1;
 }
 
+/* A gate whose matrix has only entries 0 and 1, with one 1 in every row
+ * and column, maps basis states to basis states. */
+static int gate_is_permutation(const or_gate *g)
+{
+    int dim = 1 << g->k;
+    for (int r = 0; r < dim; ++r) {
+        int ones_row = 0, ones_col = 0;
+        for (int c = 0; c < dim; ++c) {
+            double a = g->m[2 * (r * dim + c)], b = g->m[2 * (r * dim + c) + 1];
+            double ac = g->m[2 * (c * dim + r)], bc = g->m[2 * (c * dim + r) + 1];
+            if (b != 0.0 || !(a == 0.0 || a == 1.0)) return 0;
+            ones_row += a == 1.0;
+            ones_col += ac == 1.0 && bc == 0.0;
+        }
+        if (ones_row != 1 || ones_col != 1) return 0;
+    }
+    return 1;
+}
+
+/* A sweep moves whole tiles when every gate is a permutation whose
+ * targets and controls are all qubits >= c: each tile's amplitudes go,
+ * unchanged and in the same order, to one tile.  Such a sweep moves the
+ * tile streams without decompressing them, so it applies no normalize
+ * (the norm of the stored state is unchanged, and the next decompressing
+ * sweep applies the scale). */
+static int sweep_moves_tiles(const or_gate *g, int ng, int c)
+{
+    uint64_t low = (1ull << c) - 1;
+    for (int i = 0; i < ng; ++i) {
+        if (!gate_is_permutation(&g[i]) || (g[i].cmask & low)) return 0;
+        for (int j = 0; j < g[i].k; ++j)
+            if (g[i].t[j] < c) return 0;
+    }
+    return 1;
+}
+
+/* The member each member j of an item moves to: the gates applied to a
+ * buffer of one marker value per member (member bit i <-> qubit H[i]). */
+static int item_moves(const or_gate *g, int ng, const int *H, int h, uint64_t fixed, int *dest)
+{
+    int nm = 1 << h;
+    double *mark = calloc((size_t)2 * nm, sizeof(double));
+    for (int j = 0; j < nm; ++j) mark[2 * j] = j + 1;
+    int rc = 0;
+    for (int i = 0; i < ng && rc == 0; ++i)
+        if (apply_gate_buf(mark, h, H, fixed, &g[i]) != 0) rc = -2;
+    for (int j = 0; j < nm && rc == 0; ++j)
+        dest[(int)mark[2 * j] - 1] = j;
+    free(mark);
+    return rc;
+}
+
 /*
  * One sweep: the gates g[0..ng-1] applied to every item.  An item is the
  * group of 2^h tiles whose tile indices differ only in the bits of the
@@ -906,11 +958,39 @@ static int csim_sweep_items(or_csim *cs, const or_gate *g, int ng, const int *H,
     double *buf = malloc(((size_t)1 << mb) * 16);
     int rc = 0;
     uint64_t item = 0;
+    const int moves = sweep_moves_tiles(g, ng, c);
     for (uint64_t T = 0; T < cs->ntiles && rc == 0; ++T) {
         if (T & hmask_tile) continue;
         if (item < item_lo || item >= item_hi) { ++item; continue; }
         ++item;
         uint64_t fixed = T << c;
+        if (moves) {
+            int touched = 0;
+            for (int i = 0; i < ng && !touched; ++i)
+                if (gate_touches(&g[i], fixed, fmask)) touched = 1;
+            if (!touched) { cs->items_skipped++; continue; }
+            cs->items_done++;
+            int dest[16];
+            uint64_t tj[16];
+            uint8_t *st[16];
+            uint32_t len[16];
+            u128 part[16];
+            if ((rc = item_moves(g, ng, H, h, fixed, dest)) != 0) break;
+            for (int j = 0; j < (1 << h); ++j) {
+                tj[j] = T;
+                for (int i = 0; i < h; ++i)
+                    if ((j >> i) & 1) tj[j] |= 1ull << (H[i] - c);
+                st[j] = cs->st[tj[j]];
+                len[j] = cs->len[tj[j]];
+                part[j] = cs->part[tj[j]];
+            }
+            for (int j = 0; j < (1 << h); ++j) {
+                cs->st[tj[dest[j]]] = st[j];
+                cs->len[tj[dest[j]]] = len[j];
+                cs->part[tj[dest[j]]] = part[j];
+            }
+            continue;
+        }
         int touched = alpha != 1.0;
         for (int i = 0; i < ng && !touched; ++i)
             if (gate_touches(&g[i], fixed, fmask)) touched = 1;
@@ -964,10 +1044,23 @@ int or_item_sweep(int n, int c, const int *H, int h, uint64_t base_tile,
     for (int q = c; q < n; ++q) fmask |= 1ull << q;
     for (int i = 0; i < h; ++i) fmask &= ~(1ull << H[i]);
     uint64_t fixed = base_tile << c;
-    int touched = alpha != 1.0;
+    const int moves = sweep_moves_tiles(g, ng, c);
+    int touched = alpha != 1.0 && !moves;
     for (int i = 0; i < ng && !touched; ++i)
         if (gate_touches(&g[i], fixed, fmask)) touched = 1;
     size_t used = 0;
+    if (touched && moves) {                      /* streams move to their members */
+        int dest[16], src[16];
+        if (item_moves(g, ng, H, h, fixed, dest) != 0) return -2;
+        for (int j = 0; j < (1 << h); ++j) src[dest[j]] = j;
+        for (int j = 0; j < (1 << h); ++j) {
+            if (used + in_len[src[j]] > out_cap) return -3;
+            memcpy(out + used, in[src[j]], in_len[src[j]]);
+            out_len[j] = in_len[src[j]];
+            used += in_len[src[j]];
+        }
+        return 0;
+    }
     if (!touched) {
         for (uint64_t j = 0; j < (1ull << h); ++j) {
             if (used + in_len[j] > out_cap) return -3;

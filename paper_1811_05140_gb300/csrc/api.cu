@@ -194,6 +194,23 @@ unsigned long long row_factoring(const HostGate &g) {
     return fac;
 }
 
+// Entries all exactly 0 or 1, one 1 in every row and every column: the
+// gate maps basis states to basis states.
+bool is_permutation(const HostGate &g) {
+    const int dim = 1 << g.k;
+    for (int r = 0; r < dim; ++r) {
+        int row = 0, col = 0;
+        for (int c = 0; c < dim; ++c) {
+            const double a = g.m[2 * (r * dim + c)], b = g.m[2 * (r * dim + c) + 1];
+            if (b != 0.0 || !(a == 0.0 || a == 1.0)) return false;
+            row += a == 1.0;
+            col += g.m[2 * (c * dim + r)] == 1.0 && g.m[2 * (c * dim + r) + 1] == 0.0;
+        }
+        if (row != 1 || col != 1) return false;
+    }
+    return true;
+}
+
 // FP64 instructions of one matrix entry's term, per component: zero and a
 // leading +-1 are free, real and imaginary entries take one, general two.
 double entry_cost(double ur, double ui, bool first) {
@@ -819,13 +836,16 @@ qs::SweepParams sweep_params(qsim_t h, const FlushCtx &fc, size_t j) {
     p.sweep_id = fc.id0 + (unsigned)j;
     p.use_alpha = h->normalize;
     p.low_free = 1;
+    p.moves_tiles = 1;
     const unsigned long long lowm = (1ull << h->c) - 1ull;
     for (int gi = sw.lo; gi < sw.hi && p.low_free; ++gi) {
         const HostGate &g = h->queue[gi];
         if (g.cm & lowm) p.low_free = 0;
         for (int i = 0; i < g.k; ++i)
             if (g.t[i] < h->c) p.low_free = 0;
+        if (!is_permutation(g)) p.moves_tiles = 0;
     }
+    p.moves_tiles &= p.low_free;
     return p;
 }
 

@@ -1187,6 +1187,39 @@ __device__ void wcarry(const uint8_t *in_arena, const unsigned long long *in_tab
     __syncwarp();
 }
 
+// Move one stream unchanged from tile `src` of the input arena to tile
+// `dst` of the output arena, with its norm partial (plo, phi).  Warp-wide.
+__device__ void wmove(const uint8_t *in_arena, const unsigned long long *in_table, unsigned long long src,
+                      unsigned long long dst, uint8_t *out_arena, unsigned long long out_cap,
+                      unsigned long long *out_table, unsigned long long *part, unsigned long long plo,
+                      unsigned long long phi, DevScalars *scal, unsigned sweep_id) {
+    const int lane = threadIdx.x & 31;
+    const uint8_t *sp = in_arena + in_table[src];
+    const uint32_t size = HDR + reinterpret_cast<const uint32_t *>(sp)[1];
+    unsigned long long off = 0;
+    int ok = 0;
+    if (lane == 0) {
+        off = atomicAdd(&scal->bump, (unsigned long long)size);
+        ok = off + size <= out_cap;
+        if (!ok) {
+            atomicOr(&scal->err, ERR_OVERFLOW);
+            atomicCAS(&scal->err_sweep, 0u, sweep_id + 1u);
+        }
+        atomic_add128(&scal->acc_lo, &scal->acc_hi, plo, phi);
+        part[2 * dst] = plo;
+        part[2 * dst + 1] = phi;
+        if (ok) out_table[dst] = off;
+    }
+    off = shfl64(off, 0);
+    ok = __shfl_sync(FULL, ok, 0);
+    if (ok) {
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(sp);
+        uint4 *d4 = reinterpret_cast<uint4 *>(out_arena + off);
+        for (uint32_t i = lane; i < size / 16u; i += 32) d4[i] = s4[i];
+    }
+    __syncwarp();
+}
+
 // exact norm of a decoded tile (warp-wide), for validation of imports
 __device__ void wnorm(const double *re, const double *im, int N, unsigned long long &lo,
                       unsigned long long &hi, unsigned &rng) {
@@ -1243,6 +1276,8 @@ __global__ void __launch_bounds__(SWEEP_THREADS, QS_SWEEP_MIN_BLOCKS) sweep_kern
     __shared__ SweepParams P;
     __shared__ unsigned s_act[MAX_SWEEP_GATES / 32];
     __shared__ int s_entry, s_skip, s_chunk, s_any;
+    __shared__ int s_dest[1 << MAX_PAIRS];
+    __shared__ unsigned long long s_plo[1 << MAX_PAIRS], s_phi[1 << MAX_PAIRS];
     __shared__ double s_alpha;
     const unsigned long long total = istart[nlist];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1301,11 +1336,42 @@ __global__ void __launch_bounds__(SWEEP_THREADS, QS_SWEEP_MIN_BLOCKS) sweep_kern
         }
         __syncthreads();
         const bool active = s_any != 0;
-        if (!active && !scale) {
+        if (!active && (!scale || P.moves_tiles)) {
             for (int j = warp; j < ntl; j += NWARPS)
                 wcarry(P.in_arena, P.in_table, member_tile(T, j, h, hb), P.out_arena, P.out_cap,
                        P.out_table, P.part, P.scal, P.sweep_id);
             if (threadIdx.x == 0) atomicAdd(&P.scal->items_skipped, 1ull);
+            continue;
+        }
+        // Sweeps of permutations on qubits >= c move whole tiles: member j's
+        // stream goes unchanged to the member the gates map it to (no
+        // decompression, so no normalize; the norm is unchanged).
+        if (P.moves_tiles) {
+            if ((int)threadIdx.x < ntl) {
+                unsigned L = (unsigned)threadIdx.x << c;     // buffer index of the member's first amplitude
+                for (int g = 0; g < P.ngates; ++g) {
+                    if (!((s_act[g >> 5] >> (g & 31)) & 1u)) continue;
+                    const SGate &sgl = P.sgates[g];
+                    if (sgl.kind == 0 || (L & sgl.lcm) != sgl.lcv) continue;    // identity / controls fail
+                    const int dim = 1 << sgl.k;
+                    int r = (int)((L >> sgl.p0) & 1u);
+                    if (sgl.k > 1) r |= (int)((L >> sgl.p1) & 1u) << 1;
+                    int r2 = r;
+                    for (int row = 0; row < dim; ++row)
+                        if (((sgl.cls >> (3 * (row * dim + r))) & 7ull) == EC_ONE) r2 = row;
+                    L = (L & ~(1u << sgl.p0)) | ((unsigned)(r2 & 1) << sgl.p0);
+                    if (sgl.k > 1) L = (L & ~(1u << sgl.p1)) | ((unsigned)((r2 >> 1) & 1) << sgl.p1);
+                }
+                const unsigned long long Tj = member_tile(T, threadIdx.x, h, hb);
+                s_dest[threadIdx.x] = (int)(L >> c);
+                s_plo[threadIdx.x] = P.part[2 * Tj];
+                s_phi[threadIdx.x] = P.part[2 * Tj + 1];
+            }
+            __syncthreads();
+            for (int j = warp; j < ntl; j += NWARPS)
+                wmove(P.in_arena, P.in_table, member_tile(T, j, h, hb), member_tile(T, s_dest[j], h, hb),
+                      P.out_arena, P.out_cap, P.out_table, P.part, s_plo[j], s_phi[j], P.scal, P.sweep_id);
+            if (threadIdx.x == 0) atomicAdd(&P.scal->items_done, 1ull);
             continue;
         }
         // Uniform items: when every member tile is CONST and no gate of the

@@ -115,6 +115,7 @@ struct SweepParams {
     unsigned int sweep_id;
     int use_alpha;
     int low_free;                   // no gate of the sweep targets or controls a qubit < c
+    int moves_tiles;                // low_free and every gate a permutation: tiles move whole
 };
 
 // End-of-pass bookkeeping of one state (norm, scale, used bytes).

@@ -369,3 +369,16 @@ def test_decoders_agree_on_corrupted_streams():
             agree += 1
     assert agree >= 30
     st.close()
+
+
+def test_tile_moving_sweeps_match_oracle():
+    # permutations on qubits >= c only (X, SWAP, CNOT and Toffoli-type
+    # controls on high qubits): the streams move whole, without normalize;
+    # then ordinary sweeps, all byte-identical to the oracle
+    n = 13
+    moves = [I.x(12), I.swap(8, 11), I.Gate(I.MAT_X, (9,), (10,), (1,)),
+             I.Gate(I.MAT_X, (12,), (8, 9), (1, 0)), I.x(10)]
+    gates = I.random_grid(*I.grid_shape(n), 5, 21) + moves + I.qft(n)[:30] + moves[::-1]
+    for codec, eps in (("rel", 1e-4), ("lossless", 0.0)):
+        st, cs, c = run_both(n, 8, codec, eps, gates)
+        assert_same_streams(st, cs, n, c)

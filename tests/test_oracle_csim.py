@@ -164,3 +164,35 @@ def test_normalisation_reduces_norm_drift():
     a.run(gates, 2, 1)
     b.run(gates, 2, 1)
     assert abs(a.norm() - 1) < abs(b.norm() - 1) or abs(a.norm() - 1) < 1e-3
+
+
+def test_sweeps_that_only_move_tiles():
+    """A sweep of permutation gates on qubits >= c moves whole tiles: the
+    stored state afterwards is the exact permutation of the stored state
+    before (no normalize, no re-quantisation), each stream moves unchanged
+    to its image tile, and the scale stays the same.  With a low qubit
+    involved the sweep decompresses as usual (normalize, then gates)."""
+    n, c = 10, 4
+    cs = oracle.CSim(n, c, [oracle.shift_for_eps(1e-3)], normalize=True)
+    cs.reset_basis(0)
+    cs.run(I.random_grid(2, 5, 6, 4), 2, 8)
+    alpha = cs.alpha
+    assert alpha != 1.0
+    moves = [I.x(9), I.swap(5, 8), I.Gate(I.MAT_X, (6,), (7,), (1,)), I.x(7)]
+    before = cs.dense()
+    streams = [cs.stream(t) for t in range(1 << (n - c))]
+    for lo, hi, Hs in partition(moves, n, c, 4, 8):
+        cs.sweep(moves[lo:hi], Hs)
+    want = oracle.dense_run(before.copy(), n, moves)
+    assert np.array_equal(cs.dense().view(np.uint64), want.view(np.uint64))
+    assert cs.alpha == alpha
+    # every stream is one of the old streams, moved whole
+    assert sorted(cs.stream(t) for t in range(1 << (n - c))) == sorted(streams)
+    # a permutation on a low qubit decompresses: the values are rescaled
+    cs.sweep([I.x(0)], [])
+    ref = (want.copy().view(np.float64) * alpha).view(np.complex128)
+    oracle.dense_run(ref, n, [I.x(0)])
+    got = cs.dense()
+    r, g = ref.view(np.float64), got.view(np.float64)
+    nz = r != 0
+    assert np.all(np.abs(g - r)[nz] <= 1e-3 * np.abs(r[nz]))
