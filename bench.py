@@ -555,7 +555,10 @@ def main():
         traffic, why = traffic_from_profile()
         cpu = None
         if not args.no_cpu_baseline and world == 1:
-            v, spent, desc = oracle_sample(n, args.eps, args.depth, res["xval"], 24)
+            # size the sample for about 12 s of CPU work
+            _, probe_s, _ = oracle_sample(n, args.eps, args.depth, res["xval"], 4)
+            items = max(4, min(4096, int(4 * 12.0 / max(probe_s, 1e-3))))
+            v, spent, desc = oracle_sample(n, args.eps, args.depth, res["xval"], items)
             cpu = {"value": v, "unit": "gates/s", "cores": 1, "kind": "oracle", "sample": desc,
                    "seconds": round(spent, 2)}
         line = {
