@@ -107,6 +107,32 @@ __device__ __forceinline__ void sq_units_q(unsigned long long u, int s, unsigned
     else if (sh > -64) { lo = sq >> (-sh); }
 }
 
+// Code q = (B + 2^(s-1)) >> s of the magnitude bits B = mh:lo (high and
+// low words) for 32 <= s <= 52, in 32-bit arithmetic: for s >= 33 the low
+// word cannot carry into the result, for s = 32 it adds its top bit.
+__device__ __forceinline__ uint32_t quant_hi(uint32_t mh, uint32_t lo, int s) {
+    return s == 32 ? mh + (lo >> 31) : (mh + (1u << (s - 33))) >> (s - 32);
+}
+
+// sq_units of the reconstructed value q << s (32 <= s <= 52): the same value,
+// from the code in 32-bit arithmetic (exponent q >> (52 - s), significand
+// bits above the s zero bits).
+__device__ __forceinline__ void sq_units_code(uint32_t q, int s, unsigned long long &lo,
+                                              unsigned long long &hi, unsigned &range) {
+    lo = hi = 0;
+    if (q == 0) return;
+    const int fb = 52 - s;                                   // fraction bits kept
+    const uint32_t E = q >> fb;
+    if (E >= 1027u) { range = 1; return; }
+    const uint32_t m = (q & ((1u << fb) - 1u)) | (1u << fb);
+    const unsigned long long sq = (unsigned long long)m * m;
+    const int sh = 2 * (int)E - 2038 + 2 * s;
+    if (sh >= 64) { hi = sq << (sh - 64); }
+    else if (sh > 0) { lo = sq << sh; hi = sq >> (64 - sh); }
+    else if (sh == 0) { lo = sq; }
+    else if (sh > -64) { lo = sq >> (-sh); }
+}
+
 __device__ __forceinline__ void add128(unsigned long long &lo, unsigned long long &hi,
                                        unsigned long long alo, unsigned long long ahi) {
     unsigned long long nlo = lo + alo;
@@ -683,8 +709,14 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
             }
             const unsigned long long q = carry + inc;
             if (lane < L) {
-                const unsigned long long sg = (unsigned long long)((sgw >> lane) & 1u) << 63;
-                double x = bitsd(nzl ? ((q << s) | sg) : sg);
+                double x;
+                if (s >= 32) {                               // (q << s) has a zero low word
+                    const uint32_t hw = (nzl ? (uint32_t)q << (s - 32) : 0u) | (((sgw >> lane) & 1u) << 31);
+                    x = __hiloint2double((int)hw, 0);
+                } else {
+                    const unsigned long long sg = (unsigned long long)((sgw >> lane) & 1u) << 63;
+                    x = bitsd(nzl ? ((q << s) | sg) : sg);
+                }
                 if (scale) x = __dmul_rn(x, alpha);
                 v[g * 32 + lane] = x;
             }
@@ -727,6 +759,56 @@ __device__ __forceinline__ void size_levels(const double *re, const double *im, 
     ls.nz = 0;
     ls.sw0 = ls.sw1 = ls.zw0 = ls.zw1 = 0;
     ls.f0 = ls.f1 = 0;
+    if (cc.nlev == 1 && !force0 && cc.shifts[0] >= 32) {
+        // one lossy level at shift >= 32 (the common case): the same
+        // quantities in 32-bit arithmetic on the high and low words
+        const int s = cc.shifts[0];
+        for (int k = 0; k < 2; ++k) {
+            const double *v = k ? im : re;
+            bool seen = false;
+            uint32_t lastq = 0;
+            unsigned long long first = 0, wl = 0;
+            for (int g = 0; g < G; ++g) {
+                const double x = lane < L ? v[g * 32 + lane] : 0.0;
+                const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+                const uint32_t mh = hi & 0x7FFFFFFFu;
+                const bool nzv = (mh | lo) != 0u;
+                nonfin |= mh >= 0x7FF00000u;
+                inel |= nzv && (mh < 0x00100000u || mh >= 0x7FE00000u);
+                const uint32_t sw = __ballot_sync(FULL, hi >> 31);
+                const uint32_t nzm = __ballot_sync(FULL, nzv);
+                if (lane == g) {
+                    if (k) { ls.sw1 = sw; ls.zw1 = ~nzm & lanes; }
+                    else { ls.sw0 = sw; ls.zw0 = ~nzm & lanes; }
+                }
+                if (nzm == 0u) continue;
+                const uint32_t q = quant_hi(mh, lo, s);
+                uint32_t qp;
+                if (nzm == lanes) {
+                    const uint32_t up = __shfl_up_sync(FULL, q, 1);
+                    qp = lane ? up : (seen ? lastq : q);
+                } else {
+                    const uint32_t pm = nzm & below;
+                    const uint32_t qs = __shfl_sync(FULL, q, pm ? 31 - __clz(pm) : lane);
+                    qp = pm ? qs : (seen ? lastq : q);
+                }
+                if (!seen) {
+                    const int f = __ffs(nzm) - 1;
+                    first = ((unsigned long long)__shfl_sync(FULL, mh, f) << 32) | __shfl_sync(FULL, lo, f);
+                }
+                const uint32_t r = q - qp;
+                const uint32_t z = ((nzm >> lane) & 1u) ? (r << 1) ^ (uint32_t)((int)r >> 31) : 0u;
+                const uint32_t oz = __reduce_or_sync(FULL, z);
+                const uint32_t w = oz ? 32u - (uint32_t)__clz(oz) : 0u;
+                if (w) ls.nz |= 1u;
+                if (lane == g) wl = w;
+                lastq = __shfl_sync(FULL, q, 31 - __clz(nzm));
+                seen = true;
+            }
+            if (k) { ls.f1 = first; ls.wl1 = wl; } else { ls.f0 = first; ls.wl0 = wl; }
+        }
+        return;
+    }
     for (int k = 0; k < 2; ++k) {
         const double *v = k ? im : re;
         bool seen = false;
@@ -941,10 +1023,11 @@ __device__ EncodeOut wencode(const double *re, const double *im, const CodecCfg 
             const uint32_t wk = k ? ws1 : ws0, offk = k ? off1 : off0;
             uint32_t carry = (uint32_t)quant(k ? ls.f1 : ls.f0, s);     // the anchor
             for (int g = 0; g < G; ++g) {
-                const unsigned long long B = lane < L ? (dbits(v[g * 32 + lane]) & MAG) : 0ull;
-                const uint32_t nzm = __ballot_sync(FULL, lane < L && B != 0);
+                const double x = lane < L ? v[g * 32 + lane] : 0.0;
+                const uint32_t mh = (uint32_t)__double2hiint(x) & 0x7FFFFFFFu, lo = (uint32_t)__double2loint(x);
+                const uint32_t nzm = __ballot_sync(FULL, (mh | lo) != 0u);
                 if (nzm == 0u) continue;                     // all zeros: no norm, no data
-                const uint32_t q = (uint32_t)quant(B, s);
+                const uint32_t q = (mh | lo) ? quant_hi(mh, lo, s) : 0u;
                 const bool dense = nzm == lanes;
                 uint32_t qp;
                 if (dense) {
@@ -956,9 +1039,9 @@ __device__ EncodeOut wencode(const double *re, const double *im, const CodecCfg 
                     qp = pm ? qs : carry;
                 }
                 carry = __shfl_sync(FULL, q, dense ? L - 1 : 31 - __clz(nzm));
-                if (lane < L) {
+                if (q) {
                     unsigned long long l0, h0;
-                    sq_units_q((unsigned long long)q << s, s, l0, h0, rng);
+                    sq_units_code(q, s, l0, h0, rng);
                     add128(nlo, nhi, l0, h0);
                 }
                 const uint32_t w = __shfl_sync(FULL, wk, g);
