@@ -656,8 +656,8 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
             const uint32_t *base = data + wo;
             sh = bo & 31u;
             x0 = __ldg(base + j0);
-            x1 = j0 + 1 < nwd ? __ldg(base + j0 + 1) : 0u;
-            x2 = j0 + 2 < nwd ? __ldg(base + j0 + 2) : 0u;
+            x1 = j0 + 1 < nwd && sh + w > 32u ? __ldg(base + j0 + 1) : 0u;
+            x2 = j0 + 2 < nwd && sh + w > 64u ? __ldg(base + j0 + 2) : 0u;
         }
     };
     const int T = 2 * G;
@@ -685,16 +685,22 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
             const bool nzl = (nzw >> lane) & 1u;
             unsigned long long z = 0;
             if (nzl && w) {
-                const unsigned long long lo = (unsigned long long)x0 | ((unsigned long long)x1 << 32);
-                const unsigned long long vv = sh ? ((lo >> sh) | ((unsigned long long)x2 << (64 - sh))) : lo;
-                z = w == 64 ? vv : (vv & ((1ull << w) - 1ull));
+                if (w <= 32) {                               // at most two words
+                    const uint32_t z32 = __funnelshift_r(x0, x1, sh);
+                    z = w == 32 ? z32 : (z32 & ((1u << w) - 1u));
+                } else {
+                    const unsigned long long lo = (unsigned long long)x0 | ((unsigned long long)x1 << 32);
+                    const unsigned long long vv = sh ? ((lo >> sh) | ((unsigned long long)x2 << (64 - sh))) : lo;
+                    z = w == 64 ? vv : (vv & ((1ull << w) - 1ull));
+                }
             }
             const unsigned long long r = unzigzag(z);        // 0 for zeros and lanes >= L
             unsigned long long inc;
             if (w == 0) {                                    // every residual 0
                 inc = 0;
             } else if (w <= 27) {                            // 32 partial sums of |r| < 2^26 fit in int32
-                int v32 = (int)(long long)r;
+                const uint32_t z32 = (uint32_t)z;
+                int v32 = (int)((z32 >> 1) ^ (0u - (z32 & 1u)));
                 for (int d = 1; d < 32; d <<= 1) {
                     int o = __shfl_up_sync(FULL, v32, d);
                     if (lane >= d) v32 += o;
