@@ -871,11 +871,93 @@ __device__ __forceinline__ void size_levels(const double *re, const double *im, 
     }
 }
 
+// One pass over a tile for a single lossy level at shift s >= 32 (c >= 5,
+// no value outside the lossy range): the sizes, sign and zero words and
+// anchors of size_levels, the norm partial, and the packed words of every
+// group, which are written over the group's own values in shared memory
+// once all lanes have read them (at most 32 words, the first half of the
+// group's 256 bytes).  Same quantities and words as size_levels followed
+// by the packing pass.
+__device__ void pack_onepass(double *re, double *im, int s, int G, LevelSizes &ls, unsigned long long &nlo,
+                             unsigned long long &nhi, unsigned &rng, uint32_t *wstage) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t below = lanes_below();
+    ls.wl0 = ls.wl1 = 0;
+    ls.nz = 0;
+    ls.sw0 = ls.sw1 = ls.zw0 = ls.zw1 = 0;
+    ls.f0 = ls.f1 = 0;
+    for (int k = 0; k < 2; ++k) {
+        double *v = k ? im : re;
+        bool seen = false;
+        uint32_t lastq = 0;
+        unsigned long long first = 0, wl = 0;
+        for (int g = 0; g < G; ++g) {
+            const double x = v[g * 32 + lane];
+            const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+            const uint32_t mh = hi & 0x7FFFFFFFu;
+            const bool nzv = (mh | lo) != 0u;
+            const uint32_t sw = __ballot_sync(FULL, hi >> 31);
+            const uint32_t nzm = __ballot_sync(FULL, nzv);
+            if (lane == g) {
+                if (k) { ls.sw1 = sw; ls.zw1 = ~nzm; }
+                else { ls.sw0 = sw; ls.zw0 = ~nzm; }
+            }
+            if (nzm == 0u) continue;
+            const uint32_t q = nzv ? quant_hi(mh, lo, s) : 0u;
+            const bool dense = nzm == FULL;
+            uint32_t qp;
+            if (dense) {
+                const uint32_t up = __shfl_up_sync(FULL, q, 1);
+                qp = lane ? up : (seen ? lastq : q);
+            } else {
+                const uint32_t pm = nzm & below;
+                const uint32_t qs = __shfl_sync(FULL, q, pm ? 31 - __clz(pm) : lane);
+                qp = pm ? qs : (seen ? lastq : q);
+            }
+            if (!seen) {
+                const int f = __ffs(nzm) - 1;
+                first = ((unsigned long long)__shfl_sync(FULL, mh, f) << 32) | __shfl_sync(FULL, lo, f);
+            }
+            const bool nzl = (nzm >> lane) & 1u;
+            const uint32_t r = q - qp;
+            const uint32_t z = nzl ? (r << 1) ^ (uint32_t)((int)r >> 31) : 0u;
+            const uint32_t oz = __reduce_or_sync(FULL, z);
+            const uint32_t w = oz ? 32u - (uint32_t)__clz(oz) : 0u;
+            if (lane == g) wl = w;
+            if (q) {
+                unsigned long long l0, h0;
+                sq_units_code(q, s, l0, h0, rng);
+                add128(nlo, nhi, l0, h0);
+            }
+            if (w) {
+                ls.nz = 1u;
+                const uint32_t nwd = ((uint32_t)__popc(nzm) * w + 31u) >> 5;
+                wstage[lane] = 0u;
+                __syncwarp();
+                if (nzl) {
+                    const uint32_t rank = dense ? (uint32_t)lane : (uint32_t)__popc(nzm & below);
+                    const uint32_t bo = rank * w, j0 = bo >> 5, sh = bo & 31u;
+                    atomicOr(&wstage[j0], z << sh);
+                    if (sh + w > 32) atomicOr(&wstage[j0 + 1], z >> (32 - sh));
+                }
+                __syncwarp();
+                if ((uint32_t)lane < nwd) reinterpret_cast<uint32_t *>(v + g * 32)[lane] = wstage[lane];
+                __syncwarp();
+            }
+            lastq = __shfl_sync(FULL, q, dense ? 31 : 31 - __clz(nzm));
+            seen = true;
+        }
+        if (k) { ls.f1 = first; ls.wl1 = wl; } else { ls.f0 = first; ls.wl0 = wl; }
+    }
+}
+
 // Encode planar re/im (2^c values each) of tile `tile` into the output
 // arena with Algorithm 2's ladder (every level sized in one pass).
 // Warp-wide.  Writes the stream, its table entry and norm partial, and adds
 // to the running norm.  wstage: 64 words of shared memory of this warp.
-__device__ EncodeOut wencode(const double *re, const double *im, const CodecCfg &cc,
+// With one lossy level at shift >= 32 the tile is coded in one pass and
+// its values in shared memory are overwritten.
+__device__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc,
                              unsigned long long tile, uint8_t *out_arena, unsigned long long out_cap,
                              unsigned long long *out_table, unsigned long long *part,
                              DevScalars *scal, unsigned sweep_id, uint32_t *wstage) {
@@ -887,7 +969,22 @@ __device__ EncodeOut wencode(const double *re, const double *im, const CodecCfg 
 
     LevelSizes ls;
     int nonfin = 0, inel = 0;
-    if (!cc.force_raw) {
+    unsigned long long nlo = 0, nhi = 0;
+    unsigned rng = 0;
+    bool onepass = !cc.force_raw && cc.nlev == 1 && cc.shifts[0] >= 32 && c >= 5;
+    if (onepass) {                           // every value zero or inside the lossy range?
+        bool odd = false;
+        for (int i = lane; i < N; i += 32) {
+            const uint32_t a = (uint32_t)__double2hiint(re[i]) & 0x7FFFFFFFu, al = (uint32_t)__double2loint(re[i]);
+            const uint32_t b = (uint32_t)__double2hiint(im[i]) & 0x7FFFFFFFu, bl = (uint32_t)__double2loint(im[i]);
+            odd |= a >= 0x7FE00000u || (a < 0x00100000u && (a | al) != 0u);
+            odd |= b >= 0x7FE00000u || (b < 0x00100000u && (b | bl) != 0u);
+        }
+        onepass = !__any_sync(FULL, odd);
+    }
+    if (onepass) {
+        pack_onepass(re, im, cc.shifts[0], G, ls, nlo, nhi, rng, wstage);
+    } else if (!cc.force_raw) {
         size_levels(re, im, cc, G, L, false, ls, nonfin, inel);
         nonfin = __any_sync(FULL, nonfin);
         inel = __any_sync(FULL, inel);
@@ -990,8 +1087,6 @@ __device__ EncodeOut wencode(const double *re, const double *im, const CodecCfg 
         reinterpret_cast<uint32_t *>(dst)[lane] = v;
     }
     uint8_t *b = dst + HDR;
-    unsigned long long nlo = 0, nhi = 0;
-    unsigned rng = 0;
     if (mode == M_PACKED) {
         // sign sections, then zero sections
         const uint32_t sv0 = s ? ls.sw0 & ~ls.zw0 : ls.sw0, sv1 = s ? ls.sw1 & ~ls.zw1 : ls.sw1;
@@ -1022,7 +1117,18 @@ __device__ EncodeOut wencode(const double *re, const double *im, const CodecCfg 
         const uint32_t doff = moff + wb;
         uint32_t *data = reinterpret_cast<uint32_t *>(b + doff);
         const uint32_t below = lanes_below();
-        for (int k = 0; k < 2 && s >= 32; ++k) {
+        for (int k = 0; k < 2 && onepass; ++k) {      // packed words staged in shared memory
+            const double *v = k ? im : re;
+            const uint32_t wk = k ? ws1 : ws0, offk = k ? off1 : off0, nnk = k ? ~ls.zw1 : ~ls.zw0;
+            for (int g = 0; g < G; ++g) {
+                const uint32_t w = __shfl_sync(FULL, wk, g);
+                if (w == 0) continue;
+                const uint32_t wo = __shfl_sync(FULL, offk, g);
+                const uint32_t nwd = ((uint32_t)__popc(__shfl_sync(FULL, nnk, g)) * w + 31u) >> 5;
+                if ((uint32_t)lane < nwd) (data + wo)[lane] = reinterpret_cast<const uint32_t *>(v + g * 32)[lane];
+            }
+        }
+        for (int k = 0; k < 2 && s >= 32 && !onepass; ++k) {
             // codes < 2^31 at shift >= 32: 32-bit codes, residuals and shuffles,
             // values spanning at most two words (the same bits as below)
             const double *v = k ? im : re;
@@ -1125,7 +1231,7 @@ __device__ EncodeOut wencode(const double *re, const double *im, const CodecCfg 
             double2 *o = reinterpret_cast<double2 *>(b);
             for (int i = lane; i < N; i += 32) o[i] = make_double2(re[i], im[i]);
         }
-        for (int i = lane; i < N; i += 32) {
+        for (int i = lane; i < N && !onepass; i += 32) {       // (one pass: norm already taken)
             unsigned long long u0 = dbits(re[i]) & MAG, u1 = dbits(im[i]) & MAG;
             if (mode == M_CONST) { u0 = quant(u0, s) << s; u1 = quant(u1, s) << s; }
             unsigned long long l0, h0, l1, h1;
