@@ -438,6 +438,14 @@ qsim_status qsim_server_destroy(qsim_server_t s);
 /* qsim_version -- library version string. */
 const char *qsim_version(void);
 
+/* qsim_fp64_rate -- measured FP64 fused multiply-add rate of GPU `device`
+ * (FMA per second): independent DFMA chains over every SM, timed with CUDA
+ * events after a warm-up launch (about 20 ms).  The denominator the
+ * benchmark reports beside the nominal FP64 peak for the gate arithmetic,
+ * which is FP64-bound on this part.  Errors: QSIM_ERR_ARG (null out),
+ * QSIM_ERR_CUDA. */
+qsim_status qsim_fp64_rate(int device, double *fma_per_s);
+
 #ifdef __cplusplus
 }
 #endif

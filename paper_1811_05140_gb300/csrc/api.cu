@@ -60,6 +60,7 @@ cudaError_t launch_pair_sum(const Acc4 *in, Acc4 *out, unsigned long long nout, 
                             cudaStream_t st);
 cudaError_t configure_kernels();
 int sweep_blocks_per_sm(int mb);
+cudaError_t fp64_rate(int device, double *fma_per_s);
 }  // namespace qs
 
 namespace {
@@ -516,6 +517,26 @@ unsigned long long qs_handle_footprint(qsim_t h) {
 extern "C" {
 
 const char *qsim_version(void) { return "qsim-aalc 0.1 (sm_103a)"; }
+
+qsim_status qsim_fp64_rate(int device, double *fma_per_s) {
+    if (!fma_per_s) return fail(nullptr, QSIM_ERR_ARG, "null output");
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, QSIM_ERR_CUDA, "no CUDA device");
+    }
+    if (device < 0 || device >= count) return fail(nullptr, QSIM_ERR_ARG, "no device %d", device);
+    int cur = 0;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e == cudaSuccess && cur != device) e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = qs::fp64_rate(device, fma_per_s);
+    if (cur != device) cudaSetDevice(cur);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, QSIM_ERR_CUDA, "fp64 probe: %s", cudaGetErrorString(e));
+    }
+    return QSIM_OK;
+}
 
 const char *qsim_last_error(qsim_t h) { return h ? h->err.c_str() : g_last_error.c_str(); }
 

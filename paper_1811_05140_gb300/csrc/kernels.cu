@@ -1642,6 +1642,23 @@ constexpr int TILE_WARPS = 4;
 
 // Encode a state given densely (device, interleaved) or the basis state
 // |x> (dense == nullptr) into every tile.
+// FP64 issue-rate probe: eight independent DFMA chains per thread, so the
+// pipe, not the chain latency, bounds it.  out[blockIdx.x*blockDim.x +
+// threadIdx.x] keeps the results live.
+__global__ void __launch_bounds__(256) fp64_rate_kernel(double *out, int iters, double a, double b) {
+    double x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = (double)(threadIdx.x + i);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = __fma_rn(x[i], a, b);
+    }
+    double sum = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) sum += x[i];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = sum;
+}
+
 __global__ void __launch_bounds__(32 * TILE_WARPS) init_kernel(
     const double2 *dense, unsigned long long x, CodecCfg cc, unsigned long long ntiles,
     uint8_t *out_arena, unsigned long long out_cap, unsigned long long *out_table,
@@ -2041,6 +2058,30 @@ cudaError_t configure_kernels() {
     if ((e = cudaFuncSetAttribute(probs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, t1))) return e;
     if ((e = cudaFuncSetAttribute(fidelity_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, t2))) return e;
     return cudaSuccess;
+}
+
+cudaError_t fp64_rate(int device, double *fma_per_s) {
+    cudaError_t e;
+    int sms = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device))) return e;
+    const int blocks = sms * 8, threads = 256, iters = 4096;
+    double *out = nullptr;
+    if ((e = cudaMalloc(&out, sizeof(double) * blocks * threads))) return e;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    fp64_rate_kernel<<<blocks, threads>>>(out, iters, 0.999999, 1e-9);    // warm-up
+    cudaEventRecord(e0);
+    for (int r = 0; r < 5; ++r) fp64_rate_kernel<<<blocks, threads>>>(out, iters, 0.999999, 1e-9);
+    cudaEventRecord(e1);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (e == cudaSuccess) *fma_per_s = 5.0 * blocks * threads * iters * 8.0 / (ms * 1e-3);
+    return e;
 }
 
 int sweep_blocks_per_sm(int mb) {

@@ -30,7 +30,7 @@ EXPORTS = ["qsim_create", "qsim_destroy", "qsim_set_stream", "qsim_set_aalc", "q
            "qsim_import_tiles", "qsim_plan_sweeps", "qsim_version", "qsim_set_profiling",
            "qsim_profile", "qsim_encode_noalloc", "qsim_flush_batch", "qsim_server_create",
            "qsim_server_submit", "qsim_server_result", "qsim_server_wait", "qsim_server_drain",
-           "qsim_server_stats", "qsim_server_destroy", "qsim_set_pool"]
+           "qsim_server_stats", "qsim_server_destroy", "qsim_set_pool", "qsim_fp64_rate"]
 
 
 class QsimError(RuntimeError):
@@ -113,6 +113,7 @@ def load() -> C.CDLL:
         "qsim_set_normalize": ([vp, C.c_int], C.c_int),
         "qsim_set_schedule": ([vp, C.c_int, C.c_int, C.c_int], C.c_int),
         "qsim_set_pool": ([vp, vp, C.c_size_t], C.c_int),
+        "qsim_fp64_rate": ([C.c_int, C.POINTER(C.c_double)], C.c_int),
         "qsim_reset_basis": ([vp, u64], C.c_int),
         "qsim_set_amplitudes": ([vp, dp], C.c_int),
         "qsim_apply_gate": ([vp, dp, ip, C.c_int, ip, C.c_int, u64], C.c_int),
@@ -187,6 +188,16 @@ def plan_sweeps(n: int, c: int, hmax: int, depth: int, gates) -> list[tuple[int,
         hi = lo[s + 1] if s + 1 < r else ng
         out.append((lo[s], hi, tuple(HH[4 * s + i] for i in range(hh[s]))))
     return out
+
+
+def fp64_rate(device: int = 0) -> float:
+    """Measured FP64 FMA rate of the GPU (FMA per second)."""
+    L = load()
+    out = C.c_double()
+    st = L.qsim_fp64_rate(device, C.byref(out))
+    if st != 0:
+        raise QsimError(st, L.qsim_last_error(None).decode())
+    return out.value
 
 
 def encode_noalloc(dev_amps: int, n: int, tile_log2: int, eps: float, dev_out: int,
