@@ -346,6 +346,28 @@ __device__ void diag_gate_warp(double *re, double *im, int mb, const SGate &s, u
     const int fb = cb - nin;
     const unsigned cnt = (unsigned)nr << fb;
     const unsigned base = (s.lcv & inmask) | W;
+    if (nr == 1) {
+        // one entry (controlled phases, CZ, MCZ, Z, S, T): entry, class and
+        // target bits held in registers across the loop
+        const int r = (int)(rpack & 3u);
+        const unsigned code = (unsigned)(s.cls >> (3 * r)) & 7u;
+        const double ur = s.d[2 * r], ui = s.d[2 * r + 1];
+        unsigned add = base;
+        if (s.p0 >= 0 && s.p0 < cb) add |= (unsigned)(r & 1) << s.p0;
+        if (s.k > 1 && s.p1 >= 0 && s.p1 < cb) add |= (unsigned)((r >> 1) & 1) << s.p1;
+        uint8_t pos[12];
+        for (int i = 0; i < nin; ++i) pos[i] = s.ins[i];
+        for (unsigned f = lane; f < cnt; f += 32) {
+            unsigned l = f;
+            for (int i = 0; i < nin; ++i) l = insert_zero(l, pos[i]);
+            l |= add;
+            double yr = 0.0, yi = 0.0;
+            if (code != EC_ZERO) term_first(code, ur, ui, re[l], im[l], yr, yi);
+            re[l] = yr;
+            im[l] = yi;
+        }
+        return;
+    }
     for (unsigned f = lane; f < cnt; f += 32) {
         const int r = (int)((rpack >> (2 * (f >> fb))) & 3u);
         unsigned l = f & ((1u << fb) - 1u);
