@@ -394,8 +394,14 @@ __device__ void one_target(double *re, double *im, int mb, const SGate &s, const
         // y_r = d_r (x_0 + f_r x_1), the same arithmetic as row_eval
         const double d0 = m[0], d1 = m[4];
         const unsigned f0 = (unsigned)(s.fac >> 10) & 3u, f1 = (unsigned)(s.fac >> 14) & 3u;
+        const int nins = s.nins;
+        uint8_t pos[12];
+        for (int i = 0; i < nins; ++i) pos[i] = s.ins[i];
+        const unsigned lcv = s.lcv;
         for (unsigned f = threadIdx.x; f < cnt; f += SWEEP_THREADS) {
-            const unsigned l0 = deposit(f << red, s) | s.lcv;
+            unsigned l = f << red;
+            for (int i = 0; i < nins; ++i) l = insert_zero(l, pos[i]);
+            const unsigned l0 = l | lcv;
             const unsigned l1 = l0 | bit;
             const double x0r = re[l0], x0i = im[l0], x1r = re[l1], x1i = im[l1];
             double t0r, t0i, t1r, t1i;
