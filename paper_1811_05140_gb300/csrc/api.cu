@@ -1,6 +1,6 @@
 // Host side of the compressed simulator: the C ABI of include/qsim.h, the
 // sweep planner (gate run partition, partner-tile pairing) and the pass
-// driver (launch, arena regrowth, re-run after an overflow).
+// control (launch, arena regrowth, re-run after an overflow).
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -109,3 +109,24 @@ def test_grid30_aalc_sampled_items_levels_and_fidelity():
     F = st.fidelity_state(ref)
     ref.close()
     assert F > 0.99
+
+
+def test_grover30_sampled_items_every_sweep_kind():
+    # Grover at 30 qubits, two iterations, relative bound 1e-4: sampled
+    # items of sweeps of every kind (Hadamards on uniform tiles, the oracle
+    # MCZ with Hadamards on low qubits, X layers that only move tiles, spike
+    # tiles from the diffusion) re-run by the oracle from the GPU's input
+    # streams, byte for byte; then the closed form
+    import math
+    n, it, eps = 30, 2, 1e-4
+    marked = I.seeded_basis(n, 77)
+    gates = I.grover(n, marked, it)
+    st = qsim.State(n, 22, "rel", eps)
+    st.reset_basis(0)
+    checked = run_with_samples(st, n, gates, [oracle.shift_for_eps(eps)], None,
+                               lambda m: set(range(0, m, 3)), 4, 31)
+    assert checked >= 60
+    assert st.fidelity_grover(marked, it) > 1 - 1e-9
+    th = math.asin(2.0 ** (-n / 2))
+    want = math.sin((2 * it + 1) * th)
+    assert abs(st.amplitudes(marked, 1)[0].real - want) < 1e-4 * abs(want)
