@@ -168,6 +168,28 @@ def oracle_sample(n, eps, depth, xval, items_per_sweep, budget_s=None):
     return len(gates) / est_total, spent, desc
 
 
+# ------------------------------------------------------------------ ranks
+def replica_seed(rank: int) -> int:
+    """Seed of rank's replica: every rank simulates its own basis state."""
+    from paper_1811_05140_gb300 import inputs as I
+    return I.BASE_SEED + rank
+
+
+def max_over_ranks(ms: float, world: int, device: str) -> float:
+    """The slowest rank's time (the timed region ends when every rank has)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, gates: int, steps: int, ms_max: float) -> float:
+    """Whole-job gates/s: every rank's gates over the slowest rank's time."""
+    return world * gates * steps / (ms_max / 1000.0)
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -183,7 +205,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     n, eps = args.n, args.eps
     c = min(BLOCK_LOG2, n, 8)
-    xval = I.seeded_basis(n, I.BASE_SEED + rank)
+    xval = I.seeded_basis(n, replica_seed(rank))
     gates = I.qft(n)
     stream = torch.cuda.Stream()
     st = qsim.State(n, BLOCK_LOG2, "rel", eps, stream=stream)
@@ -217,10 +239,7 @@ def run_ours(args, rank, world, local_rank):
     prof = st.profile()
     launches = st.stats()["kernel_launches"] - launches0
     stats = st.stats()
-    ms_t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks(ms, world, "cuda")
     result = {
         "ms": ms_max, "prof": prof, "launches": launches, "stats": stats,
         "clocks": clk.summary(), "xval": xval,
@@ -546,7 +565,7 @@ def main():
         n = args.n
         ng = 420 if n == 28 else len(__import__("paper_1811_05140_gb300.inputs", fromlist=["qft"]).qft(n))
         ms_step = res["ms"] / args.steps
-        value = world * ng * args.steps / (res["ms"] / 1000.0)
+        value = job_rate(world, ng, args.steps, res["ms"])
         prof = res["prof"]
         sweep_s = prof["sweep_ms"] / 1000.0
         launches = max(1, prof["sweep_launches"])
