@@ -15,7 +15,8 @@
  *       error-bound ladder of Algorithm 2.
  *   O3  compressed simulator: Algorithm 2 (decompress, normalize, gate
  *       computation, compress with the error-bound ladder) over tiles, one
- *       sweep (a run of gates) at a time.
+ *       sweep (a run of gates) at a time; a sweep whose gates only permute
+ *       whole tiles moves their streams instead (sweep_moves_tiles).
  *   N   the state norm used by "normalize": the exact sum of |a|^2 in
  *       fixed point (units of 2^-112), rounded once to double.
  *
@@ -1025,8 +1026,9 @@ static int csim_sweep_items(or_csim *cs, const or_gate *g, int ng, const int *H,
  * for the oracle: in[j] (in_len[j] bytes) is the stream of member j, the
  * tile base_tile | (bits of j at the positions H[i]-c); alpha is the
  * normalize scale of the pass.  Applies the same steps as or_csim_sweep to
- * this item (kept as it is when alpha is 1 and no gate touches it) and
- * writes the members' new streams, concatenated, to out (out_len[j] each).
+ * this item (kept as it is when alpha is 1 and no gate touches it; streams
+ * moved between members when the sweep only moves tiles) and writes the
+ * members' new streams, concatenated, to out (out_len[j] each).
  * Returns 0, -1 on a malformed stream, -2 on a gate outside the item, -3
  * when out is too small.
  */
