@@ -596,6 +596,8 @@ def main():
             "fidelity_vs_fp64_gpu": res["F_ref"], "fidelity_vs_closed_form": res["F_cf"],
             "compression_ratio_final": res["ratio_final"], "compression_ratio_min": res["ratio_min"],
             "hbm_frac": hbm_gbs / hbm_peak,
+            # every sweep reads and writes the whole logical state (16 B per amplitude each way)
+            "logical_gbs": 32.0 * 2.0 ** n * launches / sweep_s / 1e9 if sweep_s > 0 else None,
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
                          "traffic": traffic,
