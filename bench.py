@@ -51,7 +51,7 @@ def parse_args():
     ap.add_argument("--depth", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip bound sweep / AALC / e2e")
-    ap.add_argument("--workload", choices=["qft28", "serving", "grover"], default="qft28")
+    ap.add_argument("--workload", choices=["qft28", "serving", "grover", "aalc"], default="qft28")
     ap.add_argument("--grover-n", type=int, default=36, help="grover: qubits")
     ap.add_argument("--iterations", type=int, default=8, help="grover: Grover iterations")
     ap.add_argument("--requests", type=int, default=2000, help="serving: circuits")
@@ -399,6 +399,65 @@ def run_grover(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------------------ AALC threshold sweep
+def run_aalc(args):
+    """The 26-qubit QFT (the paper's size) under the error-bound ladder
+    {lossless, 1e-5, 1e-4, 1e-3, 1e-2} with thresholds 4, 8, 16, 32 and 64,
+    and under fixed bounds: fidelity against the uncompressed FP64 run,
+    minimum and final compression ratio, level histogram, gates/s."""
+    import torch
+
+    from paper_1811_05140_gb300 import build as B
+    from paper_1811_05140_gb300 import inputs as I
+    from paper_1811_05140_gb300 import qsim
+
+    B.build()
+    torch.cuda.set_device(0)
+    n = 26
+    x = I.seeded_basis(n, I.BASE_SEED)
+    gates = I.qft(n)
+    raw = 16.0 * 2.0 ** n
+    ref = qsim.State(n, 20, "none", 0.0)
+    ref.reset_basis(x)
+    ref.apply_all(gates)
+    ref.flush()
+    ladder = [1e-5, 1e-4, 1e-3, 1e-2]
+    rows = []
+
+    def one(label, make):
+        st = make()
+        st.reset_basis(x)
+        st.apply_all(gates)
+        st.flush()                                    # warm
+        st.reset_basis(x)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st.apply_all(gates)
+        st.flush()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        stats = st.stats()
+        rows.append({"setting": label, "fidelity_vs_fp64": st.fidelity_state(ref),
+                     "ratio_final": raw / st.compressed_bytes()[0],
+                     "ratio_min": raw / max(1, stats["max_stream_bytes_seen"]),
+                     "level_hist": stats["level_hist"][:len(ladder) + 1], "gates_per_s": len(gates) / dt})
+        st.close()
+
+    for theta in (4.0, 8.0, 16.0, 32.0, 64.0):
+        def make(theta=theta):
+            st = qsim.State(n, 20, "aalc", ladder[-1])
+            st.set_aalc(theta, ladder)
+            return st
+        one(f"aalc theta={theta:g}", make)
+    for eps in (1e-2, 1e-3, 1e-4):
+        one(f"fixed rel {eps:g}", lambda eps=eps: qsim.State(n, 20, "rel", eps))
+    ref.close()
+    print(json.dumps({"metric": "fidelity and compression ratio per threshold (QFT-26)", "unit": "table",
+                      "config": {"workload": "qft26_aalc_thresholds", "ladder": [0.0] + ladder,
+                                 "tile_log2": 8, "block_log2": 20},
+                      "rows": rows}))
+
+
 # ------------------------------------------------------------------ serving mix
 def serving_requests(count, nmin, nmax, seed):
     """The serving mix: 40% QFT on a random basis state, 30% Grover (2-6
@@ -555,6 +614,10 @@ def main():
     if args.workload == "grover":
         if rank == 0:
             run_grover(args)
+        return
+    if args.workload == "aalc":
+        if rank == 0:
+            run_aalc(args)
         return
     import torch
     if world > 1:
