@@ -142,10 +142,11 @@ def traffic_from_profile():
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_sample(n, eps, depth, xval, items_per_sweep, budget_s=None):
-    """Time the oracle (Algorithm 2 over tiles, plain C, 1 thread) on the
-    first `items_per_sweep` tile groups of every sweep of the QFT and
-    extrapolate to the whole circuit.  Returns (gates/s, seconds, desc)."""
+def oracle_sample(n, eps, depth, xval, items_per_sweep, seed=0):
+    """Time the oracle (Algorithm 2 over tiles, plain C, 1 thread) on a run
+    of `items_per_sweep` consecutive tile groups, at a seeded offset, of
+    every sweep of the QFT and extrapolate to the whole circuit by group
+    count.  Returns (gates/s, seconds, desc)."""
     import oracle
     from paper_1811_05140_gb300 import inputs as I
 
@@ -154,18 +155,26 @@ def oracle_sample(n, eps, depth, xval, items_per_sweep, budget_s=None):
     cs = oracle.CSim(n, c, [oracle.shift_for_eps(eps)], None, True)
     cs.reset_basis(xval)
     sweeps = oracle.partition(gates, n, c, 4, depth)
+    rng = I.Rng(I.BASE_SEED + 3 + seed)
     est_total, spent = 0.0, 0.0
     for lo, hi, H in sweeps:
         nitems = 1 << (n - c - len(H))
         k = min(items_per_sweep, nitems)
+        first = rng.below(nitems - k + 1)
         t0 = time.perf_counter()
-        cs.sweep_sample(gates[lo:hi], H, 0, k)
+        cs.sweep_sample(gates[lo:hi], H, first, first + k)
         dt = time.perf_counter() - t0
         spent += dt
         est_total += dt * nitems / k
-    desc = (f"oracle (plain C, 1 thread) on the first {items_per_sweep} tile groups of each of "
-            f"the {len(sweeps)} sweeps of the {n}-qubit QFT, extrapolated by group count")
+    desc = (f"oracle (plain C, 1 thread) on {items_per_sweep} consecutive tile groups at a seeded "
+            f"offset in each of the {len(sweeps)} sweeps of the {n}-qubit QFT, extrapolated by group count")
     return len(gates) / est_total, spent, desc
+
+
+def oracle_items_for(n, eps, depth, xval, target_s):
+    """Tile groups per sweep for about target_s seconds of oracle work."""
+    _, probe_s, _ = oracle_sample(n, eps, depth, xval, 4)
+    return max(4, min(4096, int(4 * target_s / max(probe_s, 1e-3))))
 
 
 # ------------------------------------------------------------------ ranks
@@ -579,8 +588,9 @@ def run_reference(args):
     xval = I.seeded_basis(args.n, I.BASE_SEED)
     vals = []
     desc = ""
+    items = oracle_items_for(args.n, args.eps, args.depth, xval, 8.0)     # about 8 s per step
     for i in range(args.warmup + args.steps):
-        v, spent, desc = oracle_sample(args.n, args.eps, args.depth, xval, 2)
+        v, spent, desc = oracle_sample(args.n, args.eps, args.depth, xval, items, seed=i)
         if i >= args.warmup:
             vals.append(v)
     v = statistics.median(vals)
@@ -641,8 +651,7 @@ def main():
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             # size the sample for about 12 s of CPU work
-            _, probe_s, _ = oracle_sample(n, args.eps, args.depth, res["xval"], 4)
-            items = max(4, min(4096, int(4 * 12.0 / max(probe_s, 1e-3))))
+            items = oracle_items_for(n, args.eps, args.depth, res["xval"], 12.0)
             v, spent, desc = oracle_sample(n, args.eps, args.depth, res["xval"], items)
             cpu = {"value": v, "unit": "gates/s", "cores": 1, "kind": "oracle", "sample": desc,
                    "seconds": round(spent, 2)}
