@@ -435,6 +435,25 @@ qsim_status qsim_server_stats(qsim_server_t s, qsim_server_stats_t *out);
 /* qsim_server_destroy -- finish the queued circuits, stop, release all. */
 qsim_status qsim_server_destroy(qsim_server_t s);
 
+/* Checkpoint / resume (the state saved before a job's wall time runs out
+ * and reloaded later).  qsim_save flushes the queued gates and writes
+ *   a 112-byte little-endian header: "QSIMCKP1", u32 version (1), n, c,
+ *   hmax, depth, codec, normalize, nlev, i32 shifts[8], f64 eps, theta,
+ *   u64 max_bytes, ntiles, stream bytes;
+ *   then, per chunk of up to 2^20 tiles in tile order, the u64 stream
+ *   sizes of the chunk followed by its streams (the tile stream format
+ *   above, so a host program can decode the file tile by tile).
+ * qsim_load creates a handle from such a file on the current device: the
+ * streams are validated and placed as by qsim_import_tiles, and the norm
+ * and normalize scale are recomputed from them, so continuing a circuit
+ * after save and load gives the same streams as continuing it without.
+ * Counters start from zero.  The caller owns the returned handle.
+ * Errors: QSIM_ERR_ARG (null argument, file not openable or not
+ * writable), QSIM_ERR_FORMAT (not a checkpoint, inconsistent header,
+ * truncated, a stream that does not decode), QSIM_ERR_OOM, QSIM_ERR_CUDA. */
+qsim_status qsim_save(qsim_t h, const char *path);
+qsim_status qsim_load(qsim_t *out, const char *path);
+
 /* qsim_version -- library version string. */
 const char *qsim_version(void);
 

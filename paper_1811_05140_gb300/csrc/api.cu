@@ -1482,6 +1482,137 @@ qsim_status qsim_import_tiles(qsim_t h, unsigned long long first, unsigned long 
     return read_scalars(h);
 }
 
+// ------------------------------------------------------------ checkpoints
+namespace {
+const char CKPT_MAGIC[8] = {'Q', 'S', 'I', 'M', 'C', 'K', 'P', '1'};
+constexpr unsigned long long CKPT_CHUNK = 1ull << 20;      // tiles per chunk
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version, n, c, hmax, depth, codec, normalize, nlev;
+    int32_t shifts[8];
+    double eps, theta;
+    unsigned long long max_bytes, ntiles, stream_bytes;
+};
+static_assert(sizeof(CkptHeader) == 112, "checkpoint header layout");
+
+struct FileCloser {
+    FILE *f;
+    ~FileCloser() { if (f) fclose(f); }
+};
+}  // namespace
+
+qsim_status qsim_save(qsim_t h, const char *path) {
+    qsim_status s = check_usable(h);
+    if (s != QSIM_OK) return s;
+    if (!path) return fail(h, QSIM_ERR_ARG, "null path");
+    if ((s = qsim_flush(h)) != QSIM_OK) return s;
+    FileCloser fc{fopen(path, "wb")};
+    if (!fc.f) return fail(h, QSIM_ERR_ARG, "cannot open %s for writing", path);
+    CkptHeader hd{};
+    std::memcpy(hd.magic, CKPT_MAGIC, 8);
+    hd.version = 1;
+    hd.n = (uint32_t)h->n;
+    hd.c = (uint32_t)h->c;
+    hd.hmax = (uint32_t)h->hmax;
+    hd.depth = (uint32_t)h->depth;
+    hd.codec = (uint32_t)h->codec;
+    hd.normalize = (uint32_t)h->normalize;
+    hd.nlev = (uint32_t)h->cc.nlev;
+    for (int i = 0; i < 8; ++i) hd.shifts[i] = h->cc.shifts[i];
+    hd.eps = h->eps;
+    hd.theta = h->theta;
+    hd.max_bytes = h->cc.max_bytes;
+    hd.ntiles = h->ntiles;
+    hd.stream_bytes = h->used;
+    if (fwrite(&hd, sizeof hd, 1, fc.f) != 1) return fail(h, QSIM_ERR_ARG, "write failed: %s", path);
+    std::vector<unsigned long long> sizes;
+    std::vector<uint8_t> buf;
+    for (unsigned long long first = 0; first < h->ntiles; first += CKPT_CHUNK) {
+        const unsigned long long cnt = std::min(CKPT_CHUNK, h->ntiles - first);
+        sizes.resize(cnt);
+        if ((s = qsim_export_tiles(h, first, cnt, nullptr, 0, sizes.data())) != QSIM_OK) return s;
+        unsigned long long tot = 0;
+        for (unsigned long long v : sizes) tot += v;
+        buf.resize(tot);
+        if ((s = qsim_export_tiles(h, first, cnt, buf.data(), tot, sizes.data())) != QSIM_OK) return s;
+        if (fwrite(sizes.data(), 8, cnt, fc.f) != cnt || fwrite(buf.data(), 1, tot, fc.f) != tot)
+            return fail(h, QSIM_ERR_ARG, "write failed: %s", path);
+    }
+    return QSIM_OK;
+}
+
+qsim_status qsim_load(qsim_t *out, const char *path) {
+    if (!out || !path) return fail(nullptr, QSIM_ERR_ARG, "null argument");
+    *out = nullptr;
+    FileCloser fc{fopen(path, "rb")};
+    if (!fc.f) return fail(nullptr, QSIM_ERR_ARG, "cannot open %s", path);
+    CkptHeader hd{};
+    if (fread(&hd, sizeof hd, 1, fc.f) != 1 || std::memcmp(hd.magic, CKPT_MAGIC, 8) != 0 || hd.version != 1)
+        return fail(nullptr, QSIM_ERR_FORMAT, "%s is not a checkpoint of this library", path);
+    if (hd.n < 1 || hd.n > (uint32_t)MAX_QUBITS || hd.c < 1 || hd.c > (uint32_t)qs::MAX_C || hd.c > hd.n ||
+        hd.codec > QSIM_CODEC_AALC || hd.nlev < 1 || hd.nlev > (uint32_t)qs::MAX_LEVELS ||
+        hd.ntiles != (1ull << (hd.n - hd.c)))
+        return fail(nullptr, QSIM_ERR_FORMAT, "%s: inconsistent checkpoint header", path);
+    for (uint32_t i = 0; i < hd.nlev; ++i)
+        if (hd.shifts[i] < 0 || hd.shifts[i] > 52) return fail(nullptr, QSIM_ERR_FORMAT, "%s: bad shift", path);
+    qsim_t h = nullptr;
+    qsim_status s = qsim_create(&h, (int)hd.n, (int)hd.c, (qsim_codec)hd.codec, hd.eps);
+    if (s != QSIM_OK) return s;
+    auto bail = [&](qsim_status code) { qsim_destroy(h); return code; };
+    if (hd.hmax < 1 || hd.hmax > (uint32_t)qs::MAX_PAIRS || hd.c + hd.hmax > (uint32_t)qs::MAX_ITEM_LOG2 ||
+        hd.depth < 1 || hd.depth > (uint32_t)qs::MAX_SWEEP_GATES) {
+        g_last_error = "checkpoint schedule out of range";
+        return bail(QSIM_ERR_FORMAT);
+    }
+    if (h->c != (int)hd.c) {                 // tiles of the saved size (the new state is still |0>)
+        free_tiles(h);
+        h->c = (int)hd.c;
+        h->cc.c = h->c;
+        h->used = 0;
+        if ((s = alloc_tiles(h)) != QSIM_OK || (s = encode_fresh(h, nullptr, 0)) != QSIM_OK) {
+            g_last_error = h->err;
+            return bail(s);
+        }
+    }
+    h->hmax = (int)hd.hmax;
+    h->depth = (int)hd.depth;
+    h->theta = hd.theta;
+    h->normalize = (int)hd.normalize;
+    h->cc.nlev = (int)hd.nlev;
+    for (int i = 0; i < qs::MAX_LEVELS; ++i) h->cc.shifts[i] = i < (int)hd.nlev ? hd.shifts[i] : 0;
+    h->cc.max_bytes = hd.max_bytes;
+    std::vector<unsigned long long> sizes;
+    std::vector<uint8_t> buf;
+    for (unsigned long long first = 0; first < h->ntiles; first += CKPT_CHUNK) {
+        const unsigned long long cnt = std::min(CKPT_CHUNK, h->ntiles - first);
+        sizes.resize(cnt);
+        if (fread(sizes.data(), 8, cnt, fc.f) != cnt) {
+            g_last_error = "truncated checkpoint";
+            return bail(QSIM_ERR_FORMAT);
+        }
+        unsigned long long tot = 0;
+        for (unsigned long long v : sizes) {
+            if (v > tile_bytes_worst(h)) { g_last_error = "bad stream size in checkpoint"; return bail(QSIM_ERR_FORMAT); }
+            tot += v;
+        }
+        buf.resize(tot);
+        if (fread(buf.data(), 1, tot, fc.f) != tot) {
+            g_last_error = "truncated checkpoint";
+            return bail(QSIM_ERR_FORMAT);
+        }
+        if ((s = qsim_import_tiles(h, first, cnt, buf.data(), sizes.data())) != QSIM_OK) {
+            g_last_error = h->err;
+            return bail(s);
+        }
+    }
+    h->st = qsim_stats_t{};
+    h->st.stream_bytes = h->used;
+    h->st.min_stream_bytes_seen = h->st.max_stream_bytes_seen = h->used;
+    *out = h;
+    return QSIM_OK;
+}
+
 int qsim_plan_sweeps(int n, int tile_log2, int hmax, int depth, int ngates, const int *ntargets,
                      const int *targets, const double *matrices, int *out_lo, int *out_h, int *out_H,
                      int cap) {

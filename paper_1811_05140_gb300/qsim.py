@@ -30,7 +30,8 @@ EXPORTS = ["qsim_create", "qsim_destroy", "qsim_set_stream", "qsim_set_aalc", "q
            "qsim_import_tiles", "qsim_plan_sweeps", "qsim_version", "qsim_set_profiling",
            "qsim_profile", "qsim_encode_noalloc", "qsim_flush_batch", "qsim_server_create",
            "qsim_server_submit", "qsim_server_result", "qsim_server_wait", "qsim_server_drain",
-           "qsim_server_stats", "qsim_server_destroy", "qsim_set_pool", "qsim_fp64_rate"]
+           "qsim_server_stats", "qsim_server_destroy", "qsim_set_pool", "qsim_fp64_rate",
+           "qsim_save", "qsim_load"]
 
 
 class QsimError(RuntimeError):
@@ -114,6 +115,8 @@ def load() -> C.CDLL:
         "qsim_set_schedule": ([vp, C.c_int, C.c_int, C.c_int], C.c_int),
         "qsim_set_pool": ([vp, vp, C.c_size_t], C.c_int),
         "qsim_fp64_rate": ([C.c_int, C.POINTER(C.c_double)], C.c_int),
+        "qsim_save": ([vp, C.c_char_p], C.c_int),
+        "qsim_load": ([C.POINTER(vp), C.c_char_p], C.c_int),
         "qsim_reset_basis": ([vp, u64], C.c_int),
         "qsim_set_amplitudes": ([vp, dp], C.c_int),
         "qsim_apply_gate": ([vp, dp, ip, C.c_int, ip, C.c_int, u64], C.c_int),
@@ -236,6 +239,27 @@ class State:
         self.codec = codec
         if stream is not None:
             self.set_stream(stream)
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "State":
+        """A state restored from a checkpoint written by save()."""
+        L = load()
+        h = C.c_void_p()
+        st = L.qsim_load(C.byref(h), os.fsencode(path))
+        if st != 0:
+            raise QsimError(st, L.qsim_last_error(None).decode())
+        self = cls.__new__(cls)
+        self._L = L
+        self.h = h
+        self.n = self.stats()["n_qubits"]
+        self.codec = None
+        if stream is not None:
+            self.set_stream(stream)
+        return self
+
+    def save(self, path: str):
+        """Write a checkpoint (header and every tile stream) to path."""
+        self._check(self._L.qsim_save(self.h, os.fsencode(path)))
 
     # -- plumbing
     def _check(self, status: int, h=-1):
