@@ -72,12 +72,17 @@ def lib():
         L.or_stream_cap.restype = C.c_size_t
         L.or_encode_tile.argtypes = [dp, C.c_int, ip, C.c_int, C.c_uint64, u8p, ip, ip]
         L.or_encode_tile.restype = C.c_size_t
+        L.or_encode_tile_level.argtypes = [dp, C.c_int, ip, C.c_int, u8p, ip]
+        L.or_encode_tile_level.restype = C.c_size_t
         L.or_decode_tile.argtypes = [u8p, C.c_size_t, C.c_int, dp]
         L.or_decode_tile.restype = C.c_int
         L.or_csim_new.argtypes = [C.c_int, C.c_int, ip, C.c_int, C.c_uint64, C.c_int]
         L.or_csim_new.restype = C.c_void_p
         L.or_csim_free.argtypes = [C.c_void_p]
         L.or_csim_reset_basis.argtypes = [C.c_void_p, C.c_uint64]
+        L.or_csim_set_unit.argtypes = [C.c_void_p, C.c_int, C.c_uint64]
+        L.or_csim_set_unit.restype = C.c_int
+        L.or_csim_set_dense.argtypes = [C.c_void_p, dp]
         L.or_csim_sweep.argtypes = [C.c_void_p, C.POINTER(OrGate), C.c_int, ip, C.c_int]
         L.or_csim_sweep.restype = C.c_int
         L.or_csim_sweep_sample.argtypes = [C.c_void_p, C.POINTER(OrGate), C.c_int, ip, C.c_int,
@@ -205,6 +210,17 @@ def encode_tile(amps: np.ndarray, c: int, shifts, max_bytes: int | None = None):
     return bytes(out[:n]), level.value, flags.value
 
 
+def encode_tile_level(amps: np.ndarray, c: int, shifts, k: int):
+    """Encode 2^c amplitudes at ladder level k, no size test; (bytes, flags)."""
+    a = np.ascontiguousarray(amps, dtype=np.complex128)
+    assert a.size == 1 << c and 0 <= k < len(shifts)
+    sh = (C.c_int * len(shifts))(*shifts)
+    out = (C.c_uint8 * lib().or_stream_cap(c))()
+    flags = C.c_int()
+    n = lib().or_encode_tile_level(_dptr(a.view(np.float64)), c, sh, k, out, C.byref(flags))
+    return bytes(out[:n]), flags.value
+
+
 def decode_tile(stream: bytes, c: int) -> np.ndarray:
     a = np.zeros(1 << c, dtype=np.complex128)
     buf = (C.c_uint8 * len(stream)).from_buffer_copy(stream)
@@ -269,6 +285,18 @@ class CSim:
 
     def reset_basis(self, x: int = 0):
         lib().or_csim_reset_basis(self.h, x)
+
+    def set_unit(self, unit_log2: int, theta: float) -> int:
+        """One ladder decision per stride of 2^unit_log2 amplitudes (the
+        stride Algorithm 2 decides on), ratio threshold theta; 0 = per tile.
+        Returns log2 of the tiles per decision."""
+        u = min(max(unit_log2, self.c), self.n)
+        return lib().or_csim_set_unit(self.h, unit_log2, max_bytes_for(u, theta))
+
+    def set_dense(self, amps: np.ndarray):
+        a = np.ascontiguousarray(amps, dtype=np.complex128)
+        assert a.size == 1 << self.n
+        lib().or_csim_set_dense(self.h, _dptr(a.view(np.float64)))
 
     def sweep(self, gates, H):
         H = sorted(H)

@@ -16,7 +16,9 @@
  *   O3  compressed simulator: Algorithm 2 (decompress, normalize, gate
  *       computation, compress with the error-bound ladder) over tiles, one
  *       sweep (a run of gates) at a time; a sweep whose gates only permute
- *       whole tiles moves their streams instead (sweep_moves_tiles).
+ *       whole tiles moves their streams instead (sweep_moves_tiles).  The
+ *       ladder's ratio test is made per tile, or once per stride of
+ *       several tiles as Algorithm 2 prints it (or_csim_set_unit).
  *   N   the state norm used by "normalize": the exact sum of |a|^2 in
  *       fixed point (units of 2^-112), rounded once to double.
  *
@@ -598,6 +600,35 @@ static size_t encode_at(const double *a, int c, int s, int level, uint8_t *out)
     return HDR + body;
 }
 
+/* Scan a tile: any non-finite component, and whether every component is
+ * zero or inside the lossy range (normal and below 2^1023). */
+static void scan_tile(const double *a, int c, int *nonfinite, int *eligible)
+{
+    uint64_t N = 1ull << c;
+    *nonfinite = 0;
+    *eligible = 1;
+    for (uint64_t i = 0; i < 2 * N; ++i) {
+        uint64_t B = dbits(a[i]) & MAG;
+        if (B >= INF_BITS) *nonfinite = 1;
+        else if (B != 0 && (B < MIN_NORMAL || B >= LOSSY_LIMIT)) *eligible = 0;
+    }
+}
+
+/* RAW stream of a tile holding a non-finite value (level 0; the caller
+ * reports the error). */
+static size_t encode_nonfinite(const double *a, int c, uint8_t *out)
+{
+    uint64_t N = 1ull << c;
+    size_t len = HDR + 16 * N;
+    memset(out, 0, len);
+    out[0] = M_RAW;
+    out[2] = 0;
+    put32(out + 4, (uint32_t)(16 * N));
+    out[24] = (uint8_t)c;
+    for (uint64_t i = 0; i < 2 * N; ++i) put64(out + HDR + 8 * i, dbits(a[i]));
+    return len;
+}
+
 /*
  * Encode one tile with the error-bound ladder of Algorithm 2: try the
  * levels in order (shifts[0..nlev-1], shifts[0] usually 0 = lossless) and
@@ -610,26 +641,13 @@ static size_t encode_at(const double *a, int c, int s, int level, uint8_t *out)
 size_t or_encode_tile(const double *a, int c, const int *shifts, int nlev,
                       uint64_t max_bytes, uint8_t *out, int *level, int *flags)
 {
-    uint64_t N = 1ull << c;
-    int nonfinite = 0, eligible = 1;
-    for (uint64_t i = 0; i < 2 * N; ++i) {
-        uint64_t B = dbits(a[i]) & MAG;
-        if (B >= INF_BITS) nonfinite = 1;
-        else if (B != 0 && (B < MIN_NORMAL || B >= LOSSY_LIMIT)) eligible = 0;
-    }
+    int nonfinite, eligible;
+    scan_tile(a, c, &nonfinite, &eligible);
     *flags = 0;
     if (nonfinite) {
-        /* RAW keeps the bits; the caller reports the error */
-        size_t len = HDR + 16 * N;
-        memset(out, 0, len);
-        out[0] = M_RAW;
-        out[2] = 0;
-        put32(out + 4, (uint32_t)(16 * N));
-        out[24] = (uint8_t)c;
-        for (uint64_t i = 0; i < 2 * N; ++i) put64(out + HDR + 8 * i, dbits(a[i]));
         *level = 0;
         *flags = OR_F_NONFINITE;
-        return len;
+        return encode_nonfinite(a, c, out);
     }
     if (!eligible) *flags |= OR_F_FORCED_LOSSLESS;
     size_t len = 0;
@@ -640,6 +658,26 @@ size_t or_encode_tile(const double *a, int c, const int *shifts, int nlev,
         if ((uint64_t)len <= max_bytes) break;
     }
     return len;
+}
+
+/*
+ * Encode one tile at ladder level k (shift shifts[k]) with no size test:
+ * the step Algorithm 2 takes for every tile of a stride once the stride's
+ * level is known.  Same forced-lossless and non-finite rules as
+ * or_encode_tile.
+ */
+size_t or_encode_tile_level(const double *a, int c, const int *shifts, int k,
+                            uint8_t *out, int *flags)
+{
+    int nonfinite, eligible;
+    scan_tile(a, c, &nonfinite, &eligible);
+    *flags = 0;
+    if (nonfinite) {
+        *flags = OR_F_NONFINITE;
+        return encode_nonfinite(a, c, out);
+    }
+    if (!eligible) *flags |= OR_F_FORCED_LOSSLESS;
+    return encode_at(a, c, eligible ? shifts[k] : 0, k, out);
 }
 
 /*
@@ -758,6 +796,8 @@ typedef struct {
     int n, c, nlev, normalize, err;
     int shifts[8];
     uint64_t max_bytes;
+    int ut;              /* log2 of the tiles one AALC decision covers (0: one tile) */
+    uint64_t umax;       /* the ratio threshold as a size limit of one such stride */
     uint64_t ntiles;
     uint8_t **st;
     uint32_t *len;
@@ -767,25 +807,63 @@ typedef struct {
     uint64_t items_done, items_skipped;
 } or_csim;
 
-static void csim_store(or_csim *cs, uint64_t t, const double *amps)
+/* Keep buf (len bytes, malloc'ed) as tile t's stream: count its ladder
+ * level and take the norm partial of what the next decode returns. */
+static void csim_put(or_csim *cs, uint64_t t, uint8_t *buf, size_t len)
 {
-    int c = cs->c, level = 0, flags = 0;
-    uint64_t N = 1ull << c;
-    uint8_t *buf = malloc(or_stream_cap(c));
-    size_t len = or_encode_tile(amps, c, cs->shifts, cs->nlev, cs->max_bytes,
-                                buf, &level, &flags);
-    if (flags & OR_F_NONFINITE) cs->err |= 1;
+    uint64_t N = 1ull << cs->c;
     free(cs->st[t]);
     cs->st[t] = realloc(buf, len);
     cs->len[t] = (uint32_t)len;
-    cs->hist[level] += 1;
-    /* the norm of what the next decode returns */
+    cs->hist[cs->st[t][2] & 7] += 1;
     double *rec = malloc(N * 16);
-    or_decode_tile(cs->st[t], len, c, rec);
+    or_decode_tile(cs->st[t], len, cs->c, rec);
     int range = 0;
     cs->part[t] = sum_sq(rec, 2 * N, &range);
     if (range) cs->err |= 2;
     free(rec);
+}
+
+static void csim_store(or_csim *cs, uint64_t t, const double *amps)
+{
+    int c = cs->c, level = 0, flags = 0;
+    uint8_t *buf = malloc(or_stream_cap(c));
+    size_t len = or_encode_tile(amps, c, cs->shifts, cs->nlev, cs->max_bytes,
+                                buf, &level, &flags);
+    if (flags & OR_F_NONFINITE) cs->err |= 1;
+    csim_put(cs, t, buf, len);
+}
+
+/*
+ * Algorithm 2's ratio test made once for a whole stride: the 2^ut tiles
+ * t0 .. t0 + 2^ut - 1 with amplitudes amps (2^(ut+c) complex values).
+ * Compress every tile of the stride at level k = 0, 1, ...; keep the first
+ * level at which the stride's streams together take at most umax bytes
+ * (stride ratio >= theta), else the last level.
+ */
+static void csim_store_unit(or_csim *cs, uint64_t t0, const double *amps)
+{
+    int c = cs->c;
+    uint64_t N = 1ull << c, nt = 1ull << cs->ut;
+    uint8_t **buf = malloc(nt * sizeof *buf);
+    size_t *len = malloc(nt * sizeof *len);
+    int nonfinite = 0;
+    for (uint64_t j = 0; j < nt; ++j) buf[j] = malloc(or_stream_cap(c));
+    for (int k = 0; k < cs->nlev; ++k) {
+        uint64_t total = 0;
+        nonfinite = 0;
+        for (uint64_t j = 0; j < nt; ++j) {
+            int flags = 0;
+            len[j] = or_encode_tile_level(amps + 2 * j * N, c, cs->shifts, k, buf[j], &flags);
+            if (flags & OR_F_NONFINITE) nonfinite = 1;
+            total += len[j];
+        }
+        if (total <= cs->umax) break;
+    }
+    if (nonfinite) cs->err |= 1;
+    for (uint64_t j = 0; j < nt; ++j) csim_put(cs, t0 + j, buf[j], len[j]);
+    free(buf);
+    free(len);
 }
 
 static void csim_update_alpha(or_csim *cs)
@@ -807,6 +885,8 @@ or_csim *or_csim_new(int n, int c, const int *shifts, int nlev,
     cs->nlev = nlev;
     for (int i = 0; i < nlev; ++i) cs->shifts[i] = shifts[i];
     cs->max_bytes = max_bytes;
+    cs->ut = 0;
+    cs->umax = max_bytes;
     cs->normalize = normalize;
     cs->ntiles = 1ull << (n - c);
     cs->st = calloc(cs->ntiles, sizeof(uint8_t *));
@@ -826,19 +906,50 @@ void or_csim_free(or_csim *cs)
     free(cs);
 }
 
-/* state |x>: every tile encoded from its dense values */
+/*
+ * Make one AALC decision per stride of 2^unit_log2 amplitudes (Algorithm 2
+ * decides per stride) instead of per tile, with umax the stride's size
+ * limit (floor(16 * 2^u / theta) for the stride of 2^u amplitudes).  A
+ * stride no larger than a tile, or a ladder of one level, means one
+ * decision per tile.  Strides are capped at the whole state.  Returns the
+ * log2 of the tiles per decision.
+ */
+int or_csim_set_unit(or_csim *cs, int unit_log2, uint64_t umax)
+{
+    int u = unit_log2 < cs->n ? unit_log2 : cs->n;
+    cs->ut = (u > cs->c && cs->nlev > 1) ? u - cs->c : 0;
+    cs->umax = cs->ut ? umax : cs->max_bytes;
+    return cs->ut;
+}
+
+/* state |x>: every tile (or stride) encoded from its dense values */
 void or_csim_reset_basis(or_csim *cs, uint64_t x)
 {
-    uint64_t N = 1ull << cs->c;
-    double *amps = calloc(N, 16);
-    for (uint64_t t = 0; t < cs->ntiles; ++t) {
-        memset(amps, 0, N * 16);
-        if ((x >> cs->c) == t) amps[2 * (x & (N - 1))] = 1.0;
-        csim_store(cs, t, amps);
+    uint64_t N = 1ull << cs->c, nt = 1ull << cs->ut;
+    double *amps = calloc(nt * N, 16);
+    for (uint64_t t = 0; t < cs->ntiles; t += nt) {
+        memset(amps, 0, nt * N * 16);
+        if ((x >> cs->c) >= t && (x >> cs->c) < t + nt) amps[2 * (x - (t << cs->c))] = 1.0;
+        if (cs->ut) csim_store_unit(cs, t, amps);
+        else csim_store(cs, t, amps);
     }
     free(amps);
     memset(cs->hist, 0, sizeof cs->hist);
     cs->err = 0;
+    csim_update_alpha(cs);
+}
+
+/* state given densely (2^n complex values, (re, im) interleaved), encoded
+ * tile by tile (or stride by stride) */
+void or_csim_set_dense(or_csim *cs, const double *amps)
+{
+    uint64_t N = 1ull << cs->c, nt = 1ull << cs->ut;
+    cs->err = 0;
+    for (uint64_t t = 0; t < cs->ntiles; t += nt) {
+        if (cs->ut) csim_store_unit(cs, t, amps + 2 * t * N);
+        else csim_store(cs, t, amps + 2 * t * N);
+    }
+    memset(cs->hist, 0, sizeof cs->hist);
     csim_update_alpha(cs);
 }
 
@@ -918,9 +1029,12 @@ static int item_moves(const or_gate *g, int ng, const int *H, int h, uint64_t fi
  * Per item (Algorithm 2): decompress its tiles, normalize (multiply by the
  * scale of the previous sweep when that scale is not 1), apply the gates in
  * order, compress every tile with the ladder.  An item that no gate
- * touches is kept as it is when the scale is 1.
+ * touches is kept as it is when the scale is 1.  With one decision per
+ * stride every item is computed and every stride compressed again
+ * (csim_sweep_units).
  * Returns 0, or -1 on a malformed stream, -2 on a gate that needs a
- * target outside the item.
+ * target outside the item, -4 for a sample of a sweep that decides per
+ * stride.
  */
 static int csim_sweep_items(or_csim *cs, const or_gate *g, int ng, const int *H, int h,
                             uint64_t item_lo, uint64_t item_hi, int update_alpha);
@@ -939,9 +1053,65 @@ int or_csim_sweep_sample(or_csim *cs, const or_gate *g, int ng, const int *H, in
     return csim_sweep_items(cs, g, ng, H, h, item_lo, item_hi, 0);
 }
 
+/*
+ * A sweep with one AALC decision per stride: every item is decompressed,
+ * normalized and computed, none kept and no stream moved, since Algorithm 2
+ * compresses every stride again; then each stride is compressed with its
+ * own decision (csim_store_unit).
+ */
+static int csim_sweep_units(or_csim *cs, const or_gate *g, int ng, const int *H, int h,
+                            int update_alpha)
+{
+    int c = cs->c, n = cs->n, mb = c + h;
+    uint64_t N = 1ull << c, nt = 1ull << cs->ut;
+    int qb[64];
+    for (int p = 0; p < c; ++p) qb[p] = p;
+    uint64_t hmask_tile = 0;
+    for (int i = 0; i < h; ++i) {
+        qb[c + i] = H[i];
+        hmask_tile |= 1ull << (H[i] - c);
+    }
+    double alpha = cs->alpha;
+    double *buf = malloc(((size_t)1 << mb) * 16);
+    double *state = malloc(((size_t)1 << n) * 16);
+    int rc = 0;
+    for (uint64_t T = 0; T < cs->ntiles && rc == 0; ++T) {
+        if (T & hmask_tile) continue;
+        cs->items_done++;
+        uint64_t fixed = T << c;
+        for (uint64_t j = 0; j < (1ull << h) && rc == 0; ++j) {
+            uint64_t Tj = T;
+            for (int i = 0; i < h; ++i)
+                if ((j >> i) & 1) Tj |= 1ull << (H[i] - c);
+            if (or_decode_tile(cs->st[Tj], cs->len[Tj], c, buf + 2 * j * N) != 0) rc = -1;
+        }
+        if (rc) break;
+        if (alpha != 1.0)
+            for (uint64_t i = 0; i < 2 * ((uint64_t)1 << mb); ++i) buf[i] = buf[i] * alpha;
+        for (int i = 0; i < ng && rc == 0; ++i)
+            if (apply_gate_buf(buf, mb, qb, fixed, &g[i]) != 0) rc = -2;
+        for (uint64_t j = 0; j < (1ull << h) && rc == 0; ++j) {
+            uint64_t Tj = T;
+            for (int i = 0; i < h; ++i)
+                if ((j >> i) & 1) Tj |= 1ull << (H[i] - c);
+            memcpy(state + 2 * Tj * N, buf + 2 * j * N, N * 16);
+        }
+    }
+    if (rc == 0)
+        for (uint64_t t = 0; t < cs->ntiles; t += nt) csim_store_unit(cs, t, state + 2 * t * N);
+    free(buf);
+    free(state);
+    if (rc == 0 && update_alpha) csim_update_alpha(cs);
+    return rc;
+}
+
 static int csim_sweep_items(or_csim *cs, const or_gate *g, int ng, const int *H, int h,
                             uint64_t item_lo, uint64_t item_hi, int update_alpha)
 {
+    if (cs->ut) {                        /* strides decide as a whole: no samples */
+        if (item_lo != 0 || item_hi != UINT64_MAX) return -4;
+        return csim_sweep_units(cs, g, ng, H, h, update_alpha);
+    }
     int c = cs->c, n = cs->n, mb = c + h;
     uint64_t N = 1ull << c;
     int qb[64];
