@@ -411,8 +411,9 @@ def run_grover(args):
 # ------------------------------------------------------------------ AALC threshold sweep
 def run_aalc(args):
     """The 26-qubit QFT (the paper's size) under the error-bound ladder
-    {lossless, 1e-5, 1e-4, 1e-3, 1e-2} with thresholds 4, 8, 16, 32 and 64,
-    and under fixed bounds: fidelity against the uncompressed FP64 run,
+    {lossless, 1e-5, 1e-4, 1e-3, 1e-2} with thresholds 4, 8, 16, 32 and 64
+    decided per tile, with thresholds 4, 8, 16 and 32 decided per stride of
+    2^20 amplitudes (Algorithm 2), and under fixed bounds: fidelity against the uncompressed FP64 run,
     minimum and final compression ratio, level histogram, gates/s."""
     import torch
 
@@ -458,6 +459,13 @@ def run_aalc(args):
             st.set_aalc(theta, ladder)
             return st
         one(f"aalc theta={theta:g}", make)
+    for theta in (4.0, 8.0, 16.0, 32.0):
+        def make(theta=theta):                        # Algorithm 2's decision per stride of 2^20
+            st = qsim.State(n, 20, "aalc", ladder[-1])
+            st.set_aalc(theta, ladder)
+            st.set_aalc_unit(20)
+            return st
+        one(f"aalc per stride theta={theta:g}", make)
     for eps in (1e-2, 1e-3, 1e-4):
         one(f"fixed rel {eps:g}", lambda eps=eps: qsim.State(n, 20, "rel", eps))
     ref.close()

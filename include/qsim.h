@@ -119,6 +119,24 @@ qsim_status qsim_set_stream(qsim_t h, void *cuda_stream);
 qsim_status qsim_set_aalc(qsim_t h, double theta, const double *eps_levels, int n_levels);
 
 /*
+ * qsim_set_aalc_unit -- how many amplitudes one ladder decision covers:
+ * unit_log2 = 0 (the default) decides per tile as above; unit_log2 = the
+ * handle's block_log2 decides once per stride as Algorithm 2 does: every
+ * tile of a stride of 2^u amplitudes, u = min(max(unit_log2, tile_log2),
+ * n), is stored at the stride's first level whose ratio
+ * 16*2^u / (the stride's stream bytes) is >= theta, else at the last.
+ * A sweep then computes and re-encodes every item (no tile is kept or
+ * moved as a stream) in two passes: one that sizes every tile at every
+ * level, one that encodes.  Has an effect only with a ladder of two or
+ * more levels and strides larger than a tile; the current state keeps its
+ * streams until the next encode (reset, set_amplitudes or sweep).  Such
+ * handles are flushed by qsim_flush only (qsim_flush_batch returns
+ * QSIM_ERR_ARG).  Flushes queued gates first.  Errors: QSIM_ERR_ARG
+ * (unit_log2 outside 0..40).
+ */
+qsim_status qsim_set_aalc_unit(qsim_t h, int unit_log2);
+
+/*
  * qsim_set_normalize -- switch Algorithm 2's normalize step (on = 1) for
  * REL/AALC handles.  Flushes first.
  */
@@ -180,7 +198,8 @@ qsim_status qsim_flush(qsim_t h);
  * pending sweep of every handle that has one, all rounds as one persistent
  * launch each (plus one small finalize launch) on the first handle's stream,
  * optionally captured into a CUDA graph (use_graph = 1).  Each handle's
- * result is byte-identical to its own qsim_flush.  A handle whose output
+ * result is byte-identical to its own qsim_flush.  Handles that decide
+ * per stride (qsim_set_aalc_unit) are refused with QSIM_ERR_ARG.  A handle whose output
  * arena overflows is grown and finished alone afterwards.  The handles must
  * be distinct and on one device.  Returns the first handle error (each
  * handle keeps its own qsim_last_error).
@@ -437,9 +456,9 @@ qsim_status qsim_server_destroy(qsim_server_t s);
 
 /* Checkpoint / resume (the state saved before a job's wall time runs out
  * and reloaded later).  qsim_save flushes the queued gates and writes
- *   a 112-byte little-endian header: "QSIMCKP1", u32 version (1), n, c,
+ *   a 120-byte little-endian header: "QSIMCKP1", u32 version (2), n, c,
  *   hmax, depth, codec, normalize, nlev, i32 shifts[8], f64 eps, theta,
- *   u64 max_bytes, ntiles, stream bytes;
+ *   u64 max_bytes, ntiles, stream bytes, i32 unit_log2, i32 reserved (0);
  *   then, per chunk of up to 2^20 tiles in tile order, the u64 stream
  *   sizes of the chunk followed by its streams (the tile stream format
  *   above, so a host program can decode the file tile by tile).

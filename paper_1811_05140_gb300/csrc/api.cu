@@ -20,13 +20,18 @@ void set_global_error(const char *msg);
 size_t sweep_smem_bytes(int mb);
 cudaError_t launch_sweep(const SweepParams *plist, const unsigned long long *istart, int nlist,
                          int mb, int grid, cudaStream_t st);
+cudaError_t launch_sweep_sizing(const SweepParams *plist, const unsigned long long *istart, int nlist,
+                                int mb, int grid, cudaStream_t st);
 cudaError_t launch_finalize_list(const FinalizeEntry *list, int n, cudaStream_t st);
 cudaError_t launch_finalize(DevScalars *scal, int use_alpha, unsigned long long *used_hist,
                             unsigned slot, int record_used, cudaStream_t st);
 cudaError_t launch_init(const double2 *dense, unsigned long long x, const CodecCfg &cc,
                         unsigned long long ntiles, uint8_t *arena, unsigned long long cap,
                         unsigned long long *table, unsigned long long *part, DevScalars *scal,
+                        unsigned long long *unit_bytes, const uint8_t *unit_level, int unit_shift,
                         int grid, cudaStream_t st);
+cudaError_t launch_unit_level(const unsigned long long *bytes, uint8_t *level, unsigned long long nunits,
+                              int nlev, unsigned long long limit, cudaStream_t st);
 cudaError_t launch_norm_from_parts(const unsigned long long *part, unsigned long long ntiles,
                                    DevScalars *scal, int grid, cudaStream_t st);
 cudaError_t launch_sizes(const uint8_t *arena, const unsigned long long *table,
@@ -292,6 +297,10 @@ struct qsim_state {
     std::string err;
     bool invalid = false;
     bool pool = false;                    // arenas live in a caller-owned buffer
+    int unit_log2 = 0;                    // amplitudes per ladder decision (log2); 0 = one tile
+    unsigned long long *unit_bytes = nullptr;   // per stride and level: stream bytes
+    uint8_t *unit_level = nullptr;        // per stride: chosen level
+    unsigned long long units_cap = 0;
 };
 
 namespace {
@@ -344,6 +353,35 @@ qsim_status ensure_arena(qsim_t h, int which, unsigned long long need) {
     return QSIM_OK;
 }
 
+// log2 of the tiles one ladder decision covers: 0 (per tile) unless a
+// stride of more than one tile was set and the ladder has several levels.
+int unit_tiles_log2(const qsim_state *h) {
+    if (h->unit_log2 <= 0 || h->cc.nlev < 2 || h->cc.force_raw) return 0;
+    const int u = std::min(h->unit_log2, h->n);
+    return u > h->c ? u - h->c : 0;
+}
+
+// A stride's stream size limit: ratio 16 * 2^u / size >= theta.
+unsigned long long unit_limit(const qsim_state *h) {
+    const int u = h->c + unit_tiles_log2(h);
+    return (unsigned long long)std::floor(16.0 * std::ldexp(1.0, u) / h->theta);
+}
+
+// Per-stride counters for the current tiling, grown on demand.
+qsim_status ensure_units(qsim_t h, unsigned long long nunits) {
+    if (h->units_cap >= nunits) return QSIM_OK;
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->unit_bytes) cudaFree(h->unit_bytes);
+    if (h->unit_level) cudaFree(h->unit_level);
+    h->unit_bytes = nullptr;
+    h->unit_level = nullptr;
+    h->units_cap = 0;
+    CK(cudaMalloc(&h->unit_bytes, nunits * qs::MAX_LEVELS * sizeof(unsigned long long)));
+    CK(cudaMalloc(&h->unit_level, nunits));
+    h->units_cap = nunits;
+    return QSIM_OK;
+}
+
 qsim_status read_scalars(qsim_t h) {
     CK(cudaMemcpyAsync(h->hscal, h->scal, sizeof(qs::DevScalars), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -382,8 +420,19 @@ qsim_status encode_fresh(qsim_t h, const double2 *dense, unsigned long long x) {
             return s;
         }
         CK(cudaMemsetAsync(h->scal, 0, sizeof(qs::DevScalars), h->stream));
+        const int ut = unit_tiles_log2(h);
+        if (ut) {                         // one ladder decision per stride: size, decide, encode
+            const unsigned long long nunits = h->ntiles >> ut;
+            if ((s = ensure_units(h, nunits)) != QSIM_OK) return s;
+            CK(cudaMemsetAsync(h->unit_bytes, 0, nunits * qs::MAX_LEVELS * sizeof(unsigned long long), h->stream));
+            ++h->launches; CK(qs::launch_init(dense, x, h->cc, h->ntiles, nullptr, 0, nullptr, nullptr, h->scal,
+                               h->unit_bytes, nullptr, ut, grid_for(h, h->ntiles, 4), h->stream));
+            ++h->launches; CK(qs::launch_unit_level(h->unit_bytes, h->unit_level, nunits, h->cc.nlev,
+                                                    unit_limit(h), h->stream));
+        }
         ++h->launches; CK(qs::launch_init(dense, x, h->cc, h->ntiles, h->arena[h->cur], h->cap[h->cur],
-                           h->table[h->cur], h->part, h->scal, grid_for(h, h->ntiles, 4), h->stream));
+                           h->table[h->cur], h->part, h->scal, nullptr, ut ? h->unit_level : nullptr, ut,
+                           grid_for(h, h->ntiles, 4), h->stream));
         ++h->launches; CK(qs::launch_finalize(h->scal, h->normalize, nullptr, 0, 1, h->stream));
         if ((s = read_scalars(h)) != QSIM_OK) return s;
         if (h->hscal->err & qs::ERR_OVERFLOW) {
@@ -599,6 +648,8 @@ qsim_status qsim_destroy(qsim_t h) {
     if (h->histart) cudaFreeHost(h->histart);
     if (h->used_hist) cudaFree(h->used_hist);
     if (h->hused) cudaFreeHost(h->hused);
+    if (h->unit_bytes) cudaFree(h->unit_bytes);
+    if (h->unit_level) cudaFree(h->unit_level);
     for (cudaEvent_t ev : h->events) cudaEventDestroy(ev);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
@@ -804,8 +855,8 @@ qsim_status stage_flush(qsim_t h, FlushCtx &fc, cudaStream_t st) {
         h->dparams = h->hparams = nullptr;
         h->distart = h->histart = nullptr;
         h->params_cap = 0;
-        CK(cudaMalloc(&h->dparams, ns * sizeof(qs::SweepParams)));
-        CK(cudaMallocHost(&h->hparams, ns * sizeof(qs::SweepParams)));
+        CK(cudaMalloc(&h->dparams, 2 * ns * sizeof(qs::SweepParams)));    // encode, sizing
+        CK(cudaMallocHost(&h->hparams, 2 * ns * sizeof(qs::SweepParams)));
         CK(cudaMalloc(&h->distart, 2 * ns * sizeof(unsigned long long)));
         CK(cudaMallocHost(&h->histart, 2 * ns * sizeof(unsigned long long)));
         h->params_cap = ns;
@@ -867,6 +918,13 @@ qs::SweepParams sweep_params(qsim_t h, const FlushCtx &fc, size_t j) {
         if (!is_permutation(g)) p.moves_tiles = 0;
     }
     p.moves_tiles &= p.low_free;
+    if (const int ut = unit_tiles_log2(h)) {
+        // every stride is decided and re-encoded as a whole
+        p.every_item = 1;
+        p.moves_tiles = 0;
+        p.unit_shift = ut;
+        p.unit_level = h->unit_level;
+    }
     return p;
 }
 
@@ -875,20 +933,41 @@ qs::SweepParams sweep_params(qsim_t h, const FlushCtx &fc, size_t j) {
 qsim_status run_from(qsim_t h, FlushCtx &fc, size_t k) {
     qsim_status s;
     const size_t ns = fc.ns;
+    const int ut = unit_tiles_log2(h);
+    const unsigned long long nunits = h->ntiles >> ut;
+    if (ut && (s = ensure_units(h, nunits)) != QSIM_OK) return s;
     while (k < ns) {
         for (size_t j = k; j < ns; ++j) {
             h->hparams[j] = sweep_params(h, fc, j);
             h->histart[2 * j] = 0;
             h->histart[2 * j + 1] = h->hparams[j].nitems;
+            if (ut) {                     // the sizing pass: same sweep, counts only
+                h->hparams[ns + j] = h->hparams[j];
+                h->hparams[ns + j].unit_level = nullptr;
+                h->hparams[ns + j].unit_bytes = h->unit_bytes;
+            }
         }
         CK(cudaMemcpyAsync(h->dparams + k, h->hparams + k, (ns - k) * sizeof(qs::SweepParams),
                            cudaMemcpyHostToDevice, h->stream));
+        if (ut)
+            CK(cudaMemcpyAsync(h->dparams + ns + k, h->hparams + ns + k, (ns - k) * sizeof(qs::SweepParams),
+                               cudaMemcpyHostToDevice, h->stream));
         CK(cudaMemcpyAsync(h->distart + 2 * k, h->histart + 2 * k, 2 * (ns - k) * sizeof(unsigned long long),
                            cudaMemcpyHostToDevice, h->stream));
         for (size_t j = k; j < ns; ++j) {
             const int mb = h->c + fc.sweeps[j].h;
             const int per_sm = qs::sweep_blocks_per_sm(mb);
             if (h->profiling) CK(cudaEventRecord(h->events[2 * j], h->stream));
+            if (ut) {                     // Algorithm 2's ratio test once per stride
+                CK(cudaMemsetAsync(h->unit_bytes, 0, nunits * qs::MAX_LEVELS * sizeof(unsigned long long),
+                                   h->stream));
+                ++h->launches;
+                CK(qs::launch_sweep_sizing(h->dparams + ns + j, h->distart + 2 * j, 1, mb,
+                                           grid_for(h, h->hparams[j].nitems, per_sm), h->stream));
+                ++h->launches;
+                CK(qs::launch_unit_level(h->unit_bytes, h->unit_level, nunits, h->cc.nlev, unit_limit(h),
+                                         h->stream));
+            }
             ++h->launches;
             CK(qs::launch_sweep(h->dparams + j, h->distart + 2 * j, 1, mb,
                                 grid_for(h, h->hparams[j].nitems, per_sm), h->stream));
@@ -982,6 +1061,8 @@ qsim_status qsim_flush_batch(qsim_t *handles, int count, int use_graph) {
             if (handles[j] == handles[i]) return fail(nullptr, QSIM_ERR_ARG, "qsim_flush_batch: repeated handle");
         qsim_status s = check_usable(handles[i]);
         if (s != QSIM_OK) return s;
+        if (unit_tiles_log2(handles[i]))
+            return fail(handles[i], QSIM_ERR_ARG, "qsim_flush_batch: per-stride ladder decisions run through qsim_flush");
         if (handles[i]->device != handles[0]->device)
             return fail(nullptr, QSIM_ERR_ARG, "qsim_flush_batch: handles on different devices");
     }
@@ -1141,6 +1222,15 @@ qsim_status qsim_set_aalc(qsim_t h, double theta, const double *eps_levels, int 
     h->cc.shifts[0] = 0;
     for (int i = 0; i < n_levels; ++i) h->cc.shifts[1 + i] = shift_for_eps(eps_levels[i]);
     h->cc.max_bytes = (unsigned long long)std::floor(16.0 * (double)(1ull << h->c) / theta);
+    return QSIM_OK;
+}
+
+qsim_status qsim_set_aalc_unit(qsim_t h, int unit_log2) {
+    qsim_status s = check_usable(h);
+    if (s != QSIM_OK) return s;
+    if (unit_log2 < 0 || unit_log2 > MAX_QUBITS) return fail(h, QSIM_ERR_ARG, "unit_log2 must be 0..%d", MAX_QUBITS);
+    if ((s = qsim_flush(h)) != QSIM_OK) return s;     // queued gates run under the old rule
+    h->unit_log2 = unit_log2;
     return QSIM_OK;
 }
 
@@ -1493,8 +1583,9 @@ struct CkptHeader {
     int32_t shifts[8];
     double eps, theta;
     unsigned long long max_bytes, ntiles, stream_bytes;
+    int32_t unit_log2, reserved;
 };
-static_assert(sizeof(CkptHeader) == 112, "checkpoint header layout");
+static_assert(sizeof(CkptHeader) == 120, "checkpoint header layout");
 
 struct FileCloser {
     FILE *f;
@@ -1511,7 +1602,7 @@ qsim_status qsim_save(qsim_t h, const char *path) {
     if (!fc.f) return fail(h, QSIM_ERR_ARG, "cannot open %s for writing", path);
     CkptHeader hd{};
     std::memcpy(hd.magic, CKPT_MAGIC, 8);
-    hd.version = 1;
+    hd.version = 2;
     hd.n = (uint32_t)h->n;
     hd.c = (uint32_t)h->c;
     hd.hmax = (uint32_t)h->hmax;
@@ -1525,6 +1616,7 @@ qsim_status qsim_save(qsim_t h, const char *path) {
     hd.max_bytes = h->cc.max_bytes;
     hd.ntiles = h->ntiles;
     hd.stream_bytes = h->used;
+    hd.unit_log2 = h->unit_log2;
     if (fwrite(&hd, sizeof hd, 1, fc.f) != 1) return fail(h, QSIM_ERR_ARG, "write failed: %s", path);
     std::vector<unsigned long long> sizes;
     std::vector<uint8_t> buf;
@@ -1548,11 +1640,11 @@ qsim_status qsim_load(qsim_t *out, const char *path) {
     FileCloser fc{fopen(path, "rb")};
     if (!fc.f) return fail(nullptr, QSIM_ERR_ARG, "cannot open %s", path);
     CkptHeader hd{};
-    if (fread(&hd, sizeof hd, 1, fc.f) != 1 || std::memcmp(hd.magic, CKPT_MAGIC, 8) != 0 || hd.version != 1)
+    if (fread(&hd, sizeof hd, 1, fc.f) != 1 || std::memcmp(hd.magic, CKPT_MAGIC, 8) != 0 || hd.version != 2)
         return fail(nullptr, QSIM_ERR_FORMAT, "%s is not a checkpoint of this library", path);
     if (hd.n < 1 || hd.n > (uint32_t)MAX_QUBITS || hd.c < 1 || hd.c > (uint32_t)qs::MAX_C || hd.c > hd.n ||
         hd.codec > QSIM_CODEC_AALC || hd.nlev < 1 || hd.nlev > (uint32_t)qs::MAX_LEVELS ||
-        hd.ntiles != (1ull << (hd.n - hd.c)))
+        hd.ntiles != (1ull << (hd.n - hd.c)) || hd.unit_log2 < 0 || hd.unit_log2 > MAX_QUBITS)
         return fail(nullptr, QSIM_ERR_FORMAT, "%s: inconsistent checkpoint header", path);
     for (uint32_t i = 0; i < hd.nlev; ++i)
         if (hd.shifts[i] < 0 || hd.shifts[i] > 52) return fail(nullptr, QSIM_ERR_FORMAT, "%s: bad shift", path);
@@ -1582,6 +1674,7 @@ qsim_status qsim_load(qsim_t *out, const char *path) {
     h->cc.nlev = (int)hd.nlev;
     for (int i = 0; i < qs::MAX_LEVELS; ++i) h->cc.shifts[i] = i < (int)hd.nlev ? hd.shifts[i] : 0;
     h->cc.max_bytes = hd.max_bytes;
+    h->unit_log2 = hd.unit_log2;
     std::vector<unsigned long long> sizes;
     std::vector<uint8_t> buf;
     for (unsigned long long first = 0; first < h->ntiles; first += CKPT_CHUNK) {

@@ -979,8 +979,88 @@ __device__ void pack_onepass(double *re, double *im, int s, int G, LevelSizes &l
     }
 }
 
+// Section sizes and modes of a tile sized by size_levels (warp-uniform):
+// zero words, sign words of every value (lossless) and of the nonzero
+// values (lossy), width bytes, nonzero counts per group (lane g).
+struct Sections {
+    uint32_t zb0, zb1, sbl0, sbl1, sby0, sby1, wb, nn0, nn1;
+    int zm0, zm1, sml0, sml1, smy0, smy1;
+};
+
+__device__ __forceinline__ void sections_of(const LevelSizes &ls, int G, uint32_t lanes, Sections &q) {
+    const int lane = threadIdx.x & 31;
+    q.zm0 = section_mode(ls.zw0, G, lanes, q.zb0);
+    q.zm1 = section_mode(ls.zw1, G, lanes, q.zb1);
+    q.sml0 = section_mode(ls.sw0, G, lanes, q.sbl0);
+    q.sml1 = section_mode(ls.sw1, G, lanes, q.sbl1);
+    q.smy0 = section_mode(ls.sw0 & ~ls.zw0, G, lanes, q.sby0);
+    q.smy1 = section_mode(ls.sw1 & ~ls.zw1, G, lanes, q.sby1);
+    q.wb = (2u * G + 3u) & ~3u;
+    q.nn0 = lane < G ? (uint32_t)__popc(~ls.zw0 & lanes) : 0u;
+    q.nn1 = lane < G ? (uint32_t)__popc(~ls.zw1 & lanes) : 0u;
+}
+
+// Mode and body bytes of the tile's stream at ladder level lv coded with
+// shift slv (0 when the tile holds values outside the lossy range); s0, s1
+// its sign modes.  Warp-wide: lv and slv are warp-uniform.
+__device__ __forceinline__ uint32_t level_body(const LevelSizes &ls, const Sections &q, int lv, int slv,
+                                               uint32_t raw_body, int &mode, int &s0, int &s1) {
+    s0 = slv ? q.smy0 : q.sml0;
+    s1 = slv ? q.smy1 : q.sml1;
+    const uint32_t meta = (slv ? q.sby0 + q.sby1 : q.sbl0 + q.sbl1) + q.zb0 + q.zb1;
+    if (!((ls.nz >> lv) & 1u) && s0 <= S_SET && s1 <= S_SET && q.zm0 <= S_SET && q.zm1 <= S_SET) {
+        mode = M_CONST;
+        return 0u;
+    }
+    const uint32_t w0 = (uint32_t)(ls.wl0 >> (8 * lv)) & 0xFFu, w1 = (uint32_t)(ls.wl1 >> (8 * lv)) & 0xFFu;
+    const uint32_t words = __reduce_add_sync(FULL, ((q.nn0 * w0 + 31u) >> 5) + ((q.nn1 * w1 + 31u) >> 5));
+    const uint32_t pb = (meta + q.wb + 4u * words + 15u) & ~15u;
+    if (pb < raw_body) {
+        mode = M_PACKED;
+        return pb;
+    }
+    mode = M_RAW;
+    return raw_body;
+}
+
+// Sizing pass of a per-stride ladder decision: the tile's stream size at
+// every level, added to its stride's counts bytes[0 .. nlev-1].  Writes
+// nothing else.  Warp-wide.
+__device__ __noinline__ void wsize(const double *re, const double *im, const CodecCfg &cc,
+                                   unsigned long long *bytes) {
+    const int c = cc.c, N = 1 << c;
+    const int G = N >= 32 ? N >> 5 : 1;
+    const int L = N >= 32 ? 32 : N;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lanes = L == 32 ? FULL : ((1u << L) - 1u);
+    const uint32_t raw_body = 16u * (uint32_t)N;
+    LevelSizes ls;
+    int nonfin = 0, inel = 0;
+    if (!cc.force_raw) {
+        size_levels(re, im, cc, G, L, false, ls, nonfin, inel);
+        nonfin = __any_sync(FULL, nonfin);
+        inel = __any_sync(FULL, inel);
+        if (inel && !nonfin) {
+            int d0 = 0, d1 = 0;
+            size_levels(re, im, cc, G, L, true, ls, d0, d1);
+        }
+    }
+    const bool raw_only = cc.force_raw || nonfin;
+    Sections q;
+    if (!raw_only) sections_of(ls, G, lanes, q);
+    for (int lv = 0; lv < cc.nlev; ++lv) {
+        uint32_t body = raw_body;
+        if (!raw_only) {
+            int mode, s0, s1;
+            body = level_body(ls, q, lv, inel ? 0 : cc.shifts[lv], raw_body, mode, s0, s1);
+        }
+        if (lane == 0) atomicAdd(bytes + lv, (unsigned long long)(HDR + body));
+    }
+}
+
 // Encode planar re/im (2^c values each) of tile `tile` into the output
-// arena with Algorithm 2's ladder (every level sized in one pass).
+// arena with Algorithm 2's ladder (every level sized in one pass), or at
+// ladder level force_lv when it is >= 0 (the level of the tile's stride).
 // Warp-wide.  Writes the stream, its table entry and norm partial, and adds
 // to the running norm.  wstage: 64 words of shared memory of this warp.
 // With one lossy level at shift >= 32 the tile is coded in one pass and
@@ -988,7 +1068,7 @@ __device__ void pack_onepass(double *re, double *im, int s, int G, LevelSizes &l
 __device__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc,
                              unsigned long long tile, uint8_t *out_arena, unsigned long long out_cap,
                              unsigned long long *out_table, unsigned long long *part,
-                             DevScalars *scal, unsigned sweep_id, uint32_t *wstage) {
+                             DevScalars *scal, unsigned sweep_id, uint32_t *wstage, int force_lv) {
     const int c = cc.c, N = 1 << c;
     const int G = N >= 32 ? N >> 5 : 1;
     const int L = N >= 32 ? 32 : N;
@@ -1033,38 +1113,19 @@ __device__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc,
         mode = M_RAW;
         bodyb = raw_body;
     } else {
-        uint32_t zb0, zb1, sbl0, sbl1, sby0, sby1;
-        zm[0] = section_mode(ls.zw0, G, lanes, zb0);
-        zm[1] = section_mode(ls.zw1, G, lanes, zb1);
-        const int sml0 = section_mode(ls.sw0, G, lanes, sbl0);
-        const int sml1 = section_mode(ls.sw1, G, lanes, sbl1);
-        const int smy0 = section_mode(ls.sw0 & ~ls.zw0, G, lanes, sby0);
-        const int smy1 = section_mode(ls.sw1 & ~ls.zw1, G, lanes, sby1);
-        const uint32_t wb = (2u * G + 3u) & ~3u;
-        const uint32_t nn0 = lane < G ? (uint32_t)__popc(~ls.zw0 & lanes) : 0u;
-        const uint32_t nn1 = lane < G ? (uint32_t)__popc(~ls.zw1 & lanes) : 0u;
+        Sections q;
+        sections_of(ls, G, lanes, q);
+        zm[0] = q.zm0;
+        zm[1] = q.zm1;
         mode = M_RAW;
         bodyb = raw_body;
         bool found = false;                  // first level within the size limit, else the last
 #pragma unroll
         for (int lv = 0; lv < MAX_LEVELS; ++lv) {
-            if (lv >= cc.nlev || found) continue;
-            const int slv = inel ? 0 : cc.shifts[lv];
-            const int s0 = slv ? smy0 : sml0, s1 = slv ? smy1 : sml1;
-            const uint32_t meta = (slv ? sby0 + sby1 : sbl0 + sbl1) + zb0 + zb1;
-            if (!((ls.nz >> lv) & 1u) && s0 <= S_SET && s1 <= S_SET && zm[0] <= S_SET && zm[1] <= S_SET) {
-                mode = M_CONST; bodyb = 0;
-            } else {
-                const uint32_t w0 = (uint32_t)(ls.wl0 >> (8 * lv)) & 0xFFu, w1 = (uint32_t)(ls.wl1 >> (8 * lv)) & 0xFFu;
-                const uint32_t words = __reduce_add_sync(FULL, ((nn0 * w0 + 31u) >> 5) + ((nn1 * w1 + 31u) >> 5));
-                const uint32_t pb = (meta + wb + 4u * words + 15u) & ~15u;
-                if (pb < raw_body) { mode = M_PACKED; bodyb = pb; }
-                else { mode = M_RAW; bodyb = raw_body; }
-            }
+            if (lv >= cc.nlev || found || (force_lv >= 0 && lv != force_lv)) continue;
+            bodyb = level_body(ls, q, lv, inel ? 0 : cc.shifts[lv], raw_body, mode, sm[0], sm[1]);
             level = lv;
-            sm[0] = s0;
-            sm[1] = s1;
-            found = (unsigned long long)(HDR + bodyb) <= cc.max_bytes;
+            found = force_lv >= 0 || (unsigned long long)(HDR + bodyb) <= cc.max_bytes;
         }
         s = mode == M_RAW ? 0 : (inel ? 0 : cc.shifts[level]);
     }
@@ -1307,15 +1368,26 @@ __device__ __forceinline__ bool const_value(const uint8_t *src, int c, double al
     return true;
 }
 
+// Fill a tile with its first amplitude (a uniform tile held as one value).
+// Warp-wide.
+__device__ __forceinline__ void fill_uniform(double *re, double *im, int N) {
+    const int lane = threadIdx.x & 31;
+    const double vr = re[0], vi = im[0];
+    __syncwarp();
+    for (int i = lane; i < N; i += 32) { re[i] = vr; im[i] = vi; }
+    __syncwarp();
+}
+
 // Encode a uniform tile (every amplitude equal to re[0], im[0]) exactly as
 // wencode would: a CONST stream at the first level whose 32 bytes fit the
-// size limit, else at the last level.  Components that are non-finite or
-// outside the lossy range, and uncompressed storage, are left to wencode:
-// the tile is filled and false returned.  Warp-wide.
+// size limit, else at the last level, or at level force_lv when >= 0.
+// Components that are non-finite or outside the lossy range, and
+// uncompressed storage, are left to wencode: the tile is filled and false
+// returned.  Warp-wide.
 __device__ bool wencode_uniform(double *re, double *im, const CodecCfg &cc, unsigned long long tile,
                                 uint8_t *out_arena, unsigned long long out_cap,
                                 unsigned long long *out_table, unsigned long long *part,
-                                DevScalars *scal, unsigned sweep_id) {
+                                DevScalars *scal, unsigned sweep_id, int force_lv) {
     const int c = cc.c, N = 1 << c;
     const int lane = threadIdx.x & 31;
     const double vr = re[0], vi = im[0];
@@ -1328,7 +1400,7 @@ __device__ bool wencode_uniform(double *re, double *im, const CodecCfg &cc, unsi
         __syncwarp();
         return false;
     }
-    const int level = cc.max_bytes >= (unsigned long long)HDR ? 0 : cc.nlev - 1;
+    const int level = force_lv >= 0 ? force_lv : (cc.max_bytes >= (unsigned long long)HDR ? 0 : cc.nlev - 1);
     const int s = cc.shifts[level];
     // stored signs: a zero keeps its sign only at shift 0
     const uint32_t sm0 = ((u0 >> 63) && (s == 0 || B0 != 0)) ? S_SET : S_CLEAR;
@@ -1490,6 +1562,10 @@ __device__ __forceinline__ unsigned long long member_tile(unsigned long long T, 
 // the gate run, compress with the ladder.  Persistent CTAs loop over items;
 // within an item every warp codes its own tiles.  A CTA reloads the
 // parameters and gates whenever it crosses into another entry's items.
+// SIZING: the sizing pass of per-stride ladder decisions (the same sweep,
+// stream sizes counted per stride and level, nothing written); a separate
+// instance so that the encoding sweep carries no extra call site.
+template <bool SIZING>
 __global__ void __launch_bounds__(SWEEP_THREADS, QS_SWEEP_MIN_BLOCKS) sweep_kernel(const SweepParams *__restrict__ plist,
                                                           const unsigned long long *__restrict__ istart,
                                                           int nlist) {
@@ -1559,7 +1635,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, QS_SWEEP_MIN_BLOCKS) sweep_kern
         }
         __syncthreads();
         const bool active = s_any != 0;
-        if (!active && (!scale || P.moves_tiles)) {
+        if (!active && (!scale || P.moves_tiles) && !P.every_item) {
             for (int j = warp; j < ntl; j += NWARPS)
                 wcarry(P.in_arena, P.in_table, member_tile(T, j, h, hb), P.out_arena, P.out_cap,
                        P.out_table, P.part, P.scal, P.sweep_id);
@@ -1627,13 +1703,19 @@ __global__ void __launch_bounds__(SWEEP_THREADS, QS_SWEEP_MIN_BLOCKS) sweep_kern
         }
         for (int j = warp; j < ntl; j += NWARPS) {
             const unsigned long long Tj = member_tile(T, j, h, hb);
+            if (SIZING) {
+                if (uni) fill_uniform(re + j * N, im + j * N, N);
+                wsize(re + j * N, im + j * N, P.cc, P.unit_bytes + (Tj >> P.unit_shift) * MAX_LEVELS);
+                continue;
+            }
+            const int flv = P.unit_level ? (int)P.unit_level[Tj >> P.unit_shift] : -1;
             if (uni && wencode_uniform(re + j * N, im + j * N, P.cc, Tj, P.out_arena, P.out_cap, P.out_table,
-                                       P.part, P.scal, P.sweep_id))
+                                       P.part, P.scal, P.sweep_id, flv))
                 continue;
             wencode(re + j * N, im + j * N, P.cc, Tj, P.out_arena, P.out_cap, P.out_table, P.part, P.scal,
-                    P.sweep_id, wst);
+                    P.sweep_id, wst, flv);
         }
-        if (threadIdx.x == 0) atomicAdd(&P.scal->items_done, 1ull);
+        if (threadIdx.x == 0 && !SIZING) atomicAdd(&P.scal->items_done, 1ull);
     }
 }
 
@@ -1687,10 +1769,15 @@ __global__ void __launch_bounds__(256) fp64_rate_kernel(double *out, int iters, 
     out[blockIdx.x * blockDim.x + threadIdx.x] = sum;
 }
 
+// Encode a fresh state (dense amplitudes, or the basis state |x> when
+// dense is null), one warp per tile.  With unit_bytes set this is the
+// sizing pass of per-stride decisions (nothing written but the counts);
+// with unit_level set every tile is coded at its stride's level.
 __global__ void __launch_bounds__(32 * TILE_WARPS) init_kernel(
     const double2 *dense, unsigned long long x, CodecCfg cc, unsigned long long ntiles,
     uint8_t *out_arena, unsigned long long out_cap, unsigned long long *out_table,
-    unsigned long long *part, DevScalars *scal) {
+    unsigned long long *part, DevScalars *scal, unsigned long long *unit_bytes,
+    const uint8_t *unit_level, int unit_shift) {
     extern __shared__ double smem[];
     __shared__ uint32_t stage[64 * TILE_WARPS];
     const int c = cc.c, N = 1 << c;
@@ -1702,6 +1789,10 @@ __global__ void __launch_bounds__(32 * TILE_WARPS) init_kernel(
         if (dense == nullptr && (x >> c) != t) {
             // all-zero tile: CONST at every level (32 bytes), or RAW zeros
             const uint32_t size = cc.force_raw ? HDR + 16u * N : HDR;
+            if (unit_bytes) {
+                if (lane < cc.nlev) atomicAdd(unit_bytes + (t >> unit_shift) * MAX_LEVELS + lane, (unsigned long long)size);
+                continue;
+            }
             unsigned long long off = 0;
             int ok = 0;
             if (lane == 0) {
@@ -1712,7 +1803,8 @@ __global__ void __launch_bounds__(32 * TILE_WARPS) init_kernel(
             off = shfl64(off, 0);
             ok = __shfl_sync(FULL, ok, 0);
             if (!ok) continue;
-            const int lv = cc.max_bytes >= (unsigned long long)HDR ? 0 : cc.nlev - 1;
+            const int lv = unit_level ? (int)unit_level[t >> unit_shift]
+                                      : (cc.max_bytes >= (unsigned long long)HDR ? 0 : cc.nlev - 1);
             const int s = cc.force_raw ? 0 : cc.shifts[lv];
             uint32_t *d = reinterpret_cast<uint32_t *>(out_arena + off);
             if (lane < 8) {
@@ -1744,7 +1836,26 @@ __global__ void __launch_bounds__(32 * TILE_WARPS) init_kernel(
             }
         }
         __syncwarp();
-        wencode(re, im, cc, t, out_arena, out_cap, out_table, part, scal, 0u, wst);
+        if (unit_bytes) {
+            wsize(re, im, cc, unit_bytes + (t >> unit_shift) * MAX_LEVELS);
+            continue;
+        }
+        wencode(re, im, cc, t, out_arena, out_cap, out_table, part, scal, 0u, wst,
+                unit_level ? (int)unit_level[t >> unit_shift] : -1);
+    }
+}
+
+// Ladder level of every stride from its streams' bytes at each level:
+// the first level within the stride's size limit, else the last
+// (Algorithm 2's ratio test, made once per stride).
+__global__ void unit_level_kernel(const unsigned long long *bytes, uint8_t *level, unsigned long long nunits,
+                                  int nlev, unsigned long long limit) {
+    for (unsigned long long u = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; u < nunits;
+         u += (unsigned long long)gridDim.x * blockDim.x) {
+        int k = nlev - 1;
+        for (int lv = nlev - 1; lv >= 0; --lv)
+            if (bytes[u * MAX_LEVELS + lv] <= limit) k = lv;
+        level[u] = (uint8_t)k;
     }
 }
 
@@ -1966,7 +2077,13 @@ static size_t tile_smem_bytes(int c, int bufs) { return (size_t)TILE_WARPS * buf
 
 cudaError_t launch_sweep(const SweepParams *plist, const unsigned long long *istart, int nlist,
                          int mb, int grid, cudaStream_t st) {
-    sweep_kernel<<<grid, SWEEP_THREADS, sweep_smem_bytes(mb), st>>>(plist, istart, nlist);
+    sweep_kernel<false><<<grid, SWEEP_THREADS, sweep_smem_bytes(mb), st>>>(plist, istart, nlist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_sizing(const SweepParams *plist, const unsigned long long *istart, int nlist,
+                                int mb, int grid, cudaStream_t st) {
+    sweep_kernel<true><<<grid, SWEEP_THREADS, sweep_smem_bytes(mb), st>>>(plist, istart, nlist);
     return cudaGetLastError();
 }
 
@@ -1992,9 +2109,17 @@ static int tile_grid(int grid, unsigned long long ntiles) {
 cudaError_t launch_init(const double2 *dense, unsigned long long x, const CodecCfg &cc,
                         unsigned long long ntiles, uint8_t *arena, unsigned long long cap,
                         unsigned long long *table, unsigned long long *part, DevScalars *scal,
+                        unsigned long long *unit_bytes, const uint8_t *unit_level, int unit_shift,
                         int grid, cudaStream_t st) {
     init_kernel<<<tile_grid(grid, ntiles), 32 * TILE_WARPS, tile_smem_bytes(cc.c, 1), st>>>(
-        dense, x, cc, ntiles, arena, cap, table, part, scal);
+        dense, x, cc, ntiles, arena, cap, table, part, scal, unit_bytes, unit_level, unit_shift);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unit_level(const unsigned long long *bytes, uint8_t *level, unsigned long long nunits,
+                              int nlev, unsigned long long limit, cudaStream_t st) {
+    const unsigned long long g = (nunits + THREADS - 1) / THREADS;
+    unit_level_kernel<<<g < 4096ull ? (int)g : 4096, THREADS, 0, st>>>(bytes, level, nunits, nlev, limit);
     return cudaGetLastError();
 }
 
@@ -2078,7 +2203,8 @@ cudaError_t launch_pair_sum(const Acc4 *in, Acc4 *out, unsigned long long nout, 
 cudaError_t configure_kernels() {
     cudaError_t e;
     const int maxsm = (int)sweep_smem_bytes(MAX_ITEM_LOG2);
-    if ((e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm))) return e;
+    if ((e = cudaFuncSetAttribute(sweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm))) return e;
+    if ((e = cudaFuncSetAttribute(sweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm))) return e;
     const int t1 = (int)tile_smem_bytes(MAX_C, 1), t2 = (int)tile_smem_bytes(MAX_C, 2);
     if ((e = cudaFuncSetAttribute(init_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, t1))) return e;
     if ((e = cudaFuncSetAttribute(validate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, t1))) return e;
@@ -2114,7 +2240,7 @@ cudaError_t fp64_rate(int device, double *fma_per_s) {
 
 int sweep_blocks_per_sm(int mb) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel, SWEEP_THREADS, sweep_smem_bytes(mb));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<false>, SWEEP_THREADS, sweep_smem_bytes(mb));
     return nb > 0 ? nb : 1;
 }
 

@@ -15,6 +15,7 @@ namespace qs {
 cudaError_t launch_init(const double2 *dense, unsigned long long x, const CodecCfg &cc,
                         unsigned long long ntiles, uint8_t *arena, unsigned long long cap,
                         unsigned long long *table, unsigned long long *part, DevScalars *scal,
+                        unsigned long long *unit_bytes, const uint8_t *unit_level, int unit_shift,
                         int grid, cudaStream_t st);
 cudaError_t configure_kernels();
 void set_global_error(const char *msg);
@@ -105,7 +106,7 @@ extern "C" qsim_status qsim_encode_noalloc(const double *dev_amps, int n_qubits,
     if (e == cudaSuccess)
         e = qs::launch_init(reinterpret_cast<const double2 *>(dev_amps), 0ull, cc, ntiles,
                             static_cast<uint8_t *>(dev_out), out_cap, dev_table, scr->part,
-                            &scr->scal, (int)grid, st);
+                            &scr->scal, nullptr, nullptr, 0, (int)grid, st);
     unsigned long long bump = 0;
     unsigned int err = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bump, &scr->scal.bump, sizeof bump, cudaMemcpyDeviceToHost, st);

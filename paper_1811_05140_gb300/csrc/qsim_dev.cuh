@@ -116,6 +116,10 @@ struct SweepParams {
     int use_alpha;
     int low_free;                   // no gate of the sweep targets or controls a qubit < c
     int moves_tiles;                // low_free and every gate a permutation: tiles move whole
+    int every_item;                 // compute and re-encode every item (per-stride decisions)
+    int unit_shift;                 // log2 of the tiles one ladder decision covers
+    unsigned long long *unit_bytes; // sizing pass: stream bytes per (stride, level); else null
+    const uint8_t *unit_level;      // encode pass: ladder level of every stride; else null
 };
 
 // End-of-pass bookkeeping of one state (norm, scale, used bytes).

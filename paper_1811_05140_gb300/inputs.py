@@ -225,3 +225,21 @@ def random_state(n: int, seed: int) -> np.ndarray:
     g = np.sqrt(-2.0 * np.log(1.0 - u1)) * np.cos(2 * math.pi * u2)
     psi = g[0::2] + 1j * g[1::2]
     return psi / np.linalg.norm(psi)
+
+
+def strided_mix_state(n: int, tile_log2: int, stride_log2: int, seed: int) -> np.ndarray:
+    """A seeded state whose strides of 2^stride_log2 amplitudes come in
+    four kinds in turn: all zero; Gaussian with the first tile zero; a
+    smooth phase ramp; Gaussian (strides that compress very differently)."""
+    N, span = 1 << tile_log2, 1 << stride_log2
+    psi = random_state(n, seed)
+    ramp = np.exp(2j * np.pi * np.arange(1 << n) / (1 << n)) / math.sqrt(1 << n)
+    for s0 in range(0, 1 << n, span):
+        kind = (s0 // span) % 4
+        if kind == 0:
+            psi[s0:s0 + span] = 0
+        elif kind == 1:
+            psi[s0:s0 + N] = 0
+        elif kind == 2:
+            psi[s0:s0 + span] = ramp[s0:s0 + span]
+    return psi

@@ -31,7 +31,7 @@ EXPORTS = ["qsim_create", "qsim_destroy", "qsim_set_stream", "qsim_set_aalc", "q
            "qsim_profile", "qsim_encode_noalloc", "qsim_flush_batch", "qsim_server_create",
            "qsim_server_submit", "qsim_server_result", "qsim_server_wait", "qsim_server_drain",
            "qsim_server_stats", "qsim_server_destroy", "qsim_set_pool", "qsim_fp64_rate",
-           "qsim_save", "qsim_load"]
+           "qsim_save", "qsim_load", "qsim_set_aalc_unit"]
 
 
 class QsimError(RuntimeError):
@@ -111,6 +111,7 @@ def load() -> C.CDLL:
         "qsim_destroy": ([vp], C.c_int),
         "qsim_set_stream": ([vp, vp], C.c_int),
         "qsim_set_aalc": ([vp, C.c_double, dp, C.c_int], C.c_int),
+        "qsim_set_aalc_unit": ([vp, C.c_int], C.c_int),
         "qsim_set_normalize": ([vp, C.c_int], C.c_int),
         "qsim_set_schedule": ([vp, C.c_int, C.c_int, C.c_int], C.c_int),
         "qsim_set_pool": ([vp, vp, C.c_size_t], C.c_int),
@@ -236,6 +237,7 @@ class State:
         self._check(self._L.qsim_create(C.byref(h), n, block_log2, CODECS[codec], eps), None)
         self.h = h
         self.n = n
+        self.block_log2 = block_log2
         self.codec = codec
         if stream is not None:
             self.set_stream(stream)
@@ -252,6 +254,7 @@ class State:
         self._L = L
         self.h = h
         self.n = self.stats()["n_qubits"]
+        self.block_log2 = None              # the stride decision unit is restored from the file
         self.codec = None
         if stream is not None:
             self.set_stream(stream)
@@ -294,6 +297,15 @@ class State:
     def set_aalc(self, theta: float, levels):
         arr = (C.c_double * max(1, len(levels)))(*levels)
         self._check(self._L.qsim_set_aalc(self.h, theta, arr, len(levels)))
+
+    def set_aalc_unit(self, unit_log2: int | None = None):
+        """One ladder decision per stride of 2^unit_log2 amplitudes
+        (default: the block_log2 of the constructor, Algorithm 2's stride);
+        0 decides per tile."""
+        u = self.block_log2 if unit_log2 is None else unit_log2
+        if u is None:
+            raise ValueError("give unit_log2 for a state loaded from a checkpoint")
+        self._check(self._L.qsim_set_aalc_unit(self.h, int(u)))
 
     def set_normalize(self, on: bool):
         self._check(self._L.qsim_set_normalize(self.h, int(bool(on))))

@@ -62,11 +62,12 @@ def test_checkpoint_file_decodes_in_the_oracle(tmp_path):
     st.save(path)
     data = open(path, "rb").read()
     assert data[:8] == b"QSIMCKP1"
-    hdr = struct.unpack_from("<8I8i2d3Q", data, 8)
-    assert hdr[1] == n and hdr[2] == c
-    ntiles = hdr[-2]
-    sizes = struct.unpack_from(f"<{ntiles}Q", data, 112)
-    off = 112 + 8 * ntiles
+    hdr = struct.unpack_from("<8I8i2d3Q2i", data, 8)
+    assert hdr[0] == 2 and hdr[1] == n and hdr[2] == c
+    assert hdr[-2:] == (0, 0)                 # decisions per tile, reserved
+    ntiles = hdr[-4]
+    sizes = struct.unpack_from(f"<{ntiles}Q", data, 120)
+    off = 120 + 8 * ntiles
     amps = []
     for t in range(ntiles):
         amps.append(oracle.decode_tile(data[off:off + sizes[t]], c))
@@ -88,7 +89,8 @@ def test_broken_checkpoints_are_rejected(tmp_path):
     for mutate in (lambda d: d.__setitem__(0, ord("X")),            # magic
                    lambda d: d.__setitem__(12, 99),                 # n
                    lambda d: d.__delitem__(slice(len(d) - 40, None)),  # truncated
-                   lambda d: d.__setitem__(112 + 8 * 4 + 24, 7)):   # a stream's tile size field
+                   lambda d: d.__setitem__(112, 99),                # decision unit
+                   lambda d: d.__setitem__(120 + 8 * 4 + 24, 7)):   # a stream's tile size field
         d = bytearray(data)
         mutate(d)
         open(bad, "wb").write(bytes(d))

@@ -14,7 +14,6 @@ stride's ratio against theta, retry at the next bound, keep the last).
   give the same streams as tile sweeps; after a lossy QFT every stride holds one level
   and meets its limit unless it is at the last level.
 """
-import math
 
 import numpy as np
 import pytest
@@ -40,21 +39,7 @@ def level_of(stream):
 
 
 def mixed_state(n, c, u, seed):
-    """Strides of four kinds in turn: all zero; one zero tile and the
-    rest Gaussian; a smooth phase ramp; Gaussian."""
-    N, nt = 1 << c, 1 << (u - c)
-    psi = I.random_state(n, seed)
-    k = np.arange(1 << n)
-    ramp = np.exp(2j * np.pi * k / (1 << n)) / math.sqrt(1 << n)
-    for s0 in range(0, 1 << n, nt * N):
-        kind = (s0 // (nt * N)) % 4
-        if kind == 0:
-            psi[s0:s0 + nt * N] = 0
-        elif kind == 1:
-            psi[s0:s0 + N] = 0
-        elif kind == 2:
-            psi[s0:s0 + nt * N] = ramp[s0:s0 + nt * N]
-    return psi
+    return I.strided_mix_state(n, c, u, seed)
 
 
 def test_decision_unit_is_capped():
