@@ -278,7 +278,10 @@ qsim_status qsim_stats(qsim_t h, qsim_stats_t *out);
 /*
  * Profile of the sweep kernels (Algorithm 2 passes) since profiling was
  * switched on.  Device times come from CUDA events recorded on the
- * handle's stream around each sweep launch.  dp_ops counts the FP64
+ * handle's stream around each sweep's launches (with per-stride ladder
+ * decisions: the sizing pass, the level pass and the encoding pass).
+ * Every flush and sweep is also an NVTX range ("qsim_flush", "qsim sweep
+ * <id> (<gates> gates)", "qsim_flush_batch") for profilers.  dp_ops counts the FP64
  * instructions of the canonical gate arithmetic (per matrix entry: first
  * term real/imaginary 1 per component, general 2; later terms 1 or 2;
  * entries 0 and leading +-1 free) plus 2 per amplitude for normalize;

@@ -2,6 +2,7 @@
 // sweep planner (gate run partition, partner-tile pairing) and the pass
 // control (launch, arena regrowth, re-run after an overflow).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -352,6 +353,15 @@ qsim_status ensure_arena(qsim_t h, int which, unsigned long long need) {
     h->cap[which] = nc;
     return QSIM_OK;
 }
+
+// An NVTX range for the lifetime of the object: profilers attribute the
+// launches enqueued inside it to the range (e.g. ncu --nvtx-include).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // log2 of the tiles one ladder decision covers: 0 (per tile) unless a
 // stride of more than one tile was set and the ladder has several levels.
@@ -957,6 +967,10 @@ qsim_status run_from(qsim_t h, FlushCtx &fc, size_t k) {
         for (size_t j = k; j < ns; ++j) {
             const int mb = h->c + fc.sweeps[j].h;
             const int per_sm = qs::sweep_blocks_per_sm(mb);
+            char label[64];
+            std::snprintf(label, sizeof label, "qsim sweep %u (%d gates)", fc.id0 + (unsigned)j,
+                          fc.sweeps[j].hi - fc.sweeps[j].lo);
+            NvtxRange range(label);
             if (h->profiling) CK(cudaEventRecord(h->events[2 * j], h->stream));
             if (ut) {                     // Algorithm 2's ratio test once per stride
                 CK(cudaMemsetAsync(h->unit_bytes, 0, nunits * qs::MAX_LEVELS * sizeof(unsigned long long),
@@ -1043,6 +1057,7 @@ qsim_status qsim_flush(qsim_t h) {
     qsim_status s = check_usable(h);
     if (s != QSIM_OK) return s;
     if (h->queue.empty()) return QSIM_OK;
+    NvtxRange range("qsim_flush");
     FlushCtx fc;
     if ((s = stage_flush(h, fc, h->stream)) != QSIM_OK) return s;
     if ((s = run_from(h, fc, 0)) != QSIM_OK) {
@@ -1131,6 +1146,7 @@ qsim_status qsim_flush_batch(qsim_t *handles, int count, int use_graph) {
     CK(cudaMemcpyAsync(g_batch.dI, g_batch.hI, ii * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    NvtxRange range("qsim_flush_batch");
     if (use_graph) CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     for (size_t r = 0; r < rounds; ++r) {
         const int n_r = (int)(rstart[r + 1] - rstart[r]);
