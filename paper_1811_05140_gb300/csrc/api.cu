@@ -20,9 +20,9 @@ namespace qs {
 void set_global_error(const char *msg);
 size_t sweep_smem_bytes(int mb);
 cudaError_t launch_sweep(const SweepParams *plist, const unsigned long long *istart, int nlist,
-                         int mb, int grid, cudaStream_t st);
+                         int mb, int grid, unsigned long long *work, cudaStream_t st);
 cudaError_t launch_sweep_sizing(const SweepParams *plist, const unsigned long long *istart, int nlist,
-                                int mb, int grid, cudaStream_t st);
+                                int mb, int grid, unsigned long long *work, cudaStream_t st);
 cudaError_t launch_finalize_list(const FinalizeEntry *list, int n, cudaStream_t st);
 cudaError_t launch_finalize(DevScalars *scal, int use_alpha, unsigned long long *used_hist,
                             unsigned slot, int record_used, cudaStream_t st);
@@ -977,14 +977,15 @@ qsim_status run_from(qsim_t h, FlushCtx &fc, size_t k) {
                                    h->stream));
                 ++h->launches;
                 CK(qs::launch_sweep_sizing(h->dparams + ns + j, h->distart + 2 * j, 1, mb,
-                                           grid_for(h, h->hparams[j].nitems, per_sm), h->stream));
+                                           grid_for(h, h->hparams[j].nitems, per_sm), &h->scal->work,
+                                           h->stream));
                 ++h->launches;
                 CK(qs::launch_unit_level(h->unit_bytes, h->unit_level, nunits, h->cc.nlev, unit_limit(h),
                                          h->stream));
             }
             ++h->launches;
             CK(qs::launch_sweep(h->dparams + j, h->distart + 2 * j, 1, mb,
-                                grid_for(h, h->hparams[j].nitems, per_sm), h->stream));
+                                grid_for(h, h->hparams[j].nitems, per_sm), &h->scal->work, h->stream));
             if (h->profiling) CK(cudaEventRecord(h->events[2 * j + 1], h->stream));
             ++h->launches;
             CK(qs::launch_finalize(h->scal, h->normalize, h->used_hist, (unsigned)j, 1, h->stream));
@@ -1046,6 +1047,7 @@ struct BatchSpace {
     qs::SweepParams *dP = nullptr, *hP = nullptr;
     unsigned long long *dI = nullptr, *hI = nullptr;
     qs::FinalizeEntry *dF = nullptr, *hF = nullptr;
+    unsigned long long *dW = nullptr;     // item counter of the round in flight
     size_t capP = 0, capI = 0;
 } g_batch;
 
@@ -1107,6 +1109,7 @@ qsim_status qsim_flush_batch(qsim_t *handles, int count, int use_graph) {
         if (g_batch.hI) cudaFreeHost(g_batch.hI);
         if (g_batch.dF) cudaFree(g_batch.dF);
         if (g_batch.hF) cudaFreeHost(g_batch.hF);
+        if (g_batch.dW) cudaFree(g_batch.dW);
         g_batch = BatchSpace{};
         const size_t cp = std::max<size_t>(entries, 64), ci = cp + std::max<size_t>(rounds, 64);
         CK(cudaMalloc(&g_batch.dP, cp * sizeof(qs::SweepParams)));
@@ -1115,6 +1118,7 @@ qsim_status qsim_flush_batch(qsim_t *handles, int count, int use_graph) {
         CK(cudaMallocHost(&g_batch.hF, cp * sizeof(qs::FinalizeEntry)));
         CK(cudaMalloc(&g_batch.dI, ci * sizeof(unsigned long long)));
         CK(cudaMallocHost(&g_batch.hI, ci * sizeof(unsigned long long)));
+        CK(cudaMalloc(&g_batch.dW, sizeof(unsigned long long)));
         g_batch.capP = cp;
         g_batch.capI = ci;
     }
@@ -1153,7 +1157,7 @@ qsim_status qsim_flush_batch(qsim_t *handles, int count, int use_graph) {
         const int mb = (int)rmb[r];
         const int per_sm = qs::sweep_blocks_per_sm(mb);
         cudaError_t le = qs::launch_sweep(g_batch.dP + rstart[r], g_batch.dI + istart_at[r], n_r, mb,
-                                          grid_for(h0, ritems[r], per_sm), st);
+                                          grid_for(h0, ritems[r], per_sm), g_batch.dW, st);
         if (le == cudaSuccess) le = qs::launch_finalize_list(g_batch.dF + rstart[r], n_r, st);
         if (le != cudaSuccess) {
             if (use_graph) { cudaStreamEndCapture(st, &graph); if (graph) cudaGraphDestroy(graph); }

@@ -1565,16 +1565,19 @@ __device__ __forceinline__ unsigned long long member_tile(unsigned long long T, 
 // SIZING: the sizing pass of per-stride ladder decisions (the same sweep,
 // stream sizes counted per stride and level, nothing written); a separate
 // instance so that the encoding sweep carries no extra call site.
+// Items are handed out by an atomic counter (work, zero at launch), so a
+// CTA that runs faster than its neighbours takes more items.
 template <bool SIZING>
 __global__ void __launch_bounds__(SWEEP_THREADS, QS_SWEEP_MIN_BLOCKS) sweep_kernel(const SweepParams *__restrict__ plist,
                                                           const unsigned long long *__restrict__ istart,
-                                                          int nlist) {
+                                                          int nlist, unsigned long long *work) {
     extern __shared__ double smem[];
     __shared__ SGate sg[GATE_CHUNK];
     __shared__ uint32_t stage[64 * NWARPS];
     __shared__ SweepParams P;
     __shared__ unsigned s_act[MAX_SWEEP_GATES / 32];
     __shared__ int s_entry, s_skip, s_chunk, s_any;
+    __shared__ unsigned long long s_gi;
     __shared__ int s_dest[1 << MAX_PAIRS];
     __shared__ unsigned long long s_plo[1 << MAX_PAIRS], s_phi[1 << MAX_PAIRS];
     __shared__ double s_alpha;
@@ -1582,17 +1585,21 @@ __global__ void __launch_bounds__(SWEEP_THREADS, QS_SWEEP_MIN_BLOCKS) sweep_kern
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *wst = stage + 64 * warp;
     int cur = -1;
-    for (unsigned long long gi = blockIdx.x; gi < total; gi += gridDim.x) {
+    for (;;) {
         __syncthreads();                  // previous item finished by every warp
-        if (threadIdx.x == 0) {           // entry owning gi: last e with istart[e] <= gi
+        if (threadIdx.x == 0) {           // next item; entry owning it: last e with istart[e] <= gi
+            const unsigned long long g = atomicAdd(work, 1ull);
             int lo = 0, hi = nlist - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (istart[mid] <= gi) lo = mid; else hi = mid - 1;
+                if (istart[mid] <= g) lo = mid; else hi = mid - 1;
             }
+            s_gi = g;
             s_entry = lo;
         }
         __syncthreads();
+        const unsigned long long gi = s_gi;
+        if (gi >= total) break;
         const int e = s_entry;
         if (e != cur) {
             {
@@ -2075,15 +2082,20 @@ namespace qs {
 size_t sweep_smem_bytes(int mb) { return (size_t)16 << mb; }
 static size_t tile_smem_bytes(int c, int bufs) { return (size_t)TILE_WARPS * bufs * (16u << c); }
 
+// work: the launch's item counter, zeroed on st before the launch.
 cudaError_t launch_sweep(const SweepParams *plist, const unsigned long long *istart, int nlist,
-                         int mb, int grid, cudaStream_t st) {
-    sweep_kernel<false><<<grid, SWEEP_THREADS, sweep_smem_bytes(mb), st>>>(plist, istart, nlist);
+                         int mb, int grid, unsigned long long *work, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    sweep_kernel<false><<<grid, SWEEP_THREADS, sweep_smem_bytes(mb), st>>>(plist, istart, nlist, work);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sweep_sizing(const SweepParams *plist, const unsigned long long *istart, int nlist,
-                                int mb, int grid, cudaStream_t st) {
-    sweep_kernel<true><<<grid, SWEEP_THREADS, sweep_smem_bytes(mb), st>>>(plist, istart, nlist);
+                                int mb, int grid, unsigned long long *work, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    sweep_kernel<true><<<grid, SWEEP_THREADS, sweep_smem_bytes(mb), st>>>(plist, istart, nlist, work);
     return cudaGetLastError();
 }
 

@@ -42,7 +42,8 @@ struct DevScalars {
     unsigned long long used;        // stream bytes of the last finished pass
     unsigned long long hist[MAX_LEVELS];
     unsigned long long items_done, items_skipped;
-    unsigned long long pad[3];
+    unsigned long long work;        // item counter of the sweep launch in flight
+    unsigned long long pad[2];
 };
 
 // A gate prepared for one sweep (positions are item-buffer bits).
