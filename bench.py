@@ -43,7 +43,8 @@ KERNEL_SRC = os.path.join(ROOT, "paper_1811_05140_gb300", "csrc", "kernels.cu")
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 5; 1 for --workload grover, minutes per circuit)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=N_QUBITS)
@@ -60,7 +61,10 @@ def parse_args():
     ap.add_argument("--alone", type=int, default=0, help="serving: circuits timed one at a time (0 = all)")
     ap.add_argument("--rate-factor", type=float, default=1.5, help="serving: arrival rate / one-at-a-time capacity")
     ap.add_argument("--tune", action="store_true", help="serving: autotuned schedule per (n, class)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 1 if args.workload == "grover" else 5
+    return args
 
 
 def measured_peaks():
