@@ -161,3 +161,24 @@ def test_stride_sweeps_cannot_be_sampled():
     cs.reset_basis(0)
     with pytest.raises(RuntimeError):
         cs.sweep_sample([I.h(0)], [], 0, 1)
+
+
+def test_level_encoder_special_values():
+    # the level encoder keeps the per-tile rules: a non-finite value gives a
+    # RAW stream (mode 2) at level 0 and the non-finite flag; a subnormal
+    # forces shift 0 but keeps the requested level byte
+    c, sh = 4, shifts()
+    a = I.random_state(c, I.BASE_SEED + 44)
+    st, fl = oracle.encode_tile_level(a, c, sh, 3)
+    want, _, _ = oracle.encode_tile(a, c, [sh[3]])
+    assert fl == 0 and st[2] == 3 and st[1] == sh[3]
+    assert st[:2] + st[3:] == want[:2] + want[3:]
+    b = a.copy()
+    b[5] = complex(float("nan"), 0.0)
+    st, fl = oracle.encode_tile_level(b, c, sh, 3)
+    assert fl & 1 and st[0] == 2 and st[2] == 0 and len(st) == 32 + 16 * (1 << c)
+    b = a.copy()
+    b[7] = complex(5e-324, 0.0)
+    st, fl = oracle.encode_tile_level(b, c, sh, 4)
+    assert fl & 2 and st[1] == 0 and st[2] == 4
+    assert np.array_equal(oracle.decode_tile(st, c).view(np.uint64), b.view(np.uint64))
