@@ -22,7 +22,8 @@
  *     error other than arena growth the handle is marked invalid and only
  *     qsim_destroy, qsim_last_error and qsim_stats remain usable.
  *   - Not thread-safe per handle; distinct handles may be used from
- *     distinct threads.
+ *     distinct threads (batched flushes of distinct handle sets are
+ *     serialised internally).
  *
  * Tile stream format (identical in the CPU oracle, written independently):
  *   A tile holds 2^c amplitudes; its re and im components each form a
@@ -303,7 +304,8 @@ qsim_status qsim_set_profiling(qsim_t h, int on);
 /* qsim_profile -- copy the counters (flushes first). */
 qsim_status qsim_profile(qsim_t h, qsim_profile_t *out);
 
-/* Message of the handle's last failing call ("" if none; h NULL: global). */
+/* Message of the handle's last failing call ("" if none); h NULL: the
+ * calling thread's last failing call that had no usable handle. */
 const char *qsim_last_error(qsim_t h);
 
 /*

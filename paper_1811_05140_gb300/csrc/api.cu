@@ -10,6 +10,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -88,7 +89,8 @@ struct Sweep {
     int H[4];
 };
 
-std::string g_last_error;
+// Message of the calling thread's last failing call without a handle.
+thread_local std::string g_last_error;
 
 bool matrix_is_diagonal(int k, const double *m) {
     int dim = 1 << k;
@@ -622,12 +624,11 @@ qsim_status qsim_create(qsim_t *out, int n_qubits, int block_log2, qsim_codec co
     auto bail = [&](qsim_status code) { qsim_destroy(h); return code; };
     if (cudaGetDevice(&h->device) != cudaSuccess) return bail(fail(nullptr, QSIM_ERR_CUDA, "cudaGetDevice failed"));
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = qs::configure_kernels();
-        if (e != cudaSuccess) return bail(fail(nullptr, QSIM_ERR_CUDA, "kernel setup: %s", cudaGetErrorString(e)));
-        configured = true;
-    }
+    static std::once_flag configured;
+    static cudaError_t config_err = cudaSuccess;
+    std::call_once(configured, [] { config_err = qs::configure_kernels(); });
+    if (config_err != cudaSuccess)
+        return bail(fail(nullptr, QSIM_ERR_CUDA, "kernel setup: %s", cudaGetErrorString(config_err)));
     if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(nullptr, QSIM_ERR_CUDA, "stream creation failed"));
     h->stream = h->own_stream;
@@ -1050,6 +1051,7 @@ struct BatchSpace {
     unsigned long long *dW = nullptr;     // item counter of the round in flight
     size_t capP = 0, capI = 0;
 } g_batch;
+std::mutex g_batch_mutex;                 // one batched flush at a time uses g_batch
 
 }  // namespace
 
@@ -1072,6 +1074,7 @@ qsim_status qsim_flush(qsim_t h) {
 
 qsim_status qsim_flush_batch(qsim_t *handles, int count, int use_graph) {
     if (!handles || count < 1) return fail(nullptr, QSIM_ERR_ARG, "qsim_flush_batch: no handles");
+    std::lock_guard<std::mutex> batch_lock(g_batch_mutex);
     for (int i = 0; i < count; ++i) {
         if (!handles[i]) return fail(nullptr, QSIM_ERR_ARG, "qsim_flush_batch: NULL handle");
         for (int j = 0; j < i; ++j)
