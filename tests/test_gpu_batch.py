@@ -4,7 +4,6 @@ circuit flushed alone, with and without CUDA-graph capture, including a
 circuit whose arena has to grow during the batch; one of them is also
 checked against the oracle.
 """
-import numpy as np
 import pytest
 
 import oracle

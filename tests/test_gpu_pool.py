@@ -3,7 +3,6 @@ the compressed state.  Streams stay byte-identical to a library-owned run
 (and to the oracle), the tensor's bytes are the ones written, a pool that
 is too small fails with OOM and invalidates the handle, and the state
 moves back to library arenas intact."""
-import numpy as np
 import pytest
 
 import oracle
