@@ -75,7 +75,7 @@ typedef enum {
     QSIM_ERR_OOM = 2,            /* device or host allocation failed */
     QSIM_ERR_CUDA = 3,           /* CUDA runtime error (no GPU, launch failure) */
     QSIM_ERR_NONFINITE = 4,      /* a gate produced NaN/Inf; state invalid */
-    QSIM_ERR_TIMEOUT = 5,        /* reserved: no call waits on the device */
+    QSIM_ERR_TIMEOUT = 5,        /* a host-side wait of the serving loop ran out (no call waits on the device) */
     QSIM_ERR_STATE_INVALID = 6,  /* handle unusable after an earlier error */
     QSIM_ERR_FORMAT = 7          /* malformed tile stream (import) */
 } qsim_status;
@@ -90,8 +90,9 @@ typedef enum {
 /*
  * qsim_create -- new state |0...0> of n_qubits (1..40), stored in tiles of
  * 2^min(block_log2, n_qubits, 8) amplitudes (Sec. III strides; block_log2
- * >= 1; qsim_set_schedule changes the tile size, up to 2^10).  codec as above; rel_err_bound is the point-wise relative bound
- * eps of REL, and the largest ladder bound of AALC (default ladder
+ * >= 1; qsim_set_schedule changes the tile size, up to 2^10).  codec as
+ * above; rel_err_bound is the point-wise relative bound eps of REL, and
+ * the largest ladder bound of AALC (default ladder
  * {lossless, 1e-5, 1e-4, 1e-3, 1e-2} cut at eps, theta = 16; see
  * qsim_set_aalc).  REL and AALC normalise before every sweep (Algorithm 2);
  * NONE and LOSSLESS do not (Algorithm 1).  *out receives the handle.
@@ -146,9 +147,9 @@ qsim_status qsim_set_normalize(qsim_t h, int on);
 /*
  * qsim_set_schedule -- tile_log2 c (1..10, <= n), pair slots hmax (1..4,
  * c + hmax <= 12; default 4) and sweep depth (max gates per sweep, 1..512;
- * default 512).  Re-tiles
- * the current state (lossless re-encode is exact only for RAW/lossless
- * tiles; call it before the first gate).  Used by the autotuner.
+ * default 512).  Re-tiles the current state (re-encoding is exact only for
+ * RAW/lossless tiles; call it before the first gate; n <= 32).  Used by
+ * the autotuner.  Errors: ARG (ranges), OOM, CUDA.
  */
 qsim_status qsim_set_schedule(qsim_t h, int tile_log2, int hmax, int depth);
 
@@ -200,10 +201,10 @@ qsim_status qsim_flush(qsim_t h);
  * launch each (plus one small finalize launch) on the first handle's stream,
  * optionally captured into a CUDA graph (use_graph = 1).  Each handle's
  * result is byte-identical to its own qsim_flush.  Handles that decide
- * per stride (qsim_set_aalc_unit) are refused with QSIM_ERR_ARG.  A handle whose output
- * arena overflows is grown and finished alone afterwards.  The handles must
- * be distinct and on one device.  Returns the first handle error (each
- * handle keeps its own qsim_last_error).
+ * per stride (qsim_set_aalc_unit) are refused with QSIM_ERR_ARG.  A handle
+ * whose output arena overflows is grown and finished alone afterwards.
+ * The handles must be distinct and on one device.  Returns the first
+ * handle error (each handle keeps its own qsim_last_error).
  */
 qsim_status qsim_flush_batch(qsim_t *handles, int count, int use_graph);
 
@@ -282,8 +283,8 @@ qsim_status qsim_stats(qsim_t h, qsim_stats_t *out);
  * handle's stream around each sweep's launches (with per-stride ladder
  * decisions: the sizing pass, the level pass and the encoding pass).
  * Every flush and sweep is also an NVTX range ("qsim_flush", "qsim sweep
- * <id> (<gates> gates)", "qsim_flush_batch") for profilers.  dp_ops counts the FP64
- * instructions of the canonical gate arithmetic (per matrix entry: first
+ * <id> (<gates> gates)", "qsim_flush_batch") for profilers.  dp_ops counts
+ * the FP64 instructions of the canonical gate arithmetic (per matrix entry: first
  * term real/imaginary 1 per component, general 2; later terms 1 or 2;
  * entries 0 and leading +-1 free) plus 2 per amplitude for normalize;
  * bytes counts compressed stream bytes read and written plus 32 bytes per
@@ -331,8 +332,8 @@ qsim_status qsim_import_tiles(qsim_t h, unsigned long long first, unsigned long 
  * a gate list (no GPU needed).  Gate g has ntargets[g] targets in
  * targets[2g..], matrix in matrices[32g..] (row-major complex, zero-padded).
  * Writes per sweep its first gate to out_lo, its pair count to out_h and
- * its pair qubits to out_H[4s..] (ascending; unused slots 0).  Returns the number of sweeps, or -1 on
- * bad arguments, or -2 when cap is too small.
+ * its pair qubits to out_H[4s..] (ascending; unused slots 0).  Returns the
+ * number of sweeps, or -1 on bad arguments, or -2 when cap is too small.
  */
 int qsim_plan_sweeps(int n, int tile_log2, int hmax, int depth, int ngates,
                      const int *ntargets, const int *targets, const double *matrices,
