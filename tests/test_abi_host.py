@@ -63,3 +63,25 @@ def test_create_without_device_reports_error(lib):
     with pytest.raises(qsim.QsimError) as e:
         qsim.State(10, 8, "rel", 1e-4)
     assert e.value.status == 3            # QSIM_ERR_CUDA
+
+
+def test_header_compiles_as_c_and_links(lib, tmp_path):
+    """A plain C99 program (tests/abi_example.c) builds against
+    include/qsim.h with warnings as errors, links libqsim.so and runs: the
+    host-only planner works, and creating a state either succeeds (GPU
+    present) or returns QSIM_ERR_CUDA with a message."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    libdir = os.path.join(ROOT, "paper_1811_05140_gb300")
+    exe = os.path.join(str(tmp_path), "abi_example")
+    subprocess.check_call([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                           "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "abi_example.c"),
+                           "-o", exe, "-L", libdir, "-lqsim", "-Wl,-rpath," + libdir, "-lm"])
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    lines = r.stdout.split("\n")
+    assert lines[0].startswith("sweeps ") and int(lines[0].split()[1]) >= 1
+    assert lines[1].startswith("create 3 ") or lines[1].startswith("fidelity ")
