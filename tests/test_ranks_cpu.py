@@ -48,3 +48,23 @@ def test_two_gloo_ranks_take_the_slowest_time():
 def test_single_rank_needs_no_process_group():
     assert bench.max_over_ranks(17.5, 1, "cpu") == 17.5
     assert bench.job_rate(1, 420, 5, 1000.0) == 2100.0
+
+
+def test_serving_mix_is_seeded_and_shaped():
+    """The serving workload's request stream: the same seed gives the same
+    circuits; the class mix is about 40 / 30 / 30 (QFT / Grover / grid); n,
+    the bounds and the read-out qubits stay in range."""
+    a = bench.serving_requests(400, 10, 14, 77)
+    b = bench.serving_requests(400, 10, 14, 77)
+    assert [(r["n"], r["cls"], r["x"], r["eps"], r["readout"], len(r["gates"])) for r in a] == \
+           [(r["n"], r["cls"], r["x"], r["eps"], r["readout"], len(r["gates"])) for r in b]
+    counts = {k: sum(r["cls"] == k for r in a) for k in ("qft", "grover", "grid")}
+    assert abs(counts["qft"] / 400 - 0.4) < 0.08
+    assert abs(counts["grover"] / 400 - 0.3) < 0.08
+    assert abs(counts["grid"] / 400 - 0.3) < 0.08
+    for r in a:
+        assert 10 <= r["n"] <= 14 and r["eps"] in (1e-3, 1e-4)
+        assert 1 <= len(r["readout"]) <= 3 and len(set(r["readout"])) == len(r["readout"])
+        assert all(0 <= q < r["n"] for q in r["readout"])
+        assert 0 <= r["x"] < (1 << r["n"])
+        assert all(max(g.targets) < r["n"] for g in r["gates"])
