@@ -72,6 +72,8 @@ def lib():
         L.or_stream_cap.restype = C.c_size_t
         L.or_encode_tile.argtypes = [dp, C.c_int, ip, C.c_int, C.c_uint64, u8p, ip, ip]
         L.or_encode_tile.restype = C.c_size_t
+        L.or_check_bound.argtypes = [C.c_int, C.c_uint64, C.c_uint64]
+        L.or_check_bound.restype = C.c_uint64
         L.or_encode_tile_level.argtypes = [dp, C.c_int, ip, C.c_int, u8p, ip]
         L.or_encode_tile_level.restype = C.c_size_t
         L.or_decode_tile.argtypes = [u8p, C.c_size_t, C.c_int, dp]
@@ -208,6 +210,12 @@ def encode_tile(amps: np.ndarray, c: int, shifts, max_bytes: int | None = None):
     n = lib().or_encode_tile(_dptr(a.view(np.float64)), c, sh, len(shifts), mb, out,
                              C.byref(level), C.byref(flags))
     return bytes(out[:n]), level.value, flags.value
+
+
+def check_bound(s: int, count: int, seed: int) -> int:
+    """Violations of |x^ - x| < 2^(s-53)|x| over count seeded random
+    magnitudes through the quantiser (0 expected)."""
+    return lib().or_check_bound(s, count, seed)
 
 
 def encode_tile_level(amps: np.ndarray, c: int, shifts, k: int):

@@ -600,6 +600,33 @@ static size_t encode_at(const double *a, int c, int s, int level, uint8_t *out)
     return HDR + body;
 }
 
+/*
+ * The quantiser's point-wise relative bound (Sec. III, made relative as in
+ * ref. [xin2018]) on count magnitude bit patterns drawn with SplitMix64
+ * (Steele, Lea and Flood, 2014) from seed, uniform over the normal range
+ * from 2^-962 up to the lossy limit: every reconstruction
+ * x^ = bits(quant(B, s) << s) must satisfy |x^ - x| < 2^(s-53) x.  The
+ * difference is exact (x^ / x lies in [1/2, 2]) and the bound is a power
+ * of two times x, still normal, so the comparison is exact.  Returns the
+ * number of violations.  Test infrastructure.
+ */
+uint64_t or_check_bound(int s, uint64_t count, uint64_t seed)
+{
+    const uint64_t lo = MIN_NORMAL + (60ull << 52);
+    uint64_t bad = 0, st = seed;
+    for (uint64_t i = 0; i < count; ++i) {
+        st += 0x9E3779B97F4A7C15ull;
+        uint64_t z = st;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        uint64_t B = lo + z % (LOSSY_LIMIT - lo);
+        double x = bitsd(B), xr = bitsd(quant(B, s) << s);
+        if (!(fabs(xr - x) < ldexp(x, s - 53))) ++bad;
+    }
+    return bad;
+}
+
 /* Scan a tile: any non-finite component, and whether every component is
  * zero or inside the lossy range (normal and below 2^1023). */
 static void scan_tile(const double *a, int c, int *nonfinite, int *eligible)

@@ -297,3 +297,11 @@ def test_single_spike_tile_is_small():
         assert stream[0] == 1 and len(stream) == 80
         back = oracle.decode_tile(stream, c)
         assert np.count_nonzero(back) == 1 and abs(back[pos] - a[pos]) < 1e-4
+
+
+def test_relative_bound_hundred_million_values():
+    # 1.04*10^8 seeded magnitudes through the oracle's quantiser: 2*10^6 at
+    # each shift 1..52 (the binades below 2^-962 are covered exactly above);
+    # a truncating quantiser would exceed the bound by up to a factor 2
+    bad = sum(oracle.check_bound(s, 2_000_000, 0x5EED + s) for s in range(1, 53))
+    assert bad == 0
