@@ -95,6 +95,11 @@ def lib():
                                     C.POINTER(OrGate), C.c_int, ip, C.c_int, C.c_uint64, u8p,
                                     C.c_size_t, C.POINTER(C.c_uint32)]
         L.or_item_sweep.restype = C.c_int
+        L.or_stride_sweep.argtypes = [C.c_int, C.c_int, ip, C.c_int, C.c_int, C.c_uint64, C.c_uint64,
+                                      u64p, C.POINTER(C.c_void_p), C.POINTER(C.c_uint32), C.c_uint64,
+                                      C.c_double, C.POINTER(OrGate), C.c_int, ip, C.c_int, u8p,
+                                      C.c_size_t, C.POINTER(C.c_uint32)]
+        L.or_stride_sweep.restype = C.c_int
         L.or_csim_dense.argtypes = [C.c_void_p, dp]
         L.or_csim_dense.restype = C.c_int
         L.or_csim_stream.argtypes = [C.c_void_p, C.c_uint64, u8p, C.c_uint32]
@@ -262,6 +267,51 @@ def item_sweep(n: int, c: int, H, base_tile: int, streams, alpha: float, gates, 
     res, off = [], 0
     raw = bytes(out)
     for j in range(len(streams)):
+        res.append(raw[off:off + out_len[j]])
+        off += out_len[j]
+    return res
+
+
+def stride_items_tiles(c: int, H, stride_log2: int, t0: int) -> list[int]:
+    """Every member tile of every item that holds a tile of the stride of
+    2^(stride_log2 - c) tiles starting at tile t0 (ascending)."""
+    hb = [q - c for q in sorted(H)]
+    hmask = sum(1 << b for b in hb)
+    nt = 1 << (stride_log2 - c)
+    out = set()
+    for t in range(t0, t0 + nt):
+        T = t & ~hmask
+        for j in range(1 << len(hb)):
+            out.add(T | sum(1 << b for i, b in enumerate(hb) if (j >> i) & 1))
+    return sorted(out)
+
+
+def stride_sweep(n: int, c: int, H, stride_log2: int, theta: float, t0: int, streams: dict,
+                 alpha: float, gates, shifts):
+    """One stride of a sweep that decides per stride (sampled checks of large
+    states): streams maps every tile of stride_items_tiles(...) to its input
+    stream; returns the stride's new streams in tile order."""
+    H = sorted(H)
+    ut = stride_log2 - c
+    tiles = sorted(streams)
+    bufs = [(C.c_uint8 * len(streams[t])).from_buffer_copy(streams[t]) for t in tiles]
+    ptrs = (C.c_void_p * len(bufs))(*[C.addressof(b) for b in bufs])
+    lens = (C.c_uint32 * len(bufs))(*[len(streams[t]) for t in tiles])
+    tarr = (C.c_uint64 * len(tiles))(*tiles)
+    hh = (C.c_int * max(1, len(H)))(*H)
+    sh = (C.c_int * len(shifts))(*shifts)
+    cap = (1 << ut) * lib().or_stream_cap(c)
+    out = (C.c_uint8 * cap)()
+    out_len = (C.c_uint32 * (1 << ut))()
+    arr = gate_array(gates)
+    rc = lib().or_stride_sweep(n, c, hh, len(H), ut, max_bytes_for(stride_log2, theta), t0, tarr, ptrs,
+                               lens, len(tiles), alpha, arr, len(gates), sh, len(shifts), out, cap,
+                               out_len)
+    if rc != 0:
+        raise RuntimeError(f"oracle stride sweep failed ({rc})")
+    res, off = [], 0
+    raw = bytes(out)
+    for j in range(1 << ut):
         res.append(raw[off:off + out_len[j]])
         off += out_len[j]
     return res

@@ -18,7 +18,9 @@
  *       sweep (a run of gates) at a time; a sweep whose gates only permute
  *       whole tiles moves their streams instead (sweep_moves_tiles).  The
  *       ladder's ratio test is made per tile, or once per stride of
- *       several tiles as Algorithm 2 prints it (or_csim_set_unit).
+ *       several tiles as Algorithm 2 prints it (or_csim_set_unit); single
+ *       items (or_item_sweep) and single strides (or_stride_sweep) can be
+ *       recomputed on their own for sampled checks of large states.
  *   N   the state norm used by "normalize": the exact sum of |a|^2 in
  *       fixed point (units of 2^-112), rounded once to double.
  *
@@ -868,26 +870,38 @@ static void csim_store(or_csim *cs, uint64_t t, const double *amps)
  * level at which the stride's streams together take at most umax bytes
  * (stride ratio >= theta), else the last level.
  */
-static void csim_store_unit(or_csim *cs, uint64_t t0, const double *amps)
+/* The ratio test of one stride: the nt tiles of amps (nt * 2^c complex
+ * values) coded at level k = 0, 1, ... until their streams together take at
+ * most umax bytes, else at the last level; buf[j] (or_stream_cap(c) bytes
+ * each) and len[j] receive tile j's stream.  Returns 1 when a value is not
+ * finite. */
+static int encode_stride(const double *amps, uint64_t nt, int c, const int *shifts, int nlev,
+                         uint64_t umax, uint8_t **buf, size_t *len)
 {
-    int c = cs->c;
-    uint64_t N = 1ull << c, nt = 1ull << cs->ut;
-    uint8_t **buf = malloc(nt * sizeof *buf);
-    size_t *len = malloc(nt * sizeof *len);
+    uint64_t N = 1ull << c;
     int nonfinite = 0;
-    for (uint64_t j = 0; j < nt; ++j) buf[j] = malloc(or_stream_cap(c));
-    for (int k = 0; k < cs->nlev; ++k) {
+    for (int k = 0; k < nlev; ++k) {
         uint64_t total = 0;
         nonfinite = 0;
         for (uint64_t j = 0; j < nt; ++j) {
             int flags = 0;
-            len[j] = or_encode_tile_level(amps + 2 * j * N, c, cs->shifts, k, buf[j], &flags);
+            len[j] = or_encode_tile_level(amps + 2 * j * N, c, shifts, k, buf[j], &flags);
             if (flags & OR_F_NONFINITE) nonfinite = 1;
             total += len[j];
         }
-        if (total <= cs->umax) break;
+        if (total <= umax) break;
     }
-    if (nonfinite) cs->err |= 1;
+    return nonfinite;
+}
+
+static void csim_store_unit(or_csim *cs, uint64_t t0, const double *amps)
+{
+    int c = cs->c;
+    uint64_t nt = 1ull << cs->ut;
+    uint8_t **buf = malloc(nt * sizeof *buf);
+    size_t *len = malloc(nt * sizeof *len);
+    for (uint64_t j = 0; j < nt; ++j) buf[j] = malloc(or_stream_cap(c));
+    if (encode_stride(amps, nt, c, cs->shifts, cs->nlev, cs->umax, buf, len)) cs->err |= 1;
     for (uint64_t j = 0; j < nt; ++j) csim_put(cs, t0 + j, buf[j], len[j]);
     free(buf);
     free(len);
@@ -1288,6 +1302,95 @@ int or_item_sweep(int n, int c, const int *H, int h, uint64_t base_tile,
     }
     free(buf);
     free(tmp);
+    return rc;
+}
+
+static int cmp_u64(const void *a, const void *b)
+{
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return x < y ? -1 : x > y;
+}
+
+/*
+ * One stride of a sweep that decides per stride, on its own (sampled checks
+ * of states too large for the oracle): the stride of 2^ut tiles starting at
+ * tile t0, ladder decision against umax bytes.  The caller passes the input
+ * streams of every member of every item that holds a tile of the stride:
+ * ntl tiles, indices ascending in tiles[], stream k in in[k] (in_len[k]
+ * bytes).  alpha is the pass's normalize scale.  The items are decoded,
+ * normalized and computed as or_csim_sweep computes every item, then the
+ * stride's tiles are compressed with one ladder decision (the rule of
+ * csim_store_unit) and their streams written in tile order to out
+ * (out_len[j] each).
+ * Returns 0, -1 on a malformed stream, -2 on a gate outside an item, -3
+ * when out is too small, -5 when a needed tile is missing from tiles[].
+ */
+int or_stride_sweep(int n, int c, const int *H, int h, int ut, uint64_t umax, uint64_t t0,
+                    const uint64_t *tiles, const uint8_t *const *in, const uint32_t *in_len,
+                    uint64_t ntl, double alpha, const or_gate *g, int ng, const int *shifts,
+                    int nlev, uint8_t *out, size_t out_cap, uint32_t *out_len)
+{
+    uint64_t N = 1ull << c, nt = 1ull << ut;
+    int mb = c + h, rc = 0;
+    int qb[64];
+    for (int p = 0; p < c; ++p) qb[p] = p;
+    uint64_t hmask_tile = 0;
+    for (int i = 0; i < h; ++i) {
+        qb[c + i] = H[i];
+        hmask_tile |= 1ull << (H[i] - c);
+    }
+    (void)n;
+    /* the items holding the stride's tiles, each once */
+    uint64_t *items = malloc(nt * sizeof *items);
+    for (uint64_t j = 0; j < nt; ++j) items[j] = (t0 + j) & ~hmask_tile;
+    qsort(items, nt, sizeof *items, cmp_u64);
+    double *buf = malloc(((size_t)1 << mb) * 16);
+    double *sbuf = malloc(nt * N * 16);
+    for (uint64_t ii = 0; ii < nt && rc == 0; ++ii) {
+        if (ii && items[ii] == items[ii - 1]) continue;
+        uint64_t T = items[ii];
+        for (uint64_t j = 0; j < (1ull << h) && rc == 0; ++j) {
+            uint64_t Tj = T;
+            for (int i = 0; i < h; ++i)
+                if ((j >> i) & 1) Tj |= 1ull << (H[i] - c);
+            const uint64_t *hit = bsearch(&Tj, tiles, ntl, sizeof *tiles, cmp_u64);
+            if (!hit) { rc = -5; break; }
+            uint64_t k = (uint64_t)(hit - tiles);
+            if (or_decode_tile(in[k], in_len[k], c, buf + 2 * j * N) != 0) rc = -1;
+        }
+        if (rc) break;
+        if (alpha != 1.0)
+            for (uint64_t i = 0; i < 2 * ((uint64_t)1 << mb); ++i) buf[i] = buf[i] * alpha;
+        for (int i = 0; i < ng && rc == 0; ++i)
+            if (apply_gate_buf(buf, mb, qb, T << c, &g[i]) != 0) rc = -2;
+        for (uint64_t j = 0; j < (1ull << h) && rc == 0; ++j) {
+            uint64_t Tj = T;
+            for (int i = 0; i < h; ++i)
+                if ((j >> i) & 1) Tj |= 1ull << (H[i] - c);
+            if (Tj >= t0 && Tj < t0 + nt) memcpy(sbuf + 2 * (Tj - t0) * N, buf + 2 * j * N, N * 16);
+        }
+    }
+    if (rc == 0) {
+        uint8_t **sb = malloc(nt * sizeof *sb);
+        size_t *len = malloc(nt * sizeof *len);
+        for (uint64_t j = 0; j < nt; ++j) sb[j] = malloc(or_stream_cap(c));
+        encode_stride(sbuf, nt, c, shifts, nlev, umax, sb, len);
+        size_t used = 0;
+        for (uint64_t j = 0; j < nt; ++j) {
+            if (rc == 0 && used + len[j] > out_cap) rc = -3;
+            if (rc == 0) {
+                memcpy(out + used, sb[j], len[j]);
+                out_len[j] = (uint32_t)len[j];
+                used += len[j];
+            }
+            free(sb[j]);
+        }
+        free(sb);
+        free(len);
+    }
+    free(items);
+    free(buf);
+    free(sbuf);
     return rc;
 }
 

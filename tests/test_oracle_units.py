@@ -182,3 +182,26 @@ def test_level_encoder_special_values():
     st, fl = oracle.encode_tile_level(b, c, sh, 4)
     assert fl & 2 and st[1] == 0 and st[2] == 4
     assert np.array_equal(oracle.decode_tile(st, c).view(np.uint64), b.view(np.uint64))
+
+
+def test_stride_sweep_on_its_own_matches_the_full_sweep():
+    # every stride of every sweep recomputed from the sweep's input streams
+    # of the items that hold its tiles, against the full per-stride sweep
+    from oracle.partition import partition
+    n, c, u, theta = 11, 4, 7, 4.0
+    gates = I.basis_gates(n, 0x2A5) + I.qft(n) + I.random_grid(*I.grid_shape(n), 3, 4)
+    cs, ut = unit_csim(n, c, u, theta)
+    cs.reset_basis(0)
+    for lo, hi, H in partition(gates, n, c, 4, 9):
+        before = [cs.stream(t) for t in range(1 << (n - c))]
+        alpha = cs.alpha
+        cs.sweep(gates[lo:hi], H)
+        for t0 in range(0, 1 << (n - c), 1 << ut):
+            need = oracle.stride_items_tiles(c, H, u, t0)
+            got = oracle.stride_sweep(n, c, H, u, theta, t0, {t: before[t] for t in need}, alpha,
+                                      gates[lo:hi], shifts())
+            assert got == [cs.stream(t0 + j) for j in range(1 << ut)]
+    need = oracle.stride_items_tiles(c, [c + 3], u, 0)
+    with pytest.raises(RuntimeError):
+        oracle.stride_sweep(n, c, [c + 3], u, theta, 0, {t: before[t] for t in need[:-1]}, 1.0,
+                            [I.h(c + 3)], shifts())
