@@ -273,6 +273,8 @@ typedef struct {
     unsigned long long kernel_launches; /* kernels launched by the handle */
     double alpha;                      /* scale of the next normalize step */
     int tile_log2, hmax, depth, n_qubits;
+    unsigned long long h2d_bytes;      /* bytes the handle's calls copied host -> device */
+    unsigned long long d2h_bytes;      /* bytes the handle's calls copied device -> host */
 } qsim_stats_t;
 
 qsim_status qsim_stats(qsim_t h, qsim_stats_t *out);
@@ -319,6 +321,18 @@ qsim_status qsim_export_tiles(qsim_t h, unsigned long long first, unsigned long 
                               void *out, unsigned long long cap, unsigned long long *sizes);
 
 /*
+ * qsim_export_tile_set -- as qsim_export_tiles for an arbitrary set of
+ * tiles: tiles (host, count entries, each < 2^(n - tile_log2), repeats
+ * allowed) lists them; their streams are concatenated in list order into
+ * out (host, cap bytes) and their sizes written to sizes (host, count
+ * entries).  With out NULL only the sizes are written.  Used to read the
+ * tile groups of sampled items of large states.  Errors: ARG (null
+ * arguments, a tile out of range, cap too small).
+ */
+qsim_status qsim_export_tile_set(qsim_t h, const unsigned long long *tiles, unsigned long long count,
+                                 void *out, unsigned long long cap, unsigned long long *sizes);
+
+/*
  * qsim_import_tiles -- flush, then replace tiles first .. first+count-1 by
  * the concatenated streams in data (host) with the given sizes.  Every
  * stream is first decoded on the device; if any fails, FORMAT is returned
@@ -363,7 +377,10 @@ int qsim_plan_sweeps(int n, int tile_log2, int hmax, int depth, int ngates,
  * (n_qubits - tile_log2 <= 12), held by every GPU that loads the library
  * until the process exits.  Larger states are rejected with ERR_ARG.
  * The first call on a device looks up the array's device address (and sets
- * kernel attributes); make that first call before any stream capture.  All
+ * kernel attributes), once per device even when several host threads make
+ * their first call at the same time; make that first call before any
+ * stream capture.  cuda_stream must belong to the current device (ERR_ARG
+ * otherwise), since the scratch address is the current device's.  All
  * calls share the array and it keeps the last call's contents; each call
  * clears what must start at zero.  Calls that overlap on the GPU (several
  * streams or threads at once) race on the array and must be serialised by

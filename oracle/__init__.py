@@ -27,14 +27,14 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
 
-CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-pthread"]
 
 
 def build(force: bool = False) -> str:
     """Compile oracle.c with gcc into liboracle.so next to it."""
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
         tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", *CFLAGS, SRC, "-o", tmp, "-lm"])
+        subprocess.check_call(["gcc", *CFLAGS, SRC, "-o", tmp, "-lm", "-lpthread"])
         os.replace(tmp, LIB)
     return LIB
 
@@ -95,6 +95,11 @@ def lib():
                                     C.POINTER(OrGate), C.c_int, ip, C.c_int, C.c_uint64, u8p,
                                     C.c_size_t, C.POINTER(C.c_uint32)]
         L.or_item_sweep.restype = C.c_int
+        L.or_item_sweep_batch.argtypes = [C.c_int, C.c_int, ip, C.c_int, C.c_uint64, u64p, u8p, u64p,
+                                          C.POINTER(C.c_uint32), C.c_double, C.POINTER(OrGate), C.c_int,
+                                          ip, C.c_int, C.c_uint64, u8p, C.c_size_t,
+                                          C.POINTER(C.c_uint32), ip, C.c_int]
+        L.or_item_sweep_batch.restype = C.c_int
         L.or_stride_sweep.argtypes = [C.c_int, C.c_int, ip, C.c_int, C.c_int, C.c_uint64, C.c_uint64,
                                       u64p, C.POINTER(C.c_void_p), C.POINTER(C.c_uint32), C.c_uint64,
                                       C.c_double, C.POINTER(OrGate), C.c_int, ip, C.c_int, u8p,
@@ -269,6 +274,55 @@ def item_sweep(n: int, c: int, H, base_tile: int, streams, alpha: float, gates, 
     for j in range(len(streams)):
         res.append(raw[off:off + out_len[j]])
         off += out_len[j]
+    return res
+
+
+def item_sweep_batch(n: int, c: int, H, bases, raw: bytes, sizes, alpha: float, gates, shifts,
+                     max_bytes: int | None = None, threads: int | None = None):
+    """Many items of one sweep, each as item_sweep computes it, on `threads`
+    host threads (default: every core).  raw holds the members' streams
+    concatenated item by item (member order as in item_sweep), sizes their
+    lengths.  Returns a list, per item, of the members' new streams."""
+    H = sorted(H)
+    h = len(H)
+    nm = 1 << h
+    nitems = len(bases)
+    assert len(sizes) == nitems * nm
+    if nitems == 0:
+        return []
+    threads = threads or os.cpu_count() or 1
+    offs = np.zeros(len(sizes), dtype=np.uint64)
+    np.cumsum(np.asarray(sizes[:-1], dtype=np.uint64), out=offs[1:])
+    inb = np.frombuffer(raw, dtype=np.uint8) if raw else np.zeros(1, np.uint8)
+    inb = np.ascontiguousarray(inb)
+    lens = np.asarray(sizes, dtype=np.uint32)
+    bs = np.asarray(bases, dtype=np.uint64)
+    stride = nm * lib().or_stream_cap(c)
+    out = np.zeros(nitems * stride, dtype=np.uint8)
+    out_len = np.zeros(nitems * nm, dtype=np.uint32)
+    rc = np.zeros(nitems, dtype=np.int32)
+    hh = (C.c_int * max(1, h))(*H)
+    sh = (C.c_int * len(shifts))(*shifts)
+    arr = gate_array(gates)
+    mb = (1 << 64) - 1 if max_bytes is None else max_bytes
+    u64p = C.POINTER(C.c_uint64)
+    u8p = C.POINTER(C.c_uint8)
+    bad = lib().or_item_sweep_batch(
+        n, c, hh, h, nitems, bs.ctypes.data_as(u64p), inb.ctypes.data_as(u8p), offs.ctypes.data_as(u64p),
+        lens.ctypes.data_as(C.POINTER(C.c_uint32)), alpha, arr, len(gates), sh, len(shifts), mb,
+        out.ctypes.data_as(u8p), stride, out_len.ctypes.data_as(C.POINTER(C.c_uint32)),
+        rc.ctypes.data_as(C.POINTER(C.c_int)), threads)
+    if bad:
+        raise RuntimeError(f"oracle item sweep failed for {bad} item(s), codes {sorted(set(rc.tolist()))}")
+    res = []
+    for i in range(nitems):
+        off = i * stride
+        mem = []
+        for j in range(nm):
+            ln = int(out_len[i * nm + j])
+            mem.append(out[off:off + ln].tobytes())
+            off += ln
+        res.append(mem)
     return res
 
 

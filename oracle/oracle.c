@@ -38,6 +38,7 @@
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#include <pthread.h>
 
 typedef unsigned __int128 u128;
 
@@ -1303,6 +1304,75 @@ int or_item_sweep(int n, int c, const int *H, int h, uint64_t base_tile,
     free(buf);
     free(tmp);
     return rc;
+}
+
+/*
+ * Many items of one sweep, each exactly as or_item_sweep computes it, run
+ * on `threads` host threads (the items are independent: each thread takes
+ * items i = k, k + threads, ...).  Item i has base tile bases[i]; the
+ * stream of its member j is in_buf + in_off[i*2^h + j], in_len[...] bytes.
+ * Its output streams are written concatenated at out + i*out_stride
+ * (out_len[i*2^h + j] bytes each) and its return code (as or_item_sweep)
+ * to rc[i].  Used for sampled checks of large states and for the
+ * all-cores timing of the oracle.  Returns the number of items whose code
+ * is not 0.
+ */
+typedef struct {
+    int n, c, h, ng, nlev, threads, k;
+    const int *H;
+    uint64_t nitems, max_bytes;
+    const uint64_t *bases, *in_off;
+    const uint8_t *in_buf;
+    const uint32_t *in_len;
+    double alpha;
+    const or_gate *g;
+    const int *shifts;
+    uint8_t *out;
+    size_t out_stride;
+    uint32_t *out_len;
+    int *rc;
+} batch_job;
+
+static void *batch_worker(void *arg)
+{
+    batch_job *b = arg;
+    uint64_t nm = 1ull << b->h;
+    const uint8_t *ptrs[16];
+    for (uint64_t i = (uint64_t)b->k; i < b->nitems; i += (uint64_t)b->threads) {
+        for (uint64_t j = 0; j < nm; ++j) ptrs[j] = b->in_buf + b->in_off[i * nm + j];
+        b->rc[i] = or_item_sweep(b->n, b->c, b->H, b->h, b->bases[i], ptrs, b->in_len + i * nm,
+                                 b->alpha, b->g, b->ng, b->shifts, b->nlev, b->max_bytes,
+                                 b->out + i * b->out_stride, b->out_stride, b->out_len + i * nm);
+    }
+    return NULL;
+}
+
+int or_item_sweep_batch(int n, int c, const int *H, int h, uint64_t nitems, const uint64_t *bases,
+                        const uint8_t *in_buf, const uint64_t *in_off, const uint32_t *in_len,
+                        double alpha, const or_gate *g, int ng, const int *shifts, int nlev,
+                        uint64_t max_bytes, uint8_t *out, size_t out_stride, uint32_t *out_len,
+                        int *rc, int threads)
+{
+    if (h < 0 || h > 4) return -1;
+    if (threads < 1) threads = 1;
+    if (threads > 256) threads = 256;
+    batch_job jobs[256];
+    pthread_t tid[256];
+    int started[256];
+    for (int k = 0; k < threads; ++k) {
+        batch_job b = {n, c, h, ng, nlev, threads, k, H, nitems, max_bytes, bases, in_off, in_buf,
+                       in_len, alpha, g, shifts, out, out_stride, out_len, rc};
+        jobs[k] = b;
+        started[k] = k > 0 && pthread_create(&tid[k], NULL, batch_worker, &jobs[k]) == 0;
+    }
+    batch_worker(&jobs[0]);
+    for (int k = 1; k < threads; ++k) {
+        if (started[k]) pthread_join(tid[k], NULL);
+        else batch_worker(&jobs[k]);          /* no thread could start: run its share here */
+    }
+    int bad = 0;
+    for (uint64_t i = 0; i < nitems; ++i) bad += rc[i] != 0;
+    return bad;
 }
 
 static int cmp_u64(const void *a, const void *b)

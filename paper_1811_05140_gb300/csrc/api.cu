@@ -37,13 +37,13 @@ cudaError_t launch_unit_level(const unsigned long long *bytes, uint8_t *level, u
 cudaError_t launch_norm_from_parts(const unsigned long long *part, unsigned long long ntiles,
                                    DevScalars *scal, int grid, cudaStream_t st);
 cudaError_t launch_sizes(const uint8_t *arena, const unsigned long long *table,
-                         unsigned long long first, unsigned long long count,
+                         unsigned long long first, unsigned long long count, const unsigned long long *list,
                          unsigned long long *sizes, int grid, cudaStream_t st);
 cudaError_t launch_sum_sizes(const uint8_t *arena, const unsigned long long *table,
                              unsigned long long ntiles, unsigned long long *total, int grid,
                              cudaStream_t st);
 cudaError_t launch_gather(const uint8_t *arena, const unsigned long long *table,
-                          unsigned long long first, unsigned long long count,
+                          unsigned long long first, unsigned long long count, const unsigned long long *list,
                           const unsigned long long *offs, const unsigned long long *sizes,
                           uint8_t *out, int grid, cudaStream_t st);
 cudaError_t launch_validate(const uint8_t *buf, const unsigned long long *offs,
@@ -60,6 +60,7 @@ cudaError_t launch_amplitudes(const uint8_t *arena, const unsigned long long *ta
 cudaError_t launch_probs(const uint8_t *arena, const unsigned long long *table, int c,
                          unsigned long long ntiles, const int *qsel, int nq,
                          unsigned long long *buckets, DevScalars *scal, int grid, cudaStream_t st);
+unsigned long long fidelity_chunk(unsigned long long ntiles);
 cudaError_t launch_fidelity(const uint8_t *arena, const unsigned long long *table, int c,
                             unsigned long long ntiles, const RefSpec &rs, Acc4 *tile_sums,
                             DevScalars *scal, int grid, cudaStream_t st);
@@ -304,6 +305,8 @@ struct qsim_state {
     unsigned long long *unit_bytes = nullptr;   // per stride and level: stream bytes
     uint8_t *unit_level = nullptr;        // per stride: chosen level
     unsigned long long units_cap = 0;
+    void *rd = nullptr;                   // read-out scratch (probabilities, fidelity, sizes)
+    size_t rd_cap = 0;
 };
 
 namespace {
@@ -394,8 +397,30 @@ qsim_status ensure_units(qsim_t h, unsigned long long nunits) {
     return QSIM_OK;
 }
 
+// cudaMemcpyAsync that counts the bytes a handle moves between host and
+// device (qsim_stats_t h2d_bytes / d2h_bytes).
+cudaError_t hcopy(qsim_t h, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind, cudaStream_t st) {
+    if (kind == cudaMemcpyHostToDevice) h->st.h2d_bytes += bytes;
+    else if (kind == cudaMemcpyDeviceToHost) h->st.d2h_bytes += bytes;
+    return cudaMemcpyAsync(dst, src, bytes, kind, st);
+}
+
+// Device scratch of the read-outs, kept by the handle and grown on demand,
+// so that repeated read-outs allocate nothing.
+qsim_status ensure_readout(qsim_t h, size_t bytes) {
+    if (h->rd_cap >= bytes) return QSIM_OK;
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->rd) cudaFree(h->rd);
+    h->rd = nullptr;
+    h->rd_cap = 0;
+    const size_t cap = std::max<size_t>(round_up(bytes, 4096), 65536);
+    CK(cudaMalloc(&h->rd, cap));
+    h->rd_cap = cap;
+    return QSIM_OK;
+}
+
 qsim_status read_scalars(qsim_t h) {
-    CK(cudaMemcpyAsync(h->hscal, h->scal, sizeof(qs::DevScalars), cudaMemcpyDeviceToHost, h->stream));
+    CK(hcopy(h, h->hscal, h->scal, sizeof(qs::DevScalars), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return QSIM_OK;
 }
@@ -403,7 +428,7 @@ qsim_status read_scalars(qsim_t h) {
 qsim_status clear_pass_state(qsim_t h) {
     // err, err_sweep, bump and the running norm restart from zero
     qs::DevScalars z{};
-    CK(cudaMemcpyAsync(&h->scal->bump, &z.bump, sizeof z.bump, cudaMemcpyHostToDevice, h->stream));
+    CK(hcopy(h, &h->scal->bump, &z.bump, sizeof z.bump, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemsetAsync(&h->scal->err, 0, 2 * sizeof(unsigned), h->stream));
     CK(cudaMemsetAsync(&h->scal->acc_lo, 0, 2 * sizeof(unsigned long long), h->stream));
     return QSIM_OK;
@@ -624,9 +649,7 @@ qsim_status qsim_create(qsim_t *out, int n_qubits, int block_log2, qsim_codec co
     auto bail = [&](qsim_status code) { qsim_destroy(h); return code; };
     if (cudaGetDevice(&h->device) != cudaSuccess) return bail(fail(nullptr, QSIM_ERR_CUDA, "cudaGetDevice failed"));
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
-    static std::once_flag configured;
-    static cudaError_t config_err = cudaSuccess;
-    std::call_once(configured, [] { config_err = qs::configure_kernels(); });
+    const cudaError_t config_err = qs::configure_kernels();     // once per device
     if (config_err != cudaSuccess)
         return bail(fail(nullptr, QSIM_ERR_CUDA, "kernel setup: %s", cudaGetErrorString(config_err)));
     if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess)
@@ -661,6 +684,7 @@ qsim_status qsim_destroy(qsim_t h) {
     if (h->hused) cudaFreeHost(h->hused);
     if (h->unit_bytes) cudaFree(h->unit_bytes);
     if (h->unit_level) cudaFree(h->unit_level);
+    if (h->rd) cudaFree(h->rd);
     for (cudaEvent_t ev : h->events) cudaEventDestroy(ev);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
@@ -686,7 +710,7 @@ qsim_status qsim_set_pool(qsim_t h, void *dev_ptr, size_t bytes) {
         const unsigned long long cap = std::max<unsigned long long>(round_up(h->used, 1ull << 21), 1ull << 22);
         uint8_t *own = nullptr;
         CK(cudaMalloc(&own, cap));
-        cudaError_t e = cudaMemcpyAsync(own, h->arena[h->cur], h->used, cudaMemcpyDeviceToDevice, h->stream);
+        cudaError_t e = hcopy(h, own, h->arena[h->cur], h->used, cudaMemcpyDeviceToDevice, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) { cudaFree(own); return fail(h, QSIM_ERR_CUDA, "set_pool: %s", cudaGetErrorString(e)); }
         h->arena[h->cur] = own;
@@ -707,7 +731,7 @@ qsim_status qsim_set_pool(qsim_t h, void *dev_ptr, size_t bytes) {
     if (half < h->used || half < 4096) return fail(h, QSIM_ERR_ARG, "pool of %zu bytes cannot hold the state (%llu bytes per arena)", bytes, h->used);
     uint8_t *base = static_cast<uint8_t *>(dev_ptr);
     uint8_t *dst = base + (h->cur ? half : 0);
-    CK(cudaMemcpyAsync(dst, h->arena[h->cur], h->used, cudaMemcpyDeviceToDevice, h->stream));
+    CK(hcopy(h, dst, h->arena[h->cur], h->used, cudaMemcpyDeviceToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     if (!h->pool)
         for (int i = 0; i < 2; ++i)
@@ -741,7 +765,7 @@ qsim_status qsim_set_amplitudes(qsim_t h, const double *amps) {
     size_t bytes = (size_t)16 << h->n;
     double2 *d = nullptr;
     CK(cudaMalloc(&d, bytes));
-    cudaError_t e = cudaMemcpyAsync(d, amps, bytes, cudaMemcpyHostToDevice, h->stream);
+    cudaError_t e = hcopy(h, d, amps, bytes, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) s = encode_fresh(h, d, 0);
     cudaStreamSynchronize(h->stream);
     cudaFree(d);
@@ -875,8 +899,8 @@ qsim_status stage_flush(qsim_t h, FlushCtx &fc, cudaStream_t st) {
     for (size_t si = 0; si < ns; ++si)
         for (int gi = fc.sweeps[si].lo; gi < fc.sweeps[si].hi; ++gi)
             prepare_gate(h->queue[gi], h->c, fc.sweeps[si], h->hgates[gi], h->hsg[gi]);
-    CK(cudaMemcpyAsync(h->dgates, h->hgates, ng * sizeof(qs::DGate), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(h->dsg, h->hsg, ng * sizeof(qs::SGate), cudaMemcpyHostToDevice, st));
+    CK(hcopy(h, h->dgates, h->hgates, ng * sizeof(qs::DGate), cudaMemcpyHostToDevice, st));
+    CK(hcopy(h, h->dsg, h->hsg, ng * sizeof(qs::SGate), cudaMemcpyHostToDevice, st));
     if (h->profiling) {
         while (h->events.size() < 2 * ns) {
             cudaEvent_t ev;
@@ -958,12 +982,12 @@ qsim_status run_from(qsim_t h, FlushCtx &fc, size_t k) {
                 h->hparams[ns + j].unit_bytes = h->unit_bytes;
             }
         }
-        CK(cudaMemcpyAsync(h->dparams + k, h->hparams + k, (ns - k) * sizeof(qs::SweepParams),
+        CK(hcopy(h, h->dparams + k, h->hparams + k, (ns - k) * sizeof(qs::SweepParams),
                            cudaMemcpyHostToDevice, h->stream));
         if (ut)
-            CK(cudaMemcpyAsync(h->dparams + ns + k, h->hparams + ns + k, (ns - k) * sizeof(qs::SweepParams),
+            CK(hcopy(h, h->dparams + ns + k, h->hparams + ns + k, (ns - k) * sizeof(qs::SweepParams),
                                cudaMemcpyHostToDevice, h->stream));
-        CK(cudaMemcpyAsync(h->distart + 2 * k, h->histart + 2 * k, 2 * (ns - k) * sizeof(unsigned long long),
+        CK(hcopy(h, h->distart + 2 * k, h->histart + 2 * k, 2 * (ns - k) * sizeof(unsigned long long),
                            cudaMemcpyHostToDevice, h->stream));
         for (size_t j = k; j < ns; ++j) {
             const int mb = h->c + fc.sweeps[j].h;
@@ -1013,7 +1037,7 @@ qsim_status run_from(qsim_t h, FlushCtx &fc, size_t k) {
 // Bookkeeping after every pass of a flush has succeeded.
 qsim_status finish_flush(qsim_t h, FlushCtx &fc, bool timed) {
     const size_t ns = fc.ns;
-    CK(cudaMemcpyAsync(h->hused, h->used_hist, ns * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+    CK(hcopy(h, h->hused, h->used_hist, ns * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->cur = fc.cur0 ^ (int)(ns & 1);
     h->used = h->hscal->used;
@@ -1328,7 +1352,7 @@ qsim_status qsim_amplitudes(qsim_t h, unsigned long long start, unsigned long lo
         ++h->launches;
         cudaError_t e = qs::launch_amplitudes(h->arena[h->cur], h->table[h->cur], h->c, start + done, cnt, d,
                                               h->scal, grid_for(h, tiles, 4), h->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(out + 2 * done, d, cnt * 16, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = hcopy(h, out + 2 * done, d, cnt * 16, cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) { cudaFree(d); return fail(h, QSIM_ERR_CUDA, "amplitudes: %s", cudaGetErrorString(e)); }
         done += cnt;
@@ -1350,19 +1374,16 @@ qsim_status qsim_probabilities(qsim_t h, const int *qubits, int nq, double *out)
     }
     if ((s = qsim_flush(h)) != QSIM_OK) return s;
     const size_t nb = (size_t)1 << nq;
-    unsigned long long *dbk = nullptr;
-    int *dq = nullptr;
-    CK(cudaMalloc(&dbk, nb * 16));
-    CK(cudaMalloc(&dq, 32 * sizeof(int)));
+    if ((s = ensure_readout(h, nb * 16 + 32 * sizeof(int))) != QSIM_OK) return s;
+    unsigned long long *dbk = static_cast<unsigned long long *>(h->rd);
+    int *dq = reinterpret_cast<int *>(dbk + 2 * nb);
     std::vector<unsigned long long> hb(2 * nb);
     cudaError_t e = cudaMemsetAsync(dbk, 0, nb * 16, h->stream);
-    if (e == cudaSuccess && nq) e = cudaMemcpyAsync(dq, qubits, nq * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && nq) e = hcopy(h, dq, qubits, nq * sizeof(int), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) ++h->launches, e = qs::launch_probs(h->arena[h->cur], h->table[h->cur], h->c, h->ntiles, dq, nq, dbk,
                                                h->scal, grid_for(h, h->ntiles, 4), h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), dbk, nb * 16, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = hcopy(h, hb.data(), dbk, nb * 16, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    cudaFree(dbk);
-    cudaFree(dq);
     if (e != cudaSuccess) return fail(h, QSIM_ERR_CUDA, "probabilities: %s", cudaGetErrorString(e));
     unsigned __int128 tot = 0;
     for (size_t j = 0; j < nb; ++j) tot += ((unsigned __int128)hb[2 * j + 1] << 64) | hb[2 * j];
@@ -1417,7 +1438,7 @@ qsim_status qsim_fidelity(qsim_t h, const qsim_ref *ref, double *F, double *over
         case QSIM_REF_DENSE_HOST:
             if (!ref->dense) return fail(h, QSIM_ERR_ARG, "dense is NULL");
             CK(cudaMalloc(&tmp, N * 16));
-            CK(cudaMemcpyAsync(tmp, ref->dense, N * 16, cudaMemcpyHostToDevice, h->stream));
+            CK(hcopy(h, tmp, ref->dense, N * 16, cudaMemcpyHostToDevice, h->stream));
             rs.kind = 3;
             rs.dense = tmp;
             break;
@@ -1429,23 +1450,24 @@ qsim_status qsim_fidelity(qsim_t h, const qsim_ref *ref, double *F, double *over
         default:
             return fail(h, QSIM_ERR_ARG, "unknown reference kind");
     }
-    qs::Acc4 *a = nullptr, *b = nullptr;
-    cudaError_t e = cudaMalloc(&a, h->ntiles * sizeof(qs::Acc4));
-    if (e == cudaSuccess) e = cudaMalloc(&b, std::max<unsigned long long>(1, h->ntiles / 2) * sizeof(qs::Acc4));
-    if (e == cudaSuccess)
-        ++h->launches, e = qs::launch_fidelity(h->arena[h->cur], h->table[h->cur], h->c, h->ntiles, rs, a, h->scal,
-                                grid_for(h, h->ntiles, 4), h->stream);
-    unsigned long long cnt = h->ntiles;
+    const unsigned long long nchunks = h->ntiles / qs::fidelity_chunk(h->ntiles);
+    if ((s = ensure_readout(h, (nchunks + nchunks / 2 + 1) * sizeof(qs::Acc4))) != QSIM_OK) {
+        if (tmp) cudaFree(tmp);
+        return s;
+    }
+    qs::Acc4 *a = static_cast<qs::Acc4 *>(h->rd), *b = a + nchunks;
+    ++h->launches;
+    cudaError_t e = qs::launch_fidelity(h->arena[h->cur], h->table[h->cur], h->c, h->ntiles, rs, a, h->scal,
+                                        grid_for(h, nchunks, 4), h->stream);
+    unsigned long long cnt = nchunks;
     while (e == cudaSuccess && cnt > 1) {
         ++h->launches, e = qs::launch_pair_sum(a, b, cnt / 2, grid_for(h, cnt / 2 / qs::THREADS + 1, 8), h->stream);
         std::swap(a, b);
         cnt /= 2;
     }
     qs::Acc4 r{};
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&r, a, sizeof r, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = hcopy(h, &r, a, sizeof r, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (a) cudaFree(a);
-    if (b) cudaFree(b);
     if (tmp) cudaFree(tmp);
     if (e != cudaSuccess) return fail(h, QSIM_ERR_CUDA, "fidelity: %s", cudaGetErrorString(e));
     double f = (r.z > 0 && r.w > 0) ? (r.x * r.x + r.y * r.y) / (r.z * r.w) : 0.0;
@@ -1460,15 +1482,15 @@ qsim_status qsim_compressed_bytes(qsim_t h, unsigned long long *stream_bytes, un
     qsim_status s = check_usable(h);
     if (s != QSIM_OK) return s;
     if ((s = qsim_flush(h)) != QSIM_OK) return s;
-    unsigned long long *d = nullptr, tot = 0;
-    CK(cudaMalloc(&d, sizeof(unsigned long long)));
+    unsigned long long tot = 0;
+    if ((s = ensure_readout(h, sizeof(unsigned long long))) != QSIM_OK) return s;
+    unsigned long long *d = static_cast<unsigned long long *>(h->rd);
     cudaError_t e = cudaMemsetAsync(d, 0, sizeof *d, h->stream);
     if (e == cudaSuccess)
         ++h->launches, e = qs::launch_sum_sizes(h->arena[h->cur], h->table[h->cur], h->ntiles, d,
                                  grid_for(h, h->ntiles / qs::THREADS + 1, 8), h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, d, sizeof tot, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = hcopy(h, &tot, d, sizeof tot, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    cudaFree(d);
     if (e != cudaSuccess) return fail(h, QSIM_ERR_CUDA, "sizes: %s", cudaGetErrorString(e));
     if (stream_bytes) *stream_bytes = tot;
     if (footprint_bytes)
@@ -1495,6 +1517,56 @@ qsim_status qsim_stats(qsim_t h, qsim_stats_t *out) {
     return QSIM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Export of tiles first..first+count-1 (list null) or of the tiles in the
+// host array list[0..count-1]: sizes, then (out not null) the streams.
+qsim_status export_impl(qsim_t h, unsigned long long first, unsigned long long count,
+                        const unsigned long long *list, void *out, unsigned long long cap,
+                        unsigned long long *sizes) {
+    unsigned long long *dsz = nullptr, *doff = nullptr, *dlist = nullptr;
+    uint8_t *dbuf = nullptr;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(h->stream);
+        if (dsz) cudaFree(dsz);
+        if (doff) cudaFree(doff);
+        if (dlist) cudaFree(dlist);
+        if (dbuf) cudaFree(dbuf);
+    };
+    cudaError_t e = cudaMalloc(&dsz, count * 8);
+    if (e == cudaSuccess && list) e = cudaMalloc(&dlist, count * 8);
+    if (e == cudaSuccess && list)
+        e = hcopy(h, dlist, list, count * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        ++h->launches, e = qs::launch_sizes(h->arena[h->cur], h->table[h->cur], first, count, dlist, dsz,
+                                            grid_for(h, count / qs::THREADS + 1, 8), h->stream);
+    if (e == cudaSuccess) e = hcopy(h, sizes, dsz, count * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) { cleanup(); return fail(h, QSIM_ERR_CUDA, "export sizes: %s", cudaGetErrorString(e)); }
+    if (!out) { cleanup(); return QSIM_OK; }
+    std::vector<unsigned long long> offs(count);
+    unsigned long long tot = 0;
+    for (unsigned long long i = 0; i < count; ++i) { offs[i] = tot; tot += sizes[i]; }
+    if (tot > cap) { cleanup(); return fail(h, QSIM_ERR_ARG, "export needs %llu bytes", tot); }
+    e = cudaMalloc(&doff, count * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&dbuf, tot);
+    if (e == cudaSuccess) e = hcopy(h, doff, offs.data(), count * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        ++h->launches, e = qs::launch_gather(h->arena[h->cur], h->table[h->cur], first, count, dlist, doff, dsz,
+                                             dbuf, grid_for(h, count, 8), h->stream);
+    if (e == cudaSuccess) e = hcopy(h, out, dbuf, tot, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cleanup();
+    if (e != cudaSuccess) return fail(h, QSIM_ERR_CUDA, "export: %s", cudaGetErrorString(e));
+    return QSIM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 qsim_status qsim_export_tiles(qsim_t h, unsigned long long first, unsigned long long count, void *out,
                               unsigned long long cap, unsigned long long *sizes) {
     qsim_status s = check_usable(h);
@@ -1502,33 +1574,19 @@ qsim_status qsim_export_tiles(qsim_t h, unsigned long long first, unsigned long 
     if (!sizes || first > h->ntiles || count > h->ntiles - first) return fail(h, QSIM_ERR_ARG, "bad tile range");
     if ((s = qsim_flush(h)) != QSIM_OK) return s;
     if (count == 0) return QSIM_OK;
-    unsigned long long *dsz = nullptr, *doff = nullptr;
-    uint8_t *dbuf = nullptr;
-    CK(cudaMalloc(&dsz, count * 8));
-    ++h->launches;
-    cudaError_t e = qs::launch_sizes(h->arena[h->cur], h->table[h->cur], first, count, dsz,
-                                     grid_for(h, count / qs::THREADS + 1, 8), h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sizes, dsz, count * 8, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) { cudaFree(dsz); return fail(h, QSIM_ERR_CUDA, "export sizes: %s", cudaGetErrorString(e)); }
-    if (!out) { cudaFree(dsz); return QSIM_OK; }
-    std::vector<unsigned long long> offs(count);
-    unsigned long long tot = 0;
-    for (unsigned long long i = 0; i < count; ++i) { offs[i] = tot; tot += sizes[i]; }
-    if (tot > cap) { cudaFree(dsz); return fail(h, QSIM_ERR_ARG, "export needs %llu bytes", tot); }
-    e = cudaMalloc(&doff, count * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&dbuf, tot);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(doff, offs.data(), count * 8, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess)
-        ++h->launches, e = qs::launch_gather(h->arena[h->cur], h->table[h->cur], first, count, doff, dsz, dbuf,
-                              grid_for(h, count, 8), h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dbuf, tot, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    cudaFree(dsz);
-    if (doff) cudaFree(doff);
-    if (dbuf) cudaFree(dbuf);
-    if (e != cudaSuccess) return fail(h, QSIM_ERR_CUDA, "export: %s", cudaGetErrorString(e));
-    return QSIM_OK;
+    return export_impl(h, first, count, nullptr, out, cap, sizes);
+}
+
+qsim_status qsim_export_tile_set(qsim_t h, const unsigned long long *tiles, unsigned long long count,
+                                 void *out, unsigned long long cap, unsigned long long *sizes) {
+    qsim_status s = check_usable(h);
+    if (s != QSIM_OK) return s;
+    if (!sizes || (count && !tiles)) return fail(h, QSIM_ERR_ARG, "null argument");
+    for (unsigned long long i = 0; i < count; ++i)
+        if (tiles[i] >= h->ntiles) return fail(h, QSIM_ERR_ARG, "tile %llu out of range", tiles[i]);
+    if ((s = qsim_flush(h)) != QSIM_OK) return s;
+    if (count == 0) return QSIM_OK;
+    return export_impl(h, 0, count, tiles, out, cap, sizes);
 }
 
 qsim_status qsim_import_tiles(qsim_t h, unsigned long long first, unsigned long long count, const void *data,
@@ -1555,11 +1613,11 @@ qsim_status qsim_import_tiles(qsim_t h, unsigned long long first, unsigned long 
     if (e == cudaSuccess) e = cudaMalloc(&dparts, count * 16);
     if (e == cudaSuccess) e = cudaMalloc(&dbad, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemsetAsync(dbad, 0, sizeof(unsigned), h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dbuf, data, tot, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(doff, offs.data(), count * 8, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dsz, sizes, count * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = hcopy(h, dbuf, data, tot, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = hcopy(h, doff, offs.data(), count * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = hcopy(h, dsz, sizes, count * 8, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) ++h->launches, e = qs::launch_validate(dbuf, doff, dsz, count, h->c, dparts, dbad, grid_for(h, count, 4), h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, dbad, sizeof hbad, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = hcopy(h, &hbad, dbad, sizeof hbad, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     auto cleanup = [&]() {
         cudaStreamSynchronize(h->stream);
@@ -1577,7 +1635,7 @@ qsim_status qsim_import_tiles(qsim_t h, unsigned long long first, unsigned long 
         uint8_t *na = nullptr;
         unsigned long long nc = round_up(need + need / 4, 1ull << 21);
         e = cudaMalloc(&na, nc);
-        if (e == cudaSuccess && h->used) e = cudaMemcpyAsync(na, h->arena[h->cur], h->used, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess && h->used) e = hcopy(h, na, h->arena[h->cur], h->used, cudaMemcpyDeviceToDevice, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) { if (na) cudaFree(na); cleanup(); return fail(h, QSIM_ERR_OOM, "import: %s", cudaGetErrorString(e)); }
         cudaFree(h->arena[h->cur]);

@@ -11,6 +11,7 @@
 //   * the codec is integer-only; the norm is an exact fixed-point sum.
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <mutex>
 
 #include "qsim_dev.cuh"
 
@@ -1877,13 +1878,15 @@ __global__ void norm_from_parts_kernel(const unsigned long long *part, unsigned 
     if ((threadIdx.x & 31) == 0 && (lo | hi)) atomic_add128(&scal->acc_lo, &scal->acc_hi, lo, hi);
 }
 
-// Stream sizes of tiles first..first+count-1
+// Stream sizes of tiles first..first+count-1, or of tiles list[0..count-1]
+// when list is not null
 __global__ void sizes_kernel(const uint8_t *arena, const unsigned long long *table,
                              unsigned long long first, unsigned long long count,
-                             unsigned long long *sizes) {
+                             const unsigned long long *list, unsigned long long *sizes) {
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < count;
          i += (unsigned long long)gridDim.x * blockDim.x) {
-        const uint32_t *h = reinterpret_cast<const uint32_t *>(arena + table[first + i]);
+        const unsigned long long t = list ? list[i] : first + i;
+        const uint32_t *h = reinterpret_cast<const uint32_t *>(arena + table[t]);
         sizes[i] = HDR + (unsigned long long)h[1];
     }
 }
@@ -1901,13 +1904,15 @@ __global__ void sum_sizes_kernel(const uint8_t *arena, const unsigned long long 
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(total, s);
 }
 
-// Gather streams into a contiguous buffer at the given offsets
+// Gather streams (tiles first.., or list[i] when list is not null) into a
+// contiguous buffer at the given offsets
 __global__ void gather_kernel(const uint8_t *arena, const unsigned long long *table,
                               unsigned long long first, unsigned long long count,
-                              const unsigned long long *offs, const unsigned long long *sizes,
-                              uint8_t *out) {
+                              const unsigned long long *list, const unsigned long long *offs,
+                              const unsigned long long *sizes, uint8_t *out) {
     for (unsigned long long i = blockIdx.x; i < count; i += gridDim.x) {
-        const uint4 *s = reinterpret_cast<const uint4 *>(arena + table[first + i]);
+        const unsigned long long t = list ? list[i] : first + i;
+        const uint4 *s = reinterpret_cast<const uint4 *>(arena + table[t]);
         uint4 *d = reinterpret_cast<uint4 *>(out + offs[i]);
         for (unsigned long long j = threadIdx.x; j < sizes[i] / 16; j += blockDim.x) d[j] = s[j];
     }
@@ -1981,16 +1986,27 @@ __global__ void __launch_bounds__(32 * TILE_WARPS) amplitudes_kernel(
 }
 
 // Exact per-outcome sums of |a|^2: bucket j gathers bit i of j from qubit qs[i].
+// With at most PROBS_SMEM_BUCKETS buckets each CTA sums into shared-memory
+// 128-bit buckets (integer adds, so the order does not matter) and adds
+// them to the global buckets once at the end; larger bucket counts add
+// straight into global memory.
+constexpr int PROBS_SMEM_BUCKETS = 1024;
 __global__ void __launch_bounds__(32 * TILE_WARPS) probs_kernel(
     const uint8_t *arena, const unsigned long long *table, int c, unsigned long long ntiles,
     const int *qs, int nq, unsigned long long *buckets, DevScalars *scal) {
     extern __shared__ double smem[];
     __shared__ int sq[32];
+    __shared__ unsigned long long sb[2 * PROBS_SMEM_BUCKETS];
     const int N = 1 << c;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double *re = smem + (size_t)warp * 2 * N, *im = re + N;
+    const int nb = 1 << nq;
+    const bool local = nb <= PROBS_SMEM_BUCKETS;
     if (threadIdx.x < nq) sq[threadIdx.x] = qs[threadIdx.x];
+    if (local)
+        for (int i = threadIdx.x; i < 2 * nb; i += blockDim.x) sb[i] = 0ull;
     __syncthreads();
+    unsigned long long *dst = local ? sb : buckets;
     for (unsigned long long t = (unsigned long long)blockIdx.x * TILE_WARPS + warp; t < ntiles;
          t += (unsigned long long)gridDim.x * TILE_WARPS) {
         if (wdecode(arena + table[t], c, re, im, 1.0, false) && lane == 0) atomicOr(&scal->err, ERR_FORMAT);
@@ -2004,24 +2020,35 @@ __global__ void __launch_bounds__(32 * TILE_WARPS) probs_kernel(
             sq_units(dbits(re[i]), l0, h0, rng);
             sq_units(dbits(im[i]), l1, h1, rng);
             add128(l0, h0, l1, h1);
-            if (l0 | h0) atomic_add128(&buckets[2 * j], &buckets[2 * j + 1], l0, h0);
+            if (l0 | h0) atomic_add128(&dst[2 * j], &dst[2 * j + 1], l0, h0);
         }
         __syncwarp();
     }
+    if (local) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < nb; i += blockDim.x)
+            if (sb[2 * i] | sb[2 * i + 1]) atomic_add128(&buckets[2 * i], &buckets[2 * i + 1], sb[2 * i], sb[2 * i + 1]);
+    }
 }
 
-// Fidelity partials per tile: <ref|psi> (re, im), <psi|psi>, <ref|ref>,
-// each summed over the tile in a fixed order (lane chunks, then a
-// pairwise shuffle tree).
+// Fidelity partials: <ref|psi> (re, im), <psi|psi>, <ref|ref>, each summed
+// over a tile in a fixed order (lane chunks, then a pairwise shuffle tree),
+// then over chunks of `chunk` consecutive tiles (a power of two, at most
+// FID_CHUNK) by the same pairwise tree in shared memory: chunk_sums[q] is
+// the subtree of tiles q*chunk .. q*chunk+chunk-1, so finishing the tree
+// over the chunk sums gives the perfect binary tree over all tiles.
+constexpr int FID_CHUNK = 1024;
 __global__ void __launch_bounds__(32 * TILE_WARPS) fidelity_kernel(
     const uint8_t *arena, const unsigned long long *table, int c, unsigned long long ntiles,
-    RefSpec rs, Acc4 *tile_sums, DevScalars *scal) {
+    int chunk, RefSpec rs, Acc4 *chunk_sums, DevScalars *scal) {
     extern __shared__ double smem[];
+    __shared__ Acc4 ssum[FID_CHUNK];
     const int N = 1 << c;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double *re = smem + (size_t)warp * 4 * N, *im = re + N, *rre = re + 2 * N, *rim = re + 3 * N;
-    for (unsigned long long t = (unsigned long long)blockIdx.x * TILE_WARPS + warp; t < ntiles;
-         t += (unsigned long long)gridDim.x * TILE_WARPS) {
+    const unsigned long long nchunks = ntiles / (unsigned long long)chunk;
+    for (unsigned long long ck = blockIdx.x; ck < nchunks; ck += gridDim.x) {
+    for (unsigned long long t = ck * chunk + warp; t < (ck + 1) * chunk; t += TILE_WARPS) {
         int bad = wdecode(arena + table[t], c, re, im, 1.0, false);
         if (rs.kind == 0) bad |= wdecode(rs.o_arena + rs.o_table[t], c, rre, rim, 1.0, false);
         if (bad && lane == 0) atomicOr(&scal->err, ERR_FORMAT);
@@ -2060,8 +2087,19 @@ __global__ void __launch_bounds__(32 * TILE_WARPS) fidelity_kernel(
             const double bz = __shfl_down_sync(FULL, acc.z, o), bw = __shfl_down_sync(FULL, acc.w, o);
             if ((lane & (2 * o - 1)) == 0) { acc.x += bx; acc.y += by; acc.z += bz; acc.w += bw; }
         }
-        if (lane == 0) tile_sums[t] = acc;
+        if (lane == 0) ssum[t - ck * chunk] = acc;
         __syncwarp();
+    }
+    __syncthreads();
+    for (int w = 1; w < chunk; w <<= 1) {
+        for (int i = threadIdx.x * 2 * w; i < chunk; i += blockDim.x * 2 * w) {
+            const Acc4 x = ssum[i], y = ssum[i + w];
+            ssum[i] = make_acc4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) chunk_sums[ck] = ssum[0];
+    __syncthreads();
     }
 }
 
@@ -2142,9 +2180,9 @@ cudaError_t launch_norm_from_parts(const unsigned long long *part, unsigned long
 }
 
 cudaError_t launch_sizes(const uint8_t *arena, const unsigned long long *table,
-                         unsigned long long first, unsigned long long count,
+                         unsigned long long first, unsigned long long count, const unsigned long long *list,
                          unsigned long long *sizes, int grid, cudaStream_t st) {
-    sizes_kernel<<<grid, THREADS, 0, st>>>(arena, table, first, count, sizes);
+    sizes_kernel<<<grid, THREADS, 0, st>>>(arena, table, first, count, list, sizes);
     return cudaGetLastError();
 }
 
@@ -2156,10 +2194,10 @@ cudaError_t launch_sum_sizes(const uint8_t *arena, const unsigned long long *tab
 }
 
 cudaError_t launch_gather(const uint8_t *arena, const unsigned long long *table,
-                          unsigned long long first, unsigned long long count,
+                          unsigned long long first, unsigned long long count, const unsigned long long *list,
                           const unsigned long long *offs, const unsigned long long *sizes,
                           uint8_t *out, int grid, cudaStream_t st) {
-    gather_kernel<<<grid, THREADS, 0, st>>>(arena, table, first, count, offs, sizes, out);
+    gather_kernel<<<grid, THREADS, 0, st>>>(arena, table, first, count, list, offs, sizes, out);
     return cudaGetLastError();
 }
 
@@ -2198,11 +2236,19 @@ cudaError_t launch_probs(const uint8_t *arena, const unsigned long long *table, 
     return cudaGetLastError();
 }
 
+// chunk sums land in chunk_sums[0 .. ntiles/fidelity_chunk(ntiles) - 1]
+unsigned long long fidelity_chunk(unsigned long long ntiles) {
+    return ntiles < (unsigned long long)FID_CHUNK ? ntiles : (unsigned long long)FID_CHUNK;
+}
+
 cudaError_t launch_fidelity(const uint8_t *arena, const unsigned long long *table, int c,
-                            unsigned long long ntiles, const RefSpec &rs, Acc4 *tile_sums,
+                            unsigned long long ntiles, const RefSpec &rs, Acc4 *chunk_sums,
                             DevScalars *scal, int grid, cudaStream_t st) {
-    fidelity_kernel<<<tile_grid(grid, ntiles), 32 * TILE_WARPS, tile_smem_bytes(c, 2), st>>>(
-        arena, table, c, ntiles, rs, tile_sums, scal);
+    const unsigned long long ch = fidelity_chunk(ntiles);
+    const unsigned long long nchunks = ntiles / ch;
+    const int g = (unsigned long long)grid < nchunks ? grid : (int)nchunks;
+    fidelity_kernel<<<g, 32 * TILE_WARPS, tile_smem_bytes(c, 2), st>>>(
+        arena, table, c, ntiles, (int)ch, rs, chunk_sums, scal);
     return cudaGetLastError();
 }
 
@@ -2212,7 +2258,10 @@ cudaError_t launch_pair_sum(const Acc4 *in, Acc4 *out, unsigned long long nout, 
     return cudaGetLastError();
 }
 
-cudaError_t configure_kernels() {
+// Kernel attributes of the current device (dynamic shared memory above
+// 48 KiB), set once per device: attributes apply to the device that is
+// current when they are set.
+static cudaError_t configure_current_device() {
     cudaError_t e;
     const int maxsm = (int)sweep_smem_bytes(MAX_ITEM_LOG2);
     if ((e = cudaFuncSetAttribute(sweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm))) return e;
@@ -2224,6 +2273,19 @@ cudaError_t configure_kernels() {
     if ((e = cudaFuncSetAttribute(probs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, t1))) return e;
     if ((e = cudaFuncSetAttribute(fidelity_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, t2))) return e;
     return cudaSuccess;
+}
+
+constexpr int MAX_CONFIG_DEVICES = 64;
+static std::once_flag g_config_once[MAX_CONFIG_DEVICES];
+static cudaError_t g_config_err[MAX_CONFIG_DEVICES];
+
+cudaError_t configure_kernels() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= MAX_CONFIG_DEVICES) return cudaErrorInvalidDevice;
+    std::call_once(g_config_once[dev], [dev] { g_config_err[dev] = configure_current_device(); });
+    return g_config_err[dev];
 }
 
 cudaError_t fp64_rate(int device, double *fma_per_s) {

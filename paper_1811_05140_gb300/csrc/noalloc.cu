@@ -7,6 +7,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 
 #include "qsim.h"
 #include "qsim_dev.cuh"
@@ -32,7 +33,12 @@ struct NoallocScratch {
 };
 
 constexpr int MAX_DEVICES = 64;
-NoallocScratch *g_scratch_addr[MAX_DEVICES];   // device address of the array, per device
+// Device address of the array and the set-up result, per device; each
+// device's set-up runs exactly once even when host threads race on the
+// first call (std::call_once).
+NoallocScratch *g_scratch_addr[MAX_DEVICES];
+cudaError_t g_setup_err[MAX_DEVICES];
+std::once_flag g_setup_once[MAX_DEVICES];
 
 qsim_status noalloc_fail(qsim_status code, const char *fmt, unsigned long long a = 0,
                          unsigned long long b = 0) {
@@ -76,18 +82,25 @@ extern "C" qsim_status qsim_encode_noalloc(const double *dev_amps, int n_qubits,
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES)
         return noalloc_fail(QSIM_ERR_CUDA, "qsim_encode_noalloc: no usable CUDA device");
-    // first call on this device: kernel attributes and the array's device address
-    if (!g_scratch_addr[dev]) {
-        cudaError_t e = qs::configure_kernels();
-        if (e != cudaSuccess) return noalloc_fail(QSIM_ERR_CUDA, "qsim_encode_noalloc: kernel setup failed");
-        void *ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess || !ptr)
-            return noalloc_fail(QSIM_ERR_CUDA, "qsim_encode_noalloc: cudaGetSymbolAddress failed");
-        g_scratch_addr[dev] = static_cast<NoallocScratch *>(ptr);
-    }
-    NoallocScratch *scr = g_scratch_addr[dev];
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (st) {
+        // the scratch address and the SM count below are the current device's
+        int sdev = -1;
+        if (cudaStreamGetDevice(st, &sdev) != cudaSuccess || sdev != dev)
+            return noalloc_fail(QSIM_ERR_ARG, "qsim_encode_noalloc: cuda_stream must belong to the current device");
+    }
+    // first call on this device: kernel attributes and the array's device address
+    std::call_once(g_setup_once[dev], [dev] {
+        cudaError_t e = qs::configure_kernels();
+        void *ptr = nullptr;
+        if (e == cudaSuccess) e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e == cudaSuccess && !ptr) e = cudaErrorInvalidSymbol;
+        if (e == cudaSuccess) g_scratch_addr[dev] = static_cast<NoallocScratch *>(ptr);
+        g_setup_err[dev] = e;
+    });
+    if (g_setup_err[dev] != cudaSuccess)
+        return noalloc_fail(QSIM_ERR_CUDA, "qsim_encode_noalloc: set-up (kernel attributes, scratch address) failed");
+    NoallocScratch *scr = g_scratch_addr[dev];
     int sms = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
 

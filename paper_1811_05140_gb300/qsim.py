@@ -31,7 +31,7 @@ EXPORTS = ["qsim_create", "qsim_destroy", "qsim_set_stream", "qsim_set_aalc", "q
            "qsim_profile", "qsim_encode_noalloc", "qsim_flush_batch", "qsim_server_create",
            "qsim_server_submit", "qsim_server_result", "qsim_server_wait", "qsim_server_drain",
            "qsim_server_stats", "qsim_server_destroy", "qsim_set_pool", "qsim_fp64_rate",
-           "qsim_save", "qsim_load", "qsim_set_aalc_unit"]
+           "qsim_save", "qsim_load", "qsim_set_aalc_unit", "qsim_export_tile_set"]
 
 
 class QsimError(RuntimeError):
@@ -54,7 +54,7 @@ class Stats(C.Structure):
                 ("arena_regrows", C.c_ulonglong), ("kernel_launches", C.c_ulonglong),
                 ("alpha", C.c_double),
                 ("tile_log2", C.c_int), ("hmax", C.c_int), ("depth", C.c_int),
-                ("n_qubits", C.c_int)]
+                ("n_qubits", C.c_int), ("h2d_bytes", C.c_ulonglong), ("d2h_bytes", C.c_ulonglong)]
 
 
 class Profile(C.Structure):
@@ -137,6 +137,7 @@ def load() -> C.CDLL:
         "qsim_stats": ([vp, C.POINTER(Stats)], C.c_int),
         "qsim_last_error": ([vp], C.c_char_p),
         "qsim_export_tiles": ([vp, u64, u64, vp, u64, u64p], C.c_int),
+        "qsim_export_tile_set": ([vp, u64p, u64, vp, u64, u64p], C.c_int),
         "qsim_import_tiles": ([vp, u64, u64, vp, u64p], C.c_int),
         "qsim_plan_sweeps": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, ip, ip, dp, ip, ip,
                               ip, C.c_int], C.c_int),
@@ -205,13 +206,16 @@ def fp64_rate(device: int = 0) -> float:
 
 
 def encode_noalloc(dev_amps: int, n: int, tile_log2: int, eps: float, dev_out: int,
-                   out_cap: int, dev_table: int, stream=None) -> int:
-    """qsim_encode_noalloc on device pointers; returns the stream bytes used."""
+                   out_cap: int, dev_table: int, stream=None, check: bool = True):
+    """qsim_encode_noalloc on device pointers; returns the stream bytes used
+    (check=False: returns (status, bytes used or needed) without raising)."""
     L = load()
     used = C.c_ulonglong()
     ptr = getattr(stream, "cuda_stream", stream)
     st = L.qsim_encode_noalloc(C.c_void_p(dev_amps), n, tile_log2, eps, C.c_void_p(dev_out),
                                out_cap, C.c_void_p(dev_table), C.byref(used), C.c_void_p(ptr or 0))
+    if not check:
+        return st, used.value
     if st != 0:
         raise QsimError(st, L.qsim_last_error(None).decode())
     return used.value
@@ -420,6 +424,33 @@ class State:
         for i in range(count):
             out.append(raw[off:off + sizes[i]])
             off += sizes[i]
+        return out
+
+    def export_tile_set_raw(self, tiles) -> tuple[bytes, list[int]]:
+        """Streams of the listed tiles (any order, repeats allowed),
+        concatenated in list order, and their sizes."""
+        count = len(tiles)
+        if count == 0:
+            return b"", []
+        lst = np.ascontiguousarray(np.asarray(tiles, dtype=np.uint64))
+        u64p = C.POINTER(C.c_ulonglong)
+        sizes = np.zeros(count, dtype=np.uint64)
+        self._check(self._L.qsim_export_tile_set(self.h, lst.ctypes.data_as(u64p), count, None, 0,
+                                                 sizes.ctypes.data_as(u64p)))
+        total = int(sizes.sum())
+        buf = np.zeros(max(1, total), dtype=np.uint8)
+        self._check(self._L.qsim_export_tile_set(self.h, lst.ctypes.data_as(u64p), count,
+                                                 buf.ctypes.data_as(C.c_void_p), total,
+                                                 sizes.ctypes.data_as(u64p)))
+        return buf[:total].tobytes(), [int(v) for v in sizes]
+
+    def export_tile_set(self, tiles) -> list[bytes]:
+        """Streams of the listed tiles (any order, repeats allowed)."""
+        raw, sizes = self.export_tile_set_raw(tiles)
+        out, off = [], 0
+        for sz in sizes:
+            out.append(raw[off:off + sz])
+            off += sz
         return out
 
     def import_tiles(self, first: int, streams):

@@ -71,3 +71,94 @@ def test_noalloc_rejects_states_beyond_its_scratch():
         qsim.encode_noalloc(16, 24, 10, 1e-4, 16, 1 << 20, 16)     # 2^14 tiles > 4096
     assert e.value.status == 1
     assert "static scratch" in e.value.message
+
+
+def encode_twice_compare(n, c, eps, psis):
+    import torch
+    ntiles = 1 << (n - c)
+    cap = ntiles * (32 + (16 << c))
+    out = torch.zeros(cap, dtype=torch.uint8, device="cuda")
+    table = torch.zeros(ntiles, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    free = []
+    for psi in psis:
+        dev = torch.from_numpy(psi.view(np.float64).copy()).to("cuda")
+        torch.cuda.synchronize()
+        used = qsim.encode_noalloc(dev.data_ptr(), n, c, eps, out.data_ptr(), cap, table.data_ptr(), stream)
+        torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
+        got = streams_from(out.cpu().numpy(), table.cpu().numpy())
+        want = regular_streams(psi, n, c, eps)
+        assert used == sum(len(s) for s in want)
+        assert got == want
+        del dev
+    return free
+
+
+def test_noalloc_at_its_tile_limit_allocates_nothing():
+    # exactly 4096 tiles (n - tile_log2 = 12), the largest state the static
+    # scratch serves; the device's free memory is the same after a second
+    # call as after the first (the call itself allocates nothing: any
+    # difference would be memory the library took)
+    import torch
+    n, c, eps = 20, 8, 1e-4
+    a = I.random_state(n, 7)
+    b = np.exp(2j * np.pi * np.arange(1 << n) / (1 << n)) / np.sqrt(1 << n)
+    ntiles = 1 << (n - c)
+    cap = ntiles * (32 + (16 << c))
+    out = torch.zeros(cap, dtype=torch.uint8, device="cuda")
+    table = torch.zeros(ntiles, dtype=torch.int64, device="cuda")
+    da = torch.from_numpy(a.view(np.float64).copy()).to("cuda")
+    db = torch.from_numpy(b.view(np.float64).copy()).to("cuda")
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    qsim.encode_noalloc(da.data_ptr(), n, c, eps, out.data_ptr(), cap, table.data_ptr(), stream)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    used = qsim.encode_noalloc(db.data_ptr(), n, c, eps, out.data_ptr(), cap, table.data_ptr(), stream)
+    torch.cuda.synchronize()
+    free2 = torch.cuda.mem_get_info()[0]
+    assert free2 == free1
+    got = streams_from(out.cpu().numpy(), table.cpu().numpy())
+    want = regular_streams(b, n, c, eps)
+    assert used == sum(len(s) for s in want) and got == want
+    # and twice in a row at the limit against the regular path
+    encode_twice_compare(n, c, eps, [b, a])
+
+
+def test_noalloc_reports_the_size_it_needs_then_fits():
+    # out_cap too small: ERR_ARG with the bytes needed in *stream_bytes;
+    # a second call with exactly that capacity gives the regular streams
+    import torch
+    n, c, eps = 14, 8, 1e-4
+    psi = I.random_state(n, 4321)
+    want = regular_streams(psi, n, c, eps)
+    need = sum(len(s) for s in want)
+    ntiles = 1 << (n - c)
+    dev = torch.from_numpy(psi.view(np.float64).copy()).to("cuda")
+    table = torch.zeros(ntiles, dtype=torch.int64, device="cuda")
+    small = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    st, used = qsim.encode_noalloc(dev.data_ptr(), n, c, eps, small.data_ptr(), 64, table.data_ptr(),
+                                   torch.cuda.current_stream(), check=False)
+    assert st == 1 and used == need
+    out = torch.zeros(used, dtype=torch.uint8, device="cuda")
+    got_used = qsim.encode_noalloc(dev.data_ptr(), n, c, eps, out.data_ptr(), used, table.data_ptr(),
+                                   torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert got_used == need
+    assert streams_from(out.cpu().numpy(), table.cpu().numpy()) == want
+
+
+def test_noalloc_rejects_a_non_finite_amplitude():
+    import torch
+    n, c = 12, 8
+    psi = I.random_state(n, 11)
+    psi[100] = complex(float("nan"), 0.0)
+    ntiles = 1 << (n - c)
+    cap = ntiles * (32 + (16 << c))
+    dev = torch.from_numpy(psi.view(np.float64).copy()).to("cuda")
+    out = torch.zeros(cap, dtype=torch.uint8, device="cuda")
+    table = torch.zeros(ntiles, dtype=torch.int64, device="cuda")
+    st, _ = qsim.encode_noalloc(dev.data_ptr(), n, c, 1e-4, out.data_ptr(), cap, table.data_ptr(),
+                                torch.cuda.current_stream(), check=False)
+    assert st == 4
