@@ -273,8 +273,8 @@ typedef struct {
     unsigned long long kernel_launches; /* kernels launched by the handle */
     double alpha;                      /* scale of the next normalize step */
     int tile_log2, hmax, depth, n_qubits;
-    unsigned long long h2d_bytes;      /* bytes the handle's calls copied host -> device */
-    unsigned long long d2h_bytes;      /* bytes the handle's calls copied device -> host */
+    unsigned long long h2d_bytes;      /* bytes the handle's calls copied host -> device since creation */
+    unsigned long long d2h_bytes;      /* bytes the handle's calls copied device -> host since creation */
 } qsim_stats_t;
 
 qsim_status qsim_stats(qsim_t h, qsim_stats_t *out);

@@ -84,6 +84,7 @@ def lib():
         L.or_csim_reset_basis.argtypes = [C.c_void_p, C.c_uint64]
         L.or_csim_set_unit.argtypes = [C.c_void_p, C.c_int, C.c_uint64]
         L.or_csim_set_unit.restype = C.c_int
+        L.or_csim_set_fuse.argtypes = [C.c_void_p, C.c_int]
         L.or_csim_set_dense.argtypes = [C.c_void_p, dp]
         L.or_csim_sweep.argtypes = [C.c_void_p, C.POINTER(OrGate), C.c_int, ip, C.c_int]
         L.or_csim_sweep.restype = C.c_int
@@ -92,17 +93,17 @@ def lib():
         L.or_csim_sweep_sample.restype = C.c_int
         L.or_item_sweep.argtypes = [C.c_int, C.c_int, ip, C.c_int, C.c_uint64,
                                     C.POINTER(C.c_void_p), C.POINTER(C.c_uint32), C.c_double,
-                                    C.POINTER(OrGate), C.c_int, ip, C.c_int, C.c_uint64, u8p,
+                                    C.POINTER(OrGate), C.c_int, ip, C.c_int, C.c_uint64, C.c_int, u8p,
                                     C.c_size_t, C.POINTER(C.c_uint32)]
         L.or_item_sweep.restype = C.c_int
         L.or_item_sweep_batch.argtypes = [C.c_int, C.c_int, ip, C.c_int, C.c_uint64, u64p, u8p, u64p,
                                           C.POINTER(C.c_uint32), C.c_double, C.POINTER(OrGate), C.c_int,
-                                          ip, C.c_int, C.c_uint64, u8p, C.c_size_t,
+                                          ip, C.c_int, C.c_uint64, C.c_int, u8p, C.c_size_t,
                                           C.POINTER(C.c_uint32), ip, C.c_int]
         L.or_item_sweep_batch.restype = C.c_int
         L.or_stride_sweep.argtypes = [C.c_int, C.c_int, ip, C.c_int, C.c_int, C.c_uint64, C.c_uint64,
                                       u64p, C.POINTER(C.c_void_p), C.POINTER(C.c_uint32), C.c_uint64,
-                                      C.c_double, C.POINTER(OrGate), C.c_int, ip, C.c_int, u8p,
+                                      C.c_double, C.POINTER(OrGate), C.c_int, ip, C.c_int, C.c_int, u8p,
                                       C.c_size_t, C.POINTER(C.c_uint32)]
         L.or_stride_sweep.restype = C.c_int
         L.or_csim_dense.argtypes = [C.c_void_p, dp]
@@ -249,7 +250,7 @@ def decode_tile(stream: bytes, c: int) -> np.ndarray:
 
 
 def item_sweep(n: int, c: int, H, base_tile: int, streams, alpha: float, gates, shifts,
-               max_bytes: int | None = None):
+               max_bytes: int | None = None, fuse: bool = True):
     """One item of a sweep on its own (sampled checks of large states):
     member j is tile base_tile | bits of j at H; returns the new streams."""
     H = sorted(H)
@@ -266,7 +267,7 @@ def item_sweep(n: int, c: int, H, base_tile: int, streams, alpha: float, gates, 
     arr = gate_array(gates)
     mb = (1 << 64) - 1 if max_bytes is None else max_bytes
     rc = lib().or_item_sweep(n, c, hh, h, base_tile, ptrs, lens, alpha, arr, len(gates), sh,
-                             len(shifts), mb, out, cap, out_len)
+                             len(shifts), mb, int(bool(fuse)), out, cap, out_len)
     if rc != 0:
         raise RuntimeError(f"oracle item sweep failed ({rc})")
     res, off = [], 0
@@ -278,7 +279,7 @@ def item_sweep(n: int, c: int, H, base_tile: int, streams, alpha: float, gates, 
 
 
 def item_sweep_batch(n: int, c: int, H, bases, raw: bytes, sizes, alpha: float, gates, shifts,
-                     max_bytes: int | None = None, threads: int | None = None):
+                     max_bytes: int | None = None, threads: int | None = None, fuse: bool = True):
     """Many items of one sweep, each as item_sweep computes it, on `threads`
     host threads (default: every core).  raw holds the members' streams
     concatenated item by item (member order as in item_sweep), sizes their
@@ -310,7 +311,7 @@ def item_sweep_batch(n: int, c: int, H, bases, raw: bytes, sizes, alpha: float, 
     bad = lib().or_item_sweep_batch(
         n, c, hh, h, nitems, bs.ctypes.data_as(u64p), inb.ctypes.data_as(u8p), offs.ctypes.data_as(u64p),
         lens.ctypes.data_as(C.POINTER(C.c_uint32)), alpha, arr, len(gates), sh, len(shifts), mb,
-        out.ctypes.data_as(u8p), stride, out_len.ctypes.data_as(C.POINTER(C.c_uint32)),
+        int(bool(fuse)), out.ctypes.data_as(u8p), stride, out_len.ctypes.data_as(C.POINTER(C.c_uint32)),
         rc.ctypes.data_as(C.POINTER(C.c_int)), threads)
     if bad:
         raise RuntimeError(f"oracle item sweep failed for {bad} item(s), codes {sorted(set(rc.tolist()))}")
@@ -341,7 +342,7 @@ def stride_items_tiles(c: int, H, stride_log2: int, t0: int) -> list[int]:
 
 
 def stride_sweep(n: int, c: int, H, stride_log2: int, theta: float, t0: int, streams: dict,
-                 alpha: float, gates, shifts):
+                 alpha: float, gates, shifts, fuse: bool = True):
     """One stride of a sweep that decides per stride (sampled checks of large
     states): streams maps every tile of stride_items_tiles(...) to its input
     stream; returns the stride's new streams in tile order."""
@@ -359,8 +360,8 @@ def stride_sweep(n: int, c: int, H, stride_log2: int, theta: float, t0: int, str
     out_len = (C.c_uint32 * (1 << ut))()
     arr = gate_array(gates)
     rc = lib().or_stride_sweep(n, c, hh, len(H), ut, max_bytes_for(stride_log2, theta), t0, tarr, ptrs,
-                               lens, len(tiles), alpha, arr, len(gates), sh, len(shifts), out, cap,
-                               out_len)
+                               lens, len(tiles), alpha, arr, len(gates), sh, len(shifts),
+                               int(bool(fuse)), out, cap, out_len)
     if rc != 0:
         raise RuntimeError(f"oracle stride sweep failed ({rc})")
     res, off = [], 0
@@ -377,11 +378,14 @@ class CSim:
 
     shifts: ladder of quantisation shifts (one entry for a fixed bound);
     max_bytes: the ratio threshold as a size limit (None = no threshold);
-    normalize: apply 'normalize' before each sweep's gate computation.
+    normalize: apply 'normalize' before each sweep's gate computation;
+    fuse: runs of two or more consecutive diagonal gates of a sweep are one
+    diagonal operator (False: every gate on its own, so that lossless
+    sweeps reproduce the dense simulator bit for bit).
     """
 
     def __init__(self, n: int, c: int, shifts, max_bytes: int | None = None,
-                 normalize: bool = True):
+                 normalize: bool = True, fuse: bool = True):
         self.n, self.c = n, c
         self.shifts = list(shifts)
         sh = (C.c_int * len(self.shifts))(*self.shifts)
@@ -389,6 +393,7 @@ class CSim:
         self.h = lib().or_csim_new(n, c, sh, len(self.shifts), mb, int(normalize))
         if not self.h:
             raise ValueError("bad oracle state parameters")
+        lib().or_csim_set_fuse(self.h, int(bool(fuse)))
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -237,6 +237,131 @@ static int apply_gate_buf(double *a, int mb, const int *qb, uint64_t fixed,
     return 0;
 }
 
+/*
+ * Diagonal runs (the O3 gate computation; reading of the sweep's fused
+ * gate run).  Two or more consecutive diagonal gates of a sweep form one
+ * diagonal operator: its entry at index x is the product of the gates'
+ * entries there, and the amplitude is multiplied by it once.  This is the
+ * product of the run's matrices, written out with one fixed rounding order:
+ *   - a gate contributes at x when its controls hold there; its factor is
+ *     its diagonal entry at x's target sub-index, and a factor exactly 1
+ *     contributes nothing;
+ *   - factors exactly -1, i or -i ("units") are collected as a power i^k
+ *     (exact: sign flips and swaps of the components);
+ *   - the other factors are multiplied left to right in gate order, each new
+ *     factor u applied to the running product p as the general complex
+ *     term u*p; gates whose targets and controls are all qubits >= c
+ *     (constant over a tile) form one product T, every other gate another
+ *     product L;
+ *   - the amplitude a becomes i^k * (G a) with G = T*L (T applied to L) when
+ *     both exist, else the one that exists, and i^k * a when neither does.
+ * Mathematically the same operator as the gates one after the other
+ * (Sec. II pair update for diagonal matrices); in rounding it multiplies
+ * every amplitude twice at most, whatever the run's length.
+ */
+
+/* general complex term y = u * x (the rounding of term_first's general case) */
+static void cmul(double ur, double ui, double xr, double xi, double *yr, double *yi)
+{
+    double r = fma(ur, xr, -(ui * xi));
+    double i = fma(ur, xi, ui * xr);
+    *yr = r;
+    *yi = i;
+}
+
+/* exponent k with u == i^k for u in {-1, i, -i} (exact comparisons), else -1 */
+static int unit_exponent(double ur, double ui)
+{
+    if (ur == -1.0 && ui == 0.0) return 2;
+    if (ur == 0.0 && ui == 1.0) return 1;
+    if (ur == 0.0 && ui == -1.0) return 3;
+    return -1;
+}
+
+/* x <- i^k x, exact */
+static void unit_apply(int k, double *xr, double *xi)
+{
+    double r = *xr, i = *xi;
+    switch (k & 3) {
+        case 1: *xr = -i; *xi = r; break;
+        case 2: *xr = -r; *xi = -i; break;
+        case 3: *xr = i; *xi = -r; break;
+        default: break;
+    }
+}
+
+/* every target and control of g is a qubit >= c */
+static int gate_on_high_qubits(const or_gate *g, int c)
+{
+    if (g->cmask & ((1ull << c) - 1)) return 0;
+    for (int i = 0; i < g->k; ++i)
+        if (g->t[i] < c) return 0;
+    return 1;
+}
+
+/* One diagonal run (gates g[0..ng-1], all diagonal) applied to a buffer as
+ * apply_gate_buf addresses it. */
+static void apply_diag_run(double *a, int mb, const int *qb, uint64_t fixed, const or_gate *g, int ng,
+                           int c)
+{
+    uint64_t nb = 1ull << mb;
+    for (uint64_t l = 0; l < nb; ++l) {
+        uint64_t gl = fixed;
+        for (int p = 0; p < mb; ++p)
+            if ((l >> p) & 1) gl |= 1ull << qb[p];
+        int k = 0, have_t = 0, have_l = 0;
+        double tr = 0.0, ti = 0.0, lr = 0.0, li = 0.0;
+        for (int i = 0; i < ng; ++i) {
+            if ((gl & g[i].cmask) != g[i].cval) continue;
+            int dim = 1 << g[i].k, r = 0;
+            for (int j = 0; j < g[i].k; ++j) r |= (int)((gl >> g[i].t[j]) & 1) << j;
+            double ur = g[i].m[2 * (r * dim + r)], ui = g[i].m[2 * (r * dim + r) + 1];
+            if (ur == 1.0 && ui == 0.0) continue;
+            int e = unit_exponent(ur, ui);
+            if (e >= 0) { k += e; continue; }
+            if (gate_on_high_qubits(&g[i], c)) {
+                if (have_t) cmul(ur, ui, tr, ti, &tr, &ti);
+                else { tr = ur; ti = ui; have_t = 1; }
+            } else {
+                if (have_l) cmul(ur, ui, lr, li, &lr, &li);
+                else { lr = ur; li = ui; have_l = 1; }
+            }
+        }
+        double xr = a[2 * l], xi = a[2 * l + 1];
+        if (have_t || have_l) {
+            double gr = have_t ? tr : lr, gi = have_t ? ti : li;
+            if (have_t && have_l) cmul(tr, ti, lr, li, &gr, &gi);
+            cmul(gr, gi, xr, xi, &xr, &xi);
+        }
+        unit_apply(k, &xr, &xi);
+        a[2 * l] = xr;
+        a[2 * l + 1] = xi;
+    }
+}
+
+/* A sweep's gates applied to an item buffer in order: with fuse set, each
+ * run of two or more consecutive diagonal gates as one diagonal operator
+ * (apply_diag_run), every other gate on its own.  Returns 0, or -1 when a
+ * non-diagonal gate has a target outside the buffer. */
+static int apply_gates_buf(double *a, int mb, const int *qb, uint64_t fixed, const or_gate *g, int ng,
+                           int c, int fuse)
+{
+    int i = 0;
+    while (i < ng) {
+        int j = i;
+        if (fuse)
+            while (j < ng && gate_is_diagonal(&g[j])) ++j;
+        if (j - i >= 2) {
+            apply_diag_run(a, mb, qb, fixed, g + i, j - i, c);
+            i = j;
+            continue;
+        }
+        if (apply_gate_buf(a, mb, qb, fixed, &g[i]) != 0) return -1;
+        ++i;
+    }
+    return 0;
+}
+
 /* O1: apply a gate to a dense 2^n state (qubit j <-> index bit j). */
 int or_dense_apply(double *psi, int n, const or_gate *g)
 {
@@ -835,6 +960,7 @@ typedef struct {
     double alpha;        /* scale applied at the next decode ("normalize") */
     uint64_t hist[8];    /* ladder level of every tile written */
     uint64_t items_done, items_skipped;
+    int fuse;            /* diagonal runs as one operator (apply_gates_buf) */
 } or_csim;
 
 /* Keep buf (len bytes, malloc'ed) as tile t's stream: count its ladder
@@ -930,6 +1056,7 @@ or_csim *or_csim_new(int n, int c, const int *shifts, int nlev,
     cs->ut = 0;
     cs->umax = max_bytes;
     cs->normalize = normalize;
+    cs->fuse = 1;
     cs->ntiles = 1ull << (n - c);
     cs->st = calloc(cs->ntiles, sizeof(uint8_t *));
     cs->len = calloc(cs->ntiles, sizeof(uint32_t));
@@ -963,6 +1090,10 @@ int or_csim_set_unit(or_csim *cs, int unit_log2, uint64_t umax)
     cs->umax = cs->ut ? umax : cs->max_bytes;
     return cs->ut;
 }
+
+/* Diagonal runs on (1, the default) or gate by gate (0); the latter makes
+ * lossless sweeps reproduce the dense simulator O1 bit for bit. */
+void or_csim_set_fuse(or_csim *cs, int on) { cs->fuse = on ? 1 : 0; }
 
 /* state |x>: every tile (or stride) encoded from its dense values */
 void or_csim_reset_basis(or_csim *cs, uint64_t x)
@@ -1130,8 +1261,7 @@ static int csim_sweep_units(or_csim *cs, const or_gate *g, int ng, const int *H,
         if (rc) break;
         if (alpha != 1.0)
             for (uint64_t i = 0; i < 2 * ((uint64_t)1 << mb); ++i) buf[i] = buf[i] * alpha;
-        for (int i = 0; i < ng && rc == 0; ++i)
-            if (apply_gate_buf(buf, mb, qb, fixed, &g[i]) != 0) rc = -2;
+        if (apply_gates_buf(buf, mb, qb, fixed, g, ng, c, cs->fuse) != 0) rc = -2;
         for (uint64_t j = 0; j < (1ull << h) && rc == 0; ++j) {
             uint64_t Tj = T;
             for (int i = 0; i < h; ++i)
@@ -1218,8 +1348,7 @@ static int csim_sweep_items(or_csim *cs, const or_gate *g, int ng, const int *H,
         if (rc) break;
         if (alpha != 1.0)
             for (uint64_t i = 0; i < 2 * ((uint64_t)1 << mb); ++i) buf[i] = buf[i] * alpha;
-        for (int i = 0; i < ng && rc == 0; ++i)
-            if (apply_gate_buf(buf, mb, qb, fixed, &g[i]) != 0) rc = -2;
+        if (apply_gates_buf(buf, mb, qb, fixed, g, ng, c, cs->fuse) != 0) rc = -2;
         if (rc) break;
         for (uint64_t j = 0; j < (1ull << h); ++j) {
             uint64_t Tj = T;
@@ -1247,7 +1376,7 @@ static int csim_sweep_items(or_csim *cs, const or_gate *g, int ng, const int *H,
 int or_item_sweep(int n, int c, const int *H, int h, uint64_t base_tile,
                   const uint8_t *const *in, const uint32_t *in_len, double alpha,
                   const or_gate *g, int ng, const int *shifts, int nlev, uint64_t max_bytes,
-                  uint8_t *out, size_t out_cap, uint32_t *out_len)
+                  int fuse, uint8_t *out, size_t out_cap, uint32_t *out_len)
 {
     uint64_t N = 1ull << c;
     int mb = c + h;
@@ -1291,8 +1420,7 @@ int or_item_sweep(int n, int c, const int *H, int h, uint64_t base_tile,
         if (or_decode_tile(in[j], in_len[j], c, buf + 2 * j * N) != 0) rc = -1;
     if (rc == 0 && alpha != 1.0)
         for (uint64_t i = 0; i < 2 * ((uint64_t)1 << mb); ++i) buf[i] = buf[i] * alpha;
-    for (int i = 0; i < ng && rc == 0; ++i)
-        if (apply_gate_buf(buf, mb, qb, fixed, &g[i]) != 0) rc = -2;
+    if (rc == 0 && apply_gates_buf(buf, mb, qb, fixed, g, ng, c, fuse) != 0) rc = -2;
     for (uint64_t j = 0; j < (1ull << h) && rc == 0; ++j) {
         int level = 0, flags = 0;
         size_t len = or_encode_tile(buf + 2 * j * N, c, shifts, nlev, max_bytes, tmp, &level, &flags);
@@ -1318,7 +1446,7 @@ int or_item_sweep(int n, int c, const int *H, int h, uint64_t base_tile,
  * is not 0.
  */
 typedef struct {
-    int n, c, h, ng, nlev, threads, k;
+    int n, c, h, ng, nlev, threads, k, fuse;
     const int *H;
     uint64_t nitems, max_bytes;
     const uint64_t *bases, *in_off;
@@ -1341,7 +1469,7 @@ static void *batch_worker(void *arg)
     for (uint64_t i = (uint64_t)b->k; i < b->nitems; i += (uint64_t)b->threads) {
         for (uint64_t j = 0; j < nm; ++j) ptrs[j] = b->in_buf + b->in_off[i * nm + j];
         b->rc[i] = or_item_sweep(b->n, b->c, b->H, b->h, b->bases[i], ptrs, b->in_len + i * nm,
-                                 b->alpha, b->g, b->ng, b->shifts, b->nlev, b->max_bytes,
+                                 b->alpha, b->g, b->ng, b->shifts, b->nlev, b->max_bytes, b->fuse,
                                  b->out + i * b->out_stride, b->out_stride, b->out_len + i * nm);
     }
     return NULL;
@@ -1350,7 +1478,7 @@ static void *batch_worker(void *arg)
 int or_item_sweep_batch(int n, int c, const int *H, int h, uint64_t nitems, const uint64_t *bases,
                         const uint8_t *in_buf, const uint64_t *in_off, const uint32_t *in_len,
                         double alpha, const or_gate *g, int ng, const int *shifts, int nlev,
-                        uint64_t max_bytes, uint8_t *out, size_t out_stride, uint32_t *out_len,
+                        uint64_t max_bytes, int fuse, uint8_t *out, size_t out_stride, uint32_t *out_len,
                         int *rc, int threads)
 {
     if (h < 0 || h > 4) return -1;
@@ -1360,7 +1488,7 @@ int or_item_sweep_batch(int n, int c, const int *H, int h, uint64_t nitems, cons
     pthread_t tid[256];
     int started[256];
     for (int k = 0; k < threads; ++k) {
-        batch_job b = {n, c, h, ng, nlev, threads, k, H, nitems, max_bytes, bases, in_off, in_buf,
+        batch_job b = {n, c, h, ng, nlev, threads, k, fuse, H, nitems, max_bytes, bases, in_off, in_buf,
                        in_len, alpha, g, shifts, out, out_stride, out_len, rc};
         jobs[k] = b;
         started[k] = k > 0 && pthread_create(&tid[k], NULL, batch_worker, &jobs[k]) == 0;
@@ -1398,7 +1526,7 @@ static int cmp_u64(const void *a, const void *b)
 int or_stride_sweep(int n, int c, const int *H, int h, int ut, uint64_t umax, uint64_t t0,
                     const uint64_t *tiles, const uint8_t *const *in, const uint32_t *in_len,
                     uint64_t ntl, double alpha, const or_gate *g, int ng, const int *shifts,
-                    int nlev, uint8_t *out, size_t out_cap, uint32_t *out_len)
+                    int nlev, int fuse, uint8_t *out, size_t out_cap, uint32_t *out_len)
 {
     uint64_t N = 1ull << c, nt = 1ull << ut;
     int mb = c + h, rc = 0;
@@ -1431,8 +1559,7 @@ int or_stride_sweep(int n, int c, const int *H, int h, int ut, uint64_t umax, ui
         if (rc) break;
         if (alpha != 1.0)
             for (uint64_t i = 0; i < 2 * ((uint64_t)1 << mb); ++i) buf[i] = buf[i] * alpha;
-        for (int i = 0; i < ng && rc == 0; ++i)
-            if (apply_gate_buf(buf, mb, qb, T << c, &g[i]) != 0) rc = -2;
+        if (apply_gates_buf(buf, mb, qb, T << c, g, ng, c, fuse) != 0) rc = -2;
         for (uint64_t j = 0; j < (1ull << h) && rc == 0; ++j) {
             uint64_t Tj = T;
             for (int i = 0; i < h; ++i)

@@ -307,6 +307,7 @@ struct qsim_state {
     unsigned long long units_cap = 0;
     void *rd = nullptr;                   // read-out scratch (probabilities, fidelity, sizes)
     size_t rd_cap = 0;
+    unsigned long long h2d_bytes = 0, d2h_bytes = 0;   // since creation (never reset)
 };
 
 namespace {
@@ -400,8 +401,8 @@ qsim_status ensure_units(qsim_t h, unsigned long long nunits) {
 // cudaMemcpyAsync that counts the bytes a handle moves between host and
 // device (qsim_stats_t h2d_bytes / d2h_bytes).
 cudaError_t hcopy(qsim_t h, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind, cudaStream_t st) {
-    if (kind == cudaMemcpyHostToDevice) h->st.h2d_bytes += bytes;
-    else if (kind == cudaMemcpyDeviceToHost) h->st.d2h_bytes += bytes;
+    if (kind == cudaMemcpyHostToDevice) h->h2d_bytes += bytes;
+    else if (kind == cudaMemcpyDeviceToHost) h->d2h_bytes += bytes;
     return cudaMemcpyAsync(dst, src, bytes, kind, st);
 }
 
@@ -1514,6 +1515,8 @@ qsim_status qsim_stats(qsim_t h, qsim_stats_t *out) {
     out->hmax = h->hmax;
     out->depth = h->depth;
     out->n_qubits = h->n;
+    out->h2d_bytes = h->h2d_bytes;
+    out->d2h_bytes = h->d2h_bytes;
     return QSIM_OK;
 }
 

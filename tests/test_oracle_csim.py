@@ -1,7 +1,7 @@
 """Pins of the oracle's compressed simulator (O3), norm and sweep partition.
 
-* Lossless level without normalisation: Algorithm 1 over compressed tiles
-  must reproduce the dense simulator bit for bit.
+* Lossless level without normalisation, every gate on its own: Algorithm 1
+  over compressed tiles must reproduce the dense simulator bit for bit.
 * Relative bound (Sec. III): after each sweep every stored component is
   within 2^(s-53)|x| of (normalize, then apply the sweep's gates) to the
   stored state before the sweep (Algorithm 2's per-stride steps).
@@ -44,7 +44,7 @@ def test_norm_units_exact():
 def test_lossless_compressed_equals_dense(n, c, hmax, depth):
     xval = I.seeded_basis(n)
     gates = I.basis_gates(n, xval) + I.qft(n) + I.random_grid(*I.grid_shape(n), 3, 9)
-    cs = oracle.CSim(n, c, [0], normalize=False)
+    cs = oracle.CSim(n, c, [0], normalize=False, fuse=False)
     cs.reset_basis(0)
     cs.run(gates, hmax, depth)
     psi = oracle.dense_run(oracle.dense_zero(n), n, gates)

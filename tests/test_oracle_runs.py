@@ -1,0 +1,141 @@
+"""Pins of the oracle's diagonal runs (O3): two or more consecutive diagonal
+gates of a sweep applied as one diagonal operator whose entry is the product
+of the gates' entries (the product of diagonal matrices, Sec. II), with
+unit factors (-1, i, -i) taken exactly and the other factors multiplied in
+gate order, split into the part on qubits >= c and the rest.
+
+* Within rounding of the gates applied one by one (the dense simulator O1),
+  on QFTs, grid circuits and random runs of controlled phases, CZ, S, T,
+  Rz and two-target diagonal gates with controls on low and high qubits.
+* Exact where the arithmetic is exact: runs of unit factors only give O1's
+  amplitudes bit for bit, and so do runs in which every amplitude meets at
+  most one other factor (G = that entry: the gate's own product).
+* The fused QFT against its closed form e^{2 pi i x k / N} / sqrt(N).
+* Runs are really fused: the QFT's amplitudes differ in rounding from the
+  gate-by-gate sweep somewhere.
+"""
+import cmath
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1811_05140_gb300 import inputs as I
+
+
+def lossless(n, c, gates, hmax, depth, fuse=True):
+    cs = oracle.CSim(n, c, [0], normalize=False, fuse=fuse)
+    cs.reset_basis(0)
+    cs.run(gates, hmax, depth)
+    return cs.dense()
+
+
+def diag(*entries):
+    return np.diag(np.asarray(entries, dtype=np.complex128))
+
+
+def random_diag_run(n, rng, count):
+    """Diagonal gates of every kind on random qubits (low and high)."""
+    gates = []
+    for _ in range(count):
+        kind = rng.integers(0, 7)
+        q = [int(v) for v in rng.permutation(n)[:4]]
+        phi = float(rng.uniform(-math.pi, math.pi))
+        if kind == 0:
+            gates.append(I.cphase(phi, q[0], q[1]))
+        elif kind == 1:
+            gates.append(I.cz(q[0], q[1]))
+        elif kind == 2:
+            gates.append(I.Gate(diag(1, 1j), (q[0],), (q[1],), (int(rng.integers(0, 2)),)))   # controlled S
+        elif kind == 3:
+            gates.append(I.Gate(diag(1, -1j), (q[0],)))                                        # S^dagger
+        elif kind == 4:
+            gates.append(I.Gate(diag(1, cmath.exp(1j * math.pi / 4)), (q[0],)))                # T
+        elif kind == 5:
+            gates.append(I.Gate(diag(cmath.exp(-1j * phi), cmath.exp(1j * phi)), (q[0],), (q[2], q[3])))  # CC-Rz
+        else:
+            gates.append(I.Gate(diag(cmath.exp(1j * phi), 1, -1, cmath.exp(-2j * phi)), (q[0], q[1])))
+    return gates
+
+
+def mixed_circuit(n, seed, layers=3):
+    rng = np.random.default_rng(seed)
+    gates = I.basis_gates(n, int(rng.integers(0, 1 << n)))
+    for _ in range(layers):
+        gates += [I.h(q) for q in range(n)]
+        gates += random_diag_run(n, rng, int(rng.integers(2, 12)))
+    return gates
+
+
+@pytest.mark.parametrize("n,c,hmax,depth", [(10, 4, 2, 512), (10, 4, 2, 6), (9, 9, 2, 40), (8, 2, 2, 7),
+                                            (11, 5, 4, 512)])
+def test_fused_runs_within_rounding_of_dense(n, c, hmax, depth):
+    for gates in (I.basis_gates(n, I.seeded_basis(n)) + I.qft(n),
+                  I.random_grid(*I.grid_shape(n), 4, 9),
+                  mixed_circuit(n, n * 100 + c)):
+        psi = oracle.dense_run(oracle.dense_zero(n), n, gates)
+        got = lossless(n, c, gates, hmax, depth)
+        # a run multiplies each amplitude at most twice instead of once per
+        # gate: a few ulps of the unit-norm state per amplitude
+        assert np.max(np.abs(got - psi)) <= 1e-14
+
+
+def test_unit_runs_are_exact():
+    # CZ, Z, S, S^dagger, multi-controlled Z: factors -1, i, -i only
+    n, c = 9, 4
+    rng = np.random.default_rng(11)
+    gates = I.basis_gates(n, 0x155)
+    for _ in range(4):
+        gates += [I.h(q) for q in range(n)]
+        for _ in range(8):
+            a, b, d = (int(v) for v in rng.permutation(n)[:3])
+            pick = int(rng.integers(0, 4))
+            if pick == 0:
+                gates.append(I.cz(a, b))
+            elif pick == 1:
+                gates.append(I.Gate(diag(1, 1j), (a,), (b,)))
+            elif pick == 2:
+                gates.append(I.Gate(diag(1, -1j), (a,), (b, d), (0, 1)))
+            else:
+                gates.append(I.mcz(n, int(rng.integers(0, 1 << n))))
+    psi = oracle.dense_run(oracle.dense_zero(n), n, gates)
+    for hmax, depth in ((2, 512), (4, 9)):
+        got = lossless(n, c, gates, hmax, depth)
+        assert np.array_equal(got.view(np.uint64), psi.view(np.uint64))
+
+
+def test_runs_with_one_general_factor_per_amplitude_are_exact():
+    # phases on one target whose controls exclude one another (values 0 and
+    # 1 of the same qubit, or of two qubits): each amplitude meets at most
+    # one general factor, so G is that entry and the product is the gate's own
+    n, c = 9, 4
+    rng = np.random.default_rng(5)
+    gates = I.basis_gates(n, 0x0F3) + [I.h(q) for q in range(n)]
+    for t, a in ((1, 6), (7, 2), (5, 8), (0, 3)):
+        p = [cmath.exp(1j * float(v)) for v in rng.uniform(0.1, 3.0, 3)]
+        gates.append(I.Gate(diag(1, p[0]), (t,), (a,), (0,)))
+        gates.append(I.Gate(diag(1, p[1]), (t,), (a,), (1,)))
+        gates.append(I.Gate(diag(p[2], 1), (t,)))                 # the other target value
+        gates += [I.h(q) for q in range(n)]
+    psi = oracle.dense_run(oracle.dense_zero(n), n, gates)
+    got = lossless(n, c, gates, 2, 512)
+    assert np.array_equal(got.view(np.uint64), psi.view(np.uint64))
+
+
+@pytest.mark.parametrize("c", [3, 5, 8])
+def test_fused_qft_closed_form(c):
+    n = 12
+    x = I.seeded_basis(n)
+    got = lossless(n, c, I.basis_gates(n, x) + I.qft(n), 4, 512)
+    k = np.arange(1 << n)
+    ref = np.exp(2j * np.pi * ((x * k) % (1 << n)) / (1 << n)) / math.sqrt(1 << n)
+    assert np.max(np.abs(got - ref)) <= 1e-12
+
+
+def test_runs_are_fused():
+    n, c = 10, 4
+    gates = I.basis_gates(n, I.seeded_basis(n)) + I.qft(n)
+    a = lossless(n, c, gates, 4, 512, fuse=True)
+    b = lossless(n, c, gates, 4, 512, fuse=False)
+    assert not np.array_equal(a.view(np.uint64), b.view(np.uint64))
