@@ -139,6 +139,24 @@ qsim_status qsim_set_aalc(qsim_t h, double theta, const double *eps_levels, int 
 qsim_status qsim_set_aalc_unit(qsim_t h, int unit_log2);
 
 /*
+ * qsim_set_fusion -- diag_runs = 1 (the default): within a sweep, every run
+ * of two or more consecutive diagonal gates is applied as one diagonal
+ * operator (the product of diagonal matrices is diagonal, Sec. II): at
+ * index x the gates whose controls hold contribute their entry at x's
+ * target sub-index; entries exactly 1 contribute nothing; entries -1, i
+ * and -i are collected exactly as i^k; the other entries are multiplied in
+ * gate order, u applied to the running product p as u*p (general complex
+ * product), into T (gates whose targets and controls are all qubits
+ * >= tile_log2) and L (the others); the amplitude a becomes
+ * i^k * ((T*L) a), with T*L replaced by whichever exists when only one
+ * does.  Each amplitude is multiplied at most twice per run however long
+ * the run is.  diag_runs = 0 applies every gate on its own (Algorithm 1
+ * and 2 gate by gate; lossless sweeps then equal the dense FP64 simulation
+ * bit for bit).  Flushes queued gates first.
+ */
+qsim_status qsim_set_fusion(qsim_t h, int diag_runs);
+
+/*
  * qsim_set_normalize -- switch Algorithm 2's normalize step (on = 1) for
  * REL/AALC handles.  Flushes first.
  */

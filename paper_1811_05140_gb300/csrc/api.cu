@@ -61,6 +61,9 @@ cudaError_t launch_probs(const uint8_t *arena, const unsigned long long *table, 
                          unsigned long long ntiles, const int *qsel, int nq,
                          unsigned long long *buckets, DevScalars *scal, int grid, cudaStream_t st);
 unsigned long long fidelity_chunk(unsigned long long ntiles);
+cudaError_t launch_run_tables(const DRun *runs, const int2 *classes, int nclasses, const RGate *rgates, int c,
+                              double2 *tab, uint8_t *meta, RunClass *rcls, DevScalars *scal, int grid,
+                              cudaStream_t st);
 cudaError_t launch_fidelity(const uint8_t *arena, const unsigned long long *table, int c,
                             unsigned long long ntiles, const RefSpec &rs, Acc4 *tile_sums,
                             DevScalars *scal, int grid, cudaStream_t st);
@@ -308,6 +311,20 @@ struct qsim_state {
     void *rd = nullptr;                   // read-out scratch (probabilities, fidelity, sizes)
     size_t rd_cap = 0;
     unsigned long long h2d_bytes = 0, d2h_bytes = 0;   // since creation (never reset)
+    int fuse = 1;                         // diagonal runs as one operator
+    // diagonal runs of the flush in progress (host staging, device copies)
+    std::vector<qs::DRun> hruns;
+    std::vector<qs::RGate> hrg;
+    std::vector<int2> hclasses;
+    qs::DRun *druns = nullptr;
+    qs::RGate *drg = nullptr;
+    int2 *dclasses = nullptr;
+    size_t druns_cap = 0, drg_cap = 0, dclasses_cap = 0;
+    double2 *rtab = nullptr;
+    uint8_t *rmeta = nullptr;
+    size_t rtab_cap = 0, rmeta_cap = 0;
+    qs::RunClass *rcls = nullptr;
+    size_t rcls_cap = 0;
 };
 
 namespace {
@@ -573,6 +590,7 @@ void prepare_gate(const HostGate &g, int c, const Sweep &sw, qs::DGate &d, qs::S
     sgt.fcv = d.fcv;
     sgt.lcm = (uint32_t)d.lcm;
     sgt.lcv = (uint32_t)d.lcv;
+    sgt.run = -1;
     if (g.diag) {
         for (int r = 0; r < dim; ++r) {
             sgt.d[2 * r] = g.m[2 * (r * dim + r)];
@@ -686,6 +704,12 @@ qsim_status qsim_destroy(qsim_t h) {
     if (h->unit_bytes) cudaFree(h->unit_bytes);
     if (h->unit_level) cudaFree(h->unit_level);
     if (h->rd) cudaFree(h->rd);
+    if (h->druns) cudaFree(h->druns);
+    if (h->drg) cudaFree(h->drg);
+    if (h->dclasses) cudaFree(h->dclasses);
+    if (h->rtab) cudaFree(h->rtab);
+    if (h->rmeta) cudaFree(h->rmeta);
+    if (h->rcls) cudaFree(h->rcls);
     for (cudaEvent_t ev : h->events) cudaEventDestroy(ev);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
@@ -840,7 +864,147 @@ struct FlushCtx {
     unsigned id0 = 0;
     unsigned long long used_before = 0;
     int regrows = 0;
+    std::vector<int> run_first, nruns;    // per sweep: its diagonal runs
+    std::vector<char> in_run;             // per gate: part of a diagonal run
+    unsigned long long run_dp0 = 0;       // device FP64 count of runs when the flush began
 };
+
+constexpr int MAX_FLUSH_RUNS = 32767;     // SGate::run is 16-bit
+constexpr unsigned long long MAX_RUN_TABLE = 1ull << 22;   // table entries per flush (17 bytes each)
+
+// A diagonal gate in the form a run evaluates: entries classified exactly
+// (1 contributes nothing; -1, i, -i are unit factors; the rest general).
+qs::RGate run_gate(const HostGate &g) {
+    qs::RGate r{};
+    const int dim = 1 << g.k;
+    r.k = (uint8_t)g.k;
+    r.t0 = (uint8_t)g.t[0];
+    r.t1 = (uint8_t)(g.k > 1 ? g.t[1] : 0);
+    r.cm = g.cm;
+    r.cv = g.cv;
+    for (int i = 0; i < dim; ++i) {
+        const double ur = g.m[2 * (i * dim + i)], ui = g.m[2 * (i * dim + i) + 1];
+        r.e[2 * i] = ur;
+        r.e[2 * i + 1] = ui;
+        if (ur == 1.0 && ui == 0.0) r.code[i] = 0;
+        else if (ur == -1.0 && ui == 0.0) { r.code[i] = 1; r.uexp[i] = 2; }
+        else if (ur == 0.0 && ui == 1.0) { r.code[i] = 1; r.uexp[i] = 1; }
+        else if (ur == 0.0 && ui == -1.0) { r.code[i] = 1; r.uexp[i] = 3; }
+        else r.code[i] = 2;
+    }
+    return r;
+}
+
+// every target and control of g is a qubit >= c (its factor is constant over a tile)
+bool on_high_qubits(const HostGate &g, int c) {
+    if (g.cm & ((1ull << c) - 1ull)) return false;
+    for (int i = 0; i < g.k; ++i)
+        if (g.t[i] < c) return false;
+    return true;
+}
+
+// Find the diagonal runs of every sweep of a flush (two or more consecutive
+// diagonal gates), mark their gates in the staged compact gates, and build
+// the run descriptors, run gates and table classes.
+void plan_runs(qsim_t h, FlushCtx &fc) {
+    h->hruns.clear();
+    h->hrg.clear();
+    h->hclasses.clear();
+    fc.run_first.assign(fc.ns, 0);
+    fc.nruns.assign(fc.ns, 0);
+    fc.in_run.assign(fc.ng, 0);
+    unsigned long long tab = 0;
+    int cls = 0;
+    for (size_t si = 0; si < fc.ns; ++si) {
+        const Sweep &sw = fc.sweeps[si];
+        fc.run_first[si] = (int)h->hruns.size();
+        int i = sw.lo;
+        while (i < sw.hi) {
+            int j = i;
+            if (h->fuse)
+                while (j < sw.hi && h->queue[j].diag) ++j;
+            if (j - i < 2 || (int)h->hruns.size() >= MAX_FLUSH_RUNS) { i = std::max(i + 1, j); continue; }
+            qs::DRun R{};
+            R.first = i - sw.lo;
+            R.len = j - i;
+            unsigned long long qmask = 0;
+            std::vector<qs::RGate> tile, local;
+            for (int g = i; g < j; ++g) {
+                const HostGate &hg = h->queue[g];
+                if (on_high_qubits(hg, h->c)) { tile.push_back(run_gate(hg)); continue; }
+                local.push_back(run_gate(hg));
+                qmask |= hg.cm & ~((1ull << h->c) - 1ull);
+                for (int t = 0; t < hg.k; ++t)
+                    if (hg.t[t] >= h->c) qmask |= 1ull << hg.t[t];
+            }
+            R.tg = (int)h->hrg.size();
+            R.nt = (int)tile.size();
+            h->hrg.insert(h->hrg.end(), tile.begin(), tile.end());
+            R.lg = (int)h->hrg.size();
+            R.nl = (int)local.size();
+            h->hrg.insert(h->hrg.end(), local.begin(), local.end());
+            R.nq = popcount64(qmask);
+            const unsigned long long entries = (1ull << R.nq) << h->c;
+            R.tabled = R.nl > 0 && R.nq <= qs::RUN_QMAX && tab + entries <= MAX_RUN_TABLE;
+            if (R.tabled) {
+                int b = 0;
+                for (int q = 0; q < 64; ++q)
+                    if ((qmask >> q) & 1ull) R.q[b++] = q;
+                R.table = tab;
+                R.cls = cls;
+                const int rid = (int)h->hruns.size();
+                for (int kap = 0; kap < (1 << R.nq); ++kap) h->hclasses.push_back(make_int2(rid, kap));
+                tab += entries;
+                cls += 1 << R.nq;
+            } else {
+                R.nq = 0;
+            }
+            h->hsg[i].run = (int16_t)h->hruns.size();
+            for (int g = i; g < j; ++g) fc.in_run[g] = 1;
+            for (int g = i + 1; g < j; ++g) h->hsg[g].run = -2;
+            h->hruns.push_back(R);
+            i = j;
+        }
+        fc.nruns[si] = (int)h->hruns.size() - fc.run_first[si];
+    }
+}
+
+// Upload the flush's runs and build their tables on the device (stream st).
+qsim_status stage_runs(qsim_t h, FlushCtx &fc, cudaStream_t st) {
+    fc.run_dp0 = h->hscal->run_dp;
+    if (h->hruns.empty()) return QSIM_OK;
+    auto grow = [&](void **p, size_t &cap, size_t need, size_t unit) -> cudaError_t {
+        if (cap >= need) return cudaSuccess;
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+        cap = 0;
+        const size_t n = std::max<size_t>(need, 16);
+        e = cudaMalloc(p, n * unit);
+        if (e == cudaSuccess) cap = n;
+        return e;
+    };
+    unsigned long long entries = 0;
+    int ncls = 0;
+    for (const qs::DRun &R : h->hruns)
+        if (R.tabled) { entries += (1ull << R.nq) << h->c; ncls += 1 << R.nq; }
+    CK(grow((void **)&h->druns, h->druns_cap, h->hruns.size(), sizeof(qs::DRun)));
+    CK(grow((void **)&h->drg, h->drg_cap, std::max<size_t>(1, h->hrg.size()), sizeof(qs::RGate)));
+    CK(hcopy(h, h->druns, h->hruns.data(), h->hruns.size() * sizeof(qs::DRun), cudaMemcpyHostToDevice, st));
+    if (!h->hrg.empty())
+        CK(hcopy(h, h->drg, h->hrg.data(), h->hrg.size() * sizeof(qs::RGate), cudaMemcpyHostToDevice, st));
+    if (ncls == 0) return QSIM_OK;
+    CK(grow((void **)&h->dclasses, h->dclasses_cap, (size_t)ncls, sizeof(int2)));
+    CK(grow((void **)&h->rcls, h->rcls_cap, (size_t)ncls, sizeof(qs::RunClass)));
+    CK(grow((void **)&h->rtab, h->rtab_cap, (size_t)entries, sizeof(double2)));
+    CK(grow((void **)&h->rmeta, h->rmeta_cap, (size_t)entries, 1));
+    CK(hcopy(h, h->dclasses, h->hclasses.data(), (size_t)ncls * sizeof(int2), cudaMemcpyHostToDevice, st));
+    ++h->launches;
+    CK(qs::launch_run_tables(h->druns, h->dclasses, ncls, h->drg, h->c, h->rtab, h->rmeta, h->rcls, h->scal,
+                             grid_for(h, (unsigned long long)ncls, 4), st));
+    return QSIM_OK;
+}
 
 // Plan the queued gates into sweeps and upload them (prepared for their
 // sweep) on stream st; size the per-sweep buffers.
@@ -900,8 +1064,13 @@ qsim_status stage_flush(qsim_t h, FlushCtx &fc, cudaStream_t st) {
     for (size_t si = 0; si < ns; ++si)
         for (int gi = fc.sweeps[si].lo; gi < fc.sweeps[si].hi; ++gi)
             prepare_gate(h->queue[gi], h->c, fc.sweeps[si], h->hgates[gi], h->hsg[gi]);
+    plan_runs(h, fc);
     CK(hcopy(h, h->dgates, h->hgates, ng * sizeof(qs::DGate), cudaMemcpyHostToDevice, st));
     CK(hcopy(h, h->dsg, h->hsg, ng * sizeof(qs::SGate), cudaMemcpyHostToDevice, st));
+    {
+        qsim_status rs = stage_runs(h, fc, st);
+        if (rs != QSIM_OK) return rs;
+    }
     if (h->profiling) {
         while (h->events.size() < 2 * ns) {
             cudaEvent_t ev;
@@ -942,6 +1111,13 @@ qs::SweepParams sweep_params(qsim_t h, const FlushCtx &fc, size_t j) {
     p.cc = h->cc;
     p.nitems = h->ntiles >> sw.h;
     p.sweep_id = fc.id0 + (unsigned)j;
+    p.runs = h->druns;
+    p.rgates = h->drg;
+    p.rtab = h->rtab;
+    p.rmeta = h->rmeta;
+    p.rcls = h->rcls;
+    p.run_first = fc.run_first.empty() ? 0 : fc.run_first[j];
+    p.nruns = fc.nruns.empty() ? 0 : fc.nruns[j];
     p.use_alpha = h->normalize;
     p.low_free = 1;
     p.moves_tiles = 1;
@@ -1058,12 +1234,15 @@ qsim_status finish_flush(qsim_t h, FlushCtx &fc, bool timed) {
             h->prof.sweep_ms += ms;
             h->prof.sweep_launches += 1;
             double dp = h->normalize ? 2.0 * std::ldexp(1.0, h->n) : 0.0;
-            for (int gi = fc.sweeps[j].lo; gi < fc.sweeps[j].hi; ++gi) dp += gate_dp_ops(h->queue[gi], h->n);
+            for (int gi = fc.sweeps[j].lo; gi < fc.sweeps[j].hi; ++gi)
+                if (!fc.in_run[gi]) dp += gate_dp_ops(h->queue[gi], h->n);
             h->prof.dp_ops += dp;
             const unsigned long long in = j == 0 ? fc.used_before : h->hused[j - 1];
             h->prof.bytes += (double)in + (double)h->hused[j] + 32.0 * (double)h->ntiles;
         }
     }
+    if (h->profiling && timed)             // diagonal runs: counted on the device as executed
+        h->prof.dp_ops += (double)(h->hscal->run_dp - fc.run_dp0);
     h->queue.clear();
     return QSIM_OK;
 }
@@ -1279,6 +1458,14 @@ qsim_status qsim_set_aalc_unit(qsim_t h, int unit_log2) {
     if (unit_log2 < 0 || unit_log2 > MAX_QUBITS) return fail(h, QSIM_ERR_ARG, "unit_log2 must be 0..%d", MAX_QUBITS);
     if ((s = qsim_flush(h)) != QSIM_OK) return s;     // queued gates run under the old rule
     h->unit_log2 = unit_log2;
+    return QSIM_OK;
+}
+
+qsim_status qsim_set_fusion(qsim_t h, int diag_runs) {
+    qsim_status s = check_usable(h);
+    if (s != QSIM_OK) return s;
+    if ((s = qsim_flush(h)) != QSIM_OK) return s;
+    h->fuse = diag_runs ? 1 : 0;
     return QSIM_OK;
 }
 

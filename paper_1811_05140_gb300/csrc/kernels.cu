@@ -447,6 +447,221 @@ __device__ void two_target(double *re, double *im, int mb, const SGate &s, const
     }
 }
 
+// tile index of an item: zero bits inserted at the tile-index positions
+// hb[0] < hb[1] < ... of the h paired qubits
+__device__ __forceinline__ unsigned long long expand_item(unsigned long long item, int h,
+                                                           const int *hb) {
+    unsigned long long v = item;
+#pragma unroll
+    for (int i = 0; i < MAX_PAIRS; ++i) {
+        if (i >= h) break;
+        const unsigned long long m = (1ull << hb[i]) - 1ull;
+        v = ((v & ~m) << 1) | (v & m);
+    }
+    return v;
+}
+
+// tile of member j of the item whose first tile is T
+__device__ __forceinline__ unsigned long long member_tile(unsigned long long T, int j, int h,
+                                                          const int *hb) {
+#pragma unroll
+    for (int i = 0; i < MAX_PAIRS; ++i) {
+        if (i >= h) break;
+        T |= (unsigned long long)((j >> i) & 1) << hb[i];
+    }
+    return T;
+}
+
+// ---------------------------------------------------------------- diagonal runs
+// general complex term y = u x (term_first's general arithmetic)
+__device__ __forceinline__ void cmul(double ur, double ui, double xr, double xi, double &yr, double &yi) {
+    const double r = __fma_rn(ur, xr, -__dmul_rn(ui, xi));
+    const double i = __fma_rn(ur, xi, __dmul_rn(ui, xr));
+    yr = r;
+    yi = i;
+}
+
+// x <- i^k x (exact: a swap and sign-bit flips)
+__device__ __forceinline__ void unit_pow(unsigned k, double &xr, double &xi) {
+    k &= 3u;
+    if (k == 0u) return;
+    const unsigned f = k == 1u ? 2u : (k == 2u ? 1u : 3u);      // unit_times codes: 1 -> -1, 2 -> i, 3 -> -i
+    double tr, ti;
+    unit_times(f, xr, xi, tr, ti);
+    xr = tr;
+    xi = ti;
+}
+
+// Ordered product of the factors of gates g[0..n-1] at global index x:
+// general factors into (pr, pi) (have set when one exists), unit
+// exponents added to k.  Returns the FP64 instructions executed.
+__device__ __forceinline__ unsigned run_factor(const RGate *g, int n, unsigned long long x, bool &have,
+                                               double &pr, double &pi, unsigned &k) {
+    unsigned ops = 0;
+    for (int i = 0; i < n; ++i) {
+        const RGate &G = g[i];
+        if ((x & G.cm) != G.cv) continue;
+        int r = (int)((x >> G.t0) & 1ull);
+        if (G.k > 1) r |= (int)((x >> G.t1) & 1ull) << 1;
+        const unsigned code = G.code[r];
+        if (code == 0u) continue;
+        if (code == 1u) { k += G.uexp[r]; continue; }
+        if (have) { cmul(G.e[2 * r], G.e[2 * r + 1], pr, pi, pr, pi); ops += 4; }
+        else { pr = G.e[2 * r]; pi = G.e[2 * r + 1]; have = true; }
+    }
+    return ops;
+}
+
+// Tables of the local product L of every tabled run: one CTA per (run,
+// class), entry x_lo at runs[r].table + class * 2^c + x_lo; then the
+// class's summary (active / general entry counts, tile bits common to the
+// active entries).  The class index's bit i is index bit q[i].
+__global__ void __launch_bounds__(256) run_tables_kernel(const DRun *runs, const int2 *classes, int nclasses,
+                                                         const RGate *rgates, int c, double2 *tab,
+                                                         uint8_t *meta, RunClass *rcls, DevScalars *scal) {
+    __shared__ unsigned s_active, s_have, s_and, s_or;
+    __shared__ unsigned long long s_ops;
+    const int N = 1 << c;
+    for (int ci = blockIdx.x; ci < nclasses; ci += gridDim.x) {
+        const int r = classes[ci].x, kap = classes[ci].y;
+        const DRun &R = runs[r];
+        if (threadIdx.x == 0) { s_active = 0; s_have = 0; s_and = ~0u; s_or = 0; s_ops = 0; }
+        __syncthreads();
+        unsigned long long xh = 0;
+        for (int i = 0; i < R.nq; ++i) xh |= (unsigned long long)((kap >> i) & 1) << R.q[i];
+        unsigned act = 0, hv = 0, am = ~0u, om = 0, ops = 0;
+        for (int xl = threadIdx.x; xl < N; xl += blockDim.x) {
+            bool have = false;
+            double pr = 0.0, pi = 0.0;
+            unsigned k = 0;
+            ops += run_factor(rgates + R.lg, R.nl, xh | (unsigned long long)xl, have, pr, pi, k);
+            const unsigned long long e = R.table + (unsigned long long)kap * N + xl;
+            tab[e] = make_double2(pr, pi);
+            meta[e] = (uint8_t)((have ? 1u : 0u) | ((k & 3u) << 1));
+            if (have || (k & 3u)) { ++act; am &= (unsigned)xl; om |= (unsigned)xl; }
+            if (have) ++hv;
+        }
+        atomicAdd(&s_active, act);
+        atomicAdd(&s_have, hv);
+        atomicAnd(&s_and, am);
+        atomicOr(&s_or, om);
+        atomicAdd(&s_ops, (unsigned long long)ops);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            RunClass rc;
+            rc.active = s_active;
+            rc.have = s_have;
+            const unsigned lowm = (unsigned)N - 1u;
+            rc.pin_mask = s_active ? ((s_and | ~s_or) & lowm) : 0u;
+            rc.pin_val = s_active ? (s_and & lowm) : 0u;
+            rcls[R.cls + kap] = rc;
+            if (s_ops) atomicAdd(&scal->run_dp, s_ops);
+        }
+        __syncthreads();
+    }
+}
+
+// Per member tile of an item, for the run being applied.
+struct RunMember {
+    double tr, ti;                  // tile product T
+    uint32_t count;                 // amplitudes to visit
+    uint32_t pin_mask, pin_val;     // visited tile bits: all (mask 0) or the class's pinned subset
+    uint16_t kap;                   // class
+    uint8_t have_t, k_t;
+};
+
+// One diagonal run applied to an item buffer (every thread calls it).
+// red > 0: one amplitude per tile (uniform items; such sweeps have no local
+// gates).  Returns the FP64 instructions this thread executed.
+__device__ unsigned apply_run(double *re, double *im, int c, int h, int red, const DRun &R,
+                              const SweepParams &P, unsigned long long T, const int *hb, RunMember *mem) {
+    const int ntl = 1 << h, N = 1 << c;
+    unsigned ops = 0;
+    if ((int)threadIdx.x < ntl) {
+        const int j = threadIdx.x;
+        const unsigned long long xb = member_tile(T, j, h, hb) << c;
+        bool have = false;
+        double tr = 0.0, ti = 0.0;
+        unsigned k = 0;
+        ops += run_factor(P.rgates + R.tg, R.nt, xb, have, tr, ti, k);
+        unsigned kap = 0;
+        for (int i = 0; i < R.nq; ++i) kap |= (unsigned)((xb >> R.q[i]) & 1ull) << i;
+        RunMember m;
+        m.tr = tr;
+        m.ti = ti;
+        m.have_t = have ? 1 : 0;
+        m.k_t = (uint8_t)(k & 3u);
+        m.kap = (uint16_t)kap;
+        m.pin_mask = 0;
+        m.pin_val = 0;
+        const bool tile_part = have || (k & 3u);
+        if (red) m.count = tile_part ? 1u : 0u;
+        else if (tile_part) m.count = (uint32_t)N;
+        else if (R.nl == 0) m.count = 0;
+        else if (!R.tabled) m.count = (uint32_t)N;
+        else {
+            const RunClass rc = P.rcls[R.cls + kap];
+            m.pin_mask = rc.pin_mask;
+            m.pin_val = rc.pin_val;
+            m.count = rc.active ? (uint32_t)N >> __popc(rc.pin_mask) : 0u;
+        }
+        mem[j] = m;
+    }
+    __syncthreads();
+    int j = 0;
+    unsigned base = 0;
+    for (unsigned w = threadIdx.x;; w += SWEEP_THREADS) {
+        while (j < ntl && w >= base + mem[j].count) { base += mem[j].count; ++j; }
+        if (j >= ntl) break;
+        const RunMember &m = mem[j];
+        unsigned f = w - base, xl = 0;
+        if (!red) {
+            // deposit f into the tile bits outside pin_mask, pinned bits from pin_val
+            unsigned pm = m.pin_mask;
+            xl = f;
+            while (pm) {
+                const int b = __ffs(pm) - 1;
+                xl = insert_zero(xl, b);
+                pm &= pm - 1;
+            }
+            xl |= m.pin_val;
+        }
+        bool have_l = false;
+        double lr = 0.0, li = 0.0;
+        unsigned k = m.k_t;
+        if (R.nl && !red) {
+            if (R.tabled) {
+                const unsigned long long e = R.table + (unsigned long long)m.kap * N + xl;
+                const unsigned mt = P.rmeta[e];
+                have_l = mt & 1u;
+                k += mt >> 1;
+                if (have_l) {
+                    const double2 v = P.rtab[e];
+                    lr = v.x;
+                    li = v.y;
+                }
+            } else {
+                const unsigned long long x = (member_tile(T, j, h, hb) << c) | xl;
+                ops += run_factor(P.rgates + R.lg, R.nl, x, have_l, lr, li, k);
+            }
+        }
+        const bool have_t = m.have_t;
+        if (!have_t && !have_l && (k & 3u) == 0u) continue;
+        const unsigned l = ((unsigned)j << c) | xl;
+        double xr = re[l], xi = im[l];
+        if (have_t || have_l) {
+            double gr = have_t ? m.tr : lr, gi = have_t ? m.ti : li;
+            if (have_t && have_l) { cmul(m.tr, m.ti, lr, li, gr, gi); ops += 4; }
+            cmul(gr, gi, xr, xi, xr, xi);
+            ops += 4;
+        }
+        unit_pow(k, xr, xi);
+        re[l] = xr;
+        im[l] = xi;
+    }
+    return ops;
+}
+
 // Apply the sweep's gates (in order) to an item buffer of 2^mb amplitudes.
 // act: bit g set when gate g changes something in this item.  The compact
 // gates are staged in shared memory GATE_CHUNK at a time (*chunk = first
@@ -454,10 +669,15 @@ __device__ void two_target(double *re, double *im, int mb, const SGate &s, const
 // red > 0: only the amplitudes whose low `red` index bits are 0 (one per
 // tile, for an item of uniform tiles under gates that touch no low qubit).
 // CTA-wide; every thread must call it.
-__device__ __noinline__ void apply_gates(double *re, double *im, int mb, int red, const SGate *gsrc, SGate *sg,
+// A gate that starts a diagonal run (SGate::run >= 0) applies the whole run
+// (apply_run); the run's other gates carry no activity bit (the sweep
+// kernel moves the run's activity onto its first gate).  Returns the FP64
+// instructions this thread executed in diagonal runs.
+__device__ __noinline__ unsigned apply_gates(double *re, double *im, int mb, int red, const SGate *gsrc, SGate *sg,
                             int *chunk, const DGate *dg, int ngates, const unsigned *act,
-                            unsigned long long fixed) {
+                            unsigned long long fixed, const SweepParams &P, const int *hb, RunMember *mem) {
     const bool warp_parts = red == 0 && mb - LOG_NWARPS >= 5;
+    unsigned run_ops = 0;
     bool dirty = false;                              // warp-local gates since the last CTA barrier
     for (int base = 0; base < ngates; base += GATE_CHUNK) {
         const int cn = min(GATE_CHUNK, ngates - base);
@@ -482,6 +702,13 @@ __device__ __noinline__ void apply_gates(double *re, double *im, int mb, int red
             const int g = base + i;
             if (!((act[g >> 5] >> (g & 31)) & 1u)) continue;
             const SGate &s = sg[i];
+            if (s.run != -1) {
+                if (s.run < 0) continue;            // inside a run: applied with its first gate
+                if (dirty) { __syncthreads(); dirty = false; }
+                run_ops += apply_run(re, im, P.cc.c, mb - P.cc.c, red, P.runs[s.run], P, fixed >> P.cc.c, hb, mem);
+                __syncthreads();
+                continue;
+            }
             if (s.kind == 0 && warp_parts) {
                 // runs of diagonal gates: warp-local, no CTA barrier between them
                 diag_gate_warp(re, im, mb, s, fixed);
@@ -497,6 +724,7 @@ __device__ __noinline__ void apply_gates(double *re, double *im, int mb, int red
         }
     }
     if (dirty) __syncthreads();
+    return run_ops;
 }
 
 // ---------------------------------------------------------------- warp codec
@@ -1531,31 +1759,6 @@ __device__ void wnorm(const double *re, const double *im, int N, unsigned long l
 }
 
 // ---------------------------------------------------------------- kernels
-// tile index of an item: zero bits inserted at the tile-index positions
-// hb[0] < hb[1] < ... of the h paired qubits
-__device__ __forceinline__ unsigned long long expand_item(unsigned long long item, int h,
-                                                           const int *hb) {
-    unsigned long long v = item;
-#pragma unroll
-    for (int i = 0; i < MAX_PAIRS; ++i) {
-        if (i >= h) break;
-        const unsigned long long m = (1ull << hb[i]) - 1ull;
-        v = ((v & ~m) << 1) | (v & m);
-    }
-    return v;
-}
-
-// tile of member j of the item whose first tile is T
-__device__ __forceinline__ unsigned long long member_tile(unsigned long long T, int j, int h,
-                                                          const int *hb) {
-#pragma unroll
-    for (int i = 0; i < MAX_PAIRS; ++i) {
-        if (i >= h) break;
-        T |= (unsigned long long)((j >> i) & 1) << hb[i];
-    }
-    return T;
-}
-
 // Sweeps of Algorithm 2 over all items of a work list: entry e of plist is
 // one sweep of one state, owning the global item indices istart[e] ..
 // istart[e+1]-1.  A single-state flush passes a one-entry list; a batch
@@ -1582,7 +1785,11 @@ __global__ void __launch_bounds__(SWEEP_THREADS, QS_SWEEP_MIN_BLOCKS) sweep_kern
     __shared__ int s_dest[1 << MAX_PAIRS];
     __shared__ unsigned long long s_plo[1 << MAX_PAIRS], s_phi[1 << MAX_PAIRS];
     __shared__ double s_alpha;
+    __shared__ RunMember s_mem[1 << MAX_PAIRS];
+    __shared__ unsigned long long s_rundp;
     const unsigned long long total = istart[nlist];
+    if (threadIdx.x == 0) s_rundp = 0;
+    unsigned run_ops = 0;                 // FP64 instructions of diagonal runs (this thread)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *wst = stage + 64 * warp;
     int cur = -1;
@@ -1600,8 +1807,21 @@ __global__ void __launch_bounds__(SWEEP_THREADS, QS_SWEEP_MIN_BLOCKS) sweep_kern
         }
         __syncthreads();
         const unsigned long long gi = s_gi;
+        const int e = gi >= total ? -1 : s_entry;
+        if (e != cur && cur >= 0) {
+            // the CTA's diagonal-run FP64 count for the state it leaves: one
+            // global atomic per CTA and state
+            const unsigned wsum = __reduce_add_sync(FULL, run_ops);
+            run_ops = 0;
+            if (lane == 0 && wsum) atomicAdd(&s_rundp, (unsigned long long)wsum);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (s_rundp) atomicAdd(&P.scal->run_dp, s_rundp);
+                s_rundp = 0;
+            }
+            __syncthreads();
+        }
         if (gi >= total) break;
-        const int e = s_entry;
         if (e != cur) {
             {
                 const uint32_t *src = reinterpret_cast<const uint32_t *>(plist + e);
@@ -1639,6 +1859,27 @@ __global__ void __launch_bounds__(SWEEP_THREADS, QS_SWEEP_MIN_BLOCKS) sweep_kern
             if (lane == 0) {
                 s_act[w] = bal;
                 if (bal) s_any = 1;
+            }
+        }
+        __syncthreads();
+        if (P.nruns && warp == 0) {
+            // a diagonal run is active when any of its gates is; its activity
+            // goes to its first gate, which applies the whole run
+            for (int r = 0; r < P.nruns; ++r) {
+                const DRun &R = P.runs[P.run_first + r];
+                bool any = false;
+                for (int g = R.first + lane; g < R.first + R.len; g += 32)
+                    any |= (s_act[g >> 5] >> (g & 31)) & 1u;
+                any = __any_sync(FULL, any);
+                __syncwarp();
+                for (int g = R.first + lane; g < R.first + R.len; g += 32) {
+                    const unsigned bit = 1u << (g & 31);
+                    const bool on = g == R.first && any;
+                    // lanes of one word change disjoint bits
+                    if (on) atomicOr(&s_act[g >> 5], bit);
+                    else atomicAnd(&s_act[g >> 5], ~bit);
+                }
+                __syncwarp();
             }
         }
         __syncthreads();
@@ -1707,7 +1948,8 @@ __global__ void __launch_bounds__(SWEEP_THREADS, QS_SWEEP_MIN_BLOCKS) sweep_kern
         }
         if (active) {
             __syncthreads();
-            apply_gates(re, im, mb, uni ? c : 0, P.sgates, sg, &s_chunk, P.gates, P.ngates, s_act, fixed);
+            run_ops += apply_gates(re, im, mb, uni ? c : 0, P.sgates, sg, &s_chunk, P.gates, P.ngates, s_act,
+                                   fixed, P, hb, s_mem);
         }
         for (int j = warp; j < ntl; j += NWARPS) {
             const unsigned long long Tj = member_tile(T, j, h, hb);
@@ -2249,6 +2491,14 @@ cudaError_t launch_fidelity(const uint8_t *arena, const unsigned long long *tabl
     const int g = (unsigned long long)grid < nchunks ? grid : (int)nchunks;
     fidelity_kernel<<<g, 32 * TILE_WARPS, tile_smem_bytes(c, 2), st>>>(
         arena, table, c, ntiles, (int)ch, rs, chunk_sums, scal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_run_tables(const DRun *runs, const int2 *classes, int nclasses, const RGate *rgates, int c,
+                              double2 *tab, uint8_t *meta, RunClass *rcls, DevScalars *scal, int grid,
+                              cudaStream_t st) {
+    run_tables_kernel<<<grid < nclasses ? grid : nclasses, 256, 0, st>>>(runs, classes, nclasses, rgates, c, tab,
+                                                                       meta, rcls, scal);
     return cudaGetLastError();
 }
 

@@ -43,7 +43,8 @@ struct DevScalars {
     unsigned long long hist[MAX_LEVELS];
     unsigned long long items_done, items_skipped;
     unsigned long long work;        // item counter of the sweep launch in flight
-    unsigned long long pad[2];
+    unsigned long long run_dp;      // FP64 instructions executed by diagonal runs (running total)
+    unsigned long long pad[1];
 };
 
 // A gate prepared for one sweep (positions are item-buffer bits).
@@ -71,6 +72,7 @@ struct SGate {
     uint8_t one_mask;               // diagonal: bit r set when entry r is exactly 1
     uint8_t nins;                   // buffer bits pinned by targets and local controls
     uint8_t ins[12];                // those bits, ascending
+    int16_t run;                    // >= 0: first gate of diagonal run `run`; -2 inside a run; -1 none
 };
 
 // Entry classes of a matrix entry u, decided on the host so that device
@@ -87,6 +89,49 @@ enum : unsigned {
 };
 
 constexpr int MAX_SWEEP_GATES = 512;    // gates per sweep (depth limit)
+
+// Diagonal runs: two or more consecutive diagonal gates of a sweep applied
+// as one diagonal operator.  At index x the gates whose controls hold
+// contribute their entry at x's target sub-index; entries exactly 1
+// contribute nothing, entries -1, i, -i are collected as i^k, the other
+// entries are multiplied in gate order into T (gates on qubits >= c only,
+// constant over a tile) and L (the rest); a <- i^k * ((T*L) a).
+
+// A diagonal gate of a run, with its entries classified on the host.
+struct RGate {
+    double e[8];                    // entry r (re, im), r < 2^k
+    unsigned long long cm, cv;      // controls over global index bits, required values
+    uint8_t k, t0, t1;              // targets (global qubits)
+    uint8_t code[4];                // entry r: 0 exactly 1, 1 unit, 2 general
+    uint8_t uexp[4];                // unit entry r = i^uexp[r]
+    uint8_t pad;
+};
+
+constexpr int RUN_QMAX = 4;             // class bits of a tabled run (2^4 tables)
+
+// One diagonal run of a flush.  The local product L depends on the tile
+// bits (x < 2^c) and on the class bits q[] (the qubits >= c that local
+// gates use); when tabled, L is read from 2^nq tables of 2^c entries.
+struct DRun {
+    unsigned long long table;       // first table entry of the run (tabled runs)
+    int cls;                        // first class summary of the run (tabled runs)
+    int tg, nt;                     // tile gates: rgates[tg .. tg+nt-1]
+    int lg, nl;                     // local gates: rgates[lg .. lg+nl-1]
+    int first, len;                 // the run's gates in its sweep (gate index, count)
+    int nq;                         // class bits
+    int tabled;
+    int q[RUN_QMAX];                // class bit i = index bit q[i]
+};
+
+// Per class of a tabled run: where L or a unit factor exists.
+struct RunClass {
+    uint32_t active;                // entries with L or a unit power != 1
+    uint32_t have;                  // entries with L (a general product)
+    uint32_t pin_mask, pin_val;     // tile bits common to every active entry
+};
+
+// Table entry meta byte: bit 0 L exists, bits 1-2 unit exponent.
+
 constexpr int GATE_CHUNK = 48;          // gates staged in shared memory at a time
 
 // Codec configuration of a state.
@@ -121,6 +166,12 @@ struct SweepParams {
     int unit_shift;                 // log2 of the tiles one ladder decision covers
     unsigned long long *unit_bytes; // sizing pass: stream bytes per (stride, level); else null
     const uint8_t *unit_level;      // encode pass: ladder level of every stride; else null
+    const DRun *runs;               // diagonal runs of the flush (SGate::run indexes them)
+    const RGate *rgates;
+    const double2 *rtab;            // run tables (value of L)
+    const uint8_t *rmeta;           // run tables (meta bytes)
+    const RunClass *rcls;
+    int run_first, nruns;           // this sweep's runs: runs[run_first .. run_first+nruns-1]
 };
 
 // End-of-pass bookkeeping of one state (norm, scale, used bytes).

@@ -31,7 +31,8 @@ EXPORTS = ["qsim_create", "qsim_destroy", "qsim_set_stream", "qsim_set_aalc", "q
            "qsim_profile", "qsim_encode_noalloc", "qsim_flush_batch", "qsim_server_create",
            "qsim_server_submit", "qsim_server_result", "qsim_server_wait", "qsim_server_drain",
            "qsim_server_stats", "qsim_server_destroy", "qsim_set_pool", "qsim_fp64_rate",
-           "qsim_save", "qsim_load", "qsim_set_aalc_unit", "qsim_export_tile_set"]
+           "qsim_save", "qsim_load", "qsim_set_aalc_unit", "qsim_export_tile_set",
+           "qsim_set_fusion"]
 
 
 class QsimError(RuntimeError):
@@ -113,6 +114,7 @@ def load() -> C.CDLL:
         "qsim_set_aalc": ([vp, C.c_double, dp, C.c_int], C.c_int),
         "qsim_set_aalc_unit": ([vp, C.c_int], C.c_int),
         "qsim_set_normalize": ([vp, C.c_int], C.c_int),
+        "qsim_set_fusion": ([vp, C.c_int], C.c_int),
         "qsim_set_schedule": ([vp, C.c_int, C.c_int, C.c_int], C.c_int),
         "qsim_set_pool": ([vp, vp, C.c_size_t], C.c_int),
         "qsim_fp64_rate": ([C.c_int, C.POINTER(C.c_double)], C.c_int),
@@ -313,6 +315,11 @@ class State:
 
     def set_normalize(self, on: bool):
         self._check(self._L.qsim_set_normalize(self.h, int(bool(on))))
+
+    def set_fusion(self, diag_runs: bool):
+        """Runs of consecutive diagonal gates as one operator (default) or
+        every gate on its own."""
+        self._check(self._L.qsim_set_fusion(self.h, int(bool(diag_runs))))
 
     def set_schedule(self, tile_log2: int, hmax: int = 4, depth: int = 512):
         self._check(self._L.qsim_set_schedule(self.h, tile_log2, hmax, depth))

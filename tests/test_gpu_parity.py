@@ -177,11 +177,14 @@ def test_aalc_ladder_streams():
 
 
 def test_none_and_lossless_equal_dense_oracle():
+    # gate by gate (no diagonal runs), the uncompressed and lossless paths
+    # are the dense FP64 simulation bit for bit
     n = 10
     gates = I.basis_gates(n, 0x155) + I.qft(n) + I.random_grid(2, 5, 5, 11)
     psi = oracle.dense_run(oracle.dense_zero(n), n, gates)
     for codec in ("none", "lossless"):
         st = qsim.State(n, 6, codec, 0.0)
+        st.set_fusion(False)
         st.apply_all(gates)
         st.flush()
         got = st.amplitudes()
