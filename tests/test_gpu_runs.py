@@ -76,7 +76,7 @@ def same(st, cs, n, c):
     assert st.stats()["alpha"] == cs.alpha
 
 
-@pytest.mark.parametrize("n,c,hmax", [(12, 8, 4), (12, 5, 4), (11, 6, 2), (10, 3, 1), (13, 8, 4)])
+@pytest.mark.parametrize("n,c,hmax", [(12, 8, 4), (12, 5, 4), (11, 6, 2), (10, 3, 2), (13, 8, 4)])
 def test_qft_runs_match_oracle(n, c, hmax):
     x = I.seeded_basis(n)
     st, cs = run_both(n, c, I.qft(n), x=x, hmax=hmax)
