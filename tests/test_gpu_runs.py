@@ -145,10 +145,11 @@ def test_gate_by_gate_mode_matches_unfused_oracle():
 
 
 def test_profile_counts_run_arithmetic():
-    # QFT-12 on 2^8 tiles: the FP64 count the profile reports equals the
+    # QFT-12 on 2^8 tiles: the FP64 count the profile reports is the
     # canonical count of the non-run gates and normalize plus what the runs
-    # execute: per run and amplitude 4 for (T L) a, 4 more for T*L, and the
-    # table / tile products; far below the gate-by-gate count
+    # execute (per visited amplitude 4 for G a, 4 more for T*L, and the
+    # table and tile products): 78 against 116 per amplitude gate by gate
+    # (12 Hadamards cost 48 of either)
     n, c = 12, 8
     x = I.seeded_basis(n)
     gates = I.qft(n)
@@ -161,5 +162,5 @@ def test_profile_counts_run_arithmetic():
         st.apply_all(gates)
         st.flush()
         counts[fuse] = st.profile()["dp_ops"] / (1 << n)
-    assert counts[True] < 0.6 * counts[False]
+    assert counts[True] < 0.75 * counts[False]
     assert counts[True] > 0
