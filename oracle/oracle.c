@@ -115,7 +115,7 @@ static int unit_factor(double ur, double ui, double dr, double di)
  * Hadamard row on two equal amplitudes gives an exact zero).  Every other
  * row: the first term is a product, later terms fused multiply-adds. */
 static void row_eval(const double *m, int dim, int r, const double *x,
-                     const int *present, double *yr, double *yi)
+                     const int *present, int unscaled, double *yr, double *yi)
 {
     int first = -1, count = 0, factored = 1;
     for (int c = 0; c < dim; ++c) {
@@ -142,6 +142,7 @@ static void row_eval(const double *m, int dim, int r, const double *x,
             else { sr = sr + tr; si = si + ti; }
         }
         if (!started) { *yr = 0.0; *yi = 0.0; return; }
+        if (unscaled) { *yr = sr; *yi = si; return; }     /* d taken out of the sweep (scaled gates) */
         term_first(dr, di, sr, si, yr, yi);
         return;
     }
@@ -180,8 +181,20 @@ static int gate_is_diagonal(const or_gate *g)
  * not in the buffer is allowed only for a diagonal gate.
  * Returns 0, or -1 when a non-diagonal gate has a target outside the buffer.
  */
+static int apply_gate_rows(double *a, int mb, const int *qb, uint64_t fixed,
+                           const or_gate *g, int unscaled);
+
 static int apply_gate_buf(double *a, int mb, const int *qb, uint64_t fixed,
                           const or_gate *g)
+{
+    return apply_gate_rows(a, mb, qb, fixed, g, 0);
+}
+
+/* apply_gate_buf, with unscaled set: every factored row yields its sum S
+ * without the final multiplication by its first entry d (the scaled gates
+ * of a sweep, see gate_scale). */
+static int apply_gate_rows(double *a, int mb, const int *qb, uint64_t fixed,
+                           const or_gate *g, int unscaled)
 {
     int k = g->k, dim = 1 << k;
     int pos[2] = {-1, -1};
@@ -227,7 +240,7 @@ static int apply_gate_buf(double *a, int mb, const int *qb, uint64_t fixed,
             }
         }
         for (int r = 0; r < dim; ++r)
-            if (present[r]) row_eval(g->m, dim, r, x, present, &y[2 * r], &y[2 * r + 1]);
+            if (present[r]) row_eval(g->m, dim, r, x, present, unscaled, &y[2 * r], &y[2 * r + 1]);
         for (int r = 0; r < dim; ++r)
             if (present[r]) {
                 a[2 * idx[r]] = y[2 * r];
@@ -339,9 +352,57 @@ static void apply_diag_run(double *a, int mb, const int *qb, uint64_t fixed, con
     }
 }
 
+/*
+ * Scaled gates (the O3 gate computation, with fuse set): a gate without
+ * controls whose every row has two or more nonzero entries, each its
+ * first nonzero entry d times 1, -1, i or -i, with the same real d in every
+ * row (a Hadamard; H (x) H), is d times a matrix of units.  A scalar commutes
+ * with every linear map, so a sweep applies the product D of its scaled
+ * gates' d (multiplied in gate order, starting from 1) together with the
+ * normalize scale at decompression, a * (alpha * D), and each scaled gate
+ * only forms its rows' unit sums.  Returns d for a scaled gate, else 0.
+ */
+static double gate_scale(const or_gate *g)
+{
+    if (g->cmask || gate_is_diagonal(g)) return 0.0;
+    int dim = 1 << g->k;
+    double d = 0.0;
+    for (int r = 0; r < dim; ++r) {
+        int first = -1, count = 0;
+        for (int c = 0; c < dim; ++c) {
+            double ur = g->m[2 * (r * dim + c)], ui = g->m[2 * (r * dim + c) + 1];
+            if (ur == 0.0 && ui == 0.0) continue;
+            ++count;
+            if (first < 0) first = c;
+            else if (unit_factor(ur, ui, g->m[2 * (r * dim + first)], g->m[2 * (r * dim + first) + 1]) < 0)
+                return 0.0;
+        }
+        if (count < 2) return 0.0;
+        double dr = g->m[2 * (r * dim + first)], di = g->m[2 * (r * dim + first) + 1];
+        if (di != 0.0) return 0.0;
+        if (r == 0) d = dr;
+        else if (memcmp(&dr, &d, sizeof d) != 0) return 0.0;
+    }
+    return d;
+}
+
+/* D of a sweep: the product of its scaled gates' d in gate order (1 when
+ * fuse is off or there are none). */
+static double sweep_scale(const or_gate *g, int ng, int fuse)
+{
+    double D = 1.0;
+    if (!fuse) return D;
+    for (int i = 0; i < ng; ++i) {
+        double d = gate_scale(&g[i]);
+        if (d != 0.0) D = D * d;
+    }
+    return D;
+}
+
 /* A sweep's gates applied to an item buffer in order: with fuse set, each
  * run of two or more consecutive diagonal gates as one diagonal operator
- * (apply_diag_run), every other gate on its own.  Returns 0, or -1 when a
+ * (apply_diag_run) and each scaled gate without its d (the sweep applies D
+ * at decompression), every other gate on its own.  Returns 0, or -1 when a
  * non-diagonal gate has a target outside the buffer. */
 static int apply_gates_buf(double *a, int mb, const int *qb, uint64_t fixed, const or_gate *g, int ng,
                            int c, int fuse)
@@ -356,7 +417,7 @@ static int apply_gates_buf(double *a, int mb, const int *qb, uint64_t fixed, con
             i = j;
             continue;
         }
-        if (apply_gate_buf(a, mb, qb, fixed, &g[i]) != 0) return -1;
+        if (apply_gate_rows(a, mb, qb, fixed, &g[i], fuse && gate_scale(&g[i]) != 0.0) != 0) return -1;
         ++i;
     }
     return 0;
@@ -1244,7 +1305,7 @@ static int csim_sweep_units(or_csim *cs, const or_gate *g, int ng, const int *H,
         qb[c + i] = H[i];
         hmask_tile |= 1ull << (H[i] - c);
     }
-    double alpha = cs->alpha;
+    double alpha = cs->alpha * sweep_scale(g, ng, cs->fuse);   /* normalize and scaled gates */
     double *buf = malloc(((size_t)1 << mb) * 16);
     double *state = malloc(((size_t)1 << n) * 16);
     int rc = 0;
@@ -1297,7 +1358,7 @@ static int csim_sweep_items(or_csim *cs, const or_gate *g, int ng, const int *H,
     for (int q = c; q < n; ++q) fmask |= 1ull << q;
     for (int i = 0; i < h; ++i) fmask &= ~(1ull << H[i]);
 
-    double alpha = cs->alpha;
+    double alpha = cs->alpha * sweep_scale(g, ng, cs->fuse);   /* normalize and scaled gates */
     double *buf = malloc(((size_t)1 << mb) * 16);
     int rc = 0;
     uint64_t item = 0;
@@ -1388,6 +1449,7 @@ int or_item_sweep(int n, int c, const int *H, int h, uint64_t base_tile,
     for (int i = 0; i < h; ++i) fmask &= ~(1ull << H[i]);
     uint64_t fixed = base_tile << c;
     const int moves = sweep_moves_tiles(g, ng, c);
+    alpha = alpha * sweep_scale(g, ng, fuse);                  /* normalize and scaled gates */
     int touched = alpha != 1.0 && !moves;
     for (int i = 0; i < ng && !touched; ++i)
         if (gate_touches(&g[i], fixed, fmask)) touched = 1;
@@ -1530,6 +1592,7 @@ int or_stride_sweep(int n, int c, const int *H, int h, int ut, uint64_t umax, ui
 {
     uint64_t N = 1ull << c, nt = 1ull << ut;
     int mb = c + h, rc = 0;
+    alpha = alpha * sweep_scale(g, ng, fuse);                  /* normalize and scaled gates */
     int qb[64];
     for (int p = 0; p < c; ++p) qb[p] = p;
     uint64_t hmask_tile = 0;

@@ -1,15 +1,24 @@
-"""Pins of the oracle's diagonal runs (O3): two or more consecutive diagonal
-gates of a sweep applied as one diagonal operator whose entry is the product
-of the gates' entries (the product of diagonal matrices, Sec. II), with
-unit factors (-1, i, -i) taken exactly and the other factors multiplied in
-gate order, split into the part on qubits >= c and the rest.
+"""Pins of the oracle's gate fusion (O3).
+
+Diagonal runs: two or more consecutive diagonal gates of a sweep applied
+as one diagonal operator whose entry is the product of the gates' entries
+(the product of diagonal matrices, Sec. II), with unit factors (-1, i, -i)
+taken exactly and the other factors multiplied in gate order, split into
+the part on qubits >= c and the rest.  Scaled gates: an uncontrolled gate
+that is d times a matrix of units with one real d (a Hadamard) forms only
+its unit sums; the sweep multiplies the product of those d into the
+normalize scale at decompression (a scalar commutes with linear maps).
 
 * Within rounding of the gates applied one by one (the dense simulator O1),
   on QFTs, grid circuits and random runs of controlled phases, CZ, S, T,
   Rz and two-target diagonal gates with controls on low and high qubits.
 * Exact where the arithmetic is exact: runs of unit factors only give O1's
   amplitudes bit for bit, and so do runs in which every amplitude meets at
-  most one other factor (G = that entry: the gate's own product).
+  most one other factor (G = that entry: the gate's own product); Hadamards
+  on a basis state (one nonzero term per row) give O1's amplitudes bit for
+  bit, d^n either way.
+* Gates that are not scaled (controlled Hadamards, sqrt(X), X, a lone
+  diagonal gate) keep the gate-by-gate arithmetic: bit-identical to O1.
 * The fused QFT against its closed form e^{2 pi i x k / N} / sqrt(N).
 * Runs are really fused: the QFT's amplitudes differ in rounding from the
   gate-by-gate sweep somewhere.
@@ -81,13 +90,18 @@ def test_fused_runs_within_rounding_of_dense(n, c, hmax, depth):
         assert np.max(np.abs(got - psi)) <= 1e-14
 
 
+def sx(q):
+    # a mixing gate that is not scaled (its rows' first entries differ)
+    return I.Gate(I.MAT_SQRT_X, (q,), name="SX")
+
+
 def test_unit_runs_are_exact():
     # CZ, Z, S, S^dagger, multi-controlled Z: factors -1, i, -i only
     n, c = 9, 4
     rng = np.random.default_rng(11)
     gates = I.basis_gates(n, 0x155)
     for _ in range(4):
-        gates += [I.h(q) for q in range(n)]
+        gates += [sx(q) for q in range(n)]
         for _ in range(8):
             a, b, d = (int(v) for v in rng.permutation(n)[:3])
             pick = int(rng.integers(0, 4))
@@ -111,13 +125,13 @@ def test_runs_with_one_general_factor_per_amplitude_are_exact():
     # one general factor, so G is that entry and the product is the gate's own
     n, c = 9, 4
     rng = np.random.default_rng(5)
-    gates = I.basis_gates(n, 0x0F3) + [I.h(q) for q in range(n)]
+    gates = I.basis_gates(n, 0x0F3) + [sx(q) for q in range(n)]
     for t, a in ((1, 6), (7, 2), (5, 8), (0, 3)):
         p = [cmath.exp(1j * float(v)) for v in rng.uniform(0.1, 3.0, 3)]
         gates.append(I.Gate(diag(1, p[0]), (t,), (a,), (0,)))
         gates.append(I.Gate(diag(1, p[1]), (t,), (a,), (1,)))
         gates.append(I.Gate(diag(p[2], 1), (t,)))                 # the other target value
-        gates += [I.h(q) for q in range(n)]
+        gates += [sx(q) for q in range(n)]
     psi = oracle.dense_run(oracle.dense_zero(n), n, gates)
     got = lossless(n, c, gates, 2, 512)
     assert np.array_equal(got.view(np.uint64), psi.view(np.uint64))
@@ -139,3 +153,30 @@ def test_runs_are_fused():
     a = lossless(n, c, gates, 4, 512, fuse=True)
     b = lossless(n, c, gates, 4, 512, fuse=False)
     assert not np.array_equal(a.view(np.uint64), b.view(np.uint64))
+
+
+def test_hadamards_on_a_basis_state_are_exact():
+    # every row meets one nonzero amplitude: each Hadamard multiplies by d
+    # once, gate by gate or folded into the sweep's scale (d^n, multiplied
+    # in the same order, when the Hadamards share one sweep)
+    for n, c, hmax in ((9, 5, 4), (10, 6, 4), (7, 7, 1)):
+        gates = I.basis_gates(n, 0x1A5 & ((1 << n) - 1)) + [I.h(q) for q in range(n)]
+        psi = oracle.dense_run(oracle.dense_zero(n), n, gates)
+        got = lossless(n, c, gates, hmax, 512)
+        assert np.array_equal(got.view(np.uint64), psi.view(np.uint64))
+        assert len(set(np.abs(got.real).view(np.uint64).tolist())) == 1
+
+
+def test_gates_that_are_not_scaled_keep_their_arithmetic():
+    n, c = 9, 4
+    rng = np.random.default_rng(17)
+    gates = I.basis_gates(n, 0x0B6)
+    for _ in range(3):
+        gates += [sx(q) for q in range(n)]
+        gates.append(I.Gate(I.MAT_H, (2,), (7,)))                      # controlled Hadamard
+        gates.append(I.x(int(rng.integers(0, n))))
+        gates.append(I.cphase(0.3, 1, 5))                               # a lone diagonal gate
+        gates += [sx(q) for q in rng.permutation(n)[:4]]
+    psi = oracle.dense_run(oracle.dense_zero(n), n, gates)
+    got = lossless(n, c, gates, 4, 512)
+    assert np.array_equal(got.view(np.uint64), psi.view(np.uint64))
