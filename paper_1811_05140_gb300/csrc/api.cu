@@ -61,6 +61,8 @@ cudaError_t launch_probs(const uint8_t *arena, const unsigned long long *table, 
                          unsigned long long ntiles, const int *qsel, int nq,
                          unsigned long long *buckets, DevScalars *scal, int grid, cudaStream_t st);
 unsigned long long fidelity_chunk(unsigned long long ntiles);
+cudaError_t launch_sweep_scales(const SGate *sg, const DGate *dg, const int2 *bounds, int ns, double *D,
+                                cudaStream_t st);
 cudaError_t launch_run_tables(const DRun *runs, const int2 *classes, int nclasses, const RGate *rgates, int c,
                               double2 *tab, uint8_t *meta, RunClass *rcls, DevScalars *scal, int grid,
                               cudaStream_t st);
@@ -207,6 +209,28 @@ unsigned long long row_factoring(const HostGate &g) {
     return fac;
 }
 
+// A scaled gate: no controls, not diagonal, every row factored (two or
+// more nonzero entries, each a unit multiple of the row's first nonzero
+// entry d) with the same real d in every row (a Hadamard, H (x) H).  Such
+// a gate is d times a matrix of units; with fusion on, the sweep applies d
+// in its decompression scale and the gate only forms its rows' sums.
+bool is_scaled_gate(const HostGate &g) {
+    if (g.cm || g.diag) return false;
+    const int dim = 1 << g.k;
+    const unsigned long long fac = row_factoring(g);
+    double d = 0.0;
+    for (int r = 0; r < dim; ++r) {
+        if (!((fac >> r) & 1ull)) return false;
+        int c = 0;
+        while (g.m[2 * (r * dim + c)] == 0.0 && g.m[2 * (r * dim + c) + 1] == 0.0) ++c;
+        const double dr = g.m[2 * (r * dim + c)], di = g.m[2 * (r * dim + c) + 1];
+        if (di != 0.0) return false;
+        if (r == 0) d = dr;
+        else if (std::memcmp(&dr, &d, sizeof d) != 0) return false;
+    }
+    return true;
+}
+
 // Entries all exactly 0 or 1, one 1 in every row and every column: the
 // gate maps basis states to basis states.
 bool is_permutation(const HostGate &g) {
@@ -233,8 +257,9 @@ double entry_cost(double ur, double ui, bool first) {
     return 2.0;
 }
 
-// FP64 instructions a gate needs on an n-qubit state (controls restrict it)
-double gate_dp_ops(const HostGate &g, int n) {
+// FP64 instructions a gate needs on an n-qubit state (controls restrict
+// it); a scaled gate applied without its d (fusion) costs only its sums
+double gate_dp_ops(const HostGate &g, int n, bool unscaled = false) {
     int dim = 1 << g.k;
     double groups = std::ldexp(1.0, n - g.k - popcount64(g.cm));
     const unsigned long long fac = g.diag ? 0ull : row_factoring(g);
@@ -251,7 +276,8 @@ double gate_dp_ops(const HostGate &g, int n) {
             double ur = g.m[2 * (r * dim + c)], ui = g.m[2 * (r * dim + c) + 1];
             if (ur == 0.0 && ui == 0.0) continue;
             // factored: one addition per later term, the first entry's product once
-            per += 2.0 * (factored ? (first ? entry_cost(ur, ui, true) : 1.0) : entry_cost(ur, ui, first));
+            per += 2.0 * (factored ? (first ? (unscaled ? 0.0 : entry_cost(ur, ui, true)) : 1.0)
+                                   : entry_cost(ur, ui, first));
             first = false;
         }
     }
@@ -325,6 +351,11 @@ struct qsim_state {
     size_t rtab_cap = 0, rmeta_cap = 0;
     qs::RunClass *rcls = nullptr;
     size_t rcls_cap = 0;
+    // per sweep of the flush: gate bounds and the product of its scaled gates' d
+    std::vector<int2> hbounds;
+    int2 *dbounds = nullptr;
+    double *dscale = nullptr;
+    size_t scale_cap = 0;
 };
 
 namespace {
@@ -710,6 +741,8 @@ qsim_status qsim_destroy(qsim_t h) {
     if (h->rtab) cudaFree(h->rtab);
     if (h->rmeta) cudaFree(h->rmeta);
     if (h->rcls) cudaFree(h->rcls);
+    if (h->dbounds) cudaFree(h->dbounds);
+    if (h->dscale) cudaFree(h->dscale);
     for (cudaEvent_t ev : h->events) cudaEventDestroy(ev);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
@@ -866,6 +899,8 @@ struct FlushCtx {
     int regrows = 0;
     std::vector<int> run_first, nruns;    // per sweep: its diagonal runs
     std::vector<char> in_run;             // per gate: part of a diagonal run
+    std::vector<char> scaled;             // per gate: a scaled gate applied without its d
+    std::vector<char> sweep_scaled;       // per sweep: holds a scaled gate (its scale D is not 1)
     unsigned long long run_dp0 = 0;       // device FP64 count of runs when the flush began
 };
 
@@ -1064,6 +1099,16 @@ qsim_status stage_flush(qsim_t h, FlushCtx &fc, cudaStream_t st) {
     for (size_t si = 0; si < ns; ++si)
         for (int gi = fc.sweeps[si].lo; gi < fc.sweeps[si].hi; ++gi)
             prepare_gate(h->queue[gi], h->c, fc.sweeps[si], h->hgates[gi], h->hsg[gi]);
+    fc.scaled.assign(ng, 0);
+    fc.sweep_scaled.assign(ns, 0);
+    if (h->fuse)
+        for (size_t si = 0; si < ns; ++si)
+            for (int gi = fc.sweeps[si].lo; gi < fc.sweeps[si].hi; ++gi)
+                if (is_scaled_gate(h->queue[gi])) {
+                    h->hsg[gi].unscaled = 1;
+                    fc.scaled[gi] = 1;
+                    fc.sweep_scaled[si] = 1;
+                }
     plan_runs(h, fc);
     CK(hcopy(h, h->dgates, h->hgates, ng * sizeof(qs::DGate), cudaMemcpyHostToDevice, st));
     CK(hcopy(h, h->dsg, h->hsg, ng * sizeof(qs::SGate), cudaMemcpyHostToDevice, st));
@@ -1071,6 +1116,24 @@ qsim_status stage_flush(qsim_t h, FlushCtx &fc, cudaStream_t st) {
         qsim_status rs = stage_runs(h, fc, st);
         if (rs != QSIM_OK) return rs;
     }
+    // the scale D of every sweep (product of its scaled gates' d), on the device
+    if (h->scale_cap < ns) {
+        CK(cudaStreamSynchronize(st));
+        if (h->dbounds) cudaFree(h->dbounds);
+        if (h->dscale) cudaFree(h->dscale);
+        h->dbounds = nullptr;
+        h->dscale = nullptr;
+        h->scale_cap = 0;
+        const size_t cap = std::max<size_t>(ns, 64);
+        CK(cudaMalloc(&h->dbounds, cap * sizeof(int2)));
+        CK(cudaMalloc(&h->dscale, cap * sizeof(double)));
+        h->scale_cap = cap;
+    }
+    h->hbounds.resize(ns);
+    for (size_t si = 0; si < ns; ++si) h->hbounds[si] = make_int2(fc.sweeps[si].lo, fc.sweeps[si].hi);
+    CK(hcopy(h, h->dbounds, h->hbounds.data(), ns * sizeof(int2), cudaMemcpyHostToDevice, st));
+    ++h->launches;
+    CK(qs::launch_sweep_scales(h->dsg, h->dgates, h->dbounds, (int)ns, h->dscale, st));
     if (h->profiling) {
         while (h->events.size() < 2 * ns) {
             cudaEvent_t ev;
@@ -1118,6 +1181,7 @@ qs::SweepParams sweep_params(qsim_t h, const FlushCtx &fc, size_t j) {
     p.rcls = h->rcls;
     p.run_first = fc.run_first.empty() ? 0 : fc.run_first[j];
     p.nruns = fc.nruns.empty() ? 0 : fc.nruns[j];
+    p.dscale = (!fc.sweep_scaled.empty() && fc.sweep_scaled[j]) ? h->dscale + j : nullptr;
     p.use_alpha = h->normalize;
     p.low_free = 1;
     p.moves_tiles = 1;
@@ -1233,9 +1297,10 @@ qsim_status finish_flush(qsim_t h, FlushCtx &fc, bool timed) {
             CK(cudaEventElapsedTime(&ms, h->events[2 * j], h->events[2 * j + 1]));
             h->prof.sweep_ms += ms;
             h->prof.sweep_launches += 1;
-            double dp = h->normalize ? 2.0 * std::ldexp(1.0, h->n) : 0.0;
+            // the decompression scale: normalize and / or the scaled gates' D
+            double dp = (h->normalize || fc.sweep_scaled[j]) ? 2.0 * std::ldexp(1.0, h->n) : 0.0;
             for (int gi = fc.sweeps[j].lo; gi < fc.sweeps[j].hi; ++gi)
-                if (!fc.in_run[gi]) dp += gate_dp_ops(h->queue[gi], h->n);
+                if (!fc.in_run[gi]) dp += gate_dp_ops(h->queue[gi], h->n, fc.scaled[gi]);
             h->prof.dp_ops += dp;
             const unsigned long long in = j == 0 ? fc.used_before : h->hused[j - 1];
             h->prof.bytes += (double)in + (double)h->hused[j] + 32.0 * (double)h->ntiles;

@@ -227,7 +227,7 @@ __device__ __forceinline__ void unit_times(unsigned f, double xr, double xi, dou
 template <int DIM>
 __device__ __forceinline__ void row_eval(const double *m, unsigned long long cls, unsigned long long fac,
                                          int r, const double *xr, const double *xi, double &yr,
-                                         double &yi) {
+                                         double &yi, bool unscaled = false) {
     bool first = true;
     double ar = 0.0, ai = 0.0;
     if ((fac >> r) & 1ull) {
@@ -249,6 +249,7 @@ __device__ __forceinline__ void row_eval(const double *m, unsigned long long cls
             ar = __dadd_rn(ar, tr);
             ai = __dadd_rn(ai, ti);
         }
+        if (unscaled) { yr = ar; yi = ai; return; }      // d is in the sweep's scale
         term_first(dcode, dr, di, ar, ai, yr, yi);
         return;
     }
@@ -399,6 +400,24 @@ __device__ void one_target(double *re, double *im, int mb, const SGate &s, const
         uint8_t pos[12];
         for (int i = 0; i < nins; ++i) pos[i] = s.ins[i];
         const unsigned lcv = s.lcv;
+        if (s.unscaled) {
+            // a scaled gate: d is in the sweep's scale, the rows are their sums
+            for (unsigned f = threadIdx.x; f < cnt; f += SWEEP_THREADS) {
+                unsigned l = f << red;
+                for (int i = 0; i < nins; ++i) l = insert_zero(l, pos[i]);
+                const unsigned l0 = l | lcv;
+                const unsigned l1 = l0 | bit;
+                const double x0r = re[l0], x0i = im[l0], x1r = re[l1], x1i = im[l1];
+                double t0r, t0i, t1r, t1i;
+                unit_times(f0, x1r, x1i, t0r, t0i);
+                unit_times(f1, x1r, x1i, t1r, t1i);
+                re[l0] = __dadd_rn(x0r, t0r);
+                im[l0] = __dadd_rn(x0i, t0i);
+                re[l1] = __dadd_rn(x0r, t1r);
+                im[l1] = __dadd_rn(x0i, t1i);
+            }
+            return;
+        }
         for (unsigned f = threadIdx.x; f < cnt; f += SWEEP_THREADS) {
             unsigned l = f << red;
             for (int i = 0; i < nins; ++i) l = insert_zero(l, pos[i]);
@@ -420,8 +439,8 @@ __device__ void one_target(double *re, double *im, int mb, const SGate &s, const
         unsigned l1 = l0 | bit;
         double xr[2] = {re[l0], re[l1]}, xi[2] = {im[l0], im[l1]};
         double y0r, y0i, y1r, y1i;
-        row_eval<2>(m, s.cls, s.fac, 0, xr, xi, y0r, y0i);
-        row_eval<2>(m, s.cls, s.fac, 1, xr, xi, y1r, y1i);
+        row_eval<2>(m, s.cls, s.fac, 0, xr, xi, y0r, y0i, s.unscaled);
+        row_eval<2>(m, s.cls, s.fac, 1, xr, xi, y1r, y1i, s.unscaled);
         re[l0] = y0r; im[l0] = y0i;
         re[l1] = y1r; im[l1] = y1i;
     }
@@ -441,7 +460,7 @@ __device__ void two_target(double *re, double *im, int mb, const SGate &s, const
         }
         double yr[4], yi[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) row_eval<4>(dg.m, s.cls, s.fac, r, xr, xi, yr[r], yi[r]);
+        for (int r = 0; r < 4; ++r) row_eval<4>(dg.m, s.cls, s.fac, r, xr, xi, yr[r], yi[r], s.unscaled);
 #pragma unroll
         for (int q = 0; q < 4; ++q) { re[idx[q]] = yr[q]; im[idx[q]] = yi[q]; }
     }
@@ -559,6 +578,23 @@ __global__ void __launch_bounds__(256) run_tables_kernel(const DRun *runs, const
         }
         __syncthreads();
     }
+}
+
+// D of every sweep of a flush: the product, in gate order starting from 1,
+// of the first nonzero entry d of row 0 of each scaled gate (a gate that is
+// d times a matrix of units), sweep j holding gates bounds[j].x .. .y - 1.
+__global__ void sweep_scale_kernel(const SGate *sg, const DGate *dg, const int2 *bounds, int ns, double *D) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ns) return;
+    double p = 1.0;
+    for (int g = bounds[j].x; g < bounds[j].y; ++g) {
+        if (!sg[g].unscaled) continue;
+        const int dim = 1 << sg[g].k;
+        int e = 0;
+        while (e < dim && ((sg[g].cls >> (3 * e)) & 7ull) == EC_ZERO) ++e;
+        p = __dmul_rn(p, dg[g].m[2 * e]);
+    }
+    D[j] = p;
 }
 
 // Per member tile of an item, for the run being applied.
@@ -1834,6 +1870,8 @@ __global__ void __launch_bounds__(SWEEP_THREADS, QS_SWEEP_MIN_BLOCKS) sweep_kern
                 // an earlier pass of this state failed: leave its state alone
                 s_skip = *((volatile unsigned *)&P.scal->err) != 0u;
                 s_alpha = P.use_alpha ? P.scal->alpha : 1.0;
+                // the scaled gates' product joins the normalize scale
+                if (P.dscale) s_alpha = __dmul_rn(s_alpha, *P.dscale);
             }
             __syncthreads();
             cur = e;
@@ -2499,6 +2537,12 @@ cudaError_t launch_run_tables(const DRun *runs, const int2 *classes, int nclasse
                               cudaStream_t st) {
     run_tables_kernel<<<grid < nclasses ? grid : nclasses, 256, 0, st>>>(runs, classes, nclasses, rgates, c, tab,
                                                                        meta, rcls, scal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_scales(const SGate *sg, const DGate *dg, const int2 *bounds, int ns, double *D,
+                                cudaStream_t st) {
+    sweep_scale_kernel<<<(ns + 127) / 128, 128, 0, st>>>(sg, dg, bounds, ns, D);
     return cudaGetLastError();
 }
 

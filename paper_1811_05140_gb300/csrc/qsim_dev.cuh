@@ -73,6 +73,7 @@ struct SGate {
     uint8_t nins;                   // buffer bits pinned by targets and local controls
     uint8_t ins[12];                // those bits, ascending
     int16_t run;                    // >= 0: first gate of diagonal run `run`; -2 inside a run; -1 none
+    uint8_t unscaled;               // scaled gate: factored rows give their sums, d is in the sweep's scale
 };
 
 // Entry classes of a matrix entry u, decided on the host so that device
@@ -172,6 +173,7 @@ struct SweepParams {
     const uint8_t *rmeta;           // run tables (meta bytes)
     const RunClass *rcls;
     int run_first, nruns;           // this sweep's runs: runs[run_first .. run_first+nruns-1]
+    const double *dscale;           // product of the sweep's scaled gates' d (null: 1)
 };
 
 // End-of-pass bookkeeping of one state (norm, scale, used bytes).
