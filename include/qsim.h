@@ -171,6 +171,16 @@ qsim_status qsim_set_normalize(qsim_t h, int on);
  */
 qsim_status qsim_set_schedule(qsim_t h, int tile_log2, int hmax, int depth);
 
+/*
+ * qsim_set_sweep_threads -- CTA size of the sweep kernel: 128, 256 (the
+ * default) or 512 threads, compiled for 3, 3 and 1 resident CTAs per SM
+ * (the register budget of each launch shape).  Results do not depend on it;
+ * the autotuner times the shapes.  qsim_flush_batch launches with the
+ * first handle's shape.  Flushes queued gates first.  Errors: ARG (other
+ * sizes).
+ */
+qsim_status qsim_set_sweep_threads(qsim_t h, int threads);
+
 /* Place the state's two stream arenas in a caller-owned device buffer (for
  * example the storage of a torch tensor) instead of library allocations
  * (Sec. III: the strides are stored compressed; this chooses where).
@@ -439,6 +449,8 @@ typedef struct {
     int n_gates;
     int readout[16];
     int tile_log2, hmax, depth;         /* schedule (qsim_set_schedule); 0 = default */
+    int sweep_threads;                  /* qsim_set_sweep_threads; 0 = default (a batch launches
+                                           with its first circuit's shape) */
 } qsim_request;
 
 typedef struct {

@@ -19,11 +19,12 @@
 
 namespace qs {
 void set_global_error(const char *msg);
-size_t sweep_smem_bytes(int mb);
+size_t sweep_smem_bytes(int mb, int threads);
+bool sweep_threads_ok(int threads);
 cudaError_t launch_sweep(const SweepParams *plist, const unsigned long long *istart, int nlist,
-                         int mb, int grid, unsigned long long *work, cudaStream_t st);
+                         int mb, int grid, int threads, unsigned long long *work, cudaStream_t st);
 cudaError_t launch_sweep_sizing(const SweepParams *plist, const unsigned long long *istart, int nlist,
-                                int mb, int grid, unsigned long long *work, cudaStream_t st);
+                                int mb, int grid, int threads, unsigned long long *work, cudaStream_t st);
 cudaError_t launch_finalize_list(const FinalizeEntry *list, int n, cudaStream_t st);
 cudaError_t launch_finalize(DevScalars *scal, int use_alpha, unsigned long long *used_hist,
                             unsigned slot, int record_used, cudaStream_t st);
@@ -72,7 +73,7 @@ cudaError_t launch_fidelity(const uint8_t *arena, const unsigned long long *tabl
 cudaError_t launch_pair_sum(const Acc4 *in, Acc4 *out, unsigned long long nout, int grid,
                             cudaStream_t st);
 cudaError_t configure_kernels();
-int sweep_blocks_per_sm(int mb);
+int sweep_blocks_per_sm(int mb, int threads);
 cudaError_t fp64_rate(int device, double *fma_per_s);
 }  // namespace qs
 
@@ -338,6 +339,7 @@ struct qsim_state {
     size_t rd_cap = 0;
     unsigned long long h2d_bytes = 0, d2h_bytes = 0;   // since creation (never reset)
     int fuse = 1;                         // diagonal runs as one operator
+    int threads = qs::SWEEP_THREADS;      // sweep kernel CTA size
     // diagonal runs of the flush in progress (host staging, device copies)
     std::vector<qs::DRun> hruns;
     std::vector<qs::RGate> hrg;
@@ -1232,7 +1234,7 @@ qsim_status run_from(qsim_t h, FlushCtx &fc, size_t k) {
                            cudaMemcpyHostToDevice, h->stream));
         for (size_t j = k; j < ns; ++j) {
             const int mb = h->c + fc.sweeps[j].h;
-            const int per_sm = qs::sweep_blocks_per_sm(mb);
+            const int per_sm = qs::sweep_blocks_per_sm(mb, h->threads);
             char label[64];
             std::snprintf(label, sizeof label, "qsim sweep %u (%d gates)", fc.id0 + (unsigned)j,
                           fc.sweeps[j].hi - fc.sweeps[j].lo);
@@ -1243,15 +1245,16 @@ qsim_status run_from(qsim_t h, FlushCtx &fc, size_t k) {
                                    h->stream));
                 ++h->launches;
                 CK(qs::launch_sweep_sizing(h->dparams + ns + j, h->distart + 2 * j, 1, mb,
-                                           grid_for(h, h->hparams[j].nitems, per_sm), &h->scal->work,
-                                           h->stream));
+                                           grid_for(h, h->hparams[j].nitems, per_sm), h->threads,
+                                           &h->scal->work, h->stream));
                 ++h->launches;
                 CK(qs::launch_unit_level(h->unit_bytes, h->unit_level, nunits, h->cc.nlev, unit_limit(h),
                                          h->stream));
             }
             ++h->launches;
             CK(qs::launch_sweep(h->dparams + j, h->distart + 2 * j, 1, mb,
-                                grid_for(h, h->hparams[j].nitems, per_sm), &h->scal->work, h->stream));
+                                grid_for(h, h->hparams[j].nitems, per_sm), h->threads, &h->scal->work,
+                                h->stream));
             if (h->profiling) CK(cudaEventRecord(h->events[2 * j + 1], h->stream));
             ++h->launches;
             CK(qs::launch_finalize(h->scal, h->normalize, h->used_hist, (unsigned)j, 1, h->stream));
@@ -1427,9 +1430,9 @@ qsim_status qsim_flush_batch(qsim_t *handles, int count, int use_graph) {
     for (size_t r = 0; r < rounds; ++r) {
         const int n_r = (int)(rstart[r + 1] - rstart[r]);
         const int mb = (int)rmb[r];
-        const int per_sm = qs::sweep_blocks_per_sm(mb);
+        const int per_sm = qs::sweep_blocks_per_sm(mb, h0->threads);
         cudaError_t le = qs::launch_sweep(g_batch.dP + rstart[r], g_batch.dI + istart_at[r], n_r, mb,
-                                          grid_for(h0, ritems[r], per_sm), g_batch.dW, st);
+                                          grid_for(h0, ritems[r], per_sm), h0->threads, g_batch.dW, st);
         if (le == cudaSuccess) le = qs::launch_finalize_list(g_batch.dF + rstart[r], n_r, st);
         if (le != cudaSuccess) {
             if (use_graph) { cudaStreamEndCapture(st, &graph); if (graph) cudaGraphDestroy(graph); }
@@ -1523,6 +1526,15 @@ qsim_status qsim_set_aalc_unit(qsim_t h, int unit_log2) {
     if (unit_log2 < 0 || unit_log2 > MAX_QUBITS) return fail(h, QSIM_ERR_ARG, "unit_log2 must be 0..%d", MAX_QUBITS);
     if ((s = qsim_flush(h)) != QSIM_OK) return s;     // queued gates run under the old rule
     h->unit_log2 = unit_log2;
+    return QSIM_OK;
+}
+
+qsim_status qsim_set_sweep_threads(qsim_t h, int threads) {
+    qsim_status s = check_usable(h);
+    if (s != QSIM_OK) return s;
+    if (!qs::sweep_threads_ok(threads)) return fail(h, QSIM_ERR_ARG, "sweep threads must be 128, 256 or 512");
+    if ((s = qsim_flush(h)) != QSIM_OK) return s;
+    h->threads = threads;
     return QSIM_OK;
 }
 

@@ -265,6 +265,9 @@ __device__ __forceinline__ void row_eval(const double *m, unsigned long long cls
     yi = ai;
 }
 
+// log2 of the warps of the CTA (a power of two: 4, 8 or 16 in the sweep)
+__device__ __forceinline__ int log_nwarps() { return __ffs((int)(blockDim.x >> 5)) - 1; }
+
 __device__ __forceinline__ unsigned insert_zero(unsigned v, int p) {
     unsigned lowm = (1u << p) - 1u;
     return ((v & ~lowm) << 1) | (v & lowm);
@@ -307,7 +310,7 @@ __device__ void diag_gate(double *re, double *im, int mb, const SGate &s,
     if (nr == 0) return;
     const int fb = mb - s.nins - red;           // free bits (the low `red` bits stay 0)
     const unsigned cnt = (unsigned)nr << fb;
-    for (unsigned f = threadIdx.x; f < cnt; f += SWEEP_THREADS) {
+    for (unsigned f = threadIdx.x; f < cnt; f += blockDim.x) {
         int r = (int)((rpack >> (2 * (f >> fb))) & 3u);
         unsigned l = deposit((f & ((1u << fb) - 1u)) << red, s) | s.lcv;
         if (s.p0 >= 0) l |= (unsigned)(r & 1) << s.p0;
@@ -321,13 +324,13 @@ __device__ void diag_gate(double *re, double *im, int mb, const SGate &s,
 }
 
 // Warp-local form of diag_gate for an item of 2^mb amplitudes: warp w
-// handles the amplitudes whose top LOG_NWARPS index bits equal w, so
+// handles the amplitudes whose top log2(warps) index bits equal w, so
 // consecutive diagonal gates need only __syncwarp between them (each
 // amplitude still sees the gates in order, with the same arithmetic).
-// Needs mb - LOG_NWARPS >= 5.
+// Needs mb - log2(warps) >= 5.
 __device__ void diag_gate_warp(double *re, double *im, int mb, const SGate &s, unsigned long long fixed) {
     const int lane = threadIdx.x & 31;
-    const int cb = mb - LOG_NWARPS;                 // index bits that vary inside a warp's part
+    const int cb = mb - log_nwarps();               // index bits that vary inside a warp's part
     const unsigned inmask = (1u << cb) - 1u;
     const unsigned W = (unsigned)(threadIdx.x >> 5) << cb;
     if (((W ^ s.lcv) & s.lcm & ~inmask) != 0u) return;      // a control outside the part fails
@@ -402,7 +405,7 @@ __device__ void one_target(double *re, double *im, int mb, const SGate &s, const
         const unsigned lcv = s.lcv;
         if (s.unscaled) {
             // a scaled gate: d is in the sweep's scale, the rows are their sums
-            for (unsigned f = threadIdx.x; f < cnt; f += SWEEP_THREADS) {
+            for (unsigned f = threadIdx.x; f < cnt; f += blockDim.x) {
                 unsigned l = f << red;
                 for (int i = 0; i < nins; ++i) l = insert_zero(l, pos[i]);
                 const unsigned l0 = l | lcv;
@@ -418,7 +421,7 @@ __device__ void one_target(double *re, double *im, int mb, const SGate &s, const
             }
             return;
         }
-        for (unsigned f = threadIdx.x; f < cnt; f += SWEEP_THREADS) {
+        for (unsigned f = threadIdx.x; f < cnt; f += blockDim.x) {
             unsigned l = f << red;
             for (int i = 0; i < nins; ++i) l = insert_zero(l, pos[i]);
             const unsigned l0 = l | lcv;
@@ -434,7 +437,7 @@ __device__ void one_target(double *re, double *im, int mb, const SGate &s, const
         }
         return;
     }
-    for (unsigned f = threadIdx.x; f < cnt; f += SWEEP_THREADS) {
+    for (unsigned f = threadIdx.x; f < cnt; f += blockDim.x) {
         unsigned l0 = deposit(f << red, s) | s.lcv;
         unsigned l1 = l0 | bit;
         double xr[2] = {re[l0], re[l1]}, xi[2] = {im[l0], im[l1]};
@@ -448,7 +451,7 @@ __device__ void one_target(double *re, double *im, int mb, const SGate &s, const
 
 __device__ void two_target(double *re, double *im, int mb, const SGate &s, const DGate &dg, int red) {
     const unsigned cnt = 1u << (mb - s.nins - red);
-    for (unsigned f = threadIdx.x; f < cnt; f += SWEEP_THREADS) {
+    for (unsigned f = threadIdx.x; f < cnt; f += blockDim.x) {
         unsigned l = deposit(f << red, s) | s.lcv;
         unsigned idx[4];
         double xr[4], xi[4];
@@ -646,7 +649,7 @@ __device__ unsigned apply_run(double *re, double *im, int c, int h, int red, con
     __syncthreads();
     int j = 0;
     unsigned base = 0;
-    for (unsigned w = threadIdx.x;; w += SWEEP_THREADS) {
+    for (unsigned w = threadIdx.x;; w += blockDim.x) {
         while (j < ntl && w >= base + mem[j].count) { base += mem[j].count; ++j; }
         if (j >= ntl) break;
         const RunMember &m = mem[j];
@@ -712,7 +715,7 @@ __device__ unsigned apply_run(double *re, double *im, int c, int h, int red, con
 __device__ __noinline__ unsigned apply_gates(double *re, double *im, int mb, int red, const SGate *gsrc, SGate *sg,
                             int *chunk, const DGate *dg, int ngates, const unsigned *act,
                             unsigned long long fixed, const SweepParams &P, const int *hb, RunMember *mem) {
-    const bool warp_parts = red == 0 && mb - LOG_NWARPS >= 5;
+    const bool warp_parts = red == 0 && mb - log_nwarps() >= 5;
     unsigned run_ops = 0;
     bool dirty = false;                              // warp-local gates since the last CTA barrier
     for (int base = 0; base < ngates; base += GATE_CHUNK) {
@@ -730,7 +733,7 @@ __device__ __noinline__ unsigned apply_gates(double *re, double *im, int mb, int
             const uint32_t *src = reinterpret_cast<const uint32_t *>(gsrc + base);
             uint32_t *dst = reinterpret_cast<uint32_t *>(sg);
             const int words = cn * (int)(sizeof(SGate) / 4);
-            for (int i = threadIdx.x; i < words; i += SWEEP_THREADS) dst[i] = src[i];
+            for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
             if (threadIdx.x == 0) *chunk = base;
             __syncthreads();
         }
@@ -1807,13 +1810,12 @@ __device__ void wnorm(const double *re, const double *im, int N, unsigned long l
 // instance so that the encoding sweep carries no extra call site.
 // Items are handed out by an atomic counter (work, zero at launch), so a
 // CTA that runs faster than its neighbours takes more items.
-template <bool SIZING>
-__global__ void __launch_bounds__(SWEEP_THREADS, QS_SWEEP_MIN_BLOCKS) sweep_kernel(const SweepParams *__restrict__ plist,
+template <bool SIZING, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) sweep_kernel(const SweepParams *__restrict__ plist,
                                                           const unsigned long long *__restrict__ istart,
                                                           int nlist, unsigned long long *work) {
     extern __shared__ double smem[];
     __shared__ SGate sg[GATE_CHUNK];
-    __shared__ uint32_t stage[64 * NWARPS];
     __shared__ SweepParams P;
     __shared__ unsigned s_act[MAX_SWEEP_GATES / 32];
     __shared__ int s_entry, s_skip, s_chunk, s_any;
@@ -1826,9 +1828,10 @@ __global__ void __launch_bounds__(SWEEP_THREADS, QS_SWEEP_MIN_BLOCKS) sweep_kern
     const unsigned long long total = istart[nlist];
     if (threadIdx.x == 0) s_rundp = 0;
     unsigned run_ops = 0;                 // FP64 instructions of diagonal runs (this thread)
+    constexpr int NWARPS = NT / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *wst = stage + 64 * warp;
     int cur = -1;
+    uint32_t *wst = nullptr;              // the warp's packing stage, after the item buffer
     for (;;) {
         __syncthreads();                  // previous item finished by every warp
         if (threadIdx.x == 0) {           // next item; entry owning it: last e with istart[e] <= gi
@@ -1862,7 +1865,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, QS_SWEEP_MIN_BLOCKS) sweep_kern
             {
                 const uint32_t *src = reinterpret_cast<const uint32_t *>(plist + e);
                 uint32_t *dst = reinterpret_cast<uint32_t *>(&P);
-                for (int i = threadIdx.x; i < (int)(sizeof(SweepParams) / 4); i += SWEEP_THREADS) dst[i] = src[i];
+                for (int i = threadIdx.x; i < (int)(sizeof(SweepParams) / 4); i += NT) dst[i] = src[i];
             }
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -1879,6 +1882,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS, QS_SWEEP_MIN_BLOCKS) sweep_kern
         if (s_skip) continue;
         const int c = P.cc.c, N = 1 << c, h = P.h, mb = c + h, ntl = 1 << h;
         double *re = smem, *im = smem + (1 << mb);
+        wst = reinterpret_cast<uint32_t *>(smem + (2 << mb)) + 64 * warp;
         const double alpha = s_alpha;
         const bool scale = alpha != 1.0;
         int hb[MAX_PAIRS];
@@ -2397,24 +2401,38 @@ __global__ void pair_sum_kernel(const Acc4 *in, Acc4 *out, unsigned long long no
 // ---------------------------------------------------------------- launchers
 namespace qs {
 
-size_t sweep_smem_bytes(int mb) { return (size_t)16 << mb; }
+// dynamic shared memory of a sweep CTA: the item buffer (planar re / im)
+// and a 256-byte packing stage per warp
+size_t sweep_smem_bytes(int mb, int threads) { return ((size_t)16 << mb) + 256u * (size_t)(threads / 32); }
+
+// the sweep kernel's launch shapes: threads per CTA and the CTAs per SM its
+// register budget is compiled for (80 registers at 256 x 3)
+bool sweep_threads_ok(int threads) { return threads == 128 || threads == 256 || threads == 512; }
 static size_t tile_smem_bytes(int c, int bufs) { return (size_t)TILE_WARPS * bufs * (16u << c); }
 
-// work: the launch's item counter, zeroed on st before the launch.
-cudaError_t launch_sweep(const SweepParams *plist, const unsigned long long *istart, int nlist,
-                         int mb, int grid, unsigned long long *work, cudaStream_t st) {
+template <bool SIZING>
+static cudaError_t launch_sweep_shape(const SweepParams *plist, const unsigned long long *istart, int nlist,
+                                      int mb, int grid, int threads, unsigned long long *work, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    sweep_kernel<false><<<grid, SWEEP_THREADS, sweep_smem_bytes(mb), st>>>(plist, istart, nlist, work);
+    const size_t sm = sweep_smem_bytes(mb, threads);
+    switch (threads) {
+        case 128: sweep_kernel<SIZING, 128, 3><<<grid, 128, sm, st>>>(plist, istart, nlist, work); break;
+        case 512: sweep_kernel<SIZING, 512, 1><<<grid, 512, sm, st>>>(plist, istart, nlist, work); break;
+        default: sweep_kernel<SIZING, 256, 3><<<grid, 256, sm, st>>>(plist, istart, nlist, work); break;
+    }
     return cudaGetLastError();
 }
 
+// work: the launch's item counter, zeroed on st before the launch.
+cudaError_t launch_sweep(const SweepParams *plist, const unsigned long long *istart, int nlist,
+                         int mb, int grid, int threads, unsigned long long *work, cudaStream_t st) {
+    return launch_sweep_shape<false>(plist, istart, nlist, mb, grid, threads, work, st);
+}
+
 cudaError_t launch_sweep_sizing(const SweepParams *plist, const unsigned long long *istart, int nlist,
-                                int mb, int grid, unsigned long long *work, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
-    if (e != cudaSuccess) return e;
-    sweep_kernel<true><<<grid, SWEEP_THREADS, sweep_smem_bytes(mb), st>>>(plist, istart, nlist, work);
-    return cudaGetLastError();
+                                int mb, int grid, int threads, unsigned long long *work, cudaStream_t st) {
+    return launch_sweep_shape<true>(plist, istart, nlist, mb, grid, threads, work, st);
 }
 
 cudaError_t launch_finalize(DevScalars *scal, int use_alpha, unsigned long long *used_hist,
@@ -2557,9 +2575,15 @@ cudaError_t launch_pair_sum(const Acc4 *in, Acc4 *out, unsigned long long nout, 
 // current when they are set.
 static cudaError_t configure_current_device() {
     cudaError_t e;
-    const int maxsm = (int)sweep_smem_bytes(MAX_ITEM_LOG2);
-    if ((e = cudaFuncSetAttribute(sweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm))) return e;
-    if ((e = cudaFuncSetAttribute(sweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm))) return e;
+    const int sm128 = (int)sweep_smem_bytes(MAX_ITEM_LOG2, 128), sm256 = (int)sweep_smem_bytes(MAX_ITEM_LOG2, 256),
+              sm512 = (int)sweep_smem_bytes(MAX_ITEM_LOG2, 512);
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if ((e = cudaFuncSetAttribute(sweep_kernel<false, 128, 3>, A, sm128))) return e;
+    if ((e = cudaFuncSetAttribute(sweep_kernel<true, 128, 3>, A, sm128))) return e;
+    if ((e = cudaFuncSetAttribute(sweep_kernel<false, 256, 3>, A, sm256))) return e;
+    if ((e = cudaFuncSetAttribute(sweep_kernel<true, 256, 3>, A, sm256))) return e;
+    if ((e = cudaFuncSetAttribute(sweep_kernel<false, 512, 1>, A, sm512))) return e;
+    if ((e = cudaFuncSetAttribute(sweep_kernel<true, 512, 1>, A, sm512))) return e;
     const int t1 = (int)tile_smem_bytes(MAX_C, 1), t2 = (int)tile_smem_bytes(MAX_C, 2);
     if ((e = cudaFuncSetAttribute(init_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, t1))) return e;
     if ((e = cudaFuncSetAttribute(validate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, t1))) return e;
@@ -2606,9 +2630,12 @@ cudaError_t fp64_rate(int device, double *fma_per_s) {
     return e;
 }
 
-int sweep_blocks_per_sm(int mb) {
+int sweep_blocks_per_sm(int mb, int threads) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<false>, SWEEP_THREADS, sweep_smem_bytes(mb));
+    const size_t sm = sweep_smem_bytes(mb, threads);
+    if (threads == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<false, 128, 3>, 128, sm);
+    else if (threads == 512) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<false, 512, 1>, 512, sm);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<false, 256, 3>, 256, sm);
     return nb > 0 ? nb : 1;
 }
 

@@ -7,16 +7,7 @@
 namespace qs {
 
 constexpr int THREADS = 256;            // CTA size of the helper kernels
-#ifndef QS_SWEEP_THREADS
-#define QS_SWEEP_THREADS 256
-#endif
-#ifndef QS_SWEEP_MIN_BLOCKS
-#define QS_SWEEP_MIN_BLOCKS 3
-#endif
-constexpr int SWEEP_THREADS = QS_SWEEP_THREADS;      // CTA size of the sweep kernel
-constexpr int NWARPS = SWEEP_THREADS / 32;
-constexpr int LOG_NWARPS = NWARPS == 16 ? 4 : (NWARPS == 8 ? 3 : (NWARPS == 4 ? 2 : 1));
-static_assert((1 << LOG_NWARPS) == NWARPS, "sweep CTA: 2, 4, 8 or 16 warps");
+constexpr int SWEEP_THREADS = 256;      // default CTA size of the sweep kernel (128, 256 or 512)
 constexpr int MAX_C = 10;               // tile_log2 limit: G = 2^c/32 <= 32 groups
 constexpr int MAX_ITEM_LOG2 = 12;       // c + pair count: 4096 amplitudes on chip
 constexpr int MAX_PAIRS = 4;            // paired high qubits per sweep

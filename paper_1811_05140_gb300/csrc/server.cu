@@ -135,6 +135,7 @@ int admit(qsim_server *S, Req *q) {
                                r.depth ? r.depth : d.depth);
         if (st != QSIM_OK) return st;
     }
+    if (r.sweep_threads && (st = qsim_set_sweep_threads(q->h, r.sweep_threads)) != QSIM_OK) return st;
     if (r.basis && (st = qsim_reset_basis(q->h, r.basis)) != QSIM_OK) return st;
     // the circuit's own sweep partition: ticks cut only at sweep boundaries,
     // so every pass is the one the circuit would run alone

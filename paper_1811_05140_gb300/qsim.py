@@ -32,7 +32,7 @@ EXPORTS = ["qsim_create", "qsim_destroy", "qsim_set_stream", "qsim_set_aalc", "q
            "qsim_server_submit", "qsim_server_result", "qsim_server_wait", "qsim_server_drain",
            "qsim_server_stats", "qsim_server_destroy", "qsim_set_pool", "qsim_fp64_rate",
            "qsim_save", "qsim_load", "qsim_set_aalc_unit", "qsim_export_tile_set",
-           "qsim_set_fusion"]
+           "qsim_set_fusion", "qsim_set_sweep_threads"]
 
 
 class QsimError(RuntimeError):
@@ -75,7 +75,7 @@ class Request(C.Structure):
                 ("n_readout", C.c_int), ("rel_err_bound", C.c_double), ("theta", C.c_double),
                 ("basis", C.c_ulonglong), ("gates", C.POINTER(GateRec)), ("n_gates", C.c_int),
                 ("readout", C.c_int * 16), ("tile_log2", C.c_int), ("hmax", C.c_int),
-                ("depth", C.c_int)]
+                ("depth", C.c_int), ("sweep_threads", C.c_int)]
 
 
 class TicketInfo(C.Structure):
@@ -115,6 +115,7 @@ def load() -> C.CDLL:
         "qsim_set_aalc_unit": ([vp, C.c_int], C.c_int),
         "qsim_set_normalize": ([vp, C.c_int], C.c_int),
         "qsim_set_fusion": ([vp, C.c_int], C.c_int),
+        "qsim_set_sweep_threads": ([vp, C.c_int], C.c_int),
         "qsim_set_schedule": ([vp, C.c_int, C.c_int, C.c_int], C.c_int),
         "qsim_set_pool": ([vp, vp, C.c_size_t], C.c_int),
         "qsim_fp64_rate": ([C.c_int, C.POINTER(C.c_double)], C.c_int),
@@ -316,6 +317,10 @@ class State:
     def set_normalize(self, on: bool):
         self._check(self._L.qsim_set_normalize(self.h, int(bool(on))))
 
+    def set_sweep_threads(self, threads: int):
+        """CTA size of the sweep kernel (128, 256 or 512)."""
+        self._check(self._L.qsim_set_sweep_threads(self.h, int(threads)))
+
     def set_fusion(self, diag_runs: bool):
         """Runs of consecutive diagonal gates as one operator (default) or
         every gate on its own."""
@@ -505,7 +510,9 @@ class Server:
         for i, q in enumerate(readout):
             req.readout[i] = q
         if schedule:
-            req.tile_log2, req.hmax, req.depth = schedule
+            req.tile_log2, req.hmax, req.depth = schedule[:3]
+            if len(schedule) > 3:
+                req.sweep_threads = schedule[3]
         t = C.c_ulonglong()
         st = self._L.qsim_server_submit(self.h, C.byref(req), C.byref(t))
         if st != 0:

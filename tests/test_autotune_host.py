@@ -17,16 +17,17 @@ def test_tune_picks_the_fastest_valid_candidate(monkeypatch):
 
     def fake(n, gates, schedule, codec, eps, basis, reps):
         seen.append(schedule)
-        c, hmax, depth = schedule
-        return 1.0 + 0.01 * c + 0.001 * depth / 512 - 0.02 * hmax
+        c, hmax, depth, threads = autotune.full(schedule)
+        return 1.0 + 0.01 * c + 0.001 * depth / 512 - 0.02 * hmax + 0.0001 * abs(threads - 128)
 
     monkeypatch.setattr(autotune, "time_schedule", fake)
-    cands = [(8, 4, 512), (9, 4, 512), (7, 4, 48), (10, 2, 512), (12, 1, 512)]
+    cands = [(8, 4, 512), (9, 4, 512), (7, 4, 48), (10, 2, 512), (12, 1, 512), (7, 4, 48, 128),
+             (7, 4, 48, 512), (7, 4, 48, 300)]
     res = autotune.tune(20, [], candidates=cands)
-    assert (9, 4, 512) not in seen and (12, 1, 512) not in seen
-    assert res["best"] == (7, 4, 48)
+    assert (9, 4, 512) not in seen and (12, 1, 512) not in seen and (7, 4, 48, 300) not in seen
+    assert res["best"] == (7, 4, 48, 128)                  # the threads axis decides among equals
     secs = [row["seconds"] for row in res["table"]]
-    assert secs == sorted(secs) and len(secs) == 3
+    assert secs == sorted(secs) and len(secs) == 5
 
 
 def test_tuner_caches_per_key(monkeypatch):

@@ -21,11 +21,13 @@ def test_tuned_schedule_is_valid_and_exact():
     gates = I.qft(n)
     x = I.seeded_basis(n)
     res = autotune.tune(n, gates, "rel", 1e-4, x, reps=1)
-    c, hmax, depth = res["best"]
+    c, hmax, depth, threads = res["best"]
     assert autotune.valid(n, c, hmax) and len(res["table"]) >= 3
     assert all(r["seconds"] > 0 for r in res["table"])
+    assert {autotune.full(r["schedule"])[3] for r in res["table"]} == {128, 256, 512}
     st = qsim.State(n, 20, "rel", 1e-4)
     st.set_schedule(c, hmax, depth)
+    st.set_sweep_threads(threads)
     st.reset_basis(x)
     st.apply_all(gates)
     st.flush()
@@ -35,3 +37,19 @@ def test_tuned_schedule_is_valid_and_exact():
     assert all(s == cs.stream(t) for t, s in enumerate(st.export_tiles()))
     tuner = autotune.Tuner(reps=1)
     assert tuner.schedule(n, "qft", gates, "rel", 1e-4, x) == tuner.schedule(n, "qft", gates, "rel", 1e-4, x)
+
+
+@pytest.mark.parametrize("threads", [128, 512])
+def test_every_sweep_shape_matches_oracle(threads):
+    # the CTA size changes nothing in the result: QFT and a random grid
+    # under each launch shape, byte for byte against the oracle
+    for n, gates, x in ((12, I.qft(12), I.seeded_basis(12)), (12, I.random_grid(3, 4, 6, 77), 0)):
+        st = qsim.State(n, 8, "rel", 1e-4)
+        st.set_sweep_threads(threads)
+        st.reset_basis(x)
+        st.apply_all(gates)
+        st.flush()
+        cs = oracle.CSim(n, 8, [oracle.shift_for_eps(1e-4)], None, True)
+        cs.reset_basis(x)
+        cs.run(gates, 4, 512)
+        assert all(s == cs.stream(t) for t, s in enumerate(st.export_tiles()))
