@@ -85,6 +85,13 @@ def lib():
         L.or_csim_set_unit.argtypes = [C.c_void_p, C.c_int, C.c_uint64]
         L.or_csim_set_unit.restype = C.c_int
         L.or_csim_set_fuse.argtypes = [C.c_void_p, C.c_int]
+        L.or_csim_set_polar.argtypes = [C.c_void_p, C.c_int]
+        L.or_polar_table.argtypes = [u64p, C.c_int]
+        L.or_polar_angle.argtypes = [C.c_double, C.c_double]
+        L.or_polar_angle.restype = C.c_uint64
+        L.or_polar_recon.argtypes = [C.c_uint64, C.c_uint64, C.c_int, dp, dp]
+        L.or_encode_tile_opt.argtypes = [dp, C.c_int, ip, C.c_int, C.c_uint64, C.c_int, u8p, ip, ip]
+        L.or_encode_tile_opt.restype = C.c_size_t
         L.or_csim_set_dense.argtypes = [C.c_void_p, dp]
         L.or_csim_sweep.argtypes = [C.c_void_p, C.POINTER(OrGate), C.c_int, ip, C.c_int]
         L.or_csim_sweep.restype = C.c_int
@@ -209,8 +216,9 @@ def max_bytes_for(c: int, theta: float | None) -> int:
     return int(math.floor((16.0 * (1 << c)) / theta))
 
 
-def encode_tile(amps: np.ndarray, c: int, shifts, max_bytes: int | None = None):
-    """Encode 2^c amplitudes; returns (stream bytes, level, flags)."""
+def encode_tile(amps: np.ndarray, c: int, shifts, max_bytes: int | None = None, polar: bool = False):
+    """Encode 2^c amplitudes; returns (stream bytes, level, flags).  polar:
+    every lossy level also tries the POLAR mode and keeps the shorter."""
     a = np.ascontiguousarray(amps, dtype=np.complex128)
     assert a.size == 1 << c
     sh = (C.c_int * len(shifts))(*shifts)
@@ -218,9 +226,28 @@ def encode_tile(amps: np.ndarray, c: int, shifts, max_bytes: int | None = None):
     out = (C.c_uint8 * cap)()
     level, flags = C.c_int(), C.c_int()
     mb = (1 << 64) - 1 if max_bytes is None else max_bytes
-    n = lib().or_encode_tile(_dptr(a.view(np.float64)), c, sh, len(shifts), mb, out,
-                             C.byref(level), C.byref(flags))
+    n = lib().or_encode_tile_opt(_dptr(a.view(np.float64)), c, sh, len(shifts), mb, int(bool(polar)), out,
+                                 C.byref(level), C.byref(flags))
     return bytes(out[:n]), level.value, flags.value
+
+
+def polar_table(count: int = 30) -> list[int]:
+    """The POLAR mode's angle table: round(2^64 atan(2^-k) / (2 pi))."""
+    out = (C.c_uint64 * count)()
+    lib().or_polar_table(out, count)
+    return list(out)
+
+
+def polar_angle(x: float, y: float) -> int:
+    """Angle of (x, y) in units of 2^-64 turn (the POLAR mode's CORDIC)."""
+    return lib().or_polar_angle(x, y)
+
+
+def polar_recon(qm: int, qa: int, s: int) -> complex:
+    """The POLAR reconstruction of magnitude code qm and angle code qa at shift s."""
+    re, im = C.c_double(), C.c_double()
+    lib().or_polar_recon(qm, qa, s, C.byref(re), C.byref(im))
+    return complex(re.value, im.value)
 
 
 def check_bound(s: int, count: int, seed: int) -> int:
@@ -249,8 +276,12 @@ def decode_tile(stream: bytes, c: int) -> np.ndarray:
     return a
 
 
+def _opts(fuse: bool, polar: bool) -> int:
+    return int(bool(fuse)) | (int(bool(polar)) << 1)
+
+
 def item_sweep(n: int, c: int, H, base_tile: int, streams, alpha: float, gates, shifts,
-               max_bytes: int | None = None, fuse: bool = True):
+               max_bytes: int | None = None, fuse: bool = True, polar: bool = False):
     """One item of a sweep on its own (sampled checks of large states):
     member j is tile base_tile | bits of j at H; returns the new streams."""
     H = sorted(H)
@@ -267,7 +298,7 @@ def item_sweep(n: int, c: int, H, base_tile: int, streams, alpha: float, gates, 
     arr = gate_array(gates)
     mb = (1 << 64) - 1 if max_bytes is None else max_bytes
     rc = lib().or_item_sweep(n, c, hh, h, base_tile, ptrs, lens, alpha, arr, len(gates), sh,
-                             len(shifts), mb, int(bool(fuse)), out, cap, out_len)
+                             len(shifts), mb, _opts(fuse, polar), out, cap, out_len)
     if rc != 0:
         raise RuntimeError(f"oracle item sweep failed ({rc})")
     res, off = [], 0
@@ -279,7 +310,8 @@ def item_sweep(n: int, c: int, H, base_tile: int, streams, alpha: float, gates, 
 
 
 def item_sweep_batch(n: int, c: int, H, bases, raw: bytes, sizes, alpha: float, gates, shifts,
-                     max_bytes: int | None = None, threads: int | None = None, fuse: bool = True):
+                     max_bytes: int | None = None, threads: int | None = None, fuse: bool = True,
+                     polar: bool = False):
     """Many items of one sweep, each as item_sweep computes it, on `threads`
     host threads (default: every core).  raw holds the members' streams
     concatenated item by item (member order as in item_sweep), sizes their
@@ -311,7 +343,7 @@ def item_sweep_batch(n: int, c: int, H, bases, raw: bytes, sizes, alpha: float, 
     bad = lib().or_item_sweep_batch(
         n, c, hh, h, nitems, bs.ctypes.data_as(u64p), inb.ctypes.data_as(u8p), offs.ctypes.data_as(u64p),
         lens.ctypes.data_as(C.POINTER(C.c_uint32)), alpha, arr, len(gates), sh, len(shifts), mb,
-        int(bool(fuse)), out.ctypes.data_as(u8p), stride, out_len.ctypes.data_as(C.POINTER(C.c_uint32)),
+        _opts(fuse, polar), out.ctypes.data_as(u8p), stride, out_len.ctypes.data_as(C.POINTER(C.c_uint32)),
         rc.ctypes.data_as(C.POINTER(C.c_int)), threads)
     if bad:
         raise RuntimeError(f"oracle item sweep failed for {bad} item(s), codes {sorted(set(rc.tolist()))}")
@@ -342,7 +374,7 @@ def stride_items_tiles(c: int, H, stride_log2: int, t0: int) -> list[int]:
 
 
 def stride_sweep(n: int, c: int, H, stride_log2: int, theta: float, t0: int, streams: dict,
-                 alpha: float, gates, shifts, fuse: bool = True):
+                 alpha: float, gates, shifts, fuse: bool = True, polar: bool = False):
     """One stride of a sweep that decides per stride (sampled checks of large
     states): streams maps every tile of stride_items_tiles(...) to its input
     stream; returns the stride's new streams in tile order."""
@@ -361,7 +393,7 @@ def stride_sweep(n: int, c: int, H, stride_log2: int, theta: float, t0: int, str
     arr = gate_array(gates)
     rc = lib().or_stride_sweep(n, c, hh, len(H), ut, max_bytes_for(stride_log2, theta), t0, tarr, ptrs,
                                lens, len(tiles), alpha, arr, len(gates), sh, len(shifts),
-                               int(bool(fuse)), out, cap, out_len)
+                               _opts(fuse, polar), out, cap, out_len)
     if rc != 0:
         raise RuntimeError(f"oracle stride sweep failed ({rc})")
     res, off = [], 0
@@ -381,11 +413,13 @@ class CSim:
     normalize: apply 'normalize' before each sweep's gate computation;
     fuse: runs of two or more consecutive diagonal gates of a sweep are one
     diagonal operator (False: every gate on its own, so that lossless
-    sweeps reproduce the dense simulator bit for bit).
+    sweeps reproduce the dense simulator bit for bit); polar: every lossy
+    level also tries the POLAR mode (magnitude + phase) and keeps the
+    shorter stream.
     """
 
     def __init__(self, n: int, c: int, shifts, max_bytes: int | None = None,
-                 normalize: bool = True, fuse: bool = True):
+                 normalize: bool = True, fuse: bool = True, polar: bool = False):
         self.n, self.c = n, c
         self.shifts = list(shifts)
         sh = (C.c_int * len(self.shifts))(*self.shifts)
@@ -394,6 +428,7 @@ class CSim:
         if not self.h:
             raise ValueError("bad oracle state parameters")
         lib().or_csim_set_fuse(self.h, int(bool(fuse)))
+        lib().or_csim_set_polar(self.h, int(bool(polar)))
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -545,7 +545,7 @@ double or_units_to_double(uint64_t lo, uint64_t hi)
  * shorter than 16N; else RAW.
  */
 #define HDR 32
-enum { M_CONST = 0, M_PACKED = 1, M_RAW = 2 };
+enum { M_CONST = 0, M_PACKED = 1, M_RAW = 2, M_POLAR = 3 };
 /* modes of a section of per-group bit words (sign words, zero words) */
 enum { S_CLEAR = 0, S_SET = 1, S_EXC_CLEAR = 2, S_EXC_SET = 3, S_WORDS = 4 };
 #define MAG 0x7FFFFFFFFFFFFFFFull
@@ -659,6 +659,101 @@ size_t or_stream_cap(int c)
 }
 
 /*
+ * Write a tile stream from its per-component word sections, zigzag
+ * residuals and group widths (shared by the componentwise and the polar
+ * modes).  polar = 0: CONST when every residual is 0 and every section
+ * mode is 0 or 1, else PACKED when shorter than RAW, else RAW.  polar = 1:
+ * the POLAR mode with the PACKED body layout (its sign sections clear),
+ * d1 in header bytes 26..31; returns 0 when that body is not shorter than
+ * RAW.  Returns the stream length.
+ */
+static size_t write_stream(const double *a, int c, int s, int level, const uint64_t *anchor, int allzero,
+                           uint32_t **sw, uint32_t **zw, uint64_t **z, int **w, int **nnz,
+                           const int *smode, const int *zmode, int polar, uint64_t d1, uint8_t *out)
+{
+    uint64_t N = 1ull << c;
+    int G = N >= 32 ? (int)(N / 32) : 1;
+    int L = N >= 32 ? 32 : (int)N;
+    uint32_t lanes = L == 32 ? 0xFFFFFFFFu : ((1u << L) - 1);
+    size_t raw_body = 16 * N;
+    int mode;
+    size_t body;
+    size_t data_words = 0;
+    for (int k = 0; k < 2; ++k)
+        for (int g = 0; g < G; ++g)
+            data_words += ((size_t)nnz[k][g] * w[k][g] + 31) / 32;
+    size_t meta = 0;
+    for (int k = 0; k < 2; ++k)
+        meta += section_bytes(smode[k], sw[k], G, lanes) + section_bytes(zmode[k], zw[k], G, lanes);
+    size_t wbytes = round_up(meta + 2 * (size_t)G, 4) - meta;
+    size_t packed_body = round_up(meta + wbytes + 4 * data_words, 16);
+
+    if (polar) {
+        if (packed_body >= raw_body) return 0;
+        mode = M_POLAR;
+        body = packed_body;
+    } else if (allzero && smode[0] <= S_SET && smode[1] <= S_SET && zmode[0] <= S_SET && zmode[1] <= S_SET) {
+        mode = M_CONST;
+        body = 0;
+    } else if (packed_body < raw_body) {
+        mode = M_PACKED;
+        body = packed_body;
+    } else {
+        mode = M_RAW;
+        body = raw_body;
+    }
+
+    memset(out, 0, HDR + body);
+    out[0] = (uint8_t)mode;
+    out[1] = (uint8_t)(mode == M_RAW ? 0 : s);
+    out[2] = (uint8_t)level;
+    if (mode != M_RAW) out[3] = (uint8_t)(smode[0] | (smode[1] << 3));
+    if (mode == M_PACKED || mode == M_POLAR) out[25] = (uint8_t)(zmode[0] | (zmode[1] << 3));
+    put32(out + 4, (uint32_t)body);
+    if (mode != M_RAW) {
+        put64(out + 8, anchor[0]);
+        put64(out + 16, anchor[1]);
+    }
+    out[24] = (uint8_t)c;
+    if (mode == M_POLAR)
+        for (int i = 0; i < 6; ++i) out[26 + i] = (uint8_t)(d1 >> (8 * i));
+
+    uint8_t *b = out + HDR;
+    if (mode == M_RAW) {
+        for (uint64_t i = 0; i < 2 * N; ++i) put64(b + 8 * i, dbits(a[i]));
+    } else if (mode == M_PACKED || mode == M_POLAR) {
+        size_t off = 0;
+        for (int k = 0; k < 2; ++k) off = write_section(b, off, smode[k], sw[k], G, lanes);
+        for (int k = 0; k < 2; ++k) off = write_section(b, off, zmode[k], zw[k], G, lanes);
+        for (int k = 0; k < 2; ++k)
+            for (int g = 0; g < G; ++g) b[off++] = (uint8_t)w[k][g];
+        off = round_up(off, 4);
+        /* lane-major bit packing of the nonzero values: the k-th nonzero
+         * value of a group occupies bits [k*w, (k+1)*w) of the group's
+         * little-endian bit string */
+        for (int k = 0; k < 2; ++k)
+            for (int g = 0; g < G; ++g) {
+                int wg = w[k][g];
+                size_t nwords = ((size_t)nnz[k][g] * wg + 31) / 32;
+                size_t rank = 0;
+                for (int l = 0; l < L; ++l) {
+                    uint64_t i = (uint64_t)g * 32 + l;
+                    if ((zw[k][g] >> l) & 1) continue;
+                    uint64_t v = z[k][i];
+                    for (int bit = 0; bit < wg; ++bit)
+                        if ((v >> bit) & 1) {
+                            size_t pos = rank * wg + bit;
+                            b[off + pos / 8] |= (uint8_t)(1u << (pos % 8));
+                        }
+                    ++rank;
+                }
+                off += 4 * nwords;
+            }
+    }
+    return HDR + body;
+}
+
+/*
  * Encode one tile of 2^c amplitudes (re, im interleaved) at quantisation
  * shift s, as ladder level 'level'.  Writes the stream to out and returns
  * its length in bytes.
@@ -714,79 +809,257 @@ static size_t encode_at(const double *a, int c, int s, int level, uint8_t *out)
         zmode[k] = word_mode(zw[k], G, lanes);
     }
 
-    size_t raw_body = 16 * N;
-    int mode;
-    size_t body;
-    size_t data_words = 0;
-    for (int k = 0; k < 2; ++k)
-        for (int g = 0; g < G; ++g)
-            data_words += ((size_t)nnz[k][g] * w[k][g] + 31) / 32;
-    size_t meta = 0;
-    for (int k = 0; k < 2; ++k)
-        meta += section_bytes(smode[k], sw[k], G, lanes) + section_bytes(zmode[k], zw[k], G, lanes);
-    size_t wbytes = round_up(meta + 2 * (size_t)G, 4) - meta;
-    size_t packed_body = round_up(meta + wbytes + 4 * data_words, 16);
-
-    if (allzero && smode[0] <= S_SET && smode[1] <= S_SET && zmode[0] <= S_SET && zmode[1] <= S_SET) {
-        mode = M_CONST;
-        body = 0;
-    } else if (packed_body < raw_body) {
-        mode = M_PACKED;
-        body = packed_body;
-    } else {
-        mode = M_RAW;
-        body = raw_body;
-    }
-
-    memset(out, 0, HDR + body);
-    out[0] = (uint8_t)mode;
-    out[1] = (uint8_t)(mode == M_RAW ? 0 : s);
-    out[2] = (uint8_t)level;
-    if (mode != M_RAW) out[3] = (uint8_t)(smode[0] | (smode[1] << 3));
-    if (mode == M_PACKED) out[25] = (uint8_t)(zmode[0] | (zmode[1] << 3));
-    put32(out + 4, (uint32_t)body);
-    if (mode != M_RAW) {
-        put64(out + 8, anchor[0]);
-        put64(out + 16, anchor[1]);
-    }
-    out[24] = (uint8_t)c;
-
-    uint8_t *b = out + HDR;
-    if (mode == M_RAW) {
-        for (uint64_t i = 0; i < 2 * N; ++i) put64(b + 8 * i, dbits(a[i]));
-    } else if (mode == M_PACKED) {
-        size_t off = 0;
-        for (int k = 0; k < 2; ++k) off = write_section(b, off, smode[k], sw[k], G, lanes);
-        for (int k = 0; k < 2; ++k) off = write_section(b, off, zmode[k], zw[k], G, lanes);
-        for (int k = 0; k < 2; ++k)
-            for (int g = 0; g < G; ++g) b[off++] = (uint8_t)w[k][g];
-        off = round_up(off, 4);
-        /* lane-major bit packing of the nonzero values: the k-th nonzero
-         * value of a group occupies bits [k*w, (k+1)*w) of the group's
-         * little-endian bit string */
-        for (int k = 0; k < 2; ++k)
-            for (int g = 0; g < G; ++g) {
-                int wg = w[k][g];
-                size_t nwords = ((size_t)nnz[k][g] * wg + 31) / 32;
-                size_t rank = 0;
-                for (int l = 0; l < L; ++l) {
-                    uint64_t i = (uint64_t)g * 32 + l;
-                    if (!q[k][i]) continue;
-                    uint64_t v = z[k][i];
-                    for (int bit = 0; bit < wg; ++bit)
-                        if ((v >> bit) & 1) {
-                            size_t pos = rank * wg + bit;
-                            b[off + pos / 8] |= (uint8_t)(1u << (pos % 8));
-                        }
-                    ++rank;
-                }
-                off += 4 * nwords;
-            }
-    }
+    size_t len = write_stream(a, c, s, level, anchor, allzero, sw, zw, z, w, nnz, smode, zmode, 0, 0, out);
     for (int k = 0; k < 2; ++k) {
         free(q[k]); free(z[k]); free(sw[k]); free(zw[k]); free(w[k]); free(nnz[k]);
     }
-    return HDR + body;
+    return len;
+}
+
+/* ------------------------------------------------------------------ */
+/* O2': polar tile mode (log-magnitude + phase)                        */
+/* ------------------------------------------------------------------ */
+
+/*
+ * POLAR mode (a codec variant: amplitude-aware coding of magnitude and
+ * phase instead of the two components).  At a lossy level of shift s
+ * (8 <= s <= 52) every nonzero amplitude a = x + iy is coded as
+ *   magnitude: m = sqrt(fma(x, x, y*y)) (IEEE, correctly rounded), code
+ *     qm = quant(bits(m), s - 2), reconstructed m^ = bits(qm << (s - 2));
+ *   phase: the angle of (x, y) in units of 2^-64 turn from the integer
+ *     CORDIC below, code qa = round(angle / 2^P) mod 2^B with P = s + 8,
+ *     B = 64 - P bits, reconstructed direction (X, Y) = CORDIC rotation of
+ *     (2^59, 0) by qa << P;
+ *   a^ = (m^ (Xd / l), m^ (Yd / l)) with Xd, Yd the doubles nearest X, Y
+ *     and l = sqrt(fma(Xd, Xd, Yd*Yd)).
+ * The mode is used only when every amplitude then satisfies
+ * |a^ - a|^2 <= 2^(2(s-53)) (1 - 2^-10) |a|^2 (checked in IEEE arithmetic;
+ * the margin covers the check's own rounding), i.e. the level's bound on
+ * the complex amplitude (the componentwise mode bounds each component,
+ * which implies it), and every component is 0 or has 2^-400 <= |x| < 16.
+ * Codes run along the nonzero amplitudes: magnitudes by order-1 Lorenzo
+ * from their anchor (header 8..15); phases by order-2 Lorenzo modulo 2^B
+ * from u0 (header 16..23) and the first difference d1 (header 26..31):
+ * residual r_j = u_j - 2 u_(j-1) + u_(j-2) for j >= 2 (0 for j < 2), as a
+ * signed B-bit value, zigzagged.  A QFT's tiles (equal magnitudes, phases
+ * linear in the index) code to residuals 0 or +-1.  Body: the PACKED
+ * layout with clear sign sections and the zero words of both components
+ * equal (a zero amplitude).
+ */
+#define POLAR_ITERS 30
+#define POLAR_MIN_EXP 623                /* |x| >= 2^-400: biased exponent >= 1023 - 400 */
+#define POLAR_MAX_EXP 1027               /* |x| < 16 */
+
+static uint64_t polar_atan_turns[POLAR_ITERS];
+static pthread_once_t polar_once = PTHREAD_ONCE_INIT;
+
+/* arctan(1/n) in fixed point with 124 fractional bits, by its alternating
+ * series sum (-1)^j / ((2j+1) n^(2j+1)); every term truncated (the error
+ * stays below 2^-117, far under the 2^-64 of the table) */
+static u128 atan_inv_fix(uint64_t n)
+{
+    u128 p = ((u128)1 << 124) / n, sum = 0;
+    int neg = 0;
+    for (uint64_t j = 0; p; ++j) {
+        u128 t = p / (2 * j + 1);
+        if (neg) sum -= t; else sum += t;
+        neg = !neg;
+        p /= (u128)n * n;
+    }
+    return sum;
+}
+
+/* Table of atan(2^-k) / (2 pi) in units of 2^-64 turn, rounded to nearest:
+ * atan(1) = atan(1/2) + atan(1/3) (Euler), 2 pi = 8 atan(1). */
+static void polar_init(void)
+{
+    u128 one = atan_inv_fix(2) + atan_inv_fix(3);           /* pi/4 */
+    u128 twopi = one * 8;
+    for (int k = 0; k < POLAR_ITERS; ++k) {
+        u128 v = k == 0 ? one : atan_inv_fix(1ull << k);
+        /* round(v * 2^64 / twopi) by binary long division (v < twopi) */
+        u128 rem = v;
+        uint64_t q = 0;
+        for (int i = 0; i < 64; ++i) {
+            rem <<= 1;
+            q <<= 1;
+            if (rem >= twopi) { rem -= twopi; q |= 1; }
+        }
+        if (rem >= twopi - rem) ++q;
+        polar_atan_turns[k] = q;
+    }
+}
+
+void or_polar_table(uint64_t *out, int n)
+{
+    pthread_once(&polar_once, polar_init);
+    for (int k = 0; k < n && k < POLAR_ITERS; ++k) out[k] = polar_atan_turns[k];
+}
+
+/* signed fixed-point value of x with the exponent of the larger component
+ * (biased exponent emax) mapped to 2^59: mantissa << (7 + e - emax),
+ * truncated toward zero when the shift is negative */
+static int64_t polar_fix(double x, int emax)
+{
+    uint64_t u = dbits(x);
+    uint64_t e = (u >> 52) & 0x7FF, f = u & 0xFFFFFFFFFFFFFull;
+    if (e == 0 && f == 0) return 0;
+    uint64_t m = f | (1ull << 52);
+    int sh = 7 + (int)e - emax;
+    uint64_t v = sh >= 0 ? m << sh : (sh > -64 ? m >> (-sh) : 0);
+    return (u >> 63) ? -(int64_t)v : (int64_t)v;
+}
+
+/* angle of (x, y) in units of 2^-64 turn: CORDIC vectoring on the fixed
+ * point values (right half-plane first), POLAR_ITERS steps */
+uint64_t or_polar_angle(double x, double y)
+{
+    pthread_once(&polar_once, polar_init);
+    int ex = (int)((dbits(x) >> 52) & 0x7FF), ey = (int)((dbits(y) >> 52) & 0x7FF);
+    int emax = ex > ey ? ex : ey;
+    int64_t X = polar_fix(x, emax), Y = polar_fix(y, emax);
+    uint64_t th = 0;
+    if (X < 0) { X = -X; Y = -Y; th = 1ull << 63; }
+    for (int k = 0; k < POLAR_ITERS; ++k) {
+        int64_t dx = Y >> k, dy = X >> k;
+        if (Y >= 0) { X += dx; Y -= dy; th += polar_atan_turns[k]; }
+        else { X -= dx; Y += dy; th -= polar_atan_turns[k]; }
+    }
+    return th;
+}
+
+/* direction of angle th (units of 2^-64 turn): CORDIC rotation of
+ * (2^59, 0), a half turn first when th is in the left half-plane */
+static void polar_dir(uint64_t th, int64_t *px, int64_t *py)
+{
+    int64_t X = (int64_t)1 << 59, Y = 0;
+    uint64_t z = th;
+    if (((th >> 62) + 1) & 2) { X = -X; z = th - (1ull << 63); }    /* th in [1/4, 3/4) turn */
+    int64_t zz = (int64_t)z;
+    for (int k = 0; k < POLAR_ITERS; ++k) {
+        int64_t dx = Y >> k, dy = X >> k;
+        if (zz >= 0) { X -= dx; Y += dy; zz -= (int64_t)polar_atan_turns[k]; }
+        else { X += dx; Y -= dy; zz += (int64_t)polar_atan_turns[k]; }
+    }
+    *px = X;
+    *py = Y;
+}
+
+/* the reconstruction of (qm, qa) at shift s */
+static void polar_recon(uint64_t qm, uint64_t qa, int s, double *re, double *im)
+{
+    int P = s + 8;
+    double m = bitsd(qm << (s - 2));
+    int64_t X, Y;
+    polar_dir(qa << P, &X, &Y);
+    double xd = (double)X, yd = (double)Y;
+    double l = sqrt(fma(xd, xd, yd * yd));
+    *re = m * (xd / l);
+    *im = m * (yd / l);
+}
+
+void or_polar_recon(uint64_t qm, uint64_t qa, int s, double *re, double *im)
+{
+    pthread_once(&polar_once, polar_init);
+    polar_recon(qm, qa, s, re, im);
+}
+
+static int polar_comp_ok(double x)
+{
+    uint64_t e = (dbits(x) >> 52) & 0x7FF;
+    return (dbits(x) & MAG) == 0 || (e >= POLAR_MIN_EXP && e < POLAR_MAX_EXP);
+}
+
+/* POLAR stream of a tile at shift s as ladder level `level`, or 0 when the
+ * tile cannot use the mode (a value out of range or over the bound, or a
+ * body not shorter than RAW). */
+static size_t encode_polar_at(const double *a, int c, int s, int level, uint8_t *out)
+{
+    if (s < 8 || s > 52) return 0;
+    pthread_once(&polar_once, polar_init);
+    uint64_t N = 1ull << c;
+    int G = N >= 32 ? (int)(N / 32) : 1;
+    int L = N >= 32 ? 32 : (int)N;
+    uint32_t lanes = L == 32 ? 0xFFFFFFFFu : ((1u << L) - 1);
+    int P = s + 8, B = 64 - P;
+    uint64_t bmask = (1ull << B) - 1, half = 1ull << (B - 1);
+    double lim = ldexp(1.0 - ldexp(1.0, -10), 2 * (s - 53));
+    uint64_t *qm = calloc(N, 8), *qa = calloc(N, 8);
+    uint64_t *z[2] = {calloc(N, 8), calloc(N, 8)};
+    uint32_t *sw[2] = {calloc((size_t)G, 4), calloc((size_t)G, 4)};
+    uint32_t *zw[2] = {calloc((size_t)G, 4), calloc((size_t)G, 4)};
+    int *w[2] = {calloc((size_t)G, sizeof(int)), calloc((size_t)G, sizeof(int))};
+    int *nnz[2] = {calloc((size_t)G, sizeof(int)), calloc((size_t)G, sizeof(int))};
+    int ok = 1;
+    for (uint64_t i = 0; i < N && ok; ++i) {
+        double x = a[2 * i], y = a[2 * i + 1];
+        if (!polar_comp_ok(x) || !polar_comp_ok(y)) { ok = 0; break; }
+        if ((dbits(x) & MAG) == 0 && (dbits(y) & MAG) == 0) {
+            zw[0][i / 32] |= 1u << (i % 32);
+            zw[1][i / 32] |= 1u << (i % 32);
+            continue;
+        }
+        double m = sqrt(fma(x, x, y * y));
+        qm[i] = quant(dbits(m), s - 2);
+        uint64_t th = or_polar_angle(x, y);
+        qa[i] = ((th + (1ull << (P - 1))) >> P) & bmask;
+        double xr, xi;
+        polar_recon(qm[i], qa[i], s, &xr, &xi);
+        double dr = xr - x, di = xi - y;
+        if (!(fma(dr, dr, di * di) <= lim * fma(x, x, y * y))) ok = 0;
+    }
+    size_t len = 0;
+    if (ok) {
+        uint64_t anchor[2] = {0, 0}, d1 = 0;
+        int j = 0;
+        uint64_t prevm = 0, u1 = 0, u2 = 0;            /* previous two angle codes */
+        for (uint64_t i = 0; i < N; ++i) {
+            if ((zw[0][i / 32] >> (i % 32)) & 1) continue;
+            if (j == 0) { anchor[0] = qm[i]; anchor[1] = qa[i]; prevm = qm[i]; }
+            uint64_t rm = qm[i] - prevm;
+            prevm = qm[i];
+            z[0][i] = (rm << 1) ^ (uint64_t)((int64_t)rm >> 63);
+            uint64_t ra = 0;
+            if (j == 1) d1 = (qa[i] - u1) & bmask;
+            if (j >= 2) ra = (qa[i] - 2 * u1 + u2) & bmask;
+            int64_t rs = (int64_t)((ra ^ half) - half);     /* signed B-bit residual */
+            z[1][i] = ((uint64_t)rs << 1) ^ (uint64_t)(rs >> 63);
+            u2 = u1;
+            u1 = qa[i];
+            ++j;
+        }
+        int smode[2] = {S_CLEAR, S_CLEAR}, zmode[2];
+        for (int k = 0; k < 2; ++k) {
+            for (int g = 0; g < G; ++g) {
+                uint64_t o = 0;
+                for (int l = 0; l < L; ++l) o |= z[k][(uint64_t)g * 32 + l];
+                w[k][g] = bitlen64(o);
+                nnz[k][g] = popcount32(~zw[k][g] & lanes);
+            }
+            zmode[k] = word_mode(zw[k], G, lanes);
+        }
+        len = write_stream(a, c, s, level, anchor, 0, sw, zw, z, w, nnz, smode, zmode, 1, d1, out);
+    }
+    free(qm); free(qa);
+    for (int k = 0; k < 2; ++k) { free(z[k]); free(sw[k]); free(zw[k]); free(w[k]); free(nnz[k]); }
+    return len;
+}
+
+/* A lossy level with the polar variant on: the POLAR stream when the tile
+ * can use it and it is shorter than the componentwise stream, else the
+ * componentwise stream (encode_at). */
+static size_t encode_level(const double *a, int c, int s, int level, int polar, uint8_t *out)
+{
+    size_t len = encode_at(a, c, s, level, out);
+    if (!polar || s < 8) return len;
+    uint8_t *tmp = malloc(or_stream_cap(c));
+    size_t lp = encode_polar_at(a, c, s, level, tmp);
+    if (lp && lp < len) {
+        memcpy(out, tmp, lp);
+        len = lp;
+    }
+    free(tmp);
+    return len;
 }
 
 /*
@@ -854,8 +1127,19 @@ static size_t encode_nonfinite(const double *a, int c, uint8_t *out)
  * is coded with shift 0 at every level; a non-finite value forces RAW and
  * sets OR_F_NONFINITE.  out must hold or_stream_cap(c) bytes.
  */
+size_t or_encode_tile_opt(const double *a, int c, const int *shifts, int nlev, uint64_t max_bytes,
+                          int polar, uint8_t *out, int *level, int *flags);
+
 size_t or_encode_tile(const double *a, int c, const int *shifts, int nlev,
                       uint64_t max_bytes, uint8_t *out, int *level, int *flags)
+{
+    return or_encode_tile_opt(a, c, shifts, nlev, max_bytes, 0, out, level, flags);
+}
+
+/* or_encode_tile with the polar variant on every lossy level (polar = 1):
+ * each level keeps the shorter of its POLAR and componentwise streams. */
+size_t or_encode_tile_opt(const double *a, int c, const int *shifts, int nlev, uint64_t max_bytes,
+                          int polar, uint8_t *out, int *level, int *flags)
 {
     int nonfinite, eligible;
     scan_tile(a, c, &nonfinite, &eligible);
@@ -869,7 +1153,7 @@ size_t or_encode_tile(const double *a, int c, const int *shifts, int nlev,
     size_t len = 0;
     for (int k = 0; k < nlev; ++k) {
         int s = eligible ? shifts[k] : 0;
-        len = encode_at(a, c, s, k, out);
+        len = encode_level(a, c, s, k, polar, out);
         *level = k;
         if ((uint64_t)len <= max_bytes) break;
     }
@@ -882,8 +1166,17 @@ size_t or_encode_tile(const double *a, int c, const int *shifts, int nlev,
  * level is known.  Same forced-lossless and non-finite rules as
  * or_encode_tile.
  */
+size_t or_encode_tile_level_opt(const double *a, int c, const int *shifts, int k, int polar,
+                                uint8_t *out, int *flags);
+
 size_t or_encode_tile_level(const double *a, int c, const int *shifts, int k,
                             uint8_t *out, int *flags)
+{
+    return or_encode_tile_level_opt(a, c, shifts, k, 0, out, flags);
+}
+
+size_t or_encode_tile_level_opt(const double *a, int c, const int *shifts, int k, int polar,
+                                uint8_t *out, int *flags)
 {
     int nonfinite, eligible;
     scan_tile(a, c, &nonfinite, &eligible);
@@ -893,7 +1186,7 @@ size_t or_encode_tile_level(const double *a, int c, const int *shifts, int k,
         return encode_nonfinite(a, c, out);
     }
     if (!eligible) *flags |= OR_F_FORCED_LOSSLESS;
-    return encode_at(a, c, eligible ? shifts[k] : 0, k, out);
+    return encode_level(a, c, eligible ? shifts[k] : 0, k, polar, out);
 }
 
 /*
@@ -929,7 +1222,8 @@ int or_decode_tile(const uint8_t *in, size_t len, int c, double *a)
         }
         return 0;
     }
-    if (mode != M_PACKED) return -7;
+    if (mode != M_PACKED && mode != M_POLAR) return -7;
+    if (mode == M_POLAR && (s < 8 || sm[0] != S_CLEAR || sm[1] != S_CLEAR)) return -7;
     size_t off = 0;
     uint32_t *sw[2], *zw[2];
     for (int k = 0; k < 2; ++k) { sw[k] = calloc((size_t)G, 4); zw[k] = calloc((size_t)G, 4); }
@@ -973,6 +1267,13 @@ int or_decode_tile(const uint8_t *in, size_t len, int c, double *a)
         }
         off = round_up(off + 2 * (size_t)G, 4);
     }
+    if (rc == 0 && mode == M_POLAR) {
+        for (int g = 0; g < G; ++g)
+            if (zw[0][g] != zw[1][g]) rc = -12;     /* a zero amplitude is zero in both codes */
+    }
+    /* POLAR: the residuals of the two code streams, kept for the
+     * reconstruction below */
+    uint64_t *pz = mode == M_POLAR ? calloc(2 * N, 8) : NULL;
     for (int k = 0; k < 2 && rc == 0; ++k) {
         uint64_t q = anchor[k];
         for (int g = 0; g < G && rc == 0; ++g) {
@@ -994,12 +1295,34 @@ int or_decode_tile(const uint8_t *in, size_t len, int c, double *a)
                     v |= (uint64_t)((b[off + pos / 8] >> (pos % 8)) & 1) << bit;
                 }
                 ++rank;
+                if (pz) { pz[2 * i + k] = v; continue; }
                 q += (v >> 1) ^ (0 - (v & 1));       /* un-zigzag, running sum */
                 a[2 * i + k] = bitsd((q << s) | (sg << 63));
             }
             off += 4 * nwords;
         }
     }
+    if (pz && rc == 0) {
+        /* magnitudes: running sum from the anchor; phases: second-order
+         * running sums modulo 2^B from u0 and d1 */
+        pthread_once(&polar_once, polar_init);
+        int B = 56 - s;
+        uint64_t bmask = (1ull << B) - 1, d1 = 0;
+        for (int i = 0; i < 6; ++i) d1 |= (uint64_t)in[26 + i] << (8 * i);
+        uint64_t qm = anchor[0], u = anchor[1] & bmask, d = d1 & bmask;
+        uint64_t j = 0;
+        for (uint64_t i = 0; i < N; ++i) {
+            if ((zw[0][i / 32] >> (i % 32)) & 1) { a[2 * i] = 0.0; a[2 * i + 1] = 0.0; continue; }
+            uint64_t vm = pz[2 * i], va = pz[2 * i + 1];
+            qm += (vm >> 1) ^ (0 - (vm & 1));
+            uint64_t ra = ((va >> 1) ^ (0 - (va & 1))) & bmask;
+            if (j == 1) u = (u + d) & bmask;
+            else if (j >= 2) { d = (d + ra) & bmask; u = (u + d) & bmask; }
+            ++j;
+            polar_recon(qm, u, s, &a[2 * i], &a[2 * i + 1]);
+        }
+    }
+    free(pz);
     for (int k = 0; k < 2; ++k) { free(sw[k]); free(zw[k]); free(w[k]); }
     return rc;
 }
@@ -1022,6 +1345,7 @@ typedef struct {
     uint64_t hist[8];    /* ladder level of every tile written */
     uint64_t items_done, items_skipped;
     int fuse;            /* diagonal runs as one operator (apply_gates_buf) */
+    int polar;           /* lossy levels also try the POLAR mode */
 } or_csim;
 
 /* Keep buf (len bytes, malloc'ed) as tile t's stream: count its ladder
@@ -1045,8 +1369,8 @@ static void csim_store(or_csim *cs, uint64_t t, const double *amps)
 {
     int c = cs->c, level = 0, flags = 0;
     uint8_t *buf = malloc(or_stream_cap(c));
-    size_t len = or_encode_tile(amps, c, cs->shifts, cs->nlev, cs->max_bytes,
-                                buf, &level, &flags);
+    size_t len = or_encode_tile_opt(amps, c, cs->shifts, cs->nlev, cs->max_bytes, cs->polar,
+                                    buf, &level, &flags);
     if (flags & OR_F_NONFINITE) cs->err |= 1;
     csim_put(cs, t, buf, len);
 }
@@ -1064,7 +1388,7 @@ static void csim_store(or_csim *cs, uint64_t t, const double *amps)
  * each) and len[j] receive tile j's stream.  Returns 1 when a value is not
  * finite. */
 static int encode_stride(const double *amps, uint64_t nt, int c, const int *shifts, int nlev,
-                         uint64_t umax, uint8_t **buf, size_t *len)
+                         uint64_t umax, int polar, uint8_t **buf, size_t *len)
 {
     uint64_t N = 1ull << c;
     int nonfinite = 0;
@@ -1073,7 +1397,7 @@ static int encode_stride(const double *amps, uint64_t nt, int c, const int *shif
         nonfinite = 0;
         for (uint64_t j = 0; j < nt; ++j) {
             int flags = 0;
-            len[j] = or_encode_tile_level(amps + 2 * j * N, c, shifts, k, buf[j], &flags);
+            len[j] = or_encode_tile_level_opt(amps + 2 * j * N, c, shifts, k, polar, buf[j], &flags);
             if (flags & OR_F_NONFINITE) nonfinite = 1;
             total += len[j];
         }
@@ -1089,7 +1413,7 @@ static void csim_store_unit(or_csim *cs, uint64_t t0, const double *amps)
     uint8_t **buf = malloc(nt * sizeof *buf);
     size_t *len = malloc(nt * sizeof *len);
     for (uint64_t j = 0; j < nt; ++j) buf[j] = malloc(or_stream_cap(c));
-    if (encode_stride(amps, nt, c, cs->shifts, cs->nlev, cs->umax, buf, len)) cs->err |= 1;
+    if (encode_stride(amps, nt, c, cs->shifts, cs->nlev, cs->umax, cs->polar, buf, len)) cs->err |= 1;
     for (uint64_t j = 0; j < nt; ++j) csim_put(cs, t0 + j, buf[j], len[j]);
     free(buf);
     free(len);
@@ -1155,6 +1479,10 @@ int or_csim_set_unit(or_csim *cs, int unit_log2, uint64_t umax)
 /* Diagonal runs on (1, the default) or gate by gate (0); the latter makes
  * lossless sweeps reproduce the dense simulator O1 bit for bit. */
 void or_csim_set_fuse(or_csim *cs, int on) { cs->fuse = on ? 1 : 0; }
+
+/* Lossy levels also try the POLAR mode (1) or only the componentwise one
+ * (0, the default). */
+void or_csim_set_polar(or_csim *cs, int on) { cs->polar = on ? 1 : 0; }
 
 /* state |x>: every tile (or stride) encoded from its dense values */
 void or_csim_reset_basis(or_csim *cs, uint64_t x)
@@ -1431,13 +1759,15 @@ static int csim_sweep_items(or_csim *cs, const or_gate *g, int ng, const int *H,
  * this item (kept as it is when alpha is 1 and no gate touches it; streams
  * moved between members when the sweep only moves tiles) and writes the
  * members' new streams, concatenated, to out (out_len[j] each).
+ * opts: bit 0 the fusion rules (diagonal runs, scaled gates; CSim fuse),
+ * bit 1 the POLAR variant on lossy levels (CSim polar).
  * Returns 0, -1 on a malformed stream, -2 on a gate outside the item, -3
  * when out is too small.
  */
 int or_item_sweep(int n, int c, const int *H, int h, uint64_t base_tile,
                   const uint8_t *const *in, const uint32_t *in_len, double alpha,
                   const or_gate *g, int ng, const int *shifts, int nlev, uint64_t max_bytes,
-                  int fuse, uint8_t *out, size_t out_cap, uint32_t *out_len)
+                  int opts, uint8_t *out, size_t out_cap, uint32_t *out_len)
 {
     uint64_t N = 1ull << c;
     int mb = c + h;
@@ -1449,7 +1779,7 @@ int or_item_sweep(int n, int c, const int *H, int h, uint64_t base_tile,
     for (int i = 0; i < h; ++i) fmask &= ~(1ull << H[i]);
     uint64_t fixed = base_tile << c;
     const int moves = sweep_moves_tiles(g, ng, c);
-    alpha = alpha * sweep_scale(g, ng, fuse);                  /* normalize and scaled gates */
+    alpha = alpha * sweep_scale(g, ng, opts & 1);              /* normalize and scaled gates */
     int touched = alpha != 1.0 && !moves;
     for (int i = 0; i < ng && !touched; ++i)
         if (gate_touches(&g[i], fixed, fmask)) touched = 1;
@@ -1482,10 +1812,11 @@ int or_item_sweep(int n, int c, const int *H, int h, uint64_t base_tile,
         if (or_decode_tile(in[j], in_len[j], c, buf + 2 * j * N) != 0) rc = -1;
     if (rc == 0 && alpha != 1.0)
         for (uint64_t i = 0; i < 2 * ((uint64_t)1 << mb); ++i) buf[i] = buf[i] * alpha;
-    if (rc == 0 && apply_gates_buf(buf, mb, qb, fixed, g, ng, c, fuse) != 0) rc = -2;
+    if (rc == 0 && apply_gates_buf(buf, mb, qb, fixed, g, ng, c, opts & 1) != 0) rc = -2;
     for (uint64_t j = 0; j < (1ull << h) && rc == 0; ++j) {
         int level = 0, flags = 0;
-        size_t len = or_encode_tile(buf + 2 * j * N, c, shifts, nlev, max_bytes, tmp, &level, &flags);
+        size_t len = or_encode_tile_opt(buf + 2 * j * N, c, shifts, nlev, max_bytes, (opts >> 1) & 1, tmp,
+                                        &level, &flags);
         if (used + len > out_cap) { rc = -3; break; }
         memcpy(out + used, tmp, len);
         out_len[j] = (uint32_t)len;
@@ -1508,7 +1839,7 @@ int or_item_sweep(int n, int c, const int *H, int h, uint64_t base_tile,
  * is not 0.
  */
 typedef struct {
-    int n, c, h, ng, nlev, threads, k, fuse;
+    int n, c, h, ng, nlev, threads, k, opts;
     const int *H;
     uint64_t nitems, max_bytes;
     const uint64_t *bases, *in_off;
@@ -1531,7 +1862,7 @@ static void *batch_worker(void *arg)
     for (uint64_t i = (uint64_t)b->k; i < b->nitems; i += (uint64_t)b->threads) {
         for (uint64_t j = 0; j < nm; ++j) ptrs[j] = b->in_buf + b->in_off[i * nm + j];
         b->rc[i] = or_item_sweep(b->n, b->c, b->H, b->h, b->bases[i], ptrs, b->in_len + i * nm,
-                                 b->alpha, b->g, b->ng, b->shifts, b->nlev, b->max_bytes, b->fuse,
+                                 b->alpha, b->g, b->ng, b->shifts, b->nlev, b->max_bytes, b->opts,
                                  b->out + i * b->out_stride, b->out_stride, b->out_len + i * nm);
     }
     return NULL;
@@ -1540,7 +1871,7 @@ static void *batch_worker(void *arg)
 int or_item_sweep_batch(int n, int c, const int *H, int h, uint64_t nitems, const uint64_t *bases,
                         const uint8_t *in_buf, const uint64_t *in_off, const uint32_t *in_len,
                         double alpha, const or_gate *g, int ng, const int *shifts, int nlev,
-                        uint64_t max_bytes, int fuse, uint8_t *out, size_t out_stride, uint32_t *out_len,
+                        uint64_t max_bytes, int opts, uint8_t *out, size_t out_stride, uint32_t *out_len,
                         int *rc, int threads)
 {
     if (h < 0 || h > 4) return -1;
@@ -1550,7 +1881,7 @@ int or_item_sweep_batch(int n, int c, const int *H, int h, uint64_t nitems, cons
     pthread_t tid[256];
     int started[256];
     for (int k = 0; k < threads; ++k) {
-        batch_job b = {n, c, h, ng, nlev, threads, k, fuse, H, nitems, max_bytes, bases, in_off, in_buf,
+        batch_job b = {n, c, h, ng, nlev, threads, k, opts, H, nitems, max_bytes, bases, in_off, in_buf,
                        in_len, alpha, g, shifts, out, out_stride, out_len, rc};
         jobs[k] = b;
         started[k] = k > 0 && pthread_create(&tid[k], NULL, batch_worker, &jobs[k]) == 0;
@@ -1588,11 +1919,11 @@ static int cmp_u64(const void *a, const void *b)
 int or_stride_sweep(int n, int c, const int *H, int h, int ut, uint64_t umax, uint64_t t0,
                     const uint64_t *tiles, const uint8_t *const *in, const uint32_t *in_len,
                     uint64_t ntl, double alpha, const or_gate *g, int ng, const int *shifts,
-                    int nlev, int fuse, uint8_t *out, size_t out_cap, uint32_t *out_len)
+                    int nlev, int opts, uint8_t *out, size_t out_cap, uint32_t *out_len)
 {
     uint64_t N = 1ull << c, nt = 1ull << ut;
     int mb = c + h, rc = 0;
-    alpha = alpha * sweep_scale(g, ng, fuse);                  /* normalize and scaled gates */
+    alpha = alpha * sweep_scale(g, ng, opts & 1);              /* normalize and scaled gates */
     int qb[64];
     for (int p = 0; p < c; ++p) qb[p] = p;
     uint64_t hmask_tile = 0;
@@ -1622,7 +1953,7 @@ int or_stride_sweep(int n, int c, const int *H, int h, int ut, uint64_t umax, ui
         if (rc) break;
         if (alpha != 1.0)
             for (uint64_t i = 0; i < 2 * ((uint64_t)1 << mb); ++i) buf[i] = buf[i] * alpha;
-        if (apply_gates_buf(buf, mb, qb, T << c, g, ng, c, fuse) != 0) rc = -2;
+        if (apply_gates_buf(buf, mb, qb, T << c, g, ng, c, opts & 1) != 0) rc = -2;
         for (uint64_t j = 0; j < (1ull << h) && rc == 0; ++j) {
             uint64_t Tj = T;
             for (int i = 0; i < h; ++i)
@@ -1634,7 +1965,7 @@ int or_stride_sweep(int n, int c, const int *H, int h, int ut, uint64_t umax, ui
         uint8_t **sb = malloc(nt * sizeof *sb);
         size_t *len = malloc(nt * sizeof *len);
         for (uint64_t j = 0; j < nt; ++j) sb[j] = malloc(or_stream_cap(c));
-        encode_stride(sbuf, nt, c, shifts, nlev, umax, sb, len);
+        encode_stride(sbuf, nt, c, shifts, nlev, umax, (opts >> 1) & 1, sb, len);
         size_t used = 0;
         for (uint64_t j = 0; j < nt; ++j) {
             if (rc == 0 && used + len[j] > out_cap) rc = -3;
