@@ -830,8 +830,8 @@ static size_t encode_at(const double *a, int c, int s, int level, uint8_t *out)
  *     CORDIC below, code qa = round(angle / 2^P) mod 2^B with P = s + 8,
  *     B = 64 - P bits, reconstructed direction (X, Y) = CORDIC rotation of
  *     (2^59, 0) by qa << P;
- *   a^ = (m^ (Xd / l), m^ (Yd / l)) with Xd, Yd the doubles nearest X, Y
- *     and l = sqrt(fma(Xd, Xd, Yd*Yd)).
+ *   a^ = (m^ (Xd r), m^ (Yd r)) with Xd, Yd the doubles nearest X, Y
+ *     and r = 1 / sqrt(fma(Xd, Xd, Yd*Yd)) (IEEE division and square root).
  * The mode is used only when every amplitude then satisfies
  * |a^ - a|^2 <= 2^(2(s-53)) (1 - 2^-10) |a|^2 (checked in IEEE arithmetic;
  * the margin covers the check's own rounding), i.e. the level's bound on
@@ -953,9 +953,9 @@ static void polar_recon(uint64_t qm, uint64_t qa, int s, double *re, double *im)
     int64_t X, Y;
     polar_dir(qa << P, &X, &Y);
     double xd = (double)X, yd = (double)Y;
-    double l = sqrt(fma(xd, xd, yd * yd));
-    *re = m * (xd / l);
-    *im = m * (yd / l);
+    double r = 1.0 / sqrt(fma(xd, xd, yd * yd));
+    *re = m * (xd * r);
+    *im = m * (yd * r);
 }
 
 void or_polar_recon(uint64_t qm, uint64_t qa, int s, double *re, double *im)
