@@ -172,6 +172,30 @@ qsim_status qsim_set_normalize(qsim_t h, int on);
 qsim_status qsim_set_schedule(qsim_t h, int tile_log2, int hmax, int depth);
 
 /*
+ * qsim_set_polar -- on = 1: every lossy level of a REL or AALC handle also
+ * codes each tile in the POLAR mode and keeps the shorter stream (a codec
+ * variant; the level decision of AALC then uses that size).  POLAR stream
+ * (mode byte 3): each nonzero amplitude a = x + iy as its magnitude
+ * m = sqrt(fma(x, x, y*y)) quantised like a component with shift s - 2,
+ * and its angle from an integer CORDIC (30 steps of
+ * round(2^64 atan(2^-k) / (2 pi)), units of 2^-64 turn) quantised with
+ * shift s + 8 to B = 56 - s bits; reconstruction: the CORDIC rotation
+ * (X, Y) of (2^59, 0) by the angle code, a^ = (m^ Xd r, m^ Yd r) with
+ * r = 1 / sqrt(Xd^2 + Yd^2).  Magnitude codes: order-1 residuals from the
+ * anchor (header 8..15); angle codes: order-2 residuals modulo 2^B from
+ * u0 (header 16..23) and the first difference d1 (header 26..31, 48 bits),
+ * the first two nonzero amplitudes taking residual 0; body as PACKED with
+ * clear sign sections and equal zero sections.  A tile takes the mode
+ * only for 8 <= s <= 52, every component 0 or in [2^-400, 16), and every
+ * amplitude within |a^ - a|^2 <= 2^(2(s-53)) (1 - 2^-10) |a|^2: the
+ * level's bound on the complex amplitude, not on each component.  Phases
+ * linear in the index (the QFT's tiles) cost almost nothing.  Saved in
+ * checkpoints.  Flushes queued gates first.  Errors: ARG (codec NONE or
+ * LOSSLESS).
+ */
+qsim_status qsim_set_polar(qsim_t h, int on);
+
+/*
  * qsim_set_sweep_threads -- CTA size of the sweep kernel: 128, 256 (the
  * default) or 512 threads, compiled for 3, 3 and 1 resident CTAs per SM
  * (the register budget of each launch shape).  Results do not depend on it;
@@ -511,7 +535,8 @@ qsim_status qsim_server_destroy(qsim_server_t s);
  * and reloaded later).  qsim_save flushes the queued gates and writes
  *   a 120-byte little-endian header: "QSIMCKP1", u32 version (2), n, c,
  *   hmax, depth, codec, normalize, nlev, i32 shifts[8], f64 eps, theta,
- *   u64 max_bytes, ntiles, stream bytes, i32 unit_log2, i32 reserved (0);
+ *   u64 max_bytes, ntiles, stream bytes, i32 unit_log2, i32 flags (bit 0 the
+ *   POLAR mode, bit 1 gate by gate, see qsim_set_fusion; other bits 0);
  *   then, per chunk of up to 2^20 tiles in tile order, the u64 stream
  *   sizes of the chunk followed by its streams (the tile stream format
  *   above, so a host program can decode the file tile by tile).

@@ -339,6 +339,7 @@ struct qsim_state {
     size_t rd_cap = 0;
     unsigned long long h2d_bytes = 0, d2h_bytes = 0;   // since creation (never reset)
     int fuse = 1;                         // diagonal runs as one operator
+    int polar = 0;                        // lossy levels also try the POLAR mode
     int threads = qs::SWEEP_THREADS;      // sweep kernel CTA size
     // diagonal runs of the flush in progress (host staging, device copies)
     std::vector<qs::DRun> hruns;
@@ -562,6 +563,7 @@ void set_codec(qsim_t h) {
     cc = qs::CodecCfg{};
     cc.c = h->c;
     cc.max_bytes = ~0ull;
+    cc.polar = h->polar;
     switch (h->codec) {
         case QSIM_CODEC_NONE:
             cc.force_raw = 1; cc.nlev = 1; cc.shifts[0] = 0; h->normalize = 0; break;
@@ -1529,6 +1531,17 @@ qsim_status qsim_set_aalc_unit(qsim_t h, int unit_log2) {
     return QSIM_OK;
 }
 
+qsim_status qsim_set_polar(qsim_t h, int on) {
+    qsim_status s = check_usable(h);
+    if (s != QSIM_OK) return s;
+    if (h->codec != QSIM_CODEC_REL && h->codec != QSIM_CODEC_AALC)
+        return fail(h, QSIM_ERR_ARG, "the POLAR mode needs a lossy codec (REL or AALC)");
+    if ((s = qsim_flush(h)) != QSIM_OK) return s;
+    h->polar = on ? 1 : 0;
+    h->cc.polar = h->polar;
+    return QSIM_OK;
+}
+
 qsim_status qsim_set_sweep_threads(qsim_t h, int threads) {
     qsim_status s = check_usable(h);
     if (s != QSIM_OK) return s;
@@ -1965,6 +1978,7 @@ qsim_status qsim_save(qsim_t h, const char *path) {
     hd.ntiles = h->ntiles;
     hd.stream_bytes = h->used;
     hd.unit_log2 = h->unit_log2;
+    hd.reserved = (h->polar ? 1 : 0) | (h->fuse ? 0 : 2);      // flags: POLAR mode, gate by gate
     if (fwrite(&hd, sizeof hd, 1, fc.f) != 1) return fail(h, QSIM_ERR_ARG, "write failed: %s", path);
     std::vector<unsigned long long> sizes;
     std::vector<uint8_t> buf;
@@ -2023,6 +2037,10 @@ qsim_status qsim_load(qsim_t *out, const char *path) {
     for (int i = 0; i < qs::MAX_LEVELS; ++i) h->cc.shifts[i] = i < (int)hd.nlev ? hd.shifts[i] : 0;
     h->cc.max_bytes = hd.max_bytes;
     h->unit_log2 = hd.unit_log2;
+    if (hd.reserved & ~3) { g_last_error = "unknown checkpoint flags"; return bail(QSIM_ERR_FORMAT); }
+    h->polar = hd.reserved & 1;
+    h->cc.polar = h->polar;
+    h->fuse = (hd.reserved & 2) ? 0 : 1;
     std::vector<unsigned long long> sizes;
     std::vector<uint8_t> buf;
     for (unsigned long long first = 0; first < h->ntiles; first += CKPT_CHUNK) {

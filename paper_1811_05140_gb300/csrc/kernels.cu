@@ -24,7 +24,7 @@ constexpr unsigned long long INF_BITS = 0x7FF0000000000000ull;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr unsigned long long SIGN_BIT = 0x8000000000000000ull;
 
-enum { M_CONST = 0, M_PACKED = 1, M_RAW = 2 };
+enum { M_CONST = 0, M_PACKED = 1, M_RAW = 2, M_POLAR = 3 };
 enum { S_CLEAR = 0, S_SET = 1, S_EXC_CLEAR = 2, S_EXC_SET = 3, S_WORDS = 4 };
 
 __device__ __forceinline__ Acc4 make_acc4(double x, double y, double z, double w) {
@@ -857,6 +857,207 @@ __device__ __forceinline__ uint32_t read_section(const uint32_t *b32, uint32_t m
     return size;
 }
 
+// ---------------------------------------------------------------- polar mode
+// POLAR tiles: every nonzero amplitude a = x + iy coded as its magnitude
+// m = sqrt(fma(x, x, y*y)), quantised like a component with shift s - 2,
+// and its angle in units of 2^-64 turn from a 30-step integer CORDIC,
+// quantised with shift P = s + 8 to B = 56 - s bits.  Reconstruction:
+// the CORDIC rotation (X, Y) of (2^59, 0) by the angle code, then
+// a^ = (m^ (Xd r), m^ (Yd r)) with r = 1 / sqrt(fma(Xd, Xd, Yd*Yd)).  Used
+// at a lossy level (8 <= s <= 52) only when every component is 0 or in
+// [2^-400, 16), every reconstruction satisfies |a^ - a|^2 <= 2^(2(s-53))
+// (1 - 2^-10) |a|^2, and the stream is shorter than the componentwise one.
+// Codes run along the nonzero amplitudes: magnitudes by order-1 Lorenzo,
+// angles by order-2 Lorenzo modulo 2^B from the anchor u0 and the first
+// difference d1 (header bytes 26..31); the PACKED body layout with clear
+// sign sections.
+
+// round(2^64 atan(2^-k) / (2 pi)), written by configure_kernels
+__constant__ unsigned long long c_polar_atan[POLAR_ITERS];
+
+// fixed point of x with the larger component's biased exponent emax at 2^59
+__device__ __forceinline__ long long polar_fix(double x, int emax) {
+    const unsigned long long u = dbits(x);
+    const int e = (int)((u >> 52) & 0x7FFull);
+    const unsigned long long f = u & 0xFFFFFFFFFFFFFull;
+    if (e == 0 && f == 0) return 0;
+    const unsigned long long m = f | (1ull << 52);
+    const int sh = 7 + e - emax;
+    const unsigned long long v = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> (-sh)) : 0ull);
+    return (u >> 63) ? -(long long)v : (long long)v;
+}
+
+// angle of (x, y) in units of 2^-64 turn (CORDIC vectoring)
+__device__ __noinline__ unsigned long long polar_angle(double x, double y) {
+    const int ex = (int)((dbits(x) >> 52) & 0x7FFull), ey = (int)((dbits(y) >> 52) & 0x7FFull);
+    const int emax = ex > ey ? ex : ey;
+    long long X = polar_fix(x, emax), Y = polar_fix(y, emax);
+    unsigned long long th = 0;
+    if (X < 0) { X = -X; Y = -Y; th = 1ull << 63; }
+    for (int k = 0; k < POLAR_ITERS; ++k) {
+        const long long dx = Y >> k, dy = X >> k;
+        if (Y >= 0) { X += dx; Y -= dy; th += c_polar_atan[k]; }
+        else { X -= dx; Y += dy; th -= c_polar_atan[k]; }
+    }
+    return th;
+}
+
+// a^ of magnitude code qm and angle code qa at shift s (CORDIC rotation)
+__device__ __noinline__ void polar_recon(unsigned long long qm, unsigned long long qa, int s, double &re,
+                                         double &im) {
+    const unsigned long long th = qa << (s + 8);
+    long long X = 1ll << 59, Y = 0;
+    unsigned long long z = th;
+    if (((th >> 62) + 1ull) & 2ull) { X = -X; z = th - (1ull << 63); }
+    long long zz = (long long)z;
+    for (int k = 0; k < POLAR_ITERS; ++k) {
+        const long long dx = Y >> k, dy = X >> k;
+        if (zz >= 0) { X -= dx; Y += dy; zz -= (long long)c_polar_atan[k]; }
+        else { X += dx; Y -= dy; zz += (long long)c_polar_atan[k]; }
+    }
+    const double m = bitsd(qm << (s - 2));
+    const double xd = __ll2double_rn(X), yd = __ll2double_rn(Y);
+    const double r = __ddiv_rn(1.0, __dsqrt_rn(__fma_rn(xd, xd, __dmul_rn(yd, yd))));
+    re = __dmul_rn(m, __dmul_rn(xd, r));
+    im = __dmul_rn(m, __dmul_rn(yd, r));
+}
+
+__device__ __forceinline__ bool polar_comp_ok(double x) {
+    const unsigned long long u = dbits(x);
+    const unsigned e = (unsigned)((u >> 52) & 0x7FFull);
+    return (u & MAG) == 0ull || (e >= 623u && e < 1027u);
+}
+
+// Codes of one amplitude at shift s; false when the amplitude rules the
+// mode out.  nz: the amplitude is not zero.
+__device__ __forceinline__ bool polar_codes(double x, double y, int s, bool &nz, unsigned long long &qm,
+                                            unsigned long long &qa, double &xr, double &xi) {
+    nz = false;
+    qm = qa = 0ull;
+    xr = xi = 0.0;
+    if (!polar_comp_ok(x) || !polar_comp_ok(y)) return false;
+    if ((dbits(x) & MAG) == 0ull && (dbits(y) & MAG) == 0ull) return true;
+    nz = true;
+    const int P = s + 8, B = 64 - P;
+    const double mm = __fma_rn(x, x, __dmul_rn(y, y));
+    qm = quant(dbits(__dsqrt_rn(mm)), s - 2);
+    qa = ((polar_angle(x, y) + (1ull << (P - 1))) >> P) & ((1ull << B) - 1ull);
+    polar_recon(qm, qa, s, xr, xi);
+    const double dr = __dsub_rn(xr, x), di = __dsub_rn(xi, y);
+    const double lim = ldexp(1.0 - 0x1p-10, 2 * (s - 53));
+    return __fma_rn(dr, dr, __dmul_rn(di, di)) <= __dmul_rn(lim, mm);
+}
+
+// Sizing (WRITE false) or packing (WRITE true) pass of the POLAR mode over
+// a tile at shift s.  Sizing: ok (every amplitude codable), the anchors
+// am / au, the first angle difference d1, and in lane g the zero word and
+// the two residual widths of group g.  Packing: writes the residuals of
+// group g at data + o0 (magnitudes) and data + o1 (angles), the word
+// offsets held in lane g, and adds the reconstructed values' norm.
+struct PolarInfo {
+    unsigned long long am, au, d1;
+    uint32_t zw, w0, w1;
+    bool ok;
+};
+
+template <bool WRITE>
+__device__ __noinline__ void polar_pass(const double *re, const double *im, int s, int G, int L, PolarInfo &pi,
+                                        uint32_t *data, uint32_t o0, uint32_t o1, uint32_t *wstage,
+                                        unsigned long long &nlo, unsigned long long &nhi, unsigned &rng) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t below = lanes_below();
+    const uint32_t lanes = L == 32 ? FULL : ((1u << L) - 1u);
+    const int B = 56 - s;
+    const unsigned long long bmask = (1ull << B) - 1ull, half = 1ull << (B - 1);
+    unsigned long long lastm = 0, last1 = 0, last2 = 0;
+    uint32_t seen = 0;
+    if (!WRITE) { pi.am = pi.au = pi.d1 = 0; pi.zw = pi.w0 = pi.w1 = 0; pi.ok = true; }
+    for (int g = 0; g < G; ++g) {
+        const int i = g * 32 + lane;
+        const double x = lane < L ? re[i] : 0.0, y = lane < L ? im[i] : 0.0;
+        bool nz;
+        unsigned long long qm, qa;
+        double xr, xi;
+        const bool okv = lane < L ? polar_codes(x, y, s, nz, qm, qa, xr, xi) : (nz = false, qm = qa = 0, xr = xi = 0.0, true);
+        if (!WRITE && !__all_sync(FULL, okv)) { pi.ok = false; return; }
+        const uint32_t nzm = __ballot_sync(FULL, nz);
+        if (!WRITE && lane == g) pi.zw = ~nzm & lanes;
+        if (nzm == 0u) continue;
+        const uint32_t pm = nzm & below;
+        const int p1 = pm ? 31 - __clz(pm) : lane;
+        const uint32_t pm2 = pm & ~(1u << (p1 & 31));
+        const int p2 = pm2 ? 31 - __clz(pm2) : lane;
+        const unsigned long long m1 = shfl64(qm, p1), a1 = shfl64(qa, p1), a2 = shfl64(qa, p2);
+        const uint32_t rank = (uint32_t)__popc(pm), cnt = (uint32_t)__popc(nzm);
+        const unsigned long long prevm = pm ? m1 : (seen ? lastm : qm);
+        const unsigned long long prev1 = pm ? a1 : last1;
+        const unsigned long long prev2 = pm2 ? a2 : (pm ? last1 : last2);
+        const unsigned long long ra = (seen + rank >= 2u) ? ((qa - 2ull * prev1 + prev2) & bmask) : 0ull;
+        const long long rs = (long long)((ra ^ half) - half);
+        const bool nzl = nz;
+        const unsigned long long zm = nzl ? zigzag(qm - prevm) : 0ull;
+        const unsigned long long za = nzl ? (((unsigned long long)rs << 1) ^ (unsigned long long)(rs >> 63)) : 0ull;
+        const int f0 = __ffs(nzm) - 1;
+        if (!WRITE) {
+            if (seen == 0u) { pi.am = shfl64(qm, f0); pi.au = shfl64(qa, f0); }
+            if (seen < 2u && seen + cnt >= 2u) {
+                // the second nonzero amplitude of the tile and its predecessor
+                const int l1 = seen == 1u ? f0 : __ffs(nzm & ~(1u << f0)) - 1;
+                const unsigned long long u1 = shfl64(qa, l1);
+                pi.d1 = (u1 - (seen == 1u ? last1 : shfl64(qa, f0))) & bmask;
+            }
+            const uint32_t w0 = (uint32_t)bitlen64(warp_or64(zm)), w1 = (uint32_t)bitlen64(warp_or64(za));
+            if (lane == g) { pi.w0 = w0; pi.w1 = w1; }
+        } else {
+            if (nzl) {
+                unsigned long long l0, h0, l1v, h1v;
+                sq_units(dbits(xr) & MAG, l0, h0, rng);
+                sq_units(dbits(xi) & MAG, l1v, h1v, rng);
+                add128(l0, h0, l1v, h1v);
+                add128(nlo, nhi, l0, h0);
+            }
+            for (int k = 0; k < 2; ++k) {
+                const uint32_t w = __shfl_sync(FULL, k ? pi.w1 : pi.w0, g);
+                if (w == 0) continue;
+                const uint32_t wo = __shfl_sync(FULL, k ? o1 : o0, g);
+                const uint32_t nwd = (cnt * w + 31u) >> 5;
+                const unsigned long long z = k ? za : zm;
+                wstage[lane] = 0u;
+                wstage[lane + 32] = 0u;
+                __syncwarp();
+                if (nzl) {
+                    const uint32_t bo = rank * w, j0 = bo >> 5, sh = bo & 31u;
+                    atomicOr(&wstage[j0], (uint32_t)(z << sh));
+                    if (sh + w > 32) atomicOr(&wstage[j0 + 1], (uint32_t)(z >> (32 - sh)));
+                    if (sh + w > 64) atomicOr(&wstage[j0 + 2], (uint32_t)(z >> (64 - sh)));
+                }
+                __syncwarp();
+                if ((uint32_t)lane < nwd) data[wo + lane] = wstage[lane];
+                if ((uint32_t)lane + 32 < nwd) data[wo + lane + 32] = wstage[lane + 32];
+                __syncwarp();
+            }
+        }
+        const int lastl = 31 - __clz(nzm);
+        const unsigned long long ql = shfl64(qm, lastl), al = shfl64(qa, lastl);
+        const uint32_t pml = nzm & ~(1u << lastl);
+        const unsigned long long al2 = shfl64(qa, pml ? 31 - __clz(pml) : lastl);
+        last2 = cnt >= 2u ? al2 : last1;
+        last1 = al;
+        lastm = ql;
+        seen += cnt;
+    }
+}
+
+// Body bytes of a POLAR stream from its sizing pass (warp-uniform).
+__device__ __forceinline__ uint32_t polar_body(const PolarInfo &pi, int G, uint32_t lanes, int &zmode) {
+    const int lane = threadIdx.x & 31;
+    uint32_t zb;
+    zmode = section_mode(pi.zw, G, lanes, zb);
+    const uint32_t nn = lane < G ? (uint32_t)__popc(~pi.zw & lanes) : 0u;
+    const uint32_t words = __reduce_add_sync(FULL, ((nn * pi.w0 + 31u) >> 5) + ((nn * pi.w1 + 31u) >> 5));
+    return (2u * zb + ((2u * (uint32_t)G + 3u) & ~3u) + 4u * words + 15u) & ~15u;
+}
+
 // Decode one stream into planar re/im (2^c values each), multiplied by
 // alpha when `scale` (Algorithm 2's normalize, fused).  Warp-wide; returns
 // nonzero (and zero-fills) on a malformed stream.  The first 128 body bytes
@@ -871,14 +1072,16 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
     const uint32_t h0 = __shfl_sync(FULL, hw, 0), body = __shfl_sync(FULL, hw, 1);
     const unsigned long long a0 = ((unsigned long long)__shfl_sync(FULL, hw, 3) << 32) | __shfl_sync(FULL, hw, 2);
     const unsigned long long a1 = ((unsigned long long)__shfl_sync(FULL, hw, 5) << 32) | __shfl_sync(FULL, hw, 4);
-    const uint32_t h6 = __shfl_sync(FULL, hw, 6);
+    const uint32_t h6 = __shfl_sync(FULL, hw, 6), h7 = __shfl_sync(FULL, hw, 7);
     const int hc = h6 & 0xFF;
     const int mode = h0 & 0xFF, s = (h0 >> 8) & 0xFF;
     const int sm0 = (h0 >> 24) & 7, sm1 = (h0 >> 27) & 7;
     const int zm0 = (h6 >> 8) & 7, zm1 = (h6 >> 11) & 7;
     const uint8_t *b = src + HDR;
     const uint32_t *b32 = reinterpret_cast<const uint32_t *>(b);
-    bool bad = hc != c || mode > 2 || (mode != M_RAW && s > 52) || (body & 15u);
+    const bool polar = mode == M_POLAR;
+    bool bad = hc != c || mode > 3 || (mode != M_RAW && s > 52) || (body & 15u);
+    if (!bad && polar) bad = s < 8 || sm0 != S_CLEAR || sm1 != S_CLEAR;
     if (!bad && mode == M_RAW) bad = body != 16u * (uint32_t)N;
     if (!bad && mode == M_CONST) bad = body != 0 || sm0 > 1 || sm1 > 1 || ((h6 >> 8) & 0xFFu);
     if (!bad && mode == M_CONST) {
@@ -923,6 +1126,8 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
             doff = (off + 2u * G + 3u) & ~3u;
             const uint32_t wmax = __reduce_max_sync(FULL, max(w0, w1));
             bad = wmax > 64 || (unsigned long long)doff + 4ull * (tot0 + tot1) > body;
+            // POLAR: a zero amplitude is zero in both code streams
+            if (!bad && polar) bad = __any_sync(FULL, lane < G && zw0 != zw1);
         }
     }
     if (bad) {
@@ -961,6 +1166,13 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
     meta(0, w, wo, sgw, nzw);
     fetch(w, wo, nzw, x0, x1, x2, sh);
     unsigned long long carry = a0;
+    // POLAR: magnitudes (component 0) are the codes with shift s - 2, kept
+    // unscaled in re until the angles (component 1) reconstruct the values
+    const int sv = polar ? s - 2 : s;
+    const unsigned long long bmask = polar ? (1ull << (56 - s)) - 1ull : 0ull;
+    const unsigned long long d1 = ((unsigned long long)h7 << 16) | (h6 >> 16);
+    unsigned long long cu = 0, cd = 0;                       // angle carries: last code, last difference
+    uint32_t seen = 0;                                       // nonzero amplitudes before this group
     for (int t = 0; t < T; ++t) {
         uint32_t wn = 0, won = 0, sgwn = 0, nzwn = 0, y0 = 0, y1 = 0, y2 = 0, shn = 0;
         if (t + 1 < T) {                                     // next group's words, in flight meanwhile
@@ -969,14 +1181,58 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
         }
         const bool k = t >= G;
         const int g = k ? t - G : t;
-        if (t == G) carry = a1;
+        if (t == G) {
+            carry = a1;
+            cu = (a1 - d1) & bmask;
+            cd = d1 & bmask;
+        }
         double *v = k ? im : re;
         if (nzw == 0u) {                                     // all zeros: signs only
             if (lane < L) {
                 double x = bitsd((unsigned long long)((sgw >> lane) & 1u) << 63);
-                if (scale) x = __dmul_rn(x, alpha);
+                if (scale && !polar) x = __dmul_rn(x, alpha);
                 v[g * 32 + lane] = x;
             }
+        } else if (polar && k) {
+            // angles: second-order running sums modulo 2^B, the first two
+            // nonzero amplitudes of the tile taking no residual
+            const bool nzl = (nzw >> lane) & 1u;
+            unsigned long long z = 0;
+            if (nzl && w) {
+                if (w <= 32) {
+                    const uint32_t z32 = __funnelshift_r(x0, x1, sh);
+                    z = w == 32 ? z32 : (z32 & ((1u << w) - 1u));
+                } else {
+                    const unsigned long long lo = (unsigned long long)x0 | ((unsigned long long)x1 << 32);
+                    const unsigned long long vv = sh ? ((lo >> sh) | ((unsigned long long)x2 << (64 - sh))) : lo;
+                    z = w == 64 ? vv : (vv & ((1ull << w) - 1ull));
+                }
+            }
+            const uint32_t rank = (uint32_t)__popc(nzw & below);
+            const unsigned long long rr = (nzl && seen + rank >= 2u) ? (unzigzag(z) & bmask) : 0ull;
+            unsigned long long s1 = rr;
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned long long o = shfl_up64(s1, d);
+                if (lane >= d) s1 += o;
+            }
+            unsigned long long s2 = nzl ? cd + s1 : 0ull;
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned long long o = shfl_up64(s2, d);
+                if (lane >= d) s2 += o;
+            }
+            if (lane < L) {
+                double ar = 0.0, ai = 0.0;
+                if (nzl) {
+                    const unsigned long long qm = dbits(re[g * 32 + lane]) >> sv;
+                    polar_recon(qm, (cu + s2) & bmask, s, ar, ai);
+                    if (scale) { ar = __dmul_rn(ar, alpha); ai = __dmul_rn(ai, alpha); }
+                }
+                re[g * 32 + lane] = ar;
+                im[g * 32 + lane] = ai;
+            }
+            cd = (cd + shfl64(s1, 31)) & bmask;
+            cu = (cu + shfl64(s2, 31)) & bmask;
+            seen += (uint32_t)__popc(nzw);
         } else {
             const bool nzl = (nzw >> lane) & 1u;
             unsigned long long z = 0;
@@ -1012,14 +1268,14 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
             const unsigned long long q = carry + inc;
             if (lane < L) {
                 double x;
-                if (s >= 32) {                               // (q << s) has a zero low word
-                    const uint32_t hw = (nzl ? (uint32_t)q << (s - 32) : 0u) | (((sgw >> lane) & 1u) << 31);
+                if (sv >= 32) {                              // (q << sv) has a zero low word
+                    const uint32_t hw = (nzl ? (uint32_t)q << (sv - 32) : 0u) | (((sgw >> lane) & 1u) << 31);
                     x = __hiloint2double((int)hw, 0);
                 } else {
                     const unsigned long long sg = (unsigned long long)((sgw >> lane) & 1u) << 63;
-                    x = bitsd(nzl ? ((q << s) | sg) : sg);
+                    x = bitsd(nzl ? ((q << sv) | sg) : sg);
                 }
-                if (scale) x = __dmul_rn(x, alpha);
+                if (scale && !polar) x = __dmul_rn(x, alpha);
                 v[g * 32 + lane] = x;
             }
             carry = shfl64(q, L - 1);
@@ -1320,7 +1576,19 @@ __device__ __noinline__ void wsize(const double *re, const double *im, const Cod
         uint32_t body = raw_body;
         if (!raw_only) {
             int mode, s0, s1;
-            body = level_body(ls, q, lv, inel ? 0 : cc.shifts[lv], raw_body, mode, s0, s1);
+            const int slv = inel ? 0 : cc.shifts[lv];
+            body = level_body(ls, q, lv, slv, raw_body, mode, s0, s1);
+            if (cc.polar && !inel && slv >= 8 && slv <= 52) {
+                unsigned long long d0 = 0, d1 = 0;
+                unsigned dr = 0;
+                PolarInfo pi;
+                polar_pass<false>(re, im, slv, G, L, pi, nullptr, 0u, 0u, nullptr, d0, d1, dr);
+                if (pi.ok) {
+                    int pz;
+                    const uint32_t pb = polar_body(pi, G, lanes, pz);
+                    if (pb < body) body = pb;
+                }
+            }
         }
         if (lane == 0) atomicAdd(bytes + lv, (unsigned long long)(HDR + body));
     }
@@ -1347,7 +1615,7 @@ __device__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc,
     int nonfin = 0, inel = 0;
     unsigned long long nlo = 0, nhi = 0;
     unsigned rng = 0;
-    bool onepass = !cc.force_raw && cc.nlev == 1 && cc.shifts[0] >= 32 && c >= 5;
+    bool onepass = !cc.force_raw && !cc.polar && cc.nlev == 1 && cc.shifts[0] >= 32 && c >= 5;
     if (onepass) {                           // every value zero or inside the lossy range?
         bool odd = false;
         for (int i = lane; i < N; i += 32) {
@@ -1377,6 +1645,7 @@ __device__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc,
     int mode, level = 0, s = 0, sm[2] = {0, 0}, zm[2] = {0, 0};
     uint32_t bodyb;
     const uint32_t raw_body = 16u * (uint32_t)N;
+    PolarInfo pinfo{};
     if (raw_only) {
         mode = M_RAW;
         bodyb = raw_body;
@@ -1388,10 +1657,30 @@ __device__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc,
         mode = M_RAW;
         bodyb = raw_body;
         bool found = false;                  // first level within the size limit, else the last
+        const bool try_polar = cc.polar && !inel;
 #pragma unroll
         for (int lv = 0; lv < MAX_LEVELS; ++lv) {
             if (lv >= cc.nlev || found || (force_lv >= 0 && lv != force_lv)) continue;
-            bodyb = level_body(ls, q, lv, inel ? 0 : cc.shifts[lv], raw_body, mode, sm[0], sm[1]);
+            const int slv = inel ? 0 : cc.shifts[lv];
+            bodyb = level_body(ls, q, lv, slv, raw_body, mode, sm[0], sm[1]);
+            if (try_polar && slv >= 8 && slv <= 52) {
+                // the POLAR variant of this level, kept when shorter
+                unsigned long long d0 = 0, d1 = 0;
+                unsigned dr = 0;
+                PolarInfo pi;
+                polar_pass<false>(re, im, slv, G, L, pi, nullptr, 0u, 0u, wstage, d0, d1, dr);
+                if (pi.ok) {
+                    int pz;
+                    const uint32_t pb = polar_body(pi, G, lanes, pz);
+                    if (pb < bodyb) {
+                        mode = M_POLAR;
+                        bodyb = pb;
+                        sm[0] = sm[1] = S_CLEAR;
+                        zm[0] = zm[1] = pz;
+                        pinfo = pi;
+                    }
+                }
+            }
             level = lv;
             found = force_lv >= 0 || (unsigned long long)(HDR + bodyb) <= cc.max_bytes;
         }
@@ -1417,7 +1706,10 @@ __device__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc,
 
     // header
     unsigned long long anc0 = 0, anc1 = 0;
-    if (mode != M_RAW) {
+    if (mode == M_POLAR) {
+        anc0 = pinfo.am;
+        anc1 = pinfo.au;
+    } else if (mode != M_RAW) {
         anc0 = quant(ls.f0, s);
         anc1 = quant(ls.f1, s);
     }
@@ -1435,16 +1727,41 @@ __device__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc,
             case 4: v = (uint32_t)anc1; break;
             case 5: v = (uint32_t)(anc1 >> 32); break;
             case 6: {
-                const uint32_t zmb = mode == M_PACKED ? (uint32_t)(zm[0] | (zm[1] << 3)) : 0u;
+                const uint32_t zmb = (mode == M_PACKED || mode == M_POLAR) ? (uint32_t)(zm[0] | (zm[1] << 3)) : 0u;
                 v = (uint32_t)c | (zmb << 8);
+                if (mode == M_POLAR) v |= (uint32_t)(pinfo.d1 & 0xFFFFull) << 16;
                 break;
             }
+            case 7: v = mode == M_POLAR ? (uint32_t)(pinfo.d1 >> 16) : 0u; break;
             default: v = 0; break;
         }
         reinterpret_cast<uint32_t *>(dst)[lane] = v;
     }
     uint8_t *b = dst + HDR;
-    if (mode == M_PACKED) {
+    if (mode == M_POLAR) {
+        // zero sections (sign sections clear), widths, residual words
+        uint32_t moff = 0, sz;
+        write_section(reinterpret_cast<uint32_t *>(b), zm[0], pinfo.zw, G, lanes);
+        moff += (section_mode(pinfo.zw, G, lanes, sz), sz);
+        write_section(reinterpret_cast<uint32_t *>(b + moff), zm[1], pinfo.zw, G, lanes);
+        moff += sz;
+        const uint32_t nn = lane < G ? (uint32_t)__popc(~pinfo.zw & lanes) : 0u;
+        uint32_t tot0, tot1;
+        const uint32_t o0 = warp_exscan(lane < G ? (nn * pinfo.w0 + 31u) >> 5 : 0u, tot0);
+        const uint32_t o1 = warp_exscan(lane < G ? (nn * pinfo.w1 + 31u) >> 5 : 0u, tot1) + tot0;
+        const uint32_t wb = (2u * G + 3u) & ~3u;
+        for (uint32_t base = 0; base < wb; base += 32) {          // uniform trip count
+            const int t = (int)base + lane;
+            const int src = t < G ? t : (t < 2 * G ? t - G : 0);
+            const uint32_t a = __shfl_sync(FULL, pinfo.w0, src & 31);
+            const uint32_t bb = __shfl_sync(FULL, pinfo.w1, src & 31);
+            if ((uint32_t)t < wb) b[moff + t] = (uint8_t)(t < G ? a : (t < 2 * G ? bb : 0u));
+        }
+        const uint32_t doff = moff + wb;
+        polar_pass<true>(re, im, s, G, L, pinfo, reinterpret_cast<uint32_t *>(b + doff), o0, o1, wstage, nlo, nhi,
+                         rng);
+        for (uint32_t p = doff + 4u * (tot0 + tot1) + lane; p < bodyb; p += 32) b[p] = 0;
+    } else if (mode == M_PACKED) {
         // sign sections, then zero sections
         const uint32_t sv0 = s ? ls.sw0 & ~ls.zw0 : ls.sw0, sv1 = s ? ls.sw1 & ~ls.zw1 : ls.sw1;
         uint32_t moff = 0, sz;
@@ -2570,11 +2887,47 @@ cudaError_t launch_pair_sum(const Acc4 *in, Acc4 *out, unsigned long long nout, 
     return cudaGetLastError();
 }
 
+// Fixed point with 124 fractional bits: arctan(1/n) = sum over j of
+// (-1)^j / ((2j+1) n^(2j+1)), the positive and the negative terms summed
+// apart (each truncated; the total error stays far below 2^-100).
+static unsigned __int128 host_atan_recip(unsigned long long n) {
+    const unsigned __int128 one = (unsigned __int128)1 << 124;
+    unsigned __int128 pos = 0, neg = 0, pw = one / n;
+    const unsigned __int128 n2 = (unsigned __int128)n * n;
+    for (unsigned long long j = 0; pw != 0; ++j, pw /= n2) {
+        if (j & 1) neg += pw / (2 * j + 1);
+        else pos += pw / (2 * j + 1);
+    }
+    return pos - neg;
+}
+
+// The POLAR mode's CORDIC table: atan(2^-k) / (2 pi) in units of 2^-64
+// turn, rounded to nearest; k = 0 is exactly 1/8 turn, pi comes from
+// Machin's formula pi/4 = 4 atan(1/5) - atan(1/239).
+static void host_polar_table(unsigned long long *t) {
+    const unsigned __int128 quarter_pi = 4 * host_atan_recip(5) - host_atan_recip(239);
+    const unsigned __int128 two_pi = 8 * quarter_pi;
+    t[0] = 1ull << 61;
+    for (int k = 1; k < POLAR_ITERS; ++k) {
+        unsigned __int128 rem = host_atan_recip(1ull << k);          // < two_pi
+        unsigned long long q = 0;
+        for (int i = 0; i < 64; ++i) {                                // floor(rem * 2^64 / two_pi)
+            rem <<= 1;
+            q <<= 1;
+            if (rem >= two_pi) { rem -= two_pi; q |= 1ull; }
+        }
+        t[k] = q + (2 * rem >= two_pi ? 1ull : 0ull);                 // round to nearest
+    }
+}
+
 // Kernel attributes of the current device (dynamic shared memory above
-// 48 KiB), set once per device: attributes apply to the device that is
-// current when they are set.
+// 48 KiB) and the POLAR table in its constant memory, set once per device:
+// attributes apply to the device that is current when they are set.
 static cudaError_t configure_current_device() {
     cudaError_t e;
+    unsigned long long tab[POLAR_ITERS];
+    host_polar_table(tab);
+    if ((e = cudaMemcpyToSymbol(c_polar_atan, tab, sizeof tab))) return e;
     const int sm128 = (int)sweep_smem_bytes(MAX_ITEM_LOG2, 128), sm256 = (int)sweep_smem_bytes(MAX_ITEM_LOG2, 256),
               sm512 = (int)sweep_smem_bytes(MAX_ITEM_LOG2, 512);
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;

@@ -133,7 +133,10 @@ struct CodecCfg {
     int shifts[MAX_LEVELS];         // quantisation shift per level
     unsigned long long max_bytes;   // ratio threshold as a stream size limit
     int force_raw;                  // uncompressed storage (QSIM_CODEC_NONE)
+    int polar;                      // lossy levels also try the POLAR mode (magnitude + phase)
 };
+
+constexpr int POLAR_ITERS = 30;         // CORDIC steps of the POLAR mode
 
 struct SweepParams {
     const uint8_t *in_arena;

@@ -32,7 +32,7 @@ EXPORTS = ["qsim_create", "qsim_destroy", "qsim_set_stream", "qsim_set_aalc", "q
            "qsim_server_submit", "qsim_server_result", "qsim_server_wait", "qsim_server_drain",
            "qsim_server_stats", "qsim_server_destroy", "qsim_set_pool", "qsim_fp64_rate",
            "qsim_save", "qsim_load", "qsim_set_aalc_unit", "qsim_export_tile_set",
-           "qsim_set_fusion", "qsim_set_sweep_threads"]
+           "qsim_set_fusion", "qsim_set_sweep_threads", "qsim_set_polar"]
 
 
 class QsimError(RuntimeError):
@@ -116,6 +116,7 @@ def load() -> C.CDLL:
         "qsim_set_normalize": ([vp, C.c_int], C.c_int),
         "qsim_set_fusion": ([vp, C.c_int], C.c_int),
         "qsim_set_sweep_threads": ([vp, C.c_int], C.c_int),
+        "qsim_set_polar": ([vp, C.c_int], C.c_int),
         "qsim_set_schedule": ([vp, C.c_int, C.c_int, C.c_int], C.c_int),
         "qsim_set_pool": ([vp, vp, C.c_size_t], C.c_int),
         "qsim_fp64_rate": ([C.c_int, C.POINTER(C.c_double)], C.c_int),
@@ -316,6 +317,10 @@ class State:
 
     def set_normalize(self, on: bool):
         self._check(self._L.qsim_set_normalize(self.h, int(bool(on))))
+
+    def set_polar(self, on: bool = True):
+        """Lossy levels also try the POLAR mode (magnitude + phase)."""
+        self._check(self._L.qsim_set_polar(self.h, int(bool(on))))
 
     def set_sweep_threads(self, threads: int):
         """CTA size of the sweep kernel (128, 256 or 512)."""
