@@ -486,8 +486,10 @@ def run_aalc(args):
     """The 26-qubit QFT (the paper's size) under the error-bound ladder
     {lossless, 1e-5, 1e-4, 1e-3, 1e-2} with thresholds 4, 8, 16, 32 and 64
     decided per tile, with thresholds 4, 8, 16 and 32 decided per stride of
-    2^20 amplitudes (Algorithm 2), and under fixed bounds: fidelity against the uncompressed FP64 run,
-    minimum and final compression ratio, level histogram, gates/s."""
+    2^20 amplitudes (Algorithm 2), with the POLAR variant on every lossy
+    level, and under fixed bounds: fidelity against the uncompressed FP64
+    run, minimum and final compression ratio, level histogram, tiles that
+    met no level's size limit (over every sweep), gates/s."""
     import torch
 
     from paper_1811_05140_gb300 import build as B
@@ -523,7 +525,9 @@ def run_aalc(args):
         rows.append({"setting": label, "fidelity_vs_fp64": st.fidelity_state(ref),
                      "ratio_final": raw / st.compressed_bytes()[0],
                      "ratio_min": raw / max(1, stats["max_stream_bytes_seen"]),
-                     "level_hist": stats["level_hist"][:len(ladder) + 1], "gates_per_s": len(gates) / dt})
+                     "level_hist": stats["level_hist"][:len(ladder) + 1],
+                     "tiles_over_limit": stats["tiles_over_limit"],
+                     "tiles_written": sum(stats["level_hist"]), "gates_per_s": len(gates) / dt})
         st.close()
 
     for theta in (4.0, 8.0, 16.0, 32.0, 64.0):
@@ -539,8 +543,21 @@ def run_aalc(args):
             st.set_aalc_unit(20)
             return st
         one(f"aalc per stride theta={theta:g}", make)
+    for theta in (4.0, 8.0, 16.0, 32.0, 64.0):
+        def make(theta=theta):                        # the POLAR variant on every lossy level
+            st = qsim.State(n, 20, "aalc", ladder[-1])
+            st.set_aalc(theta, ladder)
+            st.set_polar(True)
+            return st
+        one(f"aalc polar theta={theta:g}", make)
     for eps in (1e-2, 1e-3, 1e-4):
         one(f"fixed rel {eps:g}", lambda eps=eps: qsim.State(n, 20, "rel", eps))
+    for eps in (1e-3, 1e-4):
+        def make(eps=eps):
+            st = qsim.State(n, 20, "rel", eps)
+            st.set_polar(True)
+            return st
+        one(f"fixed rel {eps:g} polar", make)
     ref.close()
     print(json.dumps({"metric": "fidelity and compression ratio per threshold (QFT-26)", "unit": "table",
                       "config": {"workload": "qft26_aalc_thresholds", "ladder": [0.0] + ladder,

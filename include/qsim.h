@@ -327,6 +327,7 @@ typedef struct {
     int tile_log2, hmax, depth, n_qubits;
     unsigned long long h2d_bytes;      /* bytes the handle's calls copied host -> device since creation */
     unsigned long long d2h_bytes;      /* bytes the handle's calls copied device -> host since creation */
+    unsigned long long tiles_over_limit; /* tiles written larger than the AALC size limit (no level met theta) */
 } qsim_stats_t;
 
 qsim_status qsim_stats(qsim_t h, qsim_stats_t *out);

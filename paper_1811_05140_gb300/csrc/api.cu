@@ -1794,6 +1794,7 @@ qsim_status qsim_stats(qsim_t h, qsim_stats_t *out) {
     out->n_qubits = h->n;
     out->h2d_bytes = h->h2d_bytes;
     out->d2h_bytes = h->d2h_bytes;
+    out->tiles_over_limit = h->hscal->over_limit;
     return QSIM_OK;
 }
 

@@ -1686,6 +1686,7 @@ __device__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc,
         }
         s = mode == M_RAW ? 0 : (inel ? 0 : cc.shifts[level]);
     }
+    const bool over = (unsigned long long)(HDR + bodyb) > cc.max_bytes;
     const uint32_t size = HDR + bodyb;
     unsigned long long off = 0;
     int ok = 0;
@@ -1928,6 +1929,7 @@ __device__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc,
         atomic_add128(&scal->acc_lo, &scal->acc_hi, nlo, nhi);
         out_table[tile] = off;
         atomicAdd(&scal->hist[level], 1ull);
+        if (over) atomicAdd(&scal->over_limit, 1ull);
         if (rng) atomicOr(&scal->err, ERR_RANGE);
     }
     __syncwarp();
@@ -2030,6 +2032,7 @@ __device__ bool wencode_uniform(double *re, double *im, const CodecCfg &cc, unsi
         atomic_add128(&scal->acc_lo, &scal->acc_hi, nlo, nhi);
         out_table[tile] = off;
         atomicAdd(&scal->hist[level], 1ull);
+        if ((unsigned long long)HDR > cc.max_bytes) atomicAdd(&scal->over_limit, 1ull);
         if (rng) atomicOr(&scal->err, ERR_RANGE);
     }
     __syncwarp();

@@ -35,7 +35,7 @@ struct DevScalars {
     unsigned long long items_done, items_skipped;
     unsigned long long work;        // item counter of the sweep launch in flight
     unsigned long long run_dp;      // FP64 instructions executed by diagonal runs (running total)
-    unsigned long long pad[1];
+    unsigned long long over_limit;  // tiles written above the ratio threshold's size (no level met it)
 };
 
 // A gate prepared for one sweep (positions are item-buffer bits).

@@ -55,7 +55,8 @@ class Stats(C.Structure):
                 ("arena_regrows", C.c_ulonglong), ("kernel_launches", C.c_ulonglong),
                 ("alpha", C.c_double),
                 ("tile_log2", C.c_int), ("hmax", C.c_int), ("depth", C.c_int),
-                ("n_qubits", C.c_int), ("h2d_bytes", C.c_ulonglong), ("d2h_bytes", C.c_ulonglong)]
+                ("n_qubits", C.c_int), ("h2d_bytes", C.c_ulonglong), ("d2h_bytes", C.c_ulonglong),
+                ("tiles_over_limit", C.c_ulonglong)]
 
 
 class Profile(C.Structure):

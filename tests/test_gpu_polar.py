@@ -75,6 +75,7 @@ def test_aalc_with_polar_meets_theta_on_every_tile():
         st, cs = run_pair(n, c, I.qft(n), "aalc", 1e-2, x=x, aalc=(theta, [1e-5, 1e-4, 1e-3, 1e-2]))
         got = same(st, cs)
         assert all(16 * (1 << c) / len(s) >= theta for s in got)
+        assert st.stats()["tiles_over_limit"] == 0           # every tile of every sweep met theta
         assert st.fidelity_qft(x) > 0.9999
 
 
