@@ -545,7 +545,7 @@ double or_units_to_double(uint64_t lo, uint64_t hi)
  * shorter than 16N; else RAW.
  */
 #define HDR 32
-enum { M_CONST = 0, M_PACKED = 1, M_RAW = 2, M_POLAR = 3 };
+enum { M_CONST = 0, M_PACKED = 1, M_RAW = 2, M_POLAR = 3, M_POLAR_B = 4 };
 /* modes of a section of per-group bit words (sign words, zero words) */
 enum { S_CLEAR = 0, S_SET = 1, S_EXC_CLEAR = 2, S_EXC_SET = 3, S_WORDS = 4 };
 #define MAG 0x7FFFFFFFFFFFFFFFull
@@ -669,7 +669,8 @@ size_t or_stream_cap(int c)
  */
 static size_t write_stream(const double *a, int c, int s, int level, const uint64_t *anchor, int allzero,
                            uint32_t **sw, uint32_t **zw, uint64_t **z, int **w, int **nnz,
-                           const int *smode, const int *zmode, int polar, uint64_t d1, uint8_t *out)
+                           const int *smode, const int *zmode, int polar, uint64_t d1,
+                           const uint32_t *basis, size_t nbasis, uint8_t *out)
 {
     uint64_t N = 1ull << c;
     int G = N >= 32 ? (int)(N / 32) : 1;
@@ -686,11 +687,11 @@ static size_t write_stream(const double *a, int c, int s, int level, const uint6
     for (int k = 0; k < 2; ++k)
         meta += section_bytes(smode[k], sw[k], G, lanes) + section_bytes(zmode[k], zw[k], G, lanes);
     size_t wbytes = round_up(meta + 2 * (size_t)G, 4) - meta;
-    size_t packed_body = round_up(meta + wbytes + 4 * data_words, 16);
+    size_t packed_body = round_up(meta + wbytes + 4 * (nbasis + data_words), 16);
 
     if (polar) {
         if (packed_body >= raw_body) return 0;
-        mode = M_POLAR;
+        mode = polar == 2 ? M_POLAR_B : M_POLAR;
         body = packed_body;
     } else if (allzero && smode[0] <= S_SET && smode[1] <= S_SET && zmode[0] <= S_SET && zmode[1] <= S_SET) {
         mode = M_CONST;
@@ -708,7 +709,7 @@ static size_t write_stream(const double *a, int c, int s, int level, const uint6
     out[1] = (uint8_t)(mode == M_RAW ? 0 : s);
     out[2] = (uint8_t)level;
     if (mode != M_RAW) out[3] = (uint8_t)(smode[0] | (smode[1] << 3));
-    if (mode == M_PACKED || mode == M_POLAR) out[25] = (uint8_t)(zmode[0] | (zmode[1] << 3));
+    if (mode == M_PACKED || mode == M_POLAR || mode == M_POLAR_B) out[25] = (uint8_t)(zmode[0] | (zmode[1] << 3));
     put32(out + 4, (uint32_t)body);
     if (mode != M_RAW) {
         put64(out + 8, anchor[0]);
@@ -721,13 +722,14 @@ static size_t write_stream(const double *a, int c, int s, int level, const uint6
     uint8_t *b = out + HDR;
     if (mode == M_RAW) {
         for (uint64_t i = 0; i < 2 * N; ++i) put64(b + 8 * i, dbits(a[i]));
-    } else if (mode == M_PACKED || mode == M_POLAR) {
+    } else if (mode == M_PACKED || mode == M_POLAR || mode == M_POLAR_B) {
         size_t off = 0;
         for (int k = 0; k < 2; ++k) off = write_section(b, off, smode[k], sw[k], G, lanes);
         for (int k = 0; k < 2; ++k) off = write_section(b, off, zmode[k], zw[k], G, lanes);
         for (int k = 0; k < 2; ++k)
             for (int g = 0; g < G; ++g) b[off++] = (uint8_t)w[k][g];
         off = round_up(off, 4);
+        for (size_t i = 0; i < nbasis; ++i, off += 4) put32(b + off, basis[i]);
         /* lane-major bit packing of the nonzero values: the k-th nonzero
          * value of a group occupies bits [k*w, (k+1)*w) of the group's
          * little-endian bit string */
@@ -809,7 +811,7 @@ static size_t encode_at(const double *a, int c, int s, int level, uint8_t *out)
         zmode[k] = word_mode(zw[k], G, lanes);
     }
 
-    size_t len = write_stream(a, c, s, level, anchor, allzero, sw, zw, z, w, nnz, smode, zmode, 0, 0, out);
+    size_t len = write_stream(a, c, s, level, anchor, allzero, sw, zw, z, w, nnz, smode, zmode, 0, 0, NULL, 0, out);
     for (int k = 0; k < 2; ++k) {
         free(q[k]); free(z[k]); free(sw[k]); free(zw[k]); free(w[k]); free(nnz[k]);
     }
@@ -825,7 +827,7 @@ static size_t encode_at(const double *a, int c, int s, int level, uint8_t *out)
  * phase instead of the two components).  At a lossy level of shift s
  * (8 <= s <= 52) every nonzero amplitude a = x + iy is coded as
  *   magnitude: m = sqrt(fma(x, x, y*y)) (IEEE, correctly rounded), code
- *     qm = quant(bits(m), s - 2), reconstructed m^ = bits(qm << (s - 2));
+ *     qm = quant(bits(m), s - 1), reconstructed m^ = bits(qm << (s - 1));
  *   phase: the angle of (x, y) in units of 2^-64 turn from the integer
  *     CORDIC below, code qa = round(angle / 2^P) mod 2^B with P = s + 8,
  *     B = 64 - P bits, reconstructed direction (X, Y) = CORDIC rotation of
@@ -841,12 +843,23 @@ static size_t encode_at(const double *a, int c, int s, int level, uint8_t *out)
  * from their anchor (header 8..15); phases by order-2 Lorenzo modulo 2^B
  * from u0 (header 16..23) and the first difference d1 (header 26..31):
  * residual r_j = u_j - 2 u_(j-1) + u_(j-2) for j >= 2 (0 for j < 2), as a
- * signed B-bit value, zigzagged.  A QFT's tiles (equal magnitudes, phases
- * linear in the index) code to residuals 0 or +-1.  Body: the PACKED
- * layout with clear sign sections and the zero words of both components
- * equal (a zero amplitude).
+ * signed B-bit value, zigzagged (mode 3).  A tile without zero amplitudes
+ * may instead take the bitwise-linear angle predictor (mode 4): with
+ * hp(i) the angle of amplitude i rounded to B + 8 bits (8 more than the
+ * code), hp(0) in header 16..23 and D_b = hp(2^b) - hp(0) mod 2^(B+8)
+ * for b < c (a basis section of ceil(c (B+8) / 32) words after the widths,
+ * D_b at bits [b (B+8), (b+1) (B+8))), the prediction of u_i is
+ * (hp(0) + sum of D_b over the set bits b of i) mod 2^(B+8), rounded to B
+ * bits, and the residual u_i - prediction is coded as above (header
+ * 26..31 zero).  A product state over the index bits (the QFT before its
+ * swaps, whose phases are sums of one phase per set bit) then costs
+ * residuals near 0, like a phase linear in the index.  The encoder codes a
+ * dense tile both ways and keeps the shorter (mode 3 on a tie).  Body: the
+ * PACKED layout with clear sign sections and the zero words of both
+ * components equal (a zero amplitude; mode 4 has none).
  */
 #define POLAR_ITERS 30
+#define POLAR_EXTRA 8                    /* extra angle bits of the bitwise-linear predictor */
 #define POLAR_MIN_EXP 623                /* |x| >= 2^-400: biased exponent >= 1023 - 400 */
 #define POLAR_MAX_EXP 1027               /* |x| < 16 */
 
@@ -949,7 +962,7 @@ static void polar_dir(uint64_t th, int64_t *px, int64_t *py)
 static void polar_recon(uint64_t qm, uint64_t qa, int s, double *re, double *im)
 {
     int P = s + 8;
-    double m = bitsd(qm << (s - 2));
+    double m = bitsd(qm << (s - 1));
     int64_t X, Y;
     polar_dir(qa << P, &X, &Y);
     double xd = (double)X, yd = (double)Y;
@@ -970,9 +983,24 @@ static int polar_comp_ok(double x)
     return (dbits(x) & MAG) == 0 || (e >= POLAR_MIN_EXP && e < POLAR_MAX_EXP);
 }
 
+/* Residual words of a code stream: zigzag z per value, group widths and
+ * nonzero counts for the PACKED layout. */
+static void code_widths(uint64_t *const *z, uint32_t *const *zw, int G, int L, uint32_t lanes, int **w, int **nnz)
+{
+    for (int k = 0; k < 2; ++k)
+        for (int g = 0; g < G; ++g) {
+            uint64_t o = 0;
+            for (int l = 0; l < L; ++l) o |= z[k][(uint64_t)g * 32 + l];
+            w[k][g] = bitlen64(o);
+            nnz[k][g] = popcount32(~zw[k][g] & lanes);
+        }
+}
+
 /* POLAR stream of a tile at shift s as ladder level `level`, or 0 when the
  * tile cannot use the mode (a value out of range or over the bound, or a
- * body not shorter than RAW). */
+ * body not shorter than RAW).  A tile without zero amplitudes is coded
+ * with both angle predictors, order 2 (mode 3) and bitwise linear (mode
+ * 4), and keeps the shorter (mode 3 on a tie). */
 static size_t encode_polar_at(const double *a, int c, int s, int level, uint8_t *out)
 {
     if (s < 8 || s > 52) return 0;
@@ -981,28 +1009,30 @@ static size_t encode_polar_at(const double *a, int c, int s, int level, uint8_t 
     int G = N >= 32 ? (int)(N / 32) : 1;
     int L = N >= 32 ? 32 : (int)N;
     uint32_t lanes = L == 32 ? 0xFFFFFFFFu : ((1u << L) - 1);
-    int P = s + 8, B = 64 - P;
-    uint64_t bmask = (1ull << B) - 1, half = 1ull << (B - 1);
+    int P = s + 8, B = 64 - P, BE = B + POLAR_EXTRA;
+    uint64_t bmask = (1ull << B) - 1, half = 1ull << (B - 1), emask = (1ull << BE) - 1;
     double lim = ldexp(1.0 - ldexp(1.0, -10), 2 * (s - 53));
-    uint64_t *qm = calloc(N, 8), *qa = calloc(N, 8);
-    uint64_t *z[2] = {calloc(N, 8), calloc(N, 8)};
+    uint64_t *qm = calloc(N, 8), *qa = calloc(N, 8), *hp = calloc(N, 8);
+    uint64_t *z[2] = {calloc(N, 8), calloc(N, 8)}, *zb = calloc(N, 8);
     uint32_t *sw[2] = {calloc((size_t)G, 4), calloc((size_t)G, 4)};
     uint32_t *zw[2] = {calloc((size_t)G, 4), calloc((size_t)G, 4)};
     int *w[2] = {calloc((size_t)G, sizeof(int)), calloc((size_t)G, sizeof(int))};
     int *nnz[2] = {calloc((size_t)G, sizeof(int)), calloc((size_t)G, sizeof(int))};
-    int ok = 1;
+    int ok = 1, dense = 1;
     for (uint64_t i = 0; i < N && ok; ++i) {
         double x = a[2 * i], y = a[2 * i + 1];
         if (!polar_comp_ok(x) || !polar_comp_ok(y)) { ok = 0; break; }
         if ((dbits(x) & MAG) == 0 && (dbits(y) & MAG) == 0) {
             zw[0][i / 32] |= 1u << (i % 32);
             zw[1][i / 32] |= 1u << (i % 32);
+            dense = 0;
             continue;
         }
         double m = sqrt(fma(x, x, y * y));
-        qm[i] = quant(dbits(m), s - 2);
+        qm[i] = quant(dbits(m), s - 1);
         uint64_t th = or_polar_angle(x, y);
         qa[i] = ((th + (1ull << (P - 1))) >> P) & bmask;
+        hp[i] = ((th + (1ull << (P - POLAR_EXTRA - 1))) >> (P - POLAR_EXTRA)) & emask;
         double xr, xi;
         polar_recon(qm[i], qa[i], s, &xr, &xi);
         double dr = xr - x, di = xi - y;
@@ -1029,18 +1059,47 @@ static size_t encode_polar_at(const double *a, int c, int s, int level, uint8_t 
             ++j;
         }
         int smode[2] = {S_CLEAR, S_CLEAR}, zmode[2];
-        for (int k = 0; k < 2; ++k) {
-            for (int g = 0; g < G; ++g) {
-                uint64_t o = 0;
-                for (int l = 0; l < L; ++l) o |= z[k][(uint64_t)g * 32 + l];
-                w[k][g] = bitlen64(o);
-                nnz[k][g] = popcount32(~zw[k][g] & lanes);
+        code_widths(z, zw, G, L, lanes, w, nnz);
+        for (int k = 0; k < 2; ++k) zmode[k] = word_mode(zw[k], G, lanes);
+        len = write_stream(a, c, s, level, anchor, 0, sw, zw, z, w, nnz, smode, zmode, 1, d1, NULL, 0, out);
+        if (dense) {
+            /* bitwise linear: the angle of index i predicted from hp(0) and
+             * the differences D_b = hp(2^b) - hp(0) of its set bits, at
+             * POLAR_EXTRA more bits, then rounded to the code */
+            uint64_t D[16];
+            size_t nb = ((size_t)c * BE + 31) / 32;
+            uint32_t basis[32];
+            memset(basis, 0, sizeof basis);
+            for (int b = 0; b < c; ++b) {
+                D[b] = (hp[1ull << b] - hp[0]) & emask;
+                for (int bit = 0; bit < BE; ++bit)
+                    if ((D[b] >> bit) & 1) {
+                        size_t pos = (size_t)b * BE + bit;
+                        basis[pos / 32] |= 1u << (pos % 32);
+                    }
             }
-            zmode[k] = word_mode(zw[k], G, lanes);
+            for (uint64_t i = 0; i < N; ++i) {
+                uint64_t p = hp[0];
+                for (int b = 0; b < c; ++b)
+                    if ((i >> b) & 1) p += D[b];
+                uint64_t pred = (((p + (1ull << (POLAR_EXTRA - 1))) & emask) >> POLAR_EXTRA) & bmask;
+                uint64_t ra = (qa[i] - pred) & bmask;
+                int64_t rs = (int64_t)((ra ^ half) - half);
+                zb[i] = ((uint64_t)rs << 1) ^ (uint64_t)(rs >> 63);
+            }
+            uint64_t *zz[2] = {z[0], zb};
+            code_widths(zz, zw, G, L, lanes, w, nnz);
+            uint64_t anb[2] = {anchor[0], hp[0]};
+            uint8_t *tmp = malloc(or_stream_cap(c) + 256);
+            size_t lb = write_stream(a, c, s, level, anb, 0, sw, zw, zz, w, nnz, smode, zmode, 2, 0, basis, nb, tmp);
+            if (lb && (!len || lb < len)) {
+                memcpy(out, tmp, lb);
+                len = lb;
+            }
+            free(tmp);
         }
-        len = write_stream(a, c, s, level, anchor, 0, sw, zw, z, w, nnz, smode, zmode, 1, d1, out);
     }
-    free(qm); free(qa);
+    free(qm); free(qa); free(hp); free(zb);
     for (int k = 0; k < 2; ++k) { free(z[k]); free(sw[k]); free(zw[k]); free(w[k]); free(nnz[k]); }
     return len;
 }
@@ -1222,8 +1281,9 @@ int or_decode_tile(const uint8_t *in, size_t len, int c, double *a)
         }
         return 0;
     }
-    if (mode != M_PACKED && mode != M_POLAR) return -7;
-    if (mode == M_POLAR && (s < 8 || sm[0] != S_CLEAR || sm[1] != S_CLEAR)) return -7;
+    if (mode != M_PACKED && mode != M_POLAR && mode != M_POLAR_B) return -7;
+    if ((mode == M_POLAR || mode == M_POLAR_B) && (s < 8 || sm[0] != S_CLEAR || sm[1] != S_CLEAR)) return -7;
+    if (mode == M_POLAR_B && (zm[0] != S_CLEAR || zm[1] != S_CLEAR)) return -7;    /* no zero amplitude */
     size_t off = 0;
     uint32_t *sw[2], *zw[2];
     for (int k = 0; k < 2; ++k) { sw[k] = calloc((size_t)G, 4); zw[k] = calloc((size_t)G, 4); }
@@ -1271,9 +1331,24 @@ int or_decode_tile(const uint8_t *in, size_t len, int c, double *a)
         for (int g = 0; g < G; ++g)
             if (zw[0][g] != zw[1][g]) rc = -12;     /* a zero amplitude is zero in both codes */
     }
+    /* POLAR_B: the basis differences D_b (BE bits each) after the widths */
+    uint64_t D[16];
+    if (rc == 0 && mode == M_POLAR_B) {
+        int BE = 56 - s + POLAR_EXTRA;
+        size_t nb = ((size_t)c * BE + 31) / 32;
+        if (off + 4 * nb > body) rc = -13;
+        for (int bb = 0; bb < c && rc == 0; ++bb) {
+            D[bb] = 0;
+            for (int bit = 0; bit < BE; ++bit) {
+                size_t pos = (size_t)bb * BE + bit;
+                D[bb] |= (uint64_t)((get32(b + off + 4 * (pos / 32)) >> (pos % 32)) & 1) << bit;
+            }
+        }
+        off += 4 * nb;
+    }
     /* POLAR: the residuals of the two code streams, kept for the
      * reconstruction below */
-    uint64_t *pz = mode == M_POLAR ? calloc(2 * N, 8) : NULL;
+    uint64_t *pz = (mode == M_POLAR || mode == M_POLAR_B) ? calloc(2 * N, 8) : NULL;
     for (int k = 0; k < 2 && rc == 0; ++k) {
         uint64_t q = anchor[k];
         for (int g = 0; g < G && rc == 0; ++g) {
@@ -1306,8 +1381,8 @@ int or_decode_tile(const uint8_t *in, size_t len, int c, double *a)
         /* magnitudes: running sum from the anchor; phases: second-order
          * running sums modulo 2^B from u0 and d1 */
         pthread_once(&polar_once, polar_init);
-        int B = 56 - s;
-        uint64_t bmask = (1ull << B) - 1, d1 = 0;
+        int B = 56 - s, BE = B + POLAR_EXTRA;
+        uint64_t bmask = (1ull << B) - 1, emask = (1ull << BE) - 1, d1 = 0;
         for (int i = 0; i < 6; ++i) d1 |= (uint64_t)in[26 + i] << (8 * i);
         uint64_t qm = anchor[0], u = anchor[1] & bmask, d = d1 & bmask;
         uint64_t j = 0;
@@ -1316,7 +1391,12 @@ int or_decode_tile(const uint8_t *in, size_t len, int c, double *a)
             uint64_t vm = pz[2 * i], va = pz[2 * i + 1];
             qm += (vm >> 1) ^ (0 - (vm & 1));
             uint64_t ra = ((va >> 1) ^ (0 - (va & 1))) & bmask;
-            if (j == 1) u = (u + d) & bmask;
+            if (mode == M_POLAR_B) {
+                uint64_t p = anchor[1];
+                for (int bb = 0; bb < c; ++bb)
+                    if ((i >> bb) & 1) p += D[bb];
+                u = ((((p + (1ull << (POLAR_EXTRA - 1))) & emask) >> POLAR_EXTRA) + ra) & bmask;
+            } else if (j == 1) u = (u + d) & bmask;
             else if (j >= 2) { d = (d + ra) & bmask; u = (u + d) & bmask; }
             ++j;
             polar_recon(qm, u, s, &a[2 * i], &a[2 * i + 1]);

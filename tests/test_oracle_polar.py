@@ -15,6 +15,11 @@ phase instead of the two components).
   tiles) code to at least 30 times smaller streams; the mode is kept only
   when shorter than the componentwise stream; tiles it cannot serve (a
   component below 2^-400, shifts below 8, the lossless level) never use it.
+* The bitwise-linear angle predictor (mode 4: a dense tile's angles from
+  the angle at index 0 and one difference per index bit) gives a product
+  state over the index bits zero residuals up to rounding: such a tile
+  codes about as small as a linear one, and far smaller than with the
+  order-2 predictor alone.
 * The compressed QFT with the variant on keeps the paper's fidelity.
 """
 import decimal
@@ -101,7 +106,7 @@ def test_polar_streams_meet_the_bound(s):
             a = np.abs(a).max() * np.exp(2j * np.pi * (0.01 * k + 0.3)) * (np.abs(a) > 0)
         st, _, _ = oracle.encode_tile(a, c, [s], polar=True)
         dec = oracle.decode_tile(st, c)
-        if st[0] == 3:
+        if st[0] in (3, 4):
             used += 1
             assert exact_within(dec, a, s)
         st0, _, _ = oracle.encode_tile(a, c, [s])
@@ -118,16 +123,16 @@ def test_linear_phase_tiles_code_small_and_ineligible_tiles_do_not_use_polar():
         for eps in (1e-3, 1e-4, 1e-5):
             s = oracle.shift_for_eps(eps)
             st, _, _ = oracle.encode_tile(a, c, [s], polar=True)
-            assert st[0] == 3 and 16 * (1 << c) / len(st) >= 30
+            assert st[0] in (3, 4) and 16 * (1 << c) / len(st) >= 30
             assert exact_within(oracle.decode_tile(st, c), a, s)
     a = np.exp(2j * np.pi * 5 * k / 2 ** 20) / 16
     a[4] = 2.0 ** -420 + 0j                                    # below 2^-400: the mode cannot serve it
     st, _, _ = oracle.encode_tile(a, c, [39], polar=True)
-    assert st[0] != 3
+    assert st[0] not in (3, 4)
     b = np.exp(2j * np.pi * 5 * k / 2 ** 20) / 16
     for s in (0, 4, 7):
         st, _, _ = oracle.encode_tile(b, c, [s], polar=True)
-        assert st[0] != 3
+        assert st[0] not in (3, 4)
 
 
 def test_compressed_qft_with_polar_keeps_fidelity_and_shrinks():
@@ -145,3 +150,22 @@ def test_compressed_qft_with_polar_keeps_fidelity_and_shrinks():
         assert F >= 0.9999
         sizes[polar] = cs.nbytes()
     assert sizes[True] * 4 < sizes[False]
+
+
+def test_bitwise_linear_phases_use_the_bitwise_predictor():
+    # phases sum_b phi_b k_b with unrelated phi_b (a product state over the
+    # index bits, the QFT before its swaps): mode 4, small, within the bound
+    c = 8
+    rng = np.random.default_rng(41)
+    phi = rng.uniform(0, 2 * np.pi, c)
+    k = np.arange(1 << c)
+    bits = (k[:, None] >> np.arange(c)) & 1
+    a = np.exp(1j * (bits @ phi)) / 2 ** 10
+    for eps in (1e-2, 1e-4, 1e-5):
+        s = oracle.shift_for_eps(eps)
+        st, _, _ = oracle.encode_tile(a, c, [s], polar=True)
+        assert st[0] == 4 and 16 * (1 << c) / len(st) >= 25, (eps, len(st))
+        assert exact_within(oracle.decode_tile(st, c), a, s)
+    a[17] = 0.0                                                # a zero amplitude: order 2 only
+    st, _, _ = oracle.encode_tile(a, c, [oracle.shift_for_eps(1e-4)], polar=True)
+    assert st[0] == 3
