@@ -24,7 +24,8 @@ constexpr unsigned long long INF_BITS = 0x7FF0000000000000ull;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr unsigned long long SIGN_BIT = 0x8000000000000000ull;
 
-enum { M_CONST = 0, M_PACKED = 1, M_RAW = 2, M_POLAR = 3 };
+enum { M_CONST = 0, M_PACKED = 1, M_RAW = 2, M_POLAR = 3, M_POLAR_B = 4 };
+constexpr int POLAR_EXTRA = 8;          // extra angle bits of the bitwise-linear predictor
 enum { S_CLEAR = 0, S_SET = 1, S_EXC_CLEAR = 2, S_EXC_SET = 3, S_WORDS = 4 };
 
 __device__ __forceinline__ Acc4 make_acc4(double x, double y, double z, double w) {
@@ -915,7 +916,7 @@ __device__ __noinline__ void polar_recon(unsigned long long qm, unsigned long lo
         if (zz >= 0) { X -= dx; Y += dy; zz -= (long long)c_polar_atan[k]; }
         else { X += dx; Y -= dy; zz += (long long)c_polar_atan[k]; }
     }
-    const double m = bitsd(qm << (s - 2));
+    const double m = bitsd(qm << (s - 1));
     const double xd = __ll2double_rn(X), yd = __ll2double_rn(Y);
     const double r = __ddiv_rn(1.0, __dsqrt_rn(__fma_rn(xd, xd, __dmul_rn(yd, yd))));
     re = __dmul_rn(m, __dmul_rn(xd, r));
@@ -931,17 +932,19 @@ __device__ __forceinline__ bool polar_comp_ok(double x) {
 // Codes of one amplitude at shift s; false when the amplitude rules the
 // mode out.  nz: the amplitude is not zero.
 __device__ __forceinline__ bool polar_codes(double x, double y, int s, bool &nz, unsigned long long &qm,
-                                            unsigned long long &qa, double &xr, double &xi) {
+                                            unsigned long long &qa, unsigned long long &th, double &xr,
+                                            double &xi) {
     nz = false;
-    qm = qa = 0ull;
+    qm = qa = th = 0ull;
     xr = xi = 0.0;
     if (!polar_comp_ok(x) || !polar_comp_ok(y)) return false;
     if ((dbits(x) & MAG) == 0ull && (dbits(y) & MAG) == 0ull) return true;
     nz = true;
     const int P = s + 8, B = 64 - P;
     const double mm = __fma_rn(x, x, __dmul_rn(y, y));
-    qm = quant(dbits(__dsqrt_rn(mm)), s - 2);
-    qa = ((polar_angle(x, y) + (1ull << (P - 1))) >> P) & ((1ull << B) - 1ull);
+    qm = quant(dbits(__dsqrt_rn(mm)), s - 1);
+    th = polar_angle(x, y);
+    qa = ((th + (1ull << (P - 1))) >> P) & ((1ull << B) - 1ull);
     polar_recon(qm, qa, s, xr, xi);
     const double dr = __dsub_rn(xr, x), di = __dsub_rn(xi, y);
     const double lim = ldexp(1.0 - 0x1p-10, 2 * (s - 53));
@@ -949,39 +952,84 @@ __device__ __forceinline__ bool polar_codes(double x, double y, int s, bool &nz,
 }
 
 // Sizing (WRITE false) or packing (WRITE true) pass of the POLAR mode over
-// a tile at shift s.  Sizing: ok (every amplitude codable), the anchors
-// am / au, the first angle difference d1, and in lane g the zero word and
-// the two residual widths of group g.  Packing: writes the residuals of
-// group g at data + o0 (magnitudes) and data + o1 (angles), the word
-// offsets held in lane g, and adds the reconstructed values' norm.
+// a tile at shift s.  Sizing: ok (every amplitude codable), dense (no zero
+// amplitude), the anchors am / au, the first angle difference d1, hp0 and
+// the basis differences D_b of the bitwise-linear predictor (lane b holds
+// D_b for b < 5 in dl, lane b - 5 holds D_b for b >= 5 in dh), and in lane
+// g the zero word and the residual widths of group g (w0 magnitudes, w1
+// angles by order 2, w1b angles bitwise).  Packing: writes the residuals
+// of group g at data + o0 (magnitudes) and data + o1 (angles of the
+// predictor `bitwise`), the word offsets held in lane g, and adds the
+// reconstructed values' norm.
 struct PolarInfo {
-    unsigned long long am, au, d1;
-    uint32_t zw, w0, w1;
-    bool ok;
+    unsigned long long am, au, d1, hp0, dl, dh;
+    uint32_t zw, w0, w1, w1b;
+    bool ok, dense;
 };
 
 template <bool WRITE>
-__device__ __noinline__ void polar_pass(const double *re, const double *im, int s, int G, int L, PolarInfo &pi,
-                                        uint32_t *data, uint32_t o0, uint32_t o1, uint32_t *wstage,
-                                        unsigned long long &nlo, unsigned long long &nhi, unsigned &rng) {
+__device__ __noinline__ void polar_pass(const double *re, const double *im, int s, int c, int G, int L,
+                                        PolarInfo &pi, bool bitwise, uint32_t *data, uint32_t o0, uint32_t o1,
+                                        uint32_t *wstage, unsigned long long &nlo, unsigned long long &nhi,
+                                        unsigned &rng) {
     const int lane = threadIdx.x & 31;
     const uint32_t below = lanes_below();
     const uint32_t lanes = L == 32 ? FULL : ((1u << L) - 1u);
-    const int B = 56 - s;
-    const unsigned long long bmask = (1ull << B) - 1ull, half = 1ull << (B - 1);
+    const int B = 56 - s, P = s + 8, BE = B + POLAR_EXTRA;
+    const unsigned long long bmask = (1ull << B) - 1ull, half = 1ull << (B - 1), emask = (1ull << BE) - 1ull;
     unsigned long long lastm = 0, last1 = 0, last2 = 0;
     uint32_t seen = 0;
-    if (!WRITE) { pi.am = pi.au = pi.d1 = 0; pi.zw = pi.w0 = pi.w1 = 0; pi.ok = true; }
+    unsigned long long lowsum = 0;                   // this lane's sum of D_b over its lane bits
+    if (!WRITE) {
+        pi.am = pi.au = pi.d1 = pi.hp0 = pi.dl = pi.dh = 0;
+        pi.zw = pi.w0 = pi.w1 = pi.w1b = 0;
+        pi.ok = true;
+        pi.dense = true;
+    }
     for (int g = 0; g < G; ++g) {
         const int i = g * 32 + lane;
         const double x = lane < L ? re[i] : 0.0, y = lane < L ? im[i] : 0.0;
         bool nz;
-        unsigned long long qm, qa;
+        unsigned long long qm, qa, th = 0;
         double xr, xi;
-        const bool okv = lane < L ? polar_codes(x, y, s, nz, qm, qa, xr, xi) : (nz = false, qm = qa = 0, xr = xi = 0.0, true);
+        const bool okv = lane < L ? polar_codes(x, y, s, nz, qm, qa, th, xr, xi)
+                                  : (nz = false, qm = qa = 0, xr = xi = 0.0, true);
         if (!WRITE && !__all_sync(FULL, okv)) { pi.ok = false; return; }
         const uint32_t nzm = __ballot_sync(FULL, nz);
-        if (!WRITE && lane == g) pi.zw = ~nzm & lanes;
+        if (!WRITE) {
+            if (lane == g) pi.zw = ~nzm & lanes;
+            if (nzm != lanes) pi.dense = false;
+        }
+        // the bitwise-linear predictor's angle at B + 8 bits and its basis
+        const unsigned long long hp = ((th + (1ull << (P - POLAR_EXTRA - 1))) >> (P - POLAR_EXTRA)) & emask;
+        if (!WRITE) {
+            if (g == 0) {
+                pi.hp0 = shfl64(hp, 0);
+                const unsigned long long hb = shfl64(hp, (1 << (lane & 7)) & 31);    // lane b < 5: hp(2^b)
+                if (lane < 5 && lane < c) pi.dl = (hb - pi.hp0) & emask;
+            }
+            if (g > 0 && (g & (g - 1)) == 0) {       // group 2^(b-5): lane 0 is index 2^b
+                const int b = 5 + (31 - __clz(g));
+                const unsigned long long v = (shfl64(hp, 0) - pi.hp0) & emask;
+                if (lane == b - 5) pi.dh = v;
+            }
+        }
+        if (g == 0) {
+            lowsum = 0;
+            for (int b = 0; b < 5 && b < c; ++b) {
+                const unsigned long long db = shfl64(pi.dl, b);
+                if ((lane >> b) & 1) lowsum += db;
+            }
+        }
+        unsigned long long gsum = 0;                 // sum of D_b over the set bits of g
+        for (int b = 5; b < c; ++b) {
+            const unsigned long long db = shfl64(pi.dh, b - 5);
+            if ((g >> (b - 5)) & 1) gsum += db;
+        }
+        const unsigned long long pp = (pi.hp0 + lowsum + gsum + (1ull << (POLAR_EXTRA - 1))) & emask;
+        const unsigned long long rb = (qa - (pp >> POLAR_EXTRA)) & bmask;
+        const long long rbs = (long long)((rb ^ half) - half);
+        const unsigned long long zb = nz ? (((unsigned long long)rbs << 1) ^ (unsigned long long)(rbs >> 63)) : 0ull;
         if (nzm == 0u) continue;
         const uint32_t pm = nzm & below;
         const int p1 = pm ? 31 - __clz(pm) : lane;
@@ -1007,7 +1055,8 @@ __device__ __noinline__ void polar_pass(const double *re, const double *im, int 
                 pi.d1 = (u1 - (seen == 1u ? last1 : shfl64(qa, f0))) & bmask;
             }
             const uint32_t w0 = (uint32_t)bitlen64(warp_or64(zm)), w1 = (uint32_t)bitlen64(warp_or64(za));
-            if (lane == g) { pi.w0 = w0; pi.w1 = w1; }
+            const uint32_t w1b = (uint32_t)bitlen64(warp_or64(zb));
+            if (lane == g) { pi.w0 = w0; pi.w1 = w1; pi.w1b = w1b; }
         } else {
             if (nzl) {
                 unsigned long long l0, h0, l1v, h1v;
@@ -1017,11 +1066,11 @@ __device__ __noinline__ void polar_pass(const double *re, const double *im, int 
                 add128(nlo, nhi, l0, h0);
             }
             for (int k = 0; k < 2; ++k) {
-                const uint32_t w = __shfl_sync(FULL, k ? pi.w1 : pi.w0, g);
+                const uint32_t w = __shfl_sync(FULL, k ? (bitwise ? pi.w1b : pi.w1) : pi.w0, g);
                 if (w == 0) continue;
                 const uint32_t wo = __shfl_sync(FULL, k ? o1 : o0, g);
                 const uint32_t nwd = (cnt * w + 31u) >> 5;
-                const unsigned long long z = k ? za : zm;
+                const unsigned long long z = k ? (bitwise ? zb : za) : zm;
                 wstage[lane] = 0u;
                 wstage[lane + 32] = 0u;
                 __syncwarp();
@@ -1048,14 +1097,50 @@ __device__ __noinline__ void polar_pass(const double *re, const double *im, int 
     }
 }
 
-// Body bytes of a POLAR stream from its sizing pass (warp-uniform).
-__device__ __forceinline__ uint32_t polar_body(const PolarInfo &pi, int G, uint32_t lanes, int &zmode) {
+// Words of the bitwise predictor's basis section: c differences of B + 8 bits.
+__device__ __forceinline__ uint32_t polar_basis_words(int c, int s) {
+    return ((uint32_t)c * (uint32_t)(56 - s + POLAR_EXTRA) + 31u) >> 5;
+}
+
+// Write the basis section (D_b at bits [b (B+8), (b+1) (B+8))) at sec.
+__device__ void polar_write_basis(const PolarInfo &pi, int c, int s, uint32_t *sec, uint32_t *wstage) {
+    const int lane = threadIdx.x & 31;
+    const int BE = 56 - s + POLAR_EXTRA;
+    const uint32_t nb = polar_basis_words(c, s);
+    const unsigned long long dhs = shfl64(pi.dh, (lane - 5) & 31);
+    const unsigned long long d = lane < 5 ? pi.dl : dhs;
+    wstage[lane] = 0u;
+    __syncwarp();
+    if (lane < c) {
+        const uint32_t bo = (uint32_t)lane * (uint32_t)BE, j0 = bo >> 5, sh = bo & 31u;
+        atomicOr(&wstage[j0], (uint32_t)(d << sh));
+        if (sh + BE > 32) atomicOr(&wstage[j0 + 1], (uint32_t)(d >> (32 - sh)));
+        if (sh + BE > 64) atomicOr(&wstage[j0 + 2], (uint32_t)(d >> (64 - sh)));
+    }
+    __syncwarp();
+    if ((uint32_t)lane < nb) sec[lane] = wstage[lane];
+    __syncwarp();
+}
+
+// Body bytes of a POLAR stream from its sizing pass (warp-uniform): the
+// order-2 stream, and when the tile is dense the bitwise stream if shorter
+// (*bitwise set).
+__device__ __forceinline__ uint32_t polar_body(const PolarInfo &pi, int c, int s, int G, uint32_t lanes, int &zmode,
+                                               bool &bitwise) {
     const int lane = threadIdx.x & 31;
     uint32_t zb;
     zmode = section_mode(pi.zw, G, lanes, zb);
     const uint32_t nn = lane < G ? (uint32_t)__popc(~pi.zw & lanes) : 0u;
-    const uint32_t words = __reduce_add_sync(FULL, ((nn * pi.w0 + 31u) >> 5) + ((nn * pi.w1 + 31u) >> 5));
-    return (2u * zb + ((2u * (uint32_t)G + 3u) & ~3u) + 4u * words + 15u) & ~15u;
+    const uint32_t wm = __reduce_add_sync(FULL, (nn * pi.w0 + 31u) >> 5);
+    const uint32_t w2 = __reduce_add_sync(FULL, (nn * pi.w1 + 31u) >> 5);
+    const uint32_t wbw = __reduce_add_sync(FULL, (nn * pi.w1b + 31u) >> 5);
+    const uint32_t head = 2u * zb + ((2u * (uint32_t)G + 3u) & ~3u);
+    const uint32_t b2 = (head + 4u * (wm + w2) + 15u) & ~15u;
+    bitwise = false;
+    if (!pi.dense) return b2;
+    const uint32_t bb = (head + 4u * (polar_basis_words(c, s) + wm + wbw) + 15u) & ~15u;
+    if (bb < b2) { bitwise = true; return bb; }
+    return b2;
 }
 
 // Decode one stream into planar re/im (2^c values each), multiplied by
@@ -1079,9 +1164,10 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
     const int zm0 = (h6 >> 8) & 7, zm1 = (h6 >> 11) & 7;
     const uint8_t *b = src + HDR;
     const uint32_t *b32 = reinterpret_cast<const uint32_t *>(b);
-    const bool polar = mode == M_POLAR;
-    bool bad = hc != c || mode > 3 || (mode != M_RAW && s > 52) || (body & 15u);
+    const bool polar = mode == M_POLAR || mode == M_POLAR_B, pbit = mode == M_POLAR_B;
+    bool bad = hc != c || mode > 4 || (mode != M_RAW && s > 52) || (body & 15u);
     if (!bad && polar) bad = s < 8 || sm0 != S_CLEAR || sm1 != S_CLEAR;
+    if (!bad && pbit) bad = zm0 != S_CLEAR || zm1 != S_CLEAR;             // no zero amplitude
     if (!bad && mode == M_RAW) bad = body != 16u * (uint32_t)N;
     if (!bad && mode == M_CONST) bad = body != 0 || sm0 > 1 || sm1 > 1 || ((h6 >> 8) & 0xFFu);
     if (!bad && mode == M_CONST) {
@@ -1102,7 +1188,7 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
         return 0;
     }
     const uint32_t lanes = L == 32 ? FULL : ((1u << L) - 1u);
-    uint32_t sw0 = 0, sw1 = 0, zw0 = 0, zw1 = 0, w0 = 0, w1 = 0, doff = 0, off0 = 0, off1 = 0;
+    uint32_t sw0 = 0, sw1 = 0, zw0 = 0, zw1 = 0, w0 = 0, w1 = 0, doff = 0, off0 = 0, off1 = 0, boff = 0;
     if (!bad) {
         const uint32_t mw = 4u * (uint32_t)lane < body ? __ldg(b32 + lane) : 0u;
         uint32_t off = 0;
@@ -1124,6 +1210,11 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
             off0 = warp_exscan(((uint32_t)__popc(~zw0 & lanes) * w0 + 31u) >> 5, tot0);
             off1 = warp_exscan(((uint32_t)__popc(~zw1 & lanes) * w1 + 31u) >> 5, tot1) + tot0;
             doff = (off + 2u * G + 3u) & ~3u;
+            if (pbit) {
+                // the basis section precedes the residual words
+                boff = doff;
+                doff += 4u * polar_basis_words(c, s);
+            }
             const uint32_t wmax = __reduce_max_sync(FULL, max(w0, w1));
             bad = wmax > 64 || (unsigned long long)doff + 4ull * (tot0 + tot1) > body;
             // POLAR: a zero amplitude is zero in both code streams
@@ -1166,13 +1257,33 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
     meta(0, w, wo, sgw, nzw);
     fetch(w, wo, nzw, x0, x1, x2, sh);
     unsigned long long carry = a0;
-    // POLAR: magnitudes (component 0) are the codes with shift s - 2, kept
+    // POLAR: magnitudes (component 0) are the codes with shift s - 1, kept
     // unscaled in re until the angles (component 1) reconstruct the values
-    const int sv = polar ? s - 2 : s;
+    const int sv = polar ? s - 1 : s;
     const unsigned long long bmask = polar ? (1ull << (56 - s)) - 1ull : 0ull;
     const unsigned long long d1 = ((unsigned long long)h7 << 16) | (h6 >> 16);
     unsigned long long cu = 0, cd = 0;                       // angle carries: last code, last difference
     uint32_t seen = 0;                                       // nonzero amplitudes before this group
+    // bitwise-linear predictor: lane b < c holds D_b; lowsum = sum of D_b
+    // over this lane's set bits (b < 5)
+    unsigned long long dbase = 0, lowsum = 0;
+    const int BE = 56 - s + POLAR_EXTRA;
+    const unsigned long long emask = pbit ? (1ull << BE) - 1ull : 0ull;
+    if (pbit) {
+        const uint32_t bo = (uint32_t)lane * (uint32_t)BE, j0 = bo >> 5, shb = bo & 31u;
+        const uint32_t *bw = reinterpret_cast<const uint32_t *>(b + boff);
+        const uint32_t nb = polar_basis_words(c, s);
+        if (lane < c) {
+            const unsigned long long lo = (unsigned long long)__ldg(bw + j0) |
+                                          (j0 + 1 < nb ? (unsigned long long)__ldg(bw + j0 + 1) << 32 : 0ull);
+            const unsigned long long hi = j0 + 2 < nb ? (unsigned long long)__ldg(bw + j0 + 2) : 0ull;
+            dbase = ((lo >> shb) | (shb ? hi << (64 - shb) : 0ull)) & emask;
+        }
+        for (int bb = 0; bb < 5 && bb < c; ++bb) {
+            const unsigned long long db = shfl64(dbase, bb);
+            if ((lane >> bb) & 1) lowsum += db;
+        }
+    }
     for (int t = 0; t < T; ++t) {
         uint32_t wn = 0, won = 0, sgwn = 0, nzwn = 0, y0 = 0, y1 = 0, y2 = 0, shn = 0;
         if (t + 1 < T) {                                     // next group's words, in flight meanwhile
@@ -1192,6 +1303,34 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
                 double x = bitsd((unsigned long long)((sgw >> lane) & 1u) << 63);
                 if (scale && !polar) x = __dmul_rn(x, alpha);
                 v[g * 32 + lane] = x;
+            }
+        } else if (pbit && k) {
+            // angles: the bitwise-linear prediction plus the residual
+            unsigned long long z = 0;
+            if (w) {
+                if (w <= 32) {
+                    const uint32_t z32 = __funnelshift_r(x0, x1, sh);
+                    z = w == 32 ? z32 : (z32 & ((1u << w) - 1u));
+                } else {
+                    const unsigned long long lo = (unsigned long long)x0 | ((unsigned long long)x1 << 32);
+                    const unsigned long long vv = sh ? ((lo >> sh) | ((unsigned long long)x2 << (64 - sh))) : lo;
+                    z = w == 64 ? vv : (vv & ((1ull << w) - 1ull));
+                }
+            }
+            unsigned long long gsum = 0;
+            for (int bb = 5; bb < c; ++bb) {
+                const unsigned long long db = shfl64(dbase, bb);
+                if ((g >> (bb - 5)) & 1) gsum += db;
+            }
+            if (lane < L) {
+                const unsigned long long pp = (a1 + lowsum + gsum + (1ull << (POLAR_EXTRA - 1))) & emask;
+                const unsigned long long u = ((pp >> POLAR_EXTRA) + unzigzag(z)) & bmask;
+                const unsigned long long qm = dbits(re[g * 32 + lane]) >> sv;
+                double ar, ai;
+                polar_recon(qm, u, s, ar, ai);
+                if (scale) { ar = __dmul_rn(ar, alpha); ai = __dmul_rn(ai, alpha); }
+                re[g * 32 + lane] = ar;
+                im[g * 32 + lane] = ai;
             }
         } else if (polar && k) {
             // angles: second-order running sums modulo 2^B, the first two
@@ -1582,10 +1721,11 @@ __device__ __noinline__ void wsize(const double *re, const double *im, const Cod
                 unsigned long long d0 = 0, d1 = 0;
                 unsigned dr = 0;
                 PolarInfo pi;
-                polar_pass<false>(re, im, slv, G, L, pi, nullptr, 0u, 0u, nullptr, d0, d1, dr);
+                polar_pass<false>(re, im, slv, c, G, L, pi, false, nullptr, 0u, 0u, nullptr, d0, d1, dr);
                 if (pi.ok) {
                     int pz;
-                    const uint32_t pb = polar_body(pi, G, lanes, pz);
+                    bool bw;
+                    const uint32_t pb = polar_body(pi, c, slv, G, lanes, pz, bw);
                     if (pb < body) body = pb;
                 }
             }
@@ -1668,12 +1808,13 @@ __device__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc,
                 unsigned long long d0 = 0, d1 = 0;
                 unsigned dr = 0;
                 PolarInfo pi;
-                polar_pass<false>(re, im, slv, G, L, pi, nullptr, 0u, 0u, wstage, d0, d1, dr);
+                polar_pass<false>(re, im, slv, c, G, L, pi, false, nullptr, 0u, 0u, wstage, d0, d1, dr);
                 if (pi.ok) {
                     int pz;
-                    const uint32_t pb = polar_body(pi, G, lanes, pz);
+                    bool bw;
+                    const uint32_t pb = polar_body(pi, c, slv, G, lanes, pz, bw);
                     if (pb < bodyb) {
-                        mode = M_POLAR;
+                        mode = bw ? M_POLAR_B : M_POLAR;
                         bodyb = pb;
                         sm[0] = sm[1] = S_CLEAR;
                         zm[0] = zm[1] = pz;
@@ -1707,9 +1848,9 @@ __device__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc,
 
     // header
     unsigned long long anc0 = 0, anc1 = 0;
-    if (mode == M_POLAR) {
+    if (mode == M_POLAR || mode == M_POLAR_B) {
         anc0 = pinfo.am;
-        anc1 = pinfo.au;
+        anc1 = mode == M_POLAR ? pinfo.au : pinfo.hp0;
     } else if (mode != M_RAW) {
         anc0 = quant(ls.f0, s);
         anc1 = quant(ls.f1, s);
@@ -1728,7 +1869,8 @@ __device__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc,
             case 4: v = (uint32_t)anc1; break;
             case 5: v = (uint32_t)(anc1 >> 32); break;
             case 6: {
-                const uint32_t zmb = (mode == M_PACKED || mode == M_POLAR) ? (uint32_t)(zm[0] | (zm[1] << 3)) : 0u;
+                const uint32_t zmb = (mode == M_PACKED || mode == M_POLAR || mode == M_POLAR_B)
+                                         ? (uint32_t)(zm[0] | (zm[1] << 3)) : 0u;
                 v = (uint32_t)c | (zmb << 8);
                 if (mode == M_POLAR) v |= (uint32_t)(pinfo.d1 & 0xFFFFull) << 16;
                 break;
@@ -1739,8 +1881,10 @@ __device__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc,
         reinterpret_cast<uint32_t *>(dst)[lane] = v;
     }
     uint8_t *b = dst + HDR;
-    if (mode == M_POLAR) {
-        // zero sections (sign sections clear), widths, residual words
+    if (mode == M_POLAR || mode == M_POLAR_B) {
+        // zero sections (sign sections clear), widths, [basis,] residual words
+        const bool bw = mode == M_POLAR_B;
+        const uint32_t wa = bw ? pinfo.w1b : pinfo.w1;
         uint32_t moff = 0, sz;
         write_section(reinterpret_cast<uint32_t *>(b), zm[0], pinfo.zw, G, lanes);
         moff += (section_mode(pinfo.zw, G, lanes, sz), sz);
@@ -1749,18 +1893,22 @@ __device__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc,
         const uint32_t nn = lane < G ? (uint32_t)__popc(~pinfo.zw & lanes) : 0u;
         uint32_t tot0, tot1;
         const uint32_t o0 = warp_exscan(lane < G ? (nn * pinfo.w0 + 31u) >> 5 : 0u, tot0);
-        const uint32_t o1 = warp_exscan(lane < G ? (nn * pinfo.w1 + 31u) >> 5 : 0u, tot1) + tot0;
+        const uint32_t o1 = warp_exscan(lane < G ? (nn * wa + 31u) >> 5 : 0u, tot1) + tot0;
         const uint32_t wb = (2u * G + 3u) & ~3u;
         for (uint32_t base = 0; base < wb; base += 32) {          // uniform trip count
             const int t = (int)base + lane;
             const int src = t < G ? t : (t < 2 * G ? t - G : 0);
             const uint32_t a = __shfl_sync(FULL, pinfo.w0, src & 31);
-            const uint32_t bb = __shfl_sync(FULL, pinfo.w1, src & 31);
+            const uint32_t bb = __shfl_sync(FULL, wa, src & 31);
             if ((uint32_t)t < wb) b[moff + t] = (uint8_t)(t < G ? a : (t < 2 * G ? bb : 0u));
         }
-        const uint32_t doff = moff + wb;
-        polar_pass<true>(re, im, s, G, L, pinfo, reinterpret_cast<uint32_t *>(b + doff), o0, o1, wstage, nlo, nhi,
-                         rng);
+        uint32_t doff = moff + wb;
+        if (bw) {
+            polar_write_basis(pinfo, c, s, reinterpret_cast<uint32_t *>(b + doff), wstage);
+            doff += 4u * polar_basis_words(c, s);
+        }
+        polar_pass<true>(re, im, s, c, G, L, pinfo, bw, reinterpret_cast<uint32_t *>(b + doff), o0, o1, wstage,
+                         nlo, nhi, rng);
         for (uint32_t p = doff + 4u * (tot0 + tot1) + lane; p < bodyb; p += 32) b[p] = 0;
     } else if (mode == M_PACKED) {
         // sign sections, then zero sections
