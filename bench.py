@@ -50,6 +50,9 @@ def parse_args():
     ap.add_argument("--n", type=int, default=N_QUBITS)
     ap.add_argument("--eps", type=float, default=EPS)
     ap.add_argument("--depth", type=int, default=512)
+    ap.add_argument("--tile-log2", type=int, default=8, help="tile size (log2 amplitudes)")
+    ap.add_argument("--pairs", type=int, default=4, help="paired high qubits per sweep")
+    ap.add_argument("--sweep-threads", type=int, default=256, help="sweep kernel CTA size (128, 256, 512)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip bound sweep / AALC / e2e")
     ap.add_argument("--workload", choices=["qft28", "serving", "grover", "aalc"], default="qft28")
@@ -288,8 +291,11 @@ def run_ours(args, rank, world, local_rank):
     gates = I.qft(n)
     stream = torch.cuda.Stream()
     st = qsim.State(n, BLOCK_LOG2, "rel", eps, stream=stream)
-    if args.depth != 512:
-        st.set_schedule(c, 4, args.depth)
+    c = min(args.tile_log2, n)
+    if args.depth != 512 or c != 8 or args.pairs != 4:
+        st.set_schedule(c, args.pairs, args.depth)
+    if args.sweep_threads != 256:
+        st.set_sweep_threads(args.sweep_threads)
 
     def step():
         st.reset_basis(xval)
@@ -330,6 +336,8 @@ def run_ours(args, rank, world, local_rank):
     raw = 16.0 * (1 << n)
     sb, fp = st.compressed_bytes()
     ref = qsim.State(n, BLOCK_LOG2, "none", 0.0, stream=stream)
+    if c != 8 or args.pairs != 4:
+        ref.set_schedule(c, args.pairs, 512)               # same tiles: fidelity is taken tile by tile
     ref.reset_basis(xval)
     ref.apply_all(gates)
     ref.flush()
@@ -766,7 +774,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"qft{n}_rel{args.eps:g}", "n_qubits": n,
-                       "block_log2": BLOCK_LOG2, "tile_log2": min(8, n), "pair_slots": 4, "rel_err_bound": args.eps,
+                       "block_log2": BLOCK_LOG2, "tile_log2": min(args.tile_log2, n), "pair_slots": args.pairs,
+                       "sweep_threads": args.sweep_threads, "rel_err_bound": args.eps,
                        "gates": ng, "sweep_depth": args.depth, "normalize": True,
                        "l2": "inputs larger than L2 (compressed state > 129 MB), no flush",
                        "parallelism": f"replicas x{world}"},

@@ -1148,7 +1148,9 @@ __device__ __forceinline__ uint32_t polar_body(const PolarInfo &pi, int c, int s
 // nonzero (and zero-fills) on a malformed stream.  The first 128 body bytes
 // (sections and widths, usually) come in with one load, and the packed
 // words of the next group are loaded while the current one is scanned.
-__device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double alpha, bool scale) {
+template <bool POLAR>
+__device__ __forceinline__ int wdecode_impl(const uint8_t *src, int c, double *re, double *im, double alpha,
+                                            bool scale) {
     const int N = 1 << c;
     const int G = N >= 32 ? N >> 5 : 1;
     const int L = N >= 32 ? 32 : N;
@@ -1164,8 +1166,8 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
     const int zm0 = (h6 >> 8) & 7, zm1 = (h6 >> 11) & 7;
     const uint8_t *b = src + HDR;
     const uint32_t *b32 = reinterpret_cast<const uint32_t *>(b);
-    const bool polar = mode == M_POLAR || mode == M_POLAR_B, pbit = mode == M_POLAR_B;
-    bool bad = hc != c || mode > 4 || (mode != M_RAW && s > 52) || (body & 15u);
+    const bool polar = POLAR && (mode == M_POLAR || mode == M_POLAR_B), pbit = POLAR && mode == M_POLAR_B;
+    bool bad = hc != c || mode > (POLAR ? 4 : 2) || (mode != M_RAW && s > 52) || (body & 15u);
     if (!bad && polar) bad = s < 8 || sm0 != S_CLEAR || sm1 != S_CLEAR;
     if (!bad && pbit) bad = zm0 != S_CLEAR || zm1 != S_CLEAR;             // no zero amplitude
     if (!bad && mode == M_RAW) bad = body != 16u * (uint32_t)N;
@@ -1423,6 +1425,20 @@ __device__ int wdecode(const uint8_t *src, int c, double *re, double *im, double
         x0 = y0; x1 = y1; x2 = y2; sh = shn;
     }
     return 0;
+}
+
+// Decode one stream (warp-wide): POLAR streams through their own function,
+// so that the componentwise decoder keeps its registers.
+__device__ __noinline__ int wdecode_polar(const uint8_t *src, int c, double *re, double *im, double alpha,
+                                          bool scale) {
+    return wdecode_impl<true>(src, c, re, im, alpha, scale);
+}
+
+__device__ __forceinline__ int wdecode(const uint8_t *src, int c, double *re, double *im, double alpha,
+                                       bool scale) {
+    const uint32_t h0 = __ldg(reinterpret_cast<const uint32_t *>(src));
+    if ((h0 & 0xFFu) >= (uint32_t)M_POLAR) return wdecode_polar(src, c, re, im, alpha, scale);
+    return wdecode_impl<false>(src, c, re, im, alpha, scale);
 }
 
 struct EncodeOut {
@@ -1734,6 +1750,134 @@ __device__ __noinline__ void wsize(const double *re, const double *im, const Cod
     }
 }
 
+// The ladder of a tile with the POLAR variant on (a separate function so
+// that the componentwise encoder keeps its registers): every level sized
+// componentwise and in the POLAR mode, the shorter kept, the first level
+// within the size limit (else the last, or force_lv) chosen.  When the
+// chosen stream is a POLAR one it is written here (stream, table entry,
+// norm, counters; *off = its offset, ~0 on overflow) and true returned;
+// otherwise mode, level, bodyb and sm describe the componentwise stream
+// for the caller to write.  Warp-wide.
+__device__ __noinline__ bool polar_ladder(const double *re, const double *im, const CodecCfg &cc,
+                                          const LevelSizes &ls, const Sections &q, uint32_t raw_body, int force_lv,
+                                          unsigned long long tile, uint8_t *out_arena, unsigned long long out_cap,
+                                          unsigned long long *out_table, unsigned long long *part,
+                                          DevScalars *scal, unsigned sweep_id, uint32_t *wstage, int &mode,
+                                          int &level, uint32_t &bodyb, int *sm, unsigned long long &off) {
+    const int c = cc.c, N = 1 << c;
+    const int G = N >= 32 ? N >> 5 : 1;
+    const int L = N >= 32 ? 32 : N;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lanes = L == 32 ? FULL : ((1u << L) - 1u);
+    PolarInfo pinfo{};
+    int pz = 0;
+    bool found = false;
+    for (int lv = 0; lv < cc.nlev && !found; ++lv) {
+        if (force_lv >= 0 && lv != force_lv) continue;
+        const int slv = cc.shifts[lv];
+        bodyb = level_body(ls, q, lv, slv, raw_body, mode, sm[0], sm[1]);
+        if (slv >= 8 && slv <= 52) {
+            unsigned long long d0 = 0, d1 = 0;
+            unsigned dr = 0;
+            PolarInfo pi;
+            polar_pass<false>(re, im, slv, c, G, L, pi, false, nullptr, 0u, 0u, wstage, d0, d1, dr);
+            if (pi.ok) {
+                int z;
+                bool bw;
+                const uint32_t pb = polar_body(pi, c, slv, G, lanes, z, bw);
+                if (pb < bodyb) {
+                    mode = bw ? M_POLAR_B : M_POLAR;
+                    bodyb = pb;
+                    sm[0] = sm[1] = S_CLEAR;
+                    pz = z;
+                    pinfo = pi;
+                }
+            }
+        }
+        level = lv;
+        found = force_lv >= 0 || (unsigned long long)(HDR + bodyb) <= cc.max_bytes;
+    }
+    if (mode != M_POLAR && mode != M_POLAR_B) return false;
+    const int s = cc.shifts[level];
+    const bool bw = mode == M_POLAR_B;
+    const uint32_t size = HDR + bodyb;
+    int ok = 0;
+    off = 0;
+    if (lane == 0) {
+        off = atomicAdd(&scal->bump, (unsigned long long)size);
+        ok = off + size <= out_cap;
+        if (!ok) {
+            atomicOr(&scal->err, ERR_OVERFLOW);
+            atomicCAS(&scal->err_sweep, 0u, sweep_id + 1u);
+        }
+    }
+    off = shfl64(off, 0);
+    ok = __shfl_sync(FULL, ok, 0);
+    if (!ok) { off = ~0ull; return true; }
+    uint8_t *dst = out_arena + off;
+    const unsigned long long anc0 = pinfo.am, anc1 = bw ? pinfo.hp0 : pinfo.au;
+    if (lane < 8) {
+        uint32_t v = 0;
+        switch (lane) {
+            case 0: v = (uint32_t)mode | ((uint32_t)s << 8) | ((uint32_t)level << 16); break;
+            case 1: v = bodyb; break;
+            case 2: v = (uint32_t)anc0; break;
+            case 3: v = (uint32_t)(anc0 >> 32); break;
+            case 4: v = (uint32_t)anc1; break;
+            case 5: v = (uint32_t)(anc1 >> 32); break;
+            case 6:
+                v = (uint32_t)c | ((uint32_t)(pz | (pz << 3)) << 8);
+                if (!bw) v |= (uint32_t)(pinfo.d1 & 0xFFFFull) << 16;
+                break;
+            default: v = bw ? 0u : (uint32_t)(pinfo.d1 >> 16); break;
+        }
+        reinterpret_cast<uint32_t *>(dst)[lane] = v;
+    }
+    uint8_t *b = dst + HDR;
+    // zero sections (sign sections clear), widths, [basis,] residual words
+    const uint32_t wa = bw ? pinfo.w1b : pinfo.w1;
+    uint32_t moff = 0, sz;
+    write_section(reinterpret_cast<uint32_t *>(b), pz, pinfo.zw, G, lanes);
+    moff += (section_mode(pinfo.zw, G, lanes, sz), sz);
+    write_section(reinterpret_cast<uint32_t *>(b + moff), pz, pinfo.zw, G, lanes);
+    moff += sz;
+    const uint32_t nn = lane < G ? (uint32_t)__popc(~pinfo.zw & lanes) : 0u;
+    uint32_t tot0, tot1;
+    const uint32_t o0 = warp_exscan(lane < G ? (nn * pinfo.w0 + 31u) >> 5 : 0u, tot0);
+    const uint32_t o1 = warp_exscan(lane < G ? (nn * wa + 31u) >> 5 : 0u, tot1) + tot0;
+    const uint32_t wb = (2u * G + 3u) & ~3u;
+    for (uint32_t base = 0; base < wb; base += 32) {          // uniform trip count
+        const int t = (int)base + lane;
+        const int src = t < G ? t : (t < 2 * G ? t - G : 0);
+        const uint32_t a = __shfl_sync(FULL, pinfo.w0, src & 31);
+        const uint32_t bb = __shfl_sync(FULL, wa, src & 31);
+        if ((uint32_t)t < wb) b[moff + t] = (uint8_t)(t < G ? a : (t < 2 * G ? bb : 0u));
+    }
+    uint32_t doff = moff + wb;
+    if (bw) {
+        polar_write_basis(pinfo, c, s, reinterpret_cast<uint32_t *>(b + doff), wstage);
+        doff += 4u * polar_basis_words(c, s);
+    }
+    unsigned long long nlo = 0, nhi = 0;
+    unsigned rng = 0;
+    polar_pass<true>(re, im, s, c, G, L, pinfo, bw, reinterpret_cast<uint32_t *>(b + doff), o0, o1, wstage,
+                     nlo, nhi, rng);
+    for (uint32_t p = doff + 4u * (tot0 + tot1) + lane; p < bodyb; p += 32) b[p] = 0;
+    warp_sum128(nlo, nhi);
+    rng = __any_sync(FULL, rng);
+    if (lane == 0) {
+        part[2 * tile] = nlo;
+        part[2 * tile + 1] = nhi;
+        atomic_add128(&scal->acc_lo, &scal->acc_hi, nlo, nhi);
+        out_table[tile] = off;
+        atomicAdd(&scal->hist[level], 1ull);
+        if ((unsigned long long)size > cc.max_bytes) atomicAdd(&scal->over_limit, 1ull);
+        if (rng) atomicOr(&scal->err, ERR_RANGE);
+    }
+    __syncwarp();
+    return true;
+}
+
 // Encode planar re/im (2^c values each) of tile `tile` into the output
 // arena with Algorithm 2's ladder (every level sized in one pass), or at
 // ladder level force_lv when it is >= 0 (the level of the tile's stride).
@@ -1741,7 +1885,8 @@ __device__ __noinline__ void wsize(const double *re, const double *im, const Cod
 // to the running norm.  wstage: 64 words of shared memory of this warp.
 // With one lossy level at shift >= 32 the tile is coded in one pass and
 // its values in shared memory are overwritten.
-__device__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc,
+template <bool POLAR>
+__device__ __forceinline__ EncodeOut wencode_impl(double *re, double *im, const CodecCfg &cc,
                              unsigned long long tile, uint8_t *out_arena, unsigned long long out_cap,
                              unsigned long long *out_table, unsigned long long *part,
                              DevScalars *scal, unsigned sweep_id, uint32_t *wstage, int force_lv) {
@@ -1785,7 +1930,7 @@ __device__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc,
     int mode, level = 0, s = 0, sm[2] = {0, 0}, zm[2] = {0, 0};
     uint32_t bodyb;
     const uint32_t raw_body = 16u * (uint32_t)N;
-    PolarInfo pinfo{};
+    unsigned long long res_off = 0;
     if (raw_only) {
         mode = M_RAW;
         bodyb = raw_body;
@@ -1796,34 +1941,24 @@ __device__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc,
         zm[1] = q.zm1;
         mode = M_RAW;
         bodyb = raw_body;
-        bool found = false;                  // first level within the size limit, else the last
-        const bool try_polar = cc.polar && !inel;
+        bool polar_done = false;
+        if constexpr (POLAR) {
+            // the ladder with the POLAR variant of every lossy level; a
+            // POLAR stream is written there and the tile is done
+            if (!inel && polar_ladder(re, im, cc, ls, q, raw_body, force_lv, tile, out_arena, out_cap, out_table,
+                                      part, scal, sweep_id, wstage, mode, level, bodyb, sm, res_off))
+                return EncodeOut{res_off, res_off != ~0ull};
+            polar_done = !inel;
+        }
+        if (!polar_done) {
+            bool found = false;              // first level within the size limit, else the last
 #pragma unroll
-        for (int lv = 0; lv < MAX_LEVELS; ++lv) {
-            if (lv >= cc.nlev || found || (force_lv >= 0 && lv != force_lv)) continue;
-            const int slv = inel ? 0 : cc.shifts[lv];
-            bodyb = level_body(ls, q, lv, slv, raw_body, mode, sm[0], sm[1]);
-            if (try_polar && slv >= 8 && slv <= 52) {
-                // the POLAR variant of this level, kept when shorter
-                unsigned long long d0 = 0, d1 = 0;
-                unsigned dr = 0;
-                PolarInfo pi;
-                polar_pass<false>(re, im, slv, c, G, L, pi, false, nullptr, 0u, 0u, wstage, d0, d1, dr);
-                if (pi.ok) {
-                    int pz;
-                    bool bw;
-                    const uint32_t pb = polar_body(pi, c, slv, G, lanes, pz, bw);
-                    if (pb < bodyb) {
-                        mode = bw ? M_POLAR_B : M_POLAR;
-                        bodyb = pb;
-                        sm[0] = sm[1] = S_CLEAR;
-                        zm[0] = zm[1] = pz;
-                        pinfo = pi;
-                    }
-                }
+            for (int lv = 0; lv < MAX_LEVELS; ++lv) {
+                if (lv >= cc.nlev || found || (force_lv >= 0 && lv != force_lv)) continue;
+                bodyb = level_body(ls, q, lv, inel ? 0 : cc.shifts[lv], raw_body, mode, sm[0], sm[1]);
+                level = lv;
+                found = force_lv >= 0 || (unsigned long long)(HDR + bodyb) <= cc.max_bytes;
             }
-            level = lv;
-            found = force_lv >= 0 || (unsigned long long)(HDR + bodyb) <= cc.max_bytes;
         }
         s = mode == M_RAW ? 0 : (inel ? 0 : cc.shifts[level]);
     }
@@ -1848,10 +1983,7 @@ __device__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc,
 
     // header
     unsigned long long anc0 = 0, anc1 = 0;
-    if (mode == M_POLAR || mode == M_POLAR_B) {
-        anc0 = pinfo.am;
-        anc1 = mode == M_POLAR ? pinfo.au : pinfo.hp0;
-    } else if (mode != M_RAW) {
+    if (mode != M_RAW) {
         anc0 = quant(ls.f0, s);
         anc1 = quant(ls.f1, s);
     }
@@ -1869,48 +2001,16 @@ __device__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc,
             case 4: v = (uint32_t)anc1; break;
             case 5: v = (uint32_t)(anc1 >> 32); break;
             case 6: {
-                const uint32_t zmb = (mode == M_PACKED || mode == M_POLAR || mode == M_POLAR_B)
-                                         ? (uint32_t)(zm[0] | (zm[1] << 3)) : 0u;
+                const uint32_t zmb = mode == M_PACKED ? (uint32_t)(zm[0] | (zm[1] << 3)) : 0u;
                 v = (uint32_t)c | (zmb << 8);
-                if (mode == M_POLAR) v |= (uint32_t)(pinfo.d1 & 0xFFFFull) << 16;
                 break;
             }
-            case 7: v = mode == M_POLAR ? (uint32_t)(pinfo.d1 >> 16) : 0u; break;
             default: v = 0; break;
         }
         reinterpret_cast<uint32_t *>(dst)[lane] = v;
     }
     uint8_t *b = dst + HDR;
-    if (mode == M_POLAR || mode == M_POLAR_B) {
-        // zero sections (sign sections clear), widths, [basis,] residual words
-        const bool bw = mode == M_POLAR_B;
-        const uint32_t wa = bw ? pinfo.w1b : pinfo.w1;
-        uint32_t moff = 0, sz;
-        write_section(reinterpret_cast<uint32_t *>(b), zm[0], pinfo.zw, G, lanes);
-        moff += (section_mode(pinfo.zw, G, lanes, sz), sz);
-        write_section(reinterpret_cast<uint32_t *>(b + moff), zm[1], pinfo.zw, G, lanes);
-        moff += sz;
-        const uint32_t nn = lane < G ? (uint32_t)__popc(~pinfo.zw & lanes) : 0u;
-        uint32_t tot0, tot1;
-        const uint32_t o0 = warp_exscan(lane < G ? (nn * pinfo.w0 + 31u) >> 5 : 0u, tot0);
-        const uint32_t o1 = warp_exscan(lane < G ? (nn * wa + 31u) >> 5 : 0u, tot1) + tot0;
-        const uint32_t wb = (2u * G + 3u) & ~3u;
-        for (uint32_t base = 0; base < wb; base += 32) {          // uniform trip count
-            const int t = (int)base + lane;
-            const int src = t < G ? t : (t < 2 * G ? t - G : 0);
-            const uint32_t a = __shfl_sync(FULL, pinfo.w0, src & 31);
-            const uint32_t bb = __shfl_sync(FULL, wa, src & 31);
-            if ((uint32_t)t < wb) b[moff + t] = (uint8_t)(t < G ? a : (t < 2 * G ? bb : 0u));
-        }
-        uint32_t doff = moff + wb;
-        if (bw) {
-            polar_write_basis(pinfo, c, s, reinterpret_cast<uint32_t *>(b + doff), wstage);
-            doff += 4u * polar_basis_words(c, s);
-        }
-        polar_pass<true>(re, im, s, c, G, L, pinfo, bw, reinterpret_cast<uint32_t *>(b + doff), o0, o1, wstage,
-                         nlo, nhi, rng);
-        for (uint32_t p = doff + 4u * (tot0 + tot1) + lane; p < bodyb; p += 32) b[p] = 0;
-    } else if (mode == M_PACKED) {
+    if (mode == M_PACKED) {
         // sign sections, then zero sections
         const uint32_t sv0 = s ? ls.sw0 & ~ls.zw0 : ls.sw0, sv1 = s ? ls.sw1 & ~ls.zw1 : ls.sw1;
         uint32_t moff = 0, sz;
@@ -2082,6 +2182,26 @@ __device__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc,
     }
     __syncwarp();
     return res;
+}
+
+// Encode with the POLAR variant (its own function, so that the
+// componentwise encoder below keeps its registers).
+__device__ __noinline__ EncodeOut wencode_polar(double *re, double *im, const CodecCfg &cc, unsigned long long tile,
+                                                uint8_t *out_arena, unsigned long long out_cap,
+                                                unsigned long long *out_table, unsigned long long *part,
+                                                DevScalars *scal, unsigned sweep_id, uint32_t *wstage, int force_lv) {
+    return wencode_impl<true>(re, im, cc, tile, out_arena, out_cap, out_table, part, scal, sweep_id, wstage,
+                              force_lv);
+}
+
+__device__ __forceinline__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc, unsigned long long tile,
+                                             uint8_t *out_arena, unsigned long long out_cap,
+                                             unsigned long long *out_table, unsigned long long *part,
+                                             DevScalars *scal, unsigned sweep_id, uint32_t *wstage, int force_lv) {
+    if (cc.polar)
+        return wencode_polar(re, im, cc, tile, out_arena, out_cap, out_table, part, scal, sweep_id, wstage, force_lv);
+    return wencode_impl<false>(re, im, cc, tile, out_arena, out_cap, out_table, part, scal, sweep_id, wstage,
+                               force_lv);
 }
 
 // Value of a well-formed CONST stream (the checks of wdecode), scaled like
