@@ -362,6 +362,23 @@ def run_ours(args, rank, world, local_rank):
                               "gates_per_s": round(len(gates) / dt, 1)})
             s2.close()
         result["per_bound"] = per_bound
+        per_bound_polar = []
+        for e in (1e-2, 1e-3, 1e-4, 1e-5):                # the POLAR variant (magnitude + phase)
+            s2 = qsim.State(n, BLOCK_LOG2, "rel", e, stream=stream)
+            s2.set_polar(True)
+            s2.reset_basis(xval)
+            t0 = time.perf_counter()
+            s2.apply_all(gates)
+            s2.flush()
+            dt = time.perf_counter() - t0
+            b2, _ = s2.compressed_bytes()
+            st2 = s2.stats()
+            per_bound_polar.append({"eps": e, "fidelity_vs_fp64": round(s2.fidelity_state(ref), 9),
+                                    "ratio_final": round(raw / b2, 3),
+                                    "ratio_min": round(raw / max(1, st2["max_stream_bytes_seen"]), 3),
+                                    "gates_per_s": round(len(gates) / dt, 1)})
+            s2.close()
+        result["per_bound_polar"] = per_bound_polar
         s3 = qsim.State(n, BLOCK_LOG2, "aalc", 1e-2, stream=stream)
         s3.set_aalc(16.0, [1e-5, 1e-4, 1e-3, 1e-2])
         s3.reset_basis(xval)
@@ -374,6 +391,20 @@ def run_ours(args, rank, world, local_rank):
                                   "ratio_min": round(raw / max(1, st3["max_stream_bytes_seen"]), 3),
                                   "level_hist": st3["level_hist"][:5]}
         s3.close()
+        s4 = qsim.State(n, BLOCK_LOG2, "aalc", 1e-2, stream=stream)
+        s4.set_aalc(16.0, [1e-5, 1e-4, 1e-3, 1e-2])
+        s4.set_polar(True)
+        s4.reset_basis(xval)
+        s4.apply_all(gates)
+        s4.flush()
+        b4, _ = s4.compressed_bytes()
+        st4 = s4.stats()
+        result["aalc_theta16_polar"] = {"fidelity_vs_fp64": round(s4.fidelity_state(ref), 9),
+                                        "ratio_final": round(raw / b4, 3),
+                                        "ratio_min": round(raw / max(1, st4["max_stream_bytes_seen"]), 3),
+                                        "tiles_over_limit": st4["tiles_over_limit"],
+                                        "level_hist": st4["level_hist"][:5]}
+        s4.close()
         # end to end through the public API: host gate list in, host result out
         qs = [0, n // 2, n - 1]
         st.reset_basis(xval)
@@ -804,7 +835,9 @@ def main():
             line["e2e"] = {"value": ng / res["e2e_s"], "unit": "gates/s",
                            "h2d_bytes_per_step": res["e2e_h2d"], "d2h_bytes_per_step": res["e2e_d2h"]}
             line["per_bound"] = res["per_bound"]
+            line["per_bound_polar"] = res["per_bound_polar"]
             line["aalc_theta16"] = res["aalc_theta16"]
+            line["aalc_theta16_polar"] = res["aalc_theta16_polar"]
         print(json.dumps(line))
     if world > 1:
         import torch
