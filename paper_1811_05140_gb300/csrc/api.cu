@@ -1303,7 +1303,9 @@ qsim_status finish_flush(qsim_t h, FlushCtx &fc, bool timed) {
             h->prof.sweep_ms += ms;
             h->prof.sweep_launches += 1;
             // the decompression scale: normalize and / or the scaled gates' D
-            double dp = (h->normalize || fc.sweep_scaled[j]) ? 2.0 * std::ldexp(1.0, h->n) : 0.0;
+            // (none in sweeps that move whole tiles: nothing is decompressed)
+            const bool moved = sweep_params(h, fc, j).moves_tiles != 0;
+            double dp = (!moved && (h->normalize || fc.sweep_scaled[j])) ? 2.0 * std::ldexp(1.0, h->n) : 0.0;
             for (int gi = fc.sweeps[j].lo; gi < fc.sweeps[j].hi; ++gi)
                 if (!fc.in_run[gi]) dp += gate_dp_ops(h->queue[gi], h->n, fc.scaled[gi]);
             h->prof.dp_ops += dp;
