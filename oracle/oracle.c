@@ -192,7 +192,9 @@ static int apply_gate_buf(double *a, int mb, const int *qb, uint64_t fixed,
 
 /* apply_gate_buf, with unscaled set: every factored row yields its sum S
  * without the final multiplication by its first entry d (the scaled gates
- * of a sweep, see gate_scale). */
+ * of a sweep, see gate_scale), and a group of 2^k amplitudes that are all
+ * exactly zero (either sign) is left as it is: its sums are zeros, and only
+ * the IEEE sign of a zero could differ from forming them. */
 static int apply_gate_rows(double *a, int mb, const int *qb, uint64_t fixed,
                            const or_gate *g, int unscaled)
 {
@@ -239,6 +241,12 @@ static int apply_gate_rows(double *a, int mb, const int *qb, uint64_t fixed,
                 x[2 * s + 1] = 0.0;
             }
         }
+        if (unscaled) {
+            /* a scaled gate leaves a group of exactly-zero amplitudes as it is */
+            int nz = 0;
+            for (int j = 0; j < 2 * dim; ++j) nz |= x[j] != 0.0;
+            if (!nz) continue;
+        }
         for (int r = 0; r < dim; ++r)
             if (present[r]) row_eval(g->m, dim, r, x, present, unscaled, &y[2 * r], &y[2 * r + 1]);
         for (int r = 0; r < dim; ++r)
@@ -267,7 +275,10 @@ static int apply_gate_rows(double *a, int mb, const int *qb, uint64_t fixed,
  *     (constant over a tile) form one product T, every other gate another
  *     product L;
  *   - the amplitude a becomes i^k * (G a) with G = T*L (T applied to L) when
- *     both exist, else the one that exists, and i^k * a when neither does.
+ *     both exist, else the one that exists, and i^k * a when neither does;
+ *   - an amplitude that is exactly zero (both components +0 or -0) is left
+ *     as it is (every factor keeps it zero; only the IEEE sign of a zero
+ *     could differ from multiplying it).
  * Mathematically the same operator as the gates one after the other
  * (Sec. II pair update for diagonal matrices); in rounding it multiplies
  * every amplitude twice at most, whatever the run's length.
@@ -319,6 +330,7 @@ static void apply_diag_run(double *a, int mb, const int *qb, uint64_t fixed, con
 {
     uint64_t nb = 1ull << mb;
     for (uint64_t l = 0; l < nb; ++l) {
+        if (a[2 * l] == 0.0 && a[2 * l + 1] == 0.0) continue;     /* a zero stays as it is */
         uint64_t gl = fixed;
         for (int p = 0; p < mb; ++p)
             if ((l >> p) & 1) gl |= 1ull << qb[p];

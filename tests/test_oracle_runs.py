@@ -22,6 +22,9 @@ normalize scale at decompression (a scalar commutes with linear maps).
 * The fused QFT against its closed form e^{2 pi i x k / N} / sqrt(N).
 * Runs are really fused: the QFT's amplitudes differ in rounding from the
   gate-by-gate sweep somewhere.
+* Exact zeros: an amplitude whose components are both zero (either sign)
+  keeps its bits under a run, and so does a pair of them under a scaled
+  gate; an amplitude with one zero component is multiplied like any other.
 """
 import cmath
 import math
@@ -180,3 +183,61 @@ def test_gates_that_are_not_scaled_keep_their_arithmetic():
     psi = oracle.dense_run(oracle.dense_zero(n), n, gates)
     got = lossless(n, c, gates, 4, 512)
     assert np.array_equal(got.view(np.uint64), psi.view(np.uint64))
+
+
+def zero_mixed_state(n, seed):
+    """A random state with exact zeros of both signs (both components),
+    amplitudes with one zero component, and pairs (l, l ^ 8) of zeros."""
+    rng = np.random.default_rng(seed)
+    psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    psi /= np.linalg.norm(psi)
+    nz, pz = -0.0, 0.0
+    zs = [complex(pz, pz), complex(nz, nz), complex(pz, nz), complex(nz, pz)]
+    idx = rng.permutation(1 << n)
+    for j, l in enumerate(idx[:40]):
+        psi[l] = zs[j % 4]
+    for l in idx[40:50]:
+        psi[l] = complex(0.0, psi[l].imag)            # zero real part
+    for l in idx[50:60]:
+        psi[l] = complex(psi[l].real, -0.0)           # zero imaginary part
+    for j, l in enumerate(range(0, 1 << n, 37)):
+        if not (l >> 3) & 1:                          # both members of the pair (l, l ^ 8)
+            psi[l] = zs[j % 4]
+            psi[l ^ 8] = zs[(j + 1) % 4]
+    return psi
+
+
+def test_zero_amplitudes_are_left_as_they_are():
+    n, c = 8, 4
+    psi0 = zero_mixed_state(n, 3)
+    zero0 = (psi0.real == 0) & (psi0.imag == 0)
+    # a run in which every amplitude meets one general factor (exact
+    # against the gates one by one), then a Hadamard in a sweep of its own
+    rng = np.random.default_rng(9)
+    p = [cmath.exp(1j * float(v)) for v in rng.uniform(0.3, 2.8, 3)]
+    run = [I.Gate(diag(1, p[0]), (1,), (6,), (0,)), I.Gate(diag(1, p[1]), (1,), (6,), (1,)),
+           I.Gate(diag(p[2], 1), (1,))]
+    cs = oracle.CSim(n, c, [0], normalize=False, fuse=True)
+    cs.set_dense(psi0)
+    cs.sweep(run, [])
+    got = cs.dense()
+    want = oracle.dense_run(psi0.copy(), n, run)
+    assert np.array_equal(got[zero0].view(np.uint64), psi0[zero0].view(np.uint64))
+    assert np.array_equal(got[~zero0].view(np.uint64), want[~zero0].view(np.uint64))
+    # multiplying a zero would have changed some of their signs
+    assert not np.array_equal(want[zero0].view(np.uint64), psi0[zero0].view(np.uint64))
+
+    cs.sweep([I.h(3)], [])
+    got2 = cs.dense()
+    want2 = oracle.dense_run(got.copy(), n, [I.h(3)])
+    lo = np.array([l for l in range(1 << n) if not (l >> 3) & 1])
+    z = zero0.copy()
+    pair_zero = z[lo] & z[lo ^ 8]
+    one_nz = z[lo] ^ z[lo ^ 8]
+    for sel in (lo[pair_zero], lo[pair_zero] ^ 8):
+        assert np.array_equal(got2[sel].view(np.uint64), got[sel].view(np.uint64))
+    assert pair_zero.sum() >= 5 and one_nz.sum() >= 5
+    # a pair with one nonzero member: d x, exact either way
+    for sel in (lo[one_nz], lo[one_nz] ^ 8):
+        assert np.array_equal(got2[sel].view(np.uint64), want2[sel].view(np.uint64))
+    assert np.max(np.abs(got2 - want2)) <= 1e-15
