@@ -165,9 +165,12 @@ qsim_status qsim_set_normalize(qsim_t h, int on);
 /*
  * qsim_set_schedule -- tile_log2 c (1..10, <= n), pair slots hmax (1..4,
  * c + hmax <= 12; default 4) and sweep depth (max gates per sweep, 1..512;
- * default 512).  Re-tiles the current state (re-encoding is exact only for
- * RAW/lossless tiles; call it before the first gate; n <= 32).  Used by
- * the autotuner.  Errors: ARG (ranges), OOM, CUDA.
+ * default 512).  Re-tiles the current state: a basis state set by
+ * qsim_create or qsim_reset_basis (no gates applied since) is encoded
+ * afresh in the new tiles, any n; any other state is decoded into a dense
+ * device buffer of 2^(n+4) bytes and re-encoded (exact only for
+ * RAW/lossless tiles; n <= 32), so call it before the first gate.  Used
+ * by the autotuner.  Errors: ARG (ranges), OOM, CUDA.
  */
 qsim_status qsim_set_schedule(qsim_t h, int tile_log2, int hmax, int depth);
 
@@ -175,23 +178,30 @@ qsim_status qsim_set_schedule(qsim_t h, int tile_log2, int hmax, int depth);
  * qsim_set_polar -- on = 1: every lossy level of a REL or AALC handle also
  * codes each tile in the POLAR mode and keeps the shorter stream (a codec
  * variant; the level decision of AALC then uses that size).  POLAR stream
- * (mode byte 3): each nonzero amplitude a = x + iy as its magnitude
- * m = sqrt(fma(x, x, y*y)) quantised like a component with shift s - 2,
+ * (mode byte 3 or 4): each nonzero amplitude a = x + iy as its magnitude
+ * m = sqrt(fma(x, x, y*y)) quantised like a component with shift s - 1,
  * and its angle from an integer CORDIC (30 steps of
  * round(2^64 atan(2^-k) / (2 pi)), units of 2^-64 turn) quantised with
- * shift s + 8 to B = 56 - s bits; reconstruction: the CORDIC rotation
+ * shift P = s + 8 to B = 56 - s bits; reconstruction: the CORDIC rotation
  * (X, Y) of (2^59, 0) by the angle code, a^ = (m^ Xd r, m^ Yd r) with
  * r = 1 / sqrt(Xd^2 + Yd^2).  Magnitude codes: order-1 residuals from the
- * anchor (header 8..15); angle codes: order-2 residuals modulo 2^B from
- * u0 (header 16..23) and the first difference d1 (header 26..31, 48 bits),
- * the first two nonzero amplitudes taking residual 0; body as PACKED with
- * clear sign sections and equal zero sections.  A tile takes the mode
- * only for 8 <= s <= 52, every component 0 or in [2^-400, 16), and every
- * amplitude within |a^ - a|^2 <= 2^(2(s-53)) (1 - 2^-10) |a|^2: the
- * level's bound on the complex amplitude, not on each component.  Phases
- * linear in the index (the QFT's tiles) cost almost nothing.  Saved in
- * checkpoints.  Flushes queued gates first.  Errors: ARG (codec NONE or
- * LOSSLESS).
+ * anchor (header 8..15).  Angle codes, mode 3: order-2 residuals modulo
+ * 2^B from u0 (header 16..23) and the first difference d1 (header 26..31,
+ * 48 bits), the first two nonzero amplitudes taking residual 0.  Mode 4
+ * (tiles without zero amplitudes): the angle hp(i) of amplitude i rounded
+ * to B + 8 bits is predicted as hp(0) (header 16..23) plus the basis
+ * differences D_b = hp(2^b) - hp(0) mod 2^(B+8) of the set bits b of i,
+ * rounded to B bits; residual = code - prediction mod 2^B; the c values
+ * D_b follow the width bytes, packed at B + 8 bits each in u32 words
+ * (header 26..31 zero).  The encoder takes the shorter of modes 3 and 4
+ * (3 on a tie).  Body as PACKED with clear sign sections and equal zero
+ * sections.  A tile takes the mode only for 8 <= s <= 52, every component
+ * 0 or in [2^-400, 16), and every amplitude within
+ * |a^ - a|^2 <= 2^(2(s-53)) (1 - 2^-10) |a|^2: the level's bound on the
+ * complex amplitude, not on each component.  Phases linear in the index,
+ * or sums of one phase per index bit (the QFT's tiles), cost almost
+ * nothing.  Saved in checkpoints.  Flushes queued gates first.  Errors:
+ * ARG (codec NONE or LOSSLESS).
  */
 qsim_status qsim_set_polar(qsim_t h, int on);
 
@@ -501,10 +511,18 @@ typedef struct qsim_server *qsim_server_t;
 /*
  * qsim_server_create -- start a serving loop on the current device (one
  * host thread and one CUDA stream of its own).  A waiting circuit is
- * admitted while the measured device footprint of the resident circuits
- * plus the newcomer's initial footprint stays within three quarters of
- * mem_budget_bytes (the rest is headroom for growth) and fewer than
- * max_resident circuits run.  Each tick applies the next sweeps_per_tick
+ * admitted while the reservations of the resident circuits plus the
+ * newcomer's stay within mem_budget_bytes and fewer than max_resident
+ * circuits run; a circuit alone is always admitted.  A circuit's
+ * reservation is the larger of its measured device footprint (before
+ * admission: its initial footprint) and its growth bound: 32 bytes per
+ * tile plus two arenas of the codec's stream bound, which is, per tile,
+ * floor(16 * 2^c / theta) for AALC with theta > 0 (the ratio threshold),
+ * the largest PACKED stream at the codec's shift s for REL (widths of at
+ * most 65 - s bits), and the RAW size otherwise (tiles that the ladder
+ * cannot bring under theta, or that hold values outside the lossy range,
+ * may exceed it; the measured footprint then counts).  Each tick applies
+ * the next sweeps_per_tick
  * sweeps of every resident circuit (cut at the circuit's own sweep
  * boundaries, qsim_plan_sweeps) as one batched flush
  * (qsim_flush_batch, CUDA-graph captured when use_graph), so newcomers join

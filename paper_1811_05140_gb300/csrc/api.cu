@@ -330,6 +330,8 @@ struct qsim_state {
     std::vector<cudaEvent_t> events;
     std::string err;
     bool invalid = false;
+    bool basis = false;                   // the state is the basis state basis_x as encoded afresh
+    unsigned long long basis_x = 0;
     bool pool = false;                    // arenas live in a caller-owned buffer
     int unit_log2 = 0;                    // amplitudes per ladder decision (log2); 0 = one tile
     unsigned long long *unit_bytes = nullptr;   // per stride and level: stream bytes
@@ -531,6 +533,8 @@ qsim_status encode_fresh(qsim_t h, const double2 *dense, unsigned long long x) {
         if (h->hscal->err) return device_error(h, h->hscal->err);
         h->used = h->hscal->used;
         h->st.stream_bytes = h->used;
+        h->basis = dense == nullptr;
+        h->basis_x = x;
         return QSIM_OK;
     }
     return fail(h, QSIM_ERR_OOM, "arena could not hold the state");
@@ -652,6 +656,30 @@ void prepare_gate(const HostGate &g, int c, const Sweep &sw, qs::DGate &d, qs::S
 // device bytes held by a state: both arenas, tile tables, norm partials
 unsigned long long qs_handle_footprint(qsim_t h) {
     return h ? h->cap[0] + h->cap[1] + h->ntiles * 32ull : 0ull;
+}
+
+// Bound on the stream bytes of an n-qubit state in tiles of 2^c amplitudes
+// under a codec.  AALC with theta > 0: the ratio threshold's size per tile,
+// floor(16 * 2^c / theta) (the paper's ratio guarantee; a tile that no
+// level brings under it shows in the measured footprint).  REL: the largest
+// PACKED stream the format allows at the codec's shift s (two 4G-byte sign
+// and zero sections per component, 2G width bytes, 65 - s bits per value
+// and component, padding), at most the RAW size; a tile with a value
+// outside the lossy range is stored losslessly and may reach RAW.  NONE and
+// LOSSLESS: RAW.
+unsigned long long qs_stream_bound(int n, int c, int codec, double eps, double theta) {
+    const unsigned long long N = 1ull << c, G = N >= 32 ? N / 32 : 1;
+    const unsigned long long ntiles = 1ull << (n - c);
+    const unsigned long long raw = qs::HDR + 16ull * N;
+    unsigned long long per = raw;
+    if (codec == QSIM_CODEC_AALC && theta > 0.0) {
+        per = std::min(raw, std::max<unsigned long long>(qs::HDR, round_up((unsigned long long)(16.0 * (double)N / theta), 16)));
+    } else if (codec == QSIM_CODEC_REL || codec == QSIM_CODEC_AALC) {
+        const int s = shift_for_eps(eps);
+        const unsigned long long body = 16ull * G + round_up(2ull * G, 4) + N * (unsigned long long)(65 - s) / 4ull + 4ull;
+        per = std::min(raw, round_up(qs::HDR + body, 16));
+    }
+    return ntiles * per;
 }
 
 extern "C" {
@@ -1109,7 +1137,10 @@ qsim_status stage_flush(qsim_t h, FlushCtx &fc, cudaStream_t st) {
         for (size_t si = 0; si < ns; ++si)
             for (int gi = fc.sweeps[si].lo; gi < fc.sweeps[si].hi; ++gi)
                 if (is_scaled_gate(h->queue[gi])) {
-                    h->hsg[gi].unscaled = 1;
+                    // FP64 instructions of one group of 2^k amplitudes (4 for a
+                    // Hadamard, at most 24): the device counts the groups it forms
+                    const HostGate &g = h->queue[gi];
+                    h->hsg[gi].unscaled = (uint8_t)std::max(1.0, gate_dp_ops(g, g.k, true));
                     fc.scaled[gi] = 1;
                     fc.sweep_scaled[si] = 1;
                 }
@@ -1283,6 +1314,7 @@ qsim_status run_from(qsim_t h, FlushCtx &fc, size_t k) {
 // Bookkeeping after every pass of a flush has succeeded.
 qsim_status finish_flush(qsim_t h, FlushCtx &fc, bool timed) {
     const size_t ns = fc.ns;
+    if (ns) h->basis = false;
     CK(hcopy(h, h->hused, h->used_hist, ns * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->cur = fc.cur0 ^ (int)(ns & 1);
@@ -1307,13 +1339,13 @@ qsim_status finish_flush(qsim_t h, FlushCtx &fc, bool timed) {
             const bool moved = sweep_params(h, fc, j).moves_tiles != 0;
             double dp = (!moved && (h->normalize || fc.sweep_scaled[j])) ? 2.0 * std::ldexp(1.0, h->n) : 0.0;
             for (int gi = fc.sweeps[j].lo; gi < fc.sweeps[j].hi; ++gi)
-                if (!fc.in_run[gi]) dp += gate_dp_ops(h->queue[gi], h->n, fc.scaled[gi]);
+                if (!fc.in_run[gi] && !fc.scaled[gi]) dp += gate_dp_ops(h->queue[gi], h->n);
             h->prof.dp_ops += dp;
             const unsigned long long in = j == 0 ? fc.used_before : h->hused[j - 1];
             h->prof.bytes += (double)in + (double)h->hused[j] + 32.0 * (double)h->ntiles;
         }
     }
-    if (h->profiling && timed)             // diagonal runs: counted on the device as executed
+    if (h->profiling && timed)             // diagonal runs and scaled gates: counted on the device as executed
         h->prof.dp_ops += (double)(h->hscal->run_dp - fc.run_dp0);
     h->queue.clear();
     return QSIM_OK;
@@ -1586,15 +1618,21 @@ qsim_status qsim_set_schedule(qsim_t h, int tile_log2, int hmax, int depth) {
     h->hmax = hmax;
     h->depth = depth;
     if (tile_log2 == h->c) return QSIM_OK;
-    if (h->n > 32) return fail(h, QSIM_ERR_ARG, "re-tiling needs n <= 32");
-    size_t bytes = (size_t)16 << h->n;
+    // a basis state is encoded afresh in the new tiles; any other state is
+    // decoded into a dense buffer first
+    const bool basis = h->basis;
+    const unsigned long long bx = h->basis_x;
     double2 *d = nullptr;
-    CK(cudaMalloc(&d, bytes));
-    ++h->launches;
-    cudaError_t e = qs::launch_amplitudes(h->arena[h->cur], h->table[h->cur], h->c, 0, 1ull << h->n, d,
-                                          h->scal, grid_for(h, h->ntiles, 4), h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) { cudaFree(d); return fail(h, QSIM_ERR_CUDA, "re-tile: %s", cudaGetErrorString(e)); }
+    if (!basis) {
+        if (h->n > 32) return fail(h, QSIM_ERR_ARG, "re-tiling needs n <= 32");
+        size_t bytes = (size_t)16 << h->n;
+        CK(cudaMalloc(&d, bytes));
+        ++h->launches;
+        cudaError_t e = qs::launch_amplitudes(h->arena[h->cur], h->table[h->cur], h->c, 0, 1ull << h->n, d,
+                                              h->scal, grid_for(h, h->ntiles, 4), h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) { cudaFree(d); return fail(h, QSIM_ERR_CUDA, "re-tile: %s", cudaGetErrorString(e)); }
+    }
     free_tiles(h);
     h->c = tile_log2;
     double theta = h->theta;
@@ -1609,9 +1647,9 @@ qsim_status qsim_set_schedule(qsim_t h, int tile_log2, int hmax, int depth) {
     if (h->codec == QSIM_CODEC_AALC)
         h->cc.max_bytes = (unsigned long long)std::floor(16.0 * (double)(1ull << h->c) / theta);
     h->used = 0;
-    if ((s = alloc_tiles(h)) != QSIM_OK) { cudaFree(d); return s; }
-    s = encode_fresh(h, d, 0);
-    cudaFree(d);
+    if ((s = alloc_tiles(h)) != QSIM_OK) { if (d) cudaFree(d); return s; }
+    s = basis ? encode_fresh(h, nullptr, bx) : encode_fresh(h, d, 0);
+    if (d) cudaFree(d);
     return s;
 }
 
@@ -1878,6 +1916,7 @@ qsim_status qsim_import_tiles(qsim_t h, unsigned long long first, unsigned long 
     if (s != QSIM_OK) return s;
     if (!data || !sizes || first > h->ntiles || count > h->ntiles - first) return fail(h, QSIM_ERR_ARG, "bad tile range");
     if ((s = qsim_flush(h)) != QSIM_OK) return s;
+    h->basis = false;
     if (count == 0) return QSIM_OK;
     std::vector<unsigned long long> offs(count);
     unsigned long long tot = 0;

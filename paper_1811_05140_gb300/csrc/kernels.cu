@@ -266,6 +266,11 @@ __device__ __forceinline__ void row_eval(const double *m, unsigned long long cls
     yi = ai;
 }
 
+// both components exactly zero (either sign), by their bits (no FP64 compare)
+__device__ __forceinline__ bool zero_amp(double xr, double xi) {
+    return ((unsigned long long)(__double_as_longlong(xr) | __double_as_longlong(xi)) << 1) == 0ull;
+}
+
 // log2 of the warps of the CTA (a power of two: 4, 8 or 16 in the sweep)
 __device__ __forceinline__ int log_nwarps() { return __ffs((int)(blockDim.x >> 5)) - 1; }
 
@@ -389,7 +394,10 @@ __device__ void diag_gate_warp(double *re, double *im, int mb, const SGate &s, u
     }
 }
 
-__device__ void one_target(double *re, double *im, int mb, const SGate &s, const DGate &dg, int red) {
+// A scaled gate (s.unscaled != 0) leaves a pair of exactly-zero amplitudes
+// as it is and returns the FP64 instructions of the pairs it formed; other
+// gates return 0 (their canonical count is the host's).
+__device__ unsigned one_target(double *re, double *im, int mb, const SGate &s, const DGate &dg, int red) {
     double m[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) m[i] = dg.m[i];
@@ -406,12 +414,14 @@ __device__ void one_target(double *re, double *im, int mb, const SGate &s, const
         const unsigned lcv = s.lcv;
         if (s.unscaled) {
             // a scaled gate: d is in the sweep's scale, the rows are their sums
+            unsigned pairs = 0;
             for (unsigned f = threadIdx.x; f < cnt; f += blockDim.x) {
                 unsigned l = f << red;
                 for (int i = 0; i < nins; ++i) l = insert_zero(l, pos[i]);
                 const unsigned l0 = l | lcv;
                 const unsigned l1 = l0 | bit;
                 const double x0r = re[l0], x0i = im[l0], x1r = re[l1], x1i = im[l1];
+                if (zero_amp(x0r, x0i) && zero_amp(x1r, x1i)) continue;
                 double t0r, t0i, t1r, t1i;
                 unit_times(f0, x1r, x1i, t0r, t0i);
                 unit_times(f1, x1r, x1i, t1r, t1i);
@@ -419,8 +429,9 @@ __device__ void one_target(double *re, double *im, int mb, const SGate &s, const
                 im[l0] = __dadd_rn(x0i, t0i);
                 re[l1] = __dadd_rn(x0r, t1r);
                 im[l1] = __dadd_rn(x0i, t1i);
+                ++pairs;
             }
-            return;
+            return pairs * s.unscaled;
         }
         for (unsigned f = threadIdx.x; f < cnt; f += blockDim.x) {
             unsigned l = f << red;
@@ -436,22 +447,30 @@ __device__ void one_target(double *re, double *im, int mb, const SGate &s, const
             re[l1] = __dmul_rn(d1, __dadd_rn(x0r, t1r));
             im[l1] = __dmul_rn(d1, __dadd_rn(x0i, t1i));
         }
-        return;
+        return 0;
     }
+    unsigned groups = 0;
     for (unsigned f = threadIdx.x; f < cnt; f += blockDim.x) {
         unsigned l0 = deposit(f << red, s) | s.lcv;
         unsigned l1 = l0 | bit;
         double xr[2] = {re[l0], re[l1]}, xi[2] = {im[l0], im[l1]};
+        if (s.unscaled) {
+            if (zero_amp(xr[0], xi[0]) && zero_amp(xr[1], xi[1])) continue;
+            ++groups;
+        }
         double y0r, y0i, y1r, y1i;
         row_eval<2>(m, s.cls, s.fac, 0, xr, xi, y0r, y0i, s.unscaled);
         row_eval<2>(m, s.cls, s.fac, 1, xr, xi, y1r, y1i, s.unscaled);
         re[l0] = y0r; im[l0] = y0i;
         re[l1] = y1r; im[l1] = y1i;
     }
+    return groups * s.unscaled;
 }
 
-__device__ void two_target(double *re, double *im, int mb, const SGate &s, const DGate &dg, int red) {
+// As one_target, for gates on two targets.
+__device__ unsigned two_target(double *re, double *im, int mb, const SGate &s, const DGate &dg, int red) {
     const unsigned cnt = 1u << (mb - s.nins - red);
+    unsigned groups = 0;
     for (unsigned f = threadIdx.x; f < cnt; f += blockDim.x) {
         unsigned l = deposit(f << red, s) | s.lcv;
         unsigned idx[4];
@@ -462,12 +481,19 @@ __device__ void two_target(double *re, double *im, int mb, const SGate &s, const
             xr[q] = re[idx[q]];
             xi[q] = im[idx[q]];
         }
+        if (s.unscaled) {
+            if (zero_amp(xr[0], xi[0]) && zero_amp(xr[1], xi[1]) && zero_amp(xr[2], xi[2]) &&
+                zero_amp(xr[3], xi[3]))
+                continue;
+            ++groups;
+        }
         double yr[4], yi[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) row_eval<4>(dg.m, s.cls, s.fac, r, xr, xi, yr[r], yi[r], s.unscaled);
 #pragma unroll
         for (int q = 0; q < 4; ++q) { re[idx[q]] = yr[q]; im[idx[q]] = yi[q]; }
     }
+    return groups * s.unscaled;
 }
 
 // tile index of an item: zero bits inserted at the tile-index positions
@@ -612,7 +638,8 @@ struct RunMember {
 
 // One diagonal run applied to an item buffer (every thread calls it).
 // red > 0: one amplitude per tile (uniform items; such sweeps have no local
-// gates).  Returns the FP64 instructions this thread executed.
+// gates).  An amplitude that is exactly zero is left as it is.  Returns the
+// FP64 instructions this thread executed.
 __device__ unsigned apply_run(double *re, double *im, int c, int h, int red, const DRun &R,
                               const SweepParams &P, unsigned long long T, const int *hb, RunMember *mem) {
     const int ntl = 1 << h, N = 1 << c;
@@ -666,6 +693,9 @@ __device__ unsigned apply_run(double *re, double *im, int c, int h, int red, con
             }
             xl |= m.pin_val;
         }
+        const unsigned l = ((unsigned)j << c) | xl;
+        double xr = re[l], xi = im[l];
+        if (zero_amp(xr, xi)) continue;             // a zero stays as it is
         bool have_l = false;
         double lr = 0.0, li = 0.0;
         unsigned k = m.k_t;
@@ -687,8 +717,6 @@ __device__ unsigned apply_run(double *re, double *im, int c, int h, int red, con
         }
         const bool have_t = m.have_t;
         if (!have_t && !have_l && (k & 3u) == 0u) continue;
-        const unsigned l = ((unsigned)j << c) | xl;
-        double xr = re[l], xi = im[l];
         if (have_t || have_l) {
             double gr = have_t ? m.tr : lr, gi = have_t ? m.ti : li;
             if (have_t && have_l) { cmul(m.tr, m.ti, lr, li, gr, gi); ops += 4; }
@@ -712,7 +740,7 @@ __device__ unsigned apply_run(double *re, double *im, int c, int h, int red, con
 // A gate that starts a diagonal run (SGate::run >= 0) applies the whole run
 // (apply_run); the run's other gates carry no activity bit (the sweep
 // kernel moves the run's activity onto its first gate).  Returns the FP64
-// instructions this thread executed in diagonal runs.
+// instructions this thread executed in diagonal runs and scaled gates.
 __device__ __noinline__ unsigned apply_gates(double *re, double *im, int mb, int red, const SGate *gsrc, SGate *sg,
                             int *chunk, const DGate *dg, int ngates, const unsigned *act,
                             unsigned long long fixed, const SweepParams &P, const int *hb, RunMember *mem) {
@@ -758,8 +786,8 @@ __device__ __noinline__ unsigned apply_gates(double *re, double *im, int mb, int
             }
             if (dirty) { __syncthreads(); dirty = false; }
             if (s.kind == 0) diag_gate(re, im, mb, s, fixed, red);
-            else if (s.kind == 1) one_target(re, im, mb, s, dg[g], red);
-            else two_target(re, im, mb, s, dg[g], red);
+            else if (s.kind == 1) run_ops += one_target(re, im, mb, s, dg[g], red);
+            else run_ops += two_target(re, im, mb, s, dg[g], red);
             __syncthreads();
         }
     }

@@ -34,7 +34,7 @@ struct DevScalars {
     unsigned long long hist[MAX_LEVELS];
     unsigned long long items_done, items_skipped;
     unsigned long long work;        // item counter of the sweep launch in flight
-    unsigned long long run_dp;      // FP64 instructions executed by diagonal runs (running total)
+    unsigned long long run_dp;      // FP64 instructions executed by diagonal runs and scaled gates (running total)
     unsigned long long over_limit;  // tiles written above the ratio threshold's size (no level met it)
 };
 
@@ -64,7 +64,8 @@ struct SGate {
     uint8_t nins;                   // buffer bits pinned by targets and local controls
     uint8_t ins[12];                // those bits, ascending
     int16_t run;                    // >= 0: first gate of diagonal run `run`; -2 inside a run; -1 none
-    uint8_t unscaled;               // scaled gate: factored rows give their sums, d is in the sweep's scale
+    uint8_t unscaled;               // scaled gate (nonzero): factored rows give their sums, d is in the
+                                    // sweep's scale; the value is the FP64 instructions of one group
 };
 
 // Entry classes of a matrix entry u, decided on the host so that device
@@ -87,7 +88,8 @@ constexpr int MAX_SWEEP_GATES = 512;    // gates per sweep (depth limit)
 // contribute their entry at x's target sub-index; entries exactly 1
 // contribute nothing, entries -1, i, -i are collected as i^k, the other
 // entries are multiplied in gate order into T (gates on qubits >= c only,
-// constant over a tile) and L (the rest); a <- i^k * ((T*L) a).
+// constant over a tile) and L (the rest); a <- i^k * ((T*L) a).  An
+// amplitude that is exactly zero is left as it is.
 
 // A diagonal gate of a run, with its entries classified on the host.
 struct RGate {

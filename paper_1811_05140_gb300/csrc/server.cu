@@ -2,9 +2,12 @@
 //
 // A host thread owns every GPU-side object.  Requests (circuits) arrive at
 // any time through qsim_server_submit; the loop admits waiting requests
-// while the measured device footprint of the resident circuits plus the new
-// circuit's initial footprint stays inside the memory budget (not their
-// 2^(n+4)-byte uncompressed size), then runs one tick: the next few sweeps
+// while the reservations of the resident circuits plus the new circuit's
+// stay inside the memory budget (not their 2^(n+4)-byte uncompressed
+// size).  A circuit's reservation is the larger of its measured device
+// footprint and its growth bound: tables plus two arenas of the codec's
+// stream bound (for AALC the ratio threshold's 16 * 2^n / theta bytes).
+// Then it runs one tick: the next few sweeps
 // of every resident circuit (cut at the circuit's own sweep boundaries, so
 // each pass is exactly the one it would run alone) as one batched flush
 // (qsim_flush_batch), so circuits that arrived meanwhile join at the next
@@ -27,6 +30,7 @@
 #include "qsim.h"
 
 unsigned long long qs_handle_footprint(qsim_t h);
+unsigned long long qs_stream_bound(int n, int c, int codec, double eps, double theta);
 
 namespace {
 
@@ -78,15 +82,37 @@ struct qsim_server {
 
 namespace {
 
+int tile_log2_of(const qsim_request &r) {
+    return r.tile_log2 ? r.tile_log2 : std::min(std::min(r.block_log2, r.n_qubits), 8);
+}
+
 // initial device bytes of a fresh state (tables, norm partials, two arenas)
 unsigned long long initial_footprint(const qsim_request &r) {
-    int c = r.tile_log2 ? r.tile_log2 : std::min(std::min(r.block_log2, r.n_qubits), 8);
+    int c = tile_log2_of(r);
     unsigned long long ntiles = 1ull << (r.n_qubits - c);
     unsigned long long tile = 32ull + (16ull << c);
     unsigned long long a0 = ntiles * 32ull + tile;
     unsigned long long a1 = std::max<unsigned long long>(a0 + a0 / 4 + (1ull << 20), 1ull << 22);
     a0 = std::max<unsigned long long>(a0, 1ull << 22);
     return ntiles * 32ull + a0 + a1;
+}
+
+// growth bound of a circuit: tables and norm partials plus two arenas
+// (2 MiB granules, 4 MiB at least) of the codec's stream bound
+unsigned long long growth_bound(const qsim_request &r) {
+    const int c = tile_log2_of(r);
+    const unsigned long long ntiles = 1ull << (r.n_qubits - c);
+    const unsigned long long sb = qs_stream_bound(r.n_qubits, c, r.codec, r.rel_err_bound, r.theta);
+    const unsigned long long arena = std::max<unsigned long long>((sb + (2ull << 20) - 1) & ~((2ull << 20) - 1),
+                                                                  4ull << 20);
+    return ntiles * 32ull + 2ull * arena;
+}
+
+// bytes a circuit holds or may grow to: the larger of its measured
+// footprint (initial before admission) and its growth bound
+unsigned long long reservation(const qsim_request &r, qsim_t h) {
+    const unsigned long long now = h ? qs_handle_footprint(h) : initial_footprint(r);
+    return std::max(now, growth_bound(r));
 }
 
 void finish(qsim_server *S, Req *q, int status) {
@@ -169,16 +195,16 @@ void qsim_server::loop() {
             std::unique_lock<std::mutex> lk(m);
             cv_work.wait(lk, [&] { return stop || !waiting.empty() || !resident.empty(); });
             if (stop && waiting.empty() && resident.empty()) return;
-            // admission by measured footprint: resident circuits' current
-            // device bytes plus the newcomer's initial bytes, with a quarter
-            // of the budget kept free for the residents' growth
+            // admission by reservation: every resident circuit's measured
+            // footprint or growth bound, whichever is larger, plus the
+            // newcomer's; a circuit alone is always admitted
             unsigned long long fp = 0;
-            for (Req *q : resident) fp += qs_handle_footprint(q->h);
+            for (Req *q : resident) fp += reservation(q->r, q->h);
             while (!waiting.empty() && (int)(resident.size() + admitted.size()) < max_resident) {
                 Req *q = waiting.front();
-                const unsigned long long need = initial_footprint(q->r);
+                const unsigned long long need = reservation(q->r, nullptr);
                 const bool empty = resident.empty() && admitted.empty();
-                if (!empty && fp + need > budget - budget / 4) break;
+                if (!empty && fp + need > budget) break;
                 waiting.pop_front();
                 admitted.push_back(q);
                 fp += need;

@@ -53,3 +53,27 @@ def test_every_sweep_shape_matches_oracle(threads):
         cs.reset_basis(x)
         cs.run(gates, 4, 512)
         assert all(s == cs.stream(t) for t, s in enumerate(st.export_tiles()))
+
+
+def test_retiling_a_basis_state_encodes_it_afresh():
+    # a 33-qubit basis state (2^37 bytes dense, beyond the dense re-tiling
+    # path) re-tiles from 2^8 to 2^7 amplitudes per tile: its streams equal
+    # those of a state created with 2^7-amplitude tiles; once a gate has run
+    # the state is no longer a basis state and re-tiling needs n <= 32
+    n, eps = 33, 1e-4
+    x = I.seeded_basis(n, 3)
+    st = qsim.State(n, 8, "rel", eps)
+    st.reset_basis(x)
+    st.set_schedule(7, 4, 512)
+    ref = qsim.State(n, 7, "rel", eps)
+    ref.reset_basis(x)
+    tiles = [0, 1, x >> 7, (x >> 7) ^ 1, (1 << (n - 7)) - 1]
+    assert st.export_tile_set(tiles) == ref.export_tile_set(tiles)
+    assert st.stats()["tile_log2"] == 7
+    ref.close()
+    st.apply(I.h(0))
+    st.flush()
+    with pytest.raises(qsim.QsimError) as e:
+        st.set_schedule(8, 4, 512)
+    assert e.value.status == 1
+    st.close()

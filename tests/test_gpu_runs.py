@@ -146,10 +146,10 @@ def test_gate_by_gate_mode_matches_unfused_oracle():
 
 def test_profile_counts_run_arithmetic():
     # QFT-12 on 2^8 tiles: the FP64 count the profile reports is the
-    # canonical count of the non-run gates and normalize plus what the runs
-    # execute (per visited amplitude 4 for G a, 4 more for T*L, and the
-    # table and tile products): 78 against 116 per amplitude gate by gate
-    # (12 Hadamards cost 48 of either)
+    # canonical count of the gates outside runs and scaled gates, plus what
+    # the runs and scaled gates execute on the device (per visited nonzero
+    # amplitude 4 for G a, 4 more for T*L, the table and tile products; per
+    # formed Hadamard pair 4): below three quarters of the gate-by-gate count
     n, c = 12, 8
     x = I.seeded_basis(n)
     gates = I.qft(n)

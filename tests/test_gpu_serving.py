@@ -1,13 +1,15 @@
 """Serving loop (qsim_server_*): continuous batching of circuits of uneven
 sizes.  Every circuit's read-out must equal the same circuit run alone
-(bit for bit), admission must respect the memory budget, and circuits that
-arrive while others run must be admitted and finished.
+(bit for bit) and the oracle's exact probabilities of the same compressed
+run, admission must respect the memory budget, and circuits that arrive
+while others run must be admitted and finished.
 """
 import time
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_1811_05140_gb300 import inputs as I
 from paper_1811_05140_gb300 import qsim
 
@@ -18,6 +20,7 @@ pytestmark = pytest.mark.gpu
 def built():
     from paper_1811_05140_gb300 import build
     build.build()
+    oracle.build()
 
 
 def mix(count, seed, nmin=6, nmax=14):
@@ -92,4 +95,47 @@ def test_graph_captured_ticks_give_the_same_results():
     srv.drain(600)
     for job, t in zip(jobs, tickets):
         assert np.array_equal(srv.result(t)[1], alone(job))
+    srv.close()
+
+
+def oracle_probs(job):
+    """The oracle's read-out of a job: the compressed run with the library's
+    default schedule for the job's size (tile 2^min(8, n), its pair slots and
+    depth), then the exact sums of |a|^2 per read-out pattern, divided by
+    the exact total (the library's definition)."""
+    n, gates, x, eps, readout = job
+    c = min(8, n)
+    probe = qsim.State(n, 8, "rel", eps)
+    s = probe.stats()
+    probe.close()
+    cs = oracle.CSim(n, c, [oracle.shift_for_eps(eps)], None, True)
+    cs.reset_basis(x)
+    cs.run(gates, s["hmax"], s["depth"])
+    psi = cs.dense()
+    idx = np.arange(1 << n)
+    key = np.zeros(1 << n, dtype=np.int64)
+    for i, q in enumerate(readout):
+        key |= ((idx >> q) & 1) << i
+    S = [oracle.sum_sq_units(psi[key == j]) for j in range(1 << len(readout))]
+    tot = oracle.units_to_double(sum(S))
+    return np.array([oracle.units_to_double(v) / tot for v in S])
+
+
+def test_mix_results_equal_the_oracle():
+    # a mix of QFT, Grover and grid circuits of 5..12 qubits at both
+    # bounds, served together (arrivals spread over the first ticks): every
+    # read-out is bit-identical to the oracle's exact probabilities
+    jobs = mix(18, 2024, 5, 12)
+    srv = qsim.Server(2 << 30, max_resident=8, sweeps_per_tick=1)
+    tickets = []
+    for k, (n, gates, x, eps, readout) in enumerate(jobs):
+        tickets.append(srv.submit(n, gates, eps=eps, basis=x, readout=readout))
+        if k % 4 == 3:
+            time.sleep(0.005)
+    srv.drain(600)
+    assert srv.stats()["completed"] == len(jobs)
+    for job, t in zip(jobs, tickets):
+        info, probs = srv.result(t)
+        assert info["status"] == 0
+        assert np.array_equal(probs, oracle_probs(job)), job[0]
     srv.close()
