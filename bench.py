@@ -130,21 +130,59 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def traffic_from_profile():
-    """Per-launch DRAM bytes of the sweep kernel from the committed ncu
-    summary, when it was taken on the current kernel source."""
+def profile_figures():
+    """Per-launch DRAM bytes and warp instructions of the sweep kernel from
+    the committed ncu summary, when it was taken on the current kernel
+    source: ({"traffic": bytes, "warp_inst": count}, note)."""
     try:
         text = open(PROFILE_FILE).read()
     except OSError:
-        return None, None
+        return {}, "no ncu summary"
     m = re.search(r"kernels\.cu sha256:\s*([0-9a-f]{64})", text)
     t = re.search(r"dram bytes per full-size launch:\s*([0-9.eE+]+)", text)
+    w = re.search(r"warp instructions per full-size launch:\s*([0-9.eE+]+)", text)
     if not m or not t:
-        return None, None
+        return {}, "no per-launch figures in the ncu summary"
     cur = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
     if cur != m.group(1):
-        return None, "kernel changed since the ncu capture"
-    return float(t.group(1)), None
+        return {}, "kernel changed since the ncu capture"
+    out = {"traffic": float(t.group(1))}
+    if w:
+        out["warp_inst"] = float(w.group(1))
+    return out, None
+
+
+ISSUE_PER_CLK = 4 * 152                     # warp instructions per clock: 4 schedulers x 152 SMs
+
+
+def roofline_line(figs, per_launch_s, fp64_tflops, fp64_meas, traffic, hbm_gbs, hbm_peak, hbm_measured,
+                  clocks):
+    """Roofline of the sweep kernel.  The kernel is bound by instruction
+    issue and latency (integer codec and gate loops, FP64 mostly idle), so
+    the top-level figure is the issue rate: warp instructions per launch
+    (the committed ncu count, while it matches the kernel source) over the
+    live launch time, against one warp instruction per scheduler and clock
+    at the maximum SM clock.  The executed FP64 work and the DRAM bytes
+    give the two other rooflines beside it."""
+    fp64 = {"achieved": fp64_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": fp64_tflops / FP64_PEAK_TFLOPS, "counts": "FP64 instructions executed (FMA-slot flops)",
+            "measured_peak": fp64_meas, "frac_of_measured": fp64_tflops / fp64_meas}
+    hbm = {"achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak,
+           "peak_source": "measured" if hbm_measured else "fallback"}
+    line = {"kernel": "sweep_kernel", "per_launch_ms": per_launch_s * 1e3, "traffic": traffic,
+            "fp64": fp64, "hbm": hbm}
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    if "warp_inst" in figs and per_launch_s > 0:
+        peak = ISSUE_PER_CLK * mhz * 1e6 / 1e12
+        ach = figs["warp_inst"] / per_launch_s / 1e12
+        line.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "Twarp-inst/s", "frac": ach / peak,
+                     "counts": "warp instructions issued per launch (ncu summary) over the live launch time",
+                     "peak_source": "4 schedulers x 152 SMs x max SM clock"})
+    else:
+        line.update({"bound": "alu", "achieved": fp64_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": fp64_tflops / FP64_PEAK_TFLOPS, "counts": "FP64 instructions executed",
+                     "peak_source": "nominal FP64; FMA-slot flops"})
+    return line
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -833,7 +871,8 @@ def main():
         hbm_gbs = prof["bytes"] / sweep_s / 1e9 if sweep_s > 0 else 0.0
         peaks = measured_peaks()
         hbm_peak = peaks.get("hbm_gbs", 6800.0)
-        traffic, why = traffic_from_profile()
+        figs, why = profile_figures()
+        traffic = figs.get("traffic")
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             # each sample sized for about 8 s of CPU work (1 thread, all cores)
@@ -856,15 +895,8 @@ def main():
             "hbm_frac": hbm_gbs / hbm_peak,
             # every sweep reads and writes the whole logical state (16 B per amplitude each way)
             "logical_gbs": 32.0 * 2.0 ** n * launches / sweep_s / 1e9 if sweep_s > 0 else None,
-            "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
-                         "traffic": traffic,
-                         "kernel": "sweep_kernel", "per_launch_ms": per_launch_s * 1e3,
-                         "peak_source": "nominal FP64 (no measured FP64 peak in the peaks file); FMA-slot flops",
-                         "fp64_measured_tflops": res["fp64_tflops"],
-                         "frac_of_measured_fp64": achieved_tflops / res["fp64_tflops"],
-                         "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": hbm_peak,
-                         "hbm_peak_source": "measured" if "hbm_gbs" in peaks else "fallback"},
+            "roofline": roofline_line(figs, per_launch_s, achieved_tflops, res["fp64_tflops"], traffic,
+                                      hbm_gbs, hbm_peak, "hbm_gbs" in peaks, res["clocks"]),
             "gpu_launches": res["launches"],
             "clocks": res["clocks"],
         }

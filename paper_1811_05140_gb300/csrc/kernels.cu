@@ -403,6 +403,17 @@ __device__ unsigned one_target(double *re, double *im, int mb, const SGate &s, c
     for (int i = 0; i < 8; ++i) m[i] = dg.m[i];
     const unsigned bit = 1u << s.p0;
     const unsigned cnt = 1u << (mb - s.nins - red);
+    if ((s.cls & 0xFFFull) == ((unsigned long long)EC_ONE << 3 | (unsigned long long)EC_ONE << 6)) {
+        // X (entries 0 1 / 1 0, exactly): the pair is exchanged, the copies
+        // the rows would make
+        for (unsigned f = threadIdx.x; f < cnt; f += blockDim.x) {
+            const unsigned l0 = deposit(f << red, s) | s.lcv, l1 = l0 | bit;
+            const double ar = re[l0], ai = im[l0], br = re[l1], bi = im[l1];
+            re[l0] = br; im[l0] = bi;
+            re[l1] = ar; im[l1] = ai;
+        }
+        return 0;
+    }
     if ((s.fac & 3ull) == 3ull && (s.cls & 7ull) == EC_REAL && ((s.cls >> 6) & 7ull) == EC_REAL) {
         // both rows factored with a real first entry (Hadamard-like):
         // y_r = d_r (x_0 + f_r x_1), the same arithmetic as row_eval
@@ -470,6 +481,44 @@ __device__ unsigned one_target(double *re, double *im, int mb, const SGate &s, c
 // As one_target, for gates on two targets.
 __device__ unsigned two_target(double *re, double *im, int mb, const SGate &s, const DGate &dg, int red) {
     const unsigned cnt = 1u << (mb - s.nins - red);
+    // a permutation (SWAP; X on one target controlled by the other): every
+    // row one entry exactly 1 and the others exactly 0; row r copies x[src r]
+    unsigned src = 0, moved = 0;
+    bool perm = true;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        int ones = 0, zeros = 0, at = 0;
+#pragma unroll
+        for (int c2 = 0; c2 < 4; ++c2) {
+            const unsigned code = (unsigned)(s.cls >> (3 * (r * 4 + c2))) & 7u;
+            if (code == EC_ONE) { ++ones; at = c2; }
+            else if (code == EC_ZERO) ++zeros;
+        }
+        perm &= ones == 1 && zeros == 3;
+        src |= (unsigned)at << (2 * r);
+        if (at != r) moved |= 1u << r;
+    }
+    if (perm) {
+        for (unsigned f = threadIdx.x; f < cnt && moved; f += blockDim.x) {
+            const unsigned l = deposit(f << red, s) | s.lcv;
+            unsigned idx[4];
+            double xr[4], xi[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                idx[q] = l | ((unsigned)(q & 1) << s.p0) | ((unsigned)(q >> 1) << s.p1);
+                xr[q] = re[idx[q]];
+                xi[q] = im[idx[q]];
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if (!((moved >> r) & 1u)) continue;
+                const unsigned q = (src >> (2 * r)) & 3u;
+                re[idx[r]] = q == 0 ? xr[0] : q == 1 ? xr[1] : q == 2 ? xr[2] : xr[3];
+                im[idx[r]] = q == 0 ? xi[0] : q == 1 ? xi[1] : q == 2 ? xi[2] : xi[3];
+            }
+        }
+        return 0;
+    }
     unsigned groups = 0;
     for (unsigned f = threadIdx.x; f < cnt; f += blockDim.x) {
         unsigned l = deposit(f << red, s) | s.lcv;
