@@ -1229,6 +1229,19 @@ qs::SweepParams sweep_params(qsim_t h, const FlushCtx &fc, size_t j) {
         if (!is_permutation(g)) p.moves_tiles = 0;
     }
     p.moves_tiles &= p.low_free;
+    // point items (every tile zero but for one amplitude at a common index,
+    // the zeros +0): the sweep's gates leave the zeros as they are when each
+    // is a member of a diagonal run, a scaled gate or a permutation, and the
+    // mixing ones act on qubits >= c only
+    p.point_ok = h->fuse && !fc.in_run.empty();
+    for (int gi = sw.lo; gi < sw.hi && p.point_ok; ++gi) {
+        if (fc.in_run[gi]) continue;
+        const HostGate &g = h->queue[gi];
+        bool high = !(g.cm & lowm);
+        for (int i = 0; i < g.k; ++i)
+            if (g.t[i] < h->c) high = false;
+        if (!high || !(fc.scaled[gi] || is_permutation(g))) p.point_ok = 0;
+    }
     if (const int ut = unit_tiles_log2(h)) {
         // every stride is decided and re-encoded as a whole
         p.every_item = 1;

@@ -271,6 +271,33 @@ __device__ __forceinline__ bool zero_amp(double xr, double xi) {
     return ((unsigned long long)(__double_as_longlong(xr) | __double_as_longlong(xi)) << 1) == 0ull;
 }
 
+// Point items: every member tile exactly +0 (all bits clear) but for at
+// most one amplitude, at a tile index p common to the tiles.  Scans a
+// decoded tile (warp-wide; the warp wrote it) and merges into the item's
+// state: *pos the common index (-1: none seen yet), *bad set when a tile
+// holds two such amplitudes or the tiles disagree.
+__device__ __forceinline__ void point_scan(const double *re, const double *im, int N, int *pos, int *bad) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    unsigned cnt = 0;
+    int at = -1;
+    for (int b = 0; b < N; b += 32) {
+        const int i = b + lane;
+        const bool v = i < N && (unsigned long long)(__double_as_longlong(re[i]) | __double_as_longlong(im[i])) != 0ull;
+        const unsigned bal = __ballot_sync(FULL, v);
+        cnt += (unsigned)__popc(bal);
+        if (bal) at = b + 31 - __clz(bal);
+    }
+    if (lane == 0 && cnt) {
+        if (cnt > 1) {
+            atomicOr(bad, 1);
+        } else {
+            const int old = atomicCAS(pos, -1, at);
+            if (old != -1 && old != at) atomicOr(bad, 1);
+        }
+    }
+}
+
 // log2 of the warps of the CTA (a power of two: 4, 8 or 16 in the sweep)
 __device__ __forceinline__ int log_nwarps() { return __ffs((int)(blockDim.x >> 5)) - 1; }
 
@@ -303,7 +330,7 @@ __device__ __forceinline__ bool gate_active(const SGate &s, unsigned long long f
 // entry other than exactly 1.  Enumerating just those keeps every lane of
 // every FP64 instruction busy (masked lanes cost the same on this part).
 __device__ void diag_gate(double *re, double *im, int mb, const SGate &s,
-                          unsigned long long fixed, int red) {
+                          unsigned long long fixed, int red, unsigned roff) {
     // sub-indices r to visit: entry != 1 and consistent with fixed targets
     unsigned rpack = 0;          // sub-indices, 2 bits each
     int nr = 0;
@@ -318,7 +345,7 @@ __device__ void diag_gate(double *re, double *im, int mb, const SGate &s,
     const unsigned cnt = (unsigned)nr << fb;
     for (unsigned f = threadIdx.x; f < cnt; f += blockDim.x) {
         int r = (int)((rpack >> (2 * (f >> fb))) & 3u);
-        unsigned l = deposit((f & ((1u << fb) - 1u)) << red, s) | s.lcv;
+        unsigned l = deposit((f & ((1u << fb) - 1u)) << red, s) | s.lcv | roff;
         if (s.p0 >= 0) l |= (unsigned)(r & 1) << s.p0;
         if (s.k > 1 && s.p1 >= 0) l |= (unsigned)((r >> 1) & 1) << s.p1;
         unsigned code = (unsigned)(s.cls >> (3 * r)) & 7u;
@@ -397,7 +424,8 @@ __device__ void diag_gate_warp(double *re, double *im, int mb, const SGate &s, u
 // A scaled gate (s.unscaled != 0) leaves a pair of exactly-zero amplitudes
 // as it is and returns the FP64 instructions of the pairs it formed; other
 // gates return 0 (their canonical count is the host's).
-__device__ unsigned one_target(double *re, double *im, int mb, const SGate &s, const DGate &dg, int red) {
+__device__ unsigned one_target(double *re, double *im, int mb, const SGate &s, const DGate &dg, int red,
+                               unsigned roff) {
     double m[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) m[i] = dg.m[i];
@@ -407,7 +435,7 @@ __device__ unsigned one_target(double *re, double *im, int mb, const SGate &s, c
         // X (entries 0 1 / 1 0, exactly): the pair is exchanged, the copies
         // the rows would make
         for (unsigned f = threadIdx.x; f < cnt; f += blockDim.x) {
-            const unsigned l0 = deposit(f << red, s) | s.lcv, l1 = l0 | bit;
+            const unsigned l0 = deposit(f << red, s) | s.lcv | roff, l1 = l0 | bit;
             const double ar = re[l0], ai = im[l0], br = re[l1], bi = im[l1];
             re[l0] = br; im[l0] = bi;
             re[l1] = ar; im[l1] = ai;
@@ -422,7 +450,7 @@ __device__ unsigned one_target(double *re, double *im, int mb, const SGate &s, c
         const int nins = s.nins;
         uint8_t pos[12];
         for (int i = 0; i < nins; ++i) pos[i] = s.ins[i];
-        const unsigned lcv = s.lcv;
+        const unsigned lcv = s.lcv | roff;
         if (s.unscaled) {
             // a scaled gate: d is in the sweep's scale, the rows are their sums
             unsigned pairs = 0;
@@ -462,7 +490,7 @@ __device__ unsigned one_target(double *re, double *im, int mb, const SGate &s, c
     }
     unsigned groups = 0;
     for (unsigned f = threadIdx.x; f < cnt; f += blockDim.x) {
-        unsigned l0 = deposit(f << red, s) | s.lcv;
+        unsigned l0 = deposit(f << red, s) | s.lcv | roff;
         unsigned l1 = l0 | bit;
         double xr[2] = {re[l0], re[l1]}, xi[2] = {im[l0], im[l1]};
         if (s.unscaled) {
@@ -479,7 +507,8 @@ __device__ unsigned one_target(double *re, double *im, int mb, const SGate &s, c
 }
 
 // As one_target, for gates on two targets.
-__device__ unsigned two_target(double *re, double *im, int mb, const SGate &s, const DGate &dg, int red) {
+__device__ unsigned two_target(double *re, double *im, int mb, const SGate &s, const DGate &dg, int red,
+                               unsigned roff) {
     const unsigned cnt = 1u << (mb - s.nins - red);
     // a permutation (SWAP; X on one target controlled by the other): every
     // row one entry exactly 1 and the others exactly 0; row r copies x[src r]
@@ -500,7 +529,7 @@ __device__ unsigned two_target(double *re, double *im, int mb, const SGate &s, c
     }
     if (perm) {
         for (unsigned f = threadIdx.x; f < cnt && moved; f += blockDim.x) {
-            const unsigned l = deposit(f << red, s) | s.lcv;
+            const unsigned l = deposit(f << red, s) | s.lcv | roff;
             unsigned idx[4];
             double xr[4], xi[4];
 #pragma unroll
@@ -521,7 +550,7 @@ __device__ unsigned two_target(double *re, double *im, int mb, const SGate &s, c
     }
     unsigned groups = 0;
     for (unsigned f = threadIdx.x; f < cnt; f += blockDim.x) {
-        unsigned l = deposit(f << red, s) | s.lcv;
+        unsigned l = deposit(f << red, s) | s.lcv | roff;
         unsigned idx[4];
         double xr[4], xi[4];
 #pragma unroll
@@ -689,17 +718,31 @@ struct RunMember {
 // red > 0: one amplitude per tile (uniform items; such sweeps have no local
 // gates).  An amplitude that is exactly zero is left as it is.  Returns the
 // FP64 instructions this thread executed.
-__device__ unsigned apply_run(double *re, double *im, int c, int h, int red, const DRun &R,
-                              const SweepParams &P, unsigned long long T, const int *hb, RunMember *mem) {
+__device__ unsigned apply_run(double *re, double *im, int c, int h, int red, const DRun &Rg,
+                              const SweepParams &P, unsigned long long T, const int *hb, RunMember *mem,
+                              uint32_t *stage, int stage_words, unsigned roff) {
+    const DRun R = Rg;                             // in registers: one load of the descriptor
     const int ntl = 1 << h, N = 1 << c;
     unsigned ops = 0;
+    // the run's tile gates copied to shared memory by the whole CTA (stage:
+    // the encoder's packing area, idle while gates run), so that the member
+    // products below walk them without a global load per gate
+    const int nt = R.nt, tg = R.tg;
+    const int nst = min(nt, stage_words / (int)(sizeof(RGate) / 4));
+    {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(P.rgates + tg);
+        const int words = nst * (int)(sizeof(RGate) / 4);
+        for (int i = threadIdx.x; i < words; i += blockDim.x) stage[i] = src[i];
+    }
+    __syncthreads();
     if ((int)threadIdx.x < ntl) {
         const int j = threadIdx.x;
         const unsigned long long xb = member_tile(T, j, h, hb) << c;
         bool have = false;
         double tr = 0.0, ti = 0.0;
         unsigned k = 0;
-        ops += run_factor(P.rgates + R.tg, R.nt, xb, have, tr, ti, k);
+        ops += run_factor(reinterpret_cast<const RGate *>(stage), nst, xb, have, tr, ti, k);
+        ops += run_factor(P.rgates + tg + nst, nt - nst, xb, have, tr, ti, k);
         unsigned kap = 0;
         for (int i = 0; i < R.nq; ++i) kap |= (unsigned)((xb >> R.q[i]) & 1ull) << i;
         RunMember m;
@@ -711,7 +754,7 @@ __device__ unsigned apply_run(double *re, double *im, int c, int h, int red, con
         m.pin_mask = 0;
         m.pin_val = 0;
         const bool tile_part = have || (k & 3u);
-        if (red) m.count = tile_part ? 1u : 0u;
+        if (red) m.count = (tile_part || R.nl) ? 1u : 0u;
         else if (tile_part) m.count = (uint32_t)N;
         else if (R.nl == 0) m.count = 0;
         else if (!R.tabled) m.count = (uint32_t)N;
@@ -730,7 +773,7 @@ __device__ unsigned apply_run(double *re, double *im, int c, int h, int red, con
         while (j < ntl && w >= base + mem[j].count) { base += mem[j].count; ++j; }
         if (j >= ntl) break;
         const RunMember &m = mem[j];
-        unsigned f = w - base, xl = 0;
+        unsigned f = w - base, xl = roff;
         if (!red) {
             // deposit f into the tile bits outside pin_mask, pinned bits from pin_val
             unsigned pm = m.pin_mask;
@@ -748,7 +791,7 @@ __device__ unsigned apply_run(double *re, double *im, int c, int h, int red, con
         bool have_l = false;
         double lr = 0.0, li = 0.0;
         unsigned k = m.k_t;
-        if (R.nl && !red) {
+        if (R.nl) {
             if (R.tabled) {
                 const unsigned long long e = R.table + (unsigned long long)m.kap * N + xl;
                 const unsigned mt = P.rmeta[e];
@@ -783,16 +826,17 @@ __device__ unsigned apply_run(double *re, double *im, int c, int h, int red, con
 // act: bit g set when gate g changes something in this item.  The compact
 // gates are staged in shared memory GATE_CHUNK at a time (*chunk = first
 // gate staged, -1 none); chunks without an active gate are not staged.
-// red > 0: only the amplitudes whose low `red` index bits are 0 (one per
-// tile, for an item of uniform tiles under gates that touch no low qubit).
-// CTA-wide; every thread must call it.
+// red > 0: one amplitude per tile, at tile index roff (uniform items: 0,
+// gates that touch no low qubit; point items: the common index of the
+// tiles' one nonzero amplitude).  CTA-wide; every thread must call it.
 // A gate that starts a diagonal run (SGate::run >= 0) applies the whole run
 // (apply_run); the run's other gates carry no activity bit (the sweep
 // kernel moves the run's activity onto its first gate).  Returns the FP64
 // instructions this thread executed in diagonal runs and scaled gates.
 __device__ __noinline__ unsigned apply_gates(double *re, double *im, int mb, int red, const SGate *gsrc, SGate *sg,
                             int *chunk, const DGate *dg, int ngates, const unsigned *act,
-                            unsigned long long fixed, const SweepParams &P, const int *hb, RunMember *mem) {
+                            unsigned long long fixed, const SweepParams &P, const int *hb, RunMember *mem,
+                            uint32_t *stage, int stage_words, unsigned roff) {
     const bool warp_parts = red == 0 && mb - log_nwarps() >= 5;
     unsigned run_ops = 0;
     bool dirty = false;                              // warp-local gates since the last CTA barrier
@@ -822,7 +866,8 @@ __device__ __noinline__ unsigned apply_gates(double *re, double *im, int mb, int
             if (s.run != -1) {
                 if (s.run < 0) continue;            // inside a run: applied with its first gate
                 if (dirty) { __syncthreads(); dirty = false; }
-                run_ops += apply_run(re, im, P.cc.c, mb - P.cc.c, red, P.runs[s.run], P, fixed >> P.cc.c, hb, mem);
+                run_ops += apply_run(re, im, P.cc.c, mb - P.cc.c, red, P.runs[s.run], P, fixed >> P.cc.c, hb, mem,
+                                     stage, stage_words, roff);
                 __syncthreads();
                 continue;
             }
@@ -834,9 +879,9 @@ __device__ __noinline__ unsigned apply_gates(double *re, double *im, int mb, int
                 continue;
             }
             if (dirty) { __syncthreads(); dirty = false; }
-            if (s.kind == 0) diag_gate(re, im, mb, s, fixed, red);
-            else if (s.kind == 1) run_ops += one_target(re, im, mb, s, dg[g], red);
-            else run_ops += two_target(re, im, mb, s, dg[g], red);
+            if (s.kind == 0) diag_gate(re, im, mb, s, fixed, red, roff);
+            else if (s.kind == 1) run_ops += one_target(re, im, mb, s, dg[g], red, roff);
+            else run_ops += two_target(re, im, mb, s, dg[g], red, roff);
             __syncthreads();
         }
     }
@@ -2483,7 +2528,7 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(const SweepParams *__re
     __shared__ SGate sg[GATE_CHUNK];
     __shared__ SweepParams P;
     __shared__ unsigned s_act[MAX_SWEEP_GATES / 32];
-    __shared__ int s_entry, s_skip, s_chunk, s_any;
+    __shared__ int s_entry, s_skip, s_chunk, s_any, s_ppos, s_pbad;
     __shared__ unsigned long long s_gi;
     __shared__ int s_dest[1 << MAX_PAIRS];
     __shared__ unsigned long long s_plo[1 << MAX_PAIRS], s_phi[1 << MAX_PAIRS];
@@ -2557,7 +2602,7 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(const SweepParams *__re
         const unsigned long long fixed = T << c;
         // which gates change something in this item (from the compact
         // gates in global memory; one word of 32 gates per warp)
-        if (threadIdx.x == 0) s_any = 0;
+        if (threadIdx.x == 0) { s_any = 0; s_ppos = -1; s_pbad = 0; }
         __syncthreads();
         for (int w = warp; w < (P.ngates + 31) >> 5; w += NWARPS) {
             const int g = (w << 5) + lane;
@@ -2573,7 +2618,7 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(const SweepParams *__re
             // a diagonal run is active when any of its gates is; its activity
             // goes to its first gate, which applies the whole run
             for (int r = 0; r < P.nruns; ++r) {
-                const DRun &R = P.runs[P.run_first + r];
+                const DRun R = P.runs[P.run_first + r];
                 bool any = false;
                 for (int g = R.first + lane; g < R.first + R.len; g += 32)
                     any |= (s_act[g >> 5] >> (g & 31)) & 1u;
@@ -2645,18 +2690,28 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(const SweepParams *__re
             }
             uni = __syncthreads_and(ok);
         }
+        // point items: the gates run on one amplitude per tile (red = c) at
+        // the tiles' common nonzero index; the other amplitudes are +0 and
+        // every gate of such a sweep leaves them so
+        const bool pscan = active && !uni && P.point_ok;
         if (!uni) {
             int bad = 0;
             for (int j = warp; j < ntl; j += NWARPS) {
                 const unsigned long long Tj = member_tile(T, j, h, hb);
                 bad |= wdecode(P.in_arena + P.in_table[Tj], c, re + j * N, im + j * N, alpha, scale);
+                if (pscan) point_scan(re + j * N, im + j * N, N, &s_ppos, &s_pbad);
             }
             if (bad && lane == 0) atomicOr(&P.scal->err, ERR_FORMAT);
         }
         if (active) {
             __syncthreads();
-            run_ops += apply_gates(re, im, mb, uni ? c : 0, P.sgates, sg, &s_chunk, P.gates, P.ngates, s_act,
-                                   fixed, P, hb, s_mem);
+            const bool point = pscan && !s_pbad;
+            const unsigned roff = point && s_ppos > 0 ? (unsigned)s_ppos : 0u;
+            // the packing stage after the item buffer (64 words per warp) is
+            // free until the encoder runs
+            run_ops += apply_gates(re, im, mb, (uni || point) ? c : 0, P.sgates, sg, &s_chunk, P.gates, P.ngates,
+                                   s_act, fixed, P, hb, s_mem, reinterpret_cast<uint32_t *>(smem + (2 << mb)),
+                                   64 * NWARPS, roff);
         }
         for (int j = warp; j < ntl; j += NWARPS) {
             const unsigned long long Tj = member_tile(T, j, h, hb);

@@ -100,6 +100,7 @@ struct RGate {
     uint8_t uexp[4];                // unit entry r = i^uexp[r]
     uint8_t pad;
 };
+static_assert(sizeof(RGate) % 8 == 0, "RGate is copied to shared memory in whole words");
 
 constexpr int RUN_QMAX = 4;             // class bits of a tabled run (2^4 tables)
 
@@ -170,6 +171,8 @@ struct SweepParams {
     const RunClass *rcls;
     int run_first, nruns;           // this sweep's runs: runs[run_first .. run_first+nruns-1]
     const double *dscale;           // product of the sweep's scaled gates' d (null: 1)
+    int point_ok;                   // every gate a run member, or a scaled gate or permutation on
+                                    // qubits >= c: items of point tiles take one amplitude per tile
 };
 
 // End-of-pass bookkeeping of one state (norm, scale, used bytes).
