@@ -158,6 +158,48 @@ __device__ __forceinline__ void atomic_add128(unsigned long long *alo, unsigned 
     if (hi + carry) atomicAdd(ahi, hi + carry);
 }
 
+// Per-CTA sums of one state's pass (norm units, tiles per ladder level,
+// tiles over the size limit), kept in shared memory and added to the
+// state's counters once per CTA and state: the tiles of a sweep then make
+// no global atomics on these shared words, only the CTAs do.
+struct PassAcc {
+    unsigned long long lo, hi, over;
+    unsigned long long hist[MAX_LEVELS];
+};
+
+// The bookkeeping of one written tile (one thread): its norm partial, its
+// level and whether it is over the size limit; into acc, or into the
+// state's counters when acc is null.
+__device__ __forceinline__ void tally_tile(PassAcc *acc, DevScalars *scal, unsigned long long nlo,
+                                           unsigned long long nhi, int level, bool over) {
+    if (acc) {
+        atomic_add128(&acc->lo, &acc->hi, nlo, nhi);
+        atomicAdd(&acc->hist[level], 1ull);
+        if (over) atomicAdd(&acc->over, 1ull);
+    } else {
+        atomic_add128(&scal->acc_lo, &scal->acc_hi, nlo, nhi);
+        atomicAdd(&scal->hist[level], 1ull);
+        if (over) atomicAdd(&scal->over_limit, 1ull);
+    }
+}
+
+// A stream carried or moved unchanged: its norm partial only.
+__device__ __forceinline__ void tally_norm(PassAcc *acc, DevScalars *scal, unsigned long long nlo,
+                                           unsigned long long nhi) {
+    if (acc) atomic_add128(&acc->lo, &acc->hi, nlo, nhi);
+    else atomic_add128(&scal->acc_lo, &scal->acc_hi, nlo, nhi);
+}
+
+// Adds a CTA's sums to the state's counters and clears them (one thread).
+__device__ void flush_acc(PassAcc *acc, DevScalars *scal) {
+    if (acc->lo | acc->hi) atomic_add128(&scal->acc_lo, &scal->acc_hi, acc->lo, acc->hi);
+    for (int lv = 0; lv < MAX_LEVELS; ++lv)
+        if (acc->hist[lv]) atomicAdd(&scal->hist[lv], acc->hist[lv]);
+    if (acc->over) atomicAdd(&scal->over_limit, acc->over);
+    acc->lo = acc->hi = acc->over = 0;
+    for (int lv = 0; lv < MAX_LEVELS; ++lv) acc->hist[lv] = 0;
+}
+
 // correctly rounded double of (hi, lo) * 2^-112
 __device__ double units_to_double(unsigned long long lo, unsigned long long hi) {
     if (hi == 0 && lo == 0) return 0.0;
@@ -1885,7 +1927,8 @@ __device__ __noinline__ bool polar_ladder(const double *re, const double *im, co
                                           unsigned long long tile, uint8_t *out_arena, unsigned long long out_cap,
                                           unsigned long long *out_table, unsigned long long *part,
                                           DevScalars *scal, unsigned sweep_id, uint32_t *wstage, int &mode,
-                                          int &level, uint32_t &bodyb, int *sm, unsigned long long &off) {
+                                          int &level, uint32_t &bodyb, int *sm, unsigned long long &off,
+                                          PassAcc *acc) {
     const int c = cc.c, N = 1 << c;
     const int G = N >= 32 ? N >> 5 : 1;
     const int L = N >= 32 ? 32 : N;
@@ -1990,10 +2033,8 @@ __device__ __noinline__ bool polar_ladder(const double *re, const double *im, co
     if (lane == 0) {
         part[2 * tile] = nlo;
         part[2 * tile + 1] = nhi;
-        atomic_add128(&scal->acc_lo, &scal->acc_hi, nlo, nhi);
+        tally_tile(acc, scal, nlo, nhi, level, (unsigned long long)size > cc.max_bytes);
         out_table[tile] = off;
-        atomicAdd(&scal->hist[level], 1ull);
-        if ((unsigned long long)size > cc.max_bytes) atomicAdd(&scal->over_limit, 1ull);
         if (rng) atomicOr(&scal->err, ERR_RANGE);
     }
     __syncwarp();
@@ -2011,7 +2052,8 @@ template <bool POLAR>
 __device__ __forceinline__ EncodeOut wencode_impl(double *re, double *im, const CodecCfg &cc,
                              unsigned long long tile, uint8_t *out_arena, unsigned long long out_cap,
                              unsigned long long *out_table, unsigned long long *part,
-                             DevScalars *scal, unsigned sweep_id, uint32_t *wstage, int force_lv) {
+                             DevScalars *scal, unsigned sweep_id, uint32_t *wstage, int force_lv,
+                             PassAcc *acc) {
     const int c = cc.c, N = 1 << c;
     const int G = N >= 32 ? N >> 5 : 1;
     const int L = N >= 32 ? 32 : N;
@@ -2068,7 +2110,7 @@ __device__ __forceinline__ EncodeOut wencode_impl(double *re, double *im, const 
             // the ladder with the POLAR variant of every lossy level; a
             // POLAR stream is written there and the tile is done
             if (!inel && polar_ladder(re, im, cc, ls, q, raw_body, force_lv, tile, out_arena, out_cap, out_table,
-                                      part, scal, sweep_id, wstage, mode, level, bodyb, sm, res_off))
+                                      part, scal, sweep_id, wstage, mode, level, bodyb, sm, res_off, acc))
                 return EncodeOut{res_off, res_off != ~0ull};
             polar_done = !inel;
         }
@@ -2296,10 +2338,8 @@ __device__ __forceinline__ EncodeOut wencode_impl(double *re, double *im, const 
     if (lane == 0) {
         part[2 * tile] = nlo;
         part[2 * tile + 1] = nhi;
-        atomic_add128(&scal->acc_lo, &scal->acc_hi, nlo, nhi);
+        tally_tile(acc, scal, nlo, nhi, level, over);
         out_table[tile] = off;
-        atomicAdd(&scal->hist[level], 1ull);
-        if (over) atomicAdd(&scal->over_limit, 1ull);
         if (rng) atomicOr(&scal->err, ERR_RANGE);
     }
     __syncwarp();
@@ -2311,19 +2351,22 @@ __device__ __forceinline__ EncodeOut wencode_impl(double *re, double *im, const 
 __device__ __noinline__ EncodeOut wencode_polar(double *re, double *im, const CodecCfg &cc, unsigned long long tile,
                                                 uint8_t *out_arena, unsigned long long out_cap,
                                                 unsigned long long *out_table, unsigned long long *part,
-                                                DevScalars *scal, unsigned sweep_id, uint32_t *wstage, int force_lv) {
+                                                DevScalars *scal, unsigned sweep_id, uint32_t *wstage, int force_lv,
+                                                PassAcc *acc) {
     return wencode_impl<true>(re, im, cc, tile, out_arena, out_cap, out_table, part, scal, sweep_id, wstage,
-                              force_lv);
+                              force_lv, acc);
 }
 
 __device__ __forceinline__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc, unsigned long long tile,
                                              uint8_t *out_arena, unsigned long long out_cap,
                                              unsigned long long *out_table, unsigned long long *part,
-                                             DevScalars *scal, unsigned sweep_id, uint32_t *wstage, int force_lv) {
+                                             DevScalars *scal, unsigned sweep_id, uint32_t *wstage, int force_lv,
+                                             PassAcc *acc) {
     if (cc.polar)
-        return wencode_polar(re, im, cc, tile, out_arena, out_cap, out_table, part, scal, sweep_id, wstage, force_lv);
+        return wencode_polar(re, im, cc, tile, out_arena, out_cap, out_table, part, scal, sweep_id, wstage, force_lv,
+                             acc);
     return wencode_impl<false>(re, im, cc, tile, out_arena, out_cap, out_table, part, scal, sweep_id, wstage,
-                               force_lv);
+                               force_lv, acc);
 }
 
 // Value of a well-formed CONST stream (the checks of wdecode), scaled like
@@ -2364,7 +2407,7 @@ __device__ __forceinline__ void fill_uniform(double *re, double *im, int N) {
 __device__ bool wencode_uniform(double *re, double *im, const CodecCfg &cc, unsigned long long tile,
                                 uint8_t *out_arena, unsigned long long out_cap,
                                 unsigned long long *out_table, unsigned long long *part,
-                                DevScalars *scal, unsigned sweep_id, int force_lv) {
+                                DevScalars *scal, unsigned sweep_id, int force_lv, PassAcc *acc) {
     const int c = cc.c, N = 1 << c;
     const int lane = threadIdx.x & 31;
     const double vr = re[0], vi = im[0];
@@ -2419,10 +2462,8 @@ __device__ bool wencode_uniform(double *re, double *im, const CodecCfg &cc, unsi
         const unsigned long long nlo = l0 << c, nhi = (h0 << c) | (c ? l0 >> (64 - c) : 0ull);
         part[2 * tile] = nlo;
         part[2 * tile + 1] = nhi;
-        atomic_add128(&scal->acc_lo, &scal->acc_hi, nlo, nhi);
+        tally_tile(acc, scal, nlo, nhi, level, (unsigned long long)HDR > cc.max_bytes);
         out_table[tile] = off;
-        atomicAdd(&scal->hist[level], 1ull);
-        if ((unsigned long long)HDR > cc.max_bytes) atomicAdd(&scal->over_limit, 1ull);
         if (rng) atomicOr(&scal->err, ERR_RANGE);
     }
     __syncwarp();
@@ -2434,7 +2475,7 @@ __device__ bool wencode_uniform(double *re, double *im, const CodecCfg &cc, unsi
 __device__ void wcarry(const uint8_t *in_arena, const unsigned long long *in_table,
                        unsigned long long tile, uint8_t *out_arena, unsigned long long out_cap,
                        unsigned long long *out_table, const unsigned long long *part,
-                       DevScalars *scal, unsigned sweep_id) {
+                       DevScalars *scal, unsigned sweep_id, PassAcc *acc) {
     const int lane = threadIdx.x & 31;
     const uint8_t *src = in_arena + in_table[tile];
     const uint32_t size = HDR + reinterpret_cast<const uint32_t *>(src)[1];
@@ -2447,7 +2488,7 @@ __device__ void wcarry(const uint8_t *in_arena, const unsigned long long *in_tab
             atomicOr(&scal->err, ERR_OVERFLOW);
             atomicCAS(&scal->err_sweep, 0u, sweep_id + 1u);
         }
-        atomic_add128(&scal->acc_lo, &scal->acc_hi, part[2 * tile], part[2 * tile + 1]);
+        tally_norm(acc, scal, part[2 * tile], part[2 * tile + 1]);
         if (ok) out_table[tile] = off;
     }
     off = shfl64(off, 0);
@@ -2465,7 +2506,7 @@ __device__ void wcarry(const uint8_t *in_arena, const unsigned long long *in_tab
 __device__ void wmove(const uint8_t *in_arena, const unsigned long long *in_table, unsigned long long src,
                       unsigned long long dst, uint8_t *out_arena, unsigned long long out_cap,
                       unsigned long long *out_table, unsigned long long *part, unsigned long long plo,
-                      unsigned long long phi, DevScalars *scal, unsigned sweep_id) {
+                      unsigned long long phi, DevScalars *scal, unsigned sweep_id, PassAcc *acc) {
     const int lane = threadIdx.x & 31;
     const uint8_t *sp = in_arena + in_table[src];
     const uint32_t size = HDR + reinterpret_cast<const uint32_t *>(sp)[1];
@@ -2478,7 +2519,7 @@ __device__ void wmove(const uint8_t *in_arena, const unsigned long long *in_tabl
             atomicOr(&scal->err, ERR_OVERFLOW);
             atomicCAS(&scal->err_sweep, 0u, sweep_id + 1u);
         }
-        atomic_add128(&scal->acc_lo, &scal->acc_hi, plo, phi);
+        tally_norm(acc, scal, plo, phi);
         part[2 * dst] = plo;
         part[2 * dst + 1] = phi;
         if (ok) out_table[dst] = off;
@@ -2535,8 +2576,13 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(const SweepParams *__re
     __shared__ double s_alpha;
     __shared__ RunMember s_mem[1 << MAX_PAIRS];
     __shared__ unsigned long long s_rundp;
+    __shared__ PassAcc s_acc;
     const unsigned long long total = istart[nlist];
-    if (threadIdx.x == 0) s_rundp = 0;
+    if (threadIdx.x == 0) {
+        s_rundp = 0;
+        s_acc.lo = s_acc.hi = s_acc.over = 0;
+        for (int lv = 0; lv < MAX_LEVELS; ++lv) s_acc.hist[lv] = 0;
+    }
     unsigned run_ops = 0;                 // FP64 instructions of diagonal runs (this thread)
     constexpr int NWARPS = NT / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -2567,6 +2613,7 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(const SweepParams *__re
             if (threadIdx.x == 0) {
                 if (s_rundp) atomicAdd(&P.scal->run_dp, s_rundp);
                 s_rundp = 0;
+                flush_acc(&s_acc, P.scal);      // the norm and level sums of the state it leaves
             }
             __syncthreads();
         }
@@ -2639,7 +2686,7 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(const SweepParams *__re
         if (!active && (!scale || P.moves_tiles) && !P.every_item) {
             for (int j = warp; j < ntl; j += NWARPS)
                 wcarry(P.in_arena, P.in_table, member_tile(T, j, h, hb), P.out_arena, P.out_cap,
-                       P.out_table, P.part, P.scal, P.sweep_id);
+                       P.out_table, P.part, P.scal, P.sweep_id, &s_acc);
             if (threadIdx.x == 0) atomicAdd(&P.scal->items_skipped, 1ull);
             continue;
         }
@@ -2670,7 +2717,7 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(const SweepParams *__re
             __syncthreads();
             for (int j = warp; j < ntl; j += NWARPS)
                 wmove(P.in_arena, P.in_table, member_tile(T, j, h, hb), member_tile(T, s_dest[j], h, hb),
-                      P.out_arena, P.out_cap, P.out_table, P.part, s_plo[j], s_phi[j], P.scal, P.sweep_id);
+                      P.out_arena, P.out_cap, P.out_table, P.part, s_plo[j], s_phi[j], P.scal, P.sweep_id, &s_acc);
             if (threadIdx.x == 0) atomicAdd(&P.scal->items_done, 1ull);
             continue;
         }
@@ -2722,10 +2769,10 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(const SweepParams *__re
             }
             const int flv = P.unit_level ? (int)P.unit_level[Tj >> P.unit_shift] : -1;
             if (uni && wencode_uniform(re + j * N, im + j * N, P.cc, Tj, P.out_arena, P.out_cap, P.out_table,
-                                       P.part, P.scal, P.sweep_id, flv))
+                                       P.part, P.scal, P.sweep_id, flv, &s_acc))
                 continue;
             wencode(re + j * N, im + j * N, P.cc, Tj, P.out_arena, P.out_cap, P.out_table, P.part, P.scal,
-                    P.sweep_id, wst, flv);
+                    P.sweep_id, wst, flv, &s_acc);
         }
         if (threadIdx.x == 0 && !SIZING) atomicAdd(&P.scal->items_done, 1ull);
     }
@@ -2853,7 +2900,7 @@ __global__ void __launch_bounds__(32 * TILE_WARPS) init_kernel(
             continue;
         }
         wencode(re, im, cc, t, out_arena, out_cap, out_table, part, scal, 0u, wst,
-                unit_level ? (int)unit_level[t >> unit_shift] : -1);
+                unit_level ? (int)unit_level[t >> unit_shift] : -1, nullptr);
     }
 }
 
