@@ -2839,10 +2839,20 @@ __global__ void __launch_bounds__(32 * TILE_WARPS) init_kernel(
     const uint8_t *unit_level, int unit_shift) {
     extern __shared__ double smem[];
     __shared__ uint32_t stage[64 * TILE_WARPS];
+    __shared__ unsigned long long s_hist[MAX_LEVELS];
     const int c = cc.c, N = 1 << c;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double *re = smem + (size_t)warp * 2 * N, *im = re + N;
     uint32_t *wst = stage + 64 * warp;
+    // A basis state's zero tiles are 32-byte CONST streams at fixed places
+    // (tile t at 32 t, less one slot past the nonzero tile); the warp of the
+    // nonzero tile reserves their range on the bump counter before its own
+    // stream, which then follows them, so the zero tiles take no atomic each.
+    // Their level counts are summed per CTA.
+    const unsigned long long tx = x >> c;
+    const bool zfixed = dense == nullptr && !cc.force_raw && unit_bytes == nullptr;
+    if (threadIdx.x < MAX_LEVELS) s_hist[threadIdx.x] = 0;
+    __syncthreads();
     for (unsigned long long t = (unsigned long long)blockIdx.x * TILE_WARPS + warp; t < ntiles;
          t += (unsigned long long)gridDim.x * TILE_WARPS) {
         if (dense == nullptr && (x >> c) != t) {
@@ -2855,7 +2865,8 @@ __global__ void __launch_bounds__(32 * TILE_WARPS) init_kernel(
             unsigned long long off = 0;
             int ok = 0;
             if (lane == 0) {
-                off = atomicAdd(&scal->bump, (unsigned long long)size);
+                off = zfixed ? (unsigned long long)HDR * (t - (t > tx ? 1ull : 0ull))
+                             : atomicAdd(&scal->bump, (unsigned long long)size);
                 ok = off + size <= out_cap;
                 if (!ok) atomicOr(&scal->err, ERR_OVERFLOW);
             }
@@ -2880,7 +2891,7 @@ __global__ void __launch_bounds__(32 * TILE_WARPS) init_kernel(
             if (lane == 0) {
                 out_table[t] = off;
                 part[2 * t] = part[2 * t + 1] = 0;
-                atomicAdd(&scal->hist[cc.force_raw ? 0 : lv], 1ull);
+                atomicAdd(&s_hist[cc.force_raw ? 0 : lv], 1ull);
             }
             continue;
         }
@@ -2899,9 +2910,13 @@ __global__ void __launch_bounds__(32 * TILE_WARPS) init_kernel(
             wsize(re, im, cc, unit_bytes + (t >> unit_shift) * MAX_LEVELS);
             continue;
         }
+        if (zfixed && lane == 0) atomicAdd(&scal->bump, (unsigned long long)HDR * (ntiles - 1));
+        __syncwarp();
         wencode(re, im, cc, t, out_arena, out_cap, out_table, part, scal, 0u, wst,
                 unit_level ? (int)unit_level[t >> unit_shift] : -1, nullptr);
     }
+    __syncthreads();
+    if (threadIdx.x < MAX_LEVELS && s_hist[threadIdx.x]) atomicAdd(&scal->hist[threadIdx.x], s_hist[threadIdx.x]);
 }
 
 // Ladder level of every stride from its streams' bytes at each level:
