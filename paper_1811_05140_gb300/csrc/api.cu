@@ -314,6 +314,8 @@ struct qsim_state {
     qs::DGate *hgates = nullptr;          // pinned staging
     size_t hgates_cap = 0;
     qs::SGate *dsg = nullptr, *hsg = nullptr;
+    int *dglist = nullptr;                // per flush: the gates that can apply, sweep by sweep
+    std::vector<int> hglist;
     qs::SweepParams *dparams = nullptr, *hparams = nullptr;   // one entry per sweep
     unsigned long long *distart = nullptr, *histart = nullptr; // (0, nitems) per sweep
     size_t params_cap = 0;
@@ -758,6 +760,7 @@ qsim_status qsim_destroy(qsim_t h) {
     if (h->hgates) cudaFreeHost(h->hgates);
     if (h->dsg) cudaFree(h->dsg);
     if (h->hsg) cudaFreeHost(h->hsg);
+    if (h->dglist) cudaFree(h->dglist);
     if (h->dparams) cudaFree(h->dparams);
     if (h->hparams) cudaFreeHost(h->hparams);
     if (h->distart) cudaFree(h->distart);
@@ -930,6 +933,7 @@ struct FlushCtx {
     unsigned long long used_before = 0;
     int regrows = 0;
     std::vector<int> run_first, nruns;    // per sweep: its diagonal runs
+    std::vector<int> list_first, list_n;  // per sweep: its gates that can apply (hglist)
     std::vector<char> in_run;             // per gate: part of a diagonal run
     std::vector<char> scaled;             // per gate: a scaled gate applied without its d
     std::vector<char> sweep_scaled;       // per sweep: holds a scaled gate (its scale D is not 1)
@@ -1095,11 +1099,14 @@ qsim_status stage_flush(qsim_t h, FlushCtx &fc, cudaStream_t st) {
         CK(cudaStreamSynchronize(st));
         if (h->dgates) cudaFree(h->dgates);
         if (h->dsg) cudaFree(h->dsg);
+        if (h->dglist) cudaFree(h->dglist);
         h->dgates = nullptr;
         h->dsg = nullptr;
+        h->dglist = nullptr;
         h->dgates_cap = 0;
         CK(cudaMalloc(&h->dgates, ng * sizeof(qs::DGate)));
         CK(cudaMalloc(&h->dsg, ng * sizeof(qs::SGate)));
+        CK(cudaMalloc(&h->dglist, ng * sizeof(int)));
         h->dgates_cap = ng;
     }
     if (h->used_hist_cap < ns) {
@@ -1145,6 +1152,18 @@ qsim_status stage_flush(qsim_t h, FlushCtx &fc, cudaStream_t st) {
                     fc.sweep_scaled[si] = 1;
                 }
     plan_runs(h, fc);
+    // per sweep, the gates that can apply: all but the later gates of runs
+    h->hglist.clear();
+    fc.list_first.assign(ns, 0);
+    fc.list_n.assign(ns, 0);
+    for (size_t si = 0; si < ns; ++si) {
+        fc.list_first[si] = (int)h->hglist.size();
+        for (int gi = fc.sweeps[si].lo; gi < fc.sweeps[si].hi; ++gi)
+            if (h->hsg[gi].run != -2) h->hglist.push_back(gi - fc.sweeps[si].lo);
+        fc.list_n[si] = (int)h->hglist.size() - fc.list_first[si];
+    }
+    if (!h->hglist.empty())
+        CK(hcopy(h, h->dglist, h->hglist.data(), h->hglist.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     CK(hcopy(h, h->dgates, h->hgates, ng * sizeof(qs::DGate), cudaMemcpyHostToDevice, st));
     CK(hcopy(h, h->dsg, h->hsg, ng * sizeof(qs::SGate), cudaMemcpyHostToDevice, st));
     {
@@ -1233,6 +1252,8 @@ qs::SweepParams sweep_params(qsim_t h, const FlushCtx &fc, size_t j) {
     // the zeros +0): the sweep's gates leave the zeros as they are when each
     // is a member of a diagonal run, a scaled gate or a permutation, and the
     // mixing ones act on qubits >= c only
+    p.glist = h->dglist + fc.list_first[j];
+    p.nglist = fc.list_n[j];
     p.point_ok = h->fuse && !fc.in_run.empty();
     for (int gi = sw.lo; gi < sw.hi && p.point_ok; ++gi) {
         if (fc.in_run[gi]) continue;

@@ -776,6 +776,42 @@ __device__ unsigned apply_run(double *re, double *im, int c, int h, int red, con
         const int words = nst * (int)(sizeof(RGate) / 4);
         for (int i = threadIdx.x; i < words; i += blockDim.x) stage[i] = src[i];
     }
+    // the run at amplitude xl of member j (whose setup is m)
+    auto visit = [&](int j, unsigned xl, const RunMember &m) {
+        const unsigned l = ((unsigned)j << c) | xl;
+        double xr = re[l], xi = im[l];
+        if (zero_amp(xr, xi)) return;             // a zero stays as it is
+        bool have_l = false;
+        double lr = 0.0, li = 0.0;
+        unsigned k = m.k_t;
+        if (R.nl) {
+            if (R.tabled) {
+                const unsigned long long e = R.table + (unsigned long long)m.kap * N + xl;
+                const unsigned mt = P.rmeta[e];
+                have_l = mt & 1u;
+                k += mt >> 1;
+                if (have_l) {
+                    const double2 v = P.rtab[e];
+                    lr = v.x;
+                    li = v.y;
+                }
+            } else {
+                const unsigned long long x = (member_tile(T, j, h, hb) << c) | xl;
+                ops += run_factor(P.rgates + R.lg, R.nl, x, have_l, lr, li, k);
+            }
+        }
+        const bool have_t = m.have_t;
+        if (!have_t && !have_l && (k & 3u) == 0u) return;
+        if (have_t || have_l) {
+            double gr = have_t ? m.tr : lr, gi = have_t ? m.ti : li;
+            if (have_t && have_l) { cmul(m.tr, m.ti, lr, li, gr, gi); ops += 4; }
+            cmul(gr, gi, xr, xi, xr, xi);
+            ops += 4;
+        }
+        unit_pow(k, xr, xi);
+        re[l] = xr;
+        im[l] = xi;
+    };
     __syncthreads();
     if ((int)threadIdx.x < ntl) {
         const int j = threadIdx.x;
@@ -806,8 +842,14 @@ __device__ unsigned apply_run(double *re, double *im, int c, int h, int red, con
             m.pin_val = rc.pin_val;
             m.count = rc.active ? (uint32_t)N >> __popc(rc.pin_mask) : 0u;
         }
-        mem[j] = m;
+        // one amplitude per tile: member j's own thread visits it, no barrier
+        if (red) {
+            if (m.count) visit(j, roff, m);
+        } else {
+            mem[j] = m;
+        }
     }
+    if (red) return ops;
     __syncthreads();
     int j = 0;
     unsigned base = 0;
@@ -815,51 +857,16 @@ __device__ unsigned apply_run(double *re, double *im, int c, int h, int red, con
         while (j < ntl && w >= base + mem[j].count) { base += mem[j].count; ++j; }
         if (j >= ntl) break;
         const RunMember &m = mem[j];
-        unsigned f = w - base, xl = roff;
-        if (!red) {
-            // deposit f into the tile bits outside pin_mask, pinned bits from pin_val
-            unsigned pm = m.pin_mask;
-            xl = f;
-            while (pm) {
-                const int b = __ffs(pm) - 1;
-                xl = insert_zero(xl, b);
-                pm &= pm - 1;
-            }
-            xl |= m.pin_val;
+        unsigned f = w - base;
+        // deposit f into the tile bits outside pin_mask, pinned bits from pin_val
+        unsigned pm = m.pin_mask, xl = f;
+        while (pm) {
+            const int b = __ffs(pm) - 1;
+            xl = insert_zero(xl, b);
+            pm &= pm - 1;
         }
-        const unsigned l = ((unsigned)j << c) | xl;
-        double xr = re[l], xi = im[l];
-        if (zero_amp(xr, xi)) continue;             // a zero stays as it is
-        bool have_l = false;
-        double lr = 0.0, li = 0.0;
-        unsigned k = m.k_t;
-        if (R.nl) {
-            if (R.tabled) {
-                const unsigned long long e = R.table + (unsigned long long)m.kap * N + xl;
-                const unsigned mt = P.rmeta[e];
-                have_l = mt & 1u;
-                k += mt >> 1;
-                if (have_l) {
-                    const double2 v = P.rtab[e];
-                    lr = v.x;
-                    li = v.y;
-                }
-            } else {
-                const unsigned long long x = (member_tile(T, j, h, hb) << c) | xl;
-                ops += run_factor(P.rgates + R.lg, R.nl, x, have_l, lr, li, k);
-            }
-        }
-        const bool have_t = m.have_t;
-        if (!have_t && !have_l && (k & 3u) == 0u) continue;
-        if (have_t || have_l) {
-            double gr = have_t ? m.tr : lr, gi = have_t ? m.ti : li;
-            if (have_t && have_l) { cmul(m.tr, m.ti, lr, li, gr, gi); ops += 4; }
-            cmul(gr, gi, xr, xi, xr, xi);
-            ops += 4;
-        }
-        unit_pow(k, xr, xi);
-        re[l] = xr;
-        im[l] = xi;
+        xl |= m.pin_val;
+        visit(j, xl, m);
     }
     return ops;
 }
@@ -882,27 +889,31 @@ __device__ __noinline__ unsigned apply_gates(double *re, double *im, int mb, int
     const bool warp_parts = red == 0 && mb - log_nwarps() >= 5;
     unsigned run_ops = 0;
     bool dirty = false;                              // warp-local gates since the last CTA barrier
-    for (int base = 0; base < ngates; base += GATE_CHUNK) {
-        const int cn = min(GATE_CHUNK, ngates - base);
+    // the gates that can apply (a diagonal run's later gates apply with its
+    // first): staged GATE_CHUNK list positions at a time
+    const int *gl = P.glist;
+    const int nl = P.nglist;
+    constexpr int SW = (int)(sizeof(SGate) / 4);
+    for (int base = 0; base < nl; base += GATE_CHUNK) {
+        const int cn = min(GATE_CHUNK, nl - base);
         bool any = false;
-        for (int w = base >> 5; w <= (base + cn - 1) >> 5; ++w) {
-            unsigned m = act[w];
-            const int lo = max(base, w << 5) - (w << 5), hi = min(base + cn, (w + 1) << 5) - (w << 5);
-            m &= (hi == 32 ? FULL : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
-            any |= m != 0u;
+        for (int i = 0; i < cn && !any; ++i) {
+            const int g = gl[base + i];
+            any = (act[g >> 5] >> (g & 31)) & 1u;
         }
         if (!any) continue;
         if (*chunk != base) {
             __syncthreads();
-            const uint32_t *src = reinterpret_cast<const uint32_t *>(gsrc + base);
             uint32_t *dst = reinterpret_cast<uint32_t *>(sg);
-            const int words = cn * (int)(sizeof(SGate) / 4);
-            for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+            for (int idx = threadIdx.x; idx < cn * SW; idx += blockDim.x) {
+                const int i = idx / SW;
+                dst[idx] = reinterpret_cast<const uint32_t *>(gsrc + gl[base + i])[idx - i * SW];
+            }
             if (threadIdx.x == 0) *chunk = base;
             __syncthreads();
         }
         for (int i = 0; i < cn; ++i) {
-            const int g = base + i;
+            const int g = gl[base + i];
             if (!((act[g >> 5] >> (g & 31)) & 1u)) continue;
             const SGate &s = sg[i];
             if (s.run != -1) {

@@ -173,6 +173,8 @@ struct SweepParams {
     const double *dscale;           // product of the sweep's scaled gates' d (null: 1)
     int point_ok;                   // every gate a run member, or a scaled gate or permutation on
                                     // qubits >= c: items of point tiles take one amplitude per tile
+    const int *glist;               // the gates that can apply (no later gate of a run), in order
+    int nglist;
 };
 
 // End-of-pass bookkeeping of one state (norm, scale, used bytes).
