@@ -367,12 +367,20 @@ __device__ __forceinline__ bool gate_active(const SGate &s, unsigned long long f
     return true;
 }
 
+// The barrier of a gate pass: the CTA's, or the warp's when one warp
+// applies the gates alone (nth == 32: items of one amplitude per tile).
+__device__ __forceinline__ void gsync(unsigned nth) {
+    if (nth == 32u) __syncwarp();
+    else __syncthreads();
+}
+
 // One diagonal gate, applied only where it changes something: the
 // amplitudes whose local controls hold and whose target sub-index r has an
 // entry other than exactly 1.  Enumerating just those keeps every lane of
 // every FP64 instruction busy (masked lanes cost the same on this part).
 __device__ void diag_gate(double *re, double *im, int mb, const SGate &s,
-                          unsigned long long fixed, int red, unsigned roff) {
+                          unsigned long long fixed, int red, unsigned roff,
+                          unsigned tid, unsigned nth) {
     // sub-indices r to visit: entry != 1 and consistent with fixed targets
     unsigned rpack = 0;          // sub-indices, 2 bits each
     int nr = 0;
@@ -385,7 +393,7 @@ __device__ void diag_gate(double *re, double *im, int mb, const SGate &s,
     if (nr == 0) return;
     const int fb = mb - s.nins - red;           // free bits (the low `red` bits stay 0)
     const unsigned cnt = (unsigned)nr << fb;
-    for (unsigned f = threadIdx.x; f < cnt; f += blockDim.x) {
+    for (unsigned f = tid; f < cnt; f += nth) {
         int r = (int)((rpack >> (2 * (f >> fb))) & 3u);
         unsigned l = deposit((f & ((1u << fb) - 1u)) << red, s) | s.lcv | roff;
         if (s.p0 >= 0) l |= (unsigned)(r & 1) << s.p0;
@@ -467,7 +475,7 @@ __device__ void diag_gate_warp(double *re, double *im, int mb, const SGate &s, u
 // as it is and returns the FP64 instructions of the pairs it formed; other
 // gates return 0 (their canonical count is the host's).
 __device__ unsigned one_target(double *re, double *im, int mb, const SGate &s, const DGate &dg, int red,
-                               unsigned roff) {
+                               unsigned roff, unsigned tid, unsigned nth) {
     double m[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) m[i] = dg.m[i];
@@ -476,7 +484,7 @@ __device__ unsigned one_target(double *re, double *im, int mb, const SGate &s, c
     if ((s.cls & 0xFFFull) == ((unsigned long long)EC_ONE << 3 | (unsigned long long)EC_ONE << 6)) {
         // X (entries 0 1 / 1 0, exactly): the pair is exchanged, the copies
         // the rows would make
-        for (unsigned f = threadIdx.x; f < cnt; f += blockDim.x) {
+        for (unsigned f = tid; f < cnt; f += nth) {
             const unsigned l0 = deposit(f << red, s) | s.lcv | roff, l1 = l0 | bit;
             const double ar = re[l0], ai = im[l0], br = re[l1], bi = im[l1];
             re[l0] = br; im[l0] = bi;
@@ -496,7 +504,7 @@ __device__ unsigned one_target(double *re, double *im, int mb, const SGate &s, c
         if (s.unscaled) {
             // a scaled gate: d is in the sweep's scale, the rows are their sums
             unsigned pairs = 0;
-            for (unsigned f = threadIdx.x; f < cnt; f += blockDim.x) {
+            for (unsigned f = tid; f < cnt; f += nth) {
                 unsigned l = f << red;
                 for (int i = 0; i < nins; ++i) l = insert_zero(l, pos[i]);
                 const unsigned l0 = l | lcv;
@@ -514,7 +522,7 @@ __device__ unsigned one_target(double *re, double *im, int mb, const SGate &s, c
             }
             return pairs * s.unscaled;
         }
-        for (unsigned f = threadIdx.x; f < cnt; f += blockDim.x) {
+        for (unsigned f = tid; f < cnt; f += nth) {
             unsigned l = f << red;
             for (int i = 0; i < nins; ++i) l = insert_zero(l, pos[i]);
             const unsigned l0 = l | lcv;
@@ -531,7 +539,7 @@ __device__ unsigned one_target(double *re, double *im, int mb, const SGate &s, c
         return 0;
     }
     unsigned groups = 0;
-    for (unsigned f = threadIdx.x; f < cnt; f += blockDim.x) {
+    for (unsigned f = tid; f < cnt; f += nth) {
         unsigned l0 = deposit(f << red, s) | s.lcv | roff;
         unsigned l1 = l0 | bit;
         double xr[2] = {re[l0], re[l1]}, xi[2] = {im[l0], im[l1]};
@@ -550,7 +558,7 @@ __device__ unsigned one_target(double *re, double *im, int mb, const SGate &s, c
 
 // As one_target, for gates on two targets.
 __device__ unsigned two_target(double *re, double *im, int mb, const SGate &s, const DGate &dg, int red,
-                               unsigned roff) {
+                               unsigned roff, unsigned tid, unsigned nth) {
     const unsigned cnt = 1u << (mb - s.nins - red);
     // a permutation (SWAP; X on one target controlled by the other): every
     // row one entry exactly 1 and the others exactly 0; row r copies x[src r]
@@ -570,7 +578,7 @@ __device__ unsigned two_target(double *re, double *im, int mb, const SGate &s, c
         if (at != r) moved |= 1u << r;
     }
     if (perm) {
-        for (unsigned f = threadIdx.x; f < cnt && moved; f += blockDim.x) {
+        for (unsigned f = tid; f < cnt && moved; f += nth) {
             const unsigned l = deposit(f << red, s) | s.lcv | roff;
             unsigned idx[4];
             double xr[4], xi[4];
@@ -591,7 +599,7 @@ __device__ unsigned two_target(double *re, double *im, int mb, const SGate &s, c
         return 0;
     }
     unsigned groups = 0;
-    for (unsigned f = threadIdx.x; f < cnt; f += blockDim.x) {
+    for (unsigned f = tid; f < cnt; f += nth) {
         unsigned l = deposit(f << red, s) | s.lcv | roff;
         unsigned idx[4];
         double xr[4], xi[4];
@@ -762,7 +770,8 @@ struct RunMember {
 // FP64 instructions this thread executed.
 __device__ unsigned apply_run(double *re, double *im, int c, int h, int red, const DRun &Rg,
                               const SweepParams &P, unsigned long long T, const int *hb, RunMember *mem,
-                              uint32_t *stage, int stage_words, unsigned roff) {
+                              uint32_t *stage, int stage_words, unsigned roff,
+                              unsigned tid, unsigned nth) {
     const DRun R = Rg;                             // in registers: one load of the descriptor
     const int ntl = 1 << h, N = 1 << c;
     unsigned ops = 0;
@@ -774,7 +783,7 @@ __device__ unsigned apply_run(double *re, double *im, int c, int h, int red, con
     {
         const uint32_t *src = reinterpret_cast<const uint32_t *>(P.rgates + tg);
         const int words = nst * (int)(sizeof(RGate) / 4);
-        for (int i = threadIdx.x; i < words; i += blockDim.x) stage[i] = src[i];
+        for (int i = tid; i < words; i += nth) stage[i] = src[i];
     }
     // the run at amplitude xl of member j (whose setup is m)
     auto visit = [&](int j, unsigned xl, const RunMember &m) {
@@ -812,9 +821,9 @@ __device__ unsigned apply_run(double *re, double *im, int c, int h, int red, con
         re[l] = xr;
         im[l] = xi;
     };
-    __syncthreads();
-    if ((int)threadIdx.x < ntl) {
-        const int j = threadIdx.x;
+    gsync(nth);
+    if ((int)tid < ntl) {
+        const int j = tid;
         const unsigned long long xb = member_tile(T, j, h, hb) << c;
         bool have = false;
         double tr = 0.0, ti = 0.0;
@@ -850,10 +859,10 @@ __device__ unsigned apply_run(double *re, double *im, int c, int h, int red, con
         }
     }
     if (red) return ops;
-    __syncthreads();
+    gsync(nth);
     int j = 0;
     unsigned base = 0;
-    for (unsigned w = threadIdx.x;; w += blockDim.x) {
+    for (unsigned w = tid;; w += nth) {
         while (j < ntl && w >= base + mem[j].count) { base += mem[j].count; ++j; }
         if (j >= ntl) break;
         const RunMember &m = mem[j];
@@ -877,7 +886,8 @@ __device__ unsigned apply_run(double *re, double *im, int c, int h, int red, con
 // gate staged, -1 none); chunks without an active gate are not staged.
 // red > 0: one amplitude per tile, at tile index roff (uniform items: 0,
 // gates that touch no low qubit; point items: the common index of the
-// tiles' one nonzero amplitude).  CTA-wide; every thread must call it.
+// tiles' one nonzero amplitude); warp 0 applies them alone and the other
+// warps return at once.  Every thread must call it.
 // A gate that starts a diagonal run (SGate::run >= 0) applies the whole run
 // (apply_run); the run's other gates carry no activity bit (the sweep
 // kernel moves the run's activity onto its first gate).  Returns the FP64
@@ -887,6 +897,11 @@ __device__ __noinline__ unsigned apply_gates(double *re, double *im, int mb, int
                             unsigned long long fixed, const SweepParams &P, const int *hb, RunMember *mem,
                             uint32_t *stage, int stage_words, unsigned roff) {
     const bool warp_parts = red == 0 && mb - log_nwarps() >= 5;
+    // one amplitude per tile (red > 0): warp 0 applies the gates alone,
+    // with warp barriers; the caller joins the CTA afterwards
+    const bool wo = red > 0;
+    if (wo && threadIdx.x >= 32u) return 0;
+    const unsigned tid = wo ? (threadIdx.x & 31u) : threadIdx.x, nth = wo ? 32u : blockDim.x;
     unsigned run_ops = 0;
     bool dirty = false;                              // warp-local gates since the last CTA barrier
     // the gates that can apply (a diagonal run's later gates apply with its
@@ -903,14 +918,14 @@ __device__ __noinline__ unsigned apply_gates(double *re, double *im, int mb, int
         }
         if (!any) continue;
         if (*chunk != base) {
-            __syncthreads();
+            gsync(nth);
             uint32_t *dst = reinterpret_cast<uint32_t *>(sg);
-            for (int idx = threadIdx.x; idx < cn * SW; idx += blockDim.x) {
+            for (int idx = (int)tid; idx < cn * SW; idx += (int)nth) {
                 const int i = idx / SW;
                 dst[idx] = reinterpret_cast<const uint32_t *>(gsrc + gl[base + i])[idx - i * SW];
             }
-            if (threadIdx.x == 0) *chunk = base;
-            __syncthreads();
+            if (tid == 0) *chunk = base;
+            gsync(nth);
         }
         for (int i = 0; i < cn; ++i) {
             const int g = gl[base + i];
@@ -920,8 +935,8 @@ __device__ __noinline__ unsigned apply_gates(double *re, double *im, int mb, int
                 if (s.run < 0) continue;            // inside a run: applied with its first gate
                 if (dirty) { __syncthreads(); dirty = false; }
                 run_ops += apply_run(re, im, P.cc.c, mb - P.cc.c, red, P.runs[s.run], P, fixed >> P.cc.c, hb, mem,
-                                     stage, stage_words, roff);
-                __syncthreads();
+                                     stage, stage_words, roff, tid, nth);
+                gsync(nth);
                 continue;
             }
             if (s.kind == 0 && warp_parts) {
@@ -932,10 +947,10 @@ __device__ __noinline__ unsigned apply_gates(double *re, double *im, int mb, int
                 continue;
             }
             if (dirty) { __syncthreads(); dirty = false; }
-            if (s.kind == 0) diag_gate(re, im, mb, s, fixed, red, roff);
-            else if (s.kind == 1) run_ops += one_target(re, im, mb, s, dg[g], red, roff);
-            else run_ops += two_target(re, im, mb, s, dg[g], red, roff);
-            __syncthreads();
+            if (s.kind == 0) diag_gate(re, im, mb, s, fixed, red, roff, tid, nth);
+            else if (s.kind == 1) run_ops += one_target(re, im, mb, s, dg[g], red, roff, tid, nth);
+            else run_ops += two_target(re, im, mb, s, dg[g], red, roff, tid, nth);
+            gsync(nth);
         }
     }
     if (dirty) __syncthreads();
@@ -2770,6 +2785,7 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(const SweepParams *__re
             run_ops += apply_gates(re, im, mb, (uni || point) ? c : 0, P.sgates, sg, &s_chunk, P.gates, P.ngates,
                                    s_act, fixed, P, hb, s_mem, reinterpret_cast<uint32_t *>(smem + (2 << mb)),
                                    64 * NWARPS, roff);
+            if (uni || point) __syncthreads();       // warp 0 applied them alone
         }
         for (int j = warp; j < ntl; j += NWARPS) {
             const unsigned long long Tj = member_tile(T, j, h, hb);
