@@ -781,9 +781,13 @@ __device__ unsigned apply_run(double *re, double *im, int c, int h, int red, con
     const int nt = R.nt, tg = R.tg;
     const int nst = min(nt, stage_words / (int)(sizeof(RGate) / 4));
     {
-        const uint32_t *src = reinterpret_cast<const uint32_t *>(P.rgates + tg);
-        const int words = nst * (int)(sizeof(RGate) / 4);
-        for (int i = tid; i < words; i += nth) stage[i] = src[i];
+        // 16-byte copies, several in flight per thread (one warp copies alone
+        // in items of one amplitude per tile)
+        const uint4 *src = reinterpret_cast<const uint4 *>(P.rgates + tg);
+        uint4 *dst = reinterpret_cast<uint4 *>(stage);
+        const int n4 = nst * (int)(sizeof(RGate) / 16);
+#pragma unroll 4
+        for (int i = (int)tid; i < n4; i += (int)nth) dst[i] = src[i];
     }
     // the run at amplitude xl of member j (whose setup is m)
     auto visit = [&](int j, unsigned xl, const RunMember &m) {

@@ -100,7 +100,7 @@ struct RGate {
     uint8_t uexp[4];                // unit entry r = i^uexp[r]
     uint8_t pad;
 };
-static_assert(sizeof(RGate) % 8 == 0, "RGate is copied to shared memory in whole words");
+static_assert(sizeof(RGate) % 16 == 0, "RGate is copied to shared memory in 16-byte pieces");
 
 constexpr int RUN_QMAX = 4;             // class bits of a tabled run (2^4 tables)
 
