@@ -1342,9 +1342,14 @@ __device__ __forceinline__ uint32_t polar_body(const PolarInfo &pi, int c, int s
 // nonzero (and zero-fills) on a malformed stream.  The first 128 body bytes
 // (sections and widths, usually) come in with one load, and the packed
 // words of the next group are loaded while the current one is scanned.
+// sp != nullptr: a stream of one amplitude (at most one nonzero code per
+// component, at a common index, every residual zero, and every zero
+// decoding to +0) is decoded into that amplitude alone: its value is
+// written at its index p, the other entries are left unwritten, *sp = p
+// and the result is 2.
 template <bool POLAR>
 __device__ __forceinline__ int wdecode_impl(const uint8_t *src, int c, double *re, double *im, double alpha,
-                                            bool scale) {
+                                            bool scale, int *sp) {
     const int N = 1 << c;
     const int G = N >= 32 ? N >> 5 : 1;
     const int L = N >= 32 ? 32 : N;
@@ -1384,7 +1389,7 @@ __device__ __forceinline__ int wdecode_impl(const uint8_t *src, int c, double *r
         return 0;
     }
     const uint32_t lanes = L == 32 ? FULL : ((1u << L) - 1u);
-    uint32_t sw0 = 0, sw1 = 0, zw0 = 0, zw1 = 0, w0 = 0, w1 = 0, doff = 0, off0 = 0, off1 = 0, boff = 0;
+    uint32_t sw0 = 0, sw1 = 0, zw0 = 0, zw1 = 0, w0 = 0, w1 = 0, doff = 0, off0 = 0, off1 = 0, boff = 0, wmax = 0;
     if (!bad) {
         const uint32_t mw = 4u * (uint32_t)lane < body ? __ldg(b32 + lane) : 0u;
         uint32_t off = 0;
@@ -1411,7 +1416,7 @@ __device__ __forceinline__ int wdecode_impl(const uint8_t *src, int c, double *r
                 boff = doff;
                 doff += 4u * polar_basis_words(c, s);
             }
-            const uint32_t wmax = __reduce_max_sync(FULL, max(w0, w1));
+            wmax = __reduce_max_sync(FULL, max(w0, w1));
             bad = wmax > 64 || (unsigned long long)doff + 4ull * (tot0 + tot1) > body;
             // POLAR: a zero amplitude is zero in both code streams
             if (!bad && polar) bad = __any_sync(FULL, lane < G && zw0 != zw1);
@@ -1420,6 +1425,37 @@ __device__ __forceinline__ int wdecode_impl(const uint8_t *src, int c, double *r
     if (bad) {
         for (int i = lane; i < N; i += 32) { re[i] = 0.0; im[i] = 0.0; }
         return 1;
+    }
+    if (!POLAR && sp != nullptr && mode == M_PACKED && wmax == 0u && L == 32) {
+        // every residual zero: a nonzero code of component k is its anchor
+        const uint32_t nz0 = lane < G ? ~zw0 : 0u, nz1 = lane < G ? ~zw1 : 0u;
+        const uint32_t n0 = __reduce_add_sync(FULL, (uint32_t)__popc(nz0));
+        const uint32_t n1 = __reduce_add_sync(FULL, (uint32_t)__popc(nz1));
+        const uint32_t zsg = __reduce_or_sync(FULL, lane < G ? ((sw0 & zw0) | (sw1 & zw1)) : 0u);
+        const double zs = scale ? __dmul_rn(0.0, alpha) : 0.0;
+        if (n0 <= 1u && n1 <= 1u && n0 + n1 >= 1u && zsg == 0u && dbits(zs) == 0ull) {
+            const uint32_t gb0 = __ballot_sync(FULL, nz0 != 0u), gb1 = __ballot_sync(FULL, nz1 != 0u);
+            const int g0 = gb0 ? __ffs(gb0) - 1 : 0, g1 = gb1 ? __ffs(gb1) - 1 : 0;
+            const uint32_t m0 = __shfl_sync(FULL, nz0, g0), m1 = __shfl_sync(FULL, nz1, g1);
+            const int p0 = n0 ? g0 * 32 + __ffs(m0) - 1 : -1, p1 = n1 ? g1 * 32 + __ffs(m1) - 1 : -1;
+            const int p = n0 ? p0 : p1;
+            const uint32_t sg0 = (__shfl_sync(FULL, sw0, p >> 5) >> (p & 31)) & 1u;
+            const uint32_t sg1 = (__shfl_sync(FULL, sw1, p >> 5) >> (p & 31)) & 1u;
+            // the full decode's value at p (a zero component: +0, its sign clear)
+            auto value = [&](uint32_t n, unsigned long long q, uint32_t sg) {
+                double x;
+                if (!n) x = 0.0;
+                else if (s >= 32) x = __hiloint2double((int)(((uint32_t)q << (s - 32)) | (sg << 31)), 0);
+                else x = bitsd((q << s) | ((unsigned long long)sg << 63));
+                return scale ? __dmul_rn(x, alpha) : x;
+            };
+            const double x0 = value(n0, a0, sg0), x1 = value(n1, a1, sg1);
+            if (!(n0 && n1 && p0 != p1) && (dbits(x0) | dbits(x1)) != 0ull) {
+                if (lane == 0) { re[p] = x0; im[p] = x1; }
+                *sp = p;
+                return 2;
+            }
+        }
     }
     const uint32_t *data = reinterpret_cast<const uint32_t *>(b + doff);
     const uint32_t below = lanes_below();
@@ -1625,14 +1661,27 @@ __device__ __forceinline__ int wdecode_impl(const uint8_t *src, int c, double *r
 // so that the componentwise decoder keeps its registers.
 __device__ __noinline__ int wdecode_polar(const uint8_t *src, int c, double *re, double *im, double alpha,
                                           bool scale) {
-    return wdecode_impl<true>(src, c, re, im, alpha, scale);
+    return wdecode_impl<true>(src, c, re, im, alpha, scale, nullptr);
 }
 
 __device__ __forceinline__ int wdecode(const uint8_t *src, int c, double *re, double *im, double alpha,
                                        bool scale) {
     const uint32_t h0 = __ldg(reinterpret_cast<const uint32_t *>(src));
     if ((h0 & 0xFFu) >= (uint32_t)M_POLAR) return wdecode_polar(src, c, re, im, alpha, scale);
-    return wdecode_impl<false>(src, c, re, im, alpha, scale);
+    return wdecode_impl<false>(src, c, re, im, alpha, scale, nullptr);
+}
+
+// wdecode, with a stream of one amplitude decoded as that amplitude alone
+// (see wdecode_impl): 2 + its index p, the tile's other entries
+// unwritten; else wdecode's result.  Its own function, so that the
+// decoder of the other sweeps keeps its registers.  Warp-wide.
+__device__ __noinline__ int wdecode_one(const uint8_t *src, int c, double *re, double *im, double alpha,
+                                        bool scale) {
+    const uint32_t h0 = __ldg(reinterpret_cast<const uint32_t *>(src));
+    if ((h0 & 0xFFu) >= (uint32_t)M_POLAR) return wdecode_polar(src, c, re, im, alpha, scale);
+    int p = 0;
+    const int r = wdecode_impl<false>(src, c, re, im, alpha, scale, &p);
+    return r == 2 ? 2 + p : r;
 }
 
 struct EncodeOut {
@@ -2078,12 +2127,16 @@ __device__ __noinline__ bool polar_ladder(const double *re, const double *im, co
 // to the running norm.  wstage: 64 words of shared memory of this warp.
 // With one lossy level at shift >= 32 the tile is coded in one pass and
 // its values in shared memory are overwritten.
-template <bool POLAR>
+// PT: the tile is +0 but for the amplitude (pvr, pvi) at index pp, which
+// holds values that are zero or inside the lossy range (no uncompressed
+// storage forced, c >= 5, componentwise codec); re and im are not read.
+// The sizes, the stream and the norm are those of the full tile.
+template <bool POLAR, bool PT = false>
 __device__ __forceinline__ EncodeOut wencode_impl(double *re, double *im, const CodecCfg &cc,
                              unsigned long long tile, uint8_t *out_arena, unsigned long long out_cap,
                              unsigned long long *out_table, unsigned long long *part,
                              DevScalars *scal, unsigned sweep_id, uint32_t *wstage, int force_lv,
-                             PassAcc *acc) {
+                             PassAcc *acc, double pvr = 0.0, double pvi = 0.0, int pp = 0) {
     const int c = cc.c, N = 1 << c;
     const int G = N >= 32 ? N >> 5 : 1;
     const int L = N >= 32 ? 32 : N;
@@ -2094,8 +2147,23 @@ __device__ __forceinline__ EncodeOut wencode_impl(double *re, double *im, const 
     int nonfin = 0, inel = 0;
     unsigned long long nlo = 0, nhi = 0;
     unsigned rng = 0;
-    bool onepass = !cc.force_raw && !cc.polar && cc.nlev == 1 && cc.shifts[0] >= 32 && c >= 5;
-    if (onepass) {                           // every value zero or inside the lossy range?
+    bool onepass = !PT && !cc.force_raw && !cc.polar && cc.nlev == 1 && cc.shifts[0] >= 32 && c >= 5;
+    if (PT) {
+        // the words of size_levels for one amplitude: group pp >> 5 holds
+        // it (lane g: group g's words), no residual is nonzero, the anchors
+        // are its magnitudes
+        const unsigned long long B0 = dbits(pvr) & MAG, B1 = dbits(pvi) & MAG;
+        const uint32_t bit = 1u << (pp & 31);
+        const bool at = lane == (pp >> 5);
+        ls.wl0 = ls.wl1 = 0;
+        ls.nz = 0;
+        ls.sw0 = at && (dbits(pvr) >> 63) ? bit : 0u;
+        ls.sw1 = at && (dbits(pvi) >> 63) ? bit : 0u;
+        ls.zw0 = lane < G ? (at && B0 ? ~bit : FULL) : 0u;
+        ls.zw1 = lane < G ? (at && B1 ? ~bit : FULL) : 0u;
+        ls.f0 = B0;
+        ls.f1 = B1;
+    } else if (onepass) {                    // every value zero or inside the lossy range?
         bool odd = false;
         for (int i = lane; i < N; i += 32) {
             const uint32_t a = (uint32_t)__double2hiint(re[i]) & 0x7FFFFFFFu, al = (uint32_t)__double2loint(re[i]);
@@ -2107,7 +2175,7 @@ __device__ __forceinline__ EncodeOut wencode_impl(double *re, double *im, const 
     }
     if (onepass) {
         pack_onepass(re, im, cc.shifts[0], G, ls, nlo, nhi, rng, wstage);
-    } else if (!cc.force_raw) {
+    } else if (!PT && !cc.force_raw) {
         size_levels(re, im, cc, G, L, false, ls, nonfin, inel);
         nonfin = __any_sync(FULL, nonfin);
         inel = __any_sync(FULL, inel);
@@ -2245,7 +2313,7 @@ __device__ __forceinline__ EncodeOut wencode_impl(double *re, double *im, const 
                 if ((uint32_t)lane < nwd) (data + wo)[lane] = reinterpret_cast<const uint32_t *>(v + g * 32)[lane];
             }
         }
-        for (int k = 0; k < 2 && s >= 32 && !onepass; ++k) {
+        for (int k = 0; k < 2 && s >= 32 && !onepass && !PT; ++k) {
             // codes < 2^31 at shift >= 32: 32-bit codes, residuals and shuffles,
             // values spanning at most two words (the same bits as below)
             const double *v = k ? im : re;
@@ -2293,7 +2361,7 @@ __device__ __forceinline__ EncodeOut wencode_impl(double *re, double *im, const 
                 __syncwarp();
             }
         }
-        for (int k = 0; k < 2 && s < 32; ++k) {
+        for (int k = 0; k < 2 && s < 32 && !PT; ++k) {
             const double *v = k ? im : re;
             const uint32_t wk = k ? ws1 : ws0, offk = k ? off1 : off0;
             unsigned long long carry = quant(k ? ls.f1 : ls.f0, s);     // the anchor
@@ -2346,9 +2414,10 @@ __device__ __forceinline__ EncodeOut wencode_impl(double *re, double *im, const 
     } else {
         if (mode == M_RAW) {
             double2 *o = reinterpret_cast<double2 *>(b);
-            for (int i = lane; i < N; i += 32) o[i] = make_double2(re[i], im[i]);
+            for (int i = lane; i < N; i += 32)
+                o[i] = PT ? make_double2(i == pp ? pvr : 0.0, i == pp ? pvi : 0.0) : make_double2(re[i], im[i]);
         }
-        for (int i = lane; i < N && !onepass; i += 32) {       // (one pass: norm already taken)
+        for (int i = lane; i < N && !onepass && !PT; i += 32) {       // (one pass: norm already taken)
             unsigned long long u0 = dbits(re[i]) & MAG, u1 = dbits(im[i]) & MAG;
             if (mode == M_CONST) { u0 = quant(u0, s) << s; u1 = quant(u1, s) << s; }
             unsigned long long l0, h0, l1, h1;
@@ -2362,6 +2431,16 @@ __device__ __forceinline__ EncodeOut wencode_impl(double *re, double *im, const 
             add128(nlo, nhi, l0, h0);
             add128(nlo, nhi, l1, h1);
         }
+    }
+    if (PT && lane == 0) {
+        // the norm partial of the full tile: the amplitude's reconstruction
+        unsigned long long l0, h0, l1, h1;
+        const unsigned long long B0 = dbits(pvr) & MAG, B1 = dbits(pvi) & MAG;
+        sq_units(mode == M_RAW ? B0 : quant(B0, s) << s, l0, h0, rng);
+        sq_units(mode == M_RAW ? B1 : quant(B1, s) << s, l1, h1, rng);
+        add128(l0, h0, l1, h1);
+        nlo = l0;
+        nhi = h0;
     }
     warp_sum128(nlo, nhi);
     rng = __any_sync(FULL, rng);
@@ -2385,6 +2464,24 @@ __device__ __noinline__ EncodeOut wencode_polar(double *re, double *im, const Co
                                                 PassAcc *acc) {
     return wencode_impl<true>(re, im, cc, tile, out_arena, out_cap, out_table, part, scal, sweep_id, wstage,
                               force_lv, acc);
+}
+
+// Encode a tile that is +0 but for the amplitude (vr, vi) at index p,
+// exactly as wencode would, without reading the tile.  Tiles it does not
+// take (uncompressed storage forced, the POLAR variant, c < 5, a nonzero
+// component outside the lossy range) are left to wencode: false, nothing
+// written.  Warp-wide.
+__device__ __noinline__ bool wencode_point(double vr, double vi, int p, const CodecCfg &cc, unsigned long long tile,
+                                           uint8_t *out_arena, unsigned long long out_cap,
+                                           unsigned long long *out_table, unsigned long long *part,
+                                           DevScalars *scal, unsigned sweep_id, int force_lv, PassAcc *acc) {
+    const unsigned long long B0 = dbits(vr) & MAG, B1 = dbits(vi) & MAG;
+    const bool odd = (B0 != 0ull && (B0 < MIN_NORMAL || B0 >= LOSSY_LIMIT)) ||
+                     (B1 != 0ull && (B1 < MIN_NORMAL || B1 >= LOSSY_LIMIT));
+    if (cc.force_raw || cc.polar || cc.c < 5 || odd) return false;
+    wencode_impl<false, true>(nullptr, nullptr, cc, tile, out_arena, out_cap, out_table, part, scal, sweep_id,
+                              nullptr, force_lv, acc, vr, vi, p);
+    return true;
 }
 
 __device__ __forceinline__ EncodeOut wencode(double *re, double *im, const CodecCfg &cc, unsigned long long tile,
@@ -2578,6 +2675,181 @@ __device__ void wnorm(const double *re, const double *im, int N, unsigned long l
     warp_sum128(lo, hi);
 }
 
+// ---------------------------------------------------------------- point items, one per warp
+// A point item (every member tile +0 but for at most one amplitude, at a
+// tile index p common to the members) held as its 2^h amplitudes: entry j
+// of cre/cim is member j's amplitude at p.  The gates run on those entries
+// with the arithmetic of the item buffer's red = c pass, so the result is
+// the same.
+
+// apply_run (red = c) on the compact entries: lane j < 2^h takes member j.
+__device__ unsigned apply_run_point(double *cre, double *cim, int c, int h, const DRun &Rg, const SweepParams &P,
+                                    unsigned long long T, const int *hb, unsigned p) {
+    const DRun R = Rg;
+    const int j = threadIdx.x & 31, N = 1 << c;
+    unsigned ops = 0;
+    if (j >= (1 << h)) return 0;
+    const unsigned long long xb = member_tile(T, j, h, hb) << c;
+    bool have_t = false;
+    double tr = 0.0, ti = 0.0;
+    unsigned k = 0;
+    ops += run_factor(P.rgates + R.tg, R.nt, xb, have_t, tr, ti, k);
+    if (!(have_t || (k & 3u)) && R.nl == 0) return ops;          // nothing to visit
+    double xr = cre[j], xi = cim[j];
+    if (zero_amp(xr, xi)) return ops;                              // a zero stays as it is
+    k &= 3u;
+    bool have_l = false;
+    double lr = 0.0, li = 0.0;
+    if (R.nl) {
+        if (R.tabled) {
+            unsigned kap = 0;
+            for (int i = 0; i < R.nq; ++i) kap |= (unsigned)((xb >> R.q[i]) & 1ull) << i;
+            const unsigned long long e = R.table + (unsigned long long)kap * N + p;
+            const unsigned mt = P.rmeta[e];
+            have_l = mt & 1u;
+            k += mt >> 1;
+            if (have_l) {
+                const double2 v = P.rtab[e];
+                lr = v.x;
+                li = v.y;
+            }
+        } else {
+            ops += run_factor(P.rgates + R.lg, R.nl, xb | p, have_l, lr, li, k);
+        }
+    }
+    if (!have_t && !have_l && (k & 3u) == 0u) return ops;
+    if (have_t || have_l) {
+        double gr = have_t ? tr : lr, gi = have_t ? ti : li;
+        if (have_t && have_l) { cmul(tr, ti, lr, li, gr, gi); ops += 4; }
+        cmul(gr, gi, xr, xi, xr, xi);
+        ops += 4;
+    }
+    unit_pow(k, xr, xi);
+    cre[j] = xr;
+    cim[j] = xi;
+    return ops;
+}
+
+// One item of a sweep whose gates keep zeros as they are (runs, scaled
+// gates, permutations; the mixing ones on qubits >= c), on one warp with
+// no CTA barrier.  wre/wim: the warp's tile scratch (2^c each); cre/cim:
+// its 2^h entries; act: its activity words; wst: its packing stage.
+// Returns false, having written nothing, when the item is not a point item
+// (or holds a malformed stream): the CTA path takes it then.
+__device__ __noinline__ bool point_item_warp(const SweepParams &P, unsigned long long item, double alpha, bool scale,
+                                             double *wre, double *wim, double *cre, double *cim, unsigned *act,
+                                             uint32_t *wst, PassAcc *acc, unsigned &run_ops) {
+    const int lane = threadIdx.x & 31;
+    const int c = P.cc.c, N = 1 << c, h = P.h, ntl = 1 << h;
+    int hb[MAX_PAIRS];
+#pragma unroll
+    for (int i = 0; i < MAX_PAIRS; ++i) hb[i] = i < h ? P.H[i] - c : 0;
+    const unsigned long long T = expand_item(item, h, hb);
+    const unsigned long long fixed = T << c;
+    // which gates change something here; a run's activity on its first gate
+    bool any = false;
+    for (int w = 0; w < (P.ngates + 31) >> 5; ++w) {
+        const int g = (w << 5) + lane;
+        const bool a = g < P.ngates && gate_active(P.sgates[g], fixed);
+        const unsigned bal = __ballot_sync(FULL, a);
+        if (lane == 0) act[w] = bal;
+        any |= bal != 0u;
+    }
+    __syncwarp();
+    for (int r = 0; r < P.nruns && any; ++r) {
+        const DRun R = P.runs[P.run_first + r];
+        bool ra = false;
+        for (int g = R.first + lane; g < R.first + R.len; g += 32) ra |= (act[g >> 5] >> (g & 31)) & 1u;
+        ra = __any_sync(FULL, ra);
+        __syncwarp();
+        for (int g = R.first + lane; g < R.first + R.len; g += 32) {
+            const unsigned bit = 1u << (g & 31);
+            if (g == R.first && ra) atomicOr(&act[g >> 5], bit);
+            else atomicAnd(&act[g >> 5], ~bit);
+        }
+        __syncwarp();
+    }
+    if (!any && !scale) {
+        for (int j = 0; j < ntl; ++j)
+            wcarry(P.in_arena, P.in_table, member_tile(T, j, h, hb), P.out_arena, P.out_cap, P.out_table, P.part,
+                   P.scal, P.sweep_id, acc);
+        if (lane == 0) atomicAdd(&P.scal->items_skipped, 1ull);
+        return true;
+    }
+    // members' amplitudes; every other entry must be +0
+    int pos = -1;
+    for (int j = 0; j < ntl; ++j) {
+        const int r = wdecode_one(P.in_arena + P.in_table[member_tile(T, j, h, hb)], c, wre, wim, alpha, scale);
+        if (r == 1) return false;
+        int at = -1;
+        if (r >= 2) {
+            at = r - 2;
+        } else {
+            __syncwarp();
+            unsigned cnt = 0;
+            for (int b = 0; b < N; b += 32) {
+                const int i = b + lane;
+                const bool v = (unsigned long long)(__double_as_longlong(wre[i]) | __double_as_longlong(wim[i])) != 0ull;
+                const unsigned bal = __ballot_sync(FULL, v);
+                cnt += (unsigned)__popc(bal);
+                if (bal) at = b + 31 - __clz(bal);
+            }
+            if (cnt > 1u) return false;
+        }
+        __syncwarp();
+        double vr = 0.0, vi = 0.0;
+        if (at >= 0) {
+            if (pos >= 0 && pos != at) return false;
+            pos = at;
+            vr = wre[at];
+            vi = wim[at];
+        }
+        __syncwarp();
+        if (lane == 0) { cre[j] = vr; cim[j] = vi; }
+    }
+    __syncwarp();
+    const unsigned roff = pos > 0 ? (unsigned)pos : 0u;
+    if (any) {
+        for (int i = 0; i < P.nglist; ++i) {
+            const int g = P.glist[i];
+            if (!((act[g >> 5] >> (g & 31)) & 1u)) continue;
+            SGate s = P.sgates[g];
+            if (s.run != -1) {
+                if (s.run >= 0) run_ops += apply_run_point(cre, cim, c, h, P.runs[s.run], P, T, hb, roff);
+                __syncwarp();
+                continue;
+            }
+            // the gate on the 2^h entries: its buffer bits (all >= c in
+            // such a sweep) lowered by c
+            if (s.p0 >= 0) s.p0 = (int8_t)(s.p0 - c);
+            if (s.p1 >= 0) s.p1 = (int8_t)(s.p1 - c);
+            for (int q = 0; q < s.nins; ++q) s.ins[q] = (uint8_t)(s.ins[q] - c);
+            s.lcm >>= c;
+            s.lcv >>= c;
+            if (s.kind == 0) diag_gate(cre, cim, h, s, fixed, 0, 0u, (unsigned)lane, 32u);
+            else if (s.kind == 1) run_ops += one_target(cre, cim, h, s, P.gates[g], 0, 0u, (unsigned)lane, 32u);
+            else run_ops += two_target(cre, cim, h, s, P.gates[g], 0, 0u, (unsigned)lane, 32u);
+            __syncwarp();
+        }
+    }
+    for (int j = 0; j < ntl; ++j) {
+        const unsigned long long Tj = member_tile(T, j, h, hb);
+        const int flv = P.unit_level ? (int)P.unit_level[Tj >> P.unit_shift] : -1;
+        const double vr = cre[j], vi = cim[j];
+        if (wencode_point(vr, vi, (int)roff, P.cc, Tj, P.out_arena, P.out_cap, P.out_table, P.part, P.scal,
+                          P.sweep_id, flv, acc))
+            continue;
+        for (int i = lane; i < N; i += 32) {
+            wre[i] = i == (int)roff ? vr : 0.0;
+            wim[i] = i == (int)roff ? vi : 0.0;
+        }
+        __syncwarp();
+        wencode(wre, wim, P.cc, Tj, P.out_arena, P.out_cap, P.out_table, P.part, P.scal, P.sweep_id, wst, flv, acc);
+    }
+    if (lane == 0) atomicAdd(&P.scal->items_done, 1ull);
+    return true;
+}
+
 // ---------------------------------------------------------------- kernels
 // Sweeps of Algorithm 2 over all items of a work list: entry e of plist is
 // one sweep of one state, owning the global item indices istart[e] ..
@@ -2607,21 +2879,72 @@ __global__ void __launch_bounds__(NT, MINB) sweep_kernel(const SweepParams *__re
     __shared__ RunMember s_mem[1 << MAX_PAIRS];
     __shared__ unsigned long long s_rundp;
     __shared__ PassAcc s_acc;
+    constexpr int NWARPS = NT / 32;
+    __shared__ unsigned long long s_defer[NWARPS];    // items handed back by the warps (~0: none)
+    __shared__ int s_dn, s_wm;
     const unsigned long long total = istart[nlist];
     if (threadIdx.x == 0) {
         s_rundp = 0;
         s_acc.lo = s_acc.hi = s_acc.over = 0;
         for (int lv = 0; lv < MAX_LEVELS; ++lv) s_acc.hist[lv] = 0;
+        s_dn = NWARPS;
     }
     unsigned run_ops = 0;                 // FP64 instructions of diagonal runs (this thread)
-    constexpr int NWARPS = NT / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int cur = -1;
     uint32_t *wst = nullptr;              // the warp's packing stage, after the item buffer
+    if (!SIZING && nlist == 1) {
+        // A single state's sweep whose gates keep zeros as they are: its
+        // point items run one per warp, with no CTA barrier, until the
+        // items run out or the warp meets an item that is not a point item
+        // (handed back to the CTA loop below, which takes it first).
+        {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(plist);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&P);
+            for (int i = threadIdx.x; i < (int)(sizeof(SweepParams) / 4); i += NT) dst[i] = src[i];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_chunk = -1;
+            s_skip = *((volatile unsigned *)&P.scal->err) != 0u;
+            s_alpha = P.use_alpha ? P.scal->alpha : 1.0;
+            if (P.dscale) s_alpha = __dmul_rn(s_alpha, *P.dscale);
+            const int c = P.cc.c, mb = c + P.h;
+            // per warp: a tile (2^(c+1) doubles), 2^h entries of each
+            // component (32 doubles at most) and the activity words (8)
+            const bool fits = (long long)NWARPS * ((2ll << c) + 40) <= (2ll << mb);
+            s_wm = P.point_ok && !P.moves_tiles && !P.every_item && !s_skip && c >= 5 && fits;
+            if (s_wm) s_dn = 0;
+        }
+        __syncthreads();
+        cur = 0;
+        if (s_wm) {
+            const int N = 1 << P.cc.c;
+            double *wre = smem + warp * (2 * N + 40), *wim = wre + N, *cre = wim + N, *cim = cre + 16;
+            unsigned *wact = reinterpret_cast<unsigned *>(cim + 16);
+            wst = reinterpret_cast<uint32_t *>(smem + (2 << (P.cc.c + P.h))) + 64 * warp;
+            const double alpha = s_alpha;
+            unsigned long long mine = ~0ull;
+            for (;;) {
+                unsigned long long g = 0;
+                if (lane == 0) g = atomicAdd(work, 1ull);
+                g = shfl64(g, 0);
+                if (g >= total) break;
+                if (!point_item_warp(P, g - istart[0], alpha, alpha != 1.0, wre, wim, cre, cim, wact, wst, &s_acc,
+                                     run_ops)) {
+                    mine = g;
+                    break;
+                }
+            }
+            if (lane == 0) s_defer[warp] = mine;
+        }
+    }
     for (;;) {
         __syncthreads();                  // previous item finished by every warp
         if (threadIdx.x == 0) {           // next item; entry owning it: last e with istart[e] <= gi
-            const unsigned long long g = atomicAdd(work, 1ull);
+            // items handed back by the warps first, then the counter
+            while (s_dn < NWARPS && s_defer[s_dn] == ~0ull) ++s_dn;
+            const unsigned long long g = s_dn < NWARPS ? s_defer[s_dn++] : atomicAdd(work, 1ull);
             int lo = 0, hi = nlist - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;

@@ -116,3 +116,20 @@ def test_items_that_are_not_point_items():
             psi[l] = complex(-0.0, -0.0)
     run_pair(n, c, gates, "lossless", 0.0, psi=psi)
     run_pair(n, c, gates, "rel", 1e-4, psi=psi)
+
+
+def test_point_items_under_a_negative_scale():
+    """A scaled gate whose common factor is negative (-H) makes the decode
+    scale negative, so exact zeros decode to -0: such items are not point
+    items, and the streams still equal the oracle's; later sweeps of the
+    same circuit (positive scale again) take the point path."""
+    n, c = 12, 8
+    rng = np.random.default_rng(7)
+    hi = list(range(c, n))
+    x = I.seeded_basis(n, 5)
+    gates = [I.h(hi[0]), I.cphase(0.3, hi[0], 2), I.Gate(-I.MAT_H, (hi[1],), name="mH"),
+             I.cphase(-1.1, hi[1], hi[0]), I.cphase(0.9, 3, hi[1])]
+    gates += point_sweep_gates(n, c, rng)
+    for hmax in (4, 2):
+        run_pair(n, c, gates, "rel", 1e-4, x=x, hmax=hmax)
+        run_pair(n, c, gates, "lossless", 0.0, x=x, hmax=hmax)
