@@ -305,3 +305,52 @@ def test_relative_bound_hundred_million_values():
     # a truncating quantiser would exceed the bound by up to a factor 2
     bad = sum(oracle.check_bound(s, 2_000_000, 0x5EED + s) for s in range(1, 53))
     assert bad == 0
+
+
+def _sections_end(stream: bytes, G: int) -> int:
+    """Body offset after the four word sections (signs re/im, zeros re/im)."""
+    w0, = struct.unpack_from("<I", stream, 0)
+    w6, = struct.unpack_from("<I", stream, 24)
+    modes = [(w0 >> 24) & 7, (w0 >> 27) & 7, (w6 >> 8) & 7, (w6 >> 11) & 7]
+    off = 0
+    for m in modes:
+        if m in (2, 3):          # exceptions: a bitmap word, then one word per set bit
+            bm, = struct.unpack_from("<I", stream, 32 + off)
+            off += 4 + 4 * bin(bm & ((1 << G) - 1)).count("1")
+        elif m == 4:             # every word
+            off += 4 * G
+    return off
+
+
+@pytest.mark.parametrize("s", [0, 21, 39, 52])
+def test_one_amplitude_stream_is_its_anchors(s):
+    """A tile that is +0 but for one amplitude: the first nonzero value of a
+    component is coded against itself, so every residual and every width
+    byte is zero and the header's anchors hold the amplitude's codes (the
+    property a decoder may use to read such a tile from its header and
+    sections alone)."""
+    c = 8
+    G = (1 << c) >> 5
+    rng = np.random.default_rng(s)
+    for pos in (0, 31, 32, 200, 255):
+        for v in (complex(rng.normal(), rng.normal()), complex(-abs(rng.normal()), 0.0),
+                  complex(0.0, rng.normal())):
+            a = np.zeros(1 << c, dtype=np.complex128)
+            a[pos] = v
+            stream, _, _ = oracle.encode_tile(a, c, [s])
+            assert stream[0] == 1                                   # PACKED
+            body, = struct.unpack_from("<I", stream, 4)
+            assert len(stream) == 32 + body
+            a0, a1 = struct.unpack_from("<QQ", stream, 8)
+            for comp, anc in ((v.real, a0), (v.imag, a1)):
+                B = bits(comp) & ((1 << 63) - 1)
+                q = B if s == 0 else (B + (1 << (s - 1))) >> s
+                assert anc == q
+            off = _sections_end(stream, G)
+            widths = stream[32 + off: 32 + off + 2 * G]
+            assert widths == bytes(2 * G)
+            assert stream[32 + off:] == bytes(len(stream) - 32 - off)   # no data words
+            back = oracle.decode_tile(stream, c)
+            assert np.count_nonzero(back) == 1
+            others = np.delete(back, pos)
+            assert not np.any(others.view(np.uint64))                # every other entry +0
